@@ -1,0 +1,153 @@
+/*
+ * tmg -- time multigrid for DG-in-time discretisations on one GB300 (sm_103a).
+ *
+ * C ABI of the GPU library libtmg.so.  Plain pointers and sizes only; every
+ * array argument of tmg_solve / tmg_cycle / tmg_residual is a DEVICE pointer
+ * on the plan's CUDA stream unless its name ends in _host.
+ *
+ * The problem (Gander & Neumueller, arXiv:1409.5254, Section 2, eq.
+ * chap4_generalLinearSystemODE, generalised to u' + lambda u = f):
+ *
+ *   (K + z Mhat) u_n = f_n + N u_{n-1},  n = 1..N,  z = lambda * tau,
+ *
+ * with the degree-p_t shifted Legendre basis psi_k(s) = P_k(2s - 1) on each
+ * interval, K the upwind DG stiffness block, Mhat the reference mass matrix,
+ * N = a b^T (a_k = psi_k(0) = (-1)^k, b_l = psi_l(1) = 1) and u_0 := the initial
+ * value.  Array layout: interval-major [N][p_t + 1] float64, i.e. element
+ * (n, k) (0-based interval n, Legendre coefficient k) at offset n*(p_t+1)+k.
+ * The right-hand side f is the assembled load vector f_n[k] = int f psi_k^n dt
+ * (Section 2, definition of the right-hand sides); the initial value enters as
+ * a*u0 in the first interval inside the library (f is never modified).
+ *
+ * The solver is the paper's multigrid in time (Section 3): damped block Jacobi
+ * smoothing (eq. chap4_ODESmoother) with the damping omega* of Lemma
+ * chap4_lemma7 per level, restriction R = [R1 R2] and prolongation P = R^T
+ * (eqs. chap4_restrictionTime, chap4_prolongationTime), V- or W-cycles on
+ * factor-2 coarsened meshes (eq. chap4_errorTwoGridCycle), and an exact
+ * coarsest solve by a parallel prefix scan over affine interval maps.  Each
+ * cycle is a correction step: r = F - L u in FP64, one cycle on L c = r in
+ * the cycle precision (FP64, or FP32 for TMG_MIXED), u += c in FP64.  The
+ * stopping test is ||F - L u||_2 <= tol * ||F||_2 evaluated in FP64.
+ *
+ * Errors: every function returns a tmg_status; nothing aborts or exits.  A
+ * failed CUDA call returns TMG_ECUDA (the CUDA error is kept, see
+ * tmg_last_cuda_error).  Plans are not thread-safe; use one plan per host
+ * thread or serialise calls.
+ */
+#ifndef TMG_H
+#define TMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tmg_plan tmg_plan;
+
+typedef enum {
+    TMG_OK = 0,
+    TMG_EINVAL = 1,     /* bad argument (see tmg_setup for the rules) */
+    TMG_ENOMEM = 2,     /* device or host allocation failed */
+    TMG_ECUDA = 3,      /* a CUDA runtime call failed */
+    TMG_ENOTCONV = 4,   /* max_cycles reached before tol; u holds the last iterate */
+    TMG_ENUMERIC = 5,   /* a residual norm was NaN or Inf */
+    TMG_ETIMEOUT = 6,   /* a bounded device-side wait ran out */
+    TMG_EUNSUPPORTED = 7 /* valid request this build does not implement */
+} tmg_status;
+
+enum { TMG_FP64 = 0, TMG_MIXED = 1 };
+
+typedef struct {
+    double tol;         /* relative residual target ||F-Lu||/||F|| (default 1e-10) */
+    int max_cycles;     /* cycle limit (default 100) */
+    int nu1, nu2;       /* pre/post smoothing sweeps (default 1, 1); 0..8 */
+    int gamma;          /* 1 = V-cycle, 2 = W-cycle (default 1) */
+    int precision;      /* TMG_FP64 or TMG_MIXED (default TMG_MIXED) */
+    int64_t n_min;      /* coarsen while N_l is even and N_l > n_min (default 64) */
+    int use_graph;      /* 1: whole solve as one CUDA graph launch (default 1) */
+    int initial_guess;  /* 1: tmg_solve starts from the u passed in (default 0: u = 0) */
+    int64_t tail_cap;   /* most intervals the on-chip coarse solver takes (0: default 8192);
+                           smaller values move more levels to the streaming kernels */
+} tmg_opts;
+
+/* Fill *opts with the defaults listed above. */
+void tmg_opts_default(tmg_opts *opts);
+
+/*
+ * Build a plan for one problem: degree p_t in {0,1,2,3}, step tau > 0,
+ * lambda >= 0 (finite), N >= 1 intervals.  levels <= 0 picks the hierarchy
+ * from opts->n_min; levels >= 1 caps the number of levels.  omega <= 0 uses
+ * omega*(alpha(lambda tau_l)) per level (Lemma chap4_lemma7); 0 < omega < 2
+ * uses that damping on every level (omega in (1,2) converges but not
+ * uniformly, remark after Theorem chap4_theorem3).  stream is a cudaStream_t
+ * (NULL = legacy default stream).  All setup arithmetic is FP64 on the host
+ * (block inverses, alpha, omega*, transfer matrices); the library allocates
+ * and owns every workspace.  Returns TMG_EINVAL for bad arguments,
+ * TMG_EUNSUPPORTED if the coarsest level is larger than the on-chip coarse
+ * solver holds, TMG_ENOMEM / TMG_ECUDA on allocation failure.
+ */
+tmg_status tmg_setup(tmg_plan **plan, int p_t, double tau, double lambda, int64_t N, int levels,
+                     double omega, const tmg_opts *opts, void *stream);
+
+/*
+ * Solve L u = F.  f: device [N][p_t+1] load vector (read only); u0: initial
+ * value; u: device [N][p_t+1] output (input too when opts->initial_guess).
+ * f and u must be 16-byte aligned and must not overlap.  Returns TMG_OK when
+ * the FP64 relative residual reached tol, TMG_ENOTCONV after max_cycles.
+ * Synchronises the plan's stream before returning.
+ */
+tmg_status tmg_solve(tmg_plan *plan, const double *f, double u0, double *u);
+
+/*
+ * Same solve with HOST arrays: copies f_host to the device, solves, copies u
+ * back (all on the plan's stream, inside the call).  Pinned host memory gives
+ * full copy bandwidth; pageable memory works too.
+ */
+tmg_status tmg_solve_host(tmg_plan *plan, const double *f_host, double u0, double *u_host);
+
+/*
+ * Apply exactly one correction cycle to u in place (no convergence test):
+ * u <- u + C (F - L u) with C one V/W-cycle in the plan's precision.
+ */
+tmg_status tmg_cycle(tmg_plan *plan, const double *f, double u0, double *u);
+
+/* r = F - L u (FP64, device arrays [N][p_t+1]); F is f with a*u0 folded in. */
+tmg_status tmg_residual(tmg_plan *plan, const double *f, double u0, const double *u, double *r);
+
+/*
+ * Statistics of the last tmg_solve: number of cycles applied, final relative
+ * residual, and up to hist_len entries of the residual history
+ * (hist[k] = ||F - L u_k|| / ||F||, k = 0..cycles).  Any pointer may be NULL.
+ */
+tmg_status tmg_stats(const tmg_plan *plan, int *cycles, double *rel_res, double *hist, int hist_len);
+
+/* Level count and the first level handled by the on-chip coarse solver. */
+tmg_status tmg_plan_info(const tmg_plan *plan, int *num_levels, int *tail_level, int64_t *tail_intervals,
+                         double *omega_per_level, int omega_len);
+
+/*
+ * Copy one of the plan's internal level vectors to host memory (inspection
+ * and testing; synchronises the stream).  which: 0 = right-hand side f_l,
+ * 1 = correction u_l of level l (levels 0..tail level), 2 = the level-0
+ * residual r (level ignored).  The vector holds N_l*(p_t+1) values of the
+ * cycle precision (8-byte double for TMG_FP64, 4-byte float for TMG_MIXED);
+ * bytes must be at least that size.
+ */
+tmg_status tmg_inspect(const tmg_plan *plan, int which, int level, void *host_dst, size_t bytes);
+
+/* Release the plan and every resource it owns.  NULL is ignored. */
+void tmg_destroy(tmg_plan *plan);
+
+/* Static text for a status code. */
+const char *tmg_strerror(tmg_status status);
+
+/* Last CUDA error code seen by the library in this process (0 if none). */
+int tmg_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TMG_H */

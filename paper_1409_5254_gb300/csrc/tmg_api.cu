@@ -1,0 +1,521 @@
+// C ABI of the time-multigrid library: plan set-up (FP64 host arithmetic),
+// workspaces, the CUDA-graph solve loop, and the public entry points.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "tmg_plan.h"
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+tmg_status cuda_fail(cudaError_t e) {
+    g_last_cuda = (int)e;
+    return TMG_ECUDA;
+}
+
+#define TMG_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t _e = (call);                        \
+        if (_e != cudaSuccess) return cuda_fail(_e);    \
+    } while (0)
+
+// ------------------------------------------------ FP64 set-up arithmetic --
+//
+// Shifted Legendre basis psi_k(s) = P_k(2s-1) on the reference interval.
+// Legendre identities give the local matrices of Section 2 in closed form:
+//   K[k,l] = 1 - 2 [l < k and k + l odd]   (from P_k(1) = 1 and the expansion of P_k')
+//   Mhat   = diag(1 / (2k + 1))             (orthogonality)
+//   a_k    = P_k(-1) = (-1)^k,  b_l = P_l(1) = 1.
+
+void local_blocks(int d, double z, double* A) {
+    for (int k = 0; k < d; ++k)
+        for (int l = 0; l < d; ++l) {
+            double v = (l < k && ((k + l) & 1)) ? -1.0 : 1.0;
+            if (k == l) v += z / (2.0 * k + 1.0);
+            A[k * d + l] = v;
+        }
+}
+
+// Gauss-Jordan inversion with partial pivoting; returns false if singular.
+bool invert(int d, const double* A, double* Ainv) {
+    double M[4][8];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < 2 * d; ++j) M[i][j] = j < d ? A[i * d + j] : (j - d == i ? 1.0 : 0.0);
+    for (int c = 0; c < d; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < d; ++r)
+            if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+        if (M[piv][c] == 0.0) return false;
+        if (piv != c)
+            for (int j = 0; j < 2 * d; ++j) {
+                double t = M[c][j];
+                M[c][j] = M[piv][j];
+                M[piv][j] = t;
+            }
+        const double inv = 1.0 / M[c][c];
+        for (int j = 0; j < 2 * d; ++j) M[c][j] *= inv;
+        for (int r = 0; r < d; ++r) {
+            if (r == c || M[r][c] == 0.0) continue;
+            const double m = M[r][c];
+            for (int j = 0; j < 2 * d; ++j) M[r][j] -= m * M[c][j];
+        }
+    }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) Ainv[i * d + j] = M[i][j + d];
+    return true;
+}
+
+void level_setup(int d, double z, double omega_user, tmg_level_host* L) {
+    L->z = z;
+    local_blocks(d, z, L->A);
+    invert(d, L->A, L->Ainv);
+    double al = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double gk = 0.0, ck = 0.0;
+        for (int l = 0; l < d; ++l) {
+            gk += L->Ainv[k * d + l] * ((l & 1) ? -1.0 : 1.0);   // A^{-1} a
+            ck += L->Ainv[l * d + k];                              // (b^T A^{-1})_k
+        }
+        L->g[k] = gk;
+        L->c[k] = ck;
+        al += gk;                                                  // b^T A^{-1} a
+    }
+    L->alpha = al;
+    // Lemma chap4_lemma7: omega* = 1/(1+alpha^2) for alpha >= 0, else 1
+    L->omega = omega_user > 0.0 ? omega_user : (al >= 0.0 ? 1.0 / (1.0 + al * al) : 1.0);
+}
+
+// Prolongation matrices of Section 4.2: column k of P1 (P2) holds the Legendre
+// coefficients, on the fine interval, of coarse basis function k restricted to
+// the first (second) half.  With x the fine variable on [-1,1] the coarse
+// argument is (x - 1)/2 on the first half and (x + 1)/2 on the second, so the
+// columns follow from composing P_k with that affine map and converting the
+// monomial coefficients back to the Legendre basis (exact polynomial algebra).
+void transfer_setup(int d, double* P1, double* P2) {
+    double leg[4][4] = {{0}};   // monomial coefficients of P_0..P_3
+    leg[0][0] = 1.0;
+    if (d > 1) leg[1][1] = 1.0;
+    for (int k = 1; k + 1 < d; ++k)   // (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}
+        for (int j = 0; j < 4; ++j) {
+            double v = -k * leg[k - 1][j];
+            if (j > 0) v += (2.0 * k + 1.0) * leg[k][j - 1];
+            leg[k + 1][j] = v / (k + 1.0);
+        }
+    for (int half = 0; half < 2; ++half) {
+        const double shift = half == 0 ? -1.0 : 1.0;
+        double* P = half == 0 ? P1 : P2;
+        for (int k = 0; k < d; ++k) {
+            // q(x) = P_k((x + shift) / 2) in monomials
+            double q[4] = {0, 0, 0, 0};
+            for (int j = 0; j < d; ++j) {
+                if (leg[k][j] == 0.0) continue;
+                // ((x + shift)/2)^j = 2^-j sum_i C(j,i) x^i shift^(j-i)
+                double binom = 1.0;
+                for (int i = 0; i <= j; ++i) {
+                    if (i > 0) binom = binom * (j - i + 1) / i;
+                    q[i] += leg[k][j] * ldexp(binom * pow(shift, j - i), -j);
+                }
+            }
+            // convert to Legendre coefficients, highest degree first
+            for (int j = d - 1; j >= 0; --j) {
+                const double cj = q[j] / leg[j][j];
+                P[j * d + k] = cj;
+                for (int i = 0; i <= j; ++i) q[i] -= cj * leg[j][i];
+            }
+        }
+    }
+}
+
+// Same hierarchy rule as the textbook cycle: coarsen while the level has an
+// even number of intervals, more than n_min of them, and the level cap allows.
+int count_levels(int64_t N, int64_t n_min, int max_levels) {
+    int L = 1;
+    int64_t n = N;
+    while ((max_levels <= 0 || L < max_levels) && n % 2 == 0 && n > n_min && L < tmg::kMaxLevels) {
+        n /= 2;
+        ++L;
+    }
+    return L;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+const size_t kTailSmemMax = 200 * 1024;
+const int64_t kTailNmax = 8192;
+
+tmg_status build_graph(tmg_plan* P) {
+    cudaGraph_t g = nullptr;
+    TMG_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    // cudaGraphNodeParams has no default constructor: zero a raw buffer instead
+    alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+    memset(np_buf, 0, sizeof(np_buf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(P->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    cudaError_t ek = P->ops->enqueue_cycle(P);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(P->s, &captured);
+    if (ek != cudaSuccess || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(ek != cudaSuccess ? ek : e);
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    P->graph = g;
+    P->gexec = ex;
+    P->cond = (unsigned long long)h;
+    return TMG_OK;
+}
+
+// Start-of-solve state: written through the pinned mirror with one copy.
+tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, double tol, int max_cycles,
+                       int use_cond, int nF_from_first) {
+    tmg::DevState* h = P->st_host;
+    TMG_CUDA(cudaStreamSynchronize(P->s));    // the mirror may still be read by a previous copy
+    h->F = f;
+    h->u = u;
+    h->u0 = u0;
+    h->nF = 0.0;
+    h->tol = tol;
+    h->max_cycles = max_cycles;
+    h->cycle = 0;
+    h->done = 0;
+    h->nF_from_first = nF_from_first;
+    h->use_cond = use_cond;
+    h->ticket = 0u;
+    h->cond = P->cond;
+    TMG_CUDA(cudaMemcpyAsync(P->st, h, offsetof(tmg::DevState, hist), cudaMemcpyHostToDevice, P->s));
+    return TMG_OK;
+}
+
+tmg_status check_ptr(const void* p) {
+    if (p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) != 0) return TMG_EINVAL;
+    return TMG_OK;
+}
+
+tmg_status run_solve(tmg_plan* P, const double* f, double u0, double* u) {
+    if (check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    const int use_graph = P->o.use_graph != 0;
+    if (use_graph && P->gexec == nullptr) {
+        tmg_status s = build_graph(P);
+        if (s != TMG_OK) return s;
+    }
+    tmg_status s = stage_state(P, f, u0, u, P->o.tol, P->o.max_cycles, use_graph, P->o.initial_guess ? 0 : 1);
+    if (s != TMG_OK) return s;
+    if (P->o.initial_guess) {
+        TMG_CUDA(P->ops->enqueue_normF(P));
+    } else {
+        TMG_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * P->N * P->d, P->s));
+    }
+    if (use_graph) {
+        TMG_CUDA(cudaGraphLaunch(P->gexec, P->s));
+    } else {
+        // eager loop: a few cycles per host check; kernels after convergence return at once
+        for (int k = 0; k <= P->o.max_cycles;) {
+            const int batch = 4;
+            for (int i = 0; i < batch && k <= P->o.max_cycles; ++i, ++k) TMG_CUDA(P->ops->enqueue_cycle(P));
+            TMG_CUDA(cudaMemcpyAsync(&P->st_host->done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, P->s));
+            TMG_CUDA(cudaStreamSynchronize(P->s));
+            if (P->st_host->done) break;
+        }
+    }
+    TMG_CUDA(cudaMemcpyAsync(P->st_host, P->st, sizeof(tmg::DevState), cudaMemcpyDeviceToHost, P->s));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    const tmg::DevState* h = P->st_host;
+    const int nres = h->cycle;    // residual evaluations
+    P->last_cycles = nres > 0 ? nres - 1 : 0;
+    const int nh = nres < tmg::kHist ? nres : tmg::kHist;
+    P->last_hist.assign(h->hist, h->hist + nh);
+    P->last_rel = nh > 0 ? h->hist[nh - 1] : NAN;
+    switch (h->done) {
+        case 1: return TMG_OK;
+        case 2: return TMG_ENOTCONV;
+        case 3: return TMG_ENUMERIC;
+        default: return TMG_ETIMEOUT;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void tmg_opts_default(tmg_opts* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_cycles = 100;
+    o->nu1 = 1;
+    o->nu2 = 1;
+    o->gamma = 1;
+    o->precision = TMG_MIXED;
+    o->n_min = 64;
+    o->use_graph = 1;
+    o->initial_guess = 0;
+    o->tail_cap = 0;
+}
+
+tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_t N, int levels, double omega,
+                     const tmg_opts* opts, void* stream) {
+    if (plan == nullptr) return TMG_EINVAL;
+    *plan = nullptr;
+    tmg_opts o;
+    tmg_opts_default(&o);
+    if (opts) o = *opts;
+    if (p_t < 0 || p_t > 3 || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
+        !(omega < 2.0) || !isfinite(omega) || o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 ||
+        o.gamma < 1 || o.gamma > 2 || (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 ||
+        o.max_cycles < 0 || o.max_cycles >= tmg::kHist || !(o.tol >= 0.0))
+        return TMG_EINVAL;
+
+    tmg_plan* P = new (std::nothrow) tmg_plan();
+    if (!P) return TMG_ENOMEM;
+    P->p = p_t;
+    P->d = p_t + 1;
+    P->tau = tau;
+    P->lambda = lambda;
+    P->N = N;
+    P->omega_user = omega;
+    P->o = o;
+    P->s = static_cast<cudaStream_t>(stream);
+    P->own_stream = false;
+    if (P->s == nullptr) {
+        // The legacy default stream cannot be captured into a graph; a blocking
+        // stream created here is implicitly ordered with it.
+        cudaError_t se = cudaStreamCreate(&P->s);
+        if (se != cudaSuccess) {
+            delete P;
+            return cuda_fail(se);
+        }
+        P->own_stream = true;
+    }
+    P->ops = o.precision == TMG_MIXED ? tmg_ops_f32(P->d) : tmg_ops_f64(P->d);
+
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) {
+        tmg_destroy(P);
+        return cuda_fail(ce);
+    }
+    P->max_blocks = P->nsm * 8;
+
+    // hierarchy and FP64 constants
+    P->nlev = count_levels(N, o.n_min, levels);
+    P->lev.resize(P->nlev);
+    for (int l = 0; l < P->nlev; ++l) {
+        P->lev[l].N = N >> l;
+        level_setup(P->d, lambda * ldexp(tau, l), omega, &P->lev[l]);
+    }
+    transfer_setup(P->d, P->P1, P->P2);
+
+    // first level handled on chip: the largest that fits
+    P->lt = -1;
+    for (int l = 0; l < P->nlev; ++l) {
+        const size_t b = P->ops->tail_bytes(P->lev[l].N, P->nlev - l);
+        const int64_t cap = o.tail_cap > 0 && o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax;
+        if ((P->lev[l].N <= cap || l == P->nlev - 1) && P->lev[l].N <= kTailNmax && b <= kTailSmemMax) {
+            P->lt = l;
+            P->tail_smem = b;
+            break;
+        }
+    }
+    if (P->lt < 0 || (o.gamma == 2 && P->lt > 1)) {
+        tmg_destroy(P);
+        return TMG_EUNSUPPORTED;
+    }
+
+    // workspace: level vectors in the cycle precision, level-0 residual,
+    // tail constants, block partials, device state
+    const size_t el = P->ops->elem;
+    const size_t A = 256;
+    size_t off = 0;
+    size_t off_f[tmg::kMaxLevels], off_u[tmg::kMaxLevels];
+    for (int l = 0; l <= P->lt; ++l) {
+        off_f[l] = off;
+        off = align_up(off + el * P->lev[l].N * P->d, A);
+        off_u[l] = off;
+        off = align_up(off + el * P->lev[l].N * P->d, A);
+    }
+    const size_t off_r = off;
+    off = align_up(off + el * N * P->d, A);
+    const size_t off_lk = off;
+    off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
+    const size_t off_p = off;
+    off = align_up(off + sizeof(double) * P->max_blocks, A);
+    const size_t off_st = off;
+    off = align_up(off + sizeof(tmg::DevState), A);
+    P->ws_bytes = off;
+    ce = cudaMalloc(&P->ws, P->ws_bytes);
+    if (ce != cudaSuccess) {
+        P->ws = nullptr;
+        tmg_destroy(P);
+        g_last_cuda = (int)ce;
+        return TMG_ENOMEM;
+    }
+    char* base = static_cast<char*>(P->ws);
+    for (int l = 0; l <= P->lt; ++l) {
+        P->fl[l] = base + off_f[l];
+        P->ul[l] = base + off_u[l];
+    }
+    P->rT = base + off_r;
+    P->lk_dev = base + off_lk;
+    P->partials = reinterpret_cast<double*>(base + off_p);
+    P->st = reinterpret_cast<tmg::DevState*>(base + off_st);
+    ce = cudaMallocHost(&P->st_host, sizeof(tmg::DevState));
+    if (ce != cudaSuccess) {
+        P->st_host = nullptr;
+        tmg_destroy(P);
+        g_last_cuda = (int)ce;
+        return TMG_ENOMEM;
+    }
+    memset(P->st_host, 0, sizeof(tmg::DevState));
+    ce = cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->s);
+    // the attribute is per kernel, shared by every plan: set the common ceiling
+    if (ce == cudaSuccess) ce = P->ops->set_tail_attr(kTailSmemMax);
+    if (ce == cudaSuccess) ce = P->ops->upload(P);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->s);
+    if (ce != cudaSuccess) {
+        tmg_destroy(P);
+        return cuda_fail(ce);
+    }
+    *plan = P;
+    return TMG_OK;
+}
+
+tmg_status tmg_solve(tmg_plan* P, const double* f, double u0, double* u) {
+    if (!P || !isfinite(u0)) return TMG_EINVAL;
+    return run_solve(P, f, u0, u);
+}
+
+tmg_status tmg_solve_host(tmg_plan* P, const double* f_host, double u0, double* u_host) {
+    if (!P || !f_host || !u_host || !isfinite(u0)) return TMG_EINVAL;
+    const size_t bytes = sizeof(double) * P->N * P->d;
+    if (!P->F_dev) {
+        cudaError_t e = cudaMalloc(&P->F_dev, bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&P->u_dev, bytes);
+        if (e != cudaSuccess) {
+            g_last_cuda = (int)e;
+            return TMG_ENOMEM;
+        }
+    }
+    TMG_CUDA(cudaMemcpyAsync(P->F_dev, f_host, bytes, cudaMemcpyHostToDevice, P->s));
+    if (P->o.initial_guess) TMG_CUDA(cudaMemcpyAsync(P->u_dev, u_host, bytes, cudaMemcpyHostToDevice, P->s));
+    tmg_status s = run_solve(P, P->F_dev, u0, P->u_dev);
+    if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+    TMG_CUDA(cudaMemcpyAsync(u_host, P->u_dev, bytes, cudaMemcpyDeviceToHost, P->s));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return s;
+}
+
+tmg_status tmg_cycle(tmg_plan* P, const double* f, double u0, double* u) {
+    if (!P || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    tmg_status s = stage_state(P, f, u0, u, -1.0, 1 << 30, 0, 1);
+    if (s != TMG_OK) return s;
+    TMG_CUDA(P->ops->enqueue_cycle(P));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return TMG_OK;
+}
+
+tmg_status tmg_residual(tmg_plan* P, const double* f, double u0, const double* u, double* r) {
+    if (!P || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK || check_ptr(r) != TMG_OK)
+        return TMG_EINVAL;
+    TMG_CUDA(P->ops->enqueue_residual(P, f, u0, u, r));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return TMG_OK;
+}
+
+tmg_status tmg_stats(const tmg_plan* P, int* cycles, double* rel_res, double* hist, int hist_len) {
+    if (!P) return TMG_EINVAL;
+    if (cycles) *cycles = P->last_cycles;
+    if (rel_res) *rel_res = P->last_rel;
+    if (hist)
+        for (int i = 0; i < hist_len; ++i) hist[i] = i < (int)P->last_hist.size() ? P->last_hist[i] : NAN;
+    return TMG_OK;
+}
+
+tmg_status tmg_plan_info(const tmg_plan* P, int* num_levels, int* tail_level, int64_t* tail_intervals,
+                         double* omega_per_level, int omega_len) {
+    if (!P) return TMG_EINVAL;
+    if (num_levels) *num_levels = P->nlev;
+    if (tail_level) *tail_level = P->lt;
+    if (tail_intervals) *tail_intervals = P->lev[P->lt].N;
+    if (omega_per_level)
+        for (int i = 0; i < omega_len; ++i) omega_per_level[i] = i < P->nlev ? P->lev[i].omega : NAN;
+    return TMG_OK;
+}
+
+tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, size_t bytes) {
+    if (!P || !host_dst || which < 0 || which > 2) return TMG_EINVAL;
+    const void* src = nullptr;
+    int64_t n = P->N;
+    if (which == 2) {
+        src = P->rT;
+    } else {
+        if (level < 0 || level > P->lt || (level == 0 && which == 0)) return TMG_EINVAL;
+        src = which == 0 ? P->fl[level] : P->ul[level];
+        n = P->lev[level].N;
+    }
+    const size_t need = (size_t)n * P->d * P->ops->elem;
+    if (bytes < need) return TMG_EINVAL;
+    TMG_CUDA(cudaMemcpyAsync(host_dst, src, need, cudaMemcpyDeviceToHost, P->s));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return TMG_OK;
+}
+
+void tmg_destroy(tmg_plan* P) {
+    if (!P) return;
+    cudaStreamSynchronize(P->s);
+    if (P->gexec) cudaGraphExecDestroy(P->gexec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->ws) cudaFree(P->ws);
+    if (P->st_host) cudaFreeHost(P->st_host);
+    if (P->F_dev) cudaFree(P->F_dev);
+    if (P->u_dev) cudaFree(P->u_dev);
+    if (P->own_stream) cudaStreamDestroy(P->s);
+    delete P;
+}
+
+const char* tmg_strerror(tmg_status s) {
+    switch (s) {
+        case TMG_OK: return "ok";
+        case TMG_EINVAL: return "invalid argument";
+        case TMG_ENOMEM: return "out of memory";
+        case TMG_ECUDA: return "CUDA error";
+        case TMG_ENOTCONV: return "cycle limit reached before the tolerance";
+        case TMG_ENUMERIC: return "non-finite residual";
+        case TMG_ETIMEOUT: return "device-side wait timed out";
+        case TMG_EUNSUPPORTED: return "unsupported configuration";
+        default: return "unknown status";
+    }
+}
+
+int tmg_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

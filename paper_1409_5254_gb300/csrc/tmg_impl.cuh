@@ -1,0 +1,144 @@
+// Launch orchestration of one correction cycle for cycle precision T and D = p_t + 1.
+#pragma once
+
+#include "tmg_plan.h"
+
+namespace tmg {
+
+template <typename T, int D>
+LevelK<T, D> level_consts(const tmg_level_host& L) {
+    LevelK<T, D> K;
+    for (int i = 0; i < D * D; ++i) {
+        K.A[i] = (T)L.A[i];
+        K.Ainv[i] = (T)L.Ainv[i];
+    }
+    for (int i = 0; i < D; ++i) {
+        K.g[i] = (T)L.g[i];
+        K.c[i] = (T)L.c[i];
+    }
+    K.omega = (T)L.omega;
+    K.alpha = (T)L.alpha;
+    return K;
+}
+
+template <typename T, int D>
+Xfer<T, D> xfer_consts(const tmg_plan* P) {
+    Xfer<T, D> X;
+    for (int i = 0; i < D * D; ++i) {
+        X.P1[i] = (T)P->P1[i];
+        X.P2[i] = (T)P->P2[i];
+    }
+    return X;
+}
+
+inline Res0 res0_consts(const tmg_plan* P) {
+    Res0 R;
+    for (int k = 0; k < kMaxD; ++k) R.zm[k] = P->lev[0].z / (2.0 * k + 1.0);
+    return R;
+}
+
+// Halo lanes per warp tile: S sweeps that read e_{n-1} need ceil(S/2) lanes.
+inline int halo_lanes(int S) { return (S + 1) / 2; }
+inline int sweeps_down(int nu1) { return (nu1 > 0 ? nu1 - 1 : 0) + 1; }
+inline int sweeps_up(int nu1, int nu2) { return (nu1 > 0 ? nu1 - 1 : 0) + nu2; }
+
+inline int grid_for(const tmg_plan* P, int64_t nchunks, int H) {
+    const int64_t per = 32 - H;
+    const int64_t tiles = (nchunks + per - 1) / per;
+    int64_t blocks = (tiles + (kNT / 32) - 1) / (kNT / 32);
+    if (blocks > P->max_blocks) blocks = P->max_blocks;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+inline int grid_flat(const tmg_plan* P, int64_t n) {
+    int64_t blocks = (n + kNT - 1) / kNT;
+    if (blocks > P->max_blocks) blocks = P->max_blocks;
+    if (blocks < 1) blocks = 1;
+    return (int)blocks;
+}
+
+template <typename T, int D>
+struct Impl {
+    static size_t tail_bytes(int64_t Nt, int nl) { return tail_smem_bytes<T, D>(Nt, nl); }
+
+    static cudaError_t set_tail_attr(size_t bytes) {
+        return cudaFuncSetAttribute(k_tail<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    }
+
+    static cudaError_t upload(tmg_plan* P) {
+        const int nl = P->nlev - P->lt;
+        std::vector<LevelK<T, D>> lk(nl);
+        for (int j = 0; j < nl; ++j) lk[j] = level_consts<T, D>(P->lev[P->lt + j]);
+        return cudaMemcpyAsync(P->lk_dev, lk.data(), sizeof(LevelK<T, D>) * nl, cudaMemcpyHostToDevice, P->s);
+    }
+
+    static cudaError_t enqueue_cycle(tmg_plan* P) {
+        const int nu1 = P->o.nu1, nu2 = P->o.nu2;
+        const Xfer<T, D> X = xfer_consts<T, D>(P);
+        const Res0 R = res0_consts(P);
+        const int nl = P->nlev - P->lt;
+        const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(P->lk_dev);
+        T* rT = static_cast<T*>(P->rT);
+        if (P->lt == 0) {
+            k_res0<T, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(rT, P->N, R, P->partials, P->st);
+            k_tail<T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N, nu1,
+                                                             nu2, P->o.gamma, P->st);
+            k_update0<T><<<grid_flat(P, P->N * D), kNT, 0, P->s>>>(static_cast<const T*>(P->ul[0]), P->N * D,
+                                                                    P->st);
+            return cudaGetLastError();
+        }
+        {
+            const int H = halo_lanes(1 + sweeps_down(nu1));
+            const int64_t nch = P->N / 2;
+            k_down0<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
+                                                                  level_consts<T, D>(P->lev[0]), X, nu1, H,
+                                                                  P->partials, P->st);
+        }
+        for (int l = 1; l < P->lt; ++l) {
+            const int H = halo_lanes(sweeps_down(nu1));
+            const int64_t nch = P->lev[l].N / 2;
+            k_down<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
+                                                                 static_cast<T*>(P->fl[l + 1]), nch,
+                                                                 level_consts<T, D>(P->lev[l]), X, nu1, H, P->st);
+        }
+        k_tail<T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
+                                                         static_cast<T*>(P->ul[P->lt]), lk, X, nl,
+                                                         P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
+        for (int l = P->lt - 1; l >= 1; --l) {
+            const int H = halo_lanes(sweeps_up(nu1, nu2));
+            const int64_t nch = P->lev[l].N / 2;
+            k_up<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
+                                                               static_cast<const T*>(P->ul[l + 1]),
+                                                               static_cast<T*>(P->ul[l]), nch,
+                                                               level_consts<T, D>(P->lev[l]), X, nu1, nu2, H,
+                                                               P->st);
+        }
+        {
+            const int H = halo_lanes(sweeps_up(nu1, nu2));
+            const int64_t nch = P->N / 2;
+            k_up0<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<const T*>(P->ul[1]), nch,
+                                                                level_consts<T, D>(P->lev[0]), X, nu1, nu2, H,
+                                                                P->st);
+        }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t enqueue_normF(tmg_plan* P) {
+        k_normF<D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(P->N, P->partials, P->st);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t enqueue_residual(tmg_plan* P, const double* f, double u0, const double* u, double* r) {
+        k_residual_out<D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(f, u, u0, r, P->N, res0_consts(P));
+        return cudaGetLastError();
+    }
+
+    static const tmg_ops* ops() {
+        static const tmg_ops o = {sizeof(T), &tail_bytes, &upload, &enqueue_cycle, &enqueue_normF,
+                                  &enqueue_residual, &set_tail_attr};
+        return &o;
+    }
+};
+
+}  // namespace tmg

@@ -1,0 +1,851 @@
+// Device code of the time-multigrid solver (Gander & Neumueller, arXiv:1409.5254).
+//
+// Data layout: every level stores its vectors interval-major, [N_l][D] with
+// D = p_t + 1 shifted-Legendre coefficients per interval.  The basis fixes
+// a_k = psi_k(0) = (-1)^k and b_l = psi_l(1) = 1, so the coupling term
+// N u_{n-1} = a (b^T u_{n-1}) only needs the previous interval's endpoint
+// value e_{n-1} = sum_l u_{n-1}[l] (the one-value halo).
+//
+// Each cycle is written in correction form: level 0 forms r = F - L u in
+// FP64, every level below starts from a zero guess, and the pre-smoothed
+// iterate of a zero-started level is recomputed on the way up instead of
+// being stored.  With a zero start the damped block Jacobi sweep of
+// eq. chap4_ODESmoother gives u = omega A^{-1} f and A u = omega f, so the
+// residual after pre-smoothing is formed without an explicit A u product
+// (no cancellation in the cycle precision): we carry w = A u along.
+//
+// Streaming kernels map one lane to one coarse pair (two fine intervals,
+// the unit of the restriction R = [R1 R2]).  Halo values move between lanes
+// by warp shuffles; the first H lanes of every warp tile recompute the
+// previous tile's last pairs so that warps never wait on each other.  Each
+// sweep that needs e_{n-1} shifts the garbage entering lane 0 by one
+// interval, so H = ceil(S/2) lanes cover S such sweeps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tmg {
+
+constexpr int kMaxD = 4;
+constexpr int kMaxLevels = 48;
+constexpr int kHist = 512;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Constants of one level in the cycle precision T (row-major D x D blocks).
+template <typename T, int D>
+struct LevelK {
+    T A[D * D];      // K + z_l Mhat
+    T Ainv[D * D];   // its inverse
+    T g[D];          // A^{-1} a
+    T c[D];          // b^T A^{-1}
+    T omega;         // damping of this level
+    T alpha;         // b^T A^{-1} a
+};
+
+// Prolongation onto the two halves of a coarse interval: P1 = R1^T, P2 = R2^T.
+template <typename T, int D>
+struct Xfer {
+    T P1[D * D];
+    T P2[D * D];
+};
+
+// Level-0 residual constants (FP64): zm[k] = z_0 / (2k+1).
+struct Res0 {
+    double zm[kMaxD];
+};
+
+// Device-resident solve state.  Written by the last block of the residual
+// kernel; every other kernel of a cycle returns at once when done != 0.
+struct DevState {
+    const double* F;      // load vector of the current solve
+    double* u;            // solution of the current solve
+    double u0;            // initial value of the current solve
+    double nF;            // ||F||_2 (F with a*u0 folded in)
+    double tol;
+    int max_cycles;
+    int cycle;            // residual evaluations done so far in this solve
+    int done;             // 0 running, 1 converged, 2 cycle limit, 3 non-finite
+    int nF_from_first;    // 1: the first residual (u = 0) defines ||F||
+    int use_cond;         // 1: the solve runs as a graph while-loop
+    unsigned ticket;      // last-block ticket
+    unsigned long long cond;   // cudaGraphConditionalHandle of that loop
+    double hist[kHist];   // relative residual before each cycle
+};
+
+// ------------------------------------------------------------ helpers --
+
+template <typename T, int D>
+__device__ __forceinline__ T endval(const T (&u)[D]) {
+    T e = u[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) e += u[k];
+    return e;
+}
+
+// a_k = (-1)^k
+template <typename T>
+__device__ __forceinline__ T asgn(int k, T x) {
+    return (k & 1) ? -x : x;
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void matvec(const T* M, const T (&x)[D], T (&y)[D]) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        T s = M[i * D] * x[0];
+#pragma unroll
+        for (int j = 1; j < D; ++j) s = fma(M[i * D + j], x[j], s);
+        y[i] = s;
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ T dotc(const T* c, const T (&x)[D]) {
+    T s = c[0] * x[0];
+#pragma unroll
+    for (int j = 1; j < D; ++j) s = fma(c[j], x[j], s);
+    return s;
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_prev(T v) {
+    return __shfl_up_sync(kFull, v, 1);
+}
+
+// Vector load/store of NV contiguous T values.  The caller guarantees that
+// p is aligned to the largest power of two (<= 16 bytes) dividing NV*sizeof(T).
+template <typename T, int NV>
+struct VecIO {
+    static constexpr int B = NV * (int)sizeof(T);
+    static constexpr int W = (B % 16 == 0) ? 16 : (B % 8 == 0) ? 8 : 4;
+    using V = typename std::conditional<W == 16, uint4, typename std::conditional<W == 8, uint2, unsigned>::type>::type;
+    union U {
+        V w[B / W];
+        T v[NV];
+    };
+    static __device__ __forceinline__ void load(const T* __restrict__ p, T (&out)[NV]) {
+        U u;
+        const V* q = reinterpret_cast<const V*>(p);
+#pragma unroll
+        for (int i = 0; i < B / W; ++i) u.w[i] = q[i];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i] = u.v[i];
+    }
+    static __device__ __forceinline__ void store(T* __restrict__ p, const T (&in)[NV]) {
+        U u;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) u.v[i] = in[i];
+        V* q = reinterpret_cast<V*>(p);
+#pragma unroll
+        for (int i = 0; i < B / W; ++i) q[i] = u.w[i];
+    }
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void load_pair(const T* __restrict__ base, int64_t q, bool ok, T (&x)[2][D]) {
+    T v[2 * D];
+    if (ok) {
+        VecIO<T, 2 * D>::load(base + q * 2 * D, v);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2 * D; ++i) v[i] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        x[0][i] = v[i];
+        x[1][i] = v[D + i];
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void store_pair(T* __restrict__ base, int64_t q, const T (&x)[2][D]) {
+    T v[2 * D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        v[i] = x[0][i];
+        v[D + i] = x[1][i];
+    }
+    VecIO<T, 2 * D>::store(base + q * 2 * D, v);
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t q, bool ok, T (&x)[D]) {
+    if (ok) {
+        VecIO<T, D>::load(base + q * D, x);
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) x[i] = T(0);
+    }
+}
+
+// ------------------------------------------------ smoother building blocks --
+
+// Pre-smoothing from a zero guess for a coarse pair with right-hand side f:
+// sweep 1 gives u = omega A^{-1} f, w = A u = omega f; sweeps 2..nu1 use the
+// previous interval's endpoint value (warp shuffle).  h = A^{-1} f is kept.
+template <typename T, int D>
+__device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&f)[2][D], T (&h)[2][D],
+                                               T (&u)[2][D], T (&w)[2][D], int nu1) {
+    const T om = K.omega, om1 = T(1) - K.omega;
+    const T om_first = nu1 > 0 ? om : T(0);     // no pre-smoothing leaves u = 0
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        matvec<T, D>(K.Ainv, f[i], h[i]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[i][k] = om_first * h[i][k];
+            w[i][k] = om_first * f[i][k];
+        }
+    }
+    for (int s = 1; s < nu1; ++s) {
+        const T e0 = endval<T, D>(u[0]);
+        const T ep = shfl_prev(endval<T, D>(u[1]));
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
+            w[0][k] = om1 * w[0][k] + om * (f[0][k] + asgn(k, ep));
+            u[1][k] = om1 * u[1][k] + om * fma(K.g[k], e0, h[1][k]);
+            w[1][k] = om1 * w[1][k] + om * (f[1][k] + asgn(k, e0));
+        }
+    }
+}
+
+// Residual f + a e_{n-1} - A u of a pair, with A u = w carried along.
+template <typename T, int D>
+__device__ __forceinline__ void residual_tracked(const T (&f)[2][D], const T (&u)[2][D], const T (&w)[2][D],
+                                                 T (&r)[2][D]) {
+    const T e0 = endval<T, D>(u[0]);
+    const T ep = shfl_prev(endval<T, D>(u[1]));
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        r[0][k] = f[0][k] + asgn(k, ep) - w[0][k];
+        r[1][k] = f[1][k] + asgn(k, e0) - w[1][k];
+    }
+}
+
+// Restriction f_c = R1 r_{2m} + R2 r_{2m+1} with R_i = P_i^T (eq. chap4_restrictionTime).
+template <typename T, int D>
+__device__ __forceinline__ void restrict_pair(const Xfer<T, D>& X, const T (&r)[2][D], T (&fc)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(X.P1[l * D + k], r[0][l], fma(X.P2[l * D + k], r[1][l], s));
+        fc[k] = s;
+    }
+}
+
+// Prolongation u_{2m} += P1 uc, u_{2m+1} += P2 uc (eq. chap4_prolongationTime).
+template <typename T, int D>
+__device__ __forceinline__ void prolong_add(const Xfer<T, D>& X, const T (&uc)[D], T (&u)[2][D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T s1 = u[0][k], s2 = u[1][k];
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            s1 = fma(X.P1[k * D + l], uc[l], s1);
+            s2 = fma(X.P2[k * D + l], uc[l], s2);
+        }
+        u[0][k] = s1;
+        u[1][k] = s2;
+    }
+}
+
+// nu post-smoothing sweeps: u <- (1-omega) u + omega (A^{-1} f + g e_{n-1}).
+template <typename T, int D>
+__device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2][D], T (&u)[2][D], int nu) {
+    const T om = K.omega, om1 = T(1) - K.omega;
+    for (int s = 0; s < nu; ++s) {
+        const T e0 = endval<T, D>(u[0]);
+        const T ep = shfl_prev(endval<T, D>(u[1]));
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
+            u[1][k] = om1 * u[1][k] + om * fma(K.g[k], e0, h[1][k]);
+        }
+    }
+}
+
+// FP64 residual of the original system for one interval, using the Legendre
+// structure (K u)[k] = e - 2 S_k with S_k = sum of u[l], l < k, l of the other
+// parity than k:  r[k] = F[k] + a_k e_prev - e + 2 S_k - z/(2k+1) u[k].
+// The nearly-cancelling endpoint difference is formed first.
+template <int D>
+__device__ __forceinline__ void residual0(const double (&F)[D], const double (&u)[D], double ep, double e,
+                                          const Res0& R, double (&r)[D]) {
+    const double dp = ep - e;
+    r[0] = fma(-R.zm[0], u[0], F[0] + dp);
+    if constexpr (D > 1) {
+        const double sm = ep + e;
+        r[1] = fma(-R.zm[1], u[1], fma(2.0, u[0], F[1] - sm));
+        if constexpr (D > 2) r[2] = fma(-R.zm[2], u[2], fma(2.0, u[1], F[2] + dp));
+        if constexpr (D > 3) r[3] = fma(-R.zm[3], u[3], fma(2.0, u[0] + u[2], F[3] - sm));
+    }
+}
+
+// ------------------------------------------------- norm and stopping test --
+
+// First kernel of a cycle: a finished solve must also end the graph loop.
+__device__ __forceinline__ bool cycle_finished(const DevState* st) {
+    if (!st->done) return false;
+    if (st->use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+        cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
+    return true;
+}
+
+__device__ __forceinline__ void finalize_state(DevState* st, double ss) {
+    const int k = st->cycle;
+    const double nrm = sqrt(ss);
+    if (k == 0 && st->nF_from_first) st->nF = nrm;
+    const double rel = st->nF > 0.0 ? nrm / st->nF : nrm;
+    st->hist[k < kHist ? k : kHist - 1] = rel;
+    int done = 0;
+    if (!(rel == rel) || rel > 1.0e300) done = 3;
+    else if (rel <= st->tol) done = 1;
+    else if (k >= st->max_cycles) done = 2;
+    st->cycle = k + 1;
+    st->done = done;
+    if (done && st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
+}
+
+// Deterministic grid sum of ss: block partials in a fixed order, reduced by
+// the last block to finish (ticket), which then applies the stopping test.
+template <int NT>
+__device__ __forceinline__ void grid_norm_finalize(double ss, double* __restrict__ partials, DevState* st) {
+    __shared__ double red[NT / 32];
+    __shared__ int last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(kFull, ss, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < NT / 32; ++i) s += red[i];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        const unsigned t = atomicAdd(&st->ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double s = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += NT) s += __ldcg(&partials[i]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(kFull, s, off);
+    __syncthreads();
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < NT / 32; ++i) tot += red[i];
+        st->ticket = 0u;
+        finalize_state(st, tot);
+    }
+}
+
+// ------------------------------------------------------ streaming kernels --
+
+constexpr int kNT = 256;   // threads per block of the streaming kernels
+
+// Level l >= 1, zero guess: pre-smooth, residual, restrict.  f: [2*nchunks][D],
+// fc: [nchunks][D].
+template <typename T, int D>
+__global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __restrict__ fc, int64_t nchunks,
+                                              LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
+                                              const DevState* __restrict__ st) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
+        load_pair<T, D>(f, q, inb, fv);
+        presmooth_zero<T, D>(K, fv, h, u, w, nu1);
+        residual_tracked<T, D>(fv, u, w, r);
+        restrict_pair<T, D>(X, r, out);
+        if (inb && lane >= H) VecIO<T, D>::store(fc + q * D, out);
+    }
+}
+
+// Level l >= 1, zero guess: recompute the pre-smoothed iterate, add the
+// prolongated coarse correction uc: [nchunks][D], post-smooth, write u.
+template <typename T, int D>
+__global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __restrict__ uc, T* __restrict__ u,
+                                            int64_t nchunks, LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2,
+                                            int H, const DevState* __restrict__ st) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
+        load_pair<T, D>(f, q, inb, fv);
+        load_one<T, D>(uc, q, inb, c);
+        presmooth_zero<T, D>(K, fv, h, v, w, nu1);
+        prolong_add<T, D>(X, c, v);
+        postsmooth<T, D>(K, h, v, nu2);
+        if (inb && lane >= H) store_pair<T, D>(u, q, v);
+    }
+}
+
+// Level 0: r = F - L u in FP64 (u0 is the halo before the first interval),
+// ||r||^2 for the stopping test, r stored in the cycle precision T; then,
+// when fc != nullptr, the zero-guess pre-smoothing, residual and restriction
+// of the correction equation L c = r onto level 1.
+template <typename T, int D>
+__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, Res0 R,
+                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
+                                               double* __restrict__ partials, DevState* st) {
+    if (cycle_finished(st)) return;
+    const double* __restrict__ F = st->F;
+    const double* __restrict__ uu = st->u;
+    const double u0 = st->u0;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    double ss = 0.0;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const bool own = inb && lane >= H;
+        double uv[2][D], Fv[2][D], r[2][D];
+        load_pair<double, D>(uu, q, inb, uv);
+        load_pair<double, D>(F, q, inb, Fv);
+        const double e0 = endval<double, D>(uv[0]);
+        double e1 = endval<double, D>(uv[1]);
+        if (q < 0) e1 = u0;                       // the value before the first interval
+        const double ep = shfl_prev(e1);
+        residual0<D>(Fv[0], uv[0], ep, e0, R, r[0]);
+        residual0<D>(Fv[1], uv[1], e0, e1, R, r[1]);
+        // Lanes outside the array carry u0 only as the halo of the FP64
+        // residual; for the correction equation L c = r their r is zero.
+        T rt[2][D];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                rt[i][k] = inb ? (T)r[i][k] : T(0);
+                if (own) ss = fma(r[i][k], r[i][k], ss);
+            }
+        if (own) store_pair<T, D>(rT, q, rt);
+        if (fc != nullptr) {
+            T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
+            presmooth_zero<T, D>(K, rt, h, c, w, nu1);
+            residual_tracked<T, D>(rt, c, w, rc);
+            restrict_pair<T, D>(X, rc, out);
+            if (own) VecIO<T, D>::store(fc + q * D, out);
+        }
+    }
+    grid_norm_finalize<kNT>(ss, partials, st);
+}
+
+// Level 0 on the way up: recompute the pre-smoothed correction from r, add
+// the prolongated level-1 correction, post-smooth, and update u += c in FP64.
+template <typename T, int D>
+__global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
+                                             LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2, int H,
+                                             const DevState* __restrict__ st) {
+    if (st->done) return;
+    double* __restrict__ uu = st->u;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        T rt[2][D], h[2][D], c[2][D], w[2][D], cc[D];
+        load_pair<T, D>(rT, q, inb, rt);
+        load_one<T, D>(uc, q, inb, cc);
+        presmooth_zero<T, D>(K, rt, h, c, w, nu1);
+        prolong_add<T, D>(X, cc, c);
+        postsmooth<T, D>(K, h, c, nu2);
+        if (inb && lane >= H) {
+            double uv[2][D];
+            load_pair<double, D>(uu, q, true, uv);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) uv[i][k] += (double)c[i][k];
+            store_pair<double, D>(uu, q, uv);
+        }
+    }
+}
+
+// Level 0 residual only, one interval per thread (any N): used when the
+// on-chip solver handles the whole correction cycle.
+template <typename T, int D>
+__global__ void __launch_bounds__(kNT) k_res0(T* __restrict__ rT, int64_t N, Res0 R, double* __restrict__ partials,
+                                              DevState* st) {
+    if (cycle_finished(st)) return;
+    const double* __restrict__ F = st->F;
+    const double* __restrict__ uu = st->u;
+    const double u0 = st->u0;
+    double ss = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kNT;
+    for (int64_t n = (int64_t)blockIdx.x * kNT + threadIdx.x; n < N; n += stride) {
+        double uv[D], Fv[D], up[D], r[D];
+        load_one<double, D>(uu, n, true, uv);
+        load_one<double, D>(F, n, true, Fv);
+        double ep = u0;
+        if (n > 0) {
+            load_one<double, D>(uu, n - 1, true, up);
+            ep = endval<double, D>(up);
+        }
+        residual0<D>(Fv, uv, ep, endval<double, D>(uv), R, r);
+        T rt[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            rt[k] = (T)r[k];
+            ss = fma(r[k], r[k], ss);
+        }
+        VecIO<T, D>::store(rT + n * D, rt);
+    }
+    grid_norm_finalize<kNT>(ss, partials, st);
+}
+
+// u += c (FP64 accumulation of a level-0 correction held in precision T).
+template <typename T>
+__global__ void __launch_bounds__(kNT) k_update0(const T* __restrict__ c, int64_t n_values,
+                                                 const DevState* __restrict__ st) {
+    if (st->done) return;
+    double* __restrict__ uu = st->u;
+    const int64_t stride = (int64_t)gridDim.x * kNT;
+    for (int64_t i = (int64_t)blockIdx.x * kNT + threadIdx.x; i < n_values; i += stride) uu[i] += (double)c[i];
+}
+
+// r = F - L u into an FP64 array (public residual entry point).
+template <int D>
+__global__ void __launch_bounds__(kNT) k_residual_out(const double* __restrict__ F, const double* __restrict__ u,
+                                                      double u0, double* __restrict__ r, int64_t N, Res0 R) {
+    const int64_t stride = (int64_t)gridDim.x * kNT;
+    for (int64_t n = (int64_t)blockIdx.x * kNT + threadIdx.x; n < N; n += stride) {
+        double uv[D], Fv[D], up[D], rr[D];
+        load_one<double, D>(u, n, true, uv);
+        load_one<double, D>(F, n, true, Fv);
+        double ep = u0;
+        if (n > 0) {
+            load_one<double, D>(u, n - 1, true, up);
+            ep = endval<double, D>(up);
+        }
+        residual0<D>(Fv, uv, ep, endval<double, D>(uv), R, rr);
+        VecIO<double, D>::store(r + n * D, rr);
+    }
+}
+
+// ||F||_2 with a*u0 folded into the first interval (for a caller-given start).
+template <int D>
+__global__ void __launch_bounds__(kNT) k_normF(int64_t N, double* __restrict__ partials, DevState* st) {
+    const double* __restrict__ F = st->F;
+    const double u0 = st->u0;
+    double ss = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kNT;
+    for (int64_t n = (int64_t)blockIdx.x * kNT + threadIdx.x; n < N; n += stride) {
+        double Fv[D];
+        load_one<double, D>(F, n, true, Fv);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double v = (n == 0) ? Fv[k] + asgn(k, u0) : Fv[k];
+            ss = fma(v, v, ss);
+        }
+    }
+    // reuse the ticketed reduction, but only to store ||F||
+    __shared__ double red[kNT / 32];
+    __shared__ int last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(kFull, ss, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kNT / 32; ++i) s += red[i];
+        partials[blockIdx.x] = s;
+        __threadfence();
+        last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (unsigned i = 0; i < gridDim.x; ++i) tot += __ldcg(&partials[i]);
+        st->nF = sqrt(tot);
+        st->ticket = 0u;
+    }
+}
+
+// --------------------------------------------------- on-chip coarse solver --
+
+constexpr int kTailNT = 512;
+
+// Shared-memory image of the coarse hierarchy handled by one CTA.
+template <typename T, int D>
+struct TailView {
+    T* f[kMaxLevels];
+    T* u[kMaxLevels];
+    T* w;        // A u during pre-smoothing
+    T* e;        // endpoint values of one pass
+    T* scanA;    // [kTailNT/32] warp-total slopes of the coarsest scan
+    T* scanB;    // [2*kTailNT/32] warp-total offsets, then inclusive warp prefixes
+    int64_t N[kMaxLevels];
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void sm_load(const T* p, T (&x)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = p[k];
+}
+template <typename T, int D>
+__device__ __forceinline__ void sm_store(T* p, const T (&x)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) p[k] = x[k];
+}
+
+// Endpoint values e[n] = b^T u_n of a whole level.
+template <typename T, int D>
+__device__ __forceinline__ void tail_endvals(const T* u, T* e, int64_t N) {
+    for (int64_t n = threadIdx.x; n < N; n += kTailNT) {
+        T x[D];
+        sm_load<T, D>(u + n * D, x);
+        e[n] = endval<T, D>(x);
+    }
+}
+
+// One damped block-Jacobi sweep of a level held in shared memory; w = A u is
+// updated alongside when track_w.
+template <typename T, int D>
+__device__ void tail_sweep(const LevelK<T, D>& K, const T* f, T* u, T* w, T* e, int64_t N, bool track_w) {
+    tail_endvals<T, D>(u, e, N);
+    __syncthreads();
+    const T om = K.omega, om1 = T(1) - K.omega;
+    for (int64_t n = threadIdx.x; n < N; n += kTailNT) {
+        T fv[D], h[D], x[D];
+        sm_load<T, D>(f + n * D, fv);
+        sm_load<T, D>(u + n * D, x);
+        matvec<T, D>(K.Ainv, fv, h);
+        const T ep = n > 0 ? e[n - 1] : T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = om1 * x[k] + om * fma(K.g[k], ep, h[k]);
+        sm_store<T, D>(u + n * D, x);
+        if (track_w) {
+            T y[D];
+            sm_load<T, D>(w + n * D, y);
+#pragma unroll
+            for (int k = 0; k < D; ++k) y[k] = om1 * y[k] + om * (fv[k] + asgn(k, ep));
+            sm_store<T, D>(w + n * D, y);
+        }
+    }
+    __syncthreads();
+}
+
+// Exact solve of the level by a block-wide prefix scan over the affine maps
+// e_n = alpha e_{n-1} + c^T f_n (e_{-1} = 0), then u_n = A^{-1} f_n + g e_{n-1}.
+template <typename T, int D>
+__device__ void tail_exact(const LevelK<T, D>& K, const T* f, T* u, T* scanA, T* scanB, int64_t N) {
+    const int t = threadIdx.x;
+    const int64_t per = (N + kTailNT - 1) / kTailNT;
+    const int64_t n0 = t * per, n1 = (n0 + per < N) ? n0 + per : N;
+    T Aacc = T(1), Bacc = T(0);
+    for (int64_t n = n0; n < n1; ++n) {
+        T fv[D];
+        sm_load<T, D>(f + n * D, fv);
+        Bacc = fma(K.alpha, Bacc, dotc<T, D>(K.c, fv));
+        Aacc *= K.alpha;
+    }
+    // inclusive scan of (A, B) over threads: compose left-to-right
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T Ap = __shfl_up_sync(kFull, Aacc, off);
+        const T Bp = __shfl_up_sync(kFull, Bacc, off);
+        if (lane >= off) {
+            Bacc = fma(Aacc, Bp, Bacc);
+            Aacc = Aacc * Ap;
+        }
+    }
+    if (lane == 31) {
+        scanA[warp] = Aacc;
+        scanB[warp] = Bacc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        T Aw = lane < kTailNT / 32 ? scanA[lane] : T(1);
+        T Bw = lane < kTailNT / 32 ? scanB[lane] : T(0);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T Ap = __shfl_up_sync(kFull, Aw, off);
+            const T Bp = __shfl_up_sync(kFull, Bw, off);
+            if (lane >= off) {
+                Bw = fma(Aw, Bp, Bw);
+                Aw = Aw * Ap;
+            }
+        }
+        if (lane < kTailNT / 32) scanB[kTailNT / 32 + lane] = Bw;   // inclusive warp prefixes
+    }
+    __syncthreads();
+    // exclusive prefix for this thread: warps before, then lanes before
+    const T ew = warp > 0 ? scanB[kTailNT / 32 + warp - 1] : T(0);
+    T Ain = __shfl_up_sync(kFull, Aacc, 1), Bin = __shfl_up_sync(kFull, Bacc, 1);
+    if (lane == 0) {
+        Ain = T(1);
+        Bin = T(0);
+    }
+    T e = fma(Ain, ew, Bin);
+    for (int64_t n = n0; n < n1; ++n) {
+        T fv[D], h[D];
+        sm_load<T, D>(f + n * D, fv);
+        matvec<T, D>(K.Ainv, fv, h);
+#pragma unroll
+        for (int k = 0; k < D; ++k) h[k] = fma(K.g[k], e, h[k]);
+        sm_store<T, D>(u + n * D, h);
+        e = fma(K.alpha, e, dotc<T, D>(K.c, fv));
+    }
+    __syncthreads();
+}
+
+// The coarse part of the cycle, levels lt..lt+nl-1 (tail index j = l - lt),
+// entirely in shared memory: V (gamma = 1) or W (gamma = 2) recursion written
+// as a loop; coarsest tail level solved exactly.  f_in is the right-hand side
+// of level lt, u_out receives its correction.
+template <typename T, int D>
+__global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T* __restrict__ u_out,
+                                                  const LevelK<T, D>* __restrict__ lk, Xfer<T, D> X, int nl,
+                                                  int64_t Nt, int nu1, int nu2, int gamma,
+                                                  const DevState* __restrict__ st) {
+    if (st != nullptr && st->done) return;
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    TailView<T, D> V;
+    T* p = reinterpret_cast<T*>(tail_smem);
+    for (int j = 0; j < nl; ++j) {
+        V.N[j] = Nt >> j;
+        V.f[j] = p;
+        p += V.N[j] * D;
+    }
+    for (int j = 0; j < nl; ++j) {
+        V.u[j] = p;
+        p += V.N[j] * D;
+    }
+    V.w = p;
+    p += Nt * D;
+    V.e = p;
+    p += Nt;
+    V.scanA = p;
+    p += kTailNT / 32;
+    V.scanB = p;
+
+    for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) V.f[0][i] = f_in[i];
+    __syncthreads();
+
+    int visits[kMaxLevels];
+    bool has_init[kMaxLevels];
+    for (int j = 0; j < nl; ++j) {
+        visits[j] = 0;
+        has_init[j] = false;
+    }
+    int j = 0;
+    bool down = true;
+    while (true) {
+        const LevelK<T, D>& K = lk[j];
+        const int64_t N = V.N[j];
+        if (down) {
+            if (j == nl - 1) {
+                tail_exact<T, D>(K, V.f[j], V.u[j], V.scanA, V.scanB, N);
+                if (j == 0) break;
+                --j;
+                down = false;
+                continue;
+            }
+            // pre-smoothing; a zero start gives u = omega A^{-1} f, A u = omega f
+            int sweeps = nu1;
+            if (!has_init[j]) {
+                const T om_first = nu1 > 0 ? K.omega : T(0);
+                for (int64_t n = threadIdx.x; n < N; n += kTailNT) {
+                    T fv[D], h[D], x[D], y[D];
+                    sm_load<T, D>(V.f[j] + n * D, fv);
+                    matvec<T, D>(K.Ainv, fv, h);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        x[k] = om_first * h[k];
+                        y[k] = om_first * fv[k];
+                    }
+                    sm_store<T, D>(V.u[j] + n * D, x);
+                    sm_store<T, D>(V.w + n * D, y);
+                }
+                __syncthreads();
+                sweeps = nu1 > 0 ? nu1 - 1 : 0;
+            } else {
+                for (int64_t n = threadIdx.x; n < N; n += kTailNT) {
+                    T x[D], y[D];
+                    sm_load<T, D>(V.u[j] + n * D, x);
+                    matvec<T, D>(K.A, x, y);
+                    sm_store<T, D>(V.w + n * D, y);
+                }
+                __syncthreads();
+            }
+            for (int s = 0; s < sweeps; ++s) tail_sweep<T, D>(K, V.f[j], V.u[j], V.w, V.e, N, true);
+            // residual f + a e_{n-1} - A u, restricted onto level j+1
+            tail_endvals<T, D>(V.u[j], V.e, N);
+            __syncthreads();
+            for (int64_t m = threadIdx.x; m < N / 2; m += kTailNT) {
+                T r[2][D], out[D];
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int64_t n = 2 * m + i;
+                    const T ep = n > 0 ? V.e[n - 1] : T(0);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) r[i][k] = V.f[j][n * D + k] + asgn(k, ep) - V.w[n * D + k];
+                }
+                restrict_pair<T, D>(X, r, out);
+                sm_store<T, D>(V.f[j + 1] + m * D, out);
+            }
+            __syncthreads();
+            visits[j] = 0;
+            has_init[j + 1] = false;
+            ++j;
+            continue;
+        }
+        // back from level j+1
+        if (++visits[j] < gamma) {
+            has_init[j + 1] = true;
+            ++j;
+            down = true;
+            continue;
+        }
+        for (int64_t m = threadIdx.x; m < N / 2; m += kTailNT) {
+            T x[2][D], c[D];
+            sm_load<T, D>(V.u[j] + (2 * m) * D, x[0]);
+            sm_load<T, D>(V.u[j] + (2 * m + 1) * D, x[1]);
+            sm_load<T, D>(V.u[j + 1] + m * D, c);
+            prolong_add<T, D>(X, c, x);
+            sm_store<T, D>(V.u[j] + (2 * m) * D, x[0]);
+            sm_store<T, D>(V.u[j] + (2 * m + 1) * D, x[1]);
+        }
+        __syncthreads();
+        for (int s = 0; s < nu2; ++s) tail_sweep<T, D>(K, V.f[j], V.u[j], V.w, V.e, N, false);
+        if (j == 0) break;
+        --j;
+    }
+    for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) u_out[i] = V.u[0][i];
+}
+
+// Shared-memory bytes of the tail for nl levels starting with Nt intervals.
+template <typename T, int D>
+inline size_t tail_smem_bytes(int64_t Nt, int nl) {
+    int64_t tot = 0;
+    for (int j = 0; j < nl; ++j) tot += 2 * (Nt >> j) * D;
+    tot += Nt * D + Nt + 3 * (kTailNT / 32);   // w, e, scanA, scanB (twice as long)
+    return (size_t)tot * sizeof(T);
+}
+
+}  // namespace tmg

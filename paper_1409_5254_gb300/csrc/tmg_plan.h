@@ -1,0 +1,83 @@
+// Host-side plan of the time-multigrid solver (shared by all translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/tmg.h"
+#include "tmg_kernels.cuh"
+
+// FP64 constants of one level, computed once on the host.
+struct tmg_level_host {
+    int64_t N;          // intervals
+    double z;           // lambda * tau_l
+    double A[16];       // K + z Mhat (row-major, D x D)
+    double Ainv[16];
+    double g[4];        // A^{-1} a
+    double c[4];        // b^T A^{-1}
+    double alpha;       // b^T A^{-1} a
+    double omega;
+};
+
+struct tmg_ops;
+
+struct tmg_plan {
+    int p, d;
+    double tau, lambda;
+    int64_t N;
+    double omega_user;
+    tmg_opts o;
+    cudaStream_t s;
+    bool own_stream;     // s was created by the plan
+    int nsm;
+
+    int nlev;            // levels 0..nlev-1
+    int lt;              // first level solved on chip (tail)
+    size_t tail_smem;
+    std::vector<tmg_level_host> lev;
+    double P1[16], P2[16];   // prolongation (coarse -> fine halves)
+
+    // device workspace (one allocation)
+    void* ws;
+    size_t ws_bytes;
+    tmg::DevState* st;       // device state
+    tmg::DevState* st_host;  // pinned mirror
+    double* partials;
+    int max_blocks;
+    void* fl[tmg::kMaxLevels];   // level right-hand sides (cycle precision)
+    void* ul[tmg::kMaxLevels];   // level corrections
+    void* rT;                    // level-0 residual (cycle precision)
+    void* lk_dev;                // tail level constants
+
+    // optional buffers for the host-array entry point
+    double* F_dev;
+    double* u_dev;
+
+    // CUDA graph of the whole solve (while-loop over cycles)
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    unsigned long long cond;
+
+    const tmg_ops* ops;
+
+    // statistics of the last solve
+    int last_cycles;
+    double last_rel;
+    std::vector<double> last_hist;
+};
+
+// Per-(precision, D) entry points, instantiated in tmg_inst_*.cu.
+struct tmg_ops {
+    size_t elem;                                   // sizeof(cycle precision)
+    size_t (*tail_bytes)(int64_t Nt, int nl);
+    cudaError_t (*upload)(tmg_plan*);              // per-level constants -> device
+    cudaError_t (*enqueue_cycle)(tmg_plan*);       // one correction cycle
+    cudaError_t (*enqueue_normF)(tmg_plan*);       // ||F|| for a caller-given start
+    cudaError_t (*enqueue_residual)(tmg_plan*, const double* f, double u0, const double* u, double* r);
+    cudaError_t (*set_tail_attr)(size_t bytes);
+};
+
+const tmg_ops* tmg_ops_f32(int d);
+const tmg_ops* tmg_ops_f64(int d);

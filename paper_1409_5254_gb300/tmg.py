@@ -1,0 +1,215 @@
+"""Thin Python binding of the C ABI in include/tmg.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``libtmg.so``; PyTorch only
+supplies device memory and the stream.  There is no CPU path: importing this
+module on a machine without the built library raises at first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build_ext
+
+TMG_OK, TMG_EINVAL, TMG_ENOMEM, TMG_ECUDA, TMG_ENOTCONV, TMG_ENUMERIC, TMG_ETIMEOUT, TMG_EUNSUPPORTED = range(8)
+FP64, MIXED = 0, 1
+_PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
+
+
+class TmgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().tmg_strerror(status).decode()
+        if status == TMG_ECUDA:
+            msg += f" (cudaError {_lib().tmg_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n_min", ctypes.c_int64), ("use_graph", ctypes.c_int), ("initial_guess", ctypes.c_int),
+                ("tail_cap", ctypes.c_int64)]
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual",
+           "tmg_stats", "tmg_plan_info", "tmg_inspect", "tmg_destroy", "tmg_strerror", "tmg_last_cuda_error"]
+
+
+def library_path() -> str:
+    return build_ext.LIB
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = build_ext.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libtmg.so not built ({path}); run __graft_entry__.build() "
+                              "or python -m paper_1409_5254_gb300.build_ext")
+        L = ctypes.CDLL(path)
+        L.tmg_opts_default.argtypes = [ctypes.POINTER(_Opts)]
+        L.tmg_opts_default.restype = None
+        L.tmg_setup.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Opts), _vp]
+        L.tmg_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp]
+        L.tmg_solve_host.argtypes = [_vp, _vp, ctypes.c_double, _vp]
+        L.tmg_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp]
+        L.tmg_residual.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
+        L.tmg_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, ctypes.c_int]
+        L.tmg_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int]
+        L.tmg_inspect.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]
+        L.tmg_destroy.argtypes = [_vp]
+        L.tmg_destroy.restype = None
+        L.tmg_strerror.argtypes = [ctypes.c_int]
+        L.tmg_strerror.restype = ctypes.c_char_p
+        L.tmg_last_cuda_error.argtypes = []
+        for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual", "tmg_stats",
+                     "tmg_plan_info", "tmg_inspect"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int, where: str, ok=(TMG_OK,)):
+    if status not in ok:
+        raise TmgError(status, where)
+    return status
+
+
+def _dev_ptr(t, d: int, N: int, name: str):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() != N * d:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {N}*{d}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class SolveStats:
+    status: int
+    cycles: int
+    rel_res: float
+    hist: np.ndarray
+
+
+class Plan:
+    """tmg_setup / tmg_solve / tmg_destroy for one problem (see include/tmg.h)."""
+
+    def __init__(self, p: int, tau: float, lam: float, N: int, levels: int = 0, omega: float = 0.0, *,
+                 tol: float = 1e-10, max_cycles: int = 100, nu1: int = 1, nu2: int = 1, gamma: int = 1,
+                 precision="mixed", n_min: int = 64, use_graph: bool = True, initial_guess: bool = False,
+                 tail_cap: int = 0, stream=None):
+        L = _lib()
+        o = _Opts()
+        L.tmg_opts_default(ctypes.byref(o))
+        o.tol, o.max_cycles, o.nu1, o.nu2, o.gamma = tol, max_cycles, nu1, nu2, gamma
+        o.precision = _PREC[precision]
+        o.n_min, o.use_graph, o.initial_guess = n_min, int(use_graph), int(initial_guess)
+        o.tail_cap = tail_cap
+        self.precision = _PREC[precision]
+        self.p, self.d, self.N = p, p + 1, N
+        self.tau, self.lam = tau, lam
+        self._stream = stream
+        handle = _vp()
+        sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(L.tmg_setup(ctypes.byref(handle), p, tau, lam, N, levels, omega, ctypes.byref(o), sp), "tmg_setup")
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().tmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def solve(self, f, u0: float, u=None, *, allow_notconv: bool = False) -> "torch.Tensor":
+        import torch
+        if u is None:
+            u = torch.empty((self.N, self.d), dtype=torch.float64, device=f.device)
+        st = _lib().tmg_solve(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0), _dev_ptr(u, self.d, self.N, "u"))
+        _check(st, "tmg_solve", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
+        self.last_status = st
+        return u
+
+    def solve_host(self, f_host, u0: float, u_host) -> int:
+        """f_host, u_host: contiguous float64 CPU tensors or numpy arrays (pinned tensors copy fastest)."""
+        fp = ctypes.c_void_p(_host_ptr(f_host, self.d, self.N))
+        up = ctypes.c_void_p(_host_ptr(u_host, self.d, self.N))
+        return _check(_lib().tmg_solve_host(self._h, fp, float(u0), up), "tmg_solve_host")
+
+    def cycle(self, f, u0: float, u):
+        _check(_lib().tmg_cycle(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
+                                _dev_ptr(u, self.d, self.N, "u")), "tmg_cycle")
+        return u
+
+    def residual(self, f, u0: float, u, r=None):
+        import torch
+        if r is None:
+            r = torch.empty_like(u)
+        _check(_lib().tmg_residual(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
+                                   _dev_ptr(u, self.d, self.N, "u"), _dev_ptr(r, self.d, self.N, "r")),
+               "tmg_residual")
+        return r
+
+    def stats(self, hist_len: int = 512) -> SolveStats:
+        cyc = ctypes.c_int(0)
+        rel = ctypes.c_double(0.0)
+        hist = np.full(hist_len, np.nan)
+        _check(_lib().tmg_stats(self._h, ctypes.byref(cyc), ctypes.byref(rel),
+                                hist.ctypes.data_as(_dp), hist_len), "tmg_stats")
+        h = hist[: cyc.value + 1].copy()
+        return SolveStats(getattr(self, "last_status", TMG_OK), cyc.value, rel.value, h)
+
+    def inspect(self, which: str, level: int = 0) -> np.ndarray:
+        """Copy an internal level vector ('f', 'u' of a level, or the level-0 residual 'r') to host."""
+        w = {"f": 0, "u": 1, "r": 2}[which]
+        n = self.N if w == 2 else self.N >> level
+        dt = np.float64 if self.precision == FP64 else np.float32
+        out = np.empty((n, self.d), dtype=dt)
+        _check(_lib().tmg_inspect(self._h, w, level, ctypes.c_void_p(out.ctypes.data), out.nbytes), "tmg_inspect")
+        return out
+
+    def info(self):
+        nl = ctypes.c_int(0)
+        lt = ctypes.c_int(0)
+        nt = ctypes.c_int64(0)
+        om = np.full(64, np.nan)
+        _check(_lib().tmg_plan_info(self._h, ctypes.byref(nl), ctypes.byref(lt), ctypes.byref(nt),
+                                    om.ctypes.data_as(_dp), 64), "tmg_plan_info")
+        return {"levels": nl.value, "tail_level": lt.value, "tail_intervals": nt.value,
+                "omega": om[: nl.value].copy()}
+
+
+def _host_ptr(x, d: int, N: int) -> int:
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != N * d:
+                raise TypeError("host tensor must be contiguous CPU float64 with N*d elements")
+            return x.data_ptr()
+    except ImportError:
+        pass
+    a = np.asarray(x)
+    if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != N * d:
+        raise TypeError("host array must be contiguous float64 with N*d elements")
+    return a.ctypes.data

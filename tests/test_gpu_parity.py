@@ -1,0 +1,250 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (written from the arithmetic):
+* FP64 form, iterate parity with the oracle's textbook cycle after k cycles:
+  1e-12 relative (both evaluate the same linear map in FP64; they differ only
+  in rounding order -- the GPU works in correction form with the block
+  inverse applied as a mat-vec).
+* FP64 form solved to tol 1e-13 vs exact forward substitution: 1e-11 relative
+  (the error is bounded by the residual times ||L^{-1}||).
+* Mixed form: FP64 relative residual of the returned u, evaluated by the
+  oracle, <= 1e-10 (x1.05 for the oracle's own rounding); the error against
+  forward substitution is reported.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1409_5254_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_5254_gb300 import build_ext
+    build_ext.build()
+    return torch.device("cuda:0")
+
+
+def tmg():
+    from paper_1409_5254_gb300 import tmg as T
+    return T
+
+
+def rel_err(a, b):
+    s = np.abs(b).max()
+    return np.abs(a - b).max() / (s if s > 0 else 1.0)
+
+
+def rel_residual(p, z, F, u0, u):
+    r = O.residual(p, z, F, u0, u)
+    return np.linalg.norm(r) / np.linalg.norm(O.fold_u0(p, F, u0))
+
+
+def gpu_cycles(dev, p, tau, lam, F, u0, k, **kw):
+    N = F.shape[0]
+    with tmg().Plan(p, tau, lam, N, precision="fp64", **kw) as plan:
+        Fd = torch.from_numpy(F).to(dev)
+        u = torch.zeros_like(Fd)
+        out = []
+        for _ in range(k):
+            plan.cycle(Fd, u0, u)
+            out.append(u.cpu().numpy().copy())
+        info = plan.info()
+    return out, info
+
+
+CYCLE_CASES = [
+    # (p, N, lam, T, n_min, levels, nu1, nu2, gamma, omega)
+    (1, 1024, 1.0, 1.0, 2, 0, 1, 1, 1, 0.0),          # small: on-chip solver from level 0
+    (0, 1 << 14, 1.0, 1.0, 64, 0, 1, 1, 1, 0.0),      # streaming levels + on-chip tail
+    (1, 1 << 14, 3.0, 2.0, 64, 0, 1, 1, 1, 0.0),
+    (2, 1 << 14, 1.0, 1.0, 16, 0, 1, 1, 1, 0.0),
+    (3, 1 << 14, 50.0, 1.0, 64, 0, 1, 1, 1, 0.0),
+    (1, 1 << 14, 1.0, 1.0, 64, 0, 2, 2, 1, 0.0),      # more sweeps: wider halos
+    (2, 1 << 13, 1.0, 1.0, 64, 0, 3, 1, 1, 0.0),
+    (1, 1 << 14, 1.0, 1.0, 64, 0, 1, 0, 1, 0.0),      # no post-smoothing
+    (1, 1 << 14, 1.0, 1.0, 64, 0, 0, 2, 1, 0.0),      # no pre-smoothing
+    (1, 1 << 14, 1.0, 1.0, 64, 0, 1, 1, 1, 0.5),      # uniform omega = 1/2
+    (0, 4096, 1.0, 1.0, 4, 0, 1, 1, 2, 0.0),          # W-cycle (on chip)
+    (1, 1 << 14, 1.0, 1.0, 64, 4, 1, 1, 1, 0.0),      # capped level count: large coarsest scan
+    (1, 3 * 1024, 1.0, 1.0, 2, 0, 1, 1, 1, 0.0),      # N = 3 * 2^10: odd coarsest level (3)
+]
+
+
+@pytest.mark.parametrize("case", CYCLE_CASES)
+def test_fp64_cycles_match_textbook_cycle(dev, case):
+    p, N, lam, T, n_min, levels, nu1, nu2, gamma, omega = case
+    prob = inputs.scalar_problem(N % 97, N, p, lam=lam, T=T, u0=0.75)
+    z = lam * prob["tau"]
+    Fhat = O.fold_u0(p, prob["F"], prob["u0"])
+    got, info = gpu_cycles(dev, p, prob["tau"], lam, prob["F"], prob["u0"], 3, levels=levels, omega=omega,
+                           nu1=nu1, nu2=nu2, gamma=gamma, n_min=n_min)
+    assert info["levels"] == O.num_levels(N, n_min, levels)
+    u = np.zeros_like(prob["F"])
+    for k in range(3):
+        u = O.mg_one_cycle(p, z, Fhat, u, n_min=n_min, max_levels=levels, nu1=nu1, nu2=nu2, gamma=gamma,
+                           omega=omega)
+        assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+def test_fp64_solve_matches_forward_substitution(dev, p):
+    N = 1 << 13
+    prob = inputs.scalar_problem(p, N, p, lam=1.0, T=4.0, u0=1.0)
+    z = prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    gamma = 1
+    with tmg().Plan(p, prob["tau"], 1.0, N, precision="fp64", tol=1e-13, max_cycles=300, gamma=gamma) as plan:
+        u = plan.solve(Fd, prob["u0"]).cpu().numpy()
+        st = plan.stats()
+    u_ex = O.fsub(p, z, prob["F"], prob["u0"])
+    assert rel_residual(p, z, prob["F"], prob["u0"], u) <= 1.05e-13
+    assert rel_err(u, u_ex) <= 1e-11
+    # the device-side history matches the oracle's textbook solve cycle by cycle
+    _, hist = O.mg_solve(p, z, prob["F"], prob["u0"], tol=1e-13, max_cycles=300)
+    assert abs(st.cycles - (len(hist) - 1)) <= 1
+    m = min(len(hist), len(st.hist))
+    big = hist[:m] > 1e-9
+    np.testing.assert_allclose(st.hist[:m][big], hist[:m][big], rtol=1e-6)
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("zscale", [1e-3, 1.0, 1e3])
+def test_mixed_solve_reaches_tolerance(dev, p, zscale):
+    N = 1 << 14
+    T = 1.0
+    lam = zscale * N / T
+    prob = inputs.scalar_problem(10 + p, N, p, lam=lam, T=T, u0=1.0)
+    z = lam * prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, prob["tau"], lam, N, precision="mixed", tol=1e-10, max_cycles=200) as plan:
+        u = plan.solve(Fd, prob["u0"]).cpu().numpy()
+        st = plan.stats()
+    rr = rel_residual(p, z, prob["F"], prob["u0"], u)
+    assert rr <= 1.05e-10, rr
+    assert st.rel_res <= 1e-10
+    u_ex = O.fsub(p, z, prob["F"], prob["u0"])
+    err = rel_err(u, u_ex)
+    print(f"p={p} z={z:.1e} cycles={st.cycles} rel_res={rr:.2e} err_vs_fp64={err:.2e}")
+    assert err <= 1e-6
+
+
+EDGE = [
+    (1, 1, 1.0),        # one interval
+    (2, 2, 1.0),
+    (0, 5, 1.0),        # odd: no coarsening, exact on-chip scan
+    (3, 1001, 1.0),
+    (1, 8192, 0.0),     # lambda = 0
+    (1, 4096, 1e3),     # large steps
+]
+
+
+@pytest.mark.parametrize("p,N,lam", EDGE)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_edge_cases(dev, p, N, lam, prec):
+    prob = inputs.scalar_problem(N, N, p, lam=lam, T=1.0, u0=-0.3)
+    z = lam * prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, prob["tau"], lam, N, precision=prec, tol=1e-12 if prec == "fp64" else 1e-10,
+                    n_min=2) as plan:
+        u = plan.solve(Fd, prob["u0"]).cpu().numpy()
+    u_ex = O.fsub(p, z, prob["F"], prob["u0"])
+    assert rel_residual(p, z, prob["F"], prob["u0"], u) <= (1.05e-12 if prec == "fp64" else 1.05e-10)
+    assert rel_err(u, u_ex) <= (1e-10 if prec == "fp64" else 1e-6)
+
+
+def test_deep_hierarchy_large_z(dev):
+    """lambda tau = 1e3 with many levels (z up to ~1e7 on the coarsest level)."""
+    N = 1 << 14
+    p = 2
+    lam = 1e3 * N
+    prob = inputs.scalar_problem(3, N, p, lam=lam, T=1.0, u0=1.0)
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    for prec in ("fp64", "mixed"):
+        with tmg().Plan(p, prob["tau"], lam, N, precision=prec, n_min=1) as plan:
+            u = plan.solve(Fd, prob["u0"]).cpu().numpy()
+            assert plan.info()["levels"] == 15
+        assert rel_residual(p, lam * prob["tau"], prob["F"], prob["u0"], u) <= 1.05e-10
+
+
+def test_initial_guess_and_host_entry(dev):
+    N, p = 1 << 13, 1
+    prob = inputs.scalar_problem(5, N, p, lam=2.0, T=1.0, u0=1.0)
+    z = 2.0 * prob["tau"]
+    u_ex = O.fsub(p, z, prob["F"], prob["u0"])
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, prob["tau"], 2.0, N, precision="fp64", initial_guess=True, tol=1e-12) as plan:
+        u = torch.from_numpy(u_ex * (1 + 1e-6)).to(dev)
+        plan.solve(Fd, prob["u0"], u)
+        st = plan.stats()
+        # the start is 1e-6 from the solution: about log(1e-6)/log(rho ~ 0.25) = 10 cycles
+        assert st.hist[0] == pytest.approx(1e-6, rel=0.2) and st.cycles <= 12
+        assert rel_err(u.cpu().numpy(), u_ex) <= 1e-10
+    with tmg().Plan(p, prob["tau"], 2.0, N, precision="mixed") as plan:
+        out = torch.empty((N, p + 1), dtype=torch.float64).pin_memory()
+        plan.solve_host(torch.from_numpy(prob["F"]).pin_memory(), prob["u0"], out)
+        assert rel_residual(p, z, prob["F"], prob["u0"], out.numpy()) <= 1.05e-10
+
+
+def test_residual_entry_point(dev):
+    N, p = 3000, 3
+    prob = inputs.scalar_problem(9, N, p, lam=1.0, T=1.0, u0=0.4)
+    u = np.random.default_rng(0).standard_normal((N, p + 1))
+    with tmg().Plan(p, prob["tau"], 1.0, N) as plan:
+        r = plan.residual(torch.from_numpy(prob["F"]).to(dev), prob["u0"], torch.from_numpy(u).to(dev))
+    np.testing.assert_allclose(r.cpu().numpy(), O.residual(p, prob["tau"], prob["F"], prob["u0"], u),
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_graph_and_eager_agree_and_are_deterministic(dev):
+    N, p = 1 << 15, 1
+    prob = inputs.scalar_problem(2, N, p, lam=1.0, T=8.0, u0=1.0)
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    outs = []
+    for use_graph in (True, True, False):
+        with tmg().Plan(p, prob["tau"], 1.0, N, precision="mixed", use_graph=use_graph) as plan:
+            outs.append(plan.solve(Fd, prob["u0"]).cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+def test_not_converged_status(dev):
+    N, p = 1 << 12, 1
+    prob = inputs.scalar_problem(4, N, p, lam=1.0, T=1.0, u0=1.0)
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    T = tmg()
+    with T.Plan(p, prob["tau"], 1.0, N, max_cycles=2, tol=1e-14) as plan:
+        with pytest.raises(T.TmgError) as ei:
+            plan.solve(Fd, prob["u0"])
+        assert ei.value.status == T.TMG_ENOTCONV
+        u = plan.solve(Fd, prob["u0"], allow_notconv=True)
+        assert plan.stats().cycles == 2
+
+
+def test_full_size_long_horizon_sampled(dev):
+    """The benchmark workload (N = 2^24, tau = 1e-6, lambda = 1, p = 1), in the
+    launch configuration the benchmark times: FP64 residual of the whole GPU
+    result, and sampled intervals against exact forward substitution."""
+    N, p = 1 << 24, 1
+    prob = inputs.scalar_problem(1, N, p, lam=1.0, tau=1e-6, u0=1.0)
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, 1e-6, 1.0, N, precision="mixed") as plan:
+        u = plan.solve(Fd, prob["u0"])
+        r = plan.residual(Fd, prob["u0"], u)
+        st = plan.stats()
+    Fhat = O.fold_u0(p, prob["F"], prob["u0"])
+    rr = float(torch.linalg.vector_norm(r).item()) / np.linalg.norm(Fhat)
+    assert rr <= 1.05e-10, rr
+    u_ex = O.fsub(p, 1e-6, prob["F"], prob["u0"])
+    idx = np.random.default_rng(0).integers(0, N, 4096)
+    idx = np.concatenate([idx, [0, 1, N - 2, N - 1]])
+    uh = u.cpu().numpy()
+    err = np.abs(uh[idx] - u_ex[idx]).max() / np.abs(u_ex).max()
+    print(f"full size: cycles={st.cycles} rel_res={rr:.2e} sampled err={err:.2e}")
+    assert err <= 1e-6
