@@ -1,0 +1,352 @@
+"""Benchmark of the time-multigrid solve on GB300.
+
+Workload (one step = one full solve from u = 0 to relative residual 1e-10):
+one long horizon u' + lambda u = f, lambda = 1, tau = 1e-6, N = 2^24 intervals,
+p_t = 1 (Legendre), u0 = 1, f a seeded sum of 4 sinusoids; mixed precision
+(FP32 cycles inside FP64-accurate refinement), V(1,1) with the optimal damping
+per level.  The metric is time-DoFs/s = N (p_t+1) / solve time.  Inputs (268 MB
+load vector, 268 MB solution) are resident in HBM and larger than L2.
+
+Also reported: the plain FP64 form and p_t = 0, 2, 3 on the same horizon,
+per-kernel times and the HBM roofline of the dominant kernel, an end-to-end
+number through the host-array entry point, and the CPU oracle.
+
+--impl reference times the FP64 CPU oracle (the textbook multigrid) on a
+bounded sample of the same workload.  Multi-GPU: the single long-horizon
+problem does not shard; N > 1 ranks run independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FULL = 1 << 24
+TAU = 1e-6
+LAM = 1.0
+U0 = 1.0
+P_MAIN = 1
+TOL = 1e-10
+METRIC = "time-DoFs/s solved to 1e-10 rel residual"
+WORKLOAD = "long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate refinement, V(1,1), omega*"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cycle_bytes(N: int, d: int, elem: int, lt: int):
+    """Algorithmic HBM bytes of one correction cycle and of its two level-0 kernels.
+
+    Level 0 down: read u, F (FP64), write r (elem) and the level-1 RHS (N/2 x elem).
+    Level 0 up: read r, level-1 correction, u; write u.  Level l >= 1 below the
+    on-chip solver: down reads f_l, writes f_{l+1}; up reads f_l and u_{l+1},
+    writes u_l.  The on-chip solver reads f_lt and writes u_lt once.
+    """
+    nd = N * d
+    down0 = nd * (8 + 8 + elem) + (N // 2) * d * elem
+    up0 = nd * (elem + 8 + 8) + (N // 2) * d * elem
+    coarse = 0
+    for l in range(1, lt):
+        nl = (N >> l) * d
+        coarse += (nl + nl // 2) * elem + (nl + nl // 2 + nl) * elem
+    tail_io = 2 * (N >> lt) * d * elem if lt > 0 else 0
+    return {"down0": down0, "up0": up0, "cycle": down0 + up0 + coarse + tail_io}
+
+
+def time_solves(plan, F, u, steps: int, stream, torch):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        plan.solve(F, U0, u)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1409_5254_gb300 import inputs, tmg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    hbm_peak, peak_kind = peaks()
+
+    d = P_MAIN + 1
+    prob = inputs.scalar_problem(1, N_FULL, P_MAIN, lam=LAM, tau=TAU, u0=U0)
+    F = torch.from_numpy(prob["F"]).to(dev)
+    u = torch.empty_like(F)
+    plan = tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, use_graph=not args.eager)
+    for _ in range(args.warmup):
+        plan.solve(F, U0, u)
+    st = plan.stats()
+    info = plan.info()
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ms = time_solves(plan, F, u, args.steps, stream, torch)
+    clk.stop()
+    ms_t = torch.tensor([ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    st = plan.stats()
+    value = world * N_FULL * d / (ms * 1e-3)
+
+    # accuracy of the timed result, in FP64 on the GPU (residual entry point)
+    r = plan.residual(F, U0, u)
+    Fh = torch.from_numpy(prob["F"].copy()).to(dev)
+    Fh[0, 0] += U0
+    Fh[0, 1] -= U0
+    rel_fp64 = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(Fh))
+
+    # per-kernel times of one cycle (events on the plan's stream) and the roofline
+    prof = plan.profile_cycle(F, U0, u.clone(), reps=20)
+    cb = cycle_bytes(N_FULL, d, 4, info["tail_level"])
+    dom = "down0" if prof["down0"] >= prof["up0"] else "up0"
+    achieved = cb[dom] / (prof[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_down0" if dom == "down0" else "k_up0", "achieved": round(achieved, 1),
+                "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": args.traffic if args.traffic else None,
+                "bytes_per_launch": cb[dom], "launch_ms": round(prof[dom], 5),
+                "cycle_bytes": cb["cycle"], "cycle_ms": round(prof["cycle"], 5),
+                "cycle_frac": round(cb["cycle"] / (prof["cycle"] * 1e-3) / 1e9 / hbm_peak, 4),
+                "kernel_ms": {k: round(v, 5) for k, v in prof.items()}}
+
+    kernels_per_cycle = 3 if info["tail_level"] == 0 else 2 * info["tail_level"] + 1
+    launches = args.steps * (st.cycles + 1) * kernels_per_cycle
+
+    extra = {}
+    if rank == 0 and not args.quick:
+        # plain FP64 form on the same problem
+        with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="fp64", tol=TOL, stream=stream,
+                      use_graph=not args.eager) as p64:
+            p64.solve(F, U0, u)
+            ms64 = time_solves(p64, F, u, max(2, args.steps // 4), stream, torch)
+            s64 = p64.stats()
+        extra["fp64_form"] = {"value": N_FULL * d / (ms64 * 1e-3), "ms_per_step": round(ms64, 4),
+                              "cycles": s64.cycles, "rel_res": s64.rel_res}
+        # the other degrees of the same long horizon, mixed precision
+        per_p = {}
+        for p in (0, 2, 3):
+            pr = inputs.scalar_problem(1, N_FULL, p, lam=LAM, tau=TAU, u0=U0)
+            Fp = torch.from_numpy(pr["F"]).to(dev)
+            up = torch.empty_like(Fp)
+            try:
+                with tmg.Plan(p, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, max_cycles=300,
+                              use_graph=not args.eager) as pp:
+                    pp.solve(Fp, U0, up)
+                    msp = time_solves(pp, Fp, up, max(2, args.steps // 4), stream, torch)
+                    sp = pp.stats()
+                    per_p[str(p)] = {"value": N_FULL * (p + 1) / (msp * 1e-3), "ms_per_step": round(msp, 4),
+                                     "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": "V(1,1)"}
+            except tmg.TmgError as e:
+                per_p[str(p)] = {"error": str(e)}
+            del Fp, up
+        extra["per_p_mixed"] = per_p
+
+    # end to end through the host-array entry point (pinned buffers, copies inside the call)
+    F_h = torch.from_numpy(prob["F"]).pin_memory()
+    u_h = torch.empty_like(F_h).pin_memory()
+    plan.solve_host(F_h, U0, u_h)
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    n_e2e = max(3, args.steps // 2)
+    for _ in range(n_e2e):
+        plan.solve_host(F_h, U0, u_h)
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    t_t = torch.tensor([t_e2e], device=dev)
+    if dist is not None:
+        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
+    t_e2e = float(t_t.item())
+    nbytes = N_FULL * d * 8
+    e2e = {"value": world * N_FULL * d / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "ms_per_step": round(t_e2e * 1e3, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    plan.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N_FULL, "p_t": P_MAIN, "tau": TAU, "lambda": LAM, "u0": U0,
+                           "tol": TOL, "cycles": st.cycles, "levels": info["levels"],
+                           "tail_level": info["tail_level"], "precision": "mixed",
+                           "l2": "inputs larger than L2 (268 MB load vector + 268 MB solution)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "rel_res_fp64": rel_fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary()}
+        line.update(extra)
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sample_N: int = 1 << 18):
+    """The FP64 oracle as it stands (textbook multigrid, one host thread) on the
+    first sample_N intervals of the same workload (same tau, lambda, p_t, forcing)."""
+    import numpy as np
+
+    import oracle
+    from paper_1409_5254_gb300 import inputs
+
+    d = P_MAIN + 1
+    T = N_FULL * TAU
+    forcing = inputs.Forcing.draw(np.random.default_rng(1), T)
+    F = _sample_load_vector(P_MAIN, sample_N, T, forcing)
+    t0 = time.perf_counter()
+    _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100)
+    t_mg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.fsub(P_MAIN, LAM * TAU, F, U0)
+    t_fs = time.perf_counter() - t0
+    return {"value": sample_N * d / t_mg, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_N} of the 2^24 intervals, textbook multigrid to 1e-10 ({len(hist) - 1} cycles), "
+                      f"{t_mg:.2f} s",
+            "fsub_value": sample_N * d / t_fs, "fsub_note": "exact forward substitution, same sample"}
+
+
+def _sample_load_vector(p, n, T, forcing):
+    """Load vector of the first n intervals of the 2^24-interval mesh (same step)."""
+    from paper_1409_5254_gb300 import inputs
+    return inputs.load_vector(p, N_FULL, T, forcing, n_stop=n)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1409_5254_gb300 import inputs
+
+    n = 1 << 16
+    d = P_MAIN + 1
+    T = N_FULL * TAU
+    forcing = inputs.Forcing.draw(np.random.default_rng(1), T)
+    F = _sample_load_vector(P_MAIN, n, T, forcing)
+    for _ in range(args.warmup):
+        oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = n * d / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_FULL, "p_t": P_MAIN, "tau": TAU, "lambda": LAM, "tol": TOL},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {n} of the 2^24 intervals per step, textbook multigrid "
+                                       f"({len(hist) - 1} cycles)"},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the FP64-form and other-degree side runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the dominant kernel")
+    ap.add_argument("--eager", action="store_true", help="host-driven cycle loop instead of the CUDA graph (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -128,6 +128,17 @@ tmg_status tmg_plan_info(const tmg_plan *plan, int *num_levels, int *tail_level,
                          double *omega_per_level, int omega_len);
 
 /*
+ * Measurement helper: apply reps correction cycles to u (as tmg_cycle) with a
+ * CUDA event recorded on the plan's stream around every kernel, and return the
+ * mean milliseconds per cycle in ms[0..5]: level-0 down kernel (or the level-0
+ * residual when the whole correction runs on chip), all streaming down kernels
+ * of levels >= 1, the on-chip coarse solver, all streaming up kernels, the
+ * level-0 up kernel (or update), and the whole cycle.  n_ms >= 6.
+ */
+tmg_status tmg_profile_cycle(tmg_plan *plan, const double *f, double u0, double *u, int reps, double *ms,
+                             int n_ms);
+
+/*
  * Copy one of the plan's internal level vectors to host memory (inspection
  * and testing; synchronises the stream).  which: 0 = right-hand side f_l,
  * 1 = correction u_l of level l (levels 0..tail level), 2 = the level-0

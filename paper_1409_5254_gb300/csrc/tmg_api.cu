@@ -471,6 +471,45 @@ tmg_status tmg_plan_info(const tmg_plan* P, int* num_levels, int* tail_level, in
     return TMG_OK;
 }
 
+tmg_status tmg_profile_cycle(tmg_plan* P, const double* f, double u0, double* u, int reps, double* ms, int n_ms) {
+    if (!P || reps < 1 || !ms || n_ms < 6 || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK)
+        return TMG_EINVAL;
+    const int nk = P->lt == 0 ? 3 : 2 * P->lt + 1;    // kernels per cycle
+    std::vector<cudaEvent_t> ev(nk + 1);
+    for (auto& e : ev) TMG_CUDA(cudaEventCreate(&e));
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    tmg_status status = TMG_OK;
+    for (int r = 0; r < reps && status == TMG_OK; ++r) {
+        status = stage_state(P, f, u0, u, -1.0, 1 << 30, 0, 1);
+        if (status != TMG_OK) break;
+        cudaError_t e = P->ops->enqueue_cycle_timed(P, ev.data());
+        if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
+        if (e != cudaSuccess) {
+            status = cuda_fail(e);
+            break;
+        }
+        std::vector<float> t(nk);
+        for (int k = 0; k < nk; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
+        acc[0] += t[0];
+        if (P->lt == 0) {
+            acc[2] += t[1];
+            acc[4] += t[2];
+        } else {
+            for (int k = 1; k < P->lt; ++k) acc[1] += t[k];
+            acc[2] += t[P->lt];
+            for (int k = P->lt + 1; k < 2 * P->lt; ++k) acc[3] += t[k];
+            acc[4] += t[2 * P->lt];
+        }
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, ev[0], ev[nk]);
+        acc[5] += tot;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int i = 0; i < 6; ++i) ms[i] = acc[i] / reps;
+    for (int i = 6; i < n_ms; ++i) ms[i] = 0.0;
+    return status;
+}
+
 tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, size_t bytes) {
     if (!P || !host_dst || which < 0 || which > 2) return TMG_EINVAL;
     const void* src = nullptr;

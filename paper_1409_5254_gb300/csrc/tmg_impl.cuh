@@ -73,7 +73,16 @@ struct Impl {
         return cudaMemcpyAsync(P->lk_dev, lk.data(), sizeof(LevelK<T, D>) * nl, cudaMemcpyHostToDevice, P->s);
     }
 
-    static cudaError_t enqueue_cycle(tmg_plan* P) {
+    static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr); }
+
+    // One correction cycle.  With ev != nullptr an event is recorded before
+    // every kernel and after the last one (2*lt + 2 events, or 4 when the
+    // on-chip solver starts at level 0).
+    static cudaError_t enqueue_cycle_timed(tmg_plan* P, cudaEvent_t* ev) {
+        int iev = 0;
+        auto mark = [&]() {
+            if (ev) cudaEventRecord(ev[iev++], P->s);
+        };
         const int nu1 = P->o.nu1, nu2 = P->o.nu2;
         const Xfer<T, D> X = xfer_consts<T, D>(P);
         const Res0 R = res0_consts(P);
@@ -81,16 +90,21 @@ struct Impl {
         const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(P->lk_dev);
         T* rT = static_cast<T*>(P->rT);
         if (P->lt == 0) {
+            mark();
             k_res0<T, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(rT, P->N, R, P->partials, P->st);
+            mark();
             k_tail<T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N, nu1,
                                                              nu2, P->o.gamma, P->st);
+            mark();
             k_update0<T><<<grid_flat(P, P->N * D), kNT, 0, P->s>>>(static_cast<const T*>(P->ul[0]), P->N * D,
                                                                     P->st);
+            mark();
             return cudaGetLastError();
         }
         {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
+            mark();
             k_down0<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
                                                                   level_consts<T, D>(P->lev[0]), X, nu1, H,
                                                                   P->partials, P->st);
@@ -98,16 +112,19 @@ struct Impl {
         for (int l = 1; l < P->lt; ++l) {
             const int H = halo_lanes(sweeps_down(nu1));
             const int64_t nch = P->lev[l].N / 2;
+            mark();
             k_down<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
                                                                  static_cast<T*>(P->fl[l + 1]), nch,
                                                                  level_consts<T, D>(P->lev[l]), X, nu1, H, P->st);
         }
+        mark();
         k_tail<T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
                                                          static_cast<T*>(P->ul[P->lt]), lk, X, nl,
                                                          P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
         for (int l = P->lt - 1; l >= 1; --l) {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->lev[l].N / 2;
+            mark();
             k_up<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
                                                                static_cast<const T*>(P->ul[l + 1]),
                                                                static_cast<T*>(P->ul[l]), nch,
@@ -117,10 +134,12 @@ struct Impl {
         {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->N / 2;
+            mark();
             k_up0<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<const T*>(P->ul[1]), nch,
                                                                 level_consts<T, D>(P->lev[0]), X, nu1, nu2, H,
                                                                 P->st);
         }
+        mark();
         return cudaGetLastError();
     }
 
@@ -135,8 +154,8 @@ struct Impl {
     }
 
     static const tmg_ops* ops() {
-        static const tmg_ops o = {sizeof(T), &tail_bytes, &upload, &enqueue_cycle, &enqueue_normF,
-                                  &enqueue_residual, &set_tail_attr};
+        static const tmg_ops o = {sizeof(T), &tail_bytes, &upload, &enqueue_cycle, &enqueue_cycle_timed,
+                                  &enqueue_normF, &enqueue_residual, &set_tail_attr};
         return &o;
     }
 };

@@ -59,16 +59,19 @@ def _legendre_table(p: int, s: np.ndarray) -> np.ndarray:
     return np.stack([np.polynomial.legendre.legval(x, np.eye(p + 1)[l]) for l in range(p + 1)], axis=1)
 
 
-def load_vector(p: int, N: int, T: float, f, q: int = 8, chunk: int = 1 << 20) -> np.ndarray:
-    """Load vector (N, p+1) of forcing ``f`` on the uniform mesh t_n = n T / N."""
+def load_vector(p: int, N: int, T: float, f, q: int = 8, chunk: int = 1 << 20,
+                n_stop: int | None = None) -> np.ndarray:
+    """Load vector (N, p+1) of forcing ``f`` on the uniform mesh t_n = n T / N
+    (only the first n_stop intervals when given)."""
     tau = T / N
     xg, wg = np.polynomial.legendre.leggauss(q)
     s = 0.5 * (xg + 1.0)
     w = 0.5 * wg
     tab = _legendre_table(p, s) * w[:, None]          # (q, d)
-    out = np.empty((N, p + 1), dtype=np.float64)
-    for n0 in range(0, N, chunk):
-        n1 = min(N, n0 + chunk)
+    n_out = N if n_stop is None else min(N, n_stop)
+    out = np.empty((n_out, p + 1), dtype=np.float64)
+    for n0 in range(0, n_out, chunk):
+        n1 = min(n_out, n0 + chunk)
         t = (np.arange(n0, n1, dtype=np.float64)[:, None] + s[None, :]) * tau
         out[n0:n1] = tau * (f(t) @ tab)
     return out

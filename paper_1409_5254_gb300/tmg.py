@@ -40,7 +40,7 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual",
-           "tmg_stats", "tmg_plan_info", "tmg_inspect", "tmg_destroy", "tmg_strerror", "tmg_last_cuda_error"]
+           "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_destroy", "tmg_strerror", "tmg_last_cuda_error"]
 
 
 def library_path() -> str:
@@ -67,13 +67,14 @@ def _lib():
         L.tmg_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int]
         L.tmg_inspect.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]
+        L.tmg_profile_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp, ctypes.c_int, _dp, ctypes.c_int]
         L.tmg_destroy.argtypes = [_vp]
         L.tmg_destroy.restype = None
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
         for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual", "tmg_stats",
-                     "tmg_plan_info", "tmg_inspect"):
+                     "tmg_plan_info", "tmg_inspect", "tmg_profile_cycle"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -179,6 +180,14 @@ class Plan:
                                 hist.ctypes.data_as(_dp), hist_len), "tmg_stats")
         h = hist[: cyc.value + 1].copy()
         return SolveStats(getattr(self, "last_status", TMG_OK), cyc.value, rel.value, h)
+
+    def profile_cycle(self, f, u0: float, u, reps: int = 10) -> dict:
+        """Mean per-kernel milliseconds of one correction cycle (CUDA events on the plan's stream)."""
+        ms = np.zeros(6)
+        _check(_lib().tmg_profile_cycle(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
+                                        _dev_ptr(u, self.d, self.N, "u"), reps, ms.ctypes.data_as(_dp), 6),
+               "tmg_profile_cycle")
+        return dict(zip(["down0", "down_levels", "coarse_on_chip", "up_levels", "up0", "cycle"], ms.tolist()))
 
     def inspect(self, which: str, level: int = 0) -> np.ndarray:
         """Copy an internal level vector ('f', 'u' of a level, or the level-0 residual 'r') to host."""
