@@ -148,6 +148,30 @@ tmg_status tmg_profile_cycle(tmg_plan *plan, const double *f, double u0, double 
  */
 tmg_status tmg_inspect(const tmg_plan *plan, int which, int level, void *host_dst, size_t bytes);
 
+/*
+ * Residual r = F - L u (FP64, written to r) and its norm ||r||_2 (written to
+ * the single device double *norm), with no plan and no device allocation --
+ * for callers that may not allocate device memory where they need this check
+ * (code inside another library's stream capture, real-time loops that cannot
+ * take the device synchronisation an allocation may cause, applications whose
+ * device memory all belongs to their own pool).  The paper has no counterpart;
+ * it is the level-0 residual kernel with its block partial sums kept in a
+ * fixed file-scope device array instead of a plan workspace.
+ *
+ * p_t, tau, lambda, N, f, u0, u as for tmg_setup/tmg_solve; f, u, r device
+ * [N][p_t+1] float64, 16-byte aligned; norm an 8-byte aligned device double.
+ * N may not exceed 2^21 intervals (the scratch array holds 1024 block partial
+ * sums of 2048 intervals each): larger N returns TMG_EUNSUPPORTED before any
+ * GPU work.  The first call on a device looks up the scratch array's device
+ * address with that device current; make that first call before any stream
+ * capture.  Every call on a device shares the array and leaves its contents
+ * behind; calls whose kernels may overlap on the GPU (unordered streams) race
+ * on it and must be serialised by the caller.  Asynchronous on stream
+ * (a cudaStream_t; NULL = legacy default stream).
+ */
+tmg_status tmg_residual_norm_noalloc(int p_t, double tau, double lambda, int64_t N, const double *f, double u0,
+                                     const double *u, double *r, double *norm, void *stream);
+
 /* Release the plan and every resource it owns.  NULL is ignored. */
 void tmg_destroy(tmg_plan *plan);
 

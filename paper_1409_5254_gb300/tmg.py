@@ -40,7 +40,8 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual",
-           "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_destroy", "tmg_strerror", "tmg_last_cuda_error"]
+           "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
+           "tmg_last_cuda_error"]
 
 
 def library_path() -> str:
@@ -68,6 +69,9 @@ def _lib():
                                     ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int]
         L.tmg_inspect.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]
         L.tmg_profile_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp, ctypes.c_int, _dp, ctypes.c_int]
+        L.tmg_residual_norm_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                                _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
+        L.tmg_residual_norm_noalloc.restype = ctypes.c_int
         L.tmg_destroy.argtypes = [_vp]
         L.tmg_destroy.restype = None
         L.tmg_strerror.argtypes = [ctypes.c_int]
@@ -222,3 +226,19 @@ def _host_ptr(x, d: int, N: int) -> int:
     if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != N * d:
         raise TypeError("host array must be contiguous float64 with N*d elements")
     return a.ctypes.data
+
+
+def residual_norm_noalloc(p: int, tau: float, lam: float, f, u0: float, u, r, norm, stream=None) -> None:
+    """r = F - L u and ||r||_2 (into the one-element float64 CUDA tensor ``norm``)
+    through tmg_residual_norm_noalloc: no plan and no device allocation, for
+    callers that may not allocate device memory at that point.  Asynchronous on
+    ``stream`` (default: the legacy default stream)."""
+    d = p + 1
+    N = f.numel() // d
+    import torch
+    if not (isinstance(norm, torch.Tensor) and norm.is_cuda and norm.dtype == torch.float64 and norm.numel() == 1):
+        raise TypeError("norm must be a one-element float64 CUDA tensor")
+    sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    _check(_lib().tmg_residual_norm_noalloc(p, tau, lam, N, _dev_ptr(f, d, N, "f"), float(u0), _dev_ptr(u, d, N, "u"),
+                                            _dev_ptr(r, d, N, "r"), ctypes.c_void_p(norm.data_ptr()), sp),
+           "tmg_residual_norm_noalloc")
