@@ -29,7 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_FULL = 1 << 24
+N_FULL = 1 << 24          # overridden by --n-log2 (profiling cases)
 TAU = 1e-6
 LAM = 1.0
 U0 = 1.0
@@ -341,7 +341,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the dominant kernel")
     ap.add_argument("--eager", action="store_true", help="host-driven cycle loop instead of the CUDA graph (profiling)")
+    ap.add_argument("--n-log2", type=int, default=24, help="intervals = 2^n (smaller cases for ncu captures)")
     args = ap.parse_args()
+    global N_FULL
+    N_FULL = 1 << args.n_log2
     if args.impl == "reference":
         run_reference(args)
     else:

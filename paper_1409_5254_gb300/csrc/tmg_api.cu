@@ -211,6 +211,8 @@ tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, doubl
     h->nF_from_first = nF_from_first;
     h->use_cond = use_cond;
     h->ticket = 0u;
+    h->nscale = 1.0f;
+    h->nvals = (long long)P->N * P->d;
     h->cond = P->cond;
     TMG_CUDA(cudaMemcpyAsync(P->st, h, offsetof(tmg::DevState, hist), cudaMemcpyHostToDevice, P->s));
     return TMG_OK;

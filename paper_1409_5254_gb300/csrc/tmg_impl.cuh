@@ -33,7 +33,11 @@ Xfer<T, D> xfer_consts(const tmg_plan* P) {
 
 inline Res0 res0_consts(const tmg_plan* P) {
     Res0 R;
-    for (int k = 0; k < kMaxD; ++k) R.zm[k] = P->lev[0].z / (2.0 * k + 1.0);
+    for (int k = 0; k < kMaxD; ++k) {
+        R.zm[k] = P->lev[0].z / (2.0 * k + 1.0);
+        R.zm_hi[k] = (float)R.zm[k];
+        R.zm_lo[k] = (float)(R.zm[k] - (double)R.zm_hi[k]);
+    }
     return R;
 }
 

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace tmg {
 
 constexpr int kMaxD = 4;
@@ -50,9 +52,12 @@ struct Xfer {
     T P2[D * D];
 };
 
-// Level-0 residual constants (FP64): zm[k] = z_0 / (2k+1).
+// Level-0 residual constants: zm[k] = z_0 / (2k+1) in FP64 and as an
+// unevaluated float pair zm_hi + zm_lo.
 struct Res0 {
     double zm[kMaxD];
+    float zm_hi[kMaxD];
+    float zm_lo[kMaxD];
 };
 
 // Device-resident solve state.  Written by the last block of the residual
@@ -69,6 +74,8 @@ struct DevState {
     int nF_from_first;    // 1: the first residual (u = 0) defines ||F||
     int use_cond;         // 1: the solve runs as a graph while-loop
     unsigned ticket;      // last-block ticket
+    float nscale;         // power of two that brings the residual near 1 (FP32 norm)
+    long long nvals;      // values per residual vector, N * D
     unsigned long long cond;   // cudaGraphConditionalHandle of that loop
     double hist[kHist];   // relative residual before each cycle
 };
@@ -284,6 +291,102 @@ __device__ __forceinline__ void residual0(const double (&F)[D], const double (&u
     }
 }
 
+// ------------------------------------- level-0 residual without FP64 math --
+//
+// GB300 issues about two FP64 operations per clock per SM, so the level-0
+// residual of the mixed form is evaluated with one FP64 operation per
+// interval.  Write e_n = u_n[0] + s_n with s_n = sum_{l>=1} u_n[l].  Then
+// e_{n-1} - e_n = d + s_{n-1} - s_n with d = u_{n-1}[0] - u_n[0], and the
+// Legendre form of r (see residual0) becomes
+//   r[k] = F[k] + a_k (d + s_{n-1}) - s_n + 2 [k>=2] u_n[k-1] - z/(2k+1) u_n[k].
+// Only d cancels two O(|u|) numbers; it is one FP64 subtraction (exact when
+// the two values are within a factor two).  Every other term is of the size
+// of the residual's own parts (tau-scale for smooth solutions), so each double
+// is split into a float pair hi + lo with integer operations and the terms are
+// summed with compensated FP32 arithmetic (error ~2^-48 of the terms).
+
+struct ff {
+    float hi, lo;
+};
+
+// x = hi + lo: hi is x truncated to 24 significant bits, lo the remaining 29
+// bits truncated to 24.  Integer operations only.  |x| < 2^-126 gives 0;
+// |x| >= 2^128 (or Inf/NaN) gives +-Inf so that the norm flags it.
+__device__ __forceinline__ ff split_d(double x) {
+    const unsigned hw = (unsigned)__double2hiint(x);
+    const unsigned lw = (unsigned)__double2loint(x);
+    const unsigned sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const unsigned r29 = lw & 0x1FFFFFFFu;
+    ff out;
+    if (e < 897) {
+        out.hi = 0.f;
+        out.lo = 0.f;
+    } else if (e > 1150) {
+        out.hi = __uint_as_float(sign | 0x7F800000u);
+        out.lo = 0.f;
+    } else {
+        out.hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | m23);
+        const int lz = __clz(r29);                  // 32 when r29 == 0
+        const int fe = e - 1075 + 31 - lz + 127;    // biased exponent of lo
+        const unsigned mant = ((r29 << (lz & 31)) >> 8) & 0x7FFFFFu;
+        out.lo = (r29 != 0u && fe > 0) ? __uint_as_float(sign | ((unsigned)fe << 23) | mant) : 0.f;
+    }
+    return out;
+}
+
+// Compensated accumulation: (s, c) += th + tl, with the rounding error of the
+// leading sum kept in c (Knuth's two-sum).
+__device__ __forceinline__ void acc_add(float& s, float& c, float th, float tl) {
+    const float t = s + th;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (th - bp);
+    s = t;
+    c += err + tl;
+}
+
+// Product of two float pairs (lo*lo dropped), as an unnormalised pair.
+__device__ __forceinline__ ff mul_ff(float ah, float al, ff b) {
+    ff p;
+    p.hi = ah * b.hi;
+    float e = fmaf(ah, b.hi, -p.hi);
+    e = fmaf(ah, b.lo, e);
+    p.lo = fmaf(al, b.hi, e);
+    return p;
+}
+
+// s_n = sum_{l>=1} u[l] as a float pair (0 for D = 1).
+template <int D>
+__device__ __forceinline__ ff small_sum(const double (&u)[D], ff (&us)[D]) {
+    ff s{0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < D; ++l) us[l] = split_d(u[l]);
+#pragma unroll
+    for (int l = 1; l < D; ++l) acc_add(s.hi, s.lo, us[l].hi, us[l].lo);
+    return s;
+}
+
+// r[k] of one interval, rounded to float.  up0 = u_{n-1}[0], sp = s_{n-1}.
+template <int D>
+__device__ __forceinline__ void residual0_ff(const double (&F)[D], const double (&u)[D], const ff (&us)[D],
+                                             double up0, ff sp, ff sn, const Res0& R, float (&r)[D]) {
+    const ff d = split_d(up0 - u[0]);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const ff Fk = split_d(F[k]);
+        float s = Fk.hi, c = Fk.lo;
+        const float sg = (k & 1) ? -1.f : 1.f;
+        acc_add(s, c, sg * d.hi, sg * d.lo);
+        acc_add(s, c, sg * sp.hi, sg * sp.lo);
+        acc_add(s, c, -sn.hi, -sn.lo);
+        if (k >= 2) acc_add(s, c, 2.f * us[k - 1].hi, 2.f * us[k - 1].lo);
+        const ff zu = mul_ff(R.zm_hi[k], R.zm_lo[k], us[k]);
+        acc_add(s, c, -zu.hi, -zu.lo);
+        r[k] = s + c;
+    }
+}
+
 // ------------------------------------------------- norm and stopping test --
 
 // First kernel of a cycle: a finished solve must also end the graph loop.
@@ -300,6 +403,12 @@ __device__ __forceinline__ void finalize_state(DevState* st, double ss) {
     if (k == 0 && st->nF_from_first) st->nF = nrm;
     const double rel = st->nF > 0.0 ? nrm / st->nF : nrm;
     st->hist[k < kHist ? k : kHist - 1] = rel;
+    // scale for the next FP32 norm: 2^-round(log2(rms)), kept well inside FP32 range
+    const double rms = st->nvals > 0 ? nrm / sqrt((double)st->nvals) : 0.0;
+    int ex = 0;
+    if (rms > 0.0 && rms < 1.0e300) ex = -ilogb(rms);
+    ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
+    st->nscale = ldexpf(1.0f, ex);
     int done = 0;
     if (!(rel == rel) || rel > 1.0e300) done = 3;
     else if (rel <= st->tol) done = 1;
@@ -409,35 +518,73 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
     const double* __restrict__ F = st->F;
     const double* __restrict__ uu = st->u;
     const double u0 = st->u0;
+    constexpr bool kMixed = std::is_same<T, float>::value;
+    // FP32 norm with a power-of-two scale, except in the first cycle whose
+    // residual magnitude is not known yet (FP64 then)
+    const bool fp64_norm = !kMixed || st->cycle == 0;
+    const float nsc = st->nscale;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int64_t ntiles = (nchunks + per - 1) / per;
     const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
     double ss = 0.0;
+    float ssf = 0.f;
     for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
         const int64_t q = tw * per + lane - H;
         const bool inb = q >= 0 && q < nchunks;
         const bool own = inb && lane >= H;
-        double uv[2][D], Fv[2][D], r[2][D];
+        double uv[2][D], Fv[2][D];
         load_pair<double, D>(uu, q, inb, uv);
         load_pair<double, D>(F, q, inb, Fv);
-        const double e0 = endval<double, D>(uv[0]);
-        double e1 = endval<double, D>(uv[1]);
-        if (q < 0) e1 = u0;                       // the value before the first interval
-        const double ep = shfl_prev(e1);
-        residual0<D>(Fv[0], uv[0], ep, e0, R, r[0]);
-        residual0<D>(Fv[1], uv[1], e0, e1, R, r[1]);
-        // Lanes outside the array carry u0 only as the halo of the FP64
-        // residual; for the correction equation L c = r their r is zero.
         T rt[2][D];
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
+        if constexpr (kMixed) {
+            ff us0[D], us1[D];
+            const ff s0 = small_sum<D>(uv[0], us0);
+            ff s1 = small_sum<D>(uv[1], us1);
+            double h0 = uv[1][0];
+            if (q < 0) {                        // the value before the first interval: e = u0
+                h0 = u0;
+                s1 = ff{0.f, 0.f};
+            }
+            const double up0 = shfl_prev(h0);
+            const ff sp{shfl_prev(s1.hi), shfl_prev(s1.lo)};
+            float r0[D], r1[D];
+            residual0_ff<D>(Fv[0], uv[0], us0, up0, sp, s0, R, r0);
+            residual0_ff<D>(Fv[1], uv[1], us1, uv[0][0], s0, s1, R, r1);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                rt[i][k] = inb ? (T)r[i][k] : T(0);
-                if (own) ss = fma(r[i][k], r[i][k], ss);
+                rt[0][k] = inb ? r0[k] : 0.f;
+                rt[1][k] = inb ? r1[k] : 0.f;
             }
-        if (own) store_pair<T, D>(rT, q, rt);
+        } else {
+            double r[2][D];
+            const double e0 = endval<double, D>(uv[0]);
+            double e1 = endval<double, D>(uv[1]);
+            if (q < 0) e1 = u0;                   // the value before the first interval
+            const double ep = shfl_prev(e1);
+            residual0<D>(Fv[0], uv[0], ep, e0, R, r[0]);
+            residual0<D>(Fv[1], uv[1], e0, e1, R, r[1]);
+            // Lanes outside the array carry u0 only as the halo of the FP64
+            // residual; for the correction equation L c = r their r is zero.
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) rt[i][k] = inb ? (T)r[i][k] : T(0);
+        }
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if (fp64_norm) {
+                        ss = fma((double)rt[i][k], (double)rt[i][k], ss);
+                    } else {
+                        const float v = (float)rt[i][k] * nsc;
+                        ssf = fmaf(v, v, ssf);
+                    }
+                }
+            store_pair<T, D>(rT, q, rt);
+        }
         if (fc != nullptr) {
             T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
             presmooth_zero<T, D>(K, rt, h, c, w, nu1);
@@ -446,6 +593,7 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
             if (own) VecIO<T, D>::store(fc + q * D, out);
         }
     }
+    if (!fp64_norm) ss = (double)ssf / ((double)nsc * (double)nsc);
     grid_norm_finalize<kNT>(ss, partials, st);
 }
 

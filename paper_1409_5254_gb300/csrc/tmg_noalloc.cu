@@ -134,7 +134,11 @@ extern "C" tmg_status tmg_residual_norm_noalloc(int p_t, double tau, double lamb
     if (e != cudaSuccess) return TMG_ECUDA;
 
     tmg::Res0 R;
-    for (int k = 0; k < tmg::kMaxD; ++k) R.zm[k] = lambda * tau / (2.0 * k + 1.0);
+    for (int k = 0; k < tmg::kMaxD; ++k) {
+        R.zm[k] = lambda * tau / (2.0 * k + 1.0);
+        R.zm_hi[k] = (float)R.zm[k];
+        R.zm_lo[k] = (float)(R.zm[k] - (double)R.zm_hi[k]);
+    }
     const int blocks = (int)((N + kPerBlock - 1) / kPerBlock);
     switch (p_t) {
         case 0: k_residual_norm_static<1><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
