@@ -108,6 +108,23 @@ tmg_status tmg_solve(tmg_plan *plan, const double *f, double u0, double *u);
 tmg_status tmg_solve_host(tmg_plan *plan, const double *f_host, double u0, double *u_host);
 
 /*
+ * Gradients of a loss J(u) at the solution u of L u = F, through the adjoint
+ * system L^T mu = g with g = dJ/du (device [N][p_t+1]).  L^T has diagonal
+ * blocks A^T and super-diagonal blocks -N^T = -b a^T (the transpose of eq.
+ * chap4_generalLinearSystemODE), i.e. it couples each interval to the NEXT
+ * one; read in reversed time it has the same block lower-bidiagonal form, so
+ * the library solves it with the same multigrid cycle on reversed arrays (the
+ * transfer operators keep R = P^T; the Galerkin identity transposes).  The
+ * plan's tolerance applies relative to ||g||.  Outputs: dJdf = mu (device
+ * [N][p_t+1]); *dJdu0 = a^T mu_1 (u0 enters F_1 as a*u0); *dJdlambda =
+ * -tau sum_n mu_n^T Mhat u_n (L depends on lambda through lambda*tau*Mhat);
+ * dJdu0 and dJdlambda are device doubles.  u must be the forward solution.
+ * The first call allocates a 2 N (p_t+1) double buffer owned by the plan.
+ */
+tmg_status tmg_adjoint(tmg_plan *plan, const double *g, const double *u, double *dJdf, double *dJdu0,
+                       double *dJdlambda);
+
+/*
  * Apply exactly one correction cycle to u in place (no convergence test):
  * u <- u + C (F - L u) with C one V/W-cycle in the plan's precision.
  */

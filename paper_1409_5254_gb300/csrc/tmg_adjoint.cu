@@ -1,0 +1,81 @@
+// Helpers of the adjoint solve: interval reversal and the gradient reductions.
+//
+// For a loss J(u) of the solution of L u = F (F = f with a*u0 in the first
+// interval), mu = L^{-T} dJ/du gives dJ/df = mu, dJ/du0 = a^T mu_0 and
+// dJ/dlambda = -tau sum_n mu_n^T Mhat u_n (L depends on lambda only through
+// the mass term lambda*tau*Mhat of every diagonal block, Section 2).
+#include <stdint.h>
+
+#include "tmg_plan.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) k_reverse(const double* __restrict__ src, double* __restrict__ dst,
+                                                      int64_t N, int d) {
+    const int64_t total = N * d;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += stride) {
+        const int64_t n = i / d, k = i - n * d;
+        dst[(N - 1 - n) * d + k] = src[i];
+    }
+}
+
+// Deterministic grid reduction of sum_n sum_k mu[n][k] u[n][k] / (2k+1); the
+// last block adds the partials in order and writes both gradients.
+__global__ void __launch_bounds__(kThreads) k_adjoint_grads(const double* __restrict__ mu, const double* __restrict__ u,
+                                                            int64_t N, int d, double tau,
+                                                            double* __restrict__ partials, unsigned* ticket,
+                                                            double* __restrict__ dJdu0,
+                                                            double* __restrict__ dJdlambda) {
+    double s = 0.0;
+    const int64_t total = N * d;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += stride) {
+        const int k = (int)(i % d);
+        s = fma(mu[i], u[i] / (2.0 * k + 1.0), s);
+    }
+    __shared__ double red[kThreads / 32];
+    __shared__ int last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        partials[blockIdx.x] = t;
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double tot = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(&partials[b]);
+    *dJdlambda = -tau * tot;
+    double g0 = 0.0;
+    for (int k = 0; k < d; ++k) g0 += (k & 1) ? -mu[k] : mu[k];   // a^T mu_0, a_k = (-1)^k
+    *dJdu0 = g0;
+    *ticket = 0u;
+}
+
+}  // namespace
+
+cudaError_t tmg_launch_reverse(const double* src, double* dst, int64_t N, int d, cudaStream_t s) {
+    int64_t blocks = (N * d + kThreads - 1) / kThreads;
+    if (blocks > 4096) blocks = 4096;
+    k_reverse<<<(int)blocks, kThreads, 0, s>>>(src, dst, N, d);
+    return cudaGetLastError();
+}
+
+cudaError_t tmg_launch_adjoint_grads(const double* mu, const double* u, int64_t N, int d, double tau,
+                                     double* partials, int max_blocks, unsigned* ticket, double* dJdu0,
+                                     double* dJdlambda, cudaStream_t s) {
+    int64_t blocks = (N * d + kThreads - 1) / kThreads;
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    k_adjoint_grads<<<(int)blocks, kThreads, 0, s>>>(mu, u, N, d, tau, partials, ticket, dJdu0, dJdlambda);
+    return cudaGetLastError();
+}

@@ -69,6 +69,25 @@ bool invert(int d, const double* A, double* Ainv) {
     return true;
 }
 
+// Constants of L^T written in reversed time: diagonal block A^T with coupling
+// a' = 1, b' = a, so g' = A^{-T} 1 = (b^T A^{-1})^T = c, c' = a^T A^{-T} = g,
+// and alpha' = a^T A^{-T} 1 = alpha (the same omega*).
+void level_setup_adjoint(int d, const tmg_level_host& F, tmg_level_host* L) {
+    L->N = F.N;
+    L->z = F.z;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            L->A[i * d + j] = F.A[j * d + i];
+            L->Ainv[i * d + j] = F.Ainv[j * d + i];
+        }
+    for (int k = 0; k < d; ++k) {
+        L->g[k] = F.c[k];
+        L->c[k] = F.g[k];
+    }
+    L->alpha = F.alpha;
+    L->omega = F.omega;
+}
+
 void level_setup(int d, double z, double omega_user, tmg_level_host* L) {
     L->z = z;
     local_blocks(d, z, L->A);
@@ -147,7 +166,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 const size_t kTailSmemMax = 200 * 1024;
 const int64_t kTailNmax = 8192;
 
-tmg_status build_graph(tmg_plan* P) {
+tmg_status build_graph(tmg_plan* P, int dir) {
     cudaGraph_t g = nullptr;
     TMG_CUDA(cudaGraphCreate(&g, 0));
     cudaGraphConditionalHandle h;
@@ -176,7 +195,7 @@ tmg_status build_graph(tmg_plan* P) {
         cudaGraphDestroy(g);
         return cuda_fail(e);
     }
-    cudaError_t ek = P->ops->enqueue_cycle(P);
+    cudaError_t ek = (dir == 0 ? P->ops : P->ops_adj)->enqueue_cycle(P);
     cudaGraph_t captured = nullptr;
     e = cudaStreamEndCapture(P->s, &captured);
     if (ek != cudaSuccess || e != cudaSuccess) {
@@ -189,15 +208,15 @@ tmg_status build_graph(tmg_plan* P) {
         cudaGraphDestroy(g);
         return cuda_fail(e);
     }
-    P->graph = g;
-    P->gexec = ex;
-    P->cond = (unsigned long long)h;
+    P->graph[dir] = g;
+    P->gexec[dir] = ex;
+    P->cond[dir] = (unsigned long long)h;
     return TMG_OK;
 }
 
 // Start-of-solve state: written through the pinned mirror with one copy.
 tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, double tol, int max_cycles,
-                       int use_cond, int nF_from_first) {
+                       int use_cond, int nF_from_first, int dir = 0) {
     tmg::DevState* h = P->st_host;
     TMG_CUDA(cudaStreamSynchronize(P->s));    // the mirror may still be read by a previous copy
     h->F = f;
@@ -213,7 +232,7 @@ tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, doubl
     h->ticket = 0u;
     h->nscale = 1.0f;
     h->nvals = (long long)P->N * P->d;
-    h->cond = P->cond;
+    h->cond = P->cond[dir];
     TMG_CUDA(cudaMemcpyAsync(P->st, h, offsetof(tmg::DevState, hist), cudaMemcpyHostToDevice, P->s));
     return TMG_OK;
 }
@@ -223,27 +242,29 @@ tmg_status check_ptr(const void* p) {
     return TMG_OK;
 }
 
-tmg_status run_solve(tmg_plan* P, const double* f, double u0, double* u) {
+tmg_status run_solve(tmg_plan* P, const double* f, double u0, double* u, int dir = 0, int initial_guess = -1) {
     if (check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    const tmg_ops* ops = dir == 0 ? P->ops : P->ops_adj;
+    if (initial_guess < 0) initial_guess = P->o.initial_guess;
     const int use_graph = P->o.use_graph != 0;
-    if (use_graph && P->gexec == nullptr) {
-        tmg_status s = build_graph(P);
+    if (use_graph && P->gexec[dir] == nullptr) {
+        tmg_status s = build_graph(P, dir);
         if (s != TMG_OK) return s;
     }
-    tmg_status s = stage_state(P, f, u0, u, P->o.tol, P->o.max_cycles, use_graph, P->o.initial_guess ? 0 : 1);
+    tmg_status s = stage_state(P, f, u0, u, P->o.tol, P->o.max_cycles, use_graph, initial_guess ? 0 : 1, dir);
     if (s != TMG_OK) return s;
-    if (P->o.initial_guess) {
-        TMG_CUDA(P->ops->enqueue_normF(P));
+    if (initial_guess) {
+        TMG_CUDA(ops->enqueue_normF(P));
     } else {
         TMG_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * P->N * P->d, P->s));
     }
     if (use_graph) {
-        TMG_CUDA(cudaGraphLaunch(P->gexec, P->s));
+        TMG_CUDA(cudaGraphLaunch(P->gexec[dir], P->s));
     } else {
         // eager loop: a few cycles per host check; kernels after convergence return at once
         for (int k = 0; k <= P->o.max_cycles;) {
             const int batch = 4;
-            for (int i = 0; i < batch && k <= P->o.max_cycles; ++i, ++k) TMG_CUDA(P->ops->enqueue_cycle(P));
+            for (int i = 0; i < batch && k <= P->o.max_cycles; ++i, ++k) TMG_CUDA(ops->enqueue_cycle(P));
             TMG_CUDA(cudaMemcpyAsync(&P->st_host->done, &P->st->done, sizeof(int), cudaMemcpyDeviceToHost, P->s));
             TMG_CUDA(cudaStreamSynchronize(P->s));
             if (P->st_host->done) break;
@@ -317,7 +338,8 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         }
         P->own_stream = true;
     }
-    P->ops = o.precision == TMG_MIXED ? tmg_ops_f32(P->d) : tmg_ops_f64(P->d);
+    P->ops = o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 0) : tmg_ops_f64(P->d, 0);
+    P->ops_adj = o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 1) : tmg_ops_f64(P->d, 1);
 
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -336,6 +358,8 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         level_setup(P->d, lambda * ldexp(tau, l), omega, &P->lev[l]);
     }
     transfer_setup(P->d, P->P1, P->P2);
+    P->lev_adj.resize(P->nlev);
+    for (int l = 0; l < P->nlev; ++l) level_setup_adjoint(P->d, P->lev[l], &P->lev_adj[l]);
 
     // first level handled on chip: the largest that fits
     P->lt = -1;
@@ -369,6 +393,8 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     off = align_up(off + el * N * P->d, A);
     const size_t off_lk = off;
     off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
+    const size_t off_lk_adj = off;
+    off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
     const size_t off_p = off;
     off = align_up(off + sizeof(double) * P->max_blocks, A);
     const size_t off_st = off;
@@ -388,6 +414,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     }
     P->rT = base + off_r;
     P->lk_dev = base + off_lk;
+    P->lk_dev_adj = base + off_lk_adj;
     P->partials = reinterpret_cast<double*>(base + off_p);
     P->st = reinterpret_cast<tmg::DevState*>(base + off_st);
     ce = cudaMallocHost(&P->st_host, sizeof(tmg::DevState));
@@ -401,7 +428,9 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     ce = cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->s);
     // the attribute is per kernel, shared by every plan: set the common ceiling
     if (ce == cudaSuccess) ce = P->ops->set_tail_attr(kTailSmemMax);
+    if (ce == cudaSuccess) ce = P->ops_adj->set_tail_attr(kTailSmemMax);
     if (ce == cudaSuccess) ce = P->ops->upload(P);
+    if (ce == cudaSuccess) ce = P->ops_adj->upload(P);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->s);
     if (ce != cudaSuccess) {
         tmg_destroy(P);
@@ -432,6 +461,34 @@ tmg_status tmg_solve_host(tmg_plan* P, const double* f_host, double u0, double* 
     tmg_status s = run_solve(P, P->F_dev, u0, P->u_dev);
     if (s != TMG_OK && s != TMG_ENOTCONV) return s;
     TMG_CUDA(cudaMemcpyAsync(u_host, P->u_dev, bytes, cudaMemcpyDeviceToHost, P->s));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return s;
+}
+
+tmg_status tmg_adjoint(tmg_plan* P, const double* g, const double* u, double* dJdf, double* dJdu0,
+                       double* dJdlambda) {
+    if (!P || check_ptr(g) != TMG_OK || check_ptr(u) != TMG_OK || check_ptr(dJdf) != TMG_OK || !dJdu0 ||
+        !dJdlambda || (reinterpret_cast<uintptr_t>(dJdu0) & 7u) || (reinterpret_cast<uintptr_t>(dJdlambda) & 7u))
+        return TMG_EINVAL;
+    const size_t nv = (size_t)P->N * P->d;
+    if (!P->adj_buf) {
+        cudaError_t e = cudaMalloc(&P->adj_buf, 2 * nv * sizeof(double));
+        if (e != cudaSuccess) {
+            P->adj_buf = nullptr;
+            g_last_cuda = (int)e;
+            return TMG_ENOMEM;
+        }
+    }
+    double* g_rev = P->adj_buf;
+    double* mu_rev = P->adj_buf + nv;
+    // L^T mu = g is, in reversed time, the forward structure with A^T and (a', b') = (b, a)
+    TMG_CUDA(tmg_launch_reverse(g, g_rev, P->N, P->d, P->s));
+    tmg_status s = run_solve(P, g_rev, 0.0, mu_rev, 1, 0);
+    if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+    TMG_CUDA(tmg_launch_reverse(mu_rev, dJdf, P->N, P->d, P->s));
+    TMG_CUDA(cudaMemsetAsync(&P->st->ticket, 0, sizeof(unsigned), P->s));
+    TMG_CUDA(tmg_launch_adjoint_grads(dJdf, u, P->N, P->d, P->tau, P->partials, P->max_blocks, &P->st->ticket,
+                                      dJdu0, dJdlambda, P->s));
     TMG_CUDA(cudaStreamSynchronize(P->s));
     return s;
 }
@@ -533,8 +590,11 @@ tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, 
 void tmg_destroy(tmg_plan* P) {
     if (!P) return;
     cudaStreamSynchronize(P->s);
-    if (P->gexec) cudaGraphExecDestroy(P->gexec);
-    if (P->graph) cudaGraphDestroy(P->graph);
+    for (int dir = 0; dir < 2; ++dir) {
+        if (P->gexec[dir]) cudaGraphExecDestroy(P->gexec[dir]);
+        if (P->graph[dir]) cudaGraphDestroy(P->graph[dir]);
+    }
+    if (P->adj_buf) cudaFree(P->adj_buf);
     if (P->ws) cudaFree(P->ws);
     if (P->st_host) cudaFreeHost(P->st_host);
     if (P->F_dev) cudaFree(P->F_dev);

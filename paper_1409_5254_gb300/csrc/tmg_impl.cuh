@@ -21,12 +21,14 @@ LevelK<T, D> level_consts(const tmg_level_host& L) {
     return K;
 }
 
+// Transfer matrices; in reversed time the first half of a coarse interval is
+// the second half of the original one, so P1 and P2 trade places.
 template <typename T, int D>
-Xfer<T, D> xfer_consts(const tmg_plan* P) {
+Xfer<T, D> xfer_consts(const tmg_plan* P, int dir) {
     Xfer<T, D> X;
     for (int i = 0; i < D * D; ++i) {
-        X.P1[i] = (T)P->P1[i];
-        X.P2[i] = (T)P->P2[i];
+        X.P1[i] = (T)(dir == 0 ? P->P1[i] : P->P2[i]);
+        X.P2[i] = (T)(dir == 0 ? P->P2[i] : P->P1[i]);
     }
     return X;
 }
@@ -62,19 +64,22 @@ inline int grid_flat(const tmg_plan* P, int64_t n) {
     return (int)blocks;
 }
 
-template <typename T, int D>
+template <typename T, int D, int DIR>
 struct Impl {
+    static const std::vector<tmg_level_host>& L(const tmg_plan* P) { return DIR == 0 ? P->lev : P->lev_adj; }
+
     static size_t tail_bytes(int64_t Nt, int nl) { return tail_smem_bytes<T, D>(Nt, nl); }
 
     static cudaError_t set_tail_attr(size_t bytes) {
-        return cudaFuncSetAttribute(k_tail<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        return cudaFuncSetAttribute(k_tail<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     }
 
     static cudaError_t upload(tmg_plan* P) {
         const int nl = P->nlev - P->lt;
         std::vector<LevelK<T, D>> lk(nl);
-        for (int j = 0; j < nl; ++j) lk[j] = level_consts<T, D>(P->lev[P->lt + j]);
-        return cudaMemcpyAsync(P->lk_dev, lk.data(), sizeof(LevelK<T, D>) * nl, cudaMemcpyHostToDevice, P->s);
+        for (int j = 0; j < nl; ++j) lk[j] = level_consts<T, D>(L(P)[P->lt + j]);
+        return cudaMemcpyAsync(DIR == 0 ? P->lk_dev : P->lk_dev_adj, lk.data(), sizeof(LevelK<T, D>) * nl,
+                               cudaMemcpyHostToDevice, P->s);
     }
 
     static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr); }
@@ -88,16 +93,16 @@ struct Impl {
             if (ev) cudaEventRecord(ev[iev++], P->s);
         };
         const int nu1 = P->o.nu1, nu2 = P->o.nu2;
-        const Xfer<T, D> X = xfer_consts<T, D>(P);
+        const Xfer<T, D> X = xfer_consts<T, D>(P, DIR);
         const Res0 R = res0_consts(P);
         const int nl = P->nlev - P->lt;
-        const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(P->lk_dev);
+        const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(DIR == 0 ? P->lk_dev : P->lk_dev_adj);
         T* rT = static_cast<T*>(P->rT);
         if (P->lt == 0) {
             mark();
-            k_res0<T, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(rT, P->N, R, P->partials, P->st);
+            k_res0<DIR, T, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(rT, P->N, R, P->partials, P->st);
             mark();
-            k_tail<T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N, nu1,
+            k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N, nu1,
                                                              nu2, P->o.gamma, P->st);
             mark();
             k_update0<T><<<grid_flat(P, P->N * D), kNT, 0, P->s>>>(static_cast<const T*>(P->ul[0]), P->N * D,
@@ -109,38 +114,38 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark();
-            k_down0<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
-                                                                  level_consts<T, D>(P->lev[0]), X, nu1, H,
+            k_down0<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
+                                                                  level_consts<T, D>(L(P)[0]), X, nu1, H,
                                                                   P->partials, P->st);
         }
         for (int l = 1; l < P->lt; ++l) {
             const int H = halo_lanes(sweeps_down(nu1));
             const int64_t nch = P->lev[l].N / 2;
             mark();
-            k_down<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
+            k_down<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
                                                                  static_cast<T*>(P->fl[l + 1]), nch,
-                                                                 level_consts<T, D>(P->lev[l]), X, nu1, H, P->st);
+                                                                 level_consts<T, D>(L(P)[l]), X, nu1, H, P->st);
         }
         mark();
-        k_tail<T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
+        k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
                                                          static_cast<T*>(P->ul[P->lt]), lk, X, nl,
                                                          P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
         for (int l = P->lt - 1; l >= 1; --l) {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->lev[l].N / 2;
             mark();
-            k_up<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
+            k_up<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
                                                                static_cast<const T*>(P->ul[l + 1]),
                                                                static_cast<T*>(P->ul[l]), nch,
-                                                               level_consts<T, D>(P->lev[l]), X, nu1, nu2, H,
+                                                               level_consts<T, D>(L(P)[l]), X, nu1, nu2, H,
                                                                P->st);
         }
         {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->N / 2;
             mark();
-            k_up0<T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<const T*>(P->ul[1]), nch,
-                                                                level_consts<T, D>(P->lev[0]), X, nu1, nu2, H,
+            k_up0<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<const T*>(P->ul[1]), nch,
+                                                                level_consts<T, D>(L(P)[0]), X, nu1, nu2, H,
                                                                 P->st);
         }
         mark();
@@ -148,12 +153,12 @@ struct Impl {
     }
 
     static cudaError_t enqueue_normF(tmg_plan* P) {
-        k_normF<D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(P->N, P->partials, P->st);
+        k_normF<DIR, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(P->N, P->partials, P->st);
         return cudaGetLastError();
     }
 
     static cudaError_t enqueue_residual(tmg_plan* P, const double* f, double u0, const double* u, double* r) {
-        k_residual_out<D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(f, u, u0, r, P->N, res0_consts(P));
+        k_residual_out<DIR, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(f, u, u0, r, P->N, res0_consts(P));
         return cudaGetLastError();
     }
 

@@ -1,12 +1,12 @@
 // Explicit instantiation of the solver for the mixed-precision form (FP32 cycles).
 #include "tmg_impl.cuh"
 
-const tmg_ops* tmg_ops_f32(int d) {
+const tmg_ops* tmg_ops_f32(int d, int dir) {
     switch (d) {
-        case 1: return tmg::Impl<float, 1>::ops();
-        case 2: return tmg::Impl<float, 2>::ops();
-        case 3: return tmg::Impl<float, 3>::ops();
-        case 4: return tmg::Impl<float, 4>::ops();
+        case 1: return dir == 0 ? tmg::Impl<float, 1, 0>::ops() : tmg::Impl<float, 1, 1>::ops();
+        case 2: return dir == 0 ? tmg::Impl<float, 2, 0>::ops() : tmg::Impl<float, 2, 1>::ops();
+        case 3: return dir == 0 ? tmg::Impl<float, 3, 0>::ops() : tmg::Impl<float, 3, 1>::ops();
+        case 4: return dir == 0 ? tmg::Impl<float, 4, 0>::ops() : tmg::Impl<float, 4, 1>::ops();
         default: return nullptr;
     }
 }

@@ -82,6 +82,13 @@ struct DevState {
 
 // ------------------------------------------------------------ helpers --
 
+// Coupling policy.  DIR = 0: the system of eq. chap4_generalLinearSystemODE,
+// N = a b^T with a_k = (-1)^k, b_l = 1.  DIR = 1: its transpose written in
+// reversed time, n -> N-1-n, which is again block lower-bidiagonal with
+// diagonal block A^T and N' = a' b'^T, a'_k = 1, b'_l = (-1)^l (the adjoint
+// solve runs the same cycle on reversed arrays).
+
+// Sum of the coefficients, e = 1^T u.
 template <typename T, int D>
 __device__ __forceinline__ T endval(const T (&u)[D]) {
     T e = u[0];
@@ -90,10 +97,19 @@ __device__ __forceinline__ T endval(const T (&u)[D]) {
     return e;
 }
 
-// a_k = (-1)^k
-template <typename T>
-__device__ __forceinline__ T asgn(int k, T x) {
-    return (k & 1) ? -x : x;
+// The halo functional b^T u.
+template <int DIR, typename T, int D>
+__device__ __forceinline__ T bval(const T (&u)[D]) {
+    T e = u[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) e += (DIR == 1 && (k & 1)) ? -u[k] : u[k];
+    return e;
+}
+
+// a_k x.
+template <int DIR, typename T>
+__device__ __forceinline__ T acoef(int k, T x) {
+    return (DIR == 0 && (k & 1)) ? -x : x;
 }
 
 template <typename T, int D>
@@ -191,7 +207,7 @@ __device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t q, 
 // Pre-smoothing from a zero guess for a coarse pair with right-hand side f:
 // sweep 1 gives u = omega A^{-1} f, w = A u = omega f; sweeps 2..nu1 use the
 // previous interval's endpoint value (warp shuffle).  h = A^{-1} f is kept.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&f)[2][D], T (&h)[2][D],
                                                T (&u)[2][D], T (&w)[2][D], int nu1) {
     const T om = K.omega, om1 = T(1) - K.omega;
@@ -206,28 +222,28 @@ __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&
         }
     }
     for (int s = 1; s < nu1; ++s) {
-        const T e0 = endval<T, D>(u[0]);
-        const T ep = shfl_prev(endval<T, D>(u[1]));
+        const T e0 = bval<DIR, T, D>(u[0]);
+        const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
-            w[0][k] = om1 * w[0][k] + om * (f[0][k] + asgn(k, ep));
+            w[0][k] = om1 * w[0][k] + om * (f[0][k] + acoef<DIR>(k, ep));
             u[1][k] = om1 * u[1][k] + om * fma(K.g[k], e0, h[1][k]);
-            w[1][k] = om1 * w[1][k] + om * (f[1][k] + asgn(k, e0));
+            w[1][k] = om1 * w[1][k] + om * (f[1][k] + acoef<DIR>(k, e0));
         }
     }
 }
 
 // Residual f + a e_{n-1} - A u of a pair, with A u = w carried along.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __device__ __forceinline__ void residual_tracked(const T (&f)[2][D], const T (&u)[2][D], const T (&w)[2][D],
                                                  T (&r)[2][D]) {
-    const T e0 = endval<T, D>(u[0]);
-    const T ep = shfl_prev(endval<T, D>(u[1]));
+    const T e0 = bval<DIR, T, D>(u[0]);
+    const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        r[0][k] = f[0][k] + asgn(k, ep) - w[0][k];
-        r[1][k] = f[1][k] + asgn(k, e0) - w[1][k];
+        r[0][k] = f[0][k] + acoef<DIR>(k, ep) - w[0][k];
+        r[1][k] = f[1][k] + acoef<DIR>(k, e0) - w[1][k];
     }
 }
 
@@ -260,12 +276,12 @@ __device__ __forceinline__ void prolong_add(const Xfer<T, D>& X, const T (&uc)[D
 }
 
 // nu post-smoothing sweeps: u <- (1-omega) u + omega (A^{-1} f + g e_{n-1}).
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2][D], T (&u)[2][D], int nu) {
     const T om = K.omega, om1 = T(1) - K.omega;
     for (int s = 0; s < nu; ++s) {
-        const T e0 = endval<T, D>(u[0]);
-        const T ep = shfl_prev(endval<T, D>(u[1]));
+        const T e0 = bval<DIR, T, D>(u[0]);
+        const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
@@ -274,20 +290,35 @@ __device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2
     }
 }
 
-// FP64 residual of the original system for one interval, using the Legendre
-// structure (K u)[k] = e - 2 S_k with S_k = sum of u[l], l < k, l of the other
-// parity than k:  r[k] = F[k] + a_k e_prev - e + 2 S_k - z/(2k+1) u[k].
+// FP64 residual of one interval, r = F + a (b^T u_{n-1}) - A u_n, using the
+// Legendre structure of the stiffness block.  ep = b^T u_{n-1}, E = 1^T u_n.
+// DIR = 0: (K u)[k] = E - 2 S_k, S_k = sum of u[l], l < k, l of the other
+//   parity than k, so r[k] = F[k] + a_k ep - E + 2 S_k - z/(2k+1) u[k].
+// DIR = 1: (K^T u)[k] = E - 2 T_k, T_k = sum of u[l], l > k, l of the other
+//   parity, and a'_k = 1: r[k] = F[k] + ep - E + 2 T_k - z/(2k+1) u[k].
 // The nearly-cancelling endpoint difference is formed first.
-template <int D>
-__device__ __forceinline__ void residual0(const double (&F)[D], const double (&u)[D], double ep, double e,
+template <int DIR, int D>
+__device__ __forceinline__ void residual0(const double (&F)[D], const double (&u)[D], double ep, double E,
                                           const Res0& R, double (&r)[D]) {
-    const double dp = ep - e;
-    r[0] = fma(-R.zm[0], u[0], F[0] + dp);
-    if constexpr (D > 1) {
-        const double sm = ep + e;
-        r[1] = fma(-R.zm[1], u[1], fma(2.0, u[0], F[1] - sm));
-        if constexpr (D > 2) r[2] = fma(-R.zm[2], u[2], fma(2.0, u[1], F[2] + dp));
-        if constexpr (D > 3) r[3] = fma(-R.zm[3], u[3], fma(2.0, u[0] + u[2], F[3] - sm));
+    const double dp = ep - E;
+    if constexpr (DIR == 0) {
+        r[0] = fma(-R.zm[0], u[0], F[0] + dp);
+        if constexpr (D > 1) {
+            const double sm = ep + E;
+            r[1] = fma(-R.zm[1], u[1], fma(2.0, u[0], F[1] - sm));
+            if constexpr (D > 2) r[2] = fma(-R.zm[2], u[2], fma(2.0, u[1], F[2] + dp));
+            if constexpr (D > 3) r[3] = fma(-R.zm[3], u[3], fma(2.0, u[0] + u[2], F[3] - sm));
+        }
+    } else {
+        double t[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            t[k] = 0.0;
+#pragma unroll
+            for (int l = k + 1; l < D; l += 2) t[k] += u[l];
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) r[k] = fma(-R.zm[k], u[k], fma(2.0, t[k], F[k] + dp));
     }
 }
 
@@ -346,6 +377,18 @@ __device__ __forceinline__ void acc_add(float& s, float& c, float th, float tl) 
     c += err + tl;
 }
 
+// float -> double by re-biasing the exponent with integer operations (exact;
+// the conversion instruction would occupy GB300's FP64 pipe).  Subnormal
+// floats (|c| < 2^-126) become 0.
+__device__ __forceinline__ double f2d_int(float c) {
+    const unsigned b = __float_as_uint(c);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned sign = b & 0x80000000u;
+    const unsigned hi = sign | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    const unsigned lo = (b & 0x7u) << 29;
+    return (e == 0u) ? 0.0 : (e == 0xFFu ? (double)c : __hiloint2double((int)hi, (int)lo));
+}
+
 // Product of two float pairs (lo*lo dropped), as an unnormalised pair.
 __device__ __forceinline__ ff mul_ff(float ah, float al, ff b) {
     ff p;
@@ -356,31 +399,48 @@ __device__ __forceinline__ ff mul_ff(float ah, float al, ff b) {
     return p;
 }
 
-// s_n = sum_{l>=1} u[l] as a float pair (0 for D = 1).
-template <int D>
-__device__ __forceinline__ ff small_sum(const double (&u)[D], ff (&us)[D]) {
-    ff s{0.f, 0.f};
+// Float-pair splits of one interval and the small parts of its two
+// functionals: sE = sum_{l>=1} u[l] (of 1^T u) and sB = sum_{l>=1} b_l u[l]
+// (of the halo functional b^T u; equal to sE for DIR = 0).
+template <int DIR, int D>
+__device__ __forceinline__ void small_sums(const double (&u)[D], ff (&us)[D], ff& sE, ff& sB) {
+    sE = ff{0.f, 0.f};
+    sB = ff{0.f, 0.f};
 #pragma unroll
     for (int l = 0; l < D; ++l) us[l] = split_d(u[l]);
 #pragma unroll
-    for (int l = 1; l < D; ++l) acc_add(s.hi, s.lo, us[l].hi, us[l].lo);
-    return s;
+    for (int l = 1; l < D; ++l) {
+        acc_add(sE.hi, sE.lo, us[l].hi, us[l].lo);
+        if constexpr (DIR == 1) {
+            const float sg = (l & 1) ? -1.f : 1.f;
+            acc_add(sB.hi, sB.lo, sg * us[l].hi, sg * us[l].lo);
+        }
+    }
+    if constexpr (DIR == 0) sB = sE;
 }
 
-// r[k] of one interval, rounded to float.  up0 = u_{n-1}[0], sp = s_{n-1}.
-template <int D>
+// r[k] of one interval, rounded to float.  up0 = u_{n-1}[0], spB = the small
+// part of b^T u_{n-1}, snE = the small part of 1^T u_n.  With d = up0 - u_n[0]:
+// DIR = 0: r[k] = F[k] + a_k (d + spB) - snE + 2 [k>=2] u[k-1] - z/(2k+1) u[k]
+// DIR = 1: r[k] = F[k] + (d + spB) - snE + 2 T_k - z/(2k+1) u[k]  (T_k as in residual0)
+template <int DIR, int D>
 __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double (&u)[D], const ff (&us)[D],
-                                             double up0, ff sp, ff sn, const Res0& R, float (&r)[D]) {
+                                             double up0, ff spB, ff snE, const Res0& R, float (&r)[D]) {
     const ff d = split_d(up0 - u[0]);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const ff Fk = split_d(F[k]);
         float s = Fk.hi, c = Fk.lo;
-        const float sg = (k & 1) ? -1.f : 1.f;
+        const float sg = (DIR == 0 && (k & 1)) ? -1.f : 1.f;
         acc_add(s, c, sg * d.hi, sg * d.lo);
-        acc_add(s, c, sg * sp.hi, sg * sp.lo);
-        acc_add(s, c, -sn.hi, -sn.lo);
-        if (k >= 2) acc_add(s, c, 2.f * us[k - 1].hi, 2.f * us[k - 1].lo);
+        acc_add(s, c, sg * spB.hi, sg * spB.lo);
+        acc_add(s, c, -snE.hi, -snE.lo);
+        if constexpr (DIR == 0) {
+            if (k >= 2) acc_add(s, c, 2.f * us[k - 1].hi, 2.f * us[k - 1].lo);
+        } else {
+#pragma unroll
+            for (int l = k + 1; l < D; l += 2) acc_add(s, c, 2.f * us[l].hi, 2.f * us[l].lo);
+        }
         const ff zu = mul_ff(R.zm_hi[k], R.zm_lo[k], us[k]);
         acc_add(s, c, -zu.hi, -zu.lo);
         r[k] = s + c;
@@ -461,7 +521,7 @@ constexpr int kNT = 256;   // threads per block of the streaming kernels
 
 // Level l >= 1, zero guess: pre-smooth, residual, restrict.  f: [2*nchunks][D],
 // fc: [nchunks][D].
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __restrict__ fc, int64_t nchunks,
                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
                                               const DevState* __restrict__ st) {
@@ -475,8 +535,8 @@ __global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __rest
         const bool inb = q >= 0 && q < nchunks;
         T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
         load_pair<T, D>(f, q, inb, fv);
-        presmooth_zero<T, D>(K, fv, h, u, w, nu1);
-        residual_tracked<T, D>(fv, u, w, r);
+        presmooth_zero<DIR, T, D>(K, fv, h, u, w, nu1);
+        residual_tracked<DIR, T, D>(fv, u, w, r);
         restrict_pair<T, D>(X, r, out);
         if (inb && lane >= H) VecIO<T, D>::store(fc + q * D, out);
     }
@@ -484,7 +544,7 @@ __global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __rest
 
 // Level l >= 1, zero guess: recompute the pre-smoothed iterate, add the
 // prolongated coarse correction uc: [nchunks][D], post-smooth, write u.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __restrict__ uc, T* __restrict__ u,
                                             int64_t nchunks, LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2,
                                             int H, const DevState* __restrict__ st) {
@@ -499,9 +559,9 @@ __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __
         T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
         load_pair<T, D>(f, q, inb, fv);
         load_one<T, D>(uc, q, inb, c);
-        presmooth_zero<T, D>(K, fv, h, v, w, nu1);
+        presmooth_zero<DIR, T, D>(K, fv, h, v, w, nu1);
         prolong_add<T, D>(X, c, v);
-        postsmooth<T, D>(K, h, v, nu2);
+        postsmooth<DIR, T, D>(K, h, v, nu2);
         if (inb && lane >= H) store_pair<T, D>(u, q, v);
     }
 }
@@ -510,7 +570,7 @@ __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __
 // ||r||^2 for the stopping test, r stored in the cycle precision T; then,
 // when fc != nullptr, the zero-guess pre-smoothing, residual and restriction
 // of the correction equation L c = r onto level 1.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, Res0 R,
                                                LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
                                                double* __restrict__ partials, DevState* st) {
@@ -538,19 +598,20 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
         load_pair<double, D>(F, q, inb, Fv);
         T rt[2][D];
         if constexpr (kMixed) {
-            ff us0[D], us1[D];
-            const ff s0 = small_sum<D>(uv[0], us0);
-            ff s1 = small_sum<D>(uv[1], us1);
+            ff us0[D], us1[D], sE0, sB0, sE1, sB1;
+            small_sums<DIR, D>(uv[0], us0, sE0, sB0);
+            small_sums<DIR, D>(uv[1], us1, sE1, sB1);
             double h0 = uv[1][0];
-            if (q < 0) {                        // the value before the first interval: e = u0
+            ff hB = sB1;
+            if (q < 0) {                        // the value before the first interval: b^T u = u0
                 h0 = u0;
-                s1 = ff{0.f, 0.f};
+                hB = ff{0.f, 0.f};
             }
             const double up0 = shfl_prev(h0);
-            const ff sp{shfl_prev(s1.hi), shfl_prev(s1.lo)};
+            const ff sp{shfl_prev(hB.hi), shfl_prev(hB.lo)};
             float r0[D], r1[D];
-            residual0_ff<D>(Fv[0], uv[0], us0, up0, sp, s0, R, r0);
-            residual0_ff<D>(Fv[1], uv[1], us1, uv[0][0], s0, s1, R, r1);
+            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0);
+            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 rt[0][k] = inb ? r0[k] : 0.f;
@@ -558,12 +619,14 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
             }
         } else {
             double r[2][D];
-            const double e0 = endval<double, D>(uv[0]);
-            double e1 = endval<double, D>(uv[1]);
-            if (q < 0) e1 = u0;                   // the value before the first interval
-            const double ep = shfl_prev(e1);
-            residual0<D>(Fv[0], uv[0], ep, e0, R, r[0]);
-            residual0<D>(Fv[1], uv[1], e0, e1, R, r[1]);
+            const double b0 = bval<DIR, double, D>(uv[0]);
+            double b1 = bval<DIR, double, D>(uv[1]);
+            if (q < 0) b1 = u0;                   // the value before the first interval
+            const double ep = shfl_prev(b1);
+            const double E0 = DIR == 0 ? b0 : endval<double, D>(uv[0]);
+            const double E1 = DIR == 0 ? b1 : endval<double, D>(uv[1]);
+            residual0<DIR, D>(Fv[0], uv[0], ep, E0, R, r[0]);
+            residual0<DIR, D>(Fv[1], uv[1], b0, E1, R, r[1]);
             // Lanes outside the array carry u0 only as the halo of the FP64
             // residual; for the correction equation L c = r their r is zero.
 #pragma unroll
@@ -587,8 +650,8 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
         }
         if (fc != nullptr) {
             T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
-            presmooth_zero<T, D>(K, rt, h, c, w, nu1);
-            residual_tracked<T, D>(rt, c, w, rc);
+            presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1);
+            residual_tracked<DIR, T, D>(rt, c, w, rc);
             restrict_pair<T, D>(X, rc, out);
             if (own) VecIO<T, D>::store(fc + q * D, out);
         }
@@ -599,7 +662,7 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
 
 // Level 0 on the way up: recompute the pre-smoothed correction from r, add
 // the prolongated level-1 correction, post-smooth, and update u += c in FP64.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
                                              LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2, int H,
                                              const DevState* __restrict__ st) {
@@ -615,16 +678,19 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
         T rt[2][D], h[2][D], c[2][D], w[2][D], cc[D];
         load_pair<T, D>(rT, q, inb, rt);
         load_one<T, D>(uc, q, inb, cc);
-        presmooth_zero<T, D>(K, rt, h, c, w, nu1);
+        presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1);
         prolong_add<T, D>(X, cc, c);
-        postsmooth<T, D>(K, h, c, nu2);
+        postsmooth<DIR, T, D>(K, h, c, nu2);
         if (inb && lane >= H) {
             double uv[2][D];
             load_pair<double, D>(uu, q, true, uv);
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int k = 0; k < D; ++k) uv[i][k] += (double)c[i][k];
+                for (int k = 0; k < D; ++k) {
+                    if constexpr (std::is_same<T, float>::value) uv[i][k] += f2d_int(c[i][k]);
+                    else uv[i][k] += (double)c[i][k];
+                }
             store_pair<double, D>(uu, q, uv);
         }
     }
@@ -632,7 +698,7 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
 
 // Level 0 residual only, one interval per thread (any N): used when the
 // on-chip solver handles the whole correction cycle.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_res0(T* __restrict__ rT, int64_t N, Res0 R, double* __restrict__ partials,
                                               DevState* st) {
     if (cycle_finished(st)) return;
@@ -648,9 +714,9 @@ __global__ void __launch_bounds__(kNT) k_res0(T* __restrict__ rT, int64_t N, Res
         double ep = u0;
         if (n > 0) {
             load_one<double, D>(uu, n - 1, true, up);
-            ep = endval<double, D>(up);
+            ep = bval<DIR, double, D>(up);
         }
-        residual0<D>(Fv, uv, ep, endval<double, D>(uv), R, r);
+        residual0<DIR, D>(Fv, uv, ep, endval<double, D>(uv), R, r);
         T rt[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -673,7 +739,7 @@ __global__ void __launch_bounds__(kNT) k_update0(const T* __restrict__ c, int64_
 }
 
 // r = F - L u into an FP64 array (public residual entry point).
-template <int D>
+template <int DIR, int D>
 __global__ void __launch_bounds__(kNT) k_residual_out(const double* __restrict__ F, const double* __restrict__ u,
                                                       double u0, double* __restrict__ r, int64_t N, Res0 R) {
     const int64_t stride = (int64_t)gridDim.x * kNT;
@@ -684,15 +750,15 @@ __global__ void __launch_bounds__(kNT) k_residual_out(const double* __restrict__
         double ep = u0;
         if (n > 0) {
             load_one<double, D>(u, n - 1, true, up);
-            ep = endval<double, D>(up);
+            ep = bval<DIR, double, D>(up);
         }
-        residual0<D>(Fv, uv, ep, endval<double, D>(uv), R, rr);
+        residual0<DIR, D>(Fv, uv, ep, endval<double, D>(uv), R, rr);
         VecIO<double, D>::store(r + n * D, rr);
     }
 }
 
 // ||F||_2 with a*u0 folded into the first interval (for a caller-given start).
-template <int D>
+template <int DIR, int D>
 __global__ void __launch_bounds__(kNT) k_normF(int64_t N, double* __restrict__ partials, DevState* st) {
     const double* __restrict__ F = st->F;
     const double u0 = st->u0;
@@ -703,7 +769,7 @@ __global__ void __launch_bounds__(kNT) k_normF(int64_t N, double* __restrict__ p
         load_one<double, D>(F, n, true, Fv);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            const double v = (n == 0) ? Fv[k] + asgn(k, u0) : Fv[k];
+            const double v = (n == 0) ? Fv[k] + acoef<DIR>(k, u0) : Fv[k];
             ss = fma(v, v, ss);
         }
     }
@@ -761,20 +827,20 @@ __device__ __forceinline__ void sm_store(T* p, const T (&x)[D]) {
 }
 
 // Endpoint values e[n] = b^T u_n of a whole level.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __device__ __forceinline__ void tail_endvals(const T* u, T* e, int64_t N) {
     for (int64_t n = threadIdx.x; n < N; n += kTailNT) {
         T x[D];
         sm_load<T, D>(u + n * D, x);
-        e[n] = endval<T, D>(x);
+        e[n] = bval<DIR, T, D>(x);
     }
 }
 
 // One damped block-Jacobi sweep of a level held in shared memory; w = A u is
 // updated alongside when track_w.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __device__ void tail_sweep(const LevelK<T, D>& K, const T* f, T* u, T* w, T* e, int64_t N, bool track_w) {
-    tail_endvals<T, D>(u, e, N);
+    tail_endvals<DIR, T, D>(u, e, N);
     __syncthreads();
     const T om = K.omega, om1 = T(1) - K.omega;
     for (int64_t n = threadIdx.x; n < N; n += kTailNT) {
@@ -790,7 +856,7 @@ __device__ void tail_sweep(const LevelK<T, D>& K, const T* f, T* u, T* w, T* e, 
             T y[D];
             sm_load<T, D>(w + n * D, y);
 #pragma unroll
-            for (int k = 0; k < D; ++k) y[k] = om1 * y[k] + om * (fv[k] + asgn(k, ep));
+            for (int k = 0; k < D; ++k) y[k] = om1 * y[k] + om * (fv[k] + acoef<DIR>(k, ep));
             sm_store<T, D>(w + n * D, y);
         }
     }
@@ -866,7 +932,7 @@ __device__ void tail_exact(const LevelK<T, D>& K, const T* f, T* u, T* scanA, T*
 // entirely in shared memory: V (gamma = 1) or W (gamma = 2) recursion written
 // as a loop; coarsest tail level solved exactly.  f_in is the right-hand side
 // of level lt, u_out receives its correction.
-template <typename T, int D>
+template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T* __restrict__ u_out,
                                                   const LevelK<T, D>* __restrict__ lk, Xfer<T, D> X, int nl,
                                                   int64_t Nt, int nu1, int nu2, int gamma,
@@ -941,9 +1007,9 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
                 }
                 __syncthreads();
             }
-            for (int s = 0; s < sweeps; ++s) tail_sweep<T, D>(K, V.f[j], V.u[j], V.w, V.e, N, true);
+            for (int s = 0; s < sweeps; ++s) tail_sweep<DIR, T, D>(K, V.f[j], V.u[j], V.w, V.e, N, true);
             // residual f + a e_{n-1} - A u, restricted onto level j+1
-            tail_endvals<T, D>(V.u[j], V.e, N);
+            tail_endvals<DIR, T, D>(V.u[j], V.e, N);
             __syncthreads();
             for (int64_t m = threadIdx.x; m < N / 2; m += kTailNT) {
                 T r[2][D], out[D];
@@ -952,7 +1018,7 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
                     const int64_t n = 2 * m + i;
                     const T ep = n > 0 ? V.e[n - 1] : T(0);
 #pragma unroll
-                    for (int k = 0; k < D; ++k) r[i][k] = V.f[j][n * D + k] + asgn(k, ep) - V.w[n * D + k];
+                    for (int k = 0; k < D; ++k) r[i][k] = V.f[j][n * D + k] + acoef<DIR>(k, ep) - V.w[n * D + k];
                 }
                 restrict_pair<T, D>(X, r, out);
                 sm_store<T, D>(V.f[j + 1] + m * D, out);
@@ -980,7 +1046,7 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
             sm_store<T, D>(V.u[j] + (2 * m + 1) * D, x[1]);
         }
         __syncthreads();
-        for (int s = 0; s < nu2; ++s) tail_sweep<T, D>(K, V.f[j], V.u[j], V.w, V.e, N, false);
+        for (int s = 0; s < nu2; ++s) tail_sweep<DIR, T, D>(K, V.f[j], V.u[j], V.w, V.e, N, false);
         if (j == 0) break;
         --j;
     }

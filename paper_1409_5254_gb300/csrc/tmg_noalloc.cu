@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(tmg::kNT) k_residual_norm_static(const double*
             load_one<double, D>(u, n - 1, true, up);
             ep = endval<double, D>(up);
         }
-        residual0<D>(Fv, uv, ep, endval<double, D>(uv), R, rr);
+        residual0<0, D>(Fv, uv, ep, endval<double, D>(uv), R, rr);
         VecIO<double, D>::store(r + n * D, rr);
 #pragma unroll
         for (int k = 0; k < D; ++k) ss = fma(rr[k], rr[k], ss);

@@ -36,7 +36,8 @@ struct tmg_plan {
     int nlev;            // levels 0..nlev-1
     int lt;              // first level solved on chip (tail)
     size_t tail_smem;
-    std::vector<tmg_level_host> lev;
+    std::vector<tmg_level_host> lev;       // constants of L
+    std::vector<tmg_level_host> lev_adj;   // constants of L^T in reversed time
     double P1[16], P2[16];   // prolongation (coarse -> fine halves)
 
     // device workspace (one allocation)
@@ -49,18 +50,21 @@ struct tmg_plan {
     void* fl[tmg::kMaxLevels];   // level right-hand sides (cycle precision)
     void* ul[tmg::kMaxLevels];   // level corrections
     void* rT;                    // level-0 residual (cycle precision)
-    void* lk_dev;                // tail level constants
+    void* lk_dev;                // tail level constants of L
+    void* lk_dev_adj;            // ... and of L^T in reversed time
+    double* adj_buf;             // reversed g and reversed mu (adjoint solves, allocated on first use)
 
     // optional buffers for the host-array entry point
     double* F_dev;
     double* u_dev;
 
-    // CUDA graph of the whole solve (while-loop over cycles)
-    cudaGraph_t graph;
-    cudaGraphExec_t gexec;
-    unsigned long long cond;
+    // CUDA graphs of the whole solve (while-loop over cycles), [0] = L, [1] = L^T
+    cudaGraph_t graph[2];
+    cudaGraphExec_t gexec[2];
+    unsigned long long cond[2];
 
-    const tmg_ops* ops;
+    const tmg_ops* ops;        // kernels for L
+    const tmg_ops* ops_adj;    // kernels for L^T in reversed time
 
     // statistics of the last solve
     int last_cycles;
@@ -80,5 +84,13 @@ struct tmg_ops {
     cudaError_t (*set_tail_attr)(size_t bytes);
 };
 
-const tmg_ops* tmg_ops_f32(int d);
-const tmg_ops* tmg_ops_f64(int d);
+const tmg_ops* tmg_ops_f32(int d, int dir);
+const tmg_ops* tmg_ops_f64(int d, int dir);
+
+// Adjoint helpers (tmg_adjoint.cu): reverse the interval order of an [N][d]
+// array, and the gradient reductions dJ/du0 = a^T mu_0,
+// dJ/dlambda = -tau sum_n mu_n^T Mhat u_n.
+cudaError_t tmg_launch_reverse(const double* src, double* dst, int64_t N, int d, cudaStream_t s);
+cudaError_t tmg_launch_adjoint_grads(const double* mu, const double* u, int64_t N, int d, double tau,
+                                     double* partials, int max_blocks, unsigned* ticket, double* dJdu0,
+                                     double* dJdlambda, cudaStream_t s);

@@ -39,7 +39,7 @@ _LIB = None
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
-EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual",
+EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_adjoint", "tmg_cycle", "tmg_residual",
            "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error"]
 
@@ -63,6 +63,7 @@ def _lib():
         L.tmg_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_solve_host.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp]
+        L.tmg_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.tmg_residual.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
         L.tmg_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, ctypes.c_int]
         L.tmg_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -77,7 +78,7 @@ def _lib():
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
-        for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_cycle", "tmg_residual", "tmg_stats",
+        for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_adjoint", "tmg_cycle", "tmg_residual", "tmg_stats",
                      "tmg_plan_info", "tmg_inspect", "tmg_profile_cycle"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
@@ -161,6 +162,17 @@ class Plan:
         fp = ctypes.c_void_p(_host_ptr(f_host, self.d, self.N))
         up = ctypes.c_void_p(_host_ptr(u_host, self.d, self.N))
         return _check(_lib().tmg_solve_host(self._h, fp, float(u0), up), "tmg_solve_host")
+
+    def adjoint(self, g, u, *, allow_notconv: bool = False):
+        """(dJ/df, dJ/du0, dJ/dlambda) for dJ/du = g at the forward solution u (tmg_adjoint)."""
+        import torch
+        dJdf = torch.empty_like(g)
+        scal = torch.zeros(2, dtype=torch.float64, device=g.device)
+        st = _lib().tmg_adjoint(self._h, _dev_ptr(g, self.d, self.N, "g"), _dev_ptr(u, self.d, self.N, "u"),
+                                _dev_ptr(dJdf, self.d, self.N, "dJdf"), ctypes.c_void_p(scal.data_ptr()),
+                                ctypes.c_void_p(scal.data_ptr() + 8))
+        _check(st, "tmg_adjoint", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
+        return dJdf, scal[0], scal[1]
 
     def cycle(self, f, u0: float, u):
         _check(_lib().tmg_cycle(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
