@@ -189,6 +189,52 @@ tmg_status tmg_inspect(const tmg_plan *plan, int which, int level, void *host_ds
 tmg_status tmg_residual_norm_noalloc(int p_t, double tau, double lambda, int64_t N, const double *f, double u0,
                                      const double *u, double *r, double *norm, void *stream);
 
+/* ------------------------------------------------------------ batches -- */
+
+typedef struct tmg_batch tmg_batch;
+
+/*
+ * Plan for n_inst independent problems u' + lambda_i u = f_i, u(0) = u0_i,
+ * instance i with degree p_t[i] in {0..3}, step tau[i] > 0, lambda[i] >= 0
+ * and N[i] >= 1 intervals (host arrays of length n_inst).  Packed layout of
+ * every [instance][interval][coefficient] array: instance i starts at value
+ * offset off_i = sum_{j<i} N[j] (p_t[j] + 1).  omega and opts as for
+ * tmg_setup (V-cycles only: opts->gamma must be 1; levels coarsen down to at
+ * most 64 intervals, solved exactly).  Internally the instances are grouped
+ * by p_t and padded at their end to a power-of-two length (the system is
+ * causal, so this leaves each instance's solution unchanged); every level
+ * kernel then covers all instances of a group at once.  Per-instance FP64
+ * constants are computed on the host.  Returns as tmg_setup.
+ */
+tmg_status tmg_setup_batched(tmg_batch **batch, int64_t n_inst, const int *p_t, const double *tau,
+                             const double *lambda, const int64_t *N, double omega, const tmg_opts *opts,
+                             void *stream);
+
+/*
+ * Solve every instance: f, u device packed arrays (16-byte aligned), u0
+ * device [n_inst].  Each instance stops on its own test ||F_i - L_i u_i|| <=
+ * tol ||F_i|| (its lanes are frozen afterwards); TMG_ENOTCONV if any instance
+ * reached max_cycles.  Synchronises the stream.
+ */
+tmg_status tmg_solve_batched(tmg_batch *batch, const double *f, const double *u0, double *u);
+
+/*
+ * Gradients of a loss through every instance's adjoint (see tmg_adjoint):
+ * g = dJ/du and u (the forward solutions) packed device arrays; outputs
+ * dJdf (packed), dJdu0[n_inst] and dJdlambda[n_inst] on the device.
+ */
+tmg_status tmg_adjoint_batched(tmg_batch *batch, const double *g, const double *u, double *dJdf, double *dJdu0,
+                               double *dJdlambda);
+
+/* Per-instance cycles and final relative residuals of the last batched solve
+ * (host arrays of length n_inst, may be NULL); *max_cycles_used = the most. */
+tmg_status tmg_stats_batched(const tmg_batch *batch, int *cycles, double *rel_res, int *max_cycles_used);
+
+/* Number of (p_t, padded length) groups and the padded number of values. */
+tmg_status tmg_batch_info(const tmg_batch *batch, int *n_groups, int64_t *padded_values);
+
+void tmg_destroy_batched(tmg_batch *batch);
+
 /* Release the plan and every resource it owns.  NULL is ignored. */
 void tmg_destroy(tmg_plan *plan);
 

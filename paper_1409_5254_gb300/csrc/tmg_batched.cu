@@ -1,0 +1,723 @@
+// Batched C ABI: many independent DG-in-time problems in one solve.
+//
+// Instances are grouped by degree p_t; within a group every instance is
+// padded at its end to the same power-of-two length Ng (zero right-hand side
+// on the padded intervals).  The system is causal -- u_n depends on f_1..f_n
+// only -- so padding after the last interval leaves the first N_i intervals'
+// solution unchanged, and the padded residual bounds the unpadded one.  The
+// adjoint is anti-causal; it is solved in reversed time, where padding at the
+// end is again exact.  When all instances share p_t and N = Ng the caller's
+// arrays are used in place.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "tmg_batched.cuh"
+#include "tmg_setup_math.h"
+
+using namespace tmg;
+
+struct tmg_batch_group {
+    int p, d;
+    int64_t n;           // instances in the group
+    int64_t Ng;          // padded length (power of two, >= 2)
+    int log2Ng;
+    int nlev;
+    bool direct;         // group arrays are the caller's arrays
+    std::vector<int64_t> ids;
+
+    void* ws;            // one allocation for everything below
+    size_t ws_bytes;
+    BatchState* st;
+    BatchState* st_host;
+    BatchInst bi;
+    Res0* res;
+    void* lk[2];         // LevelK table [n][nlev], per direction
+    void* rT;
+    void* fl[kMaxLevels];
+    void* ul[kMaxLevels];
+    void* c0;
+    int64_t* d_ids;
+    int64_t* d_Ni;
+    int64_t* d_off;
+    double* Fg;          // gathered right-hand side [n][Ng][d] (allocated on first use)
+    double* ug;
+    double* u0g;
+    cudaGraph_t graph[2];
+    cudaGraphExec_t gexec[2];
+    unsigned long long cond[2];
+    int last_status;
+};
+
+struct tmg_batch {
+    int64_t n_inst;
+    std::vector<int> p;
+    std::vector<int64_t> N, off;
+    std::vector<double> tau, lambda;
+    int64_t total_values;
+    tmg_opts o;
+    double omega;
+    cudaStream_t s;
+    bool own_stream;
+    int max_blocks;
+    std::vector<tmg_batch_group*> groups;
+    void* table;          // device copies of off, N (int64), tau (double), p (int) for the gradient kernel
+    std::vector<int> cycles;
+    std::vector<double> rel;
+};
+
+namespace {
+
+thread_local int g_last_cuda_b = 0;
+
+tmg_status fail(cudaError_t e) {
+    g_last_cuda_b = (int)e;
+    return TMG_ECUDA;
+}
+
+#define TB_CUDA(call)                               \
+    do {                                            \
+        cudaError_t _e = (call);                    \
+        if (_e != cudaSuccess) return fail(_e);     \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int ilog2(int64_t x) {
+    int k = 0;
+    while ((int64_t(1) << k) < x) ++k;
+    return k;
+}
+
+int halo(int S) { return (S + 1) / 2; }
+int sw_down(int nu1) { return (nu1 > 0 ? nu1 - 1 : 0) + 1; }
+int sw_up(int nu1, int nu2) { return (nu1 > 0 ? nu1 - 1 : 0) + nu2; }
+
+int grid_tiles(const tmg_batch* B, int64_t nchunks, int H) {
+    const int64_t per = 32 - H;
+    int64_t blocks = ((nchunks + per - 1) / per + (kBNT / 32) - 1) / (kBNT / 32);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, B->max_blocks));
+}
+
+int grid_flat(const tmg_batch* B, int64_t n) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kBNT - 1) / kBNT, B->max_blocks));
+}
+
+__global__ void kb_init(BatchInst bi, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        bi.active[i] = 1;
+        bi.norm2[i] = 0.0;
+        bi.cycles[i] = 0;
+        bi.rel[i] = NAN;
+    }
+}
+
+// dst[j][n][k] = src[off_j + m(n) d + k] for n < N_j (m = n, or N_j-1-n when
+// reversed), 0 on the padded intervals; also u0 of the group's instances.
+__global__ void kb_gather(const double* __restrict__ src, double* __restrict__ dst, const int64_t* __restrict__ ids,
+                          const int64_t* __restrict__ Ni, const int64_t* __restrict__ off, int64_t n, int64_t Ng,
+                          int d, int reverse, const double* __restrict__ u0src, double* __restrict__ u0dst) {
+    const int64_t total = n * Ng * d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / (Ng * d), rem = i - j * Ng * d;
+        const int64_t m = rem / d, k = rem - m * d;
+        const int64_t nj = Ni[j];
+        double v = 0.0;
+        if (m < nj) v = src[off[j] + (reverse ? nj - 1 - m : m) * d + k];
+        dst[i] = v;
+        if (u0dst && rem == 0) u0dst[j] = u0src ? u0src[ids[j]] : 0.0;
+    }
+}
+
+__global__ void kb_scatter(const double* __restrict__ src, double* __restrict__ dst, const int64_t* __restrict__ Ni,
+                           const int64_t* __restrict__ off, int64_t n, int64_t Ng, int d, int reverse) {
+    const int64_t total = n * Ng * d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / (Ng * d), rem = i - j * Ng * d;
+        const int64_t m = rem / d, k = rem - m * d;
+        const int64_t nj = Ni[j];
+        if (m < nj) dst[off[j] + (reverse ? nj - 1 - m : m) * d + k] = src[i];
+    }
+}
+
+// Per-instance gradients (one block per instance, fixed summation order):
+// dJ/du0 = a^T mu_0, dJ/dlambda = -tau sum_n mu_n^T Mhat u_n.
+__global__ void kb_grads(const double* __restrict__ mu, const double* __restrict__ u, const int64_t* __restrict__ off,
+                         const int64_t* __restrict__ Nv, const int* __restrict__ pv, const double* __restrict__ tau,
+                         int64_t n_inst, double* __restrict__ dJdu0, double* __restrict__ dJdlambda) {
+    __shared__ double red[kBNT / 32];
+    for (int64_t i = blockIdx.x; i < n_inst; i += gridDim.x) {
+        const int d = pv[i] + 1;
+        const int64_t base = off[i], len = Nv[i] * d;
+        double s = 0.0;
+        for (int64_t t = threadIdx.x; t < len; t += kBNT) {
+            const int k = (int)(t % d);
+            s = fma(mu[base + t], u[base + t] / (2.0 * k + 1.0), s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kBNT / 32; ++w) t += red[w];
+            dJdlambda[i] = -tau[i] * t;
+            double g0 = 0.0;
+            for (int k = 0; k < d; ++k) g0 += (k & 1) ? -mu[base + k] : mu[base + k];
+            dJdu0[i] = g0;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int D, int DIR>
+cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
+    const int nu1 = B->o.nu1, nu2 = B->o.nu2;
+    Xfer<T, D> X;
+    for (int i = 0; i < D * D; ++i) {   // reversed time swaps the halves
+        X.P1[i] = (T)0;
+        X.P2[i] = (T)0;
+    }
+    {
+        double P1[16], P2[16];
+        tmg_host::transfer_setup(D, P1, P2);
+        for (int i = 0; i < D * D; ++i) {
+            X.P1[i] = (T)(DIR == 0 ? P1[i] : P2[i]);
+            X.P2[i] = (T)(DIR == 0 ? P2[i] : P1[i]);
+        }
+    }
+    const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(G->lk[DIR]);
+    T* rT = static_cast<T*>(G->rT);
+    const int64_t n = G->n;
+    const int L = G->nlev;
+    {
+        const int H = halo(1 + sw_down(nu1));
+        const int64_t nch = n * G->Ng / 2;
+        kb_down0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(
+            rT, L > 1 ? static_cast<T*>(G->fl[1]) : nullptr, nch, G->log2Ng, lk, G->res, L, X, nu1, H, G->st, G->bi);
+    }
+    kb_finalize<<<grid_flat(B, n), kBNT, 0, B->s>>>(G->st, G->bi, n);
+    if (L == 1) {
+        kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, B->s>>>(rT, static_cast<T*>(G->c0), n, (int)G->Ng, lk,
+                                                                       L, 0, G->st, G->bi);
+        // u += c; the instance of value i is i / (Ng D)
+        const int64_t nv = n * G->Ng * D;
+        kb_update0<T, D><<<grid_flat(B, nv), kBNT, 0, B->s>>>(static_cast<const T*>(G->c0), nv,
+                                                               (int)(G->Ng * D), G->st, G->bi);
+        return cudaGetLastError();
+    }
+    for (int l = 1; l < L - 1; ++l) {
+        const int H = halo(sw_down(nu1));
+        const int64_t nch = n * (G->Ng >> l) / 2;
+        kb_down<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(
+            static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 1]), nch, G->log2Ng - l, lk, L, l, X, nu1, H,
+            G->st, G->bi);
+    }
+    kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, B->s>>>(static_cast<const T*>(G->fl[L - 1]),
+                                                                   static_cast<T*>(G->ul[L - 1]), n,
+                                                                   (int)(G->Ng >> (L - 1)), lk, L, L - 1, G->st,
+                                                                   G->bi);
+    for (int l = L - 2; l >= 1; --l) {
+        const int H = halo(sw_up(nu1, nu2));
+        const int64_t nch = n * (G->Ng >> l) / 2;
+        kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(
+            static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 1]), static_cast<T*>(G->ul[l]), nch,
+            G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+    }
+    {
+        const int H = halo(sw_up(nu1, nu2));
+        const int64_t nch = n * G->Ng / 2;
+        kb_up0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(rT, static_cast<const T*>(G->ul[1]), nch,
+                                                                     G->log2Ng, lk, L, X, nu1, nu2, H, G->st, G->bi);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int DIR>
+cudaError_t enqueue_cycle_d(tmg_batch* B, tmg_batch_group* G) {
+    switch (G->d) {
+        case 1: return enqueue_cycle<T, 1, DIR>(B, G);
+        case 2: return enqueue_cycle<T, 2, DIR>(B, G);
+        case 3: return enqueue_cycle<T, 3, DIR>(B, G);
+        default: return enqueue_cycle<T, 4, DIR>(B, G);
+    }
+}
+
+cudaError_t enqueue(tmg_batch* B, tmg_batch_group* G, int dir) {
+    if (B->o.precision == TMG_MIXED)
+        return dir == 0 ? enqueue_cycle_d<float, 0>(B, G) : enqueue_cycle_d<float, 1>(B, G);
+    return dir == 0 ? enqueue_cycle_d<double, 0>(B, G) : enqueue_cycle_d<double, 1>(B, G);
+}
+
+template <typename T, int D>
+void fill_tables(const tmg_batch* B, const tmg_batch_group* G, std::vector<char>& fwd, std::vector<char>& adj,
+                 std::vector<Res0>& res) {
+    fwd.resize(sizeof(LevelK<T, D>) * G->n * G->nlev);
+    adj.resize(sizeof(LevelK<T, D>) * G->n * G->nlev);
+    res.resize(G->n);
+    LevelK<T, D>* F = reinterpret_cast<LevelK<T, D>*>(fwd.data());
+    LevelK<T, D>* A = reinterpret_cast<LevelK<T, D>*>(adj.data());
+    for (int64_t j = 0; j < G->n; ++j) {
+        const int64_t i = G->ids[j];
+        const double z = B->lambda[i] * B->tau[i];
+        for (int l = 0; l < G->nlev; ++l) {
+            tmg_level_host Lf, La;
+            Lf.N = G->Ng >> l;
+            tmg_host::level_setup(D, ldexp(z, l), B->omega, &Lf);
+            tmg_host::level_setup_adjoint(D, Lf, &La);
+            for (int dir = 0; dir < 2; ++dir) {
+                const tmg_level_host& H = dir == 0 ? Lf : La;
+                LevelK<T, D>& K = (dir == 0 ? F : A)[j * G->nlev + l];
+                for (int q = 0; q < D * D; ++q) {
+                    K.A[q] = (T)H.A[q];
+                    K.Ainv[q] = (T)H.Ainv[q];
+                }
+                for (int q = 0; q < D; ++q) {
+                    K.g[q] = (T)H.g[q];
+                    K.c[q] = (T)H.c[q];
+                }
+                K.omega = (T)H.omega;
+                K.alpha = (T)H.alpha;
+            }
+        }
+        Res0& R = res[j];
+        for (int k = 0; k < kMaxD; ++k) {
+            R.zm[k] = z / (2.0 * k + 1.0);
+            R.zm_hi[k] = (float)R.zm[k];
+            R.zm_lo[k] = (float)(R.zm[k] - (double)R.zm_hi[k]);
+        }
+    }
+}
+
+tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
+    const size_t el = B->o.precision == TMG_MIXED ? sizeof(float) : sizeof(double);
+    const int64_t nmin = std::min<int64_t>(B->o.n_min, 64);
+    G->nlev = 1;
+    for (int64_t m = G->Ng; m > nmin && m % 2 == 0 && G->nlev < kMaxLevels; m /= 2) ++G->nlev;
+    if ((G->Ng >> (G->nlev - 1)) > 64) return TMG_EUNSUPPORTED;
+    // layout
+    const size_t A = 256;
+    const int64_t n = G->n, nvals = n * G->Ng * G->d;
+    size_t off = 0;
+    const size_t o_st = off;
+    off = align_up(off + sizeof(BatchState), A);
+    const size_t o_nF = off;
+    off = align_up(off + 8 * n, A);
+    const size_t o_n2 = off;
+    off = align_up(off + 8 * n, A);
+    const size_t o_act = off;
+    off = align_up(off + 4 * n, A);
+    const size_t o_cyc = off;
+    off = align_up(off + 4 * n, A);
+    const size_t o_rel = off;
+    off = align_up(off + 8 * n, A);
+    const size_t o_res = off;
+    off = align_up(off + sizeof(Res0) * n, A);
+    const size_t lk_bytes = (B->o.precision == TMG_MIXED ? sizeof(LevelK<float, 4>) : sizeof(LevelK<double, 4>)) *
+                            (size_t)n * G->nlev;
+    const size_t o_lk0 = off;
+    off = align_up(off + lk_bytes, A);
+    const size_t o_lk1 = off;
+    off = align_up(off + lk_bytes, A);
+    const size_t o_rT = off;
+    off = align_up(off + el * nvals, A);
+    size_t o_f[kMaxLevels], o_u[kMaxLevels];
+    for (int l = 1; l < G->nlev; ++l) {
+        o_f[l] = off;
+        off = align_up(off + el * (nvals >> l), A);
+        o_u[l] = off;
+        off = align_up(off + el * (nvals >> l), A);
+    }
+    const size_t o_c0 = off;
+    off = align_up(off + (G->nlev == 1 ? el * nvals : 0), A);
+    const size_t o_ids = off;
+    off = align_up(off + 8 * n, A);
+    const size_t o_Ni = off;
+    off = align_up(off + 8 * n, A);
+    const size_t o_off = off;
+    off = align_up(off + 8 * n, A);
+    G->ws_bytes = off;
+    cudaError_t e = cudaMalloc(&G->ws, G->ws_bytes);
+    if (e != cudaSuccess) {
+        G->ws = nullptr;
+        g_last_cuda_b = (int)e;
+        return TMG_ENOMEM;
+    }
+    char* b = static_cast<char*>(G->ws);
+    G->st = reinterpret_cast<BatchState*>(b + o_st);
+    G->bi.nF = reinterpret_cast<double*>(b + o_nF);
+    G->bi.norm2 = reinterpret_cast<double*>(b + o_n2);
+    G->bi.active = reinterpret_cast<int*>(b + o_act);
+    G->bi.cycles = reinterpret_cast<int*>(b + o_cyc);
+    G->bi.rel = reinterpret_cast<double*>(b + o_rel);
+    G->res = reinterpret_cast<Res0*>(b + o_res);
+    G->lk[0] = b + o_lk0;
+    G->lk[1] = b + o_lk1;
+    G->rT = b + o_rT;
+    for (int l = 1; l < G->nlev; ++l) {
+        G->fl[l] = b + o_f[l];
+        G->ul[l] = b + o_u[l];
+    }
+    G->c0 = b + o_c0;
+    G->d_ids = reinterpret_cast<int64_t*>(b + o_ids);
+    G->d_Ni = reinterpret_cast<int64_t*>(b + o_Ni);
+    G->d_off = reinterpret_cast<int64_t*>(b + o_off);
+    e = cudaMallocHost(&G->st_host, sizeof(BatchState));
+    if (e != cudaSuccess) {
+        G->st_host = nullptr;
+        g_last_cuda_b = (int)e;
+        return TMG_ENOMEM;
+    }
+    // constants (FP64 on the host, stored in the cycle precision)
+    std::vector<char> tf, ta;
+    std::vector<Res0> res;
+    const bool mixed = B->o.precision == TMG_MIXED;
+    switch (G->d) {
+        case 1: mixed ? fill_tables<float, 1>(B, G, tf, ta, res) : fill_tables<double, 1>(B, G, tf, ta, res); break;
+        case 2: mixed ? fill_tables<float, 2>(B, G, tf, ta, res) : fill_tables<double, 2>(B, G, tf, ta, res); break;
+        case 3: mixed ? fill_tables<float, 3>(B, G, tf, ta, res) : fill_tables<double, 3>(B, G, tf, ta, res); break;
+        default: mixed ? fill_tables<float, 4>(B, G, tf, ta, res) : fill_tables<double, 4>(B, G, tf, ta, res); break;
+    }
+    std::vector<int64_t> Ni(n), offs(n);
+    for (int64_t j = 0; j < n; ++j) {
+        Ni[j] = B->N[G->ids[j]];
+        offs[j] = B->off[G->ids[j]];
+    }
+    TB_CUDA(cudaMemcpyAsync(G->lk[0], tf.data(), tf.size(), cudaMemcpyHostToDevice, B->s));
+    TB_CUDA(cudaMemcpyAsync(G->lk[1], ta.data(), ta.size(), cudaMemcpyHostToDevice, B->s));
+    TB_CUDA(cudaMemcpyAsync(G->res, res.data(), sizeof(Res0) * n, cudaMemcpyHostToDevice, B->s));
+    TB_CUDA(cudaMemcpyAsync(G->d_ids, G->ids.data(), 8 * n, cudaMemcpyHostToDevice, B->s));
+    TB_CUDA(cudaMemcpyAsync(G->d_Ni, Ni.data(), 8 * n, cudaMemcpyHostToDevice, B->s));
+    TB_CUDA(cudaMemcpyAsync(G->d_off, offs.data(), 8 * n, cudaMemcpyHostToDevice, B->s));
+    TB_CUDA(cudaStreamSynchronize(B->s));   // host vectors go out of scope
+    return TMG_OK;
+}
+
+tmg_status build_graph(tmg_batch* B, tmg_batch_group* G, int dir) {
+    cudaGraph_t g = nullptr;
+    TB_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+    alignas(cudaGraphNodeParams) unsigned char buf[sizeof(cudaGraphNodeParams)];
+    memset(buf, 0, sizeof(buf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(buf);
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(B->s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ek = enqueue(B, G, dir);
+        cudaGraph_t cap = nullptr;
+        e = cudaStreamEndCapture(B->s, &cap);
+        if (ek != cudaSuccess) e = ek;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(e);
+    }
+    G->graph[dir] = g;
+    G->gexec[dir] = ex;
+    G->cond[dir] = (unsigned long long)h;
+    return TMG_OK;
+}
+
+// One group solve on the group's current F/u/u0 arrays.
+tmg_status solve_group(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0, int dir) {
+    const int use_graph = B->o.use_graph != 0;
+    if (use_graph && !G->gexec[dir]) {
+        tmg_status s = build_graph(B, G, dir);
+        if (s != TMG_OK) return s;
+    }
+    TB_CUDA(cudaStreamSynchronize(B->s));
+    BatchState* h = G->st_host;
+    memset(h, 0, sizeof(BatchState));
+    h->F = F;
+    h->u = u;
+    h->u0 = u0;
+    h->tol = B->o.tol;
+    h->max_cycles = B->o.max_cycles;
+    h->use_cond = use_graph;
+    h->cond = G->cond[dir];
+    TB_CUDA(cudaMemcpyAsync(G->st, h, sizeof(BatchState), cudaMemcpyHostToDevice, B->s));
+    kb_init<<<grid_flat(B, G->n), kBNT, 0, B->s>>>(G->bi, G->n);
+    TB_CUDA(cudaGetLastError());
+    TB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * G->n * G->Ng * G->d, B->s));
+    if (use_graph) {
+        TB_CUDA(cudaGraphLaunch(G->gexec[dir], B->s));
+    } else {
+        for (int k = 0; k <= B->o.max_cycles; k += 4) {
+            for (int i = 0; i < 4; ++i) TB_CUDA(enqueue(B, G, dir));
+            TB_CUDA(cudaMemcpyAsync(&h->done, &G->st->done, sizeof(int), cudaMemcpyDeviceToHost, B->s));
+            TB_CUDA(cudaStreamSynchronize(B->s));
+            if (h->done) break;
+        }
+    }
+    TB_CUDA(cudaMemcpyAsync(h, G->st, sizeof(BatchState), cudaMemcpyDeviceToHost, B->s));
+    std::vector<int> cyc(G->n);
+    std::vector<double> rel(G->n);
+    TB_CUDA(cudaMemcpyAsync(cyc.data(), G->bi.cycles, 4 * G->n, cudaMemcpyDeviceToHost, B->s));
+    TB_CUDA(cudaMemcpyAsync(rel.data(), G->bi.rel, 8 * G->n, cudaMemcpyDeviceToHost, B->s));
+    TB_CUDA(cudaStreamSynchronize(B->s));
+    for (int64_t j = 0; j < G->n; ++j) {
+        B->cycles[G->ids[j]] = cyc[j];
+        B->rel[G->ids[j]] = rel[j];
+    }
+    switch (h->done) {
+        case 1: return TMG_OK;
+        case 2: return TMG_ENOTCONV;
+        default: return TMG_ETIMEOUT;
+    }
+}
+
+tmg_status ensure_gather(tmg_batch_group* G) {
+    if (G->Fg) return TMG_OK;
+    const size_t nv = (size_t)G->n * G->Ng * G->d;
+    cudaError_t e = cudaMalloc(&G->Fg, 8 * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&G->ug, 8 * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&G->u0g, 8 * G->n);
+    if (e != cudaSuccess) {
+        g_last_cuda_b = (int)e;
+        return TMG_ENOMEM;
+    }
+    return TMG_OK;
+}
+
+tmg_status worst(tmg_status a, tmg_status b) {
+    if (a == TMG_OK) return b;
+    if (b == TMG_OK) return a;
+    return a == TMG_ENOTCONV ? b : a;
+}
+
+bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, const double* tau,
+                             const double* lambda, const int64_t* N, double omega, const tmg_opts* opts,
+                             void* stream) {
+    if (!out || n_inst < 1 || !p_t || !tau || !lambda || !N || !(omega < 2.0) || !isfinite(omega)) return TMG_EINVAL;
+    *out = nullptr;
+    tmg_opts o;
+    tmg_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 || o.gamma != 1 ||
+        (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 || o.max_cycles < 0 ||
+        !(o.tol >= 0.0))
+        return TMG_EINVAL;
+    for (int64_t i = 0; i < n_inst; ++i)
+        if (p_t[i] < 0 || p_t[i] > 3 || !(tau[i] > 0.0) || !isfinite(tau[i]) || !(lambda[i] >= 0.0) ||
+            !isfinite(lambda[i]) || N[i] < 1)
+            return TMG_EINVAL;
+    tmg_batch* B = new (std::nothrow) tmg_batch();
+    if (!B) return TMG_ENOMEM;
+    B->n_inst = n_inst;
+    B->p.assign(p_t, p_t + n_inst);
+    B->tau.assign(tau, tau + n_inst);
+    B->lambda.assign(lambda, lambda + n_inst);
+    B->N.assign(N, N + n_inst);
+    B->off.resize(n_inst);
+    int64_t acc = 0;
+    for (int64_t i = 0; i < n_inst; ++i) {
+        B->off[i] = acc;
+        acc += N[i] * (p_t[i] + 1);
+    }
+    B->total_values = acc;
+    B->o = o;
+    B->omega = omega;
+    B->cycles.assign(n_inst, 0);
+    B->rel.assign(n_inst, NAN);
+    B->s = static_cast<cudaStream_t>(stream);
+    if (!B->s) {
+        cudaError_t e = cudaStreamCreate(&B->s);
+        if (e != cudaSuccess) {
+            delete B;
+            return fail(e);
+        }
+        B->own_stream = true;
+    }
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        tmg_destroy_batched(B);
+        return fail(e);
+    }
+    B->max_blocks = nsm * 8;
+    // group by (p, padded length)
+    std::map<std::pair<int, int64_t>, std::vector<int64_t>> key;
+    for (int64_t i = 0; i < n_inst; ++i) {
+        int64_t Ng = 2;
+        while (Ng < N[i]) Ng *= 2;
+        key[{p_t[i], Ng}].push_back(i);
+    }
+    for (auto& kv : key) {
+        tmg_batch_group* G = new (std::nothrow) tmg_batch_group();
+        if (!G) {
+            tmg_destroy_batched(B);
+            return TMG_ENOMEM;
+        }
+        B->groups.push_back(G);
+        G->p = kv.first.first;
+        G->d = G->p + 1;
+        G->Ng = kv.first.second;
+        G->log2Ng = ilog2(G->Ng);
+        G->ids = kv.second;
+        G->n = (int64_t)G->ids.size();
+        tmg_status s = setup_group(B, G);
+        if (s != TMG_OK) {
+            tmg_destroy_batched(B);
+            return s;
+        }
+    }
+    // instance table for the gradient kernel
+    {
+        const size_t bytes = (size_t)n_inst * (8 + 8 + 8 + 4);
+        e = cudaMalloc(&B->table, bytes);
+        if (e != cudaSuccess) {
+            B->table = nullptr;
+            tmg_destroy_batched(B);
+            g_last_cuda_b = (int)e;
+            return TMG_ENOMEM;
+        }
+        std::vector<char> h(bytes);
+        memcpy(h.data(), B->off.data(), 8 * n_inst);
+        memcpy(h.data() + 8 * n_inst, B->N.data(), 8 * n_inst);
+        memcpy(h.data() + 16 * n_inst, B->tau.data(), 8 * n_inst);
+        memcpy(h.data() + 24 * n_inst, B->p.data(), 4 * n_inst);
+        e = cudaMemcpyAsync(B->table, h.data(), bytes, cudaMemcpyHostToDevice, B->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(B->s);
+        if (e != cudaSuccess) {
+            tmg_destroy_batched(B);
+            return fail(e);
+        }
+    }
+    // the caller's arrays serve directly when there is one unpadded group
+    if (B->groups.size() == 1 && B->groups[0]->Ng * B->groups[0]->n * B->groups[0]->d == B->total_values) {
+        bool unpadded = true;
+        for (int64_t i = 0; i < n_inst; ++i) unpadded = unpadded && N[i] == B->groups[0]->Ng;
+        B->groups[0]->direct = unpadded;
+    }
+    *out = B;
+    return TMG_OK;
+}
+
+tmg_status tmg_solve_batched(tmg_batch* B, const double* f, const double* u0, double* u) {
+    if (!B || !aligned16(f) || !aligned16(u) || !u0 || (reinterpret_cast<uintptr_t>(u0) & 7u)) return TMG_EINVAL;
+    tmg_status st = TMG_OK;
+    for (tmg_batch_group* G : B->groups) {
+        tmg_status s;
+        if (G->direct) {
+            s = solve_group(B, G, f, u, u0, 0);
+        } else {
+            s = ensure_gather(G);
+            if (s != TMG_OK) return s;
+            const int64_t nv = G->n * G->Ng * G->d;
+            kb_gather<<<grid_flat(B, nv), kBNT, 0, B->s>>>(f, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d,
+                                                           0, u0, G->u0g);
+            TB_CUDA(cudaGetLastError());
+            s = solve_group(B, G, G->Fg, G->ug, G->u0g, 0);
+            if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+            kb_scatter<<<grid_flat(B, nv), kBNT, 0, B->s>>>(G->ug, u, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 0);
+            TB_CUDA(cudaGetLastError());
+        }
+        if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+        st = worst(st, s);
+    }
+    TB_CUDA(cudaStreamSynchronize(B->s));
+    return st;
+}
+
+tmg_status tmg_adjoint_batched(tmg_batch* B, const double* g, const double* u, double* dJdf, double* dJdu0,
+                               double* dJdlambda) {
+    if (!B || !aligned16(g) || !aligned16(u) || !aligned16(dJdf) || !dJdu0 || !dJdlambda ||
+        (reinterpret_cast<uintptr_t>(dJdu0) & 7u) || (reinterpret_cast<uintptr_t>(dJdlambda) & 7u))
+        return TMG_EINVAL;
+    tmg_status st = TMG_OK;
+    for (tmg_batch_group* G : B->groups) {
+        tmg_status s = ensure_gather(G);
+        if (s != TMG_OK) return s;
+        const int64_t nv = G->n * G->Ng * G->d;
+        // L^T mu = g in reversed time (causal there, so padding at the end stays exact)
+        kb_gather<<<grid_flat(B, nv), kBNT, 0, B->s>>>(g, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1,
+                                                       nullptr, G->u0g);
+        TB_CUDA(cudaGetLastError());
+        s = solve_group(B, G, G->Fg, G->ug, G->u0g, 1);
+        if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+        kb_scatter<<<grid_flat(B, nv), kBNT, 0, B->s>>>(G->ug, dJdf, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1);
+        TB_CUDA(cudaGetLastError());
+        st = worst(st, s);
+    }
+    // per-instance gradients over the caller's layout
+    const int64_t n = B->n_inst;
+    const int64_t* d_off = static_cast<const int64_t*>(B->table);
+    const int64_t* d_N = d_off + n;
+    const double* d_tau = reinterpret_cast<const double*>(d_N + n);
+    const int* d_p = reinterpret_cast<const int*>(d_tau + n);
+    kb_grads<<<(int)std::min<int64_t>(n, 65535), kBNT, 0, B->s>>>(dJdf, u, d_off, d_N, d_p, d_tau, n, dJdu0,
+                                                                  dJdlambda);
+    TB_CUDA(cudaGetLastError());
+    TB_CUDA(cudaStreamSynchronize(B->s));
+    return st;
+}
+
+tmg_status tmg_stats_batched(const tmg_batch* B, int* cycles, double* rel_res, int* max_cycles_used) {
+    if (!B) return TMG_EINVAL;
+    int mx = 0;
+    for (int64_t i = 0; i < B->n_inst; ++i) {
+        if (cycles) cycles[i] = B->cycles[i];
+        if (rel_res) rel_res[i] = B->rel[i];
+        mx = std::max(mx, B->cycles[i]);
+    }
+    if (max_cycles_used) *max_cycles_used = mx;
+    return TMG_OK;
+}
+
+tmg_status tmg_batch_info(const tmg_batch* B, int* n_groups, int64_t* padded_values) {
+    if (!B) return TMG_EINVAL;
+    if (n_groups) *n_groups = (int)B->groups.size();
+    if (padded_values) {
+        int64_t t = 0;
+        for (auto* G : B->groups) t += G->n * G->Ng * G->d;
+        *padded_values = t;
+    }
+    return TMG_OK;
+}
+
+void tmg_destroy_batched(tmg_batch* B) {
+    if (!B) return;
+    cudaStreamSynchronize(B->s);
+    for (tmg_batch_group* G : B->groups) {
+        for (int dir = 0; dir < 2; ++dir) {
+            if (G->gexec[dir]) cudaGraphExecDestroy(G->gexec[dir]);
+            if (G->graph[dir]) cudaGraphDestroy(G->graph[dir]);
+        }
+        if (G->ws) cudaFree(G->ws);
+        if (G->st_host) cudaFreeHost(G->st_host);
+        if (G->Fg) cudaFree(G->Fg);
+        if (G->ug) cudaFree(G->ug);
+        if (G->u0g) cudaFree(G->u0g);
+        delete G;
+    }
+    if (B->table) cudaFree(B->table);
+    if (B->own_stream) cudaStreamDestroy(B->s);
+    delete B;
+}
+
+}  // extern "C"

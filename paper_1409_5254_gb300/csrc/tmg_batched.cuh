@@ -1,0 +1,362 @@
+// Batched solves: many independent problems u' + lambda_i u = f_i with the
+// same degree p_t and the same (power-of-two) number of intervals N in one
+// set of launches.  Instance i occupies intervals [i N, (i+1) N) of every
+// level array ([n_inst][N_l][D], N_l = N / 2^l), so a coarse pair never
+// straddles two instances and each level kernel covers all instances at once.
+// Differences from the single-problem kernels:
+//   * the one-value halo restarts at every instance (u0_i on level 0, zero on
+//     the correction levels) -- the lane whose pair opens an instance ignores
+//     the shuffled value;
+//   * level constants (A^{-1}, g, c, alpha, omega of z_i 2^l) come from a table
+//     indexed by (instance, level);
+//   * every instance has its own residual norm, stopping test and active flag;
+//     a converged instance is frozen (its lanes compute on zeros and store
+//     nothing);
+//   * the coarsest level (at most 64 intervals) is solved exactly by one warp
+//     per instance with a warp-wide scan of the affine interval maps.
+#pragma once
+
+#include "tmg_kernels.cuh"
+
+namespace tmg {
+
+struct BatchState {
+    const double* F;          // [n_inst][N][D]
+    double* u;                // [n_inst][N][D]
+    const double* u0;         // [n_inst]
+    double tol;
+    int max_cycles;
+    int cycle;                // residual evaluations done
+    int done;                 // 0 running, 1 all converged, 2 some hit the cycle limit, 3 non-finite
+    int use_cond;
+    unsigned ticket;
+    int active_count;
+    int failed;               // instances stopped by the cycle limit or a non-finite norm
+    unsigned long long cond;
+};
+
+struct BatchInst {
+    double* nF;       // ||F_i||
+    double* norm2;    // ||r_i||^2 of the current cycle
+    int* active;      // 1 while instance i iterates
+    int* cycles;      // cycles applied when instance i stopped
+    double* rel;      // its final relative residual
+};
+
+// Segmented warp sum of v over lanes with the same instance id (ids are
+// non-decreasing along the lanes); the first lane of each run adds the run's
+// total to norm2[id].
+__device__ __forceinline__ void segmented_norm_add(double v, int64_t id, bool valid, double* norm2) {
+    const int lane = threadIdx.x & 31;
+    if (!valid) id = -1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double vo = __shfl_down_sync(kFull, v, off);
+        const long long io = __shfl_down_sync(kFull, (long long)id, off);
+        if (lane + off < 32 && io == id) v += vo;
+    }
+    const long long ip = __shfl_up_sync(kFull, (long long)id, 1);
+    if (valid && (lane == 0 || ip != id)) atomicAdd(&norm2[id], v);
+}
+
+constexpr int kBNT = 256;
+
+// Level 0: residual of every active instance (float pairs for the mixed form,
+// FP64 otherwise), norms, r stored in T, zero-start pre-smoothing and
+// restriction onto level 1 (fc == nullptr when level 0 is the coarsest).
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, int log2N,
+                                                 const LevelK<T, D>* __restrict__ lk, const Res0* __restrict__ res,
+                                                 int nlev, Xfer<T, D> X, int nu1, int H,
+                                                 const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const double* __restrict__ F = st->F;
+    const double* __restrict__ uu = st->u;
+    constexpr bool kMixed = std::is_same<T, float>::value;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    const int64_t mask = (1ll << log2N) - 1;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const int64_t inst = inb ? (2 * q) >> log2N : 0;
+        const bool act = inb && bi.active[inst];
+        const bool own = act && lane >= H;
+        const bool first = ((2 * q) & mask) == 0;
+        const LevelK<T, D> K = lk[inst * nlev];
+        const Res0 R = res[inst];
+        double uv[2][D], Fv[2][D];
+        load_pair<double, D>(uu, q, act, uv);
+        load_pair<double, D>(F, q, act, Fv);
+        const double u0i = act ? st->u0[inst] : 0.0;
+        T rt[2][D];
+        if constexpr (kMixed) {
+            ff us0[D], us1[D], sE0, sB0, sE1, sB1;
+            small_sums<DIR, D>(uv[0], us0, sE0, sB0);
+            small_sums<DIR, D>(uv[1], us1, sE1, sB1);
+            double up0 = shfl_prev(uv[1][0]);
+            ff sp{shfl_prev(sB1.hi), shfl_prev(sB1.lo)};
+            if (first) {                 // the value before the instance's first interval: b^T u = u0_i
+                up0 = u0i;
+                sp = ff{0.f, 0.f};
+            }
+            float r0[D], r1[D];
+            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0);
+            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                rt[0][k] = act ? r0[k] : 0.f;
+                rt[1][k] = act ? r1[k] : 0.f;
+            }
+        } else {
+            double r[2][D];
+            const double b0 = bval<DIR, double, D>(uv[0]);
+            const double b1 = bval<DIR, double, D>(uv[1]);
+            double ep = shfl_prev(b1);
+            if (first) ep = u0i;
+            const double E0 = DIR == 0 ? b0 : endval<double, D>(uv[0]);
+            const double E1 = DIR == 0 ? b1 : endval<double, D>(uv[1]);
+            residual0<DIR, D>(Fv[0], uv[0], ep, E0, R, r[0]);
+            residual0<DIR, D>(Fv[1], uv[1], b0, E1, R, r[1]);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) rt[i][k] = act ? (T)r[i][k] : T(0);
+        }
+        double ss = 0.0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double v;
+                if constexpr (kMixed) v = f2d_int(rt[i][k]);   // no conversion instruction on the FP64 pipe
+                else v = (double)rt[i][k];
+                ss = fma(v, v, ss);
+            }
+        segmented_norm_add(ss, inst, own, bi.norm2);
+        if (own) store_pair<T, D>(rT, q, rt);
+        if (fc != nullptr) {
+            T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
+            presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1, first);
+            residual_tracked<DIR, T, D>(rt, c, w, rc, first);
+            restrict_pair<T, D>(X, rc, out);
+            if (own) VecIO<T, D>::store(fc + q * D, out);
+        }
+    }
+}
+
+// Per-instance stopping test after the level-0 residual of cycle k.
+__global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi, int64_t n_inst) {
+    if (st->done) {                          // a finished batch must also end the graph loop
+        if (st->use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+            cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
+        return;
+    }
+    const int k = st->cycle;
+    int act_local = 0, fail_local = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kBNT + threadIdx.x; i < n_inst; i += (int64_t)gridDim.x * kBNT) {
+        if (!bi.active[i]) continue;
+        const double nrm = sqrt(bi.norm2[i]);
+        bi.norm2[i] = 0.0;
+        if (k == 0) bi.nF[i] = nrm;
+        const double nF = bi.nF[i];
+        const double rel = nF > 0.0 ? nrm / nF : nrm;
+        const bool bad = !(rel == rel) || rel > 1.0e300;
+        if (bad || rel <= st->tol || k >= st->max_cycles) {
+            bi.active[i] = 0;
+            bi.cycles[i] = k;
+            bi.rel[i] = rel;
+            if (bad || rel > st->tol) ++fail_local;
+        } else {
+            ++act_local;
+        }
+    }
+    __shared__ int sa, sf;
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        sa = 0;
+        sf = 0;
+    }
+    __syncthreads();
+    if (act_local) atomicAdd(&sa, act_local);
+    if (fail_local) atomicAdd(&sf, fail_local);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sa) atomicAdd(&st->active_count, sa);
+        if (sf) atomicAdd(&st->failed, sf);
+        __threadfence();
+        last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const int remaining = atomicAdd(&st->active_count, 0);
+    st->active_count = 0;
+    st->ticket = 0u;
+    st->cycle = k + 1;
+    if (remaining == 0) {
+        st->done = st->failed ? 2 : 1;
+        if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
+    }
+}
+
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_down(const T* __restrict__ f, T* __restrict__ fc, int64_t nchunks,
+                                                int log2N, const LevelK<T, D>* __restrict__ lk, int nlev, int level,
+                                                Xfer<T, D> X, int nu1, int H, const BatchState* __restrict__ st,
+                                                BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    const int64_t mask = (1ll << log2N) - 1;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const int64_t inst = inb ? (2 * q) >> log2N : 0;
+        const bool act = inb && bi.active[inst];
+        const bool first = ((2 * q) & mask) == 0;
+        const LevelK<T, D> K = lk[inst * nlev + level];
+        T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
+        load_pair<T, D>(f, q, act, fv);
+        presmooth_zero<DIR, T, D>(K, fv, h, u, w, nu1, first);
+        residual_tracked<DIR, T, D>(fv, u, w, r, first);
+        restrict_pair<T, D>(X, r, out);
+        if (act && lane >= H) VecIO<T, D>::store(fc + q * D, out);
+    }
+}
+
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_up(const T* __restrict__ f, const T* __restrict__ uc, T* __restrict__ u,
+                                              int64_t nchunks, int log2N, const LevelK<T, D>* __restrict__ lk,
+                                              int nlev, int level, Xfer<T, D> X, int nu1, int nu2, int H,
+                                              const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    const int64_t mask = (1ll << log2N) - 1;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const int64_t inst = inb ? (2 * q) >> log2N : 0;
+        const bool act = inb && bi.active[inst];
+        const bool first = ((2 * q) & mask) == 0;
+        const LevelK<T, D> K = lk[inst * nlev + level];
+        T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
+        load_pair<T, D>(f, q, act, fv);
+        load_one<T, D>(uc, q, act, c);
+        presmooth_zero<DIR, T, D>(K, fv, h, v, w, nu1, first);
+        prolong_add<T, D>(X, c, v);
+        postsmooth<DIR, T, D>(K, h, v, nu2, first);
+        if (act && lane >= H) store_pair<T, D>(u, q, v);
+    }
+}
+
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
+                                               int log2N, const LevelK<T, D>* __restrict__ lk, int nlev, Xfer<T, D> X,
+                                               int nu1, int nu2, int H, const BatchState* __restrict__ st,
+                                               BatchInst bi) {
+    if (st->done) return;
+    double* __restrict__ uu = st->u;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    const int64_t mask = (1ll << log2N) - 1;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const int64_t inst = inb ? (2 * q) >> log2N : 0;
+        const bool act = inb && bi.active[inst];
+        const bool own = act && lane >= H;
+        const bool first = ((2 * q) & mask) == 0;
+        const LevelK<T, D> K = lk[inst * nlev];
+        T rt[2][D], h[2][D], c[2][D], w[2][D], cc[D];
+        double uv[2][D];
+        load_pair<T, D>(rT, q, act, rt);
+        load_one<T, D>(uc, q, act, cc);
+        load_pair<double, D>(uu, q, own, uv);
+        presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1, first);
+        prolong_add<T, D>(X, cc, c);
+        postsmooth<DIR, T, D>(K, h, c, nu2, first);
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    if constexpr (std::is_same<T, float>::value) uv[i][k] += f2d_int(c[i][k]);
+                    else uv[i][k] += (double)c[i][k];
+                }
+            store_pair<double, D>(uu, q, uv);
+        }
+    }
+}
+
+// Exact solve of the coarsest level (Nc <= 64 intervals per instance), one
+// warp per instance: lane j holds intervals 2j and 2j+1; the affine maps
+// e_n = alpha e_{n-1} + c^T f_n (e_{-1} = 0) are combined by a warp scan,
+// then u_n = A^{-1} f_n + g e_{n-1}.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_coarse(const T* __restrict__ f, T* __restrict__ u, int64_t n_inst, int Nc,
+                                                  const LevelK<T, D>* __restrict__ lk, int nlev, int level,
+                                                  const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * kBNT) >> 5;
+    for (int64_t inst = wid; inst < n_inst; inst += nw) {
+        if (!bi.active[inst]) continue;            // uniform across the warp
+        const LevelK<T, D> K = lk[inst * nlev + level];
+        const int n0 = 2 * lane, n1 = 2 * lane + 1;
+        T f0[D], f1[D];
+        load_one<T, D>(f + inst * (int64_t)Nc * D, n0, n0 < Nc, f0);
+        load_one<T, D>(f + inst * (int64_t)Nc * D, n1, n1 < Nc, f1);
+        const T b0 = dotc<T, D>(K.c, f0), b1 = dotc<T, D>(K.c, f1);
+        T A = n1 < Nc ? K.alpha * K.alpha : (n0 < Nc ? K.alpha : T(1));
+        T B = n1 < Nc ? fma(K.alpha, b0, b1) : (n0 < Nc ? b0 : T(0));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T Ap = __shfl_up_sync(kFull, A, off);
+            const T Bp = __shfl_up_sync(kFull, B, off);
+            if (lane >= off) {
+                B = fma(A, Bp, B);
+                A = A * Ap;
+            }
+        }
+        T ein = __shfl_up_sync(kFull, B, 1);        // e before interval 2j (inclusive prefix of lane j-1)
+        if (lane == 0) ein = T(0);
+        T x0[D], x1[D];
+        matvec<T, D>(K.Ainv, f0, x0);
+        matvec<T, D>(K.Ainv, f1, x1);
+        const T emid = fma(K.alpha, ein, b0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            x0[k] = fma(K.g[k], ein, x0[k]);
+            x1[k] = fma(K.g[k], emid, x1[k]);
+        }
+        T* ub = u + inst * (int64_t)Nc * D;
+        if (n0 < Nc) VecIO<T, D>::store(ub + n0 * D, x0);
+        if (n1 < Nc) VecIO<T, D>::store(ub + n1 * D, x1);
+    }
+}
+
+// u += c on level 0 when level 0 is itself the coarsest level.
+template <typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_update0(const T* __restrict__ c, int64_t n_values, int values_per_inst,
+                                                   const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    double* __restrict__ uu = st->u;
+    for (int64_t i = (int64_t)blockIdx.x * kBNT + threadIdx.x; i < n_values; i += (int64_t)gridDim.x * kBNT) {
+        if (!bi.active[i / values_per_inst]) continue;
+        if constexpr (std::is_same<T, float>::value) uu[i] += f2d_int(c[i]);
+        else uu[i] += (double)c[i];
+    }
+}
+
+}  // namespace tmg

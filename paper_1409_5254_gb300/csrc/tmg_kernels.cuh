@@ -209,7 +209,7 @@ __device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t q, 
 // previous interval's endpoint value (warp shuffle).  h = A^{-1} f is kept.
 template <int DIR, typename T, int D>
 __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&f)[2][D], T (&h)[2][D],
-                                               T (&u)[2][D], T (&w)[2][D], int nu1) {
+                                               T (&u)[2][D], T (&w)[2][D], int nu1, bool first = false) {
     const T om = K.omega, om1 = T(1) - K.omega;
     const T om_first = nu1 > 0 ? om : T(0);     // no pre-smoothing leaves u = 0
 #pragma unroll
@@ -223,7 +223,8 @@ __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&
     }
     for (int s = 1; s < nu1; ++s) {
         const T e0 = bval<DIR, T, D>(u[0]);
-        const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
+        const T ep_s = shfl_prev(bval<DIR, T, D>(u[1]));
+        const T ep = first ? T(0) : ep_s;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
@@ -237,9 +238,10 @@ __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&
 // Residual f + a e_{n-1} - A u of a pair, with A u = w carried along.
 template <int DIR, typename T, int D>
 __device__ __forceinline__ void residual_tracked(const T (&f)[2][D], const T (&u)[2][D], const T (&w)[2][D],
-                                                 T (&r)[2][D]) {
+                                                 T (&r)[2][D], bool first = false) {
     const T e0 = bval<DIR, T, D>(u[0]);
-    const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
+    const T ep_s = shfl_prev(bval<DIR, T, D>(u[1]));
+    const T ep = first ? T(0) : ep_s;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         r[0][k] = f[0][k] + acoef<DIR>(k, ep) - w[0][k];
@@ -277,11 +279,13 @@ __device__ __forceinline__ void prolong_add(const Xfer<T, D>& X, const T (&uc)[D
 
 // nu post-smoothing sweeps: u <- (1-omega) u + omega (A^{-1} f + g e_{n-1}).
 template <int DIR, typename T, int D>
-__device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2][D], T (&u)[2][D], int nu) {
+__device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2][D], T (&u)[2][D], int nu,
+                                           bool first = false) {
     const T om = K.omega, om1 = T(1) - K.omega;
     for (int s = 0; s < nu; ++s) {
         const T e0 = bval<DIR, T, D>(u[0]);
-        const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
+        const T ep_s = shfl_prev(bval<DIR, T, D>(u[1]));
+        const T ep = first ? T(0) : ep_s;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
@@ -675,15 +679,16 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
     for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
         const int64_t q = tw * per + lane - H;
         const bool inb = q >= 0 && q < nchunks;
+        const bool own = inb && lane >= H;
         T rt[2][D], h[2][D], c[2][D], w[2][D], cc[D];
+        double uv[2][D];
         load_pair<T, D>(rT, q, inb, rt);
         load_one<T, D>(uc, q, inb, cc);
+        load_pair<double, D>(uu, q, own, uv);      // issued early: its latency overlaps the sweeps
         presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1);
         prolong_add<T, D>(X, cc, c);
         postsmooth<DIR, T, D>(K, h, c, nu2);
-        if (inb && lane >= H) {
-            double uv[2][D];
-            load_pair<double, D>(uu, q, true, uv);
+        if (own) {
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll

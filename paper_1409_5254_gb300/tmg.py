@@ -41,7 +41,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_adjoint", "tmg_cycle", "tmg_residual",
            "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
-           "tmg_last_cuda_error"]
+           "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
+           "tmg_stats_batched", "tmg_batch_info", "tmg_destroy_batched"]
 
 
 def library_path() -> str:
@@ -75,6 +76,18 @@ def _lib():
         L.tmg_residual_norm_noalloc.restype = ctypes.c_int
         L.tmg_destroy.argtypes = [_vp]
         L.tmg_destroy.restype = None
+        _ip, _lp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)
+        L.tmg_setup_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int64, _ip, _dp, _dp, _lp, ctypes.c_double,
+                                        ctypes.POINTER(_Opts), _vp]
+        L.tmg_solve_batched.argtypes = [_vp, _vp, _vp, _vp]
+        L.tmg_adjoint_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.tmg_stats_batched.argtypes = [_vp, _ip, _dp, _ip]
+        L.tmg_batch_info.argtypes = [_vp, _ip, _lp]
+        L.tmg_destroy_batched.argtypes = [_vp]
+        L.tmg_destroy_batched.restype = None
+        for name in ("tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched", "tmg_stats_batched",
+                     "tmg_batch_info"):
+            getattr(L, name).restype = ctypes.c_int
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
@@ -254,3 +267,103 @@ def residual_norm_noalloc(p: int, tau: float, lam: float, f, u0: float, u, r, no
     _check(_lib().tmg_residual_norm_noalloc(p, tau, lam, N, _dev_ptr(f, d, N, "f"), float(u0), _dev_ptr(u, d, N, "u"),
                                             _dev_ptr(r, d, N, "r"), ctypes.c_void_p(norm.data_ptr()), sp),
            "tmg_residual_norm_noalloc")
+
+
+def _opts(**kw) -> _Opts:
+    o = _Opts()
+    _lib().tmg_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision":
+            v = _PREC[v]
+        setattr(o, k, int(v) if isinstance(v, bool) else v)
+    return o
+
+
+class Batch:
+    """tmg_setup_batched / tmg_solve_batched / tmg_adjoint_batched (include/tmg.h).
+
+    Instance i has degree p[i], step tau[i], lam[i] and N[i] intervals; device
+    arrays are packed [instance][interval][coefficient] (float64)."""
+
+    def __init__(self, p, tau, lam, N, omega: float = 0.0, *, stream=None, **opts):
+        p = np.ascontiguousarray(p, dtype=np.int32)
+        tau = np.ascontiguousarray(np.broadcast_to(tau, p.shape), dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        N = np.ascontiguousarray(np.broadcast_to(N, p.shape), dtype=np.int64)
+        self.p, self.tau, self.lam, self.N = p, tau, lam, N
+        self.n = int(p.shape[0])
+        self.offsets = np.concatenate([[0], np.cumsum(N * (p + 1))]).astype(np.int64)
+        self.total = int(self.offsets[-1])
+        self._stream = stream
+        o = _opts(**opts)
+        h = _vp()
+        sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(_lib().tmg_setup_batched(ctypes.byref(h), self.n, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        tau.ctypes.data_as(_dp), lam.ctypes.data_as(_dp),
+                                        N.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), omega, ctypes.byref(o), sp),
+               "tmg_setup_batched")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().tmg_destroy_batched(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _ptr(self, t, n, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                and t.numel() == n):
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor with {n} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def solve(self, f, u0, u=None, *, allow_notconv: bool = False):
+        import torch
+        if u is None:
+            u = torch.empty(self.total, dtype=torch.float64, device=f.device)
+        st = _lib().tmg_solve_batched(self._h, self._ptr(f, self.total, "f"), self._ptr(u0, self.n, "u0"),
+                                      self._ptr(u, self.total, "u"))
+        _check(st, "tmg_solve_batched", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
+        return u
+
+    def adjoint(self, g, u, *, allow_notconv: bool = False):
+        import torch
+        dJdf = torch.empty_like(g)
+        du0 = torch.empty(self.n, dtype=torch.float64, device=g.device)
+        dlam = torch.empty(self.n, dtype=torch.float64, device=g.device)
+        st = _lib().tmg_adjoint_batched(self._h, self._ptr(g, self.total, "g"), self._ptr(u, self.total, "u"),
+                                        self._ptr(dJdf, self.total, "dJdf"), self._ptr(du0, self.n, "dJdu0"),
+                                        self._ptr(dlam, self.n, "dJdlambda"))
+        _check(st, "tmg_adjoint_batched", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
+        return dJdf, du0, dlam
+
+    def stats(self):
+        cyc = np.zeros(self.n, dtype=np.int32)
+        rel = np.zeros(self.n)
+        mx = ctypes.c_int(0)
+        _check(_lib().tmg_stats_batched(self._h, cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        rel.ctypes.data_as(_dp), ctypes.byref(mx)), "tmg_stats_batched")
+        return cyc, rel, mx.value
+
+    def info(self):
+        ng = ctypes.c_int(0)
+        pv = ctypes.c_int64(0)
+        _check(_lib().tmg_batch_info(self._h, ctypes.byref(ng), ctypes.byref(pv)), "tmg_batch_info")
+        return {"groups": ng.value, "padded_values": pv.value}
+
+    def split(self, x):
+        """Per-instance views (N_i, p_i + 1) of a packed host array."""
+        x = np.asarray(x)
+        return [x[self.offsets[i]:self.offsets[i + 1]].reshape(int(self.N[i]), int(self.p[i]) + 1)
+                for i in range(self.n)]

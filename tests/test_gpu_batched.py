@@ -1,0 +1,125 @@
+"""Batched solves (tmg_setup_batched / tmg_solve_batched / tmg_adjoint_batched)
+against the oracle, instance by instance.
+
+Tolerances: each instance stops at its own relative residual <= tol; the test
+evaluates that residual with the oracle in FP64 (<= 1.05 tol) and the error
+against forward substitution, which is at most cond(L_i) * tol with
+cond(L_i) <= 2/z_i (bounded by 2 N_i): the allowance is 2 N_i tol.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1409_5254_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1409_5254_gb300 import build_ext
+    build_ext.build()
+    return torch.device("cuda:0")
+
+
+def make_batch(seed, p, N, z):
+    """Packed load vectors on (0, 1) per instance, tau_i = 1/N_i, lambda_i = z_i N_i."""
+    rng = np.random.default_rng(seed)
+    Fs, u0 = [], rng.standard_normal(len(p))
+    for i in range(len(p)):
+        forcing = inputs.Forcing.draw(rng, 1.0)
+        Fs.append(inputs.load_vector(int(p[i]), int(N[i]), 1.0, forcing))
+    tau = 1.0 / np.asarray(N, dtype=np.float64)
+    lam = np.asarray(z) / tau
+    return Fs, u0, tau, lam
+
+
+def check_solution(Fs, u0, tau, lam, p, N, u_packed, batch, tol):
+    us = batch.split(u_packed)
+    worst = 0.0
+    for i in range(len(p)):
+        z = lam[i] * tau[i]
+        r = O.residual(int(p[i]), z, Fs[i], u0[i], us[i])
+        rel = np.linalg.norm(r) / np.linalg.norm(O.fold_u0(int(p[i]), Fs[i], u0[i]))
+        assert rel <= 1.05 * tol, (i, rel)
+        ex = O.fsub(int(p[i]), z, Fs[i], u0[i])
+        err = np.abs(us[i] - ex).max() / np.abs(ex).max()
+        assert err <= 2 * N[i] * tol, (i, err)
+        worst = max(worst, err)
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_uniform_batch(dev, prec):
+    from paper_1409_5254_gb300 import tmg
+    n, p, N = 96, 1, 2048
+    z = 10.0 ** np.random.default_rng(1).uniform(-3, 2, n)
+    Fs, u0, tau, lam = make_batch(1, [p] * n, [N] * n, z)
+    with tmg.Batch([p] * n, tau, lam, [N] * n, precision=prec, tol=1e-10, max_cycles=200) as B:
+        assert B.info()["groups"] == 1
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+    assert (rel <= 1e-10).all()
+    err = check_solution(Fs, u0, tau, lam, [p] * n, [N] * n, u.cpu().numpy(), B, 1e-10)
+    print(f"uniform {prec}: max cycles {mx}, worst err {err:.2e}")
+
+
+def test_uneven_batch_matches_oracle(dev):
+    """Different degrees, lengths (not powers of two) and steps in one batch."""
+    from paper_1409_5254_gb300 import tmg
+    N, p, z = inputs.uneven_batch(3, 40, nmin_exp=3.0, nmax_exp=12.0)
+    Fs, u0, tau, lam = make_batch(3, p, N, z)
+    with tmg.Batch(p, tau, lam, N, precision="mixed", tol=1e-10, max_cycles=300) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        info = B.info()
+    assert info["groups"] >= 4
+    check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
+
+
+def test_batch_of_one_matches_single_solve(dev):
+    from paper_1409_5254_gb300 import tmg
+    prob = inputs.scalar_problem(4, 4096, 2, lam=3.0, T=1.0, u0=0.5)
+    F = torch.from_numpy(prob["F"]).to(dev)
+    with tmg.Plan(2, prob["tau"], 3.0, 4096, precision="fp64", tol=1e-12) as plan:
+        u1 = plan.solve(F, 0.5).cpu().numpy()
+    with tmg.Batch([2], [prob["tau"]], [3.0], [4096], precision="fp64", tol=1e-12) as B:
+        u2 = B.solve(F.reshape(-1), torch.tensor([0.5], dtype=torch.float64, device=dev)).cpu().numpy()
+    ex = O.fsub(2, 3.0 * prob["tau"], prob["F"], 0.5)
+    assert np.abs(u2.reshape(-1, 3) - ex).max() <= 1e-9 * np.abs(ex).max()
+    assert np.abs(u1 - ex).max() <= 1e-9 * np.abs(ex).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_adjoint_matches_oracle(dev, prec):
+    from paper_1409_5254_gb300 import tmg
+    N, p, z = inputs.uneven_batch(5, 12, nmin_exp=4.0, nmax_exp=11.0)
+    Fs, u0, tau, lam = make_batch(5, p, N, z)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    rng = np.random.default_rng(9)
+    with tmg.Batch(p, tau, lam, N, precision=prec, tol=tol, max_cycles=400) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        us = B.split(u.cpu().numpy())
+        gs = []
+        for i in range(len(p)):
+            _, _, _, b = O.blocks(int(p[i]))
+            y = rng.standard_normal(int(N[i]))
+            gs.append(np.outer(O.nodal_values(int(p[i]), us[i]) - y, b))
+        g = torch.from_numpy(np.concatenate([x.reshape(-1) for x in gs])).to(dev)
+        dJdf, du0, dlam = B.adjoint(g, u)
+    mus = B.split(dJdf.cpu().numpy())
+    du0, dlam = du0.cpu().numpy(), dlam.cpu().numpy()
+    for i in range(len(p)):
+        zi = lam[i] * tau[i]
+        allow = 2.0 * max(N[i], 1.0 / zi) * tol * 10
+        mu_ref = O.adj_sweep(int(p[i]), zi, gs[i])
+        assert np.abs(mus[i] - mu_ref).max() <= allow * np.abs(mu_ref).max(), i
+        _, d0, dl = O.adjoint_grads(int(p[i]), lam[i], tau[i], gs[i], us[i])
+        assert du0[i] == pytest.approx(d0, rel=allow, abs=1e-12)
+        assert dlam[i] == pytest.approx(dl, rel=allow, abs=1e-12)
