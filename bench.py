@@ -225,6 +225,7 @@ def run_ours(args):
                 per_p[str(p)] = {"error": str(e)}
             del Fp, up
         extra["per_p_mixed"] = per_p
+        extra["batched"] = run_batched_configs(dev, stream, args.steps, torch)
 
     # end to end through the host-array entry point (pinned buffers, copies inside the call)
     F_h = torch.from_numpy(prob["F"]).pin_memory()
@@ -266,6 +267,106 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _time_batch(batch, f, u0, u, steps, stream, torch):
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        batch.solve(f, u0, u)
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def run_batched_configs(dev, stream, steps, torch):
+    """The batched workloads: decoupled 2-D heat modes, an uneven batch, and
+    gradients through the adjoint.  One step = one batched solve (plus the
+    adjoint for the gradient workload); inputs resident in HBM."""
+    import numpy as np
+    from paper_1409_5254_gb300 import inputs, tmg
+
+    out = {}
+    # 65,536 heat modes, N = 4096, p_t = 1, T = 1
+    lam, amps, freqs = inputs.heat_modes_batch(2, 256, 4096, 1)
+    n, N, p = lam.shape[0], 4096, 1
+    f = inputs.sine_load_vectors(amps, freqs, 1.0, N, p, device=dev).reshape(-1)
+    u0 = torch.zeros(n, dtype=torch.float64, device=dev)
+    u = torch.empty_like(f)
+    res = {}
+    for prec in ("mixed", "fp64"):
+        with tmg.Batch([p] * n, 1.0 / N, lam, N, precision=prec, tol=TOL, max_cycles=200, stream=stream) as B:
+            B.solve(f, u0, u)
+            ms = _time_batch(B, f, u0, u, max(1, steps // 10) if prec == "mixed" else 1, stream, torch)
+            cyc, rel, mx = B.stats()
+        res[prec] = {"value": n * N * (p + 1) / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
+                     "max_rel_res": float(rel.max())}
+    out["heat_modes_65536x4096_p1"] = {"unit": "DoF/s", "instances": n, "N": N, "p_t": p,
+                                       "lambda_range": [float(lam.min()), float(lam.max())], **res}
+    del f, u, u0
+    torch.cuda.empty_cache()
+
+    # uneven batch: 10,000 instances, N log-uniform in [2^6, 2^16], p_t in {0..3}, lambda tau in [1e-3, 1e3]
+    Nv, pv, z = inputs.uneven_batch(3, 10000)
+    tau = 1.0 / Nv
+    lamv = z / tau
+    A, K = inputs.sinusoid_batch_params(3, len(Nv))
+    parts = [inputs.sine_load_vectors(A[i:i + 1], K[i:i + 1], 1.0, int(Nv[i]), int(pv[i]), device=dev).reshape(-1)
+             for i in range(len(Nv))]
+    f = torch.cat(parts)
+    del parts
+    u0 = torch.ones(len(Nv), dtype=torch.float64, device=dev)
+    u = torch.empty_like(f)
+    dofs = int((Nv * (pv + 1)).sum())
+    res = {}
+    for prec in ("mixed", "fp64"):
+        with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream) as B:
+            B.solve(f, u0, u)
+            ms = _time_batch(B, f, u0, u, max(1, steps // 10), stream, torch)
+            cyc, rel, mx = B.stats()
+            info = B.info()
+        res[prec] = {"value": dofs / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
+                     "max_rel_res": float(rel.max())}
+    out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv), "dofs": dofs, "groups": info["groups"],
+                           "padded_dofs": info["padded_values"], **res}
+    del f, u, u0
+    torch.cuda.empty_cache()
+
+    # gradients: 4096 instances, N = 16384, p_t = 2, lambda log-uniform in [1, 1e4], T = 1
+    n, N, p = 4096, 16384, 2
+    lamg, u0n, target = inputs.adjoint_problem(4, n, N, p)
+    A, K = inputs.sinusoid_batch_params(4, n)
+    f = inputs.sine_load_vectors(A, K, 1.0, N, p, device=dev).reshape(-1)
+    u0 = torch.from_numpy(u0n).to(dev)
+    y = torch.from_numpy(target).to(dev)
+    u = torch.empty_like(f)
+    with tmg.Batch([p] * n, 1.0 / N, lamg, N, precision="mixed", tol=TOL, max_cycles=300, stream=stream) as B:
+        def step():
+            B.solve(f, u0, u)
+            e = u.view(n, N, p + 1).sum(dim=2)
+            g = ((e - y)[:, :, None].expand(n, N, p + 1)).contiguous().reshape(-1)
+            return B.adjoint(g, u)
+        step()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        k = max(1, steps // 10)
+        start.record(stream)
+        for _ in range(k):
+            step()
+        end.record(stream)
+        end.synchronize()
+        ms = start.elapsed_time(end) / k
+        cyc, rel, mx = B.stats()
+    out["adjoint_4096x16384_p2"] = {"unit": "DoF/s (forward + adjoint)", "instances": n, "N": N, "p_t": p,
+                                    "value": n * N * (p + 1) / (ms * 1e-3), "gradients_per_s": 1e3 / ms,
+                                    "ms_per_step": round(ms, 3), "adjoint_max_cycles": int(mx),
+                                    "precision": "mixed"}
+    del f, u, u0, y
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(sample_N: int = 1 << 18):

@@ -151,3 +151,52 @@ def adjoint_problem(seed: int, n_inst: int, N: int, p: int = 2, T: float = 1.0):
     u0 = rng.standard_normal(n_inst)
     target = rng.standard_normal((n_inst, N))
     return lam, u0, target
+
+
+# ------------------------------------------------- large batched workloads --
+#
+# The batched workloads need billions of forcing evaluations, so their load
+# vectors are assembled with torch (on the GPU when given a CUDA device); the
+# random draws stay in numpy so every side sees the same parameters.
+
+def sine_load_vectors(amps, freqs, T, N: int, p: int, device="cpu", q: int = 8, chunk: int = 1024):
+    """Load vectors (n, N, p+1) of f_i(t) = sum_j amps[i, j] sin(2 pi freqs[i, j] t / T)
+    for n instances on the same mesh t_n = n T / N (float64)."""
+    import torch
+    amps = torch.as_tensor(np.asarray(amps, dtype=np.float64), device=device)
+    freqs = torch.as_tensor(np.asarray(freqs, dtype=np.float64), device=device)
+    n = amps.shape[0]
+    tau = T / N
+    xg, wg = np.polynomial.legendre.leggauss(q)
+    s = 0.5 * (xg + 1.0)
+    tab = torch.as_tensor(_legendre_table(p, s) * (0.5 * wg)[:, None], device=device)       # (q, d)
+    t = (torch.arange(N, dtype=torch.float64, device=device)[:, None]
+         + torch.as_tensor(s, device=device)[None, :]) * tau                                 # (N, q)
+    out = torch.empty((n, N, p + 1), dtype=torch.float64, device=device)
+    for i0 in range(0, n, chunk):
+        i1 = min(n, i0 + chunk)
+        ft = torch.zeros((i1 - i0, N, q), dtype=torch.float64, device=device)
+        for j in range(amps.shape[1]):
+            om = (2.0 * math.pi / T) * freqs[i0:i1, j]
+            ft += amps[i0:i1, j, None, None] * torch.sin(om[:, None, None] * t[None])
+        out[i0:i1] = tau * (ft @ tab)
+    return out
+
+
+def heat_modes_batch(seed: int = 2, n_grid: int = 256, N: int = 4096, p: int = 1, T: float = 1.0):
+    """Decoupled modes of a 2-D heat equation: lambda_k = 5-point Laplacian
+    eigenvalues of an n_grid^2 interior grid; f_k = (g_k / lambda_k) *
+    sum_{j<3} s_kj sin(2 pi m_kj t), g ~ N(0,1), s ~ U(-1,1), m ~ U{1..8}.
+    Returns (lam, amps, freqs) for sine_load_vectors."""
+    lam = heat_modes(n_grid)
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal(lam.shape[0])
+    s = rng.uniform(-1.0, 1.0, (lam.shape[0], 3))
+    m = rng.integers(1, 9, (lam.shape[0], 3)).astype(np.float64)
+    return lam, (g / lam)[:, None] * s, m
+
+
+def sinusoid_batch_params(seed: int, n: int, n_terms: int = 4):
+    """Per-instance sinusoid forcings as in the single-problem recipe."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, (n, n_terms)), rng.integers(1, 9, (n, n_terms)).astype(np.float64)

@@ -123,3 +123,53 @@ def test_batched_adjoint_matches_oracle(dev, prec):
         _, d0, dl = O.adjoint_grads(int(p[i]), lam[i], tau[i], gs[i], us[i])
         assert du0[i] == pytest.approx(d0, rel=allow, abs=1e-12)
         assert dlam[i] == pytest.approx(dl, rel=allow, abs=1e-12)
+
+
+def _sampled_check(B, f_dev_parts, u, idx, pv, Nv, tau, lam, u0, tol, params):
+    """Oracle check of sampled instances; their load vectors are rebuilt on the CPU."""
+    us = B.split(u.cpu().numpy())
+    A, K, T = params
+    for i in idx:
+        p, N = int(pv[i]), int(Nv[i])
+        F = inputs.sine_load_vectors(A[i:i + 1], K[i:i + 1], T, N, p, device="cpu")[0].numpy()
+        z = lam[i] * tau[i]
+        r = O.residual(p, z, F, u0[i], us[i])
+        rel = np.linalg.norm(r) / np.linalg.norm(O.fold_u0(p, F, u0[i]))
+        assert rel <= 1.05 * tol, (i, rel)
+        ex = O.fsub(p, z, F, u0[i])
+        assert np.abs(us[i] - ex).max() <= 2 * max(N, 1.0 / z) * tol * np.abs(ex).max(), i
+
+
+def test_full_size_heat_modes_sampled(dev):
+    """65,536 decoupled heat modes, N = 4096, p_t = 1, mixed: the benchmark's
+    configuration; 8 sampled instances (including the extreme lambdas)."""
+    from paper_1409_5254_gb300 import tmg
+    lam, amps, freqs = inputs.heat_modes_batch(2, 256, 4096, 1)
+    n, N, p = lam.shape[0], 4096, 1
+    f = inputs.sine_load_vectors(amps, freqs, 1.0, N, p, device=dev).reshape(-1)
+    u0 = np.zeros(n)
+    with tmg.Batch([p] * n, 1.0 / N, lam, N, precision="mixed", tol=1e-10, max_cycles=200) as B:
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+        assert (rel <= 1e-10).all()
+        idx = [int(np.argmin(lam)), int(np.argmax(lam))] + list(np.random.default_rng(0).integers(0, n, 6))
+        _sampled_check(B, None, u, idx, [p] * n, [N] * n, np.full(n, 1.0 / N), lam, u0, 1e-10, (amps, freqs, 1.0))
+
+
+def test_full_size_uneven_batch_sampled(dev):
+    """10,000 instances, N log-uniform in [2^6, 2^16], p_t in {0..3}, lambda tau
+    log-uniform in [1e-3, 1e3], mixed; 12 sampled instances."""
+    from paper_1409_5254_gb300 import tmg
+    Nv, pv, z = inputs.uneven_batch(3, 10000)
+    tau = 1.0 / Nv
+    lam = z / tau
+    A, K = inputs.sinusoid_batch_params(3, len(Nv))
+    f = torch.cat([inputs.sine_load_vectors(A[i:i + 1], K[i:i + 1], 1.0, int(Nv[i]), int(pv[i]),
+                                            device=dev).reshape(-1) for i in range(len(Nv))])
+    u0 = np.ones(len(Nv))
+    with tmg.Batch(pv, tau, lam, Nv, precision="mixed", tol=1e-10, max_cycles=300) as B:
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+        assert (rel <= 1e-10).all()
+        idx = [int(np.argmax(Nv)), int(np.argmin(Nv))] + list(np.random.default_rng(1).integers(0, len(Nv), 10))
+        _sampled_check(B, None, u, idx, pv, Nv, tau, lam, u0, 1e-10, (A, K, 1.0))
