@@ -41,38 +41,43 @@
 
 /* ---------------------------------------------------------------- basis -- */
 
+/* The quadratures below run in long double so that the FP64 blocks are the
+ * correctly rounded values of their definitions (a 12-point rule summed in
+ * double leaves errors of a few 1e-15 in the p = 3 entries). */
+typedef long double ldbl;
+
 /* Legendre P_k(x) and P_k'(x) for k = 0..n-1 by the three-term recurrence. */
-static void legendre(int n, double x, double *P, double *dP) {
-    P[0] = 1.0; dP[0] = 0.0;
-    if (n > 1) { P[1] = x; dP[1] = 1.0; }
+static void legendre(int n, ldbl x, ldbl *P, ldbl *dP) {
+    P[0] = 1.0L; dP[0] = 0.0L;
+    if (n > 1) { P[1] = x; dP[1] = 1.0L; }
     for (int k = 1; k + 1 < n; ++k) {
-        P[k + 1] = ((2.0 * k + 1.0) * x * P[k] - k * P[k - 1]) / (k + 1.0);
-        dP[k + 1] = dP[k - 1] + (2.0 * k + 1.0) * P[k];
+        P[k + 1] = ((2.0L * k + 1.0L) * x * P[k] - k * P[k - 1]) / (k + 1.0L);
+        dP[k + 1] = dP[k - 1] + (2.0L * k + 1.0L) * P[k];
     }
 }
 
 /* Gauss-Legendre nodes/weights on [0,1] by Newton's method on P_q. */
-static void gauss01(int q, double *x01, double *w01) {
-    double P[ORC_NQ + 2], dP[ORC_NQ + 2];
+static void gauss01(int q, ldbl *x01, ldbl *w01) {
+    ldbl P[ORC_NQ + 2], dP[ORC_NQ + 2];
     for (int i = 0; i < q; ++i) {
-        double x = cos(ORC_PI * (i + 0.75) / (q + 0.5));
+        ldbl x = cosl(ORC_PI * (i + 0.75L) / (q + 0.5L));
         for (int it = 0; it < 100; ++it) {
             legendre(q + 1, x, P, dP);
-            double dx = P[q] / dP[q];
+            ldbl dx = P[q] / dP[q];
             x -= dx;
-            if (fabs(dx) < 1e-16) break;
+            if (fabsl(dx) < 1e-30L) break;
         }
         legendre(q + 1, x, P, dP);
-        x01[i] = 0.5 * (x + 1.0);
-        w01[i] = 0.5 * 2.0 / ((1.0 - x * x) * dP[q] * dP[q]);
+        x01[i] = 0.5L * (x + 1.0L);
+        w01[i] = 0.5L * 2.0L / ((1.0L - x * x) * dP[q] * dP[q]);
     }
 }
 
 /* Shifted basis psi_k(s) = P_k(2s-1) and its s-derivative. */
-static void shifted(int d, double s, double *psi, double *dpsi) {
-    double P[ORC_MAXD], dP[ORC_MAXD];
-    legendre(d, 2.0 * s - 1.0, P, dP);
-    for (int k = 0; k < d; ++k) { psi[k] = P[k]; dpsi[k] = 2.0 * dP[k]; }
+static void shifted(int d, ldbl s, ldbl *psi, ldbl *dpsi) {
+    ldbl P[ORC_MAXD], dP[ORC_MAXD];
+    legendre(d, 2.0L * s - 1.0L, P, dP);
+    for (int k = 0; k < d; ++k) { psi[k] = P[k]; dpsi[k] = 2.0L * dP[k]; }
 }
 
 /*
@@ -86,25 +91,27 @@ static void shifted(int d, double s, double *psi, double *dpsi) {
  */
 void orc_blocks(int p, double *K, double *Mhat, double *a, double *b) {
     int d = p + 1;
-    double xq[ORC_NQ], wq[ORC_NQ], psi[ORC_MAXD], dpsi[ORC_MAXD];
+    ldbl xq[ORC_NQ], wq[ORC_NQ], psi[ORC_MAXD], dpsi[ORC_MAXD];
+    ldbl Kl[ORC_MAXD * ORC_MAXD] = {0}, Ml[ORC_MAXD * ORC_MAXD] = {0};
     gauss01(ORC_NQ, xq, wq);
-    memset(K, 0, sizeof(double) * d * d);
-    memset(Mhat, 0, sizeof(double) * d * d);
     for (int q = 0; q < ORC_NQ; ++q) {
         shifted(d, xq[q], psi, dpsi);
         for (int k = 0; k < d; ++k)
             for (int l = 0; l < d; ++l) {
-                K[k * d + l] -= wq[q] * psi[l] * dpsi[k];
-                Mhat[k * d + l] += wq[q] * psi[l] * psi[k];
+                Kl[k * d + l] -= wq[q] * psi[l] * dpsi[k];
+                Ml[k * d + l] += wq[q] * psi[l] * psi[k];
             }
     }
-    double psi0[ORC_MAXD], psi1[ORC_MAXD];
-    shifted(d, 0.0, psi0, dpsi);
-    shifted(d, 1.0, psi1, dpsi);
+    ldbl psi0[ORC_MAXD], psi1[ORC_MAXD];
+    shifted(d, 0.0L, psi0, dpsi);
+    shifted(d, 1.0L, psi1, dpsi);
     for (int k = 0; k < d; ++k) {
-        a[k] = psi0[k];
-        b[k] = psi1[k];
-        for (int l = 0; l < d; ++l) K[k * d + l] += psi1[l] * psi1[k];
+        a[k] = (double)psi0[k];
+        b[k] = (double)psi1[k];
+        for (int l = 0; l < d; ++l) {
+            K[k * d + l] = (double)(Kl[k * d + l] + psi1[l] * psi1[k]);
+            Mhat[k * d + l] = (double)Ml[k * d + l];
+        }
     }
 }
 
@@ -198,31 +205,50 @@ double orc_omega_star(int p, double z) {
  */
 void orc_transfer(int p, double *P1, double *P2) {
     int d = p + 1;
-    double xq[ORC_NQ], wq[ORC_NQ], psi[ORC_MAXD], dpsi[ORC_MAXD];
-    double cps[ORC_MAXD], cdps[ORC_MAXD];
-    double Mt1[ORC_MAXD * ORC_MAXD] = {0}, Mt2[ORC_MAXD * ORC_MAXD] = {0};
-    double Mh[ORC_MAXD * ORC_MAXD] = {0};
+    ldbl xq[ORC_NQ], wq[ORC_NQ], psi[ORC_MAXD], dpsi[ORC_MAXD];
+    ldbl cps[ORC_MAXD], cdps[ORC_MAXD];
+    ldbl Mt1[ORC_MAXD * ORC_MAXD] = {0}, Mt2[ORC_MAXD * ORC_MAXD] = {0};
+    ldbl Mh[ORC_MAXD * ORC_MAXD] = {0};
     gauss01(ORC_NQ, xq, wq);
     for (int q = 0; q < ORC_NQ; ++q) {
         shifted(d, xq[q], psi, dpsi);
         for (int k = 0; k < d; ++k)
             for (int l = 0; l < d; ++l) Mh[k * d + l] += wq[q] * psi[k] * psi[l];
-        shifted(d, 0.5 * xq[q], cps, cdps);          /* first half  */
+        shifted(d, 0.5L * xq[q], cps, cdps);          /* first half  */
         for (int k = 0; k < d; ++k)
             for (int l = 0; l < d; ++l) Mt1[k * d + l] += wq[q] * cps[l] * psi[k];
-        shifted(d, 0.5 * (xq[q] + 1.0), cps, cdps);  /* second half */
+        shifted(d, 0.5L * (xq[q] + 1.0L), cps, cdps);  /* second half */
         for (int k = 0; k < d; ++k)
             for (int l = 0; l < d; ++l) Mt2[k * d + l] += wq[q] * cps[l] * psi[k];
     }
-    /* Solve Mh * P = Mt column by column. */
-    double col[ORC_MAXD], x[ORC_MAXD];
-    for (int l = 0; l < d; ++l) {
-        for (int k = 0; k < d; ++k) col[k] = Mt1[k * d + l];
-        solve_small(d, Mh, col, x);
-        for (int k = 0; k < d; ++k) P1[k * d + l] = x[k];
-        for (int k = 0; k < d; ++k) col[k] = Mt2[k * d + l];
-        solve_small(d, Mh, col, x);
-        for (int k = 0; k < d; ++k) P2[k * d + l] = x[k];
+    /* The projected mass matrix is diagonal for an orthogonal basis but is
+     * solved as a general system: P = Mh^{-1} Mt, column by column, by
+     * Gaussian elimination in long double. */
+    for (int half = 0; half < 2; ++half) {
+        const ldbl *Mt = half == 0 ? Mt1 : Mt2;
+        double *P = half == 0 ? P1 : P2;
+        for (int l = 0; l < d; ++l) {
+            ldbl Ag[ORC_MAXD][ORC_MAXD + 1];
+            for (int k = 0; k < d; ++k) {
+                for (int j = 0; j < d; ++j) Ag[k][j] = Mh[k * d + j];
+                Ag[k][d] = Mt[k * d + l];
+            }
+            for (int c = 0; c < d; ++c) {
+                int piv = c;
+                for (int r = c + 1; r < d; ++r)
+                    if (fabsl(Ag[r][c]) > fabsl(Ag[piv][c])) piv = r;
+                for (int j = 0; j <= d; ++j) { ldbl t = Ag[c][j]; Ag[c][j] = Ag[piv][j]; Ag[piv][j] = t; }
+                for (int r = c + 1; r < d; ++r) {
+                    ldbl m = Ag[r][c] / Ag[c][c];
+                    for (int j = c; j <= d; ++j) Ag[r][j] -= m * Ag[c][j];
+                }
+            }
+            for (int r = d - 1; r >= 0; --r) {
+                ldbl sacc = Ag[r][d];
+                for (int j = r + 1; j < d; ++j) sacc -= Ag[r][j] * (ldbl)P[j * d + l];
+                P[r * d + l] = (double)(sacc / Ag[r][r]);
+            }
+        }
     }
 }
 
