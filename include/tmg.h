@@ -84,9 +84,12 @@ void tmg_opts_default(tmg_opts *opts);
  * uniformly, remark after Theorem chap4_theorem3).  stream is a cudaStream_t
  * (NULL = legacy default stream).  All setup arithmetic is FP64 on the host
  * (block inverses, alpha, omega*, transfer matrices); the library allocates
- * and owns every workspace.  Returns TMG_EINVAL for bad arguments,
- * TMG_EUNSUPPORTED if the coarsest level is larger than the on-chip coarse
- * solver holds, TMG_ENOMEM / TMG_ECUDA on allocation failure.
+ * and owns every workspace.  The levels below the first one that fits on one
+ * SM's shared memory run in a single-CTA coarse solver; when even the
+ * coarsest level is too large for that, it is solved exactly by a grid-wide
+ * scan (see tmg_solve_direct).  Returns TMG_EINVAL for bad arguments,
+ * TMG_EUNSUPPORTED for a W-cycle whose coarse levels are not all on chip,
+ * TMG_ENOMEM / TMG_ECUDA on allocation failure.
  */
 tmg_status tmg_setup(tmg_plan **plan, int p_t, double tau, double lambda, int64_t N, int levels,
                      double omega, const tmg_opts *opts, void *stream);
@@ -106,6 +109,18 @@ tmg_status tmg_solve(tmg_plan *plan, const double *f, double u0, double *u);
  * full copy bandwidth; pageable memory works too.
  */
 tmg_status tmg_solve_host(tmg_plan *plan, const double *f_host, double u0, double *u_host);
+
+/*
+ * Exact FP64 solve of L u = F without multigrid, by a parallel prefix scan.
+ * N = a b^T has rank one, so block forward substitution (the plain solution of
+ * eq. chap4_generalLinearSystemODE) is the scalar recurrence
+ * e_n = alpha e_{n-1} + c^T F_n for e_n = b^T u_n, then u_n = A^{-1} F_n +
+ * g e_{n-1}; affine maps compose associatively, and three passes (tile maps,
+ * tile prefixes, replay) evaluate it in parallel reading F once more than the
+ * minimum.  Not the paper's method: the reference the multigrid solve is
+ * measured against.  Arguments as for tmg_solve; synchronises the stream.
+ */
+tmg_status tmg_solve_direct(tmg_plan *plan, const double *f, double u0, double *u);
 
 /*
  * Gradients of a loss J(u) at the solution u of L u = F, through the adjoint

@@ -249,7 +249,13 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
             break;
         }
     }
-    if (P->lt < 0 || (o.gamma == 2 && P->lt > 1)) {
+    if (P->lt < 0) {
+        // the coarsest level does not fit on one chip: solve it with the grid-wide scan
+        P->lt = P->nlev - 1;
+        P->scan_coarsest = true;
+        P->tail_smem = 0;
+    }
+    if (o.gamma == 2 && (P->lt > 1 || P->scan_coarsest)) {
         tmg_destroy(P);
         return TMG_EUNSUPPORTED;
     }
@@ -274,6 +280,9 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
     const size_t off_p = off;
     off = align_up(off + sizeof(double) * P->max_blocks, A);
+    P->scan_tiles = (N + tmg::kScanTile - 1) / tmg::kScanTile;
+    const size_t off_scan = off;
+    off = align_up(off + sizeof(double) * 3 * P->scan_tiles, A);
     const size_t off_st = off;
     off = align_up(off + sizeof(tmg::DevState), A);
     P->ws_bytes = off;
@@ -293,6 +302,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     P->lk_dev = base + off_lk;
     P->lk_dev_adj = base + off_lk_adj;
     P->partials = reinterpret_cast<double*>(base + off_p);
+    P->scan_ws = base + off_scan;
     P->st = reinterpret_cast<tmg::DevState*>(base + off_st);
     ce = cudaMallocHost(&P->st_host, sizeof(tmg::DevState));
     if (ce != cudaSuccess) {
@@ -368,6 +378,13 @@ tmg_status tmg_adjoint(tmg_plan* P, const double* g, const double* u, double* dJ
                                       dJdu0, dJdlambda, P->s));
     TMG_CUDA(cudaStreamSynchronize(P->s));
     return s;
+}
+
+tmg_status tmg_solve_direct(tmg_plan* P, const double* f, double u0, double* u) {
+    if (!P || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    TMG_CUDA(tmg_ops_f64(P->d, 0)->enqueue_direct(P, f, u0, u));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return TMG_OK;
 }
 
 tmg_status tmg_cycle(tmg_plan* P, const double* f, double u0, double* u) {

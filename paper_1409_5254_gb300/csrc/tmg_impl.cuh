@@ -70,8 +70,25 @@ struct Impl {
 
     static size_t tail_bytes(int64_t Nt, int nl) { return tail_smem_bytes<T, D>(Nt, nl); }
 
+    // Kernel attributes: the on-chip solver's shared memory ceiling, and the
+    // staging buffers of the level-0 down kernel.
     static cudaError_t set_tail_attr(size_t bytes) {
-        return cudaFuncSetAttribute(k_tail<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_tail<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_scan_tiles<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)scan_smem_bytes<D, T>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_scan_apply<T, D, T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)scan_smem_bytes<D, T>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_scan_tiles<double, D, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)scan_smem_bytes<D, double>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_scan_apply<double, D, double, double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem_bytes<D, double>());
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_down0<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k_down0_smem_bytes<D>());
     }
 
     static cudaError_t upload(tmg_plan* P) {
@@ -80,6 +97,42 @@ struct Impl {
         for (int j = 0; j < nl; ++j) lk[j] = level_consts<T, D>(L(P)[P->lt + j]);
         return cudaMemcpyAsync(DIR == 0 ? P->lk_dev : P->lk_dev_adj, lk.data(), sizeof(LevelK<T, D>) * nl,
                                cudaMemcpyHostToDevice, P->s);
+    }
+
+    template <typename S>
+    static ScanK<S, D> scan_consts(const tmg_level_host& L) {
+        ScanK<S, D> K;
+        for (int i = 0; i < D * D; ++i) K.Ainv[i] = (S)L.Ainv[i];
+        for (int i = 0; i < D; ++i) {
+            K.g[i] = (S)L.g[i];
+            K.c[i] = (S)L.c[i];
+        }
+        K.alpha = (S)L.alpha;
+        return K;
+    }
+
+    // Exact solve of level l's equation L_l x = f by the three-pass scan, in
+    // precision S, from e_{-1} = e0 (or *e0p).
+    template <typename S, typename TIO>
+    static void enqueue_scan(tmg_plan* P, const TIO* f, TIO* x, int l, S e0, const double* e0p,
+                             const DevState* st) {
+        const int64_t N = P->lev[l].N;
+        const int64_t nt = (N + kScanTile - 1) / kScanTile;
+        S* aggA = static_cast<S*>(P->scan_ws);
+        S* aggB = aggA + nt;
+        S* ein = aggB + nt;
+        const ScanK<S, D> K = scan_consts<S>(L(P)[l]);
+        const int grid = (int)(nt < P->max_blocks ? nt : P->max_blocks);
+        k_scan_tiles<S, D, TIO><<<grid, kScanNT, scan_smem_bytes<D, TIO>(), P->s>>>(f, N, K, aggA, aggB, st);
+        k_scan_prefix<S><<<1, kScanNT, 0, P->s>>>(aggA, aggB, nt, e0, e0p, ein, st);
+        k_scan_apply<S, D, TIO, TIO><<<grid, kScanNT, scan_smem_bytes<D, TIO>(), P->s>>>(f, x, N, K, ein, st);
+    }
+
+    // tmg_solve_direct: the whole system by the FP64 scan (forward direction).
+    static cudaError_t enqueue_direct(tmg_plan* P, const double* f, double u0, double* u) {
+        if (DIR != 0) return cudaErrorInvalidValue;
+        Impl<double, D, 0>::template enqueue_scan<double, double>(P, f, u, 0, u0, nullptr, nullptr);
+        return cudaGetLastError();
     }
 
     static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr); }
@@ -102,8 +155,11 @@ struct Impl {
             mark();
             k_res0<DIR, T, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(rT, P->N, R, P->partials, P->st);
             mark();
-            k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N, nu1,
-                                                             nu2, P->o.gamma, P->st);
+            if (P->scan_coarsest)
+                enqueue_scan<T, T>(P, rT, static_cast<T*>(P->ul[0]), 0, T(0), nullptr, P->st);
+            else
+                k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
+                                                                      nu1, nu2, P->o.gamma, P->st);
             mark();
             k_update0<T><<<grid_flat(P, P->N * D), kNT, 0, P->s>>>(static_cast<const T*>(P->ul[0]), P->N * D,
                                                                     P->st);
@@ -114,7 +170,7 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark();
-            k_down0<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
+            k_down0<DIR, T, D><<<grid_for(P, nch, H), kNT, k_down0_smem_bytes<D>(), P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
                                                                   level_consts<T, D>(L(P)[0]), X, nu1, H,
                                                                   P->partials, P->st);
         }
@@ -127,9 +183,13 @@ struct Impl {
                                                                  level_consts<T, D>(L(P)[l]), X, nu1, H, P->st);
         }
         mark();
-        k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
-                                                         static_cast<T*>(P->ul[P->lt]), lk, X, nl,
-                                                         P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
+        if (P->scan_coarsest)
+            enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
+                               nullptr, P->st);
+        else
+            k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
+                                                             static_cast<T*>(P->ul[P->lt]), lk, X, nl,
+                                                             P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
         for (int l = P->lt - 1; l >= 1; --l) {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->lev[l].N / 2;
@@ -163,8 +223,9 @@ struct Impl {
     }
 
     static const tmg_ops* ops() {
-        static const tmg_ops o = {sizeof(T), &tail_bytes, &upload, &enqueue_cycle, &enqueue_cycle_timed,
-                                  &enqueue_normF, &enqueue_residual, &set_tail_attr};
+        static const tmg_ops o = {sizeof(T),        &tail_bytes,       &upload,        &enqueue_cycle,
+                                  &enqueue_cycle_timed, &enqueue_normF, &enqueue_residual, &set_tail_attr,
+                                  &enqueue_direct};
         return &o;
     }
 };

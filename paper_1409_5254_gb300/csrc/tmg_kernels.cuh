@@ -202,6 +202,50 @@ __device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t q, 
     }
 }
 
+// ------------------------------------------- asynchronous tile staging --
+//
+// Level-0 kernels stage the next warp tile of their FP64 inputs in shared
+// memory with cp.async while they compute the current one (two stages per
+// warp).  Each lane copies and later reads only its own bytes, stored
+// 16-byte-chunk-major so that a warp's reads of one chunk are contiguous.
+// Lanes outside the array copy zeros (source size 0).
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// NB bytes (a multiple of 16) per lane; buffer layout [NB/16][32] of 16-byte chunks.
+template <int NB>
+struct LaneStage {
+    static_assert(NB % 16 == 0, "staged lane data must be a multiple of 16 bytes");
+    static constexpr int C = NB / 16;
+    // Copy NB bytes at base + offset (in T elements); invalid lanes read nothing
+    // (source size 0, the address stays at the array base) and store zeros.
+    template <typename T>
+    static __device__ __forceinline__ void issue(uint4* buf, const T* base, int64_t offset, bool valid, int lane) {
+        const uint4* g = reinterpret_cast<const uint4*>(valid ? base + offset : base);
+#pragma unroll
+        for (int c = 0; c < C; ++c) cp_async16(&buf[c * 32 + lane], valid ? g + c : g, valid);
+    }
+    template <typename T, int NV>
+    static __device__ __forceinline__ void read(const uint4* buf, int lane, T (&out)[NV]) {
+        static_assert(NV * sizeof(T) == NB, "size mismatch");
+        union {
+            uint4 w[C];
+            T v[NV];
+        } u;
+#pragma unroll
+        for (int c = 0; c < C; ++c) u.w[c] = buf[c * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) out[i] = u.v[i];
+    }
+};
+
 // ------------------------------------------------ smoother building blocks --
 
 // Pre-smoothing from a zero guess for a coarse pair with right-hand side f:
@@ -574,32 +618,68 @@ __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __
 // ||r||^2 for the stopping test, r stored in the cycle precision T; then,
 // when fc != nullptr, the zero-guess pre-smoothing, residual and restriction
 // of the correction equation L c = r onto level 1.
-template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, Res0 R,
-                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
-                                               double* __restrict__ partials, DevState* st) {
-    if (cycle_finished(st)) return;
+// Dynamic shared memory of k_down0: 2 stages x (u, F) x 32 lanes x 2*D doubles per warp.
+template <int D>
+constexpr size_t k_down0_smem_bytes() {
+    return (size_t)(kNT / 32) * 2 * 2 * 32 * (2 * D * 8);
+}
+
+// The main loop of k_down0; FP64NORM selects the norm arithmetic at compile
+// time (FP64 squares in the first cycle, scaled FP32 squares afterwards) so
+// that no branch between the two sits inside the loop.
+template <bool FP64NORM, int DIR, typename T, int D>
+__device__ __forceinline__ double down0_loop(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks,
+                                             const Res0& R, const LevelK<T, D>& K, const Xfer<T, D>& X, int nu1,
+                                             int H, const DevState* st) {
     const double* __restrict__ F = st->F;
     const double* __restrict__ uu = st->u;
     const double u0 = st->u0;
     constexpr bool kMixed = std::is_same<T, float>::value;
-    // FP32 norm with a power-of-two scale, except in the first cycle whose
-    // residual magnitude is not known yet (FP64 then)
-    const bool fp64_norm = !kMixed || st->cycle == 0;
+    constexpr int kPairBytes = 2 * D * 8;
+    using Stage = LaneStage<kPairBytes>;
+    // two stages x (u, F) per warp, in dynamic shared memory (k_down0_smem_bytes)
+    extern __shared__ __align__(16) unsigned char k_down0_stage[];
+    auto stage = reinterpret_cast<uint4 (*)[2][2][Stage::C * 32]>(k_down0_stage);
     const float nsc = st->nscale;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int per = 32 - H;
     const int64_t ntiles = (nchunks + per - 1) / per;
     const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
     double ss = 0.0;
     float ssf = 0.f;
-    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+    int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5;
+    int sb = 0;
+    if (tw < ntiles) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        Stage::issue(stage[wib][0][0], uu, q * 2 * D, inb, lane);
+        Stage::issue(stage[wib][0][1], F, q * 2 * D, inb, lane);
+    }
+    cp_async_commit();
+    for (; tw < ntiles; tw += nwarps) {
         const int64_t q = tw * per + lane - H;
         const bool inb = q >= 0 && q < nchunks;
         const bool own = inb && lane >= H;
+        {   // prefetch the warp's next tile
+            const int64_t qn = (tw + nwarps) * per + lane - H;
+            const bool nb = tw + nwarps < ntiles && qn >= 0 && qn < nchunks;
+            Stage::issue(stage[wib][sb ^ 1][0], uu, qn * 2 * D, nb, lane);
+            Stage::issue(stage[wib][sb ^ 1][1], F, qn * 2 * D, nb, lane);
+            cp_async_commit();
+        }
+        cp_async_wait_prev();
+        double uvf[2 * D], Fvf[2 * D];
+        Stage::template read<double, 2 * D>(stage[wib][sb][0], lane, uvf);
+        Stage::template read<double, 2 * D>(stage[wib][sb][1], lane, Fvf);
+        sb ^= 1;
         double uv[2][D], Fv[2][D];
-        load_pair<double, D>(uu, q, inb, uv);
-        load_pair<double, D>(F, q, inb, Fv);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            uv[0][k] = uvf[k];
+            uv[1][k] = uvf[D + k];
+            Fv[0][k] = Fvf[k];
+            Fv[1][k] = Fvf[D + k];
+        }
         T rt[2][D];
         if constexpr (kMixed) {
             ff us0[D], us1[D], sE0, sB0, sE1, sB1;
@@ -643,7 +723,7 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    if (fp64_norm) {
+                    if constexpr (FP64NORM) {
                         ss = fma((double)rt[i][k], (double)rt[i][k], ss);
                     } else {
                         const float v = (float)rt[i][k] * nsc;
@@ -660,7 +740,22 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict
             if (own) VecIO<T, D>::store(fc + q * D, out);
         }
     }
-    if (!fp64_norm) ss = (double)ssf / ((double)nsc * (double)nsc);
+    cp_async_wait_all();
+    if constexpr (!FP64NORM) ss = (double)ssf / ((double)nsc * (double)nsc);
+    return ss;
+}
+
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, Res0 R,
+                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
+                                               double* __restrict__ partials, DevState* st) {
+    if (cycle_finished(st)) return;
+    constexpr bool kMixed = std::is_same<T, float>::value;
+    // FP32 norm with a power-of-two scale, except in the first cycle whose
+    // residual magnitude is not known yet (FP64 then)
+    double ss;
+    if (!kMixed || st->cycle == 0) ss = down0_loop<true, DIR, T, D>(rT, fc, nchunks, R, K, X, nu1, H, st);
+    else ss = down0_loop<false, DIR, T, D>(rT, fc, nchunks, R, K, X, nu1, H, st);
     grid_norm_finalize<kNT>(ss, partials, st);
 }
 

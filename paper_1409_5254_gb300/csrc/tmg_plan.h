@@ -8,6 +8,7 @@
 
 #include "../../include/tmg.h"
 #include "tmg_kernels.cuh"
+#include "tmg_scan.cuh"
 
 // FP64 constants of one level, computed once on the host.
 struct tmg_level_host {
@@ -34,7 +35,10 @@ struct tmg_plan {
     int nsm;
 
     int nlev;            // levels 0..nlev-1
-    int lt;              // first level solved on chip (tail)
+    int lt;              // first level solved on chip (tail), or the coarsest level when scanned
+    bool scan_coarsest;  // the coarsest level is too large for the chip: grid-wide scan instead of the tail
+    void* scan_ws;       // tile maps and incoming values of the scans (3 x ntiles x 8 bytes)
+    int64_t scan_tiles;
     size_t tail_smem;
     std::vector<tmg_level_host> lev;       // constants of L
     std::vector<tmg_level_host> lev_adj;   // constants of L^T in reversed time
@@ -82,6 +86,7 @@ struct tmg_ops {
     cudaError_t (*enqueue_normF)(tmg_plan*);       // ||F|| for a caller-given start
     cudaError_t (*enqueue_residual)(tmg_plan*, const double* f, double u0, const double* u, double* r);
     cudaError_t (*set_tail_attr)(size_t bytes);
+    cudaError_t (*enqueue_direct)(tmg_plan*, const double* f, double u0, double* u);   // FP64 exact scan solve
 };
 
 const tmg_ops* tmg_ops_f32(int d, int dir);

@@ -39,7 +39,7 @@ _LIB = None
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
-EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_adjoint", "tmg_cycle", "tmg_residual",
+EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
            "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
            "tmg_stats_batched", "tmg_batch_info", "tmg_destroy_batched"]
@@ -64,6 +64,7 @@ def _lib():
         L.tmg_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_solve_host.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp]
+        L.tmg_solve_direct.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.tmg_residual.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
         L.tmg_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, ctypes.c_int]
@@ -91,7 +92,7 @@ def _lib():
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
-        for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_adjoint", "tmg_cycle", "tmg_residual", "tmg_stats",
+        for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual", "tmg_stats",
                      "tmg_plan_info", "tmg_inspect", "tmg_profile_cycle"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
@@ -168,6 +169,15 @@ class Plan:
         st = _lib().tmg_solve(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0), _dev_ptr(u, self.d, self.N, "u"))
         _check(st, "tmg_solve", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
         self.last_status = st
+        return u
+
+    def solve_direct(self, f, u0: float, u=None):
+        """Exact FP64 solve by the parallel scan (tmg_solve_direct); not multigrid."""
+        import torch
+        if u is None:
+            u = torch.empty((self.N, self.d), dtype=torch.float64, device=f.device)
+        _check(_lib().tmg_solve_direct(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
+                                       _dev_ptr(u, self.d, self.N, "u")), "tmg_solve_direct")
         return u
 
     def solve_host(self, f_host, u0: float, u_host) -> int:

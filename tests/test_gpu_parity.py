@@ -74,6 +74,8 @@ CYCLE_CASES = [
     (0, 4096, 1.0, 1.0, 4, 0, 1, 1, 2, 0.0),          # W-cycle (on chip)
     (1, 1 << 14, 1.0, 1.0, 64, 4, 1, 1, 1, 0.0),      # capped level count: large coarsest scan
     (1, 3 * 1024, 1.0, 1.0, 2, 0, 1, 1, 1, 0.0),      # N = 3 * 2^10: odd coarsest level (3)
+    (2, 1 << 16, 1.0, 1.0, 16384, 0, 1, 1, 1, 0.0),   # coarsest level (16384) solved by the grid-wide scan
+    (0, 20002, 2.0, 1.0, 15000, 0, 1, 1, 1, 0.0),     # odd coarsest level of 10001 by the scan (ragged last tile)
 ]
 
 
@@ -248,3 +250,40 @@ def test_full_size_long_horizon_sampled(dev):
     err = np.abs(uh[idx] - u_ex[idx]).max() / np.abs(u_ex).max()
     print(f"full size: cycles={st.cycles} rel_res={rr:.2e} sampled err={err:.2e}")
     assert err <= 1e-6
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("N", [1, 5, 2047, 2048, 2049, 100003, (1 << 20) + 3])
+def test_direct_scan_solve(dev, p, N):
+    """tmg_solve_direct (three-pass FP64 scan) against forward substitution.
+
+    Backward error: the scan's residual is at the rounding level
+    (max(1e-13, 1e-15 sqrt(N (p+1)))).  Forward
+    error: both methods apply a correctly rounded multiplier alpha (off by up
+    to half an ulp, the same bias at every step), and the recurrence turns
+    that into a difference of up to ~N eps in alpha^N; the allowance is
+    max(1e-12, 8 N eps) relative."""
+    prob = inputs.scalar_problem(N % 13, N, p, lam=3.0, T=1.0, u0=0.9)
+    z = 3.0 * prob["tau"]
+    with tmg().Plan(p, prob["tau"], 3.0, N, levels=1) as plan:
+        u = plan.solve_direct(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
+    # per-component rounding of ~eps |u| over N (p+1) components (a random-walk sum)
+    assert rel_residual(p, z, prob["F"], prob["u0"], u) <= max(1e-13, 1e-15 * np.sqrt(N * (p + 1)))
+    ex = O.fsub(p, z, prob["F"], prob["u0"])
+    assert rel_err(u, ex) <= max(1e-12, 8 * N * 2.2e-16), rel_err(u, ex)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_single_level_large_problem_uses_scan(dev, prec):
+    """One level too large for the on-chip solver: each cycle is residual,
+    exact scan of the correction, update (FP32 scan for the mixed form)."""
+    N, p = 100000, 1
+    prob = inputs.scalar_problem(6, N, p, lam=1.0, T=10.0, u0=1.0)
+    z = prob["tau"]
+    with tmg().Plan(p, prob["tau"], 1.0, N, levels=1, precision=prec, tol=1e-10) as plan:
+        assert plan.info()["levels"] == 1
+        u = plan.solve(torch.from_numpy(prob["F"]).to(dev), 1.0).cpu().numpy()
+        st = plan.stats()
+    assert st.cycles <= (2 if prec == "fp64" else 6)
+    assert rel_residual(p, z, prob["F"], 1.0, u) <= 1.05e-10
+
