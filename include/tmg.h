@@ -70,6 +70,8 @@ typedef struct {
     int initial_guess;  /* 1: tmg_solve starts from the u passed in (default 0: u = 0) */
     int64_t tail_cap;   /* most intervals the on-chip coarse solver takes (0: default 8192);
                            smaller values move more levels to the streaming kernels */
+    int use_pdl;        /* 1: programmatic dependent launch between the kernels of a cycle,
+                           hiding each launch behind its predecessor's tail (default 1) */
 } tmg_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -179,6 +179,7 @@ void tmg_opts_default(tmg_opts* o) {
     o->use_graph = 1;
     o->initial_guess = 0;
     o->tail_cap = 0;
+    o->use_pdl = 1;
 }
 
 tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_t N, int levels, double omega,

@@ -1,6 +1,8 @@
 // Launch orchestration of one correction cycle for cycle precision T and D = p_t + 1.
 #pragma once
 
+#include <string.h>
+
 #include "tmg_plan.h"
 
 namespace tmg {
@@ -64,6 +66,25 @@ inline int grid_flat(const tmg_plan* P, int64_t n) {
     return (int)blocks;
 }
 
+// Launch with the programmatic-stream-serialisation attribute when the plan
+// asks for it (every cycle kernel starts with pdl_enter()).
+template <typename... KArgs, typename... Args>
+inline void launch(const tmg_plan* P, void (*kernel)(KArgs...), int grid, int block, size_t smem,
+                   Args... args) {
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = P->s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = P->o.use_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+}
+
 template <typename T, int D, int DIR>
 struct Impl {
     static const std::vector<tmg_level_host>& L(const tmg_plan* P) { return DIR == 0 ? P->lev : P->lev_adj; }
@@ -123,9 +144,9 @@ struct Impl {
         S* ein = aggB + nt;
         const ScanK<S, D> K = scan_consts<S>(L(P)[l]);
         const int grid = (int)(nt < P->max_blocks ? nt : P->max_blocks);
-        k_scan_tiles<S, D, TIO><<<grid, kScanNT, scan_smem_bytes<D, TIO>(), P->s>>>(f, N, K, aggA, aggB, st);
-        k_scan_prefix<S><<<1, kScanNT, 0, P->s>>>(aggA, aggB, nt, e0, e0p, ein, st);
-        k_scan_apply<S, D, TIO, TIO><<<grid, kScanNT, scan_smem_bytes<D, TIO>(), P->s>>>(f, x, N, K, ein, st);
+        launch(P, k_scan_tiles<S, D, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, N, K, aggA, aggB, st);
+        launch(P, k_scan_prefix<S>, 1, kScanNT, 0, aggA, aggB, nt, e0, e0p, ein, st);
+        launch(P, k_scan_apply<S, D, TIO, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, x, N, K, ein, st);
     }
 
     // tmg_solve_direct: the whole system by the FP64 scan (forward direction).
@@ -153,16 +174,16 @@ struct Impl {
         T* rT = static_cast<T*>(P->rT);
         if (P->lt == 0) {
             mark();
-            k_res0<DIR, T, D><<<grid_flat(P, P->N), kNT, 0, P->s>>>(rT, P->N, R, P->partials, P->st);
+            launch(P, k_res0<DIR, T, D>, grid_flat(P, P->N), kNT, 0, rT, P->N, R, P->partials, P->st);
             mark();
             if (P->scan_coarsest)
                 enqueue_scan<T, T>(P, rT, static_cast<T*>(P->ul[0]), 0, T(0), nullptr, P->st);
             else
-                k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
+                launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
                                                                       nu1, nu2, P->o.gamma, P->st);
             mark();
-            k_update0<T><<<grid_flat(P, P->N * D), kNT, 0, P->s>>>(static_cast<const T*>(P->ul[0]), P->N * D,
-                                                                    P->st);
+            launch(P, k_update0<T>, grid_flat(P, P->N * D), kNT, 0, static_cast<const T*>(P->ul[0]),
+                   (int64_t)(P->N * D), (const DevState*)P->st);
             mark();
             return cudaGetLastError();
         }
@@ -170,43 +191,39 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark();
-            k_down0<DIR, T, D><<<grid_for(P, nch, H), kNT, k_down0_smem_bytes<D>(), P->s>>>(rT, static_cast<T*>(P->fl[1]), nch, R,
-                                                                  level_consts<T, D>(L(P)[0]), X, nu1, H,
-                                                                  P->partials, P->st);
+            launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H), kNT, k_down0_smem_bytes<D>(), rT,
+                   static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
         }
         for (int l = 1; l < P->lt; ++l) {
             const int H = halo_lanes(sweeps_down(nu1));
             const int64_t nch = P->lev[l].N / 2;
             mark();
-            k_down<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
-                                                                 static_cast<T*>(P->fl[l + 1]), nch,
-                                                                 level_consts<T, D>(L(P)[l]), X, nu1, H, P->st);
+            launch(P, k_down<DIR, T, D>, grid_for(P, nch, H), kNT, 0, static_cast<const T*>(P->fl[l]),
+                   static_cast<T*>(P->fl[l + 1]), nch, level_consts<T, D>(L(P)[l]), X, nu1, H,
+                   (const DevState*)P->st);
         }
         mark();
         if (P->scan_coarsest)
             enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
                                nullptr, P->st);
         else
-            k_tail<DIR, T, D><<<1, kTailNT, P->tail_smem, P->s>>>(static_cast<const T*>(P->fl[P->lt]),
+            launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, static_cast<const T*>(P->fl[P->lt]),
                                                              static_cast<T*>(P->ul[P->lt]), lk, X, nl,
                                                              P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
         for (int l = P->lt - 1; l >= 1; --l) {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->lev[l].N / 2;
             mark();
-            k_up<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[l]),
-                                                               static_cast<const T*>(P->ul[l + 1]),
-                                                               static_cast<T*>(P->ul[l]), nch,
-                                                               level_consts<T, D>(L(P)[l]), X, nu1, nu2, H,
-                                                               P->st);
+            launch(P, k_up<DIR, T, D>, grid_for(P, nch, H), kNT, 0, static_cast<const T*>(P->fl[l]),
+                   static_cast<const T*>(P->ul[l + 1]), static_cast<T*>(P->ul[l]), nch, level_consts<T, D>(L(P)[l]),
+                   X, nu1, nu2, H, (const DevState*)P->st);
         }
         {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->N / 2;
             mark();
-            k_up0<DIR, T, D><<<grid_for(P, nch, H), kNT, 0, P->s>>>(rT, static_cast<const T*>(P->ul[1]), nch,
-                                                                level_consts<T, D>(L(P)[0]), X, nu1, nu2, H,
-                                                                P->st);
+            launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H), kNT, 0, (const T*)rT, static_cast<const T*>(P->ul[1]),
+                   nch, level_consts<T, D>(L(P)[0]), X, nu1, nu2, H, (const DevState*)P->st);
         }
         mark();
         return cudaGetLastError();

@@ -82,6 +82,16 @@ struct DevState {
 
 // ------------------------------------------------------------ helpers --
 
+// Programmatic dependent launch: a kernel of the cycle may be launched
+// before its predecessor in the stream has finished; it waits here, before
+// touching any memory, until the predecessor has completed and its writes are
+// visible, and then lets its own successor launch.  Without a programmatic
+// predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Coupling policy.  DIR = 0: the system of eq. chap4_generalLinearSystemODE,
 // N = a b^T with a_k = (-1)^k, b_l = 1.  DIR = 1: its transpose written in
 // reversed time, n -> N-1-n, which is again block lower-bidiagonal with
@@ -573,6 +583,7 @@ template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __restrict__ fc, int64_t nchunks,
                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
                                               const DevState* __restrict__ st) {
+    pdl_enter();
     if (st->done) return;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
@@ -596,6 +607,7 @@ template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __restrict__ uc, T* __restrict__ u,
                                             int64_t nchunks, LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2,
                                             int H, const DevState* __restrict__ st) {
+    pdl_enter();
     if (st->done) return;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
@@ -749,6 +761,7 @@ template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, Res0 R,
                                                LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
                                                double* __restrict__ partials, DevState* st) {
+    pdl_enter();
     if (cycle_finished(st)) return;
     constexpr bool kMixed = std::is_same<T, float>::value;
     // FP32 norm with a power-of-two scale, except in the first cycle whose
@@ -765,6 +778,7 @@ template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
                                              LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2, int H,
                                              const DevState* __restrict__ st) {
+    pdl_enter();
     if (st->done) return;
     double* __restrict__ uu = st->u;
     const int lane = threadIdx.x & 31;
@@ -801,6 +815,7 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_res0(T* __restrict__ rT, int64_t N, Res0 R, double* __restrict__ partials,
                                               DevState* st) {
+    pdl_enter();
     if (cycle_finished(st)) return;
     const double* __restrict__ F = st->F;
     const double* __restrict__ uu = st->u;
@@ -832,6 +847,7 @@ __global__ void __launch_bounds__(kNT) k_res0(T* __restrict__ rT, int64_t N, Res
 template <typename T>
 __global__ void __launch_bounds__(kNT) k_update0(const T* __restrict__ c, int64_t n_values,
                                                  const DevState* __restrict__ st) {
+    pdl_enter();
     if (st->done) return;
     double* __restrict__ uu = st->u;
     const int64_t stride = (int64_t)gridDim.x * kNT;
@@ -1037,6 +1053,7 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
                                                   const LevelK<T, D>* __restrict__ lk, Xfer<T, D> X, int nl,
                                                   int64_t Nt, int nu1, int nu2, int gamma,
                                                   const DevState* __restrict__ st) {
+    pdl_enter();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char tail_smem[];
     TailView<T, D> V;

@@ -114,6 +114,7 @@ template <typename S, int D, typename TIn>
 __global__ void __launch_bounds__(kScanNT) k_scan_tiles(const TIn* __restrict__ f, int64_t N, ScanK<S, D> K,
                                                         S* __restrict__ aggA, S* __restrict__ aggB,
                                                         const DevState* __restrict__ st) {
+    pdl_enter();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char scan_sm[];
     TIn* sm = reinterpret_cast<TIn*>(scan_sm);
@@ -136,6 +137,7 @@ template <typename S>
 __global__ void __launch_bounds__(kScanNT) k_scan_prefix(const S* __restrict__ aggA, const S* __restrict__ aggB,
                                                          int64_t ntiles, S e0, const double* e0p,
                                                          S* __restrict__ ein, const DevState* __restrict__ st) {
+    pdl_enter();
     if (st != nullptr && st->done) return;
     S carry = e0p != nullptr ? (S)(*e0p) : e0;
     for (int64_t base = 0; base < ntiles; base += kScanNT * kScanPT) {
@@ -168,6 +170,7 @@ template <typename S, int D, typename TIn, typename TOut>
 __global__ void __launch_bounds__(kScanNT) k_scan_apply(const TIn* __restrict__ f, TOut* __restrict__ u, int64_t N,
                                                         ScanK<S, D> K, const S* __restrict__ ein,
                                                         const DevState* __restrict__ st) {
+    pdl_enter();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char scan_sm[];
     TIn* sm = reinterpret_cast<TIn*>(scan_sm);

@@ -204,16 +204,16 @@ def test_residual_entry_point(dev):
                                rtol=1e-13, atol=1e-13)
 
 
-def test_graph_and_eager_agree_and_are_deterministic(dev):
+def test_graph_eager_and_pdl_agree_and_are_deterministic(dev):
     N, p = 1 << 15, 1
     prob = inputs.scalar_problem(2, N, p, lam=1.0, T=8.0, u0=1.0)
     Fd = torch.from_numpy(prob["F"]).to(dev)
     outs = []
-    for use_graph in (True, True, False):
-        with tmg().Plan(p, prob["tau"], 1.0, N, precision="mixed", use_graph=use_graph) as plan:
+    for use_graph, use_pdl in ((True, True), (True, True), (False, True), (True, False), (False, False)):
+        with tmg().Plan(p, prob["tau"], 1.0, N, precision="mixed", use_graph=use_graph, use_pdl=use_pdl) as plan:
             outs.append(plan.solve(Fd, prob["u0"]).cpu().numpy())
-    assert np.array_equal(outs[0], outs[1])
-    assert np.array_equal(outs[0], outs[2])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
 
 
 def test_not_converged_status(dev):
