@@ -154,7 +154,11 @@ def run_ours(args):
     prob = inputs.scalar_problem(1, N_FULL, P_MAIN, lam=LAM, tau=TAU, u0=U0)
     F = torch.from_numpy(prob["F"]).to(dev)
     u = torch.empty_like(F)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     plan = tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, use_graph=not args.eager)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t_setup) * 1e3
     for _ in range(args.warmup):
         plan.solve(F, U0, u)
     st = plan.stats()
@@ -180,6 +184,29 @@ def run_ours(args):
     Fh[0, 0] += U0
     Fh[0, 1] -= U0
     rel_fp64 = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(Fh))
+    del r, Fh
+
+    # exact FP64 solve by the parallel affine scan: the error of the timed
+    # result, and the direct solve as a throughput ceiling (one pass to reduce
+    # each tile of F, one to replay it: reads F twice, writes u once)
+    u_ex = plan.solve_direct(F, U0)
+    err_vs_fp64 = float((u - u_ex).abs().max() / u_ex.abs().max())
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    n_dir = max(3, args.steps // 2)
+    start.record(stream)
+    for _ in range(n_dir):
+        plan.solve_direct(F, U0, u_ex)
+    end.record(stream)
+    end.synchronize()
+    ms_dir = start.elapsed_time(end) / n_dir
+    dir_bytes = 3 * N_FULL * d * 8
+    direct = {"value": N_FULL * d / (ms_dir * 1e-3), "unit": "DoF/s", "ms_per_step": round(ms_dir, 4),
+              "precision": "fp64", "bytes_per_dof": 24, "lower_bound_bytes_per_dof": 16,
+              "hbm_frac": round(dir_bytes / (ms_dir * 1e-3) / 1e9 / hbm_peak, 4),
+              "note": "exact parallel-scan solve (not multigrid), same problem and stream"}
+    del u_ex
 
     # per-kernel times of one cycle (events on the plan's stream) and the roofline
     prof = plan.profile_cycle(F, U0, u.clone(), reps=20)
@@ -260,7 +287,8 @@ def run_ours(args):
                            "tail_level": info["tail_level"], "precision": "mixed",
                            "l2": "inputs larger than L2 (268 MB load vector + 268 MB solution)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "rel_res_fp64": rel_fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "rel_res_fp64": rel_fp64, "err_vs_fp64": err_vs_fp64, "time_steps_per_s": value / d,
+                "setup_ms": round(setup_ms, 2), "direct_scan": direct, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary()}
         line.update(extra)
         print(json.dumps(line))

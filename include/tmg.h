@@ -27,7 +27,10 @@
  * coarsest solve by a parallel prefix scan over affine interval maps.  Each
  * cycle is a correction step: r = F - L u in FP64, one cycle on L c = r in
  * the cycle precision (FP64, or FP32 for TMG_MIXED), u += c in FP64.  The
- * stopping test is ||F - L u||_2 <= tol * ||F||_2 evaluated in FP64.
+ * mixed form by default keeps r between cycles as a float pair updated by
+ * r -= L c (no FP64 operation) and recomputes it from u only at the start of
+ * a solve and to confirm convergence.  The stopping test is
+ * ||F - L u||_2 <= tol * ||F||_2 with F - L u evaluated from u in FP64.
  *
  * Errors: every function returns a tmg_status; nothing aborts or exits.  A
  * failed CUDA call returns TMG_ECUDA (the CUDA error is kept, see
@@ -72,6 +75,10 @@ typedef struct {
                            smaller values move more levels to the streaming kernels */
     int use_pdl;        /* 1: programmatic dependent launch between the kernels of a cycle,
                            hiding each launch behind its predecessor's tail (default 1) */
+    int update_residual; /* TMG_MIXED: 1 = keep the level-0 residual as a float pair (about
+                           48 bits) updated by r -= L c after each cycle, recomputed from u in
+                           FP64 only at the start and to confirm convergence (default 1);
+                           0 = recompute it from u in FP64 every cycle */
 } tmg_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -176,9 +183,11 @@ tmg_status tmg_profile_cycle(tmg_plan *plan, const double *f, double u0, double 
  * Copy one of the plan's internal level vectors to host memory (inspection
  * and testing; synchronises the stream).  which: 0 = right-hand side f_l,
  * 1 = correction u_l of level l (levels 0..tail level), 2 = the level-0
- * residual r (level ignored).  The vector holds N_l*(p_t+1) values of the
- * cycle precision (8-byte double for TMG_FP64, 4-byte float for TMG_MIXED);
- * bytes must be at least that size.
+ * residual r (level ignored), 3 = the low float parts of that residual when
+ * the plan keeps it as a float pair (TMG_MIXED with update_residual; the
+ * residual is then r + low, else TMG_EINVAL).  The vector holds N_l*(p_t+1)
+ * values of the cycle precision (8-byte double for TMG_FP64, 4-byte float for
+ * TMG_MIXED; always float for 3); bytes must be at least that size.
  */
 tmg_status tmg_inspect(const tmg_plan *plan, int which, int level, void *host_dst, size_t bytes);
 

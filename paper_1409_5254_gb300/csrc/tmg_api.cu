@@ -106,6 +106,8 @@ tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, doubl
     h->done = 0;
     h->nF_from_first = nF_from_first;
     h->use_cond = use_cond;
+    h->full = 1;
+    h->rsel = 0;
     h->ticket = 0u;
     h->nscale = 1.0f;
     h->nvals = (long long)P->N * P->d;
@@ -180,6 +182,7 @@ void tmg_opts_default(tmg_opts* o) {
     o->initial_guess = 0;
     o->tail_cap = 0;
     o->use_pdl = 1;
+    o->update_residual = 1;
 }
 
 tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_t N, int levels, double omega,
@@ -273,8 +276,13 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         off_u[l] = off;
         off = align_up(off + el * P->lev[l].N * P->d, A);
     }
+    // level-0 residual; the mixed form that keeps r as a float pair updated
+    // between cycles (k_updown0) needs two buffers of high and of low parts
+    const bool updated_res = o.precision == TMG_MIXED && o.update_residual != 0 && P->lt >= 1;
     const size_t off_r = off;
-    off = align_up(off + el * N * P->d, A);
+    off = align_up(off + el * N * P->d * (updated_res ? 2 : 1), A);
+    const size_t off_rl = off;
+    if (updated_res) off = align_up(off + sizeof(float) * N * P->d * 2, A);
     const size_t off_lk = off;
     off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
     const size_t off_lk_adj = off;
@@ -300,6 +308,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         P->ul[l] = base + off_u[l];
     }
     P->rT = base + off_r;
+    P->rl = updated_res ? base + off_rl : nullptr;
     P->lk_dev = base + off_lk;
     P->lk_dev_adj = base + off_lk_adj;
     P->partials = reinterpret_cast<double*>(base + off_p);
@@ -465,17 +474,32 @@ tmg_status tmg_profile_cycle(tmg_plan* P, const double* f, double u0, double* u,
 }
 
 tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, size_t bytes) {
-    if (!P || !host_dst || which < 0 || which > 2) return TMG_EINVAL;
+    if (!P || !host_dst || which < 0 || which > 3) return TMG_EINVAL;
     const void* src = nullptr;
     int64_t n = P->N;
-    if (which == 2) {
-        src = P->rT;
+    size_t elem = P->ops->elem;
+    if (which == 2 || which == 3) {
+        // the current one of the two residual buffers of the updated form
+        int sel = 0;
+        if (P->rl != nullptr) {
+            TMG_CUDA(cudaMemcpyAsync(&P->st_host->rsel, &P->st->rsel, sizeof(int), cudaMemcpyDeviceToHost, P->s));
+            TMG_CUDA(cudaStreamSynchronize(P->s));
+            sel = P->st_host->rsel;
+        }
+        const size_t nv = (size_t)P->N * P->d;
+        if (which == 2) {
+            src = static_cast<const char*>(P->rT) + sel * nv * elem;
+        } else {
+            if (P->rl == nullptr) return TMG_EINVAL;
+            elem = sizeof(float);
+            src = static_cast<const float*>(P->rl) + sel * nv;
+        }
     } else {
         if (level < 0 || level > P->lt || (level == 0 && which == 0)) return TMG_EINVAL;
         src = which == 0 ? P->fl[level] : P->ul[level];
         n = P->lev[level].N;
     }
-    const size_t need = (size_t)n * P->d * P->ops->elem;
+    const size_t need = (size_t)n * P->d * elem;
     if (bytes < need) return TMG_EINVAL;
     TMG_CUDA(cudaMemcpyAsync(host_dst, src, need, cudaMemcpyDeviceToHost, P->s));
     TMG_CUDA(cudaStreamSynchronize(P->s));

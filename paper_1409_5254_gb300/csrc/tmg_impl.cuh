@@ -172,6 +172,10 @@ struct Impl {
         const int nl = P->nlev - P->lt;
         const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(DIR == 0 ? P->lk_dev : P->lk_dev_adj);
         T* rT = static_cast<T*>(P->rT);
+        // mixed form with the level-0 residual kept as a float pair and updated
+        // by k_updown0 (the plan allocates rl only then)
+        constexpr bool kMixed = std::is_same<T, float>::value;
+        float* rl = kMixed && P->lt >= 1 ? static_cast<float*>(P->rl) : nullptr;
         if (P->lt == 0) {
             mark();
             launch(P, k_res0<DIR, T, D>, grid_flat(P, P->N), kNT, 0, rT, P->N, R, P->partials, P->st);
@@ -191,7 +195,7 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark();
-            launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H), kNT, k_down0_smem_bytes<D>(), rT,
+            launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H), kNT, k_down0_smem_bytes<D>(), rT, rl,
                    static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
         }
         for (int l = 1; l < P->lt; ++l) {
@@ -217,6 +221,18 @@ struct Impl {
             launch(P, k_up<DIR, T, D>, grid_for(P, nch, H), kNT, 0, static_cast<const T*>(P->fl[l]),
                    static_cast<const T*>(P->ul[l + 1]), static_cast<T*>(P->ul[l]), nch, level_consts<T, D>(L(P)[l]),
                    X, nu1, nu2, H, (const DevState*)P->st);
+        }
+        if constexpr (kMixed) {
+            if (rl != nullptr) {
+                const int H = halo_lanes(sweeps_up(nu1, nu2) + 1 + sweeps_down(nu1));
+                const int64_t nch = P->N / 2;
+                mark();
+                launch(P, k_updown0<DIR, D>, grid_for(P, nch, H), kNT, 0, rT, rl, static_cast<const float*>(P->ul[1]),
+                       static_cast<float*>(P->fl[1]), nch, R, level_consts<float, D>(L(P)[0]), X, nu1, nu2, H,
+                       P->partials, P->st);
+                mark();
+                return cudaGetLastError();
+            }
         }
         {
             const int H = halo_lanes(sweeps_up(nu1, nu2));

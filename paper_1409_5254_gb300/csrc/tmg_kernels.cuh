@@ -73,6 +73,9 @@ struct DevState {
     int done;             // 0 running, 1 converged, 2 cycle limit, 3 non-finite
     int nF_from_first;    // 1: the first residual (u = 0) defines ||F||
     int use_cond;         // 1: the solve runs as a graph while-loop
+    int full;             // 1: the next level-0 down kernel evaluates r = F - L u from u in FP64
+                          //    (start of a solve; confirmation of an updated residual that met tol)
+    int rsel;             // which of the two float-pair residual buffers holds the current residual
     unsigned ticket;      // last-block ticket
     float nscale;         // power of two that brings the residual near 1 (FP32 norm)
     long long nvals;      // values per residual vector, N * D
@@ -435,16 +438,32 @@ __device__ __forceinline__ void acc_add(float& s, float& c, float th, float tl) 
     c += err + tl;
 }
 
+// a + b = hi + lo exactly (Knuth's two-sum).
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = a + b;
+    const float bp = s - a;
+    return ff{s, (a - (s - bp)) + (b - bp)};
+}
+
+// (s, c) += t for a single float term.
+__device__ __forceinline__ void acc_add1(float& s, float& c, float t) {
+    const ff n = two_sum(s, t);
+    s = n.hi;
+    c += n.lo;
+}
+
 // float -> double by re-biasing the exponent with integer operations (exact;
 // the conversion instruction would occupy GB300's FP64 pipe).  Subnormal
-// floats (|c| < 2^-126) become 0.
+// floats (|c| < 2^-126) become +-0; Inf stays Inf and NaN stays NaN.
 __device__ __forceinline__ double f2d_int(float c) {
     const unsigned b = __float_as_uint(c);
     const unsigned e = (b >> 23) & 0xFFu;
     const unsigned sign = b & 0x80000000u;
-    const unsigned hi = sign | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-    const unsigned lo = (b & 0x7u) << 29;
-    return (e == 0u) ? 0.0 : (e == 0xFFu ? (double)c : __hiloint2double((int)hi, (int)lo));
+    const unsigned m = b & 0x7FFFFFu;
+    const unsigned ed = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
+    const unsigned mh = e == 0u ? 0u : ((m >> 3) | (e == 0xFFu && m != 0u ? 0x80000u : 0u));
+    const unsigned lo = e == 0u ? 0u : (m & 0x7u) << 29;
+    return __hiloint2double((int)(sign | (ed << 20) | mh), (int)lo);
 }
 
 // Product of two float pairs (lo*lo dropped), as an unnormalised pair.
@@ -483,7 +502,8 @@ __device__ __forceinline__ void small_sums(const double (&u)[D], ff (&us)[D], ff
 // DIR = 1: r[k] = F[k] + (d + spB) - snE + 2 T_k - z/(2k+1) u[k]  (T_k as in residual0)
 template <int DIR, int D>
 __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double (&u)[D], const ff (&us)[D],
-                                             double up0, ff spB, ff snE, const Res0& R, float (&r)[D]) {
+                                             double up0, ff spB, ff snE, const Res0& R, float (&r)[D],
+                                             float (&rlo)[D]) {
     const ff d = split_d(up0 - u[0]);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -501,8 +521,69 @@ __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double 
         }
         const ff zu = mul_ff(R.zm_hi[k], R.zm_lo[k], us[k]);
         acc_add(s, c, -zu.hi, -zu.lo);
-        r[k] = s + c;
+        const ff n = two_sum(s, c);
+        r[k] = n.hi;
+        rlo[k] = n.lo;
     }
+}
+
+// Same, rounded to one float per value.
+template <int DIR, int D>
+__device__ __forceinline__ void residual0_ff(const double (&F)[D], const double (&u)[D], const ff (&us)[D],
+                                             double up0, ff spB, ff snE, const Res0& R, float (&r)[D]) {
+    float lo[D];
+    residual0_ff<DIR, D>(F, u, us, up0, spB, snE, R, r, lo);
+}
+
+// Residual of the correction equation L c = r at a float correction c, as a
+// float pair: (rh, rl) <- r + a ep - A c, where ep = b^T c_{n-1} (a float
+// pair) and A c uses the Legendre structure of the stiffness block (see
+// residual0).  Each float term (sums of c, 2 c[l], the pair product
+// z/(2k+1) c[k]) enters a compensated sum, so the result carries ~2^-48 of
+// the terms' size -- the residual of an FP64 iterate is updated without an
+// FP64 operation.
+template <int DIR, int D>
+__device__ __forceinline__ void residual_update_ff(float (&rh)[D], float (&rl)[D], const float (&c)[D], ff ep,
+                                                   const Res0& R) {
+    ff E{c[0], 0.f};                       // 1^T c
+#pragma unroll
+    for (int l = 1; l < D; ++l) {
+        const ff t = two_sum(E.hi, c[l]);
+        E.hi = t.hi;
+        E.lo += t.lo;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float s = rh[k], e = rl[k];
+        const float sg = (DIR == 0 && (k & 1)) ? -1.f : 1.f;
+        acc_add(s, e, sg * ep.hi, sg * ep.lo);
+        acc_add(s, e, -E.hi, -E.lo);
+        if constexpr (DIR == 0) {
+#pragma unroll
+            for (int l = k - 1; l >= 0; l -= 2) acc_add1(s, e, 2.f * c[l]);
+        } else {
+#pragma unroll
+            for (int l = k + 1; l < D; l += 2) acc_add1(s, e, 2.f * c[l]);
+        }
+        const ff zu = mul_ff(R.zm_hi[k], R.zm_lo[k], ff{c[k], 0.f});
+        acc_add(s, e, -zu.hi, -zu.lo);
+        const ff n = two_sum(s, e);
+        rh[k] = n.hi;
+        rl[k] = n.lo;
+    }
+}
+
+// b^T c of a float vector as a float pair.
+template <int DIR, int D>
+__device__ __forceinline__ ff bsum_ff(const float (&c)[D]) {
+    ff b{c[0], 0.f};
+#pragma unroll
+    for (int l = 1; l < D; ++l) {
+        const ff t = two_sum(b.hi, (DIR == 1 && (l & 1)) ? -c[l] : c[l]);
+        b.hi = t.hi;
+        b.lo += t.lo;
+    }
+    return b;
 }
 
 // ------------------------------------------------- norm and stopping test --
@@ -515,10 +596,20 @@ __device__ __forceinline__ bool cycle_finished(const DevState* st) {
     return true;
 }
 
-__device__ __forceinline__ void finalize_state(DevState* st, double ss) {
-    const int k = st->cycle;
+// How a residual norm enters the solve state.
+//   kFinPlain: the residual of the current iterate, from u (one per cycle).
+//   kFinFull: the same where level 0 keeps an updated residual: at the start
+//     of a solve a new entry; later a confirmation of the updated residual of
+//     the same iterate (it replaces that entry; the solve stops only here).
+//   kFinUpdated: the updated residual of the new iterate; meeting tol asks
+//     for a confirmation from u instead of stopping.
+enum : int { kFinPlain = 0, kFinFull = 1, kFinUpdated = 2 };
+
+__device__ __forceinline__ void finalize_state(DevState* st, double ss, int mode) {
+    const bool confirm = mode == kFinFull && st->cycle > 0;
+    const int k = confirm ? st->cycle - 1 : st->cycle;
     const double nrm = sqrt(ss);
-    if (k == 0 && st->nF_from_first) st->nF = nrm;
+    if (k == 0 && !confirm && st->nF_from_first) st->nF = nrm;
     const double rel = st->nF > 0.0 ? nrm / st->nF : nrm;
     st->hist[k < kHist ? k : kHist - 1] = rel;
     // scale for the next FP32 norm: 2^-round(log2(rms)), kept well inside FP32 range
@@ -529,9 +620,14 @@ __device__ __forceinline__ void finalize_state(DevState* st, double ss) {
     st->nscale = ldexpf(1.0f, ex);
     int done = 0;
     if (!(rel == rel) || rel > 1.0e300) done = 3;
-    else if (rel <= st->tol) done = 1;
+    else if (rel <= st->tol) done = mode == kFinUpdated ? 0 : 1;
     else if (k >= st->max_cycles) done = 2;
-    st->cycle = k + 1;
+    if (mode == kFinFull) st->full = 0;
+    if (mode == kFinUpdated) {
+        st->rsel ^= 1;      // the kernel wrote the other buffer
+        if (done == 0 && rel <= st->tol) st->full = 1;
+    }
+    if (!confirm) st->cycle = k + 1;
     st->done = done;
     if (done && st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
 }
@@ -539,7 +635,8 @@ __device__ __forceinline__ void finalize_state(DevState* st, double ss) {
 // Deterministic grid sum of ss: block partials in a fixed order, reduced by
 // the last block to finish (ticket), which then applies the stopping test.
 template <int NT>
-__device__ __forceinline__ void grid_norm_finalize(double ss, double* __restrict__ partials, DevState* st) {
+__device__ __forceinline__ void grid_norm_finalize(double ss, double* __restrict__ partials, DevState* st,
+                                                   int mode = kFinPlain) {
     __shared__ double red[NT / 32];
     __shared__ int last;
 #pragma unroll
@@ -569,7 +666,7 @@ __device__ __forceinline__ void grid_norm_finalize(double ss, double* __restrict
         double tot = 0.0;
         for (int i = 0; i < NT / 32; ++i) tot += red[i];
         st->ticket = 0u;
-        finalize_state(st, tot);
+        finalize_state(st, tot, mode);
     }
 }
 
@@ -640,7 +737,8 @@ constexpr size_t k_down0_smem_bytes() {
 // time (FP64 squares in the first cycle, scaled FP32 squares afterwards) so
 // that no branch between the two sits inside the loop.
 template <bool FP64NORM, int DIR, typename T, int D>
-__device__ __forceinline__ double down0_loop(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks,
+__device__ __forceinline__ double down0_loop(T* __restrict__ rT, float* __restrict__ rlo, T* __restrict__ fc,
+                                             int64_t nchunks,
                                              const Res0& R, const LevelK<T, D>& K, const Xfer<T, D>& X, int nu1,
                                              int H, const DevState* st) {
     const double* __restrict__ F = st->F;
@@ -693,6 +791,7 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, T* __restrict__
             Fv[1][k] = Fvf[D + k];
         }
         T rt[2][D];
+        float rtl[2][D];     // low parts of the float-pair residual (mixed form)
         if constexpr (kMixed) {
             ff us0[D], us1[D], sE0, sB0, sE1, sB1;
             small_sums<DIR, D>(uv[0], us0, sE0, sB0);
@@ -705,13 +804,15 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, T* __restrict__
             }
             const double up0 = shfl_prev(h0);
             const ff sp{shfl_prev(hB.hi), shfl_prev(hB.lo)};
-            float r0[D], r1[D];
-            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0);
-            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1);
+            float r0[D], r1[D], l0[D], l1[D];
+            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0, l0);
+            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1, l1);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 rt[0][k] = inb ? r0[k] : 0.f;
                 rt[1][k] = inb ? r1[k] : 0.f;
+                rtl[0][k] = l0[k];
+                rtl[1][k] = l1[k];
             }
         } else {
             double r[2][D];
@@ -743,6 +844,9 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, T* __restrict__
                     }
                 }
             store_pair<T, D>(rT, q, rt);
+            if constexpr (kMixed) {
+                if (rlo != nullptr) store_pair<float, D>(rlo, q, rtl);
+            }
         }
         if (fc != nullptr) {
             T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
@@ -757,19 +861,31 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, T* __restrict__
     return ss;
 }
 
+//
+// With rlo != nullptr (mixed form with an updated residual) the residual is
+// stored as a float pair (rT, rlo) into buffer st->rsel of two (each nchunks
+// * 2 * D floats) and the kernel runs only when st->full is set: at the start
+// of a solve, and to confirm an updated residual that met the tolerance; in
+// every other cycle k_updown0 has done its work.
 template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, Res0 R,
-                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
-                                               double* __restrict__ partials, DevState* st) {
+__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, float* __restrict__ rlo, T* __restrict__ fc,
+                                               int64_t nchunks, Res0 R, LevelK<T, D> K, Xfer<T, D> X, int nu1,
+                                               int H, double* __restrict__ partials, DevState* st) {
     pdl_enter();
     if (cycle_finished(st)) return;
+    if (rlo != nullptr) {
+        if (!st->full) return;
+        const int64_t nv = nchunks * 2 * D;
+        rT += st->rsel * nv;
+        rlo += st->rsel * nv;
+    }
     constexpr bool kMixed = std::is_same<T, float>::value;
     // FP32 norm with a power-of-two scale, except in the first cycle whose
     // residual magnitude is not known yet (FP64 then)
     double ss;
-    if (!kMixed || st->cycle == 0) ss = down0_loop<true, DIR, T, D>(rT, fc, nchunks, R, K, X, nu1, H, st);
-    else ss = down0_loop<false, DIR, T, D>(rT, fc, nchunks, R, K, X, nu1, H, st);
-    grid_norm_finalize<kNT>(ss, partials, st);
+    if (!kMixed || st->cycle == 0) ss = down0_loop<true, DIR, T, D>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
+    else ss = down0_loop<false, DIR, T, D>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
+    grid_norm_finalize<kNT>(ss, partials, st, rlo != nullptr ? kFinFull : kFinPlain);
 }
 
 // Level 0 on the way up: recompute the pre-smoothed correction from r, add
@@ -808,6 +924,97 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
             store_pair<double, D>(uu, q, uv);
         }
     }
+}
+
+// Level 0 of the mixed form between two cycles: the way up of one cycle
+// fused with the way down of the next, with the level-0 residual updated
+// instead of recomputed from u.  The residual is kept as a float pair
+// (rh, rl), about 48 significant bits.  Per coarse pair: recompute the
+// pre-smoothed correction from rh, add the prolongated level-1 correction,
+// post-smooth (this cycle's correction c); u += c in FP64; (rh, rl) <- r - L c
+// (residual_update_ff), whose norm feeds the stopping test; then the
+// zero-start pre-smoothing, residual and restriction of the next cycle's
+// correction equation L c' = rh write the level-1 right-hand side.
+//
+// Sweeps that read the previous interval: those of k_up0, one for L c, and
+// those of k_down's part, so H = ceil(S/2) with S = sweeps_up + 1 + sweeps_down.
+// The updated residual differs from F - L u by the FP64 rounding of u += c
+// and ~2^-48 of each update's terms; before the solve stops on it, k_down0
+// recomputes it from u in FP64 (st->full).
+//
+// The residual is read from buffer st->rsel and written to the other one:
+// the halo lanes of a tile read pairs that another warp owns and updates, so
+// an in-place update would race.  rh and rl each hold two buffers of
+// nchunks * 2 * D floats.
+template <int DIR, int D>
+__global__ void __launch_bounds__(kNT) k_updown0(float* __restrict__ rh, float* __restrict__ rl,
+                                                 const float* __restrict__ uc, float* __restrict__ fc,
+                                                 int64_t nchunks, Res0 R, LevelK<float, D> K, Xfer<float, D> X,
+                                                 int nu1, int nu2, int H, double* __restrict__ partials,
+                                                 DevState* st) {
+    pdl_enter();
+    if (st->done) return;
+    double* __restrict__ uu = st->u;
+    const float nsc = st->nscale;
+    const int64_t nv = nchunks * 2 * D;
+    const int sel = st->rsel;
+    const float* __restrict__ rh_in = rh + sel * nv;
+    const float* __restrict__ rl_in = rl + sel * nv;
+    float* __restrict__ rh_out = rh + (1 - sel) * nv;
+    float* __restrict__ rl_out = rl + (1 - sel) * nv;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    float ssf = 0.f;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const bool own = inb && lane >= H;
+        float r[2][D], rlo[2][D], cc[D];
+        double uv[2][D];
+        load_pair<float, D>(rh_in, q, inb, r);
+        load_pair<float, D>(rl_in, q, inb, rlo);
+        load_one<float, D>(uc, q, inb, cc);
+        load_pair<double, D>(uu, q, own, uv);      // issued early: its latency overlaps the sweeps
+        float h[2][D], c[2][D], w[2][D];
+        presmooth_zero<DIR, float, D>(K, r, h, c, w, nu1);
+        prolong_add<float, D>(X, cc, c);
+        postsmooth<DIR, float, D>(K, h, c, nu2);
+        if (!inb) {                                 // the correction is zero outside the array
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) c[i][k] = 0.f;
+        }
+        // r <- r - L c
+        const ff b0 = bsum_ff<DIR, D>(c[0]);
+        const ff b1 = bsum_ff<DIR, D>(c[1]);
+        const ff bp{shfl_prev(b1.hi), shfl_prev(b1.lo)};
+        residual_update_ff<DIR, D>(r[0], rlo[0], c[0], bp, R);
+        residual_update_ff<DIR, D>(r[1], rlo[1], c[1], b0, R);
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    uv[i][k] += f2d_int(c[i][k]);
+                    const float v = r[i][k] * nsc;
+                    ssf = fmaf(v, v, ssf);
+                }
+            store_pair<double, D>(uu, q, uv);
+            store_pair<float, D>(rh_out, q, r);
+            store_pair<float, D>(rl_out, q, rlo);
+        }
+        // the next cycle's way down on L c' = rh
+        float rc[2][D], out[D];
+        presmooth_zero<DIR, float, D>(K, r, h, c, w, nu1);
+        residual_tracked<DIR, float, D>(r, c, w, rc);
+        restrict_pair<float, D>(X, rc, out);
+        if (own) VecIO<float, D>::store(fc + q * D, out);
+    }
+    const double ss = (double)ssf / ((double)nsc * (double)nsc);
+    grid_norm_finalize<kNT>(ss, partials, st, kFinUpdated);
 }
 
 // Level 0 residual only, one interval per thread (any N): used when the

@@ -54,6 +54,7 @@ struct tmg_plan {
     void* fl[tmg::kMaxLevels];   // level right-hand sides (cycle precision)
     void* ul[tmg::kMaxLevels];   // level corrections
     void* rT;                    // level-0 residual (cycle precision)
+    void* rl;                    // its low float parts (mixed form with an updated residual), else nullptr
     void* lk_dev;                // tail level constants of L
     void* lk_dev_adj;            // ... and of L^T in reversed time
     double* adj_buf;             // reversed g and reversed mu (adjoint solves, allocated on first use)

@@ -32,7 +32,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
                 ("n_min", ctypes.c_int64), ("use_graph", ctypes.c_int), ("initial_guess", ctypes.c_int),
-                ("tail_cap", ctypes.c_int64), ("use_pdl", ctypes.c_int)]
+                ("tail_cap", ctypes.c_int64), ("use_pdl", ctypes.c_int), ("update_residual", ctypes.c_int)]
 
 
 _LIB = None
@@ -128,7 +128,7 @@ class Plan:
     def __init__(self, p: int, tau: float, lam: float, N: int, levels: int = 0, omega: float = 0.0, *,
                  tol: float = 1e-10, max_cycles: int = 100, nu1: int = 1, nu2: int = 1, gamma: int = 1,
                  precision="mixed", n_min: int = 64, use_graph: bool = True, initial_guess: bool = False,
-                 tail_cap: int = 0, use_pdl: bool = True, stream=None):
+                 tail_cap: int = 0, use_pdl: bool = True, update_residual: bool = True, stream=None):
         L = _lib()
         o = _Opts()
         L.tmg_opts_default(ctypes.byref(o))
@@ -137,6 +137,7 @@ class Plan:
         o.n_min, o.use_graph, o.initial_guess = n_min, int(use_graph), int(initial_guess)
         o.tail_cap = tail_cap
         o.use_pdl = int(use_pdl)
+        o.update_residual = int(update_residual)
         self.precision = _PREC[precision]
         self.p, self.d, self.N = p, p + 1, N
         self.tau, self.lam = tau, lam
@@ -230,10 +231,11 @@ class Plan:
         return dict(zip(["down0", "down_levels", "coarse_on_chip", "up_levels", "up0", "cycle"], ms.tolist()))
 
     def inspect(self, which: str, level: int = 0) -> np.ndarray:
-        """Copy an internal level vector ('f', 'u' of a level, or the level-0 residual 'r') to host."""
-        w = {"f": 0, "u": 1, "r": 2}[which]
-        n = self.N if w == 2 else self.N >> level
-        dt = np.float64 if self.precision == FP64 else np.float32
+        """Copy an internal level vector ('f', 'u' of a level, the level-0 residual 'r', or the low
+        float parts 'rlo' of a residual kept as a float pair) to host."""
+        w = {"f": 0, "u": 1, "r": 2, "rlo": 3}[which]
+        n = self.N if w >= 2 else self.N >> level
+        dt = np.float64 if self.precision == FP64 and w != 3 else np.float32
         out = np.empty((n, self.d), dtype=dt)
         _check(_lib().tmg_inspect(self._h, w, level, ctypes.c_void_p(out.ctypes.data), out.nbytes), "tmg_inspect")
         return out

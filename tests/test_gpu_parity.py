@@ -287,3 +287,99 @@ def test_single_level_large_problem_uses_scan(dev, prec):
     assert st.cycles <= (2 if prec == "fp64" else 6)
     assert rel_residual(p, z, prob["F"], 1.0, u) <= 1.05e-10
 
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("zscale", [1e-3, 1.0, 1e3])
+def test_updated_residual_matches_fp64_residual(dev, p, zscale):
+    """Mixed form: after one cycle the level-0 residual kept as a float pair
+    (r + low, updated by r -= L c without FP64 arithmetic) equals F - L u of
+    the FP64 iterate, evaluated by the oracle.  The pair carries ~2^-48 of the
+    update's terms, |L| |c| with c ~ u after the first cycle, and u += c
+    rounds u in FP64: allowance 1e-13 (|r| + |L| |u|) per component, with
+    |L| |u| bounded by (2 + z) max|u| (Legendre blocks: |K| entries <= 1,
+    d <= 4 terms, plus the coupling)."""
+    N = 4096 + 64
+    T = 1.0
+    lam = zscale * N / T
+    prob = inputs.scalar_problem(20 + p, N, p, lam=lam, T=T, u0=0.7)
+    z = lam * prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, prob["tau"], lam, N, precision="mixed", tail_cap=256) as plan:
+        assert plan.info()["tail_level"] >= 1
+        u = torch.zeros_like(Fd)
+        for k in range(3):
+            plan.cycle(Fd, prob["u0"], u)
+            uh = u.cpu().numpy()
+            r_pair = plan.inspect("r").astype(np.float64) + plan.inspect("rlo").astype(np.float64)
+            r_ex = O.residual(p, z, prob["F"], prob["u0"], uh)
+            scale = np.abs(r_ex).max() + (2 + z) * (p + 1) * np.abs(uh).max()
+            err = np.abs(r_pair - r_ex).max()
+            print(f"p={p} z={z:.1e} cycle {k + 1}: |r|={np.abs(r_ex).max():.2e} pair err={err:.2e}")
+            assert err <= 1e-13 * scale, (err, scale)
+
+
+@pytest.mark.parametrize("p", [1, 3])
+def test_updated_residual_over_several_cycles_at_multi_tile_size(dev, p):
+    """The same comparison after 6 cycles that each update the residual of
+    the previous one (no recomputation from u: tol = 0, max_cycles = 6), at a
+    size where every warp of the level-0 kernel processes several tiles
+    (2^21 + 64 intervals): the halo lanes of a tile then read pairs that other
+    warps update in the same launch.  The allowance adds up the per-cycle
+    rounding of the update and of u += c: 6 x 1e-13 (|r| + |L| |u|)."""
+    N = (1 << 21) + 64
+    prob = inputs.scalar_problem(40 + p, N, p, lam=1.0, tau=1e-6, u0=1.0)
+    z = prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, prob["tau"], 1.0, N, precision="mixed", tol=0.0, max_cycles=6) as plan:
+        u = plan.solve(Fd, prob["u0"], allow_notconv=True)
+        assert plan.stats().cycles == 6
+        uh = u.cpu().numpy()
+        r_pair = plan.inspect("r").astype(np.float64) + plan.inspect("rlo").astype(np.float64)
+    r_ex = O.residual(p, z, prob["F"], prob["u0"], uh)
+    scale = np.abs(r_ex).max() + (2 + z) * (p + 1) * np.abs(uh).max()
+    err = np.abs(r_pair - r_ex).max()
+    print(f"p={p} N={N}: |r|={np.abs(r_ex).max():.2e} pair err after 6 cycles={err:.2e}")
+    assert err <= 6e-13 * scale, (err, scale)
+
+
+@pytest.mark.parametrize("p", [0, 1, 3])
+def test_updated_and_recomputed_residual_forms_agree(dev, p):
+    """The two mixed forms (residual updated between cycles, or recomputed
+    from u in FP64 every cycle) take the same number of cycles up to one, both
+    meet the tolerance, and their solutions differ by no more than the
+    tolerance allows: cond(L) ~ 2/z times 1e-10 relative (z = 0.05 here)."""
+    N = 1 << 14
+    lam = 0.05 * N
+    prob = inputs.scalar_problem(30 + p, N, p, lam=lam, T=1.0, u0=1.0)
+    z = lam * prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    res = {}
+    for upd in (True, False):
+        with tmg().Plan(p, prob["tau"], lam, N, precision="mixed", update_residual=upd, max_cycles=300) as plan:
+            u = plan.solve(Fd, prob["u0"]).cpu().numpy()
+            res[upd] = (u, plan.stats())
+        assert rel_residual(p, z, prob["F"], prob["u0"], u) <= 1.05e-10
+    (u1, s1), (u0_, s0) = res[True], res[False]
+    print(f"p={p}: cycles updated={s1.cycles} recomputed={s0.cycles} diff={rel_err(u1, u0_):.2e}")
+    assert abs(s1.cycles - s0.cycles) <= 1
+    assert rel_err(u1, u0_) <= 2.0 / z * 1e-10 * 4
+    # the solve stops on a residual confirmed from u: the reported value is the
+    # FP64 residual of the returned u (FP32 norm: 1e-4 relative)
+    assert s1.rel_res == pytest.approx(rel_residual(p, z, prob["F"], prob["u0"], u1), rel=1e-4)
+
+
+def test_confirmation_rejects_an_updated_residual_below_the_fp64_floor(dev):
+    """A tolerance below what FP64 can confirm: the updated residual may drop
+    under it, but the FP64 residual from u cannot, so the solve must run to
+    max_cycles and report TMG_ENOTCONV instead of stopping early."""
+    N, p = 1 << 13, 1
+    prob = inputs.scalar_problem(7, N, p, lam=1.0, T=1.0, u0=1.0)
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    T_ = tmg()
+    with T_.Plan(p, prob["tau"], 1.0, N, precision="mixed", tol=1e-19, max_cycles=40) as plan:
+        u = plan.solve(Fd, prob["u0"], allow_notconv=True)
+        assert plan.last_status == T_.TMG_ENOTCONV
+        st = plan.stats()
+    assert st.cycles == 40
+    assert rel_residual(p, prob["tau"], prob["F"], prob["u0"], u.cpu().numpy()) <= 1e-12
