@@ -96,23 +96,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cycle_bytes(N: int, d: int, elem: int, lt: int):
-    """Algorithmic HBM bytes of one correction cycle and of its two level-0 kernels.
+def cycle_bytes(N: int, d: int, lt: int):
+    """Algorithmic HBM bytes of the mixed-precision solve's kernels (FP32 cycle).
 
-    Level 0 down: read u, F (FP64), write r (elem) and the level-1 RHS (N/2 x elem).
-    Level 0 up: read r, level-1 correction, u; write u.  Level l >= 1 below the
-    on-chip solver: down reads f_l, writes f_{l+1}; up reads f_l and u_{l+1},
-    writes u_l.  The on-chip solver reads f_lt and writes u_lt once.
+    Start of a solve (k_down0, once, and again only to confirm convergence):
+    read u, F (FP64), write the float-pair residual (8 B per value) and the
+    level-1 right-hand side (N/2 intervals, FP32): 26 B/DoF.
+    Every cycle, level 0 (k_updown0): read the residual pair, the level-1
+    correction and u; write u, the new residual pair and the next level-1
+    right-hand side: 8 + 2 + 8 + 8 + 8 + 2 = 36 B/DoF.
+    Level l >= 1 below the on-chip solver: down reads f_l, writes f_{l+1};
+    up reads f_l and u_{l+1}, writes u_l (FP32).  The on-chip solver reads
+    f_lt and writes u_lt once.
     """
     nd = N * d
-    down0 = nd * (8 + 8 + elem) + (N // 2) * d * elem
-    up0 = nd * (elem + 8 + 8) + (N // 2) * d * elem
+    half = (N // 2) * d * 4
+    down0 = nd * (8 + 8 + 8) + half
+    updown0 = nd * (8 + 8 + 8 + 8) + 2 * half
     coarse = 0
     for l in range(1, lt):
         nl = (N >> l) * d
-        coarse += (nl + nl // 2) * elem + (nl + nl // 2 + nl) * elem
-    tail_io = 2 * (N >> lt) * d * elem if lt > 0 else 0
-    return {"down0": down0, "up0": up0, "cycle": down0 + up0 + coarse + tail_io}
+        coarse += (nl + nl // 2) * 4 + (nl + nl // 2 + nl) * 4
+    tail_io = 2 * (N >> lt) * d * 4 if lt > 0 else 0
+    return {"down0": down0, "updown0": updown0, "cycle": updown0 + coarse + tail_io}
 
 
 def time_solves(plan, F, u, steps: int, stream, torch):
@@ -208,18 +214,26 @@ def run_ours(args):
               "note": "exact parallel-scan solve (not multigrid), same problem and stream"}
     del u_ex
 
-    # per-kernel times of one cycle (events on the plan's stream) and the roofline
+    # per-kernel times of one cycle (events on the plan's stream) and the
+    # roofline of the dominant kernel, k_updown0 (the level-0 kernel of every
+    # cycle; k_down0 runs once per solve, plus once to confirm convergence)
     prof = plan.profile_cycle(F, U0, u.clone(), reps=20)
-    cb = cycle_bytes(N_FULL, d, 4, info["tail_level"])
-    dom = "down0" if prof["down0"] >= prof["up0"] else "up0"
-    achieved = cb[dom] / (prof[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_down0" if dom == "down0" else "k_up0", "achieved": round(achieved, 1),
+    cb = cycle_bytes(N_FULL, d, info["tail_level"])
+    t_dom = prof["up0"]
+    achieved = cb["updown0"] / (t_dom * 1e-3) / 1e9
+    steady_ms = prof["cycle"] - prof["down0"]
+    roofline = {"bound": "hbm", "kernel": "k_updown0", "achieved": round(achieved, 1),
                 "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                 "traffic": args.traffic if args.traffic else None,
-                "bytes_per_launch": cb[dom], "launch_ms": round(prof[dom], 5),
-                "cycle_bytes": cb["cycle"], "cycle_ms": round(prof["cycle"], 5),
-                "cycle_frac": round(cb["cycle"] / (prof["cycle"] * 1e-3) / 1e9 / hbm_peak, 4),
-                "kernel_ms": {k: round(v, 5) for k, v in prof.items()}}
+                "bytes_per_launch": cb["updown0"], "launch_ms": round(t_dom, 5), "launches_per_solve": st.cycles,
+                "cycle_bytes": cb["cycle"], "cycle_ms": round(steady_ms, 5),
+                "cycle_frac": round(cb["cycle"] / (steady_ms * 1e-3) / 1e9 / hbm_peak, 4),
+                "solve_ms_per_cycle": round(ms / max(st.cycles, 1), 5),
+                "kernel_ms": {"down0_once_per_solve": round(prof["down0"], 5),
+                              "down_levels": round(prof["down_levels"], 5),
+                              "coarse_on_chip": round(prof["coarse_on_chip"], 5),
+                              "up_levels": round(prof["up_levels"], 5), "updown0": round(prof["up0"], 5),
+                              "cycle_events": round(prof["cycle"], 5)}}
 
     kernels_per_cycle = 3 if info["tail_level"] == 0 else 2 * info["tail_level"] + 1
     launches = args.steps * (st.cycles + 1) * kernels_per_cycle

@@ -50,11 +50,24 @@ inline int halo_lanes(int S) { return (S + 1) / 2; }
 inline int sweeps_down(int nu1) { return (nu1 > 0 ? nu1 - 1 : 0) + 1; }
 inline int sweeps_up(int nu1, int nu2) { return (nu1 > 0 ? nu1 - 1 : 0) + nu2; }
 
-inline int grid_for(const tmg_plan* P, int64_t nchunks, int H) {
+// Blocks of kNT threads of a kernel that are resident on one SM at once.
+template <typename Kern>
+inline int resident_per_sm(Kern kernel, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kNT, smem) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+// Grid of a warp-tile streaming kernel: one warp per tile up to one full
+// wave of resident blocks (SMs x resident blocks per SM); larger levels loop
+// over their tiles with that persistent grid, so no partial last wave leaves
+// SMs idle.
+inline int grid_for(const tmg_plan* P, int64_t nchunks, int H, int resident) {
     const int64_t per = 32 - H;
     const int64_t tiles = (nchunks + per - 1) / per;
     int64_t blocks = (tiles + (kNT / 32) - 1) / (kNT / 32);
-    if (blocks > P->max_blocks) blocks = P->max_blocks;
+    const int64_t wave = (int64_t)P->nsm * resident;
+    if (blocks > wave) blocks = wave;
     if (blocks < 1) blocks = 1;
     return (int)blocks;
 }
@@ -195,14 +208,16 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark();
-            launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H), kNT, k_down0_smem_bytes<D>(), rT, rl,
+            static const int occ = resident_per_sm(k_down0<DIR, T, D>, k_down0_smem_bytes<D>());
+            launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, k_down0_smem_bytes<D>(), rT, rl,
                    static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
         }
         for (int l = 1; l < P->lt; ++l) {
             const int H = halo_lanes(sweeps_down(nu1));
             const int64_t nch = P->lev[l].N / 2;
             mark();
-            launch(P, k_down<DIR, T, D>, grid_for(P, nch, H), kNT, 0, static_cast<const T*>(P->fl[l]),
+            static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
+            launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                    static_cast<T*>(P->fl[l + 1]), nch, level_consts<T, D>(L(P)[l]), X, nu1, H,
                    (const DevState*)P->st);
         }
@@ -218,7 +233,8 @@ struct Impl {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->lev[l].N / 2;
             mark();
-            launch(P, k_up<DIR, T, D>, grid_for(P, nch, H), kNT, 0, static_cast<const T*>(P->fl[l]),
+            static const int occ = resident_per_sm(k_up<DIR, T, D>, 0);
+            launch(P, k_up<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                    static_cast<const T*>(P->ul[l + 1]), static_cast<T*>(P->ul[l]), nch, level_consts<T, D>(L(P)[l]),
                    X, nu1, nu2, H, (const DevState*)P->st);
         }
@@ -227,7 +243,8 @@ struct Impl {
                 const int H = halo_lanes(sweeps_up(nu1, nu2) + 1 + sweeps_down(nu1));
                 const int64_t nch = P->N / 2;
                 mark();
-                launch(P, k_updown0<DIR, D>, grid_for(P, nch, H), kNT, 0, rT, rl, static_cast<const float*>(P->ul[1]),
+                static const int occ = resident_per_sm(k_updown0<DIR, D>, 0);
+                launch(P, k_updown0<DIR, D>, grid_for(P, nch, H, occ), kNT, 0, rT, rl, static_cast<const float*>(P->ul[1]),
                        static_cast<float*>(P->fl[1]), nch, R, level_consts<float, D>(L(P)[0]), X, nu1, nu2, H,
                        P->partials, P->st);
                 mark();
@@ -238,7 +255,8 @@ struct Impl {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->N / 2;
             mark();
-            launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H), kNT, 0, (const T*)rT, static_cast<const T*>(P->ul[1]),
+            static const int occ = resident_per_sm(k_up0<DIR, T, D>, 0);
+            launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, (const T*)rT, static_cast<const T*>(P->ul[1]),
                    nch, level_consts<T, D>(L(P)[0]), X, nu1, nu2, H, (const DevState*)P->st);
         }
         mark();

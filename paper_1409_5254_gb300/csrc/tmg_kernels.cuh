@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
 // an in-place update would race.  rh and rl each hold two buffers of
 // nchunks * 2 * D floats.
 template <int DIR, int D>
-__global__ void __launch_bounds__(kNT) k_updown0(float* __restrict__ rh, float* __restrict__ rl,
+__global__ void __launch_bounds__(kNT, D <= 2 ? 4 : 2) k_updown0(float* __restrict__ rh, float* __restrict__ rl,
                                                  const float* __restrict__ uc, float* __restrict__ fc,
                                                  int64_t nchunks, Res0 R, LevelK<float, D> K, Xfer<float, D> X,
                                                  int nu1, int nu2, int H, double* __restrict__ partials,
