@@ -79,6 +79,10 @@ typedef struct {
                            48 bits) updated by r -= L c after each cycle, recomputed from u in
                            FP64 only at the start and to confirm convergence (default 1);
                            0 = recompute it from u in FP64 every cycle */
+    int fuse_levels;    /* 1: the streaming levels l >= 1 run two per kernel (levels l and
+                           l+1 on the way down and up, level l+1 never stored; the way up
+                           recomputes level l+1's right-hand side); 0: one level per
+                           kernel; -1 (default): fuse when the cycle precision is FP32 */
 } tmg_opts;
 
 /* Fill *opts with the defaults listed above. */

@@ -183,6 +183,7 @@ void tmg_opts_default(tmg_opts* o) {
     o->tail_cap = 0;
     o->use_pdl = 1;
     o->update_residual = 1;
+    o->fuse_levels = -1;
 }
 
 tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_t N, int levels, double omega,
@@ -437,34 +438,29 @@ tmg_status tmg_plan_info(const tmg_plan* P, int* num_levels, int* tail_level, in
 tmg_status tmg_profile_cycle(tmg_plan* P, const double* f, double u0, double* u, int reps, double* ms, int n_ms) {
     if (!P || reps < 1 || !ms || n_ms < 6 || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK)
         return TMG_EINVAL;
-    const int nk = P->lt == 0 ? 3 : 2 * P->lt + 1;    // kernels per cycle
-    std::vector<cudaEvent_t> ev(nk + 1);
+    const int max_ev = 2 * P->nlev + 4;    // kernel groups per cycle + 1
+    std::vector<cudaEvent_t> ev(max_ev);
+    std::vector<int> cat(max_ev, -1);
     for (auto& e : ev) TMG_CUDA(cudaEventCreate(&e));
     double acc[6] = {0, 0, 0, 0, 0, 0};
     tmg_status status = TMG_OK;
     for (int r = 0; r < reps && status == TMG_OK; ++r) {
         status = stage_state(P, f, u0, u, -1.0, 1 << 30, 0, 1);
         if (status != TMG_OK) break;
-        cudaError_t e = P->ops->enqueue_cycle_timed(P, ev.data());
+        int nev = 0;
+        cudaError_t e = P->ops->enqueue_cycle_timed(P, ev.data(), cat.data(), &nev);
         if (e == cudaSuccess) e = cudaStreamSynchronize(P->s);
         if (e != cudaSuccess) {
             status = cuda_fail(e);
             break;
         }
-        std::vector<float> t(nk);
-        for (int k = 0; k < nk; ++k) cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]);
-        acc[0] += t[0];
-        if (P->lt == 0) {
-            acc[2] += t[1];
-            acc[4] += t[2];
-        } else {
-            for (int k = 1; k < P->lt; ++k) acc[1] += t[k];
-            acc[2] += t[P->lt];
-            for (int k = P->lt + 1; k < 2 * P->lt; ++k) acc[3] += t[k];
-            acc[4] += t[2 * P->lt];
+        for (int k = 0; k + 1 < nev; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            if (cat[k] >= 0 && cat[k] < 5) acc[cat[k]] += t;
         }
         float tot = 0.f;
-        cudaEventElapsedTime(&tot, ev[0], ev[nk]);
+        cudaEventElapsedTime(&tot, ev[0], ev[nev - 1]);
         acc[5] += tot;
     }
     for (auto& e : ev) cudaEventDestroy(e);

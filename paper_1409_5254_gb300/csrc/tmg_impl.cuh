@@ -45,6 +45,9 @@ inline Res0 res0_consts(const tmg_plan* P) {
     return R;
 }
 
+// Groups of kernels of one cycle, for the per-kernel timing of tmg_profile_cycle.
+enum : int { kCatDown0 = 0, kCatDown = 1, kCatCoarse = 2, kCatUp = 3, kCatUp0 = 4, kCatEnd = -1 };
+
 // Halo lanes per warp tile: S sweeps that read e_{n-1} need ceil(S/2) lanes.
 inline int halo_lanes(int S) { return (S + 1) / 2; }
 inline int sweeps_down(int nu1) { return (nu1 > 0 ? nu1 - 1 : 0) + 1; }
@@ -169,15 +172,20 @@ struct Impl {
         return cudaGetLastError();
     }
 
-    static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr); }
+    static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr, nullptr, nullptr); }
 
     // One correction cycle.  With ev != nullptr an event is recorded before
-    // every kernel and after the last one (2*lt + 2 events, or 4 when the
-    // on-chip solver starts at level 0).
-    static cudaError_t enqueue_cycle_timed(tmg_plan* P, cudaEvent_t* ev) {
+    // every kernel group and after the last one; cat[i] receives the group
+    // between ev[i] and ev[i+1] (kCat*) and *nev the number of events
+    // (at most 2 * nlev + 4).
+    static cudaError_t enqueue_cycle_timed(tmg_plan* P, cudaEvent_t* ev, int* cat, int* nev) {
         int iev = 0;
-        auto mark = [&]() {
-            if (ev) cudaEventRecord(ev[iev++], P->s);
+        auto mark = [&](int c) {
+            if (ev) {
+                cudaEventRecord(ev[iev], P->s);
+                if (cat) cat[iev] = c;
+                ++iev;
+            }
         };
         const int nu1 = P->o.nu1, nu2 = P->o.nu2;
         const Xfer<T, D> X = xfer_consts<T, D>(P, DIR);
@@ -190,38 +198,61 @@ struct Impl {
         constexpr bool kMixed = std::is_same<T, float>::value;
         float* rl = kMixed && P->lt >= 1 ? static_cast<float*>(P->rl) : nullptr;
         if (P->lt == 0) {
-            mark();
+            mark(kCatDown0);
             launch(P, k_res0<DIR, T, D>, grid_flat(P, P->N), kNT, 0, rT, P->N, R, P->partials, P->st);
-            mark();
+            mark(kCatCoarse);
             if (P->scan_coarsest)
                 enqueue_scan<T, T>(P, rT, static_cast<T*>(P->ul[0]), 0, T(0), nullptr, P->st);
             else
                 launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
                                                                       nu1, nu2, P->o.gamma, P->st);
-            mark();
+            mark(kCatUp0);
             launch(P, k_update0<T>, grid_flat(P, P->N * D), kNT, 0, static_cast<const T*>(P->ul[0]),
                    (int64_t)(P->N * D), (const DevState*)P->st);
-            mark();
+            mark(kCatEnd);
+            if (nev) *nev = iev;
             return cudaGetLastError();
         }
         {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
-            mark();
+            mark(kCatDown0);
             static const int occ = resident_per_sm(k_down0<DIR, T, D>, k_down0_smem_bytes<D>());
             launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, k_down0_smem_bytes<D>(), rT, rl,
                    static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
         }
-        for (int l = 1; l < P->lt; ++l) {
-            const int H = halo_lanes(sweeps_down(nu1));
-            const int64_t nch = P->lev[l].N / 2;
-            mark();
-            static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
-            launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
-                   static_cast<T*>(P->fl[l + 1]), nch, level_consts<T, D>(L(P)[l]), X, nu1, H,
-                   (const DevState*)P->st);
+        // streaming levels 1 .. lt-1, two at a time where both exist
+        int grp[kMaxLevels], ng = 0;
+        for (int l = 1; l < P->lt;) {
+            // default (-1): fuse where the cycle runs in FP32; the FP64 form is
+            // bound by FP64 arithmetic, which the fused way up repeats
+            const bool fuse = P->o.fuse_levels > 0 || (P->o.fuse_levels < 0 && kMixed);
+            const int two = fuse && l + 1 < P->lt;
+            grp[ng++] = two ? -l : l;      // negative: levels l and l+1 in one kernel
+            l += two ? 2 : 1;
         }
-        mark();
+        for (int g = 0; g < ng; ++g) {
+            mark(kCatDown);
+            if (grp[g] < 0) {
+                const int l = -grp[g];
+                const int g0 = sweeps_down(nu1);
+                const int H = halo_lanes(halo_lanes(g0) + sweeps_down(nu1));
+                const int64_t nq = P->lev[l].N / 4;
+                static const int occ = resident_per_sm(k_down2<DIR, T, D>, 0);
+                launch(P, k_down2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                       static_cast<T*>(P->fl[l + 2]), nq, level_consts<T, D>(L(P)[l]),
+                       level_consts<T, D>(L(P)[l + 1]), X, nu1, H, (const DevState*)P->st);
+            } else {
+                const int l = grp[g];
+                const int H = halo_lanes(sweeps_down(nu1));
+                const int64_t nch = P->lev[l].N / 2;
+                static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
+                launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                       static_cast<T*>(P->fl[l + 1]), nch, level_consts<T, D>(L(P)[l]), X, nu1, H,
+                       (const DevState*)P->st);
+            }
+        }
+        mark(kCatCoarse);
         if (P->scan_coarsest)
             enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
                                nullptr, P->st);
@@ -229,37 +260,54 @@ struct Impl {
             launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, static_cast<const T*>(P->fl[P->lt]),
                                                              static_cast<T*>(P->ul[P->lt]), lk, X, nl,
                                                              P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
-        for (int l = P->lt - 1; l >= 1; --l) {
-            const int H = halo_lanes(sweeps_up(nu1, nu2));
-            const int64_t nch = P->lev[l].N / 2;
-            mark();
-            static const int occ = resident_per_sm(k_up<DIR, T, D>, 0);
-            launch(P, k_up<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
-                   static_cast<const T*>(P->ul[l + 1]), static_cast<T*>(P->ul[l]), nch, level_consts<T, D>(L(P)[l]),
-                   X, nu1, nu2, H, (const DevState*)P->st);
+        for (int g = ng - 1; g >= 0; --g) {
+            mark(kCatUp);
+            if (grp[g] < 0) {
+                const int l = -grp[g];
+                // level-l units: the recomputed way down, then level l+1 (recomputed
+                // pre-smoothing, post-smoothing), prolongated, then level-l post-smoothing
+                const int g1 = halo_lanes(sweeps_down(nu1)) + sweeps_up(nu1, nu2);
+                const int H = (2 * g1 + nu2 + 3) / 4;
+                const int64_t nq = P->lev[l].N / 4;
+                static const int occ = resident_per_sm(k_up2<DIR, T, D>, 0);
+                launch(P, k_up2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                       static_cast<const T*>(P->ul[l + 2]), static_cast<T*>(P->ul[l]), nq,
+                       level_consts<T, D>(L(P)[l]), level_consts<T, D>(L(P)[l + 1]), X, nu1, nu2, H,
+                       (const DevState*)P->st);
+            } else {
+                const int l = grp[g];
+                const int H = halo_lanes(sweeps_up(nu1, nu2));
+                const int64_t nch = P->lev[l].N / 2;
+                static const int occ = resident_per_sm(k_up<DIR, T, D>, 0);
+                launch(P, k_up<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                       static_cast<const T*>(P->ul[l + 1]), static_cast<T*>(P->ul[l]), nch,
+                       level_consts<T, D>(L(P)[l]), X, nu1, nu2, H, (const DevState*)P->st);
+            }
         }
         if constexpr (kMixed) {
             if (rl != nullptr) {
                 const int H = halo_lanes(sweeps_up(nu1, nu2) + 1 + sweeps_down(nu1));
                 const int64_t nch = P->N / 2;
-                mark();
+                mark(kCatUp0);
                 static const int occ = resident_per_sm(k_updown0<DIR, D>, 0);
                 launch(P, k_updown0<DIR, D>, grid_for(P, nch, H, occ), kNT, 0, rT, rl, static_cast<const float*>(P->ul[1]),
                        static_cast<float*>(P->fl[1]), nch, R, level_consts<float, D>(L(P)[0]), X, nu1, nu2, H,
                        P->partials, P->st);
-                mark();
+                mark(kCatEnd);
+                if (nev) *nev = iev;
                 return cudaGetLastError();
             }
         }
         {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->N / 2;
-            mark();
+            mark(kCatUp0);
             static const int occ = resident_per_sm(k_up0<DIR, T, D>, 0);
             launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, (const T*)rT, static_cast<const T*>(P->ul[1]),
                    nch, level_consts<T, D>(L(P)[0]), X, nu1, nu2, H, (const DevState*)P->st);
         }
-        mark();
+        mark(kCatEnd);
+        if (nev) *nev = iev;
         return cudaGetLastError();
     }
 

@@ -351,6 +351,127 @@ __device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2
     }
 }
 
+// ------------------------- M consecutive intervals per lane (two-level kernels) --
+//
+// The same building blocks for a lane that holds M consecutive intervals of
+// one level; the halo of interval 0 is the previous lane's interval M-1.
+
+template <int DIR, typename T, int D, int M>
+__device__ __forceinline__ void presmooth_zero_m(const LevelK<T, D>& K, const T (&f)[M][D], T (&h)[M][D],
+                                                 T (&u)[M][D], T (&w)[M][D], int nu1) {
+    const T om = K.omega, om1 = T(1) - K.omega;
+    const T om_first = nu1 > 0 ? om : T(0);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        matvec<T, D>(K.Ainv, f[i], h[i]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[i][k] = om_first * h[i][k];
+            w[i][k] = om_first * f[i][k];
+        }
+    }
+    for (int s = 1; s < nu1; ++s) {
+        T e[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) e[i] = bval<DIR, T, D>(u[i]);
+        const T ep0 = shfl_prev(e[M - 1]);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const T ep = i == 0 ? ep0 : e[i - 1];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                u[i][k] = om1 * u[i][k] + om * fma(K.g[k], ep, h[i][k]);
+                w[i][k] = om1 * w[i][k] + om * (f[i][k] + acoef<DIR>(k, ep));
+            }
+        }
+    }
+}
+
+template <int DIR, typename T, int D, int M>
+__device__ __forceinline__ void residual_tracked_m(const T (&f)[M][D], const T (&u)[M][D], const T (&w)[M][D],
+                                                   T (&r)[M][D]) {
+    T e[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) e[i] = bval<DIR, T, D>(u[i]);
+    const T ep0 = shfl_prev(e[M - 1]);
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const T ep = i == 0 ? ep0 : e[i - 1];
+#pragma unroll
+        for (int k = 0; k < D; ++k) r[i][k] = f[i][k] + acoef<DIR>(k, ep) - w[i][k];
+    }
+}
+
+template <int DIR, typename T, int D, int M>
+__device__ __forceinline__ void postsmooth_m(const LevelK<T, D>& K, const T (&h)[M][D], T (&u)[M][D], int nu) {
+    const T om = K.omega, om1 = T(1) - K.omega;
+    for (int s = 0; s < nu; ++s) {
+        T e[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) e[i] = bval<DIR, T, D>(u[i]);
+        const T ep0 = shfl_prev(e[M - 1]);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const T ep = i == 0 ? ep0 : e[i - 1];
+#pragma unroll
+            for (int k = 0; k < D; ++k) u[i][k] = om1 * u[i][k] + om * fma(K.g[k], ep, h[i][k]);
+        }
+    }
+}
+
+// f_c = R1 a + R2 b for the two halves a, b of one coarse interval.
+template <typename T, int D>
+__device__ __forceinline__ void restrict2(const Xfer<T, D>& X, const T (&a)[D], const T (&b)[D], T (&fc)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(X.P1[l * D + k], a[l], fma(X.P2[l * D + k], b[l], s));
+        fc[k] = s;
+    }
+}
+
+// a += P1 uc, b += P2 uc.
+template <typename T, int D>
+__device__ __forceinline__ void prolong_add2(const Xfer<T, D>& X, const T (&uc)[D], T (&a)[D], T (&b)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T s1 = a[k], s2 = b[k];
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            s1 = fma(X.P1[k * D + l], uc[l], s1);
+            s2 = fma(X.P2[k * D + l], uc[l], s2);
+        }
+        a[k] = s1;
+        b[k] = s2;
+    }
+}
+
+template <typename T, int D, int M>
+__device__ __forceinline__ void load_m(const T* __restrict__ base, int64_t q, bool ok, T (&x)[M][D]) {
+    T v[M * D];
+    if (ok) {
+        VecIO<T, M * D>::load(base + q * M * D, v);
+    } else {
+#pragma unroll
+        for (int i = 0; i < M * D; ++i) v[i] = T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[i][k] = v[i * D + k];
+}
+
+template <typename T, int D, int M>
+__device__ __forceinline__ void store_m(T* __restrict__ base, int64_t q, const T (&x)[M][D]) {
+    T v[M * D];
+#pragma unroll
+    for (int i = 0; i < M; ++i)
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[i * D + k] = x[i][k];
+    VecIO<T, M * D>::store(base + q * M * D, v);
+}
+
 // FP64 residual of one interval, r = F + a (b^T u_{n-1}) - A u_n, using the
 // Legendre structure of the stiffness block.  ep = b^T u_{n-1}, E = 1^T u_n.
 // DIR = 0: (K u)[k] = E - 2 S_k, S_k = sum of u[l], l < k, l of the other
@@ -720,6 +841,73 @@ __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __
         prolong_add<T, D>(X, c, v);
         postsmooth<DIR, T, D>(K, h, v, nu2);
         if (inb && lane >= H) store_pair<T, D>(u, q, v);
+    }
+}
+
+// Levels l and l+1 at once, zero guess on both (the way down): each lane
+// takes four consecutive intervals of level l (two coarse pairs), which
+// restrict to one pair of level l+1 and then to one interval of level l+2.
+// f_l: [4*nquads][D], f_{l+2}: [nquads][D]; f_{l+1} is never stored (the
+// way up recomputes it from f_l).  K0, K1: constants of levels l and l+1.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kNT) k_down2(const T* __restrict__ f, T* __restrict__ fcc, int64_t nquads,
+                                               LevelK<T, D> K0, LevelK<T, D> K1, Xfer<T, D> X, int nu1, int H,
+                                               const DevState* __restrict__ st) {
+    pdl_enter();
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nquads + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nquads;
+        T fv[4][D], h[4][D], u[4][D], w[4][D], r[4][D];
+        load_m<T, D, 4>(f, q, inb, fv);
+        presmooth_zero_m<DIR, T, D, 4>(K0, fv, h, u, w, nu1);
+        residual_tracked_m<DIR, T, D, 4>(fv, u, w, r);
+        T f1[2][D], h1[2][D], u1[2][D], w1[2][D], r1[2][D], out[D];
+        restrict2<T, D>(X, r[0], r[1], f1[0]);
+        restrict2<T, D>(X, r[2], r[3], f1[1]);
+        presmooth_zero<DIR, T, D>(K1, f1, h1, u1, w1, nu1);
+        residual_tracked<DIR, T, D>(f1, u1, w1, r1);
+        restrict_pair<T, D>(X, r1, out);
+        if (inb && lane >= H) VecIO<T, D>::store(fcc + q * D, out);
+    }
+}
+
+// Levels l+1 and l at once on the way up: recompute level l's pre-smoothed
+// iterate and residual and level l+1's right-hand side and pre-smoothed
+// iterate from f_l, add the prolongated level-(l+2) correction ucc, post-smooth
+// on level l+1, prolongate onto level l, post-smooth there and write u_l.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kNT) k_up2(const T* __restrict__ f, const T* __restrict__ ucc, T* __restrict__ u,
+                                             int64_t nquads, LevelK<T, D> K0, LevelK<T, D> K1, Xfer<T, D> X, int nu1,
+                                             int nu2, int H, const DevState* __restrict__ st) {
+    pdl_enter();
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nquads + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nquads;
+        T fv[4][D], h[4][D], v[4][D], w[4][D], r[4][D], cc[D];
+        load_m<T, D, 4>(f, q, inb, fv);
+        load_one<T, D>(ucc, q, inb, cc);
+        presmooth_zero_m<DIR, T, D, 4>(K0, fv, h, v, w, nu1);
+        residual_tracked_m<DIR, T, D, 4>(fv, v, w, r);
+        T f1[2][D], h1[2][D], v1[2][D], w1[2][D];
+        restrict2<T, D>(X, r[0], r[1], f1[0]);
+        restrict2<T, D>(X, r[2], r[3], f1[1]);
+        presmooth_zero<DIR, T, D>(K1, f1, h1, v1, w1, nu1);
+        prolong_add<T, D>(X, cc, v1);
+        postsmooth<DIR, T, D>(K1, h1, v1, nu2);
+        prolong_add2<T, D>(X, v1[0], v[0], v[1]);
+        prolong_add2<T, D>(X, v1[1], v[2], v[3]);
+        postsmooth_m<DIR, T, D, 4>(K0, h, v, nu2);
+        if (inb && lane >= H) store_m<T, D, 4>(u, q, v);
     }
 }
 

@@ -83,7 +83,7 @@ struct tmg_ops {
     size_t (*tail_bytes)(int64_t Nt, int nl);
     cudaError_t (*upload)(tmg_plan*);              // per-level constants -> device
     cudaError_t (*enqueue_cycle)(tmg_plan*);       // one correction cycle
-    cudaError_t (*enqueue_cycle_timed)(tmg_plan*, cudaEvent_t* ev);   // same, events around kernels
+    cudaError_t (*enqueue_cycle_timed)(tmg_plan*, cudaEvent_t* ev, int* cat, int* nev);   // same, events around kernels
     cudaError_t (*enqueue_normF)(tmg_plan*);       // ||F|| for a caller-given start
     cudaError_t (*enqueue_residual)(tmg_plan*, const double* f, double u0, const double* u, double* r);
     cudaError_t (*set_tail_attr)(size_t bytes);

@@ -32,7 +32,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
                 ("n_min", ctypes.c_int64), ("use_graph", ctypes.c_int), ("initial_guess", ctypes.c_int),
-                ("tail_cap", ctypes.c_int64), ("use_pdl", ctypes.c_int), ("update_residual", ctypes.c_int)]
+                ("tail_cap", ctypes.c_int64), ("use_pdl", ctypes.c_int), ("update_residual", ctypes.c_int),
+                ("fuse_levels", ctypes.c_int)]
 
 
 _LIB = None
@@ -128,7 +129,8 @@ class Plan:
     def __init__(self, p: int, tau: float, lam: float, N: int, levels: int = 0, omega: float = 0.0, *,
                  tol: float = 1e-10, max_cycles: int = 100, nu1: int = 1, nu2: int = 1, gamma: int = 1,
                  precision="mixed", n_min: int = 64, use_graph: bool = True, initial_guess: bool = False,
-                 tail_cap: int = 0, use_pdl: bool = True, update_residual: bool = True, stream=None):
+                 tail_cap: int = 0, use_pdl: bool = True, update_residual: bool = True,
+                 fuse_levels=None, stream=None):
         L = _lib()
         o = _Opts()
         L.tmg_opts_default(ctypes.byref(o))
@@ -138,6 +140,7 @@ class Plan:
         o.tail_cap = tail_cap
         o.use_pdl = int(use_pdl)
         o.update_residual = int(update_residual)
+        o.fuse_levels = -1 if fuse_levels is None else int(bool(fuse_levels))
         self.precision = _PREC[precision]
         self.p, self.d, self.N = p, p + 1, N
         self.tau, self.lam = tau, lam

@@ -95,6 +95,31 @@ def test_fp64_cycles_match_textbook_cycle(dev, case):
         assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
 
 
+@pytest.mark.parametrize("tail_cap", [64, 128])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1), (0, 2), (1, 0), (3, 2)])
+def test_fused_level_pairs_match_textbook_cycle(dev, tail_cap, nu):
+    """Streaming levels run two per kernel (levels l and l+1, level l+1 never
+    stored).  With a small on-chip solver there are 8 (tail_cap 64: four pairs)
+    or 7 (tail_cap 128: three pairs and a single level) streaming levels; the
+    FP64 iterates match the textbook cycle to 1e-12 for several sweep counts,
+    and the unfused kernels give the same iterates to rounding."""
+    p, N, lam = 1, 1 << 15, 4.0
+    nu1, nu2 = nu
+    prob = inputs.scalar_problem(13, N, p, lam=lam, T=1.0, u0=0.5)
+    z = lam * prob["tau"]
+    Fhat = O.fold_u0(p, prob["F"], prob["u0"])
+    got, info = gpu_cycles(dev, p, prob["tau"], lam, prob["F"], prob["u0"], 2, nu1=nu1, nu2=nu2, n_min=2,
+                           tail_cap=tail_cap, fuse_levels=True)
+    assert info["tail_level"] == (9 if tail_cap == 64 else 8)
+    unf, _ = gpu_cycles(dev, p, prob["tau"], lam, prob["F"], prob["u0"], 2, nu1=nu1, nu2=nu2, n_min=2,
+                        tail_cap=tail_cap, fuse_levels=False)
+    u = np.zeros_like(prob["F"])
+    for k in range(2):
+        u = O.mg_one_cycle(p, z, Fhat, u, n_min=2, nu1=nu1, nu2=nu2)
+        assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
+        assert rel_err(got[k], unf[k]) <= 1e-13
+
+
 @pytest.mark.parametrize("p", [0, 1, 2, 3])
 def test_fp64_solve_matches_forward_substitution(dev, p):
     N = 1 << 13
@@ -383,3 +408,23 @@ def test_confirmation_rejects_an_updated_residual_below_the_fp64_floor(dev):
         st = plan.stats()
     assert st.cycles == 40
     assert rel_residual(p, prob["tau"], prob["F"], prob["u0"], u.cpu().numpy()) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_non_finite_input_reports_numeric_error_and_plan_stays_usable(dev, prec, bad):
+    """A non-finite value in f makes the first residual norm non-finite: the
+    solve stops at once with TMG_ENUMERIC (no cycles run on garbage), and the
+    same plan then solves a clean problem."""
+    N, p = 1 << 12, 1
+    prob = inputs.scalar_problem(8, N, p, lam=1.0, T=1.0, u0=1.0)
+    T_ = tmg()
+    F_bad = prob["F"].copy()
+    F_bad[N // 3, 1] = bad
+    with T_.Plan(p, prob["tau"], 1.0, N, precision=prec) as plan:
+        with pytest.raises(T_.TmgError) as ei:
+            plan.solve(torch.from_numpy(F_bad).to(dev), prob["u0"])
+        assert ei.value.status == T_.TMG_ENUMERIC
+        assert plan.stats().cycles == 0
+        u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
+    assert rel_residual(p, prob["tau"], prob["F"], prob["u0"], u) <= 1.05e-10
