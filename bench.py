@@ -99,26 +99,36 @@ class ClockSampler:
 def cycle_bytes(N: int, d: int, lt: int):
     """Algorithmic HBM bytes of the mixed-precision solve's kernels (FP32 cycle).
 
-    Start of a solve (k_down0, once, and again only to confirm convergence):
-    read u, F (FP64), write the float-pair residual (8 B per value) and the
-    level-1 right-hand side (N/2 intervals, FP32): 26 B/DoF.
+    The level-0 residual is a float pair stored in 6 bytes per value (float
+    high part, 16-bit low part).
+    Start of a solve from u = 0 (k_down0, once): read F, write the residual
+    pair and the level-1 right-hand side (N/2 intervals, FP32): 16 B/DoF.
+    Confirmation (k_down0, once): read u, F; write the pair and f_1: 24 B/DoF.
     Every cycle, level 0 (k_updown0): read the residual pair, the level-1
     correction and u; write u, the new residual pair and the next level-1
-    right-hand side: 8 + 2 + 8 + 8 + 8 + 2 = 36 B/DoF.
-    Level l >= 1 below the on-chip solver: down reads f_l, writes f_{l+1};
-    up reads f_l and u_{l+1}, writes u_l (FP32).  The on-chip solver reads
-    f_lt and writes u_lt once.
+    right-hand side: 6 + 2 + 8 + 8 + 6 + 2 = 32 B/DoF.
+    Streaming levels l >= 1 run two per kernel: down reads f_l and writes
+    f_{l+2}; up reads f_l and u_{l+2} and writes u_l (FP32); a last single
+    level moves 1.5 + 2.5 level vectors.  The on-chip solver reads f_lt and
+    writes u_lt once.
     """
     nd = N * d
     half = (N // 2) * d * 4
-    down0 = nd * (8 + 8 + 8) + half
-    updown0 = nd * (8 + 8 + 8 + 8) + 2 * half
+    start0 = nd * (8 + 6) + half
+    confirm0 = nd * (8 + 8 + 6) + half
+    updown0 = nd * (6 + 8 + 8 + 6) + 2 * half
     coarse = 0
-    for l in range(1, lt):
-        nl = (N >> l) * d
-        coarse += (nl + nl // 2) * 4 + (nl + nl // 2 + nl) * 4
+    l = 1
+    while l < lt:
+        nl = (N >> l) * d * 4
+        if l + 1 < lt:
+            coarse += nl + nl // 4 + nl + nl // 4 + nl
+            l += 2
+        else:
+            coarse += nl + nl // 2 + nl + nl // 2 + nl
+            l += 1
     tail_io = 2 * (N >> lt) * d * 4 if lt > 0 else 0
-    return {"down0": down0, "updown0": updown0, "cycle": updown0 + coarse + tail_io}
+    return {"start0": start0, "confirm0": confirm0, "updown0": updown0, "cycle": updown0 + coarse + tail_io}
 
 
 def time_solves(plan, F, u, steps: int, stream, torch):
@@ -229,7 +239,7 @@ def run_ours(args):
                 "cycle_bytes": cb["cycle"], "cycle_ms": round(steady_ms, 5),
                 "cycle_frac": round(cb["cycle"] / (steady_ms * 1e-3) / 1e9 / hbm_peak, 4),
                 "solve_ms_per_cycle": round(ms / max(st.cycles, 1), 5),
-                "kernel_ms": {"down0_once_per_solve": round(prof["down0"], 5),
+                "kernel_ms": {"down0_confirm_once_per_solve": round(prof["down0"], 5),
                               "down_levels": round(prof["down_levels"], 5),
                               "coarse_on_chip": round(prof["coarse_on_chip"], 5),
                               "up_levels": round(prof["up_levels"], 5), "updown0": round(prof["up0"], 5),

@@ -76,7 +76,7 @@ typedef struct {
     int use_pdl;        /* 1: programmatic dependent launch between the kernels of a cycle,
                            hiding each launch behind its predecessor's tail (default 1) */
     int update_residual; /* TMG_MIXED: 1 = keep the level-0 residual as a float pair (about
-                           48 bits) updated by r -= L c after each cycle, recomputed from u in
+                           39 bits stored) updated by r -= L c after each cycle, recomputed from u in
                            FP64 only at the start and to confirm convergence (default 1);
                            0 = recompute it from u in FP64 every cycle */
     int fuse_levels;    /* 1: the streaming levels l >= 1 run two per kernel (levels l and

@@ -93,7 +93,7 @@ tmg_status build_graph(tmg_plan* P, int dir) {
 
 // Start-of-solve state: written through the pinned mirror with one copy.
 tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, double tol, int max_cycles,
-                       int use_cond, int nF_from_first, int dir = 0) {
+                       int use_cond, int nF_from_first, int dir = 0, int u_zero = 0) {
     tmg::DevState* h = P->st_host;
     TMG_CUDA(cudaStreamSynchronize(P->s));    // the mirror may still be read by a previous copy
     h->F = f;
@@ -108,6 +108,7 @@ tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, doubl
     h->use_cond = use_cond;
     h->full = 1;
     h->rsel = 0;
+    h->u_zero = u_zero;
     h->ticket = 0u;
     h->nscale = 1.0f;
     h->nvals = (long long)P->N * P->d;
@@ -130,7 +131,8 @@ tmg_status run_solve(tmg_plan* P, const double* f, double u0, double* u, int dir
         tmg_status s = build_graph(P, dir);
         if (s != TMG_OK) return s;
     }
-    tmg_status s = stage_state(P, f, u0, u, P->o.tol, P->o.max_cycles, use_graph, initial_guess ? 0 : 1, dir);
+    tmg_status s =
+        stage_state(P, f, u0, u, P->o.tol, P->o.max_cycles, use_graph, initial_guess ? 0 : 1, dir, initial_guess ? 0 : 1);
     if (s != TMG_OK) return s;
     if (initial_guess) {
         TMG_CUDA(ops->enqueue_normF(P));
@@ -283,7 +285,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     const size_t off_r = off;
     off = align_up(off + el * N * P->d * (updated_res ? 2 : 1), A);
     const size_t off_rl = off;
-    if (updated_res) off = align_up(off + sizeof(float) * N * P->d * 2, A);
+    if (updated_res) off = align_up(off + sizeof(short) * N * P->d * 2, A);
     const size_t off_lk = off;
     off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
     const size_t off_lk_adj = off;
@@ -486,9 +488,24 @@ tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, 
         if (which == 2) {
             src = static_cast<const char*>(P->rT) + sel * nv * elem;
         } else {
+            // the low parts are stored as 16-bit codes relative to ulp(hi): decode here
             if (P->rl == nullptr) return TMG_EINVAL;
-            elem = sizeof(float);
-            src = static_cast<const float*>(P->rl) + sel * nv;
+            if (bytes < nv * sizeof(float)) return TMG_EINVAL;
+            std::vector<float> hi(nv);
+            std::vector<short> code(nv);
+            TMG_CUDA(cudaMemcpyAsync(hi.data(), static_cast<const float*>(P->rT) + sel * nv, nv * sizeof(float),
+                                     cudaMemcpyDeviceToHost, P->s));
+            TMG_CUDA(cudaMemcpyAsync(code.data(), static_cast<const short*>(P->rl) + sel * nv, nv * sizeof(short),
+                                     cudaMemcpyDeviceToHost, P->s));
+            TMG_CUDA(cudaStreamSynchronize(P->s));
+            float* out = static_cast<float*>(host_dst);
+            for (size_t i = 0; i < nv; ++i) {
+                uint32_t b;
+                memcpy(&b, &hi[i], sizeof(b));
+                const int E = (int)((b >> 23) & 0xFFu);
+                out[i] = E < 39 ? 0.f : ldexpf((float)code[i], E - 165);
+            }
+            return TMG_OK;
         }
     } else {
         if (level < 0 || level > P->lt || (level == 0 && which == 0)) return TMG_EINVAL;

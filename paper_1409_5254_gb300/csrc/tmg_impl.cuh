@@ -196,7 +196,7 @@ struct Impl {
         // mixed form with the level-0 residual kept as a float pair and updated
         // by k_updown0 (the plan allocates rl only then)
         constexpr bool kMixed = std::is_same<T, float>::value;
-        float* rl = kMixed && P->lt >= 1 ? static_cast<float*>(P->rl) : nullptr;
+        short* rl = kMixed && P->lt >= 1 ? static_cast<short*>(P->rl) : nullptr;
         if (P->lt == 0) {
             mark(kCatDown0);
             launch(P, k_res0<DIR, T, D>, grid_flat(P, P->N), kNT, 0, rT, P->N, R, P->partials, P->st);

@@ -76,6 +76,7 @@ struct DevState {
     int full;             // 1: the next level-0 down kernel evaluates r = F - L u from u in FP64
                           //    (start of a solve; confirmation of an updated residual that met tol)
     int rsel;             // which of the two float-pair residual buffers holds the current residual
+    int u_zero;           // 1: the solve starts from u = 0 (the first residual is F itself)
     unsigned ticket;      // last-block ticket
     float nscale;         // power of two that brings the residual near 1 (FP32 norm)
     long long nvals;      // values per residual vector, N * D
@@ -566,6 +567,25 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
     return ff{s, (a - (s - bp)) + (b - bp)};
 }
 
+// Storage of the low part of a float pair (hi, lo) with |lo| <= ulp(hi)/2
+// (hi the rounded sum, as two_sum leaves it): a 16-bit fixed-point multiple
+// of 2^-15 ulp(hi), so the code lies in [-2^14, 2^14] and resolves 2^-16
+// ulp(hi) -- hi + lo keeps about 39 significant bits in 6 bytes instead of
+// 8.  Values with |hi| < 2^-88 keep no low part.
+__device__ __forceinline__ short lo_encode(float hi, float lo) {
+    const int E = (int)((__float_as_uint(hi) >> 23) & 0xFFu);
+    if (E < 39) return 0;
+    const float s = __uint_as_float((unsigned)(292 - E) << 23);   // 2^(165 - E)
+    return (short)__float2int_rn(lo * s);
+}
+
+__device__ __forceinline__ float lo_decode(float hi, short q) {
+    const int E = (int)((__float_as_uint(hi) >> 23) & 0xFFu);
+    if (E < 39) return 0.f;
+    const float s = __uint_as_float((unsigned)(E - 38) << 23);    // 2^(E - 165)
+    return (float)q * s;
+}
+
 // (s, c) += t for a single float term.
 __device__ __forceinline__ void acc_add1(float& s, float& c, float t) {
     const ff n = two_sum(s, t);
@@ -925,7 +945,7 @@ constexpr size_t k_down0_smem_bytes() {
 // time (FP64 squares in the first cycle, scaled FP32 squares afterwards) so
 // that no branch between the two sits inside the loop.
 template <bool FP64NORM, int DIR, typename T, int D>
-__device__ __forceinline__ double down0_loop(T* __restrict__ rT, float* __restrict__ rlo, T* __restrict__ fc,
+__device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
                                              int64_t nchunks,
                                              const Res0& R, const LevelK<T, D>& K, const Xfer<T, D>& X, int nu1,
                                              int H, const DevState* st) {
@@ -979,7 +999,7 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, float* __restri
             Fv[1][k] = Fvf[D + k];
         }
         T rt[2][D];
-        float rtl[2][D];     // low parts of the float-pair residual (mixed form)
+        short rtl[2][D];     // low parts of the float-pair residual (mixed form), encoded
         if constexpr (kMixed) {
             ff us0[D], us1[D], sE0, sB0, sE1, sB1;
             small_sums<DIR, D>(uv[0], us0, sE0, sB0);
@@ -999,8 +1019,8 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, float* __restri
             for (int k = 0; k < D; ++k) {
                 rt[0][k] = inb ? r0[k] : 0.f;
                 rt[1][k] = inb ? r1[k] : 0.f;
-                rtl[0][k] = l0[k];
-                rtl[1][k] = l1[k];
+                rtl[0][k] = lo_encode(r0[k], l0[k]);
+                rtl[1][k] = lo_encode(r1[k], l1[k]);
             }
         } else {
             double r[2][D];
@@ -1033,7 +1053,7 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, float* __restri
                 }
             store_pair<T, D>(rT, q, rt);
             if constexpr (kMixed) {
-                if (rlo != nullptr) store_pair<float, D>(rlo, q, rtl);
+                if (rlo != nullptr) store_pair<short, D>(rlo, q, rtl);
             }
         }
         if (fc != nullptr) {
@@ -1051,12 +1071,68 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, float* __restri
 
 //
 // With rlo != nullptr (mixed form with an updated residual) the residual is
-// stored as a float pair (rT, rlo) into buffer st->rsel of two (each nchunks
-// * 2 * D floats) and the kernel runs only when st->full is set: at the start
+// stored as a float pair (rT, rlo; low parts encoded by lo_encode) into buffer
+// st->rsel of two (each nchunks * 2 * D values) and the kernel runs only when
+// st->full is set: at the start
 // of a solve, and to confirm an updated residual that met the tolerance; in
 // every other cycle k_updown0 has done its work.
+// Mixed form, first residual of a solve that starts from u = 0: r = F (with
+// a u0 in the first interval) needs no product with u, so F is split into
+// float pairs directly; then the pre-smoothing and restriction of L c = r.
+template <int DIR, int D>
+__device__ __forceinline__ double start0_loop(float* __restrict__ rT, short* __restrict__ rlo,
+                                              float* __restrict__ fc, int64_t nchunks, const LevelK<float, D>& K,
+                                              const Xfer<float, D>& X, int nu1, int H, const DevState* st) {
+    const double* __restrict__ F = st->F;
+    const double u0 = st->u0;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    double ss = 0.0;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const bool own = inb && lane >= H;
+        double Fv[2][D];
+        load_pair<double, D>(F, q, inb, Fv);
+        if (q == 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) Fv[0][k] += acoef<DIR>(k, u0);
+        }
+        float rt[2][D];
+        short rq[2][D];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const ff sp = split_d(Fv[i][k]);
+                const ff n = two_sum(sp.hi, sp.lo);      // rounded high part, |lo| <= ulp/2
+                rt[i][k] = n.hi;
+                rq[i][k] = lo_encode(n.hi, n.lo);
+            }
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const double v = f2d_int(rt[i][k]);
+                    ss = fma(v, v, ss);
+                }
+            store_pair<float, D>(rT, q, rt);
+            store_pair<short, D>(rlo, q, rq);
+        }
+        float h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
+        presmooth_zero<DIR, float, D>(K, rt, h, c, w, nu1);
+        residual_tracked<DIR, float, D>(rt, c, w, rc);
+        restrict_pair<float, D>(X, rc, out);
+        if (own) VecIO<float, D>::store(fc + q * D, out);
+    }
+    return ss;
+}
+
 template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, float* __restrict__ rlo, T* __restrict__ fc,
+__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
                                                int64_t nchunks, Res0 R, LevelK<T, D> K, Xfer<T, D> X, int nu1,
                                                int H, double* __restrict__ partials, DevState* st) {
     pdl_enter();
@@ -1071,6 +1147,13 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, float* __rest
     // FP32 norm with a power-of-two scale, except in the first cycle whose
     // residual magnitude is not known yet (FP64 then)
     double ss;
+    if constexpr (kMixed) {
+        if (rlo != nullptr && st->cycle == 0 && st->u_zero) {
+            ss = start0_loop<DIR, D>(rT, rlo, fc, nchunks, K, X, nu1, H, st);
+            grid_norm_finalize<kNT>(ss, partials, st, kFinFull);
+            return;
+        }
+    }
     if (!kMixed || st->cycle == 0) ss = down0_loop<true, DIR, T, D>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
     else ss = down0_loop<false, DIR, T, D>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
     grid_norm_finalize<kNT>(ss, partials, st, rlo != nullptr ? kFinFull : kFinPlain);
@@ -1117,7 +1200,7 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
 // Level 0 of the mixed form between two cycles: the way up of one cycle
 // fused with the way down of the next, with the level-0 residual updated
 // instead of recomputed from u.  The residual is kept as a float pair
-// (rh, rl), about 48 significant bits.  Per coarse pair: recompute the
+// (rh, rl), about 39 significant bits in storage (lo_encode).  Per coarse pair: recompute the
 // pre-smoothed correction from rh, add the prolongated level-1 correction,
 // post-smooth (this cycle's correction c); u += c in FP64; (rh, rl) <- r - L c
 // (residual_update_ff), whose norm feeds the stopping test; then the
@@ -1132,10 +1215,10 @@ __global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* 
 //
 // The residual is read from buffer st->rsel and written to the other one:
 // the halo lanes of a tile read pairs that another warp owns and updates, so
-// an in-place update would race.  rh and rl each hold two buffers of
-// nchunks * 2 * D floats.
+// an in-place update would race.  rh (floats) and rl (16-bit encoded low
+// parts, lo_encode) each hold two buffers of nchunks * 2 * D values.
 template <int DIR, int D>
-__global__ void __launch_bounds__(kNT, D <= 2 ? 4 : 2) k_updown0(float* __restrict__ rh, float* __restrict__ rl,
+__global__ void __launch_bounds__(kNT, D <= 2 ? 4 : 2) k_updown0(float* __restrict__ rh, short* __restrict__ rl,
                                                  const float* __restrict__ uc, float* __restrict__ fc,
                                                  int64_t nchunks, Res0 R, LevelK<float, D> K, Xfer<float, D> X,
                                                  int nu1, int nu2, int H, double* __restrict__ partials,
@@ -1147,9 +1230,9 @@ __global__ void __launch_bounds__(kNT, D <= 2 ? 4 : 2) k_updown0(float* __restri
     const int64_t nv = nchunks * 2 * D;
     const int sel = st->rsel;
     const float* __restrict__ rh_in = rh + sel * nv;
-    const float* __restrict__ rl_in = rl + sel * nv;
+    const short* __restrict__ rl_in = rl + sel * nv;
     float* __restrict__ rh_out = rh + (1 - sel) * nv;
-    float* __restrict__ rl_out = rl + (1 - sel) * nv;
+    short* __restrict__ rl_out = rl + (1 - sel) * nv;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int64_t ntiles = (nchunks + per - 1) / per;
@@ -1160,11 +1243,16 @@ __global__ void __launch_bounds__(kNT, D <= 2 ? 4 : 2) k_updown0(float* __restri
         const bool inb = q >= 0 && q < nchunks;
         const bool own = inb && lane >= H;
         float r[2][D], rlo[2][D], cc[D];
+        short rq[2][D];
         double uv[2][D];
         load_pair<float, D>(rh_in, q, inb, r);
-        load_pair<float, D>(rl_in, q, inb, rlo);
+        load_pair<short, D>(rl_in, q, inb, rq);
         load_one<float, D>(uc, q, inb, cc);
         load_pair<double, D>(uu, q, own, uv);      // issued early: its latency overlaps the sweeps
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) rlo[i][k] = lo_decode(r[i][k], rq[i][k]);
         float h[2][D], c[2][D], w[2][D];
         presmooth_zero<DIR, float, D>(K, r, h, c, w, nu1);
         prolong_add<float, D>(X, cc, c);
@@ -1192,7 +1280,11 @@ __global__ void __launch_bounds__(kNT, D <= 2 ? 4 : 2) k_updown0(float* __restri
                 }
             store_pair<double, D>(uu, q, uv);
             store_pair<float, D>(rh_out, q, r);
-            store_pair<float, D>(rl_out, q, rlo);
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) rq[i][k] = lo_encode(r[i][k], rlo[i][k]);
+            store_pair<short, D>(rl_out, q, rq);
         }
         // the next cycle's way down on L c' = rh
         float rc[2][D], out[D];
