@@ -71,8 +71,9 @@ typedef struct {
     int64_t n_min;      /* coarsen while N_l is even and N_l > n_min (default 64) */
     int use_graph;      /* 1: whole solve as one CUDA graph launch (default 1) */
     int initial_guess;  /* 1: tmg_solve starts from the u passed in (default 0: u = 0) */
-    int64_t tail_cap;   /* most intervals the on-chip coarse solver takes (0: default 8192);
-                           smaller values move more levels to the streaming kernels */
+    int64_t tail_cap;   /* most intervals the on-chip coarse solver takes (0: default, 64 for
+                           V-cycles, 8192 for W-cycles; at most 8192); smaller values move
+                           more levels to the streaming kernels */
     int use_pdl;        /* 1: programmatic dependent launch between the kernels of a cycle,
                            hiding each launch behind its predecessor's tail (default 1) */
     int update_residual; /* TMG_MIXED: 1 = keep the level-0 residual as a float pair (about

@@ -42,6 +42,11 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 const size_t kTailSmemMax = 200 * 1024;
 const int64_t kTailNmax = 8192;
+// Default largest level of the on-chip coarse solver: small, because inside
+// a graph with programmatic dependent launch a streaming kernel on a small
+// level costs less than a level of the single-CTA solver; W-cycles need the
+// on-chip solver from level 1 and take the largest one.
+const int64_t kTailDefaultV = 64;
 
 tmg_status build_graph(tmg_plan* P, int dir) {
     cudaGraph_t g = nullptr;
@@ -249,7 +254,8 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     P->lt = -1;
     for (int l = 0; l < P->nlev; ++l) {
         const size_t b = P->ops->tail_bytes(P->lev[l].N, P->nlev - l);
-        const int64_t cap = o.tail_cap > 0 && o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax;
+        const int64_t cap = o.tail_cap > 0 ? (o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax)
+                                           : (o.gamma == 2 ? kTailNmax : kTailDefaultV);
         if ((P->lev[l].N <= cap || l == P->nlev - 1) && P->lev[l].N <= kTailNmax && b <= kTailSmemMax) {
             P->lt = l;
             P->tail_smem = b;

@@ -231,7 +231,15 @@ struct Impl {
             grp[ng++] = two ? -l : l;      // negative: levels l and l+1 in one kernel
             l += two ? 2 : 1;
         }
+        // the coarsest level (at most 64 intervals, directly below the streaming
+        // levels) is solved by the last block of the last down kernel
+        const bool coarse_in_down = P->o.gamma == 1 && !P->scan_coarsest && P->lt == P->nlev - 1 && ng > 0 &&
+                                    P->lev[P->lt].N <= 64;
+        CoarseTail<T, D> ct_none{nullptr, nullptr, nullptr, 0, nullptr};
+        CoarseTail<T, D> ct_last{lk, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]),
+                                 (int)P->lev[P->lt].N, &P->st->ticket2};
         for (int g = 0; g < ng; ++g) {
+            const CoarseTail<T, D> ct = coarse_in_down && g == ng - 1 ? ct_last : ct_none;
             mark(kCatDown);
             if (grp[g] < 0) {
                 const int l = -grp[g];
@@ -241,7 +249,7 @@ struct Impl {
                 static const int occ = resident_per_sm(k_down2<DIR, T, D>, 0);
                 launch(P, k_down2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                        static_cast<T*>(P->fl[l + 2]), nq, level_consts<T, D>(L(P)[l]),
-                       level_consts<T, D>(L(P)[l + 1]), X, nu1, H, (const DevState*)P->st);
+                       level_consts<T, D>(L(P)[l + 1]), X, nu1, H, (const DevState*)P->st, ct);
             } else {
                 const int l = grp[g];
                 const int H = halo_lanes(sweeps_down(nu1));
@@ -249,11 +257,13 @@ struct Impl {
                 static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
                 launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                        static_cast<T*>(P->fl[l + 1]), nch, level_consts<T, D>(L(P)[l]), X, nu1, H,
-                       (const DevState*)P->st);
+                       (const DevState*)P->st, ct);
             }
         }
         mark(kCatCoarse);
-        if (P->scan_coarsest)
+        if (coarse_in_down) {
+            // solved above
+        } else if (P->scan_coarsest)
             enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
                                nullptr, P->st);
         else

@@ -78,6 +78,7 @@ struct DevState {
     int rsel;             // which of the two float-pair residual buffers holds the current residual
     int u_zero;           // 1: the solve starts from u = 0 (the first residual is F itself)
     unsigned ticket;      // last-block ticket
+    unsigned ticket2;     // last-block ticket of the coarsest solve in the last down kernel
     float nscale;         // power of two that brings the residual near 1 (FP32 norm)
     long long nvals;      // values per residual vector, N * D
     unsigned long long cond;   // cudaGraphConditionalHandle of that loop
@@ -815,12 +816,82 @@ __device__ __forceinline__ void grid_norm_finalize(double ss, double* __restrict
 
 constexpr int kNT = 256;   // threads per block of the streaming kernels
 
+// Exact solve of a coarsest level of at most 64 intervals by one warp: two
+// intervals per lane, the affine maps e_n = alpha e_{n-1} + c^T f_n (e_{-1} =
+// 0) combined by a warp scan, then u_n = A^{-1} f_n + g e_{n-1}.  f is read
+// through L2 (it was written by other blocks of the same launch).
+template <typename T, int D>
+__device__ __forceinline__ void warp_coarse_solve(const LevelK<T, D>& K, const T* f, T* u, int Nc) {
+    const int lane = threadIdx.x & 31;
+    const int n0 = 2 * lane, n1 = 2 * lane + 1;
+    T f0[D], f1[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        f0[k] = n0 < Nc ? __ldcg(f + n0 * D + k) : T(0);
+        f1[k] = n1 < Nc ? __ldcg(f + n1 * D + k) : T(0);
+    }
+    const T b0 = dotc<T, D>(K.c, f0), b1 = dotc<T, D>(K.c, f1);
+    T A = n1 < Nc ? K.alpha * K.alpha : (n0 < Nc ? K.alpha : T(1));
+    T B = n1 < Nc ? fma(K.alpha, b0, b1) : (n0 < Nc ? b0 : T(0));
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T Ap = __shfl_up_sync(kFull, A, off);
+        const T Bp = __shfl_up_sync(kFull, B, off);
+        if (lane >= off) {
+            B = fma(A, Bp, B);
+            A = A * Ap;
+        }
+    }
+    T ein = __shfl_up_sync(kFull, B, 1);   // e_{2 lane - 1}: inclusive prefix of the lane before
+    if (lane == 0) ein = T(0);
+    T x0[D], x1[D];
+    matvec<T, D>(K.Ainv, f0, x0);
+    matvec<T, D>(K.Ainv, f1, x1);
+    const T emid = fma(K.alpha, ein, b0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        if (n0 < Nc) u[n0 * D + k] = fma(K.g[k], ein, x0[k]);
+        if (n1 < Nc) u[n1 * D + k] = fma(K.g[k], emid, x1[k]);
+    }
+}
+
+// The coarsest level solved by the last block of the last down kernel of a
+// cycle (u == nullptr: not this kernel's job).  Each block, after its tiles,
+// fences its writes and takes a ticket; the block that takes the last ticket
+// reads the whole coarsest right-hand side and solves it with one warp.  No
+// block waits for another.
+template <typename T, int D>
+struct CoarseTail {
+    const LevelK<T, D>* K;    // constants of the coarsest level (device)
+    const T* f;               // its right-hand side, written by this kernel
+    T* u;                     // its solution
+    int Nc;                   // intervals, at most 64
+    unsigned* ticket;         // zero between launches
+};
+
+template <typename T, int D>
+__device__ __forceinline__ void coarse_tail_last_block(const CoarseTail<T, D>& ct) {
+    if (ct.u == nullptr) return;
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ct.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < 32) {
+        const LevelK<T, D> K = *ct.K;
+        warp_coarse_solve<T, D>(K, ct.f, ct.u, ct.Nc);
+    }
+    if (threadIdx.x == 0) *ct.ticket = 0u;
+}
+
 // Level l >= 1, zero guess: pre-smooth, residual, restrict.  f: [2*nchunks][D],
 // fc: [nchunks][D].
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __restrict__ fc, int64_t nchunks,
                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int H,
-                                              const DevState* __restrict__ st) {
+                                              const DevState* __restrict__ st, CoarseTail<T, D> ct) {
     pdl_enter();
     if (st->done) return;
     const int lane = threadIdx.x & 31;
@@ -837,6 +908,7 @@ __global__ void __launch_bounds__(kNT) k_down(const T* __restrict__ f, T* __rest
         restrict_pair<T, D>(X, r, out);
         if (inb && lane >= H) VecIO<T, D>::store(fc + q * D, out);
     }
+    coarse_tail_last_block<T, D>(ct);
 }
 
 // Level l >= 1, zero guess: recompute the pre-smoothed iterate, add the
@@ -872,7 +944,7 @@ __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kNT) k_down2(const T* __restrict__ f, T* __restrict__ fcc, int64_t nquads,
                                                LevelK<T, D> K0, LevelK<T, D> K1, Xfer<T, D> X, int nu1, int H,
-                                               const DevState* __restrict__ st) {
+                                               const DevState* __restrict__ st, CoarseTail<T, D> ct) {
     pdl_enter();
     if (st->done) return;
     const int lane = threadIdx.x & 31;
@@ -894,6 +966,7 @@ __global__ void __launch_bounds__(kNT) k_down2(const T* __restrict__ f, T* __res
         restrict_pair<T, D>(X, r1, out);
         if (inb && lane >= H) VecIO<T, D>::store(fcc + q * D, out);
     }
+    coarse_tail_last_block<T, D>(ct);
 }
 
 // Levels l+1 and l at once on the way up: recompute level l's pre-smoothed
