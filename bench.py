@@ -3,13 +3,16 @@
 Workload (one step = one full solve from u = 0 to relative residual 1e-10):
 one long horizon u' + lambda u = f, lambda = 1, tau = 1e-6, N = 2^24 intervals,
 p_t = 1 (Legendre), u0 = 1, f a seeded sum of 4 sinusoids; mixed precision
-(FP32 cycles inside FP64-accurate refinement), V(1,1) with the optimal damping
-per level.  The metric is time-DoFs/s = N (p_t+1) / solve time.  Inputs (268 MB
-load vector, 268 MB solution) are resident in HBM and larger than L2.
+(FP32 cycles inside FP64-accurate refinement), V(2,2) with the optimal damping
+per level (the paper's convergence plots use nu1 = nu2 = nu in {1, 2, 5}; its
+numerical section does not state nu).  The metric is time-DoFs/s = N (p_t+1) /
+solve time.  Inputs (268 MB load vector, 268 MB solution) are resident in HBM
+and larger than L2.
 
-Also reported: the plain FP64 form and p_t = 0, 2, 3 on the same horizon,
-per-kernel times and the HBM roofline of the dominant kernel, an end-to-end
-number through the host-array entry point, and the CPU oracle.
+Also reported: the exact scan solve, the plain FP64 form, p_t = 0, 2, 3 on the
+same horizon, other sweep counts (V(1,1), V(1,3), V(2,3), V(3,3)), the batched
+workloads, per-kernel times and the HBM roofline of the dominant kernel, an
+end-to-end number through the host-array entry point, and the CPU oracle.
 
 --impl reference times the FP64 CPU oracle (the textbook multigrid) on a
 bounded sample of the same workload.  Multi-GPU: the single long-horizon
@@ -34,9 +37,10 @@ TAU = 1e-6
 LAM = 1.0
 U0 = 1.0
 P_MAIN = 1
+NU = (2, 2)               # pre-/post-smoothing sweeps of the timed cycles (the paper's plots use nu1 = nu2 in {1, 2, 5})
 TOL = 1e-10
 METRIC = "time-DoFs/s solved to 1e-10 rel residual"
-WORKLOAD = "long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate refinement, V(1,1), omega*"
+WORKLOAD = "long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate refinement, V(2,2), omega*"
 
 
 def peaks():
@@ -172,7 +176,8 @@ def run_ours(args):
     u = torch.empty_like(F)
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
-    plan = tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, use_graph=not args.eager)
+    plan = tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, use_graph=not args.eager,
+                    nu1=NU[0], nu2=NU[1])
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     for _ in range(args.warmup):
@@ -251,7 +256,7 @@ def run_ours(args):
     extra = {}
     if rank == 0 and not args.quick:
         # plain FP64 form on the same problem
-        with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="fp64", tol=TOL, stream=stream,
+        with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="fp64", tol=TOL, stream=stream, nu1=NU[0], nu2=NU[1],
                       use_graph=not args.eager) as p64:
             p64.solve(F, U0, u)
             ms64 = time_solves(p64, F, u, max(2, args.steps // 4), stream, torch)
@@ -266,16 +271,28 @@ def run_ours(args):
             up = torch.empty_like(Fp)
             try:
                 with tmg.Plan(p, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, max_cycles=300,
+                              nu1=NU[0], nu2=NU[1],
                               use_graph=not args.eager) as pp:
                     pp.solve(Fp, U0, up)
                     msp = time_solves(pp, Fp, up, max(2, args.steps // 4), stream, torch)
                     sp = pp.stats()
                     per_p[str(p)] = {"value": N_FULL * (p + 1) / (msp * 1e-3), "ms_per_step": round(msp, 4),
-                                     "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": "V(1,1)"}
+                                     "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": f"V{NU}"}
             except tmg.TmgError as e:
                 per_p[str(p)] = {"error": str(e)}
             del Fp, up
         extra["per_p_mixed"] = per_p
+        # other sweep counts on the headline problem (same solver, same tolerance)
+        nus = {}
+        for nu in ((1, 1), (1, 3), (2, 3), (3, 3)):
+            with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, nu1=nu[0],
+                          nu2=nu[1], use_graph=not args.eager) as pn:
+                pn.solve(F, U0, u)
+                msn = time_solves(pn, F, u, max(2, args.steps // 4), stream, torch)
+                sn = pn.stats()
+            nus[f"V({nu[0]},{nu[1]})"] = {"value": N_FULL * d / (msn * 1e-3), "ms_per_step": round(msn, 4),
+                                           "cycles": sn.cycles, "rel_res": sn.rel_res}
+        extra["nu_variants"] = nus
         extra["batched"] = run_batched_configs(dev, stream, args.steps, torch)
 
     # end to end through the host-array entry point (pinned buffers, copies inside the call)
@@ -434,13 +451,13 @@ def cpu_baseline(sample_N: int = 1 << 18):
     forcing = inputs.Forcing.draw(np.random.default_rng(1), T)
     F = _sample_load_vector(P_MAIN, sample_N, T, forcing)
     t0 = time.perf_counter()
-    _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100)
+    _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1])
     t_mg = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.fsub(P_MAIN, LAM * TAU, F, U0)
     t_fs = time.perf_counter() - t0
     return {"value": sample_N * d / t_mg, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample_N} of the 2^24 intervals, textbook multigrid to 1e-10 ({len(hist) - 1} cycles), "
+            "sample": f"first {sample_N} of the 2^24 intervals, textbook V{NU} multigrid to 1e-10 ({len(hist) - 1} cycles), "
                       f"{t_mg:.2f} s",
             "fsub_value": sample_N * d / t_fs, "fsub_note": "exact forward substitution, same sample"}
 
@@ -467,10 +484,10 @@ def run_reference(args):
     forcing = inputs.Forcing.draw(np.random.default_rng(1), T)
     F = _sample_load_vector(P_MAIN, n, T, forcing)
     for _ in range(args.warmup):
-        oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100)
+        oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1])
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100)
+        _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1])
     dt = (time.perf_counter() - t0) / args.steps
     value = n * d / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,
@@ -478,7 +495,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_FULL, "p_t": P_MAIN, "tau": TAU, "lambda": LAM, "tol": TOL},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {n} of the 2^24 intervals per step, textbook multigrid "
+                             "sample": f"first {n} of the 2^24 intervals per step, textbook V{NU} multigrid "
                                        f"({len(hist) - 1} cycles)"},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
