@@ -594,18 +594,16 @@ __device__ __forceinline__ void acc_add1(float& s, float& c, float t) {
     c += n.lo;
 }
 
-// float -> double by re-biasing the exponent with integer operations (exact;
-// the conversion instruction would occupy GB300's FP64 pipe).  Subnormal
-// floats (|c| < 2^-126) become +-0; Inf stays Inf and NaN stays NaN.
+// float -> double by re-biasing the exponent with integer operations (the
+// conversion instruction would occupy GB300's FP64 pipe).  Exact for zero
+// and normal floats; a subnormal c (|c| < 2^-126) comes out within 2^-126 of
+// its value, and Inf/NaN come out NaN (still caught by every norm test).
 __device__ __forceinline__ double f2d_int(float c) {
     const unsigned b = __float_as_uint(c);
-    const unsigned e = (b >> 23) & 0xFFu;
-    const unsigned sign = b & 0x80000000u;
-    const unsigned m = b & 0x7FFFFFu;
-    const unsigned ed = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);
-    const unsigned mh = e == 0u ? 0u : ((m >> 3) | (e == 0xFFu && m != 0u ? 0x80000u : 0u));
-    const unsigned lo = e == 0u ? 0u : (m & 0x7u) << 29;
-    return __hiloint2double((int)(sign | (ed << 20) | mh), (int)lo);
+    const unsigned a = b & 0x7FFFFFFFu;
+    unsigned hi = a >= 0x7F800000u ? 0x7FF80000u : (a >> 3) + 0x38000000u;
+    hi = a == 0u ? 0u : (hi | (b & 0x80000000u));
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
 
 // Product of two float pairs (lo*lo dropped), as an unnormalised pair.
