@@ -385,7 +385,8 @@ def run_batched_configs(dev, stream, steps, torch):
     u = torch.empty_like(f)
     res = {}
     for prec in ("mixed", "fp64"):
-        with tmg.Batch([p] * n, 1.0 / N, lam, N, precision=prec, tol=TOL, max_cycles=200, stream=stream) as B:
+        with tmg.Batch([p] * n, 1.0 / N, lam, N, precision=prec, tol=TOL, max_cycles=200, stream=stream,
+                       nu1=NU[0], nu2=NU[1]) as B:
             B.solve(f, u0, u)
             ms = _time_batch(B, f, u0, u, max(1, steps // 10) if prec == "mixed" else 1, stream, torch)
             cyc, rel, mx = B.stats()
@@ -410,7 +411,8 @@ def run_batched_configs(dev, stream, steps, torch):
     dofs = int((Nv * (pv + 1)).sum())
     res = {}
     for prec in ("mixed", "fp64"):
-        with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream) as B:
+        with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream,
+                       nu1=NU[0], nu2=NU[1]) as B:
             B.solve(f, u0, u)
             ms = _time_batch(B, f, u0, u, max(1, steps // 10), stream, torch)
             cyc, rel, mx = B.stats()
@@ -430,7 +432,8 @@ def run_batched_configs(dev, stream, steps, torch):
     u0 = torch.from_numpy(u0n).to(dev)
     y = torch.from_numpy(target).to(dev)
     u = torch.empty_like(f)
-    with tmg.Batch([p] * n, 1.0 / N, lamg, N, precision="mixed", tol=TOL, max_cycles=300, stream=stream) as B:
+    with tmg.Batch([p] * n, 1.0 / N, lamg, N, precision="mixed", tol=TOL, max_cycles=300, stream=stream,
+                   nu1=NU[0], nu2=NU[1]) as B:
         def step():
             B.solve(f, u0, u)
             e = u.view(n, N, p + 1).sum(dim=2)
@@ -451,7 +454,7 @@ def run_batched_configs(dev, stream, steps, torch):
     out["adjoint_4096x16384_p2"] = {"unit": "DoF/s (forward + adjoint)", "instances": n, "N": N, "p_t": p,
                                     "value": n * N * (p + 1) / (ms * 1e-3), "gradients_per_s": 1e3 / ms,
                                     "ms_per_step": round(ms, 3), "adjoint_max_cycles": int(mx),
-                                    "precision": "mixed"}
+                                    "precision": "mixed", "cycle": f"V{NU}"}
     del f, u, u0, y
     torch.cuda.empty_cache()
     return out

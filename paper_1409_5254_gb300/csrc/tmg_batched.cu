@@ -51,6 +51,8 @@ struct tmg_batch_group {
     cudaGraphExec_t gexec[2];
     unsigned long long cond[2];
     int last_status;
+    cudaStream_t s;      // the group's own stream: groups run concurrently
+    cudaEvent_t done;    // recorded on s after the group's last work of a call
 };
 
 struct tmg_batch {
@@ -65,6 +67,7 @@ struct tmg_batch {
     bool own_stream;
     int max_blocks;
     std::vector<tmg_batch_group*> groups;
+    cudaEvent_t fork;     // recorded on s at the start of a call; every group stream waits on it
     void* table;          // device copies of off, N (int64), tau (double), p (int) for the gradient kernel
     std::vector<int> cycles;
     std::vector<double> rel;
@@ -199,41 +202,41 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
     {
         const int H = halo(1 + sw_down(nu1));
         const int64_t nch = n * G->Ng / 2;
-        kb_down0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(
+        kb_down0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
             rT, L > 1 ? static_cast<T*>(G->fl[1]) : nullptr, nch, G->log2Ng, lk, G->res, L, X, nu1, H, G->st, G->bi);
     }
-    kb_finalize<<<grid_flat(B, n), kBNT, 0, B->s>>>(G->st, G->bi, n);
+    kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n);
     if (L == 1) {
-        kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, B->s>>>(rT, static_cast<T*>(G->c0), n, (int)G->Ng, lk,
+        kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(rT, static_cast<T*>(G->c0), n, (int)G->Ng, lk,
                                                                        L, 0, G->st, G->bi);
         // u += c; the instance of value i is i / (Ng D)
         const int64_t nv = n * G->Ng * D;
-        kb_update0<T, D><<<grid_flat(B, nv), kBNT, 0, B->s>>>(static_cast<const T*>(G->c0), nv,
+        kb_update0<T, D><<<grid_flat(B, nv), kBNT, 0, G->s>>>(static_cast<const T*>(G->c0), nv,
                                                                (int)(G->Ng * D), G->st, G->bi);
         return cudaGetLastError();
     }
     for (int l = 1; l < L - 1; ++l) {
         const int H = halo(sw_down(nu1));
         const int64_t nch = n * (G->Ng >> l) / 2;
-        kb_down<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(
+        kb_down<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
             static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 1]), nch, G->log2Ng - l, lk, L, l, X, nu1, H,
             G->st, G->bi);
     }
-    kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, B->s>>>(static_cast<const T*>(G->fl[L - 1]),
+    kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(static_cast<const T*>(G->fl[L - 1]),
                                                                    static_cast<T*>(G->ul[L - 1]), n,
                                                                    (int)(G->Ng >> (L - 1)), lk, L, L - 1, G->st,
                                                                    G->bi);
     for (int l = L - 2; l >= 1; --l) {
         const int H = halo(sw_up(nu1, nu2));
         const int64_t nch = n * (G->Ng >> l) / 2;
-        kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(
+        kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
             static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 1]), static_cast<T*>(G->ul[l]), nch,
             G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
     }
     {
         const int H = halo(sw_up(nu1, nu2));
         const int64_t nch = n * G->Ng / 2;
-        kb_up0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, B->s>>>(rT, static_cast<const T*>(G->ul[1]), nch,
+        kb_up0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(rT, static_cast<const T*>(G->ul[1]), nch,
                                                                      G->log2Ng, lk, L, X, nu1, nu2, H, G->st, G->bi);
     }
     return cudaGetLastError();
@@ -374,6 +377,16 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
         g_last_cuda_b = (int)e;
         return TMG_ENOMEM;
     }
+    e = cudaStreamCreateWithFlags(&G->s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        G->s = nullptr;
+        return fail(e);
+    }
+    e = cudaEventCreateWithFlags(&G->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        G->done = nullptr;
+        return fail(e);
+    }
     // constants (FP64 on the host, stored in the cycle precision)
     std::vector<char> tf, ta;
     std::vector<Res0> res;
@@ -416,12 +429,12 @@ tmg_status build_graph(tmg_batch* B, tmg_batch_group* G, int dir) {
         e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
     }
     if (e == cudaSuccess)
-        e = cudaStreamBeginCaptureToGraph(B->s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+        e = cudaStreamBeginCaptureToGraph(G->s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t ek = enqueue(B, G, dir);
         cudaGraph_t cap = nullptr;
-        e = cudaStreamEndCapture(B->s, &cap);
+        e = cudaStreamEndCapture(G->s, &cap);
         if (ek != cudaSuccess) e = ek;
     }
     cudaGraphExec_t ex = nullptr;
@@ -436,15 +449,15 @@ tmg_status build_graph(tmg_batch* B, tmg_batch_group* G, int dir) {
     return TMG_OK;
 }
 
-// One group solve on the group's current F/u/u0 arrays.
-tmg_status solve_group(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0, int dir) {
+// Start one group solve on the group's current F/u/u0 arrays, on the group's
+// stream (a graph launch; the eager form runs its cycles to the end here).
+tmg_status start_group(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0, int dir) {
     const int use_graph = B->o.use_graph != 0;
     if (use_graph && !G->gexec[dir]) {
         tmg_status s = build_graph(B, G, dir);
         if (s != TMG_OK) return s;
     }
-    TB_CUDA(cudaStreamSynchronize(B->s));
-    BatchState* h = G->st_host;
+    BatchState* h = G->st_host;   // its previous read-back finished in finish_group
     memset(h, 0, sizeof(BatchState));
     h->F = F;
     h->u = u;
@@ -453,26 +466,32 @@ tmg_status solve_group(tmg_batch* B, tmg_batch_group* G, const double* F, double
     h->max_cycles = B->o.max_cycles;
     h->use_cond = use_graph;
     h->cond = G->cond[dir];
-    TB_CUDA(cudaMemcpyAsync(G->st, h, sizeof(BatchState), cudaMemcpyHostToDevice, B->s));
-    kb_init<<<grid_flat(B, G->n), kBNT, 0, B->s>>>(G->bi, G->n);
+    TB_CUDA(cudaMemcpyAsync(G->st, h, sizeof(BatchState), cudaMemcpyHostToDevice, G->s));
+    kb_init<<<grid_flat(B, G->n), kBNT, 0, G->s>>>(G->bi, G->n);
     TB_CUDA(cudaGetLastError());
-    TB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * G->n * G->Ng * G->d, B->s));
+    TB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * G->n * G->Ng * G->d, G->s));
     if (use_graph) {
-        TB_CUDA(cudaGraphLaunch(G->gexec[dir], B->s));
+        TB_CUDA(cudaGraphLaunch(G->gexec[dir], G->s));
     } else {
         for (int k = 0; k <= B->o.max_cycles; k += 4) {
             for (int i = 0; i < 4; ++i) TB_CUDA(enqueue(B, G, dir));
-            TB_CUDA(cudaMemcpyAsync(&h->done, &G->st->done, sizeof(int), cudaMemcpyDeviceToHost, B->s));
-            TB_CUDA(cudaStreamSynchronize(B->s));
+            TB_CUDA(cudaMemcpyAsync(&h->done, &G->st->done, sizeof(int), cudaMemcpyDeviceToHost, G->s));
+            TB_CUDA(cudaStreamSynchronize(G->s));
             if (h->done) break;
         }
     }
-    TB_CUDA(cudaMemcpyAsync(h, G->st, sizeof(BatchState), cudaMemcpyDeviceToHost, B->s));
+    return TMG_OK;
+}
+
+// Read back a group's statistics (waits for the group's stream).
+tmg_status finish_group(tmg_batch* B, tmg_batch_group* G) {
+    BatchState* h = G->st_host;
+    TB_CUDA(cudaMemcpyAsync(h, G->st, sizeof(BatchState), cudaMemcpyDeviceToHost, G->s));
     std::vector<int> cyc(G->n);
     std::vector<double> rel(G->n);
-    TB_CUDA(cudaMemcpyAsync(cyc.data(), G->bi.cycles, 4 * G->n, cudaMemcpyDeviceToHost, B->s));
-    TB_CUDA(cudaMemcpyAsync(rel.data(), G->bi.rel, 8 * G->n, cudaMemcpyDeviceToHost, B->s));
-    TB_CUDA(cudaStreamSynchronize(B->s));
+    TB_CUDA(cudaMemcpyAsync(cyc.data(), G->bi.cycles, 4 * G->n, cudaMemcpyDeviceToHost, G->s));
+    TB_CUDA(cudaMemcpyAsync(rel.data(), G->bi.rel, 8 * G->n, cudaMemcpyDeviceToHost, G->s));
+    TB_CUDA(cudaStreamSynchronize(G->s));
     for (int64_t j = 0; j < G->n; ++j) {
         B->cycles[G->ids[j]] = cyc[j];
         B->rel[G->ids[j]] = rel[j];
@@ -504,6 +523,14 @@ tmg_status worst(tmg_status a, tmg_status b) {
 }
 
 bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// An error part-way through a call: wait for every group stream, so that no
+// work of this call is left running when the caller regains its buffers.
+tmg_status drain(tmg_batch* B, tmg_status s) {
+    for (tmg_batch_group* G : B->groups)
+        if (G->s) cudaStreamSynchronize(G->s);
+    return s;
+}
 
 }  // namespace
 
@@ -560,6 +587,12 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
         return fail(e);
     }
     B->max_blocks = nsm * 8;
+    e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        B->fork = nullptr;
+        tmg_destroy_batched(B);
+        return fail(e);
+    }
     // group by (p, padded length)
     std::map<std::pair<int, int64_t>, std::vector<int64_t>> key;
     for (int64_t i = 0; i < n_inst; ++i) {
@@ -620,24 +653,34 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
 
 tmg_status tmg_solve_batched(tmg_batch* B, const double* f, const double* u0, double* u) {
     if (!B || !aligned16(f) || !aligned16(u) || !u0 || (reinterpret_cast<uintptr_t>(u0) & 7u)) return TMG_EINVAL;
+    // fork: every group runs on its own stream after the caller's prior work
+    TB_CUDA(cudaEventRecord(B->fork, B->s));
     tmg_status st = TMG_OK;
     for (tmg_batch_group* G : B->groups) {
+        TB_CUDA(cudaStreamWaitEvent(G->s, B->fork, 0));
         tmg_status s;
         if (G->direct) {
-            s = solve_group(B, G, f, u, u0, 0);
+            s = start_group(B, G, f, u, u0, 0);
         } else {
             s = ensure_gather(G);
-            if (s != TMG_OK) return s;
+            if (s != TMG_OK) return drain(B, s);
             const int64_t nv = G->n * G->Ng * G->d;
-            kb_gather<<<grid_flat(B, nv), kBNT, 0, B->s>>>(f, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d,
+            kb_gather<<<grid_flat(B, nv), kBNT, 0, G->s>>>(f, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d,
                                                            0, u0, G->u0g);
             TB_CUDA(cudaGetLastError());
-            s = solve_group(B, G, G->Fg, G->ug, G->u0g, 0);
-            if (s != TMG_OK && s != TMG_ENOTCONV) return s;
-            kb_scatter<<<grid_flat(B, nv), kBNT, 0, B->s>>>(G->ug, u, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 0);
+            s = start_group(B, G, G->Fg, G->ug, G->u0g, 0);
+            if (s != TMG_OK) return drain(B, s);
+            kb_scatter<<<grid_flat(B, nv), kBNT, 0, G->s>>>(G->ug, u, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 0);
             TB_CUDA(cudaGetLastError());
         }
-        if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+        if (s != TMG_OK) return drain(B, s);
+        TB_CUDA(cudaEventRecord(G->done, G->s));
+    }
+    // join, then the statistics of every group
+    for (tmg_batch_group* G : B->groups) TB_CUDA(cudaStreamWaitEvent(B->s, G->done, 0));
+    for (tmg_batch_group* G : B->groups) {
+        tmg_status s = finish_group(B, G);
+        if (s != TMG_OK && s != TMG_ENOTCONV) return drain(B, s);
         st = worst(st, s);
     }
     TB_CUDA(cudaStreamSynchronize(B->s));
@@ -650,18 +693,26 @@ tmg_status tmg_adjoint_batched(tmg_batch* B, const double* g, const double* u, d
         (reinterpret_cast<uintptr_t>(dJdu0) & 7u) || (reinterpret_cast<uintptr_t>(dJdlambda) & 7u))
         return TMG_EINVAL;
     tmg_status st = TMG_OK;
+    TB_CUDA(cudaEventRecord(B->fork, B->s));
     for (tmg_batch_group* G : B->groups) {
+        TB_CUDA(cudaStreamWaitEvent(G->s, B->fork, 0));
         tmg_status s = ensure_gather(G);
-        if (s != TMG_OK) return s;
+        if (s != TMG_OK) return drain(B, s);
         const int64_t nv = G->n * G->Ng * G->d;
         // L^T mu = g in reversed time (causal there, so padding at the end stays exact)
-        kb_gather<<<grid_flat(B, nv), kBNT, 0, B->s>>>(g, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1,
+        kb_gather<<<grid_flat(B, nv), kBNT, 0, G->s>>>(g, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1,
                                                        nullptr, G->u0g);
         TB_CUDA(cudaGetLastError());
-        s = solve_group(B, G, G->Fg, G->ug, G->u0g, 1);
-        if (s != TMG_OK && s != TMG_ENOTCONV) return s;
-        kb_scatter<<<grid_flat(B, nv), kBNT, 0, B->s>>>(G->ug, dJdf, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1);
+        s = start_group(B, G, G->Fg, G->ug, G->u0g, 1);
+        if (s != TMG_OK) return drain(B, s);
+        kb_scatter<<<grid_flat(B, nv), kBNT, 0, G->s>>>(G->ug, dJdf, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1);
         TB_CUDA(cudaGetLastError());
+        TB_CUDA(cudaEventRecord(G->done, G->s));
+    }
+    for (tmg_batch_group* G : B->groups) TB_CUDA(cudaStreamWaitEvent(B->s, G->done, 0));
+    for (tmg_batch_group* G : B->groups) {
+        tmg_status s = finish_group(B, G);
+        if (s != TMG_OK && s != TMG_ENOTCONV) return drain(B, s);
         st = worst(st, s);
     }
     // per-instance gradients over the caller's layout
@@ -708,6 +759,11 @@ void tmg_destroy_batched(tmg_batch* B) {
             if (G->gexec[dir]) cudaGraphExecDestroy(G->gexec[dir]);
             if (G->graph[dir]) cudaGraphDestroy(G->graph[dir]);
         }
+        if (G->s) {
+            cudaStreamSynchronize(G->s);
+            cudaStreamDestroy(G->s);
+        }
+        if (G->done) cudaEventDestroy(G->done);
         if (G->ws) cudaFree(G->ws);
         if (G->st_host) cudaFreeHost(G->st_host);
         if (G->Fg) cudaFree(G->Fg);
@@ -716,6 +772,7 @@ void tmg_destroy_batched(tmg_batch* B) {
         delete G;
     }
     if (B->table) cudaFree(B->table);
+    if (B->fork) cudaEventDestroy(B->fork);
     if (B->own_stream) cudaStreamDestroy(B->s);
     delete B;
 }

@@ -82,6 +82,22 @@ def test_uneven_batch_matches_oracle(dev):
     check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
 
 
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3), (3, 1)])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_uneven_batch_other_sweep_counts(dev, nu, prec):
+    """The batched kernels with more smoothing sweeps (wider halos per tile):
+    every instance of an uneven batch against the oracle."""
+    from paper_1409_5254_gb300 import tmg
+    N, p, z = inputs.uneven_batch(7, 24, nmin_exp=3.0, nmax_exp=12.0)
+    Fs, u0, tau, lam = make_batch(7, p, N, z)
+    with tmg.Batch(p, tau, lam, N, precision=prec, tol=1e-10, max_cycles=300, nu1=nu[0], nu2=nu[1]) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+    assert (rel <= 1e-10).all()
+    check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
+
+
 def test_batch_of_one_matches_single_solve(dev):
     from paper_1409_5254_gb300 import tmg
     prob = inputs.scalar_problem(4, 4096, 2, lam=3.0, T=1.0, u0=0.5)
