@@ -411,14 +411,19 @@ def run_batched_configs(dev, stream, steps, torch):
     dofs = int((Nv * (pv + 1)).sum())
     res = {}
     for prec in ("mixed", "fp64"):
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter()
         with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream,
                        nu1=NU[0], nu2=NU[1]) as B:
+            setup_ms = (time.perf_counter() - t_setup) * 1e3
             B.solve(f, u0, u)
             ms = _time_batch(B, f, u0, u, max(1, steps // 10), stream, torch)
             cyc, rel, mx = B.stats()
             info = B.info()
+        kinds = [g["schedule"] for g in info["group_info"]]
         res[prec] = {"value": dofs / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
-                     "max_rel_res": float(rel.max())}
+                     "max_rel_res": float(rel.max()), "setup_ms_with_autotune": round(setup_ms, 1),
+                     "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid")}
     out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv), "dofs": dofs, "groups": info["groups"],
                            "padded_dofs": info["padded_values"], **res}
     del f, u, u0

@@ -84,7 +84,15 @@ typedef struct {
                            l+1 on the way down and up, level l+1 never stored; the way up
                            recomputes level l+1's right-hand side); 0: one level per
                            kernel; -1 (default): fuse when the cycle precision is FP32 */
+    int schedule;       /* batches: how each (p_t, length) group runs.  TMG_SCHED_AUTO
+                           (default): time both forms at setup on a synthetic problem and
+                           keep the faster; TMG_SCHED_GRID: level kernels over all instances
+                           of the group (graph loop); TMG_SCHED_CTA: one CTA per instance with
+                           the whole hierarchy in shared memory and all cycles in one launch
+                           (groups too large for one CTA fall back to the grid form) */
 } tmg_opts;
+
+enum { TMG_SCHED_AUTO = 0, TMG_SCHED_GRID = 1, TMG_SCHED_CTA = 2 };
 
 /* Fill *opts with the defaults listed above. */
 void tmg_opts_default(tmg_opts *opts);
@@ -263,6 +271,15 @@ tmg_status tmg_stats_batched(const tmg_batch *batch, int *cycles, double *rel_re
 
 /* Number of (p_t, padded length) groups and the padded number of values. */
 tmg_status tmg_batch_info(const tmg_batch *batch, int *n_groups, int64_t *padded_values);
+
+/*
+ * Group g (0 <= g < n_groups): degree, padded length, instances, the schedule
+ * it runs (TMG_SCHED_GRID or TMG_SCHED_CTA), and the milliseconds the setup
+ * autotuner measured for one synthetic solve in each form (NAN where a form
+ * was not timed).  Any output pointer may be NULL.
+ */
+tmg_status tmg_batch_group_info(const tmg_batch *batch, int g, int *p_t, int64_t *padded_length,
+                                int64_t *n_instances, int *schedule, double *ms_grid, double *ms_cta);
 
 void tmg_destroy_batched(tmg_batch *batch);
 

@@ -191,6 +191,7 @@ void tmg_opts_default(tmg_opts* o) {
     o->use_pdl = 1;
     o->update_residual = 1;
     o->fuse_levels = -1;
+    o->schedule = TMG_SCHED_AUTO;
 }
 
 tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_t N, int levels, double omega,

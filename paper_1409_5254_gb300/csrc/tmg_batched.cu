@@ -53,6 +53,10 @@ struct tmg_batch_group {
     int last_status;
     cudaStream_t s;      // the group's own stream: groups run concurrently
     cudaEvent_t done;    // recorded on s after the group's last work of a call
+    bool cta_ok;         // the CTA-per-instance form fits in one CTA's shared memory
+    size_t cta_smem;
+    int sched;           // TMG_SCHED_GRID or TMG_SCHED_CTA
+    double ms_tune[2];   // autotuner: one synthetic solve, grid form and CTA form (NAN: not timed)
 };
 
 struct tmg_batch {
@@ -258,6 +262,58 @@ cudaError_t enqueue(tmg_batch* B, tmg_batch_group* G, int dir) {
     return dir == 0 ? enqueue_cycle_d<double, 0>(B, G) : enqueue_cycle_d<double, 1>(B, G);
 }
 
+// Shared-memory ceiling of the CTA-per-instance form.
+constexpr size_t kCtaSmemMax = 200 * 1024;
+
+template <typename T, int D, int DIR>
+cudaError_t launch_cta(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0) {
+    Xfer<T, D> X;
+    double P1[16], P2[16];
+    tmg_host::transfer_setup(D, P1, P2);
+    for (int i = 0; i < D * D; ++i) {   // reversed time swaps the halves
+        X.P1[i] = (T)(DIR == 0 ? P1[i] : P2[i]);
+        X.P2[i] = (T)(DIR == 0 ? P2[i] : P1[i]);
+    }
+    static const cudaError_t attr = cudaFuncSetAttribute(kb_cta_solve<DIR, T, D>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmemMax);
+    if (attr != cudaSuccess) return attr;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_cta_solve<DIR, T, D>, kTailNT, G->cta_smem);
+    if (e != cudaSuccess) return e;
+    const int64_t wave = (int64_t)(B->max_blocks / 8) * (occ > 0 ? occ : 1);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(G->n, wave));
+    kb_cta_solve<DIR, T, D><<<grid, kTailNT, G->cta_smem, G->s>>>(
+        F, u, u0, G->n, (int)G->Ng, G->nlev, static_cast<const LevelK<T, D>*>(G->lk[DIR]), G->res, X, B->o.nu1,
+        B->o.nu2, B->o.gamma, G->st, G->bi);
+    return cudaGetLastError();
+}
+
+template <typename T, int DIR>
+cudaError_t launch_cta_d(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0) {
+    switch (G->d) {
+        case 1: return launch_cta<T, 1, DIR>(B, G, F, u, u0);
+        case 2: return launch_cta<T, 2, DIR>(B, G, F, u, u0);
+        case 3: return launch_cta<T, 3, DIR>(B, G, F, u, u0);
+        default: return launch_cta<T, 4, DIR>(B, G, F, u, u0);
+    }
+}
+
+cudaError_t launch_cta_any(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0, int dir) {
+    if (B->o.precision == TMG_MIXED)
+        return dir == 0 ? launch_cta_d<float, 0>(B, G, F, u, u0) : launch_cta_d<float, 1>(B, G, F, u, u0);
+    return dir == 0 ? launch_cta_d<double, 0>(B, G, F, u, u0) : launch_cta_d<double, 1>(B, G, F, u, u0);
+}
+
+size_t cta_bytes(const tmg_batch* B, const tmg_batch_group* G) {
+    const bool mixed = B->o.precision == TMG_MIXED;
+    switch (G->d) {
+        case 1: return mixed ? cta_smem_bytes<float, 1>(G->Ng, G->nlev) : cta_smem_bytes<double, 1>(G->Ng, G->nlev);
+        case 2: return mixed ? cta_smem_bytes<float, 2>(G->Ng, G->nlev) : cta_smem_bytes<double, 2>(G->Ng, G->nlev);
+        case 3: return mixed ? cta_smem_bytes<float, 3>(G->Ng, G->nlev) : cta_smem_bytes<double, 3>(G->Ng, G->nlev);
+        default: return mixed ? cta_smem_bytes<float, 4>(G->Ng, G->nlev) : cta_smem_bytes<double, 4>(G->Ng, G->nlev);
+    }
+}
+
 template <typename T, int D>
 void fill_tables(const tmg_batch* B, const tmg_batch_group* G, std::vector<char>& fwd, std::vector<char>& adj,
                  std::vector<Res0>& res) {
@@ -304,6 +360,10 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     G->nlev = 1;
     for (int64_t m = G->Ng; m > nmin && m % 2 == 0 && G->nlev < kMaxLevels; m /= 2) ++G->nlev;
     if ((G->Ng >> (G->nlev - 1)) > 64) return TMG_EUNSUPPORTED;
+    G->cta_smem = cta_bytes(B, G);
+    G->cta_ok = G->cta_smem <= kCtaSmemMax;
+    G->sched = B->o.schedule == TMG_SCHED_CTA && G->cta_ok ? TMG_SCHED_CTA : TMG_SCHED_GRID;
+    G->ms_tune[0] = G->ms_tune[1] = NAN;
     // layout
     const size_t A = 256;
     const int64_t n = G->n, nvals = n * G->Ng * G->d;
@@ -452,7 +512,21 @@ tmg_status build_graph(tmg_batch* B, tmg_batch_group* G, int dir) {
 // Start one group solve on the group's current F/u/u0 arrays, on the group's
 // stream (a graph launch; the eager form runs its cycles to the end here).
 tmg_status start_group(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0, int dir) {
-    const int use_graph = B->o.use_graph != 0;
+    const int use_graph = B->o.use_graph != 0 && G->sched == TMG_SCHED_GRID;
+    if (G->sched == TMG_SCHED_CTA) {
+        BatchState* h = G->st_host;
+        memset(h, 0, sizeof(BatchState));
+        h->F = F;
+        h->u = u;
+        h->u0 = u0;
+        h->tol = B->o.tol;
+        h->max_cycles = B->o.max_cycles;
+        TB_CUDA(cudaMemcpyAsync(G->st, h, sizeof(BatchState), cudaMemcpyHostToDevice, G->s));
+        kb_init<<<grid_flat(B, G->n), kBNT, 0, G->s>>>(G->bi, G->n);
+        TB_CUDA(cudaGetLastError());
+        TB_CUDA(launch_cta_any(B, G, F, u, u0, dir));
+        return TMG_OK;
+    }
     if (use_graph && !G->gexec[dir]) {
         tmg_status s = build_graph(B, G, dir);
         if (s != TMG_OK) return s;
@@ -524,6 +598,49 @@ tmg_status worst(tmg_status a, tmg_status b) {
 
 bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The setup autotuner: for every group that fits one CTA per instance, time
+// one solve of a synthetic problem (f = 0, u0 = 1: each instance a decaying
+// mode) in each form on the group's own scratch arrays, after one untimed
+// solve that builds the form's graph or loads its kernel, and keep the faster.
+tmg_status autotune(tmg_batch* B) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TB_CUDA(cudaEventCreate(&e0));
+    TB_CUDA(cudaEventCreate(&e1));
+    tmg_status out = TMG_OK;
+    for (tmg_batch_group* G : B->groups) {
+        if (!G->cta_ok) continue;
+        tmg_status s = ensure_gather(G);
+        if (s != TMG_OK) {
+            out = s;
+            break;
+        }
+        std::vector<double> ones(G->n, 1.0);
+        cudaError_t e = cudaMemsetAsync(G->Fg, 0, sizeof(double) * G->n * G->Ng * G->d, G->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(G->u0g, ones.data(), 8 * G->n, cudaMemcpyHostToDevice, G->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(G->s);
+        if (e != cudaSuccess) {
+            out = fail(e);
+            break;
+        }
+        for (int form = 0; form < 2 && out == TMG_OK; ++form) {
+            G->sched = form == 0 ? TMG_SCHED_GRID : TMG_SCHED_CTA;
+            for (int rep = 0; rep < 2 && out == TMG_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, G->s);
+                s = start_group(B, G, G->Fg, G->ug, G->u0g, 0);
+                if (s == TMG_OK && rep == 1) cudaEventRecord(e1, G->s);
+                if (s == TMG_OK) s = finish_group(B, G);
+                if (s != TMG_OK && s != TMG_ENOTCONV) out = s;
+            }
+            float ms = NAN;
+            if (out == TMG_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) G->ms_tune[form] = ms;
+        }
+        G->sched = G->ms_tune[1] < G->ms_tune[0] ? TMG_SCHED_CTA : TMG_SCHED_GRID;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return out;
+}
+
 // An error part-way through a call: wait for every group stream, so that no
 // work of this call is left running when the caller regains its buffers.
 tmg_status drain(tmg_batch* B, tmg_status s) {
@@ -545,6 +662,7 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
     tmg_opts_default(&o);
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 || o.gamma != 1 ||
+        o.schedule < TMG_SCHED_AUTO || o.schedule > TMG_SCHED_CTA ||
         (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 || o.max_cycles < 0 ||
         !(o.tol >= 0.0))
         return TMG_EINVAL;
@@ -647,6 +765,13 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
         for (int64_t i = 0; i < n_inst; ++i) unpadded = unpadded && N[i] == B->groups[0]->Ng;
         B->groups[0]->direct = unpadded;
     }
+    if (o.schedule == TMG_SCHED_AUTO) {
+        tmg_status s = autotune(B);
+        if (s != TMG_OK) {
+            tmg_destroy_batched(B);
+            return s;
+        }
+    }
     *out = B;
     return TMG_OK;
 }
@@ -748,6 +873,19 @@ tmg_status tmg_batch_info(const tmg_batch* B, int* n_groups, int64_t* padded_val
         for (auto* G : B->groups) t += G->n * G->Ng * G->d;
         *padded_values = t;
     }
+    return TMG_OK;
+}
+
+tmg_status tmg_batch_group_info(const tmg_batch* B, int g, int* p_t, int64_t* padded_length, int64_t* n_instances,
+                                int* schedule, double* ms_grid, double* ms_cta) {
+    if (!B || g < 0 || g >= (int)B->groups.size()) return TMG_EINVAL;
+    const tmg_batch_group* G = B->groups[g];
+    if (p_t) *p_t = G->p;
+    if (padded_length) *padded_length = G->Ng;
+    if (n_instances) *n_instances = G->n;
+    if (schedule) *schedule = G->sched;
+    if (ms_grid) *ms_grid = G->ms_tune[0];
+    if (ms_cta) *ms_cta = G->ms_tune[1];
     return TMG_OK;
 }
 

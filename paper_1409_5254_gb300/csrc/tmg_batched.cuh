@@ -360,3 +360,117 @@ __global__ void __launch_bounds__(kBNT) kb_update0(const T* __restrict__ c, int6
 }
 
 }  // namespace tmg
+
+namespace tmg {
+
+// ------------------------------------------- one CTA per small instance --
+//
+// The whole solve of one instance in one CTA's shared memory: F and u in
+// FP64, the cycle's level hierarchy in the cycle precision (the on-chip
+// solver's layout, tail_view), every cycle in the same launch.  Per cycle:
+// r = F - L u in FP64 and its norm (block reduction), the stopping test, one
+// cycle on L c = r from a zero start (tail_cycle), u += c in FP64.  Blocks
+// loop over the instances; the last block to finish sets the group's state.
+
+// Shared memory of the CTA form for a padded length Ng and nlev levels.
+template <typename T, int D>
+inline size_t cta_smem_bytes(int64_t Ng, int nlev) {
+    return (size_t)2 * Ng * D * sizeof(double) + 32 * sizeof(double) + tail_smem_bytes<T, D>(Ng, nlev);
+}
+
+// Sum of v over the block, returned to every thread.
+__device__ __forceinline__ double block_sum_all(double v, double* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(kFull, v, off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();   // red may still be read from the previous call
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    return t;
+}
+
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kTailNT) kb_cta_solve(const double* __restrict__ F, double* __restrict__ u,
+                                                        const double* __restrict__ u0, int64_t n_inst, int Ng,
+                                                        int nlev, const LevelK<T, D>* __restrict__ lk,
+                                                        const Res0* __restrict__ res, Xfer<T, D> X, int nu1, int nu2,
+                                                        int gamma, BatchState* st, BatchInst bi) {
+    extern __shared__ __align__(16) unsigned char cta_smem[];
+    double* Fs = reinterpret_cast<double*>(cta_smem);
+    double* us = Fs + (int64_t)Ng * D;
+    double* red = us + (int64_t)Ng * D;
+    const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(red + 32), Ng, nlev);
+    const int64_t nv = (int64_t)Ng * D;
+    const double tol = st->tol;
+    const int max_cycles = st->max_cycles;
+    int failed = 0;
+    for (int64_t inst = blockIdx.x; inst < n_inst; inst += gridDim.x) {
+        const LevelK<T, D>* lki = lk + inst * nlev;
+        const Res0 R = res[inst];
+        const double u0i = u0[inst];
+        for (int64_t i = threadIdx.x; i < nv; i += kTailNT) {
+            Fs[i] = F[inst * nv + i];
+            us[i] = 0.0;
+        }
+        __syncthreads();
+        double nF = 0.0, rel = 0.0;
+        int k = 0;
+        while (true) {
+            double ss = 0.0;
+            for (int64_t n = threadIdx.x; n < Ng; n += kTailNT) {
+                double uv[D], Fv[D], r[D];
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    uv[q] = us[n * D + q];
+                    Fv[q] = Fs[n * D + q];
+                }
+                double ep = u0i;
+                if (n > 0) {
+                    double up[D];
+#pragma unroll
+                    for (int q = 0; q < D; ++q) up[q] = us[(n - 1) * D + q];
+                    ep = bval<DIR, double, D>(up);
+                }
+                residual0<DIR, D>(Fv, uv, ep, endval<double, D>(uv), R, r);
+#pragma unroll
+                for (int q = 0; q < D; ++q) {
+                    V.f[0][n * D + q] = (T)r[q];
+                    ss = fma(r[q], r[q], ss);
+                }
+            }
+            const double nrm = sqrt(block_sum_all(ss, red));   // ends synchronised: V.f[0] complete
+            if (k == 0) nF = nrm;
+            rel = nF > 0.0 ? nrm / nF : nrm;
+            if (!(rel == rel) || rel > 1.0e300 || rel <= tol || k >= max_cycles) break;
+            tail_cycle<DIR, T, D>(V, lki, X, nlev, nu1, nu2, gamma);
+            for (int64_t i = threadIdx.x; i < nv; i += kTailNT) us[i] += (double)V.u[0][i];
+            __syncthreads();
+            ++k;
+        }
+        for (int64_t i = threadIdx.x; i < nv; i += kTailNT) u[inst * nv + i] = us[i];
+        if (threadIdx.x == 0) {
+            bi.cycles[inst] = k;
+            bi.rel[inst] = rel;
+            bi.active[inst] = 0;
+            if (!(rel <= tol)) ++failed;
+        }
+        __syncthreads();
+    }
+    // the last block to finish records the outcome of the group
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        if (failed) atomicAdd(&st->failed, failed);
+        __threadfence();
+        last = atomicAdd(&st->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        st->ticket = 0u;
+        st->done = atomicAdd(&st->failed, 0) ? 2 : 1;
+    }
+}
+
+}  // namespace tmg

@@ -1602,20 +1602,11 @@ __device__ void tail_exact(const LevelK<T, D>& K, const T* f, T* u, T* scanA, T*
     __syncthreads();
 }
 
-// The coarse part of the cycle, levels lt..lt+nl-1 (tail index j = l - lt),
-// entirely in shared memory: V (gamma = 1) or W (gamma = 2) recursion written
-// as a loop; coarsest tail level solved exactly.  f_in is the right-hand side
-// of level lt, u_out receives its correction.
-template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T* __restrict__ u_out,
-                                                  const LevelK<T, D>* __restrict__ lk, Xfer<T, D> X, int nl,
-                                                  int64_t Nt, int nu1, int nu2, int gamma,
-                                                  const DevState* __restrict__ st) {
-    pdl_enter();
-    if (st != nullptr && st->done) return;
-    extern __shared__ __align__(16) unsigned char tail_smem[];
+// Carve the shared-memory image of nl levels starting with Nt intervals out
+// of p (layout of tail_smem_bytes).
+template <typename T, int D>
+__device__ __forceinline__ TailView<T, D> tail_view(T* p, int64_t Nt, int nl) {
     TailView<T, D> V;
-    T* p = reinterpret_cast<T*>(tail_smem);
     for (int j = 0; j < nl; ++j) {
         V.N[j] = Nt >> j;
         V.f[j] = p;
@@ -1632,10 +1623,17 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
     V.scanA = p;
     p += kTailNT / 32;
     V.scanB = p;
+    return V;
+}
 
-    for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) V.f[0][i] = f_in[i];
-    __syncthreads();
-
+// One cycle on the levels held in V (tail index j = 0..nl-1), from a zero
+// start: V (gamma = 1) or W (gamma = 2) recursion written as a loop, the
+// coarsest level solved exactly.  V.f[0] holds the right-hand side, V.u[0]
+// receives the correction.  lk[j] are the constants of tail level j.  All
+// threads of the CTA take part; ends with the block synchronised.
+template <int DIR, typename T, int D>
+__device__ void tail_cycle(const TailView<T, D>& V, const LevelK<T, D>* __restrict__ lk, const Xfer<T, D>& X, int nl,
+                           int nu1, int nu2, int gamma) {
     int visits[kMaxLevels];
     bool has_init[kMaxLevels];
     for (int j = 0; j < nl; ++j) {
@@ -1725,6 +1723,23 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
         if (j == 0) break;
         --j;
     }
+}
+
+// The coarse part of the cycle, levels lt..lt+nl-1 (tail index j = l - lt),
+// entirely in shared memory (tail_cycle).  f_in is the right-hand side of
+// level lt, u_out receives its correction.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T* __restrict__ u_out,
+                                                  const LevelK<T, D>* __restrict__ lk, Xfer<T, D> X, int nl,
+                                                  int64_t Nt, int nu1, int nu2, int gamma,
+                                                  const DevState* __restrict__ st) {
+    pdl_enter();
+    if (st != nullptr && st->done) return;
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(tail_smem), Nt, nl);
+    for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) V.f[0][i] = f_in[i];
+    __syncthreads();
+    tail_cycle<DIR, T, D>(V, lk, X, nl, nu1, nu2, gamma);
     for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) u_out[i] = V.u[0][i];
 }
 

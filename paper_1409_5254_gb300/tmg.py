@@ -16,6 +16,7 @@ from . import build_ext
 
 TMG_OK, TMG_EINVAL, TMG_ENOMEM, TMG_ECUDA, TMG_ENOTCONV, TMG_ENUMERIC, TMG_ETIMEOUT, TMG_EUNSUPPORTED = range(8)
 FP64, MIXED = 0, 1
+SCHED_AUTO, SCHED_GRID, SCHED_CTA = 0, 1, 2
 _PREC = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}
 
 
@@ -33,7 +34,7 @@ class _Opts(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
                 ("n_min", ctypes.c_int64), ("use_graph", ctypes.c_int), ("initial_guess", ctypes.c_int),
                 ("tail_cap", ctypes.c_int64), ("use_pdl", ctypes.c_int), ("update_residual", ctypes.c_int),
-                ("fuse_levels", ctypes.c_int)]
+                ("fuse_levels", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 _LIB = None
@@ -43,7 +44,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
            "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
-           "tmg_stats_batched", "tmg_batch_info", "tmg_destroy_batched"]
+           "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_destroy_batched"]
 
 
 def library_path() -> str:
@@ -85,10 +86,11 @@ def _lib():
         L.tmg_adjoint_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.tmg_stats_batched.argtypes = [_vp, _ip, _dp, _ip]
         L.tmg_batch_info.argtypes = [_vp, _ip, _lp]
+        L.tmg_batch_group_info.argtypes = [_vp, ctypes.c_int, _ip, _lp, _lp, _ip, _dp, _dp]
         L.tmg_destroy_batched.argtypes = [_vp]
         L.tmg_destroy_batched.restype = None
         for name in ("tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched", "tmg_stats_batched",
-                     "tmg_batch_info"):
+                     "tmg_batch_info", "tmg_batch_group_info"):
             getattr(L, name).restype = ctypes.c_int
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
@@ -376,7 +378,18 @@ class Batch:
         ng = ctypes.c_int(0)
         pv = ctypes.c_int64(0)
         _check(_lib().tmg_batch_info(self._h, ctypes.byref(ng), ctypes.byref(pv)), "tmg_batch_info")
-        return {"groups": ng.value, "padded_values": pv.value}
+        groups = []
+        for g in range(ng.value):
+            p, sch = ctypes.c_int(0), ctypes.c_int(0)
+            Ng, n = ctypes.c_int64(0), ctypes.c_int64(0)
+            mg, mc = ctypes.c_double(0), ctypes.c_double(0)
+            _check(_lib().tmg_batch_group_info(self._h, g, ctypes.byref(p), ctypes.byref(Ng), ctypes.byref(n),
+                                               ctypes.byref(sch), ctypes.byref(mg), ctypes.byref(mc)),
+                   "tmg_batch_group_info")
+            groups.append({"p_t": p.value, "padded_length": Ng.value, "instances": n.value,
+                           "schedule": {1: "grid", 2: "cta"}.get(sch.value, "?"), "ms_grid": mg.value,
+                           "ms_cta": mc.value})
+        return {"groups": ng.value, "padded_values": pv.value, "group_info": groups}
 
     def split(self, x):
         """Per-instance views (N_i, p_i + 1) of a packed host array."""

@@ -98,6 +98,69 @@ def test_uneven_batch_other_sweep_counts(dev, nu, prec):
     check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("schedule", ["cta", "grid", "auto"])
+def test_schedules_match_oracle(dev, prec, schedule):
+    """The two batched schedules -- level kernels over a whole group, or one
+    CTA per instance with its hierarchy in shared memory and every cycle in one
+    launch -- and the setup autotuner that picks between them, on an uneven
+    batch of small and large instances; every instance against the oracle."""
+    from paper_1409_5254_gb300 import tmg
+    N, p, z = inputs.uneven_batch(11, 40, nmin_exp=2.0, nmax_exp=13.0)
+    Fs, u0, tau, lam = make_batch(11, p, N, z)
+    sched = {"auto": tmg.SCHED_AUTO, "grid": tmg.SCHED_GRID, "cta": tmg.SCHED_CTA}[schedule]
+    with tmg.Batch(p, tau, lam, N, precision=prec, tol=1e-10, max_cycles=300, schedule=sched, nu1=2, nu2=2) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+        info = B.info()
+    assert (rel <= 1e-10).all()
+    check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
+    kinds = [g["schedule"] for g in info["group_info"]]
+    small = [g for g in info["group_info"] if g["padded_length"] <= 256]
+    assert small, info
+    if schedule == "grid":
+        assert set(kinds) == {"grid"}
+    elif schedule == "cta":
+        assert all(g["schedule"] == "cta" for g in small)
+    else:
+        # every group that fits one CTA was timed both ways and runs the faster form
+        for g in small:
+            assert np.isfinite(g["ms_grid"]) and np.isfinite(g["ms_cta"])
+            assert g["schedule"] == ("cta" if g["ms_cta"] < g["ms_grid"] else "grid")
+    print(schedule, prec, [(g["p_t"], g["padded_length"], g["schedule"], round(g["ms_grid"], 3),
+                            round(g["ms_cta"], 3)) for g in info["group_info"]])
+
+
+def test_cta_schedule_adjoint_matches_oracle(dev):
+    """Gradients through the CTA-per-instance schedule (reversed-time solves)."""
+    from paper_1409_5254_gb300 import tmg
+    N, p, z = inputs.uneven_batch(12, 16, nmin_exp=4.0, nmax_exp=10.0)
+    Fs, u0, tau, lam = make_batch(12, p, N, z)
+    rng = np.random.default_rng(3)
+    with tmg.Batch(p, tau, lam, N, precision="mixed", tol=1e-10, max_cycles=300, schedule=tmg.SCHED_CTA) as B:
+        assert all(g["schedule"] == "cta" for g in B.info()["group_info"])
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        us = B.split(u.cpu().numpy())
+        gs = []
+        for i in range(len(p)):
+            _, _, _, b = O.blocks(int(p[i]))
+            gs.append(np.outer(O.nodal_values(int(p[i]), us[i]) - rng.standard_normal(int(N[i])), b))
+        g = torch.from_numpy(np.concatenate([x.reshape(-1) for x in gs])).to(dev)
+        dJdf, du0, dlam = B.adjoint(g, u)
+    mus = B.split(dJdf.cpu().numpy())
+    du0, dlam = du0.cpu().numpy(), dlam.cpu().numpy()
+    for i in range(len(p)):
+        zi = lam[i] * tau[i]
+        allow = 2.0 * max(N[i], 1.0 / zi) * 1e-10 * 10
+        mu_ref = O.adj_sweep(int(p[i]), zi, gs[i])
+        assert np.abs(mus[i] - mu_ref).max() <= allow * np.abs(mu_ref).max(), i
+        _, d0, dl = O.adjoint_grads(int(p[i]), lam[i], tau[i], gs[i], us[i])
+        assert du0[i] == pytest.approx(d0, rel=allow, abs=1e-12)
+        assert dlam[i] == pytest.approx(dl, rel=allow, abs=1e-12)
+
+
 def test_batch_of_one_matches_single_solve(dev):
     from paper_1409_5254_gb300 import tmg
     prob = inputs.scalar_problem(4, 4096, 2, lam=3.0, T=1.0, u0=0.5)
