@@ -38,6 +38,7 @@ struct tmg_batch_group {
     Res0* res;
     void* lk[2];         // LevelK table [n][nlev], per direction
     void* rT;
+    void* rl;            // updated-residual form: low parts of the residual pairs (two buffers), else nullptr
     void* fl[kMaxLevels];
     void* ul[kMaxLevels];
     void* c0;
@@ -120,6 +121,8 @@ __global__ void kb_init(BatchInst bi, int64_t n) {
         bi.norm2[i] = 0.0;
         bi.cycles[i] = 0;
         bi.rel[i] = NAN;
+        bi.full[i] = 1;
+        bi.nscale[i] = 1.0f;
     }
 }
 
@@ -203,13 +206,16 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
     T* rT = static_cast<T*>(G->rT);
     const int64_t n = G->n;
     const int L = G->nlev;
+    // mixed form with the level-0 residual kept as updated float pairs
+    short* rl = std::is_same<T, float>::value ? static_cast<short*>(G->rl) : nullptr;
     {
         const int H = halo(1 + sw_down(nu1));
         const int64_t nch = n * G->Ng / 2;
         kb_down0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
-            rT, L > 1 ? static_cast<T*>(G->fl[1]) : nullptr, nch, G->log2Ng, lk, G->res, L, X, nu1, H, G->st, G->bi);
+            rT, rl, L > 1 ? static_cast<T*>(G->fl[1]) : nullptr, nch, G->log2Ng, lk, G->res, L, X, nu1, H, G->st,
+            G->bi);
     }
-    kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n);
+    kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n, rl != nullptr ? kFinFull : kFinPlain);
     if (L == 1) {
         kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(rT, static_cast<T*>(G->c0), n, (int)G->Ng, lk,
                                                                        L, 0, G->st, G->bi);
@@ -236,6 +242,17 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
         kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
             static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 1]), static_cast<T*>(G->ul[l]), nch,
             G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (rl != nullptr) {
+            const int H = halo(sw_up(nu1, nu2) + 1 + sw_down(nu1));
+            const int64_t nch = n * G->Ng / 2;
+            kb_updown0<DIR, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+                rT, rl, static_cast<const float*>(G->ul[1]), static_cast<float*>(G->fl[1]), nch, G->log2Ng, lk,
+                G->res, L, X, nu1, nu2, H, G->st, G->bi);
+            kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n, kFinUpdated);
+            return cudaGetLastError();
+        }
     }
     {
         const int H = halo(sw_up(nu1, nu2));
@@ -380,6 +397,10 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     off = align_up(off + 4 * n, A);
     const size_t o_rel = off;
     off = align_up(off + 8 * n, A);
+    const size_t o_full = off;
+    off = align_up(off + 4 * n, A);
+    const size_t o_nsc = off;
+    off = align_up(off + 4 * n, A);
     const size_t o_res = off;
     off = align_up(off + sizeof(Res0) * n, A);
     const size_t lk_bytes = (B->o.precision == TMG_MIXED ? sizeof(LevelK<float, 4>) : sizeof(LevelK<double, 4>)) *
@@ -388,8 +409,13 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     off = align_up(off + lk_bytes, A);
     const size_t o_lk1 = off;
     off = align_up(off + lk_bytes, A);
+    // the mixed form keeps the level-0 residual as updated float pairs, double
+    // buffered (high parts here, 16-bit low parts in rl) when it has coarse levels
+    const bool updated = B->o.precision == TMG_MIXED && B->o.update_residual != 0 && G->nlev > 1;
     const size_t o_rT = off;
-    off = align_up(off + el * nvals, A);
+    off = align_up(off + el * nvals * (updated ? 2 : 1), A);
+    const size_t o_rl = off;
+    if (updated) off = align_up(off + sizeof(short) * nvals * 2, A);
     size_t o_f[kMaxLevels], o_u[kMaxLevels];
     for (int l = 1; l < G->nlev; ++l) {
         o_f[l] = off;
@@ -419,10 +445,14 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     G->bi.active = reinterpret_cast<int*>(b + o_act);
     G->bi.cycles = reinterpret_cast<int*>(b + o_cyc);
     G->bi.rel = reinterpret_cast<double*>(b + o_rel);
+    G->bi.full = reinterpret_cast<int*>(b + o_full);
+    G->bi.nscale = reinterpret_cast<float*>(b + o_nsc);
+    G->bi.nvals_per_inst = (long long)G->Ng * G->d;
     G->res = reinterpret_cast<Res0*>(b + o_res);
     G->lk[0] = b + o_lk0;
     G->lk[1] = b + o_lk1;
     G->rT = b + o_rT;
+    G->rl = updated ? b + o_rl : nullptr;
     for (int l = 1; l < G->nlev; ++l) {
         G->fl[l] = b + o_f[l];
         G->ul[l] = b + o_u[l];

@@ -32,6 +32,7 @@ struct BatchState {
     unsigned ticket;
     int active_count;
     int failed;               // instances stopped by the cycle limit or a non-finite norm
+    int rsel;                 // updated-residual form: buffer holding the current residual pairs
     unsigned long long cond;
 };
 
@@ -41,6 +42,9 @@ struct BatchInst {
     int* active;      // 1 while instance i iterates
     int* cycles;      // cycles applied when instance i stopped
     double* rel;      // its final relative residual
+    long long nvals_per_inst;   // values per instance and level-0 vector, N * D
+    int* full;        // updated-residual form: 1 = recompute instance i's residual from u next
+    float* nscale;    // power of two bringing instance i's residual near 1 (FP32 norms)
 };
 
 // Segmented warp sum of v over lanes with the same instance id (ids are
@@ -64,12 +68,23 @@ constexpr int kBNT = 256;
 // Level 0: residual of every active instance (float pairs for the mixed form,
 // FP64 otherwise), norms, r stored in T, zero-start pre-smoothing and
 // restriction onto level 1 (fc == nullptr when level 0 is the coarsest).
+//
+// With rlo != nullptr (mixed form with an updated residual) only instances
+// whose flag full[i] is set are processed (the start of the solve, and
+// confirmations), and the residual is stored as a float pair (rT, rlo; low
+// parts encoded by lo_encode) into buffer st->rsel of two (nchunks * 2 * D
+// values each).
 template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, T* __restrict__ fc, int64_t nchunks, int log2N,
-                                                 const LevelK<T, D>* __restrict__ lk, const Res0* __restrict__ res,
-                                                 int nlev, Xfer<T, D> X, int nu1, int H,
+__global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
+                                                 int64_t nchunks, int log2N, const LevelK<T, D>* __restrict__ lk,
+                                                 const Res0* __restrict__ res, int nlev, Xfer<T, D> X, int nu1, int H,
                                                  const BatchState* __restrict__ st, BatchInst bi) {
     if (st->done) return;
+    if (rlo != nullptr) {
+        const int64_t nv = nchunks * 2 * D;
+        rT += st->rsel * nv;
+        rlo += st->rsel * nv;
+    }
     const double* __restrict__ F = st->F;
     const double* __restrict__ uu = st->u;
     constexpr bool kMixed = std::is_same<T, float>::value;
@@ -82,12 +97,14 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, T* __restri
         const int64_t q = tw * per + lane - H;
         const bool inb = q >= 0 && q < nchunks;
         const int64_t inst = inb ? (2 * q) >> log2N : 0;
-        const bool act = inb && bi.active[inst];
+        const bool act = inb && bi.active[inst] && (rlo == nullptr || bi.full[inst]);
+        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
         const bool own = act && lane >= H;
         const bool first = ((2 * q) & mask) == 0;
         const LevelK<T, D> K = lk[inst * nlev];
         const Res0 R = res[inst];
         double uv[2][D], Fv[2][D];
+        short rq[2][D];
         load_pair<double, D>(uu, q, act, uv);
         load_pair<double, D>(F, q, act, Fv);
         const double u0i = act ? st->u0[inst] : 0.0;
@@ -102,13 +119,15 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, T* __restri
                 up0 = u0i;
                 sp = ff{0.f, 0.f};
             }
-            float r0[D], r1[D];
-            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0);
-            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1);
+            float r0[D], r1[D], l0[D], l1[D];
+            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0, l0);
+            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1, l1);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 rt[0][k] = act ? r0[k] : 0.f;
                 rt[1][k] = act ? r1[k] : 0.f;
+                rq[0][k] = lo_encode(r0[k], l0[k]);
+                rq[1][k] = lo_encode(r1[k], l1[k]);
             }
         } else {
             double r[2][D];
@@ -136,7 +155,12 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, T* __restri
                 ss = fma(v, v, ss);
             }
         segmented_norm_add(ss, inst, own, bi.norm2);
-        if (own) store_pair<T, D>(rT, q, rt);
+        if (own) {
+            store_pair<T, D>(rT, q, rt);
+            if constexpr (kMixed) {
+                if (rlo != nullptr) store_pair<short, D>(rlo, q, rq);
+            }
+        }
         if (fc != nullptr) {
             T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
             presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1, first);
@@ -147,29 +171,55 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, T* __restri
     }
 }
 
-// Per-instance stopping test after the level-0 residual of cycle k.
-__global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi, int64_t n_inst) {
+// Per-instance stopping test.
+//   kFinPlain: after the level-0 residual of cycle k, computed from u.
+//   kFinFull (updated-residual form): after kb_down0 recomputed the residual of
+//     the instances flagged full -- the start of the solve, or a confirmation;
+//     only those instances are tested, and a failed confirmation clears the flag.
+//   kFinUpdated: after kb_updown0 updated every active instance's residual:
+//     meeting tol flags the instance for confirmation instead of stopping it;
+//     the cycle counter advances and the residual buffers swap.
+__global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi, int64_t n_inst,
+                                                    int mode = kFinPlain) {
     if (st->done) {                          // a finished batch must also end the graph loop
         if (st->use_cond && blockIdx.x == 0 && threadIdx.x == 0)
             cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
         return;
     }
-    const int k = st->cycle;
+    const int k = mode == kFinUpdated ? st->cycle + 1 : st->cycle;   // corrections applied
     int act_local = 0, fail_local = 0;
     for (int64_t i = (int64_t)blockIdx.x * kBNT + threadIdx.x; i < n_inst; i += (int64_t)gridDim.x * kBNT) {
         if (!bi.active[i]) continue;
-        const double nrm = sqrt(bi.norm2[i]);
+        if (mode == kFinFull && !bi.full[i]) {
+            ++act_local;
+            continue;
+        }
+        // kb_updown0 sums squares scaled by nscale[i]^2
+        const double nrm = sqrt(bi.norm2[i]) / (mode == kFinUpdated ? (double)bi.nscale[i] : 1.0);
         bi.norm2[i] = 0.0;
-        if (k == 0) bi.nF[i] = nrm;
+        if (k == 0 && mode != kFinUpdated) bi.nF[i] = nrm;
         const double nF = bi.nF[i];
         const double rel = nF > 0.0 ? nrm / nF : nrm;
         const bool bad = !(rel == rel) || rel > 1.0e300;
-        if (bad || rel <= st->tol || k >= st->max_cycles) {
+        if (mode != kFinPlain) {
+            // scale of the next FP32 norm of this instance
+            const double rms = nrm / sqrt((double)bi.nvals_per_inst);
+            int ex = 0;
+            if (rms > 0.0 && rms < 1.0e300) ex = -ilogb(rms);
+            ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
+            bi.nscale[i] = ldexpf(1.0f, ex);
+        }
+        const bool met = rel <= st->tol;
+        if (mode == kFinUpdated && !bad && met) {
+            bi.full[i] = 1;                  // confirm from u at the start of the next cycle
+            ++act_local;
+        } else if (bad || met || k >= st->max_cycles) {
             bi.active[i] = 0;
             bi.cycles[i] = k;
             bi.rel[i] = rel;
-            if (bad || rel > st->tol) ++fail_local;
+            if (bad || !met) ++fail_local;
         } else {
+            if (mode == kFinFull) bi.full[i] = 0;
             ++act_local;
         }
     }
@@ -195,7 +245,11 @@ __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi
     const int remaining = atomicAdd(&st->active_count, 0);
     st->active_count = 0;
     st->ticket = 0u;
-    st->cycle = k + 1;
+    if (mode == kFinPlain) st->cycle = k + 1;
+    if (mode == kFinUpdated) {
+        st->cycle = k;
+        st->rsel ^= 1;      // kb_updown0 wrote the other buffer
+    }
     if (remaining == 0) {
         st->done = st->failed ? 2 : 1;
         if (st->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)st->cond, 0u);
@@ -218,6 +272,7 @@ __global__ void __launch_bounds__(kBNT) kb_down(const T* __restrict__ f, T* __re
         const bool inb = q >= 0 && q < nchunks;
         const int64_t inst = inb ? (2 * q) >> log2N : 0;
         const bool act = inb && bi.active[inst];
+        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
         const bool first = ((2 * q) & mask) == 0;
         const LevelK<T, D> K = lk[inst * nlev + level];
         T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
@@ -245,6 +300,7 @@ __global__ void __launch_bounds__(kBNT) kb_up(const T* __restrict__ f, const T* 
         const bool inb = q >= 0 && q < nchunks;
         const int64_t inst = inb ? (2 * q) >> log2N : 0;
         const bool act = inb && bi.active[inst];
+        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
         const bool first = ((2 * q) & mask) == 0;
         const LevelK<T, D> K = lk[inst * nlev + level];
         T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
@@ -274,6 +330,7 @@ __global__ void __launch_bounds__(kBNT) kb_up0(const T* __restrict__ rT, const T
         const bool inb = q >= 0 && q < nchunks;
         const int64_t inst = inb ? (2 * q) >> log2N : 0;
         const bool act = inb && bi.active[inst];
+        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
         const bool own = act && lane >= H;
         const bool first = ((2 * q) & mask) == 0;
         const LevelK<T, D> K = lk[inst * nlev];
@@ -343,6 +400,96 @@ __global__ void __launch_bounds__(kBNT) kb_coarse(const T* __restrict__ f, T* __
         T* ub = u + inst * (int64_t)Nc * D;
         if (n0 < Nc) VecIO<T, D>::store(ub + n0 * D, x0);
         if (n1 < Nc) VecIO<T, D>::store(ub + n1 * D, x1);
+    }
+}
+
+// Level 0 of the mixed form with an updated residual (see k_updown0): the way
+// up of one cycle fused with the way down of the next, for every active
+// instance; r -= L c on the residual pairs (read from buffer st->rsel, written
+// to the other), u += c in FP64, per-instance FP32 norms scaled by nscale[i].
+template <int DIR, int D>
+__global__ void __launch_bounds__(kBNT, D <= 2 ? 4 : 2) kb_updown0(float* __restrict__ rh, short* __restrict__ rl,
+                                                                   const float* __restrict__ uc,
+                                                                   float* __restrict__ fc, int64_t nchunks,
+                                                                   int log2N,
+                                                                   const LevelK<float, D>* __restrict__ lk,
+                                                                   const Res0* __restrict__ res, int nlev,
+                                                                   Xfer<float, D> X, int nu1, int nu2, int H,
+                                                                   const BatchState* __restrict__ st,
+                                                                   BatchInst bi) {
+    if (st->done) return;
+    double* __restrict__ uu = st->u;
+    const int64_t nv = nchunks * 2 * D;
+    const int sel = st->rsel;
+    const float* __restrict__ rh_in = rh + sel * nv;
+    const short* __restrict__ rl_in = rl + sel * nv;
+    float* __restrict__ rh_out = rh + (1 - sel) * nv;
+    short* __restrict__ rl_out = rl + (1 - sel) * nv;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    const int64_t mask = (1ll << log2N) - 1;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        const int64_t inst = inb ? (2 * q) >> log2N : 0;
+        const bool act = inb && bi.active[inst];
+        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
+        const bool own = act && lane >= H;
+        const bool first = ((2 * q) & mask) == 0;
+        const LevelK<float, D> K = lk[inst * nlev];
+        const Res0 R = res[inst];
+        const float nsc = bi.nscale[inst];
+        float r[2][D], rlo[2][D], cc[D];
+        short rq[2][D];
+        double uv[2][D];
+        load_pair<float, D>(rh_in, q, act, r);
+        load_pair<short, D>(rl_in, q, act, rq);
+        load_one<float, D>(uc, q, act, cc);
+        load_pair<double, D>(uu, q, own, uv);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int k = 0; k < D; ++k) rlo[i][k] = lo_decode(r[i][k], rq[i][k]);
+        float h[2][D], c[2][D], w[2][D];
+        presmooth_zero<DIR, float, D>(K, r, h, c, w, nu1, first);
+        prolong_add<float, D>(X, cc, c);
+        postsmooth<DIR, float, D>(K, h, c, nu2, first);
+        if (!act) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) c[i][k] = 0.f;
+        }
+        const ff b0 = bsum_ff<DIR, D>(c[0]);
+        const ff b1 = bsum_ff<DIR, D>(c[1]);
+        ff bp{shfl_prev(b1.hi), shfl_prev(b1.lo)};
+        if (first) bp = ff{0.f, 0.f};            // the correction starts from zero at every instance
+        residual_update_ff<DIR, D>(r[0], rlo[0], c[0], bp, R);
+        residual_update_ff<DIR, D>(r[1], rlo[1], c[1], b0, R);
+        float ssf = 0.f;
+        if (own) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    uv[i][k] += f2d_int(c[i][k]);
+                    const float v = r[i][k] * nsc;
+                    ssf = fmaf(v, v, ssf);
+                    rq[i][k] = lo_encode(r[i][k], rlo[i][k]);
+                }
+            store_pair<double, D>(uu, q, uv);
+            store_pair<float, D>(rh_out, q, r);
+            store_pair<short, D>(rl_out, q, rq);
+        }
+        segmented_norm_add(f2d_int(ssf), inst, own, bi.norm2);   // in units of nscale^2 (kb_finalize)
+        // the next cycle's way down on L c' = r
+        float rc[2][D], out[D];
+        presmooth_zero<DIR, float, D>(K, r, h, c, w, nu1, first);
+        residual_tracked<DIR, float, D>(r, c, w, rc, first);
+        restrict_pair<float, D>(X, rc, out);
+        if (own) VecIO<float, D>::store(fc + q * D, out);
     }
 }
 
