@@ -170,11 +170,9 @@ def run_ours(args):
     import torch
 
     import __graft_entry__
-    from paper_1409_5254_gb300 import inputs, tmg
+    from paper_1409_5254_gb300 import inputs, replicas, tmg
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, local, world = replicas.rank_info()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -210,12 +208,9 @@ def run_ours(args):
     clk.start()
     ms = time_solves(plan, F, u, args.steps, stream, torch)
     clk.stop()
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = replicas.max_over_ranks(ms, dev)
     st = plan.stats()
-    value = world * N_FULL * d / (ms * 1e-3)
+    value = replicas.aggregate_throughput([N_FULL * d] * world, ms)    # one replica per rank
 
     # accuracy of the timed result, in FP64 on the GPU (residual entry point)
     r = plan.residual(F, U0, u)
@@ -312,7 +307,12 @@ def run_ours(args):
             nus[f"V({nu[0]},{nu[1]})"] = {"value": N_FULL * d / (msn * 1e-3), "ms_per_step": round(msn, 4),
                                            "cycles": sn.cycles, "rel_res": sn.rel_res}
         extra["nu_variants"] = nus
-        extra["batched"] = run_batched_configs(dev, stream, args.steps, torch)
+
+    if not args.quick:
+        # every rank solves its shard of the batched workloads
+        extra_b = run_batched_configs(dev, stream, args.steps, torch, rank, world)
+        if rank == 0:
+            extra["batched"] = extra_b
 
     # end to end through the host-array entry point (pinned buffers, copies inside the call)
     F_h = torch.from_numpy(prob["F"]).pin_memory()
@@ -324,13 +324,10 @@ def run_ours(args):
     n_e2e = max(3, args.steps // 2)
     for _ in range(n_e2e):
         plan.solve_host(F_h, U0, u_h)
-    t_e2e = (time.perf_counter() - t0) / n_e2e
-    t_t = torch.tensor([t_e2e], device=dev)
-    if dist is not None:
-        dist.all_reduce(t_t, op=dist.ReduceOp.MAX)
-    t_e2e = float(t_t.item())
+    t_e2e = replicas.max_over_ranks((time.perf_counter() - t0) / n_e2e, dev)
     nbytes = N_FULL * d * 8
-    e2e = {"value": world * N_FULL * d / t_e2e, "unit": "DoF/s", "h2d_bytes_per_step": nbytes,
+    e2e = {"value": replicas.aggregate_throughput([N_FULL * d] * world, t_e2e * 1e3), "unit": "DoF/s",
+           "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes, "ms_per_step": round(t_e2e * 1e3, 3)}
 
     cpu = None
@@ -369,17 +366,25 @@ def _time_batch(batch, f, u0, u, steps, stream, torch):
     return start.elapsed_time(end) / steps
 
 
-def run_batched_configs(dev, stream, steps, torch):
+def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1):
     """The batched workloads: decoupled 2-D heat modes, an uneven batch, and
     gradients through the adjoint.  One step = one batched solve (plus the
-    adjoint for the gradient workload); inputs resident in HBM."""
+    adjoint for the gradient workload); inputs resident in HBM.  With several
+    ranks each solves its shard of the instances (balanced by N (p_t+1)); the
+    value is all instances' DoFs over the slowest rank's time."""
     import numpy as np
-    from paper_1409_5254_gb300 import inputs, tmg
+    from paper_1409_5254_gb300 import inputs, replicas, tmg
+
+    def shard(weights):
+        return replicas.partition_instances(weights, world)[rank]
 
     out = {}
     # 65,536 heat modes, N = 4096, p_t = 1, T = 1
-    lam, amps, freqs = inputs.heat_modes_batch(2, 256, 4096, 1)
-    n, N, p = lam.shape[0], 4096, 1
+    lam_all, amps_all, freqs_all = inputs.heat_modes_batch(2, 256, 4096, 1)
+    n_all, N, p = lam_all.shape[0], 4096, 1
+    idx = shard(np.full(n_all, N * (p + 1)))
+    lam, amps, freqs = lam_all[idx], amps_all[idx], freqs_all[idx]
+    n = len(idx)
     f = inputs.sine_load_vectors(amps, freqs, 1.0, N, p, device=dev).reshape(-1)
     u0 = torch.zeros(n, dtype=torch.float64, device=dev)
     u = torch.empty_like(f)
@@ -390,25 +395,30 @@ def run_batched_configs(dev, stream, steps, torch):
             B.solve(f, u0, u)
             ms = _time_batch(B, f, u0, u, max(1, steps // 10) if prec == "mixed" else 1, stream, torch)
             cyc, rel, mx = B.stats()
-        res[prec] = {"value": n * N * (p + 1) / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
-                     "max_rel_res": float(rel.max())}
-    out["heat_modes_65536x4096_p1"] = {"unit": "DoF/s", "instances": n, "N": N, "p_t": p,
-                                       "lambda_range": [float(lam.min()), float(lam.max())], **res}
+        ms = replicas.max_over_ranks(ms, dev)
+        mx = replicas.max_over_ranks(mx, dev)
+        worst = replicas.max_over_ranks(float(rel.max()), dev)
+        res[prec] = {"value": n_all * N * (p + 1) / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
+                     "max_rel_res": worst}
+    out["heat_modes_65536x4096_p1"] = {"unit": "DoF/s", "instances": n_all, "N": N, "p_t": p,
+                                       "lambda_range": [float(lam_all.min()), float(lam_all.max())], **res}
     del f, u, u0
     torch.cuda.empty_cache()
 
     # uneven batch: 10,000 instances, N log-uniform in [2^6, 2^16], p_t in {0..3}, lambda tau in [1e-3, 1e3]
-    Nv, pv, z = inputs.uneven_batch(3, 10000)
+    Nv_all, pv_all, z_all = inputs.uneven_batch(3, 10000)
+    A_all, K_all = inputs.sinusoid_batch_params(3, len(Nv_all))
+    dofs = int((Nv_all * (pv_all + 1)).sum())
+    idx = shard(Nv_all * (pv_all + 1))
+    Nv, pv, z, A, K = Nv_all[idx], pv_all[idx], z_all[idx], A_all[idx], K_all[idx]
     tau = 1.0 / Nv
     lamv = z / tau
-    A, K = inputs.sinusoid_batch_params(3, len(Nv))
     parts = [inputs.sine_load_vectors(A[i:i + 1], K[i:i + 1], 1.0, int(Nv[i]), int(pv[i]), device=dev).reshape(-1)
              for i in range(len(Nv))]
     f = torch.cat(parts)
     del parts
     u0 = torch.ones(len(Nv), dtype=torch.float64, device=dev)
     u = torch.empty_like(f)
-    dofs = int((Nv * (pv + 1)).sum())
     res = {}
     for prec in ("mixed", "fp64"):
         torch.cuda.synchronize()
@@ -420,24 +430,29 @@ def run_batched_configs(dev, stream, steps, torch):
             ms = _time_batch(B, f, u0, u, max(1, steps // 10), stream, torch)
             cyc, rel, mx = B.stats()
             info = B.info()
+        ms = replicas.max_over_ranks(ms, dev)
         kinds = [g["schedule"] for g in info["group_info"]]
-        res[prec] = {"value": dofs / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
-                     "max_rel_res": float(rel.max()), "setup_ms_with_autotune": round(setup_ms, 1),
+        res[prec] = {"value": dofs / (ms * 1e-3), "ms_per_step": round(ms, 3),
+                     "max_cycles": int(replicas.max_over_ranks(mx, dev)),
+                     "max_rel_res": replicas.max_over_ranks(float(rel.max()), dev),
+                     "setup_ms_with_autotune": round(setup_ms, 1),
                      "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid")}
-    out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv), "dofs": dofs, "groups": info["groups"],
+    out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv_all), "dofs": dofs, "groups": info["groups"],
                            "padded_dofs": info["padded_values"], **res}
     del f, u, u0
     torch.cuda.empty_cache()
 
     # gradients: 4096 instances, N = 16384, p_t = 2, lambda log-uniform in [1, 1e4], T = 1
-    n, N, p = 4096, 16384, 2
-    lamg, u0n, target = inputs.adjoint_problem(4, n, N, p)
-    A, K = inputs.sinusoid_batch_params(4, n)
-    f = inputs.sine_load_vectors(A, K, 1.0, N, p, device=dev).reshape(-1)
-    u0 = torch.from_numpy(u0n).to(dev)
-    y = torch.from_numpy(target).to(dev)
+    n_all, N, p = 4096, 16384, 2
+    lam_all, u0_all, target_all = inputs.adjoint_problem(4, n_all, N, p)
+    A_all, K_all = inputs.sinusoid_batch_params(4, n_all)
+    idx = shard(np.full(n_all, N * (p + 1)))
+    n = len(idx)
+    f = inputs.sine_load_vectors(A_all[idx], K_all[idx], 1.0, N, p, device=dev).reshape(-1)
+    u0 = torch.from_numpy(u0_all[idx]).to(dev)
+    y = torch.from_numpy(target_all[idx]).to(dev)
     u = torch.empty_like(f)
-    with tmg.Batch([p] * n, 1.0 / N, lamg, N, precision="mixed", tol=TOL, max_cycles=300, stream=stream,
+    with tmg.Batch([p] * n, 1.0 / N, lam_all[idx], N, precision="mixed", tol=TOL, max_cycles=300, stream=stream,
                    nu1=NU[0], nu2=NU[1]) as B:
         def step():
             B.solve(f, u0, u)
@@ -454,14 +469,17 @@ def run_batched_configs(dev, stream, steps, torch):
             step()
         end.record(stream)
         end.synchronize()
-        ms = start.elapsed_time(end) / k
+        ms = replicas.max_over_ranks(start.elapsed_time(end) / k, dev)
         cyc, rel, mx = B.stats()
-    out["adjoint_4096x16384_p2"] = {"unit": "DoF/s (forward + adjoint)", "instances": n, "N": N, "p_t": p,
-                                    "value": n * N * (p + 1) / (ms * 1e-3), "gradients_per_s": 1e3 / ms,
-                                    "ms_per_step": round(ms, 3), "adjoint_max_cycles": int(mx),
+    out["adjoint_4096x16384_p2"] = {"unit": "DoF/s (forward + adjoint)", "instances": n_all, "N": N, "p_t": p,
+                                    "value": n_all * N * (p + 1) / (ms * 1e-3), "gradients_per_s": 1e3 / ms,
+                                    "ms_per_step": round(ms, 3),
+                                    "adjoint_max_cycles": int(replicas.max_over_ranks(mx, dev)),
                                     "precision": "mixed", "cycle": f"V{NU}"}
     del f, u, u0, y
     torch.cuda.empty_cache()
+    if world > 1:
+        out["sharding"] = f"instances split over {world} ranks (no data exchange), weak in per-rank time"
     return out
 
 

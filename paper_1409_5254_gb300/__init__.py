@@ -3,7 +3,9 @@
 ``tmg``        -- Python binding of the C ABI (include/tmg.h) over libtmg.so
 ``inputs``     -- seeded synthetic workloads
 ``build_ext``  -- nvcc build of libtmg.so for sm_103a
+``autograd``   -- torch.autograd.Function over the batched solve and adjoint
+``replicas``   -- host logic of multi-rank runs (replicas, instance shards, timing reduction)
 The CUDA library is loaded lazily on first use so that the input generators
 import on machines without a GPU.
 """
-__all__ = ["tmg", "inputs", "build_ext"]
+__all__ = ["tmg", "inputs", "build_ext", "autograd", "replicas"]
