@@ -279,7 +279,7 @@ def run_ours(args):
                               "cycles": s64.cycles, "rel_res": s64.rel_res}
         # the other degrees of the same long horizon, mixed precision
         per_p = {}
-        for p in (0, 2, 3):
+        for p in (0, 2, 3, 4, 5):
             pr = inputs.scalar_problem(1, N_FULL, p, lam=LAM, tau=TAU, u0=U0)
             Fp = torch.from_numpy(pr["F"]).to(dev)
             up = torch.empty_like(Fp)

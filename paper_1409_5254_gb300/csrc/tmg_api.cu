@@ -201,7 +201,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     tmg_opts o;
     tmg_opts_default(&o);
     if (opts) o = *opts;
-    if (p_t < 0 || p_t > 3 || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
+    if (p_t < 0 || p_t > tmg::kMaxD - 1 || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
         !(omega < 2.0) || !isfinite(omega) || o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 ||
         o.gamma < 1 || o.gamma > 2 || (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 ||
         o.max_cycles < 0 || o.max_cycles >= tmg::kHist || !(o.tol >= 0.0))
@@ -294,9 +294,9 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     const size_t off_rl = off;
     if (updated_res) off = align_up(off + sizeof(short) * N * P->d * 2, A);
     const size_t off_lk = off;
-    off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
+    off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxD>) * (P->nlev - P->lt), A);
     const size_t off_lk_adj = off;
-    off = align_up(off + sizeof(tmg::LevelK<double, 4>) * (P->nlev - P->lt), A);
+    off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxD>) * (P->nlev - P->lt), A);
     const size_t off_p = off;
     off = align_up(off + sizeof(double) * P->max_blocks, A);
     P->scan_tiles = (N + tmg::kScanTile - 1) / tmg::kScanTile;

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
 //   kFinUpdated: after kb_updown0 updated every active instance's residual:
 //     meeting tol flags the instance for confirmation instead of stopping it;
 //     the cycle counter advances and the residual buffers swap.
-__global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi, int64_t n_inst,
+static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi, int64_t n_inst,
                                                     int mode = kFinPlain) {
     if (st->done) {                          // a finished batch must also end the graph loop
         if (st->use_cond && blockIdx.x == 0 && threadIdx.x == 0)

@@ -29,7 +29,7 @@
 
 namespace tmg {
 
-constexpr int kMaxD = 4;
+constexpr int kMaxD = 6;          // p_t <= 5
 constexpr int kMaxLevels = 48;
 constexpr int kHist = 512;
 constexpr unsigned kFull = 0xffffffffu;
@@ -485,13 +485,23 @@ template <int DIR, int D>
 __device__ __forceinline__ void residual0(const double (&F)[D], const double (&u)[D], double ep, double E,
                                           const Res0& R, double (&r)[D]) {
     const double dp = ep - E;
-    if constexpr (DIR == 0) {
+    if constexpr (DIR == 0 && D <= 4) {
         r[0] = fma(-R.zm[0], u[0], F[0] + dp);
         if constexpr (D > 1) {
             const double sm = ep + E;
             r[1] = fma(-R.zm[1], u[1], fma(2.0, u[0], F[1] - sm));
             if constexpr (D > 2) r[2] = fma(-R.zm[2], u[2], fma(2.0, u[1], F[2] + dp));
             if constexpr (D > 3) r[3] = fma(-R.zm[3], u[3], fma(2.0, u[0] + u[2], F[3] - sm));
+        }
+    } else if constexpr (DIR == 0) {
+        // S_k = sum of u[l], l < k, l of the other parity; a_k = (-1)^k
+        const double sm = ep + E;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double sk = 0.0;
+#pragma unroll
+            for (int l = k - 1; l >= 0; l -= 2) sk += u[l];
+            r[k] = fma(-R.zm[k], u[k], fma(2.0, sk, F[k] + ((k & 1) ? -sm : dp)));
         }
     } else {
         double t[D];
@@ -638,7 +648,7 @@ __device__ __forceinline__ void small_sums(const double (&u)[D], ff (&us)[D], ff
 
 // r[k] of one interval, rounded to float.  up0 = u_{n-1}[0], spB = the small
 // part of b^T u_{n-1}, snE = the small part of 1^T u_n.  With d = up0 - u_n[0]:
-// DIR = 0: r[k] = F[k] + a_k (d + spB) - snE + 2 [k>=2] u[k-1] - z/(2k+1) u[k]
+// DIR = 0: r[k] = F[k] + a_k (d + spB) - snE + 2 S'_k - z/(2k+1) u[k], S'_k = u[k-1] + u[k-3] + ... (l >= 1)
 // DIR = 1: r[k] = F[k] + (d + spB) - snE + 2 T_k - z/(2k+1) u[k]  (T_k as in residual0)
 template <int DIR, int D>
 __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double (&u)[D], const ff (&us)[D],
@@ -654,7 +664,9 @@ __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double 
         acc_add(s, c, sg * spB.hi, sg * spB.lo);
         acc_add(s, c, -snE.hi, -snE.lo);
         if constexpr (DIR == 0) {
-            if (k >= 2) acc_add(s, c, 2.f * us[k - 1].hi, 2.f * us[k - 1].lo);
+            // 2 S_k with S_k's u[0] term (odd k) already inside a_k d
+#pragma unroll
+            for (int l = k - 1; l >= 1; l -= 2) acc_add(s, c, 2.f * us[l].hi, 2.f * us[l].lo);
         } else {
 #pragma unroll
             for (int l = k + 1; l < D; l += 2) acc_add(s, c, 2.f * us[l].hi, 2.f * us[l].lo);

@@ -117,7 +117,7 @@ cudaError_t scratch_for_current_device(NormScratch** out) {
 extern "C" tmg_status tmg_residual_norm_noalloc(int p_t, double tau, double lambda, int64_t N, const double* f,
                                                 double u0, const double* u, double* r, double* norm,
                                                 void* stream) {
-    if (p_t < 0 || p_t > 3 || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
+    if (p_t < 0 || p_t > tmg::kMaxD - 1 || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
         !isfinite(u0) || !f || !u || !r || !norm)
         return TMG_EINVAL;
     if ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(r)) & 15u)
@@ -144,7 +144,9 @@ extern "C" tmg_status tmg_residual_norm_noalloc(int p_t, double tau, double lamb
         case 0: k_residual_norm_static<1><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
         case 1: k_residual_norm_static<2><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
         case 2: k_residual_norm_static<3><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
-        default: k_residual_norm_static<4><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
+        case 3: k_residual_norm_static<4><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
+        case 4: k_residual_norm_static<5><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
+        default: k_residual_norm_static<6><<<blocks, tmg::kNT, 0, s>>>(f, u, u0, r, N, R, scratch, norm); break;
     }
     return cudaGetLastError() == cudaSuccess ? TMG_OK : TMG_ECUDA;
 }

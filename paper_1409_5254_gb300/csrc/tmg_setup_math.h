@@ -28,7 +28,7 @@ inline void local_blocks(int d, double z, double* A) {
 
 // Gauss-Jordan inversion with partial pivoting; returns false if singular.
 inline bool invert(int d, const double* A, double* Ainv) {
-    double M[4][8];
+    double M[tmg::kMaxD][2 * tmg::kMaxD];
     for (int i = 0; i < d; ++i)
         for (int j = 0; j < 2 * d; ++j) M[i][j] = j < d ? A[i * d + j] : (j - d == i ? 1.0 : 0.0);
     for (int c = 0; c < d; ++c) {
@@ -101,11 +101,12 @@ inline void level_setup(int d, double z, double omega_user, tmg_level_host* L) {
 // columns follow from composing P_k with that affine map and converting the
 // monomial coefficients back to the Legendre basis (exact polynomial algebra).
 inline void transfer_setup(int d, double* P1, double* P2) {
-    double leg[4][4] = {{0}};   // monomial coefficients of P_0..P_3
+    constexpr int M = tmg::kMaxD;
+    double leg[M][M] = {{0}};   // monomial coefficients of P_0..P_{d-1}
     leg[0][0] = 1.0;
     if (d > 1) leg[1][1] = 1.0;
     for (int k = 1; k + 1 < d; ++k)   // (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < M; ++j) {
             double v = -k * leg[k - 1][j];
             if (j > 0) v += (2.0 * k + 1.0) * leg[k][j - 1];
             leg[k + 1][j] = v / (k + 1.0);
@@ -115,7 +116,7 @@ inline void transfer_setup(int d, double* P1, double* P2) {
         double* P = half == 0 ? P1 : P2;
         for (int k = 0; k < d; ++k) {
             // q(x) = P_k((x + shift) / 2) in monomials
-            double q[4] = {0, 0, 0, 0};
+            double q[M] = {0};
             for (int j = 0; j < d; ++j) {
                 if (leg[k][j] == 0.0) continue;
                 // ((x + shift)/2)^j = 2^-j sum_i C(j,i) x^i shift^(j-i)

@@ -50,6 +50,8 @@ CASES = [
     (3, 1 << 13, 300.0, "fp64"),
     (2, 1 << 14, 10.0, "mixed"),
     (1, 1 << 15, 1.0, "mixed"),
+    (5, 1 << 13, 5.0, "fp64"),      # higher degrees
+    (4, 1 << 14, 1.0, "mixed"),
 ]
 
 

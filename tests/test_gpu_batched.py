@@ -161,6 +161,24 @@ def test_cta_schedule_adjoint_matches_oracle(dev):
         assert dlam[i] == pytest.approx(dl, rel=allow, abs=1e-12)
 
 
+@pytest.mark.parametrize("schedule", ["grid", "cta"])
+def test_higher_degree_batch(dev, schedule):
+    """p_t = 4 and 5 instances (with one of p_t = 1) in both schedules."""
+    from paper_1409_5254_gb300 import tmg
+    rng = np.random.default_rng(21)
+    p = np.array([4, 5, 4, 5, 1, 5, 4, 4])
+    N = np.array([64, 96, 256, 512, 128, 1024, 32, 200])
+    z = 10.0 ** rng.uniform(-3, 2, len(p))
+    Fs, u0, tau, lam = make_batch(21, p, N, z)
+    sched = tmg.SCHED_GRID if schedule == "grid" else tmg.SCHED_CTA
+    with tmg.Batch(p, tau, lam, N, precision="mixed", tol=1e-10, max_cycles=300, schedule=sched) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+    assert (rel <= 1e-10).all()
+    check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
+
+
 def test_batch_of_one_matches_single_solve(dev):
     from paper_1409_5254_gb300 import tmg
     prob = inputs.scalar_problem(4, 4096, 2, lam=3.0, T=1.0, u0=0.5)

@@ -76,6 +76,9 @@ CYCLE_CASES = [
     (1, 3 * 1024, 1.0, 1.0, 2, 0, 1, 1, 1, 0.0),      # N = 3 * 2^10: odd coarsest level (3)
     (2, 1 << 16, 1.0, 1.0, 16384, 0, 1, 1, 1, 0.0),   # coarsest level (16384) solved by the grid-wide scan
     (0, 20002, 2.0, 1.0, 15000, 0, 1, 1, 1, 0.0),     # odd coarsest level of 10001 by the scan (ragged last tile)
+    (4, 1 << 14, 2.0, 1.0, 64, 0, 1, 1, 1, 0.0),      # higher degrees (p_t = 4, 5)
+    (5, 1 << 13, 1.0, 1.0, 16, 0, 2, 1, 1, 0.0),
+    (5, 1 << 14, 30.0, 1.0, 2, 0, 1, 2, 1, 0.0),
 ]
 
 
@@ -120,7 +123,7 @@ def test_fused_level_pairs_match_textbook_cycle(dev, tail_cap, nu):
         assert rel_err(got[k], unf[k]) <= 1e-13
 
 
-@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5])
 def test_fp64_solve_matches_forward_substitution(dev, p):
     N = 1 << 13
     prob = inputs.scalar_problem(p, N, p, lam=1.0, T=4.0, u0=1.0)
@@ -141,7 +144,7 @@ def test_fp64_solve_matches_forward_substitution(dev, p):
     np.testing.assert_allclose(st.hist[:m][big], hist[:m][big], rtol=1e-6)
 
 
-@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("zscale", [1e-3, 1.0, 1e3])
 def test_mixed_solve_reaches_tolerance(dev, p, zscale):
     N = 1 << 14
@@ -277,7 +280,7 @@ def test_full_size_long_horizon_sampled(dev):
     assert err <= 1e-6
 
 
-@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("N", [1, 5, 2047, 2048, 2049, 100003, (1 << 20) + 3])
 def test_direct_scan_solve(dev, p, N):
     """tmg_solve_direct (three-pass FP64 scan) against forward substitution.
@@ -314,7 +317,7 @@ def test_single_level_large_problem_uses_scan(dev, prec):
 
 
 
-@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("zscale", [1e-3, 1.0, 1e3])
 def test_updated_residual_matches_fp64_residual(dev, p, zscale):
     """Mixed form: after one cycle the level-0 residual kept as a float pair

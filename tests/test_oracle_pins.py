@@ -14,7 +14,7 @@ from oracle import lfa
 from paper_1409_5254_gb300 import inputs
 from conftest import load_golden
 
-PS = [0, 1, 2, 3]
+PS = [0, 1, 2, 3, 4, 5]
 
 
 def pade(p, z):
@@ -25,6 +25,36 @@ def pade(p, z):
             den = sum(c * z**i for i, c in enumerate(row[2]))
             return num / den
     raise KeyError(p)
+
+
+def pade_closed_form(m, n, z):
+    """The [m/n] Pade approximant of exp(z) from its classical closed form
+    (numerator sum_j (m+n-j)! m! / ((m+n)! j! (m-j)!) z^j, denominator the same
+    with n and -z), independent of the paper's printed list and of the oracle."""
+    from math import factorial as fa
+    num = sum(fa(m + n - j) * fa(m) / (fa(m + n) * fa(j) * fa(m - j)) * z**j for j in range(m + 1))
+    den = sum(fa(m + n - j) * fa(n) / (fa(m + n) * fa(j) * fa(n - j)) * (-z) ** j for j in range(n + 1))
+    return num / den
+
+
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+def test_pade_closed_form_reproduces_the_papers_list(p):
+    for z in (-3.0, -0.5, 0.25, 2.0):
+        assert pade_closed_form(p, p + 1, z) == pytest.approx(pade(p, z), rel=1e-14)
+
+
+@pytest.mark.parametrize("p", [4, 5])
+@pytest.mark.parametrize("z", [1e-3, 0.5, 2.0, 40.0])
+def test_homogeneous_nodal_values_higher_degrees(p, z):
+    """Degrees beyond the paper's printed list: with f = 0 the nodal values
+    follow R(-z)^n with R the (p, p+1) sub-diagonal Pade approximant
+    (Corollary chap4_corollary1) from its closed form."""
+    N = 60
+    u = O.fsub(p, z, np.zeros((N, p + 1)), 1.0)
+    e = O.nodal_values(p, u)
+    R = pade_closed_form(p, p + 1, -z)
+    np.testing.assert_allclose(e, R ** np.arange(1, N + 1), rtol=1e-10, atol=1e-300)
+    assert O.alpha(p, z) == pytest.approx(R, rel=1e-12, abs=1e-15)
 
 
 # --------------------------------------------------------------- blocks --
