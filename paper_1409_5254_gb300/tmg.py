@@ -117,6 +117,14 @@ def _dev_ptr(t, d: int, N: int, name: str):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _order_after_current(stream, t):
+    """A plan on a caller-given stream reads arrays that torch's current stream
+    may still be writing: make the plan's stream wait for it first."""
+    if stream is not None:
+        import torch
+        stream.wait_stream(torch.cuda.current_stream(t.device))
+
+
 @dataclass
 class SolveStats:
     status: int
@@ -173,6 +181,7 @@ class Plan:
         import torch
         if u is None:
             u = torch.empty((self.N, self.d), dtype=torch.float64, device=f.device)
+        _order_after_current(self._stream, f)
         st = _lib().tmg_solve(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0), _dev_ptr(u, self.d, self.N, "u"))
         _check(st, "tmg_solve", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
         self.last_status = st
@@ -183,6 +192,7 @@ class Plan:
         import torch
         if u is None:
             u = torch.empty((self.N, self.d), dtype=torch.float64, device=f.device)
+        _order_after_current(self._stream, f)
         _check(_lib().tmg_solve_direct(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
                                        _dev_ptr(u, self.d, self.N, "u")), "tmg_solve_direct")
         return u
@@ -198,6 +208,7 @@ class Plan:
         import torch
         dJdf = torch.empty_like(g)
         scal = torch.zeros(2, dtype=torch.float64, device=g.device)
+        _order_after_current(self._stream, g)
         st = _lib().tmg_adjoint(self._h, _dev_ptr(g, self.d, self.N, "g"), _dev_ptr(u, self.d, self.N, "u"),
                                 _dev_ptr(dJdf, self.d, self.N, "dJdf"), ctypes.c_void_p(scal.data_ptr()),
                                 ctypes.c_void_p(scal.data_ptr() + 8))
@@ -205,6 +216,7 @@ class Plan:
         return dJdf, scal[0], scal[1]
 
     def cycle(self, f, u0: float, u):
+        _order_after_current(self._stream, f)
         _check(_lib().tmg_cycle(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
                                 _dev_ptr(u, self.d, self.N, "u")), "tmg_cycle")
         return u
@@ -213,6 +225,7 @@ class Plan:
         import torch
         if r is None:
             r = torch.empty_like(u)
+        _order_after_current(self._stream, f)
         _check(_lib().tmg_residual(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
                                    _dev_ptr(u, self.d, self.N, "u"), _dev_ptr(r, self.d, self.N, "r")),
                "tmg_residual")
@@ -230,6 +243,7 @@ class Plan:
     def profile_cycle(self, f, u0: float, u, reps: int = 10) -> dict:
         """Mean per-kernel milliseconds of one correction cycle (CUDA events on the plan's stream)."""
         ms = np.zeros(6)
+        _order_after_current(self._stream, f)
         _check(_lib().tmg_profile_cycle(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
                                         _dev_ptr(u, self.d, self.N, "u"), reps, ms.ctypes.data_as(_dp), 6),
                "tmg_profile_cycle")
@@ -350,6 +364,7 @@ class Batch:
         import torch
         if u is None:
             u = torch.empty(self.total, dtype=torch.float64, device=f.device)
+        _order_after_current(self._stream, f)
         st = _lib().tmg_solve_batched(self._h, self._ptr(f, self.total, "f"), self._ptr(u0, self.n, "u0"),
                                       self._ptr(u, self.total, "u"))
         _check(st, "tmg_solve_batched", (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,))
@@ -360,6 +375,7 @@ class Batch:
         dJdf = torch.empty_like(g)
         du0 = torch.empty(self.n, dtype=torch.float64, device=g.device)
         dlam = torch.empty(self.n, dtype=torch.float64, device=g.device)
+        _order_after_current(self._stream, g)
         st = _lib().tmg_adjoint_batched(self._h, self._ptr(g, self.total, "g"), self._ptr(u, self.total, "u"),
                                         self._ptr(dJdf, self.total, "dJdf"), self._ptr(du0, self.n, "dJdu0"),
                                         self._ptr(dlam, self.n, "dJdlambda"))

@@ -437,3 +437,21 @@ def test_non_finite_input_reports_numeric_error_and_plan_stays_usable(dev, prec,
         assert plan.stats().cycles == 0
         u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
     assert rel_residual(p, prob["tau"], prob["F"], prob["u0"], u) <= 1.05e-10
+
+
+def test_plan_on_a_torch_stream_orders_after_the_current_stream(dev):
+    """A plan created on a caller's (non-blocking) torch stream: the load
+    vector written by torch on the current stream just before the call must be
+    complete when the solve reads it."""
+    N, p = 1 << 20, 1
+    prob = inputs.scalar_problem(14, N, p, lam=1.0, tau=1e-6, u0=1.0)
+    src = torch.from_numpy(prob["F"]).to(dev)
+    s = torch.cuda.Stream(device=dev)
+    with tmg().Plan(p, 1e-6, 1.0, N, precision="mixed", stream=s) as plan:
+        for k in range(3):
+            F = torch.zeros_like(src)
+            F.copy_(src)                       # queued on the current stream, no host sync
+            F.mul_(1.0 + k)                    # the solve must see the scaled load vector
+            u = plan.solve(F, prob["u0"] * (1.0 + k))
+            assert rel_residual(p, 1e-6, prob["F"] * (1.0 + k), prob["u0"] * (1.0 + k),
+                                u.cpu().numpy()) <= 1.05e-10
