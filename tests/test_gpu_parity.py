@@ -455,3 +455,30 @@ def test_plan_on_a_torch_stream_orders_after_the_current_stream(dev):
             u = plan.solve(F, prob["u0"] * (1.0 + k))
             assert rel_residual(p, 1e-6, prob["F"] * (1.0 + k), prob["u0"] * (1.0 + k),
                                 u.cpu().numpy()) <= 1.05e-10
+
+
+@pytest.mark.slow
+def test_largest_size_ragged_hierarchy(dev):
+    """A horizon six times the benchmark's: N = 3 * 2^25 (about 10^8 intervals,
+    1.6 GB load vector), whose hierarchy ends on a 48-interval level; the FP64
+    residual of the whole result by the oracle, and sampled intervals against
+    exact forward substitution."""
+    N, p, tau = 3 << 25, 1, 1e-6
+    rng = np.random.default_rng(77)
+    A = rng.uniform(-1.0, 1.0, (1, 4))
+    K = rng.integers(1, 9, (1, 4)).astype(float)
+    F = inputs.sine_load_vectors(A, K, N * tau, N, p, device=dev)[0]
+    with tmg().Plan(p, tau, 1.0, N, precision="mixed", nu1=2, nu2=2) as plan:
+        info = plan.info()
+        u = plan.solve(F, 1.0)
+        st = plan.stats()
+    assert info["levels"] == 22 and (N >> (info["levels"] - 1)) == 48
+    Fh, uh = F.cpu().numpy(), u.cpu().numpy()
+    del F, u
+    rr = rel_residual(p, tau, Fh, 1.0, uh)
+    assert rr <= 1.05e-10, rr
+    ex = O.fsub(p, tau, Fh, 1.0)
+    idx = np.concatenate([rng.integers(0, N, 4096), [0, 1, N // 2, N - 2, N - 1]])
+    err = np.abs(uh[idx] - ex[idx]).max() / np.abs(ex).max()
+    print(f"N={N}: cycles={st.cycles} rel_res={rr:.2e} sampled err={err:.2e}")
+    assert err <= 1e-6
