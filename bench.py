@@ -236,9 +236,18 @@ def run_ours(args):
     end.synchronize()
     ms_dir = start.elapsed_time(end) / n_dir
     dir_bytes = 3 * N_FULL * d * 8
+    # FP64 operations (an FMA or an add counts one) per interval: pass 1 c^T f and
+    # the map composition (d + 2), pass 3 c^T f, A^{-1} f + g e and the carry
+    # (d^2 + 2d + 1); the peak is 2 FP64 FMA per clock per SM (1.25 TFLOP/s
+    # nominal) at 152 SMs x 2.07 GHz
+    fp64_ops = N_FULL * (d * d + 3 * d + 3)
+    fp64_peak = 152 * 2 * 2.07e9
     direct = {"value": N_FULL * d / (ms_dir * 1e-3), "unit": "DoF/s", "ms_per_step": round(ms_dir, 4),
               "precision": "fp64", "bytes_per_dof": 24, "lower_bound_bytes_per_dof": 16,
               "hbm_frac": round(dir_bytes / (ms_dir * 1e-3) / 1e9 / hbm_peak, 4),
+              "roofline": {"bound": "alu", "achieved": round(fp64_ops / (ms_dir * 1e-3) / 1e9, 1),
+                           "peak": round(fp64_peak / 1e9, 1), "unit": "G FP64 ops/s",
+                           "frac": round(fp64_ops / (ms_dir * 1e-3) / fp64_peak, 4), "peak_kind": "nominal"},
               "note": "exact parallel-scan solve (not multigrid), same problem and stream"}
     del u_ex
 

@@ -40,7 +40,6 @@ int count_levels(int64_t N, int64_t n_min, int max_levels) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-const size_t kTailSmemMax = 200 * 1024;
 const int64_t kTailNmax = 8192;
 // Default largest level of the on-chip coarse solver: small, because inside
 // a graph with programmatic dependent launch a streaming kernel on a small
@@ -301,7 +300,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     off = align_up(off + sizeof(double) * P->max_blocks, A);
     P->scan_tiles = (N + tmg::kScanTile - 1) / tmg::kScanTile;
     const size_t off_scan = off;
-    off = align_up(off + sizeof(double) * 3 * P->scan_tiles, A);
+    off = align_up(off + sizeof(double) * (3 + 2 * tmg::kScanNT) * P->scan_tiles, A);
     const size_t off_st = off;
     off = align_up(off + sizeof(tmg::DevState), A);
     P->ws_bytes = off;
@@ -334,8 +333,6 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     memset(P->st_host, 0, sizeof(tmg::DevState));
     ce = cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->s);
     // the attribute is per kernel, shared by every plan: set the common ceiling
-    if (ce == cudaSuccess) ce = P->ops->set_tail_attr(kTailSmemMax);
-    if (ce == cudaSuccess) ce = P->ops_adj->set_tail_attr(kTailSmemMax);
     if (ce == cudaSuccess) ce = P->ops->upload(P);
     if (ce == cudaSuccess) ce = P->ops_adj->upload(P);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->s);

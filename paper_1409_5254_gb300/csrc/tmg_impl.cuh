@@ -84,6 +84,15 @@ inline int grid_flat(const tmg_plan* P, int64_t n) {
 
 // Launch with the programmatic-stream-serialisation attribute when the plan
 // asks for it (every cycle kernel starts with pdl_enter()).
+// Opt a kernel into more than 48 KB of dynamic shared memory.  Called from the
+// function that launches the kernel, once per instantiation: a kernel template
+// instantiated in several translation units has one registration per unit,
+// and the attribute must reach the one that the launching code refers to.
+template <typename... KArgs>
+inline cudaError_t allow_smem(void (*kernel)(KArgs...), size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <typename... KArgs, typename... Args>
 inline void launch(const tmg_plan* P, void (*kernel)(KArgs...), int grid, int block, size_t smem,
                    Args... args) {
@@ -106,27 +115,6 @@ struct Impl {
     static const std::vector<tmg_level_host>& L(const tmg_plan* P) { return DIR == 0 ? P->lev : P->lev_adj; }
 
     static size_t tail_bytes(int64_t Nt, int nl) { return tail_smem_bytes<T, D>(Nt, nl); }
-
-    // Kernel attributes: the on-chip solver's shared memory ceiling, and the
-    // staging buffers of the level-0 down kernel.
-    static cudaError_t set_tail_attr(size_t bytes) {
-        cudaError_t e = cudaFuncSetAttribute(k_tail<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_scan_tiles<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)scan_smem_bytes<D, T>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_scan_apply<T, D, T, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)scan_smem_bytes<D, T>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_scan_tiles<double, D, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)scan_smem_bytes<D, double>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_scan_apply<double, D, double, double>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scan_smem_bytes<D, double>());
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_down0<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)k_down0_smem_bytes<D>());
-    }
 
     static cudaError_t upload(tmg_plan* P) {
         const int nl = P->nlev - P->lt;
@@ -158,18 +146,37 @@ struct Impl {
         S* aggA = static_cast<S*>(P->scan_ws);
         S* aggB = aggA + nt;
         S* ein = aggB + nt;
+        S* thrA = ein + nt;               // per-thread chunk maps, [nt][kScanNT] each
+        S* thrB = thrA + nt * kScanNT;
         const ScanK<S, D> K = scan_consts<S>(L(P)[l]);
         const int grid = (int)(nt < P->max_blocks ? nt : P->max_blocks);
-        launch(P, k_scan_tiles<S, D, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, N, K, aggA, aggB, st);
+        // (a failed opt-in makes the launches below fail, which the caller reports)
+        static const cudaError_t attr_t = allow_smem(k_scan_tiles<S, D, TIO>, scan_smem_bytes<D, TIO>());
+        static const cudaError_t attr_a = allow_smem(k_scan_apply<S, D, TIO, TIO>, scan_smem_bytes<D, TIO>());
+        (void)attr_t;
+        (void)attr_a;
+        launch(P, k_scan_tiles<S, D, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, N, K, aggA, aggB, thrA, thrB,
+               st);
         launch(P, k_scan_prefix<S>, 1, kScanNT, 0, aggA, aggB, nt, e0, e0p, ein, st);
-        launch(P, k_scan_apply<S, D, TIO, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, x, N, K, ein, st);
+        launch(P, k_scan_apply<S, D, TIO, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, x, N, K, ein, thrA, thrB,
+               st);
     }
 
     // tmg_solve_direct: the whole system by the FP64 scan (forward direction).
     static cudaError_t enqueue_direct(tmg_plan* P, const double* f, double u0, double* u) {
-        if (DIR != 0) return cudaErrorInvalidValue;
-        Impl<double, D, 0>::template enqueue_scan<double, double>(P, f, u, 0, u0, nullptr, nullptr);
-        return cudaGetLastError();
+        if constexpr (DIR != 0 || !std::is_same<T, double>::value) {
+            return cudaErrorInvalidValue;   // only the FP64 forward ops carry the direct solve
+        } else {
+            enqueue_scan<double, double>(P, f, u, 0, u0, nullptr, nullptr);
+            return cudaGetLastError();
+        }
+    }
+
+    template <typename... Args>
+    static void launch_tail(tmg_plan* P, Args... args) {
+        static const cudaError_t attr = allow_smem(k_tail<DIR, T, D>, kTailSmemMax);
+        (void)attr;   // a failed opt-in makes the launch fail, which the caller reports
+        launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, args...);
     }
 
     static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr, nullptr, nullptr); }
@@ -204,7 +211,7 @@ struct Impl {
             if (P->scan_coarsest)
                 enqueue_scan<T, T>(P, rT, static_cast<T*>(P->ul[0]), 0, T(0), nullptr, P->st);
             else
-                launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
+                launch_tail(P,  rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
                                                                       nu1, nu2, P->o.gamma, P->st);
             mark(kCatUp0);
             launch(P, k_update0<T>, grid_flat(P, P->N * D), kNT, 0, static_cast<const T*>(P->ul[0]),
@@ -217,6 +224,8 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark(kCatDown0);
+            static const cudaError_t attr = allow_smem(k_down0<DIR, T, D>, k_down0_smem_bytes<D>());
+            if (attr != cudaSuccess) return attr;
             static const int occ = resident_per_sm(k_down0<DIR, T, D>, k_down0_smem_bytes<D>());
             launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, k_down0_smem_bytes<D>(), rT, rl,
                    static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
@@ -267,7 +276,7 @@ struct Impl {
             enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
                                nullptr, P->st);
         else
-            launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, static_cast<const T*>(P->fl[P->lt]),
+            launch_tail(P,  static_cast<const T*>(P->fl[P->lt]),
                                                              static_cast<T*>(P->ul[P->lt]), lk, X, nl,
                                                              P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
         for (int g = ng - 1; g >= 0; --g) {
@@ -333,8 +342,7 @@ struct Impl {
 
     static const tmg_ops* ops() {
         static const tmg_ops o = {sizeof(T),        &tail_bytes,       &upload,        &enqueue_cycle,
-                                  &enqueue_cycle_timed, &enqueue_normF, &enqueue_residual, &set_tail_attr,
-                                  &enqueue_direct};
+                                  &enqueue_cycle_timed, &enqueue_normF, &enqueue_residual, &enqueue_direct};
         return &o;
     }
 };

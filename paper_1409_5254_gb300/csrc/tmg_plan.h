@@ -10,6 +10,9 @@
 #include "tmg_kernels.cuh"
 #include "tmg_scan.cuh"
 
+// Shared-memory ceiling of the single-CTA coarse solver.
+constexpr size_t kTailSmemMax = 200 * 1024;
+
 // FP64 constants of one level, computed once on the host.
 struct tmg_level_host {
     int64_t N;          // intervals
@@ -37,7 +40,8 @@ struct tmg_plan {
     int nlev;            // levels 0..nlev-1
     int lt;              // first level solved on chip (tail), or the coarsest level when scanned
     bool scan_coarsest;  // the coarsest level is too large for the chip: grid-wide scan instead of the tail
-    void* scan_ws;       // tile maps and incoming values of the scans (3 x ntiles x 8 bytes)
+    void* scan_ws;       // tile maps, incoming values and per-thread chunk maps of the scans
+                         // ((3 + 2 kScanNT) x ntiles x 8 bytes)
     int64_t scan_tiles;
     size_t tail_smem;
     std::vector<tmg_level_host> lev;       // constants of L
@@ -86,7 +90,6 @@ struct tmg_ops {
     cudaError_t (*enqueue_cycle_timed)(tmg_plan*, cudaEvent_t* ev, int* cat, int* nev);   // same, events around kernels
     cudaError_t (*enqueue_normF)(tmg_plan*);       // ||F|| for a caller-given start
     cudaError_t (*enqueue_residual)(tmg_plan*, const double* f, double u0, const double* u, double* r);
-    cudaError_t (*set_tail_attr)(size_t bytes);
     cudaError_t (*enqueue_direct)(tmg_plan*, const double* f, double u0, double* u);   // FP64 exact scan solve
 };
 

@@ -8,9 +8,12 @@
 // initial value (u0 on the original system, 0 for a correction equation).
 // Each interval is the affine map e -> alpha e + beta_n; maps compose
 // associatively, so the recurrence is a scan.  Three passes, no block waits
-// for another: (1) every block reduces its tile of intervals to one map,
-// (2) one block scans the tile maps into the incoming value of every tile,
-// (3) every block replays its tile from that value and writes u.
+// for another: (1) every block reduces its tile of intervals to one map and
+// stores, per thread, the map from the tile's incoming value to the value
+// entering that thread's chunk; (2) one block scans the tile maps into the
+// incoming value of every tile; (3) every thread replays its chunk from its
+// stored map and the tile's incoming value and writes u.  On GB300 the scan is
+// bound by FP64 arithmetic, so pass 3 does not recompute pass 1's maps.
 // Tiles are staged in shared memory with coalesced loads; each thread owns a
 // contiguous chunk of kScanPT intervals.
 #pragma once
@@ -109,10 +112,12 @@ __device__ __forceinline__ void block_scan_maps(S A, S B, S& exA, S& exB, S& tot
     __syncthreads();
 }
 
-// Pass 1: one map per tile.
+// Pass 1: one map per tile, and the exclusive map of every thread's chunk
+// within its tile (thrA/thrB [ntiles][kScanNT]).
 template <typename S, int D, typename TIn>
 __global__ void __launch_bounds__(kScanNT) k_scan_tiles(const TIn* __restrict__ f, int64_t N, ScanK<S, D> K,
                                                         S* __restrict__ aggA, S* __restrict__ aggB,
+                                                        S* __restrict__ thrA, S* __restrict__ thrB,
                                                         const DevState* __restrict__ st) {
     pdl_enter();
     if (st != nullptr && st->done) return;
@@ -124,6 +129,8 @@ __global__ void __launch_bounds__(kScanNT) k_scan_tiles(const TIn* __restrict__ 
         S A, B, eA, eB, tA, tB;
         chunk_map<S, D, TIn>(K, sm, A, B);
         block_scan_maps<S>(A, B, eA, eB, tA, tB);
+        thrA[b * kScanNT + threadIdx.x] = eA;
+        thrB[b * kScanNT + threadIdx.x] = eB;
         if (threadIdx.x == 0) {
             aggA[b] = tA;
             aggB[b] = tB;
@@ -169,6 +176,7 @@ __global__ void __launch_bounds__(kScanNT) k_scan_prefix(const S* __restrict__ a
 template <typename S, int D, typename TIn, typename TOut>
 __global__ void __launch_bounds__(kScanNT) k_scan_apply(const TIn* __restrict__ f, TOut* __restrict__ u, int64_t N,
                                                         ScanK<S, D> K, const S* __restrict__ ein,
+                                                        const S* __restrict__ thrA, const S* __restrict__ thrB,
                                                         const DevState* __restrict__ st) {
     pdl_enter();
     if (st != nullptr && st->done) return;
@@ -178,10 +186,7 @@ __global__ void __launch_bounds__(kScanNT) k_scan_apply(const TIn* __restrict__ 
     for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
         const int64_t t0 = b * kScanTile;
         scan_stage<D, TIn>(f, N, t0, sm);
-        S A, B, eA, eB, tA, tB;
-        chunk_map<S, D, TIn>(K, sm, A, B);
-        block_scan_maps<S>(A, B, eA, eB, tA, tB);
-        S e = fma(eA, ein[b], eB);
+        S e = fma(thrA[b * kScanNT + threadIdx.x], ein[b], thrB[b * kScanNT + threadIdx.x]);
         TIn* p = sm + threadIdx.x * (kScanPT * D + 1);   // this thread's chunk; results overwrite it
 #pragma unroll
         for (int i = 0; i < kScanPT; ++i) {
