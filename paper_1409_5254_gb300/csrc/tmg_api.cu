@@ -110,7 +110,7 @@ tmg_status stage_state(tmg_plan* P, const double* f, double u0, double* u, doubl
     h->done = 0;
     h->nF_from_first = nF_from_first;
     h->use_cond = use_cond;
-    h->full = 1;
+    h->full = 2;
     h->rsel = 0;
     h->u_zero = u_zero;
     h->ticket = 0u;

@@ -73,8 +73,10 @@ struct DevState {
     int done;             // 0 running, 1 converged, 2 cycle limit, 3 non-finite
     int nF_from_first;    // 1: the first residual (u = 0) defines ||F||
     int use_cond;         // 1: the solve runs as a graph while-loop
-    int full;             // 1: the next level-0 down kernel evaluates r = F - L u from u in FP64
-                          //    (start of a solve; confirmation of an updated residual that met tol)
+    int full;             // what the next level-0 down kernel evaluates from u in FP64: 0 nothing,
+                          // 1 only the norm of F - L u (confirming an updated residual that met
+                          // tol), 2 the residual itself, stored, with the restriction onto level 1
+                          // (the start of a solve, and after a confirmation failed)
     int rsel;             // which of the two float-pair residual buffers holds the current residual
     int u_zero;           // 1: the solve starts from u = 0 (the first residual is F itself)
     unsigned ticket;      // last-block ticket
@@ -774,10 +776,13 @@ __device__ __forceinline__ void finalize_state(DevState* st, double ss, int mode
     if (!(rel == rel) || rel > 1.0e300) done = 3;
     else if (rel <= st->tol) done = mode == kFinUpdated ? 0 : 1;
     else if (k >= st->max_cycles) done = 2;
-    if (mode == kFinFull) st->full = 0;
+    if (mode == kFinFull) {
+        // a failed norm-only confirmation asks for the residual itself next time
+        st->full = (confirm && done == 0 && st->full == 1) ? 2 : 0;
+    }
     if (mode == kFinUpdated) {
         st->rsel ^= 1;      // the kernel wrote the other buffer
-        if (done == 0 && rel <= st->tol) st->full = 1;
+        if (done == 0 && rel <= st->tol && st->full == 0) st->full = 1;
     }
     if (!confirm) st->cycle = k + 1;
     st->done = done;
@@ -1027,7 +1032,7 @@ constexpr size_t k_down0_smem_bytes() {
 // The main loop of k_down0; FP64NORM selects the norm arithmetic at compile
 // time (FP64 squares in the first cycle, scaled FP32 squares afterwards) so
 // that no branch between the two sits inside the loop.
-template <bool FP64NORM, int DIR, typename T, int D>
+template <bool FP64NORM, int DIR, typename T, int D, bool NORM_ONLY = false>
 __device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
                                              int64_t nchunks,
                                              const Res0& R, const LevelK<T, D>& K, const Xfer<T, D>& X, int nu1,
@@ -1134,12 +1139,14 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restri
                         ssf = fmaf(v, v, ssf);
                     }
                 }
-            store_pair<T, D>(rT, q, rt);
-            if constexpr (kMixed) {
-                if (rlo != nullptr) store_pair<short, D>(rlo, q, rtl);
+            if constexpr (!NORM_ONLY) {
+                store_pair<T, D>(rT, q, rt);
+                if constexpr (kMixed) {
+                    if (rlo != nullptr) store_pair<short, D>(rlo, q, rtl);
+                }
             }
         }
-        if (fc != nullptr) {
+        if (!NORM_ONLY && fc != nullptr) {
             T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
             presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1);
             residual_tracked<DIR, T, D>(rt, c, w, rc);
@@ -1156,9 +1163,9 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restri
 // With rlo != nullptr (mixed form with an updated residual) the residual is
 // stored as a float pair (rT, rlo; low parts encoded by lo_encode) into buffer
 // st->rsel of two (each nchunks * 2 * D values) and the kernel runs only when
-// st->full is set: at the start
-// of a solve, and to confirm an updated residual that met the tolerance; in
-// every other cycle k_updown0 has done its work.
+// st->full is set: to evaluate the residual (the start of a solve, or after a
+// failed confirmation), or only its norm (to confirm an updated residual that
+// met the tolerance); in every other cycle k_updown0 has done its work.
 // Mixed form, first residual of a solve that starts from u = 0: r = F (with
 // a u0 in the first interval) needs no product with u, so F is split into
 // float pairs directly; then the pre-smoothing and restriction of L c = r.
@@ -1238,6 +1245,8 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, short* __rest
         }
     }
     if (!kMixed || st->cycle == 0) ss = down0_loop<true, DIR, T, D>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
+    else if (rlo != nullptr && st->full == 1)   // confirmation: the norm only
+        ss = down0_loop<false, DIR, T, D, true>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
     else ss = down0_loop<false, DIR, T, D>(rT, rlo, fc, nchunks, R, K, X, nu1, H, st);
     grid_norm_finalize<kNT>(ss, partials, st, rlo != nullptr ? kFinFull : kFinPlain);
 }
