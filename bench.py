@@ -273,8 +273,8 @@ def run_ours(args):
                               "up_levels": round(prof["up_levels"], 5), "updown0": round(prof["up0"], 5),
                               "cycle_events": round(prof["cycle"], 5)}}
 
-    kernels_per_cycle = 3 if info["tail_level"] == 0 else 2 * info["tail_level"] + 1
-    launches = args.steps * (st.cycles + 1) * kernels_per_cycle
+    # every kernel of the graph body launches in each of the cycles + 1 loop iterations
+    launches = args.steps * (st.cycles + 1) * plan.launches_per_cycle()
 
     extra = {}
     if rank == 0 and not args.quick:

@@ -182,6 +182,15 @@ tmg_status tmg_plan_info(const tmg_plan *plan, int *num_levels, int *tail_level,
                          double *omega_per_level, int omega_len);
 
 /*
+ * Kernels one correction cycle launches (every kernel of the solve's graph
+ * body, including those that return at once), as counted when the cycle was
+ * last enqueued (a solve, tmg_cycle or tmg_profile_cycle); 0 before that.
+ * A solve of k cycles runs the body k + 1 times (the last one confirms the
+ * residual from u).
+ */
+tmg_status tmg_plan_launches(const tmg_plan *plan, int *per_cycle);
+
+/*
  * Measurement helper: apply reps correction cycles to u (as tmg_cycle) with a
  * CUDA event recorded on the plan's stream around every kernel, and return the
  * mean milliseconds per cycle in ms[0..5]: level-0 down kernel (or the level-0

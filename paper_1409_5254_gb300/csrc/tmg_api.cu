@@ -475,6 +475,12 @@ tmg_status tmg_profile_cycle(tmg_plan* P, const double* f, double u0, double* u,
     return status;
 }
 
+tmg_status tmg_plan_launches(const tmg_plan* P, int* per_cycle) {
+    if (!P || !per_cycle) return TMG_EINVAL;
+    *per_cycle = P->launches_per_cycle;
+    return TMG_OK;
+}
+
 tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, size_t bytes) {
     if (!P || !host_dst || which < 0 || which > 3) return TMG_EINVAL;
     const void* src = nullptr;

@@ -108,6 +108,7 @@ inline void launch(const tmg_plan* P, void (*kernel)(KArgs...), int grid, int bl
     cfg.attrs = attr;
     cfg.numAttrs = P->o.use_pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kernel, ((KArgs)args)...);
+    ++P->launches_per_cycle;
 }
 
 template <typename T, int D, int DIR>
@@ -186,6 +187,7 @@ struct Impl {
     // between ev[i] and ev[i+1] (kCat*) and *nev the number of events
     // (at most 2 * nlev + 4).
     static cudaError_t enqueue_cycle_timed(tmg_plan* P, cudaEvent_t* ev, int* cat, int* nev) {
+        P->launches_per_cycle = 0;
         int iev = 0;
         auto mark = [&](int c) {
             if (ev) {

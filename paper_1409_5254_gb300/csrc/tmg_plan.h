@@ -75,6 +75,9 @@ struct tmg_plan {
     const tmg_ops* ops;        // kernels for L
     const tmg_ops* ops_adj;    // kernels for L^T in reversed time
 
+    // kernels launched by the last enqueued cycle (counted by launch())
+    mutable int launches_per_cycle;
+
     // statistics of the last solve
     int last_cycles;
     double last_rel;

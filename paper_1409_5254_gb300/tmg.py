@@ -42,7 +42,7 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
-           "tmg_stats", "tmg_plan_info", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
+           "tmg_stats", "tmg_plan_info", "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
            "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_destroy_batched"]
 
@@ -73,6 +73,7 @@ def _lib():
         L.tmg_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int]
         L.tmg_inspect.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]
+        L.tmg_plan_launches.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
         L.tmg_profile_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp, ctypes.c_int, _dp, ctypes.c_int]
         L.tmg_residual_norm_noalloc.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                                 _vp, ctypes.c_double, _vp, _vp, _vp, _vp]
@@ -96,7 +97,7 @@ def _lib():
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
         for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual", "tmg_stats",
-                     "tmg_plan_info", "tmg_inspect", "tmg_profile_cycle"):
+                     "tmg_plan_info", "tmg_plan_launches", "tmg_inspect", "tmg_profile_cycle"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -258,6 +259,12 @@ class Plan:
         out = np.empty((n, self.d), dtype=dt)
         _check(_lib().tmg_inspect(self._h, w, level, ctypes.c_void_p(out.ctypes.data), out.nbytes), "tmg_inspect")
         return out
+
+    def launches_per_cycle(self) -> int:
+        """Kernels one cycle launches (tmg_plan_launches)."""
+        n = ctypes.c_int(0)
+        _check(_lib().tmg_plan_launches(self._h, ctypes.byref(n)), "tmg_plan_launches")
+        return n.value
 
     def info(self):
         nl = ctypes.c_int(0)
