@@ -487,9 +487,9 @@ def test_largest_size_ragged_hierarchy(dev):
 def test_launch_count_per_cycle(dev):
     """tmg_plan_launches counts the kernels of one cycle: for the benchmark's
     structure (mixed, V(2,2), 2^20 intervals, 15 levels, coarsest 64 intervals)
-    that is k_down0, 7 two-level down kernels, the single level 13 (whose last
-    block solves the coarsest level), its up kernel, 7 two-level up kernels and
-    k_updown0: 18."""
+    that is k_down0, 6 two-level down kernels (levels 1-12), the single level
+    13 (whose last block solves the coarsest level), its up kernel, 6 two-level
+    up kernels and k_updown0: 16."""
     N = 1 << 20
     prob = inputs.scalar_problem(3, N, 1, lam=1.0, tau=1e-6, u0=1.0)
     with tmg().Plan(1, 1e-6, 1.0, N, precision="mixed", nu1=2, nu2=2) as plan:
@@ -497,4 +497,4 @@ def test_launch_count_per_cycle(dev):
         plan.solve(torch.from_numpy(prob["F"]).to(dev), 1.0)
         info = plan.info()
         assert info["levels"] == 15 and info["tail_level"] == 14
-        assert plan.launches_per_cycle() == 18
+        assert plan.launches_per_cycle() == 16
