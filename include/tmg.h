@@ -242,16 +242,18 @@ tmg_status tmg_residual_norm_noalloc(int p_t, double tau, double lambda, int64_t
 typedef struct tmg_batch tmg_batch;
 
 /*
- * Plan for n_inst independent problems u' + lambda_i u = f_i, u(0) = u0_i,
- * instance i with degree p_t[i] in {0..3}, step tau[i] > 0, lambda[i] >= 0
- * and N[i] >= 1 intervals (host arrays of length n_inst).  Packed layout of
+ * Plan for n_inst (1 <= n_inst <= 2^31 - 1) independent problems
+ * u' + lambda_i u = f_i, u(0) = u0_i, instance i with degree p_t[i] in
+ * {0..5}, step tau[i] > 0, lambda[i] >= 0 and N[i] >= 1 intervals (host
+ * arrays of length n_inst).  Packed layout of
  * every [instance][interval][coefficient] array: instance i starts at value
  * offset off_i = sum_{j<i} N[j] (p_t[j] + 1).  omega and opts as for
  * tmg_setup (V-cycles only: opts->gamma must be 1; levels coarsen down to at
  * most 64 intervals, solved exactly).  Internally the instances are grouped
  * by p_t and padded at their end to a power-of-two length (the system is
  * causal, so this leaves each instance's solution unchanged); every level
- * kernel then covers all instances of a group at once.  Per-instance FP64
+ * kernel then covers all instances of a group still iterating at once.
+ * Per-instance FP64
  * constants are computed on the host.  Returns as tmg_setup.
  */
 tmg_status tmg_setup_batched(tmg_batch **batch, int64_t n_inst, const int *p_t, const double *tau,

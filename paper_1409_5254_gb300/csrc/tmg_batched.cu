@@ -10,6 +10,7 @@
 // arrays are used in place.
 #include <math.h>
 #include <string.h>
+#include <stdint.h>
 
 #include <algorithm>
 #include <map>
@@ -51,6 +52,8 @@ __global__ void kb_init(BatchInst bi, int64_t n) {
         bi.rel[i] = NAN;
         bi.full[i] = 1;
         bi.nscale[i] = 1.0f;
+        bi.act_list[i] = (int)i;
+        bi.full_list[i] = (int)i;
     }
 }
 
@@ -230,6 +233,10 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     off = align_up(off + 4 * n, A);
     const size_t o_nsc = off;
     off = align_up(off + 4 * n, A);
+    const size_t o_al = off;
+    off = align_up(off + 4 * n, A);
+    const size_t o_fl = off;
+    off = align_up(off + 4 * n, A);
     const size_t o_res = off;
     off = align_up(off + sizeof(Res0) * n, A);
     const size_t lk_bytes = (B->o.precision == TMG_MIXED ? sizeof(LevelK<float, kMaxD>) : sizeof(LevelK<double, kMaxD>)) *
@@ -276,6 +283,8 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     G->bi.rel = reinterpret_cast<double*>(b + o_rel);
     G->bi.full = reinterpret_cast<int*>(b + o_full);
     G->bi.nscale = reinterpret_cast<float*>(b + o_nsc);
+    G->bi.act_list = reinterpret_cast<int*>(b + o_al);
+    G->bi.full_list = reinterpret_cast<int*>(b + o_fl);
     G->bi.nvals_per_inst = (long long)G->Ng * G->d;
     G->res = reinterpret_cast<Res0*>(b + o_res);
     G->lk[0] = b + o_lk0;
@@ -401,6 +410,8 @@ tmg_status start_group(tmg_batch* B, tmg_batch_group* G, const double* F, double
     h->max_cycles = B->o.max_cycles;
     h->use_cond = use_graph;
     h->cond = G->cond[dir];
+    h->n_act = (int)G->n;       // kb_init lists every instance in both lists
+    h->n_full = (int)G->n;
     TB_CUDA(cudaMemcpyAsync(G->st, h, sizeof(BatchState), cudaMemcpyHostToDevice, G->s));
     kb_init<<<grid_flat(B, G->n), kBNT, 0, G->s>>>(G->bi, G->n);
     TB_CUDA(cudaGetLastError());
@@ -517,7 +528,7 @@ extern "C" {
 tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, const double* tau,
                              const double* lambda, const int64_t* N, double omega, const tmg_opts* opts,
                              void* stream) {
-    if (!out || n_inst < 1 || !p_t || !tau || !lambda || !N || !(omega < 2.0) || !isfinite(omega)) return TMG_EINVAL;
+    if (!out || n_inst < 1 || n_inst > INT32_MAX || !p_t || !tau || !lambda || !N || !(omega < 2.0) || !isfinite(omega)) return TMG_EINVAL;
     *out = nullptr;
     tmg_opts o;
     tmg_opts_default(&o);

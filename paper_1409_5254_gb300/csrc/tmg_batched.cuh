@@ -10,8 +10,10 @@
 //   * level constants (A^{-1}, g, c, alpha, omega of z_i 2^l) come from a table
 //     indexed by (instance, level);
 //   * every instance has its own residual norm, stopping test and active flag;
-//     a converged instance is frozen (its lanes compute on zeros and store
-//     nothing);
+//     the stopping test compacts the instances still iterating into a list,
+//     and the level kernels tile only the listed instances' pairs (in list
+//     order, as if they were contiguous), so a converged instance costs
+//     nothing in later cycles;
 //   * the coarsest level (at most 64 intervals) is solved exactly by one warp
 //     per instance with a warp-wide scan of the affine interval maps.
 #pragma once
@@ -33,6 +35,9 @@ struct BatchState {
     int active_count;
     int failed;               // instances stopped by the cycle limit or a non-finite norm
     int rsel;                 // updated-residual form: buffer holding the current residual pairs
+    int n_act;                // instances listed in act_list
+    int n_full;               // instances listed in full_list
+    int cnt_full;             // kb_finalize's running count of full_list entries
     unsigned long long cond;
 };
 
@@ -45,7 +50,37 @@ struct BatchInst {
     long long nvals_per_inst;   // values per instance and level-0 vector, N * D
     int* full;        // updated-residual form: 1 = recompute instance i's residual from u next
     float* nscale;    // power of two bringing instance i's residual near 1 (FP32 norms)
+    int* act_list;    // the instances still iterating (st->n_act of them, any order)
+    int* full_list;   // updated-residual form: those whose residual is recomputed from u next (st->n_full)
 };
+
+// Lane `lane` of virtual tile tw over the pairs of the listed instances,
+// concatenated in list order (2^log2P pairs per instance): a tile owns `per`
+// consecutive pairs after H halo lanes, and may straddle two instances (the
+// lane that opens an instance restarts the halo).
+struct ListPos {
+    int64_t q;      // pair index in the level array
+    int64_t inst;   // its instance
+    bool inb;       // the lane maps to a listed pair
+    bool first;     // the pair opens its instance
+};
+
+__device__ __forceinline__ ListPos list_pos(int64_t tw, int per, int H, int lane, const int* __restrict__ list,
+                                            int n_list, int log2P) {
+    const int64_t qv = tw * per + lane - H;
+    const int64_t loc = qv & ((int64_t(1) << log2P) - 1);
+    ListPos p;
+    p.inb = qv >= 0 && qv < ((int64_t)n_list << log2P);
+    p.inst = p.inb ? (int64_t)list[qv >> log2P] : 0;
+    p.q = (p.inst << log2P) + loc;
+    p.first = loc == 0;
+    return p;
+}
+
+// Tiles covering n_list instances of 2^log2P pairs.
+__device__ __forceinline__ int64_t list_tiles(int n_list, int log2P, int per) {
+    return (((int64_t)n_list << log2P) + per - 1) / per;
+}
 
 // Segmented warp sum of v over lanes with the same instance id (ids are
 // non-decreasing along the lanes); the first lane of each run adds the run's
@@ -69,9 +104,9 @@ constexpr int kBNT = 256;
 // FP64 otherwise), norms, r stored in T, zero-start pre-smoothing and
 // restriction onto level 1 (fc == nullptr when level 0 is the coarsest).
 //
-// With rlo != nullptr (mixed form with an updated residual) only instances
-// whose flag full[i] is set are processed (the start of the solve, and
-// confirmations), and the residual is stored as a float pair (rT, rlo; low
+// Without rlo the instances of act_list are processed.  With rlo != nullptr
+// (mixed form with an updated residual) only those of full_list (flag full[i]
+// set: the start of the solve, and confirmations) are, and the residual is stored as a float pair (rT, rlo; low
 // parts encoded by lo_encode) into buffer st->rsel of two (nchunks * 2 * D
 // values each).
 template <int DIR, typename T, int D>
@@ -88,19 +123,17 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
     const double* __restrict__ F = st->F;
     const double* __restrict__ uu = st->u;
     constexpr bool kMixed = std::is_same<T, float>::value;
+    const int* __restrict__ list = rlo != nullptr ? bi.full_list : bi.act_list;
+    const int n_list = rlo != nullptr ? st->n_full : st->n_act;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
-    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
-    const int64_t mask = (1ll << log2N) - 1;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const int64_t q = tw * per + lane - H;
-        const bool inb = q >= 0 && q < nchunks;
-        const int64_t inst = inb ? (2 * q) >> log2N : 0;
-        const bool act = inb && bi.active[inst] && (rlo == nullptr || bi.full[inst]);
-        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
+        const ListPos P = list_pos(tw, per, H, lane, list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
-        const bool first = ((2 * q) & mask) == 0;
         const LevelK<T, D> K = lk[inst * nlev];
         const Res0 R = res[inst];
         double uv[2][D], Fv[2][D];
@@ -179,6 +212,9 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
 //   kFinUpdated: after kb_updown0 updated every active instance's residual:
 //     meeting tol flags the instance for confirmation instead of stopping it;
 //     the cycle counter advances and the residual buffers swap.
+// Every warp appends its instances that keep iterating to act_list (and,
+// after kFinUpdated, the flagged ones to full_list) with one atomic each; the
+// last block publishes the counts for the next kernels.
 static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, BatchInst bi, int64_t n_inst,
                                                     int mode = kFinPlain) {
     if (st->done) {                          // a finished batch must also end the graph loop
@@ -187,54 +223,67 @@ static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, Batch
         return;
     }
     const int k = mode == kFinUpdated ? st->cycle + 1 : st->cycle;   // corrections applied
-    int act_local = 0, fail_local = 0;
-    for (int64_t i = (int64_t)blockIdx.x * kBNT + threadIdx.x; i < n_inst; i += (int64_t)gridDim.x * kBNT) {
-        if (!bi.active[i]) continue;
-        if (mode == kFinFull && !bi.full[i]) {
-            ++act_local;
-            continue;
+    const int lane = threadIdx.x & 31;
+    int fail_local = 0;
+    const int64_t stride = (int64_t)gridDim.x * kBNT;
+    for (int64_t base = (int64_t)blockIdx.x * kBNT + (threadIdx.x & ~31); base < n_inst; base += stride) {
+        const int64_t i = base + lane;            // the warp stays converged: lists are built by ballot
+        bool keep = false;
+        if (i < n_inst && bi.active[i]) {
+            if (mode == kFinFull && !bi.full[i]) {
+                keep = true;
+            } else {
+                // kb_updown0 sums squares scaled by nscale[i]^2
+                const double nrm = sqrt(bi.norm2[i]) / (mode == kFinUpdated ? (double)bi.nscale[i] : 1.0);
+                bi.norm2[i] = 0.0;
+                if (k == 0 && mode != kFinUpdated) bi.nF[i] = nrm;
+                const double nF = bi.nF[i];
+                const double rel = nF > 0.0 ? nrm / nF : nrm;
+                const bool bad = !(rel == rel) || rel > 1.0e300;
+                if (mode != kFinPlain) {
+                    // scale of the next FP32 norm of this instance
+                    const double rms = nrm / sqrt((double)bi.nvals_per_inst);
+                    int ex = 0;
+                    if (rms > 0.0 && rms < 1.0e300) ex = -ilogb(rms);
+                    ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
+                    bi.nscale[i] = ldexpf(1.0f, ex);
+                }
+                const bool met = rel <= st->tol;
+                if (mode == kFinUpdated && !bad && met) {
+                    bi.full[i] = 1;                  // confirm from u at the start of the next cycle
+                    keep = true;
+                } else if (bad || met || k >= st->max_cycles) {
+                    bi.active[i] = 0;
+                    bi.cycles[i] = k;
+                    bi.rel[i] = rel;
+                    if (bad || !met) ++fail_local;
+                } else {
+                    if (mode == kFinFull) bi.full[i] = 0;
+                    keep = true;
+                }
+            }
         }
-        // kb_updown0 sums squares scaled by nscale[i]^2
-        const double nrm = sqrt(bi.norm2[i]) / (mode == kFinUpdated ? (double)bi.nscale[i] : 1.0);
-        bi.norm2[i] = 0.0;
-        if (k == 0 && mode != kFinUpdated) bi.nF[i] = nrm;
-        const double nF = bi.nF[i];
-        const double rel = nF > 0.0 ? nrm / nF : nrm;
-        const bool bad = !(rel == rel) || rel > 1.0e300;
-        if (mode != kFinPlain) {
-            // scale of the next FP32 norm of this instance
-            const double rms = nrm / sqrt((double)bi.nvals_per_inst);
-            int ex = 0;
-            if (rms > 0.0 && rms < 1.0e300) ex = -ilogb(rms);
-            ex = ex < -100 ? -100 : (ex > 100 ? 100 : ex);
-            bi.nscale[i] = ldexpf(1.0f, ex);
+        const bool to_full = keep && mode == kFinUpdated && bi.full[i];
+        const unsigned ka = __ballot_sync(kFull, keep);
+        const unsigned kf = __ballot_sync(kFull, to_full);
+        int oa = 0, of = 0;
+        if (lane == 0) {
+            if (ka) oa = atomicAdd(&st->active_count, __popc(ka));
+            if (kf) of = atomicAdd(&st->cnt_full, __popc(kf));
         }
-        const bool met = rel <= st->tol;
-        if (mode == kFinUpdated && !bad && met) {
-            bi.full[i] = 1;                  // confirm from u at the start of the next cycle
-            ++act_local;
-        } else if (bad || met || k >= st->max_cycles) {
-            bi.active[i] = 0;
-            bi.cycles[i] = k;
-            bi.rel[i] = rel;
-            if (bad || !met) ++fail_local;
-        } else {
-            if (mode == kFinFull) bi.full[i] = 0;
-            ++act_local;
-        }
+        oa = __shfl_sync(kFull, oa, 0);
+        of = __shfl_sync(kFull, of, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (keep) bi.act_list[oa + __popc(ka & below)] = (int)i;
+        if (to_full) bi.full_list[of + __popc(kf & below)] = (int)i;
     }
-    __shared__ int sa, sf;
+    __shared__ int sf;
     __shared__ int last;
-    if (threadIdx.x == 0) {
-        sa = 0;
-        sf = 0;
-    }
+    if (threadIdx.x == 0) sf = 0;
     __syncthreads();
-    if (act_local) atomicAdd(&sa, act_local);
     if (fail_local) atomicAdd(&sf, fail_local);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (sa) atomicAdd(&st->active_count, sa);
         if (sf) atomicAdd(&st->failed, sf);
         __threadfence();
         last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
@@ -243,7 +292,10 @@ static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, Batch
     if (!last || threadIdx.x != 0) return;
     __threadfence();
     const int remaining = atomicAdd(&st->active_count, 0);
+    st->n_act = remaining;
+    st->n_full = atomicAdd(&st->cnt_full, 0);   // zero unless kFinUpdated flagged some
     st->active_count = 0;
+    st->cnt_full = 0;
     st->ticket = 0u;
     if (mode == kFinPlain) st->cycle = k + 1;
     if (mode == kFinUpdated) {
@@ -264,16 +316,13 @@ __global__ void __launch_bounds__(kBNT) kb_down(const T* __restrict__ f, T* __re
     if (st->done) return;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
-    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
-    const int64_t mask = (1ll << log2N) - 1;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const int64_t q = tw * per + lane - H;
-        const bool inb = q >= 0 && q < nchunks;
-        const int64_t inst = inb ? (2 * q) >> log2N : 0;
-        const bool act = inb && bi.active[inst];
-        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
-        const bool first = ((2 * q) & mask) == 0;
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
         const LevelK<T, D> K = lk[inst * nlev + level];
         T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
         load_pair<T, D>(f, q, act, fv);
@@ -292,16 +341,13 @@ __global__ void __launch_bounds__(kBNT) kb_up(const T* __restrict__ f, const T* 
     if (st->done) return;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
-    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
-    const int64_t mask = (1ll << log2N) - 1;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const int64_t q = tw * per + lane - H;
-        const bool inb = q >= 0 && q < nchunks;
-        const int64_t inst = inb ? (2 * q) >> log2N : 0;
-        const bool act = inb && bi.active[inst];
-        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
-        const bool first = ((2 * q) & mask) == 0;
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
         const LevelK<T, D> K = lk[inst * nlev + level];
         T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
         load_pair<T, D>(f, q, act, fv);
@@ -322,17 +368,14 @@ __global__ void __launch_bounds__(kBNT) kb_up0(const T* __restrict__ rT, const T
     double* __restrict__ uu = st->u;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
-    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
-    const int64_t mask = (1ll << log2N) - 1;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const int64_t q = tw * per + lane - H;
-        const bool inb = q >= 0 && q < nchunks;
-        const int64_t inst = inb ? (2 * q) >> log2N : 0;
-        const bool act = inb && bi.active[inst];
-        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
-        const bool first = ((2 * q) & mask) == 0;
         const LevelK<T, D> K = lk[inst * nlev];
         T rt[2][D], h[2][D], c[2][D], w[2][D], cc[D];
         double uv[2][D];
@@ -367,8 +410,9 @@ __global__ void __launch_bounds__(kBNT) kb_coarse(const T* __restrict__ f, T* __
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kBNT) >> 5;
-    for (int64_t inst = wid; inst < n_inst; inst += nw) {
-        if (!bi.active[inst]) continue;            // uniform across the warp
+    const int n_list = st->n_act;
+    for (int64_t j = wid; j < n_list; j += nw) {
+        const int64_t inst = bi.act_list[j];
         const LevelK<T, D> K = lk[inst * nlev + level];
         const int n0 = 2 * lane, n1 = 2 * lane + 1;
         T f0[D], f1[D];
@@ -427,17 +471,14 @@ __global__ void __launch_bounds__(kBNT, D <= 2 ? 4 : 2) kb_updown0(float* __rest
     short* __restrict__ rl_out = rl + (1 - sel) * nv;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
-    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
-    const int64_t mask = (1ll << log2N) - 1;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const int64_t q = tw * per + lane - H;
-        const bool inb = q >= 0 && q < nchunks;
-        const int64_t inst = inb ? (2 * q) >> log2N : 0;
-        const bool act = inb && bi.active[inst];
-        if (!__any_sync(kFull, act)) continue;     // no lane of the tile has work (warp-uniform)
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
-        const bool first = ((2 * q) & mask) == 0;
         const LevelK<float, D> K = lk[inst * nlev];
         const Res0 R = res[inst];
         const float nsc = bi.nscale[inst];
