@@ -50,7 +50,7 @@ __global__ void kb_init(BatchInst bi, int64_t n) {
         bi.norm2[i] = 0.0;
         bi.cycles[i] = 0;
         bi.rel[i] = NAN;
-        bi.full[i] = 1;
+        bi.full[i] = 2;      // the first residual is computed (and stored) in full
         bi.nscale[i] = 1.0f;
         bi.act_list[i] = (int)i;
         bi.full_list[i] = (int)i;

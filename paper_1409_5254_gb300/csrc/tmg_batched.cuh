@@ -48,10 +48,10 @@ struct BatchInst {
     int* cycles;      // cycles applied when instance i stopped
     double* rel;      // its final relative residual
     long long nvals_per_inst;   // values per instance and level-0 vector, N * D
-    int* full;        // updated-residual form: 1 = recompute instance i's residual from u next
+    int* full;        // updated-residual form, next kb_down0: 1 = confirm (norm of F - L u), 2 = recompute r from u
     float* nscale;    // power of two bringing instance i's residual near 1 (FP32 norms)
     int* act_list;    // the instances still iterating (st->n_act of them, any order)
-    int* full_list;   // updated-residual form: those whose residual is recomputed from u next (st->n_full)
+    int* full_list;   // updated-residual form: the instances with full[i] != 0 (st->n_full of them)
 };
 
 // Lane `lane` of virtual tile tw over the pairs of the listed instances,
@@ -100,15 +100,71 @@ __device__ __forceinline__ void segmented_norm_add(double v, int64_t id, bool va
 
 constexpr int kBNT = 256;
 
+// Norm contributions without an FP64 operation per value.  A warp whose
+// valid lanes all belong to one instance (the common case) sums in FP32 --
+// warp_sumsq for raw values, a plain warp sum for squares already scaled near
+// 1 -- and adds the total with one atomic; a warp across instances falls back
+// to per-lane FP64 partials and segmented_norm_add.
+__device__ __forceinline__ bool one_instance(int64_t id, bool valid, unsigned& id0) {
+    const unsigned lo = __reduce_min_sync(kFull, valid ? (unsigned)id : 0xFFFFFFFFu);
+    const unsigned hi = __reduce_max_sync(kFull, valid ? (unsigned)id : 0u);
+    id0 = lo;                 // 0xFFFFFFFF: no valid lane
+    return lo >= hi;
+}
+
+template <int n>
+__device__ __forceinline__ void segmented_sumsq(const float (&v)[n], int64_t id, bool valid, double* norm2) {
+    unsigned id0;
+    if (one_instance(id, valid, id0)) {
+        float x[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) x[i] = valid ? v[i] : 0.f;
+        const double t = warp_sumsq<n>(x);
+        if ((threadIdx.x & 31) == 0 && id0 != 0xFFFFFFFFu) atomicAdd(&norm2[id0], t);
+        return;
+    }
+    unsigned em = 0u;                       // lane-own power-of-two scale, as in warp_sumsq
+#pragma unroll
+    for (int i = 0; i < n; ++i) em = max(em, (__float_as_uint(v[i]) >> 23) & 0xFFu);
+    int k = (int)em - 127;
+    k = k < -126 ? -126 : (k > 126 ? 126 : k);
+    const float s = __uint_as_float((unsigned)(127 - k) << 23);
+    float ss = 0.f;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const float x = v[i] * s;
+        ss = fmaf(x, x, ss);
+    }
+    segmented_norm_add(f2d_int(ss) * __hiloint2double((2 * k + 1023) << 20, 0), id, valid, norm2);
+}
+
+__device__ __forceinline__ void segmented_add_f(float v, int64_t id, bool valid, double* norm2) {
+    unsigned id0;
+    if (one_instance(id, valid, id0)) {
+        float t = valid ? v : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(kFull, t, off);
+        if ((threadIdx.x & 31) == 0 && id0 != 0xFFFFFFFFu) atomicAdd(&norm2[id0], f2d_int(t));
+        return;
+    }
+    segmented_norm_add(f2d_int(v), id, valid, norm2);
+}
+
+
 // Level 0: residual of every active instance (float pairs for the mixed form,
 // FP64 otherwise), norms, r stored in T, zero-start pre-smoothing and
 // restriction onto level 1 (fc == nullptr when level 0 is the coarsest).
+// In the first cycle of a solve u = 0, so u is not read and r = F (with
+// u0_i a in each instance's first interval); the mixed form splits F into
+// float pairs directly.
 //
 // Without rlo the instances of act_list are processed.  With rlo != nullptr
-// (mixed form with an updated residual) only those of full_list (flag full[i]
-// set: the start of the solve, and confirmations) are, and the residual is stored as a float pair (rT, rlo; low
+// (mixed form with an updated residual) only those of full_list are:
+// full[i] = 2 recomputes the residual from u (the start of the solve, or
+// after a failed confirmation) and stores it as a float pair (rT, rlo; low
 // parts encoded by lo_encode) into buffer st->rsel of two (nchunks * 2 * D
-// values each).
+// values each), with its restriction; full[i] = 1 only confirms an updated
+// residual that met the tolerance: its norm, nothing stored.
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
                                                  int64_t nchunks, int log2N, const LevelK<T, D>* __restrict__ lk,
@@ -122,6 +178,7 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
     }
     const double* __restrict__ F = st->F;
     const double* __restrict__ uu = st->u;
+    const bool start = st->cycle == 0;
     constexpr bool kMixed = std::is_same<T, float>::value;
     const int* __restrict__ list = rlo != nullptr ? bi.full_list : bi.act_list;
     const int n_list = rlo != nullptr ? st->n_full : st->n_act;
@@ -134,27 +191,44 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
+        const bool keep = act && (rlo == nullptr || bi.full[inst] == 2);   // store r and its restriction
         const LevelK<T, D> K = lk[inst * nlev];
         const Res0 R = res[inst];
         double uv[2][D], Fv[2][D];
         short rq[2][D];
-        load_pair<double, D>(uu, q, act, uv);
+        load_pair<double, D>(uu, q, act && !start, uv);
         load_pair<double, D>(F, q, act, Fv);
         const double u0i = act ? st->u0[inst] : 0.0;
         T rt[2][D];
         if constexpr (kMixed) {
-            ff us0[D], us1[D], sE0, sB0, sE1, sB1;
-            small_sums<DIR, D>(uv[0], us0, sE0, sB0);
-            small_sums<DIR, D>(uv[1], us1, sE1, sB1);
-            double up0 = shfl_prev(uv[1][0]);
-            ff sp{shfl_prev(sB1.hi), shfl_prev(sB1.lo)};
-            if (first) {                 // the value before the instance's first interval: b^T u = u0_i
-                up0 = u0i;
-                sp = ff{0.f, 0.f};
-            }
             float r0[D], r1[D], l0[D], l1[D];
-            residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0, l0);
-            residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1, l1);
+            if (start) {
+                if (first) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) Fv[0][k] += acoef<DIR>(k, u0i);
+                }
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const ff s0 = split_d(Fv[0][k]), s1 = split_d(Fv[1][k]);
+                    const ff n0 = two_sum(s0.hi, s0.lo), n1 = two_sum(s1.hi, s1.lo);   // rounded high parts
+                    r0[k] = n0.hi;
+                    l0[k] = n0.lo;
+                    r1[k] = n1.hi;
+                    l1[k] = n1.lo;
+                }
+            } else {
+                ff us0[D], us1[D], sE0, sB0, sE1, sB1;
+                small_sums<DIR, D>(uv[0], us0, sE0, sB0);
+                small_sums<DIR, D>(uv[1], us1, sE1, sB1);
+                double up0 = shfl_prev(uv[1][0]);
+                ff sp{shfl_prev(sB1.hi), shfl_prev(sB1.lo)};
+                if (first) {                 // the value before the instance's first interval: b^T u = u0_i
+                    up0 = u0i;
+                    sp = ff{0.f, 0.f};
+                }
+                residual0_ff<DIR, D>(Fv[0], uv[0], us0, up0, sp, sE0, R, r0, l0);
+                residual0_ff<DIR, D>(Fv[1], uv[1], us1, uv[0][0], sB0, sE1, R, r1, l1);
+            }
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 rt[0][k] = act ? r0[k] : 0.f;
@@ -162,6 +236,13 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
                 rq[0][k] = lo_encode(r0[k], l0[k]);
                 rq[1][k] = lo_encode(r1[k], l1[k]);
             }
+            float sq[2 * D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                sq[k] = rt[0][k];
+                sq[D + k] = rt[1][k];
+            }
+            segmented_sumsq<2 * D>(sq, inst, own, bi.norm2);
         } else {
             double r[2][D];
             const double b0 = bval<DIR, double, D>(uv[0]);
@@ -172,43 +253,37 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
             const double E1 = DIR == 0 ? b1 : endval<double, D>(uv[1]);
             residual0<DIR, D>(Fv[0], uv[0], ep, E0, R, r[0]);
             residual0<DIR, D>(Fv[1], uv[1], b0, E1, R, r[1]);
+            double ss = 0.0;
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int k = 0; k < D; ++k) rt[i][k] = act ? (T)r[i][k] : T(0);
+                for (int k = 0; k < D; ++k) {
+                    rt[i][k] = act ? (T)r[i][k] : T(0);
+                    ss = fma((double)rt[i][k], (double)rt[i][k], ss);
+                }
+            segmented_norm_add(ss, inst, own, bi.norm2);
         }
-        double ss = 0.0;
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                double v;
-                if constexpr (kMixed) v = f2d_int(rt[i][k]);   // no conversion instruction on the FP64 pipe
-                else v = (double)rt[i][k];
-                ss = fma(v, v, ss);
-            }
-        segmented_norm_add(ss, inst, own, bi.norm2);
-        if (own) {
+        if (own && keep) {
             store_pair<T, D>(rT, q, rt);
             if constexpr (kMixed) {
                 if (rlo != nullptr) store_pair<short, D>(rlo, q, rq);
             }
         }
-        if (fc != nullptr) {
+        if (fc != nullptr && __any_sync(kFull, keep)) {
             T h[2][D], c[2][D], w[2][D], rc[2][D], out[D];
             presmooth_zero<DIR, T, D>(K, rt, h, c, w, nu1, first);
             residual_tracked<DIR, T, D>(rt, c, w, rc, first);
             restrict_pair<T, D>(X, rc, out);
-            if (own) VecIO<T, D>::store(fc + q * D, out);
+            if (own && keep) VecIO<T, D>::store(fc + q * D, out);
         }
     }
 }
 
 // Per-instance stopping test.
 //   kFinPlain: after the level-0 residual of cycle k, computed from u.
-//   kFinFull (updated-residual form): after kb_down0 recomputed the residual of
-//     the instances flagged full -- the start of the solve, or a confirmation;
-//     only those instances are tested, and a failed confirmation clears the flag.
+//   kFinFull (updated-residual form): after kb_down0 evaluated the residual of
+//     the instances flagged full -- the start of the solve, a confirmation, or
+//     the recomputation after a failed one; only those instances are tested.
 //   kFinUpdated: after kb_updown0 updated every active instance's residual:
 //     meeting tol flags the instance for confirmation instead of stopping it;
 //     the cycle counter advances and the residual buffers swap.
@@ -250,7 +325,9 @@ static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, Batch
                 }
                 const bool met = rel <= st->tol;
                 if (mode == kFinUpdated && !bad && met) {
-                    bi.full[i] = 1;                  // confirm from u at the start of the next cycle
+                    // confirm from u at the start of the next cycle (a pending full
+                    // recomputation, flag 2, confirms as well)
+                    if (bi.full[i] == 0) bi.full[i] = 1;
                     keep = true;
                 } else if (bad || met || k >= st->max_cycles) {
                     bi.active[i] = 0;
@@ -258,12 +335,14 @@ static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, Batch
                     bi.rel[i] = rel;
                     if (bad || !met) ++fail_local;
                 } else {
-                    if (mode == kFinFull) bi.full[i] = 0;
+                    // a failed confirmation (flag 1) recomputes the residual in the next
+                    // cycle; this cycle goes on with the updated one
+                    if (mode == kFinFull) bi.full[i] = bi.full[i] == 1 ? 2 : 0;
                     keep = true;
                 }
             }
         }
-        const bool to_full = keep && mode == kFinUpdated && bi.full[i];
+        const bool to_full = keep && mode == kFinUpdated && bi.full[i] != 0;
         const unsigned ka = __ballot_sync(kFull, keep);
         const unsigned kf = __ballot_sync(kFull, to_full);
         int oa = 0, of = 0;
@@ -524,7 +603,7 @@ __global__ void __launch_bounds__(kBNT, D <= 2 ? 4 : 2) kb_updown0(float* __rest
             store_pair<float, D>(rh_out, q, r);
             store_pair<short, D>(rl_out, q, rq);
         }
-        segmented_norm_add(f2d_int(ssf), inst, own, bi.norm2);   // in units of nscale^2 (kb_finalize)
+        segmented_add_f(ssf, inst, own, bi.norm2);   // in units of nscale^2 (kb_finalize)
         // the next cycle's way down on L c' = r
         float rc[2][D], out[D];
         presmooth_zero<DIR, float, D>(K, r, h, c, w, nu1, first);

@@ -618,6 +618,35 @@ __device__ __forceinline__ double f2d_int(float c) {
     return __hiloint2double((int)hi, (int)(b << 29));
 }
 
+// Sum over the warp of the squares of every lane's n floats, as a double,
+// with no FP64 operation per value (GB300's FP64 pipe is narrow).  All values
+// are scaled by one power of two common to the warp, taken from the largest
+// exponent among the lanes so that no square can overflow; the squares are
+// summed in FP32 (relative error about 2^-17 for 32 n terms, far finer than a
+// stopping test needs) and the total is widened and rescaled once.  Squares
+// more than 2^-126 below the largest are flushed (a relative change of at
+// most 32 n 2^-126).  An Inf or NaN value makes the total Inf or NaN.  All
+// 32 lanes must call it; each receives the warp total.
+template <int n>
+__device__ __forceinline__ double warp_sumsq(const float (&v)[n]) {
+    unsigned em = 0u;
+#pragma unroll
+    for (int i = 0; i < n; ++i) em = max(em, (__float_as_uint(v[i]) >> 23) & 0xFFu);
+    em = __reduce_max_sync(kFull, em);
+    int k = (int)em - 127;                           // every |v| < 2^(k+1)
+    k = k < -126 ? -126 : (k > 126 ? 126 : k);
+    const float s = __uint_as_float((unsigned)(127 - k) << 23);   // 2^-k, exact scaling
+    float ss = 0.f;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const float x = v[i] * s;
+        ss = fmaf(x, x, ss);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(kFull, ss, off);
+    return f2d_int(ss) * __hiloint2double((2 * k + 1023) << 20, 0);   // times 2^(2k)
+}
+
 // Product of two float pairs (lo*lo dropped), as an unnormalised pair.
 __device__ __forceinline__ ff mul_ff(float ah, float al, ff b) {
     ff p;
@@ -1127,13 +1156,22 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restri
 #pragma unroll
                 for (int k = 0; k < D; ++k) rt[i][k] = inb ? (T)r[i][k] : T(0);
         }
+        if constexpr (FP64NORM && kMixed) {
+            float sq[2 * D];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int k = 0; k < D; ++k) sq[i * D + k] = own ? (float)rt[i][k] : 0.f;
+            const double t = warp_sumsq<2 * D>(sq);
+            if (lane == 0) ss += t;
+        }
         if (own) {
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     if constexpr (FP64NORM) {
-                        ss = fma((double)rt[i][k], (double)rt[i][k], ss);
+                        if constexpr (!kMixed) ss = fma((double)rt[i][k], (double)rt[i][k], ss);
                     } else {
                         const float v = (float)rt[i][k] * nsc;
                         ssf = fmaf(v, v, ssf);
@@ -1201,14 +1239,16 @@ __device__ __forceinline__ double start0_loop(float* __restrict__ rT, short* __r
                 rt[i][k] = n.hi;
                 rq[i][k] = lo_encode(n.hi, n.lo);
             }
-        if (own) {
+        {
+            float sq[2 * D];
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const double v = f2d_int(rt[i][k]);
-                    ss = fma(v, v, ss);
-                }
+                for (int k = 0; k < D; ++k) sq[i * D + k] = own ? rt[i][k] : 0.f;
+            const double t = warp_sumsq<2 * D>(sq);
+            if (lane == 0) ss += t;
+        }
+        if (own) {
             store_pair<float, D>(rT, q, rt);
             store_pair<short, D>(rlo, q, rq);
         }
