@@ -445,7 +445,9 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
                      "max_cycles": int(replicas.max_over_ranks(mx, dev)),
                      "max_rel_res": replicas.max_over_ranks(float(rel.max()), dev),
                      "setup_ms_with_autotune": round(setup_ms, 1),
-                     "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid")}
+                     "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid"),
+                     "autotune_whole_batch_ms": {k: (round(v, 3) if v == v else None)
+                                                 for k, v in info["whole_batch_ms"].items()}}
     out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv_all), "dofs": dofs, "groups": info["groups"],
                            "padded_dofs": info["padded_values"], **res}
     del f, u, u0

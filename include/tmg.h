@@ -284,6 +284,16 @@ tmg_status tmg_stats_batched(const tmg_batch *batch, int *cycles, double *rel_re
 tmg_status tmg_batch_info(const tmg_batch *batch, int *n_groups, int64_t *padded_values);
 
 /*
+ * The autotuner's whole-batch check (schedule TMG_SCHED_AUTO): per-group
+ * times are taken one group at a time, but a solve runs all groups at once,
+ * so when some group chose the CTA form the setup also times one solve of the
+ * whole synthetic batch with the per-group choices (*ms_tuned) and with every
+ * group on the grid form (*ms_grid), and keeps the faster.  Both are NAN when
+ * the check did not run (one group, no CTA choice, or another schedule).
+ */
+tmg_status tmg_batch_tune_info(const tmg_batch *batch, double *ms_tuned, double *ms_grid);
+
+/*
  * Group g (0 <= g < n_groups): degree, padded length, instances, the schedule
  * it runs (TMG_SCHED_GRID or TMG_SCHED_CTA), and the milliseconds the setup
  * autotuner measured for one synthetic solve in each form (NAN where a form

@@ -474,6 +474,8 @@ bool aligned16(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 15
 // one solve of a synthetic problem (f = 0, u0 = 1: each instance a decaying
 // mode) in each form on the group's own scratch arrays, after one untimed
 // solve that builds the form's graph or loads its kernel, and keep the faster.
+tmg_status drain(tmg_batch* B, tmg_status s);
+
 tmg_status autotune(tmg_batch* B) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     TB_CUDA(cudaEventCreate(&e0));
@@ -508,6 +510,62 @@ tmg_status autotune(tmg_batch* B) {
         }
         G->sched = G->ms_tune[1] < G->ms_tune[0] ? TMG_SCHED_CTA : TMG_SCHED_GRID;
     }
+    // The times above are taken one group at a time, but a solve runs all
+    // groups at once, and a CTA-per-instance block holds its SM's resources
+    // for the whole solve of its instance.  So time the whole batch on the
+    // same synthetic problem with the choices above and with every group on
+    // the grid form, and keep the faster assignment.
+    bool any_cta = false;
+    for (tmg_batch_group* G : B->groups) any_cta = any_cta || G->sched == TMG_SCHED_CTA;
+    if (out == TMG_OK && any_cta && B->groups.size() > 1) {
+        std::vector<int> tuned;
+        for (tmg_batch_group* G : B->groups) {
+            tuned.push_back(G->sched);
+            if (out != TMG_OK || G->cta_ok) continue;   // tuned groups hold the synthetic problem already
+            out = ensure_gather(G);
+            if (out != TMG_OK) break;
+            std::vector<double> ones(G->n, 1.0);
+            cudaError_t e = cudaMemsetAsync(G->Fg, 0, sizeof(double) * G->n * G->Ng * G->d, G->s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(G->u0g, ones.data(), 8 * G->n, cudaMemcpyHostToDevice, G->s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(G->s);
+            if (e != cudaSuccess) out = fail(e);
+        }
+        float whole[2] = {NAN, NAN};
+        for (int pass = 0; pass < 2 && out == TMG_OK; ++pass) {
+            for (size_t g = 0; g < B->groups.size(); ++g)
+                B->groups[g]->sched = pass == 0 ? tuned[g] : TMG_SCHED_GRID;
+            for (int rep = 0; rep < 2 && out == TMG_OK; ++rep) {
+                cudaError_t e = cudaEventRecord(B->fork, B->s);
+                if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e0, B->s);
+                for (tmg_batch_group* G : B->groups) {
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(G->s, B->fork, 0);
+                    if (e != cudaSuccess) break;
+                    tmg_status s = start_group(B, G, G->Fg, G->ug, G->u0g, 0);
+                    if (s != TMG_OK) {
+                        out = s;
+                        break;
+                    }
+                    e = cudaEventRecord(G->done, G->s);
+                }
+                for (tmg_batch_group* G : B->groups)
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->s, G->done, 0);
+                if (e == cudaSuccess && rep == 1) e = cudaEventRecord(e1, B->s);
+                if (e != cudaSuccess && out == TMG_OK) out = fail(e);
+                for (tmg_batch_group* G : B->groups) {
+                    const tmg_status s = finish_group(B, G);
+                    if (s != TMG_OK && s != TMG_ENOTCONV && out == TMG_OK) out = s;
+                }
+            }
+            float ms = NAN;
+            if (out == TMG_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) whole[pass] = ms;
+        }
+        const bool keep_tuned = !(whole[1] < whole[0]);
+        for (size_t g = 0; g < B->groups.size(); ++g)
+            B->groups[g]->sched = keep_tuned ? tuned[g] : TMG_SCHED_GRID;
+        B->ms_whole[0] = whole[0];
+        B->ms_whole[1] = whole[1];
+    }
+    if (out != TMG_OK) drain(B, out);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return out;
@@ -745,6 +803,13 @@ tmg_status tmg_batch_info(const tmg_batch* B, int* n_groups, int64_t* padded_val
         for (auto* G : B->groups) t += G->n * G->Ng * G->d;
         *padded_values = t;
     }
+    return TMG_OK;
+}
+
+tmg_status tmg_batch_tune_info(const tmg_batch* B, double* ms_tuned, double* ms_grid) {
+    if (!B || !ms_tuned || !ms_grid) return TMG_EINVAL;
+    *ms_tuned = B->ms_whole[0];
+    *ms_grid = B->ms_whole[1];
     return TMG_OK;
 }
 

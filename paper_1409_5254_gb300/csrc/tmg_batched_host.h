@@ -70,6 +70,7 @@ struct tmg_batch {
     void* table;          // device copies of off, N (int64), tau (double), p (int) for the gradient kernel
     std::vector<int> cycles;
     std::vector<double> rel;
+    double ms_whole[2] = {NAN, NAN};   // autotuner: whole synthetic batch, per-group choices / all grid
 };
 
 namespace tmgb {

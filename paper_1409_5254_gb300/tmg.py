@@ -44,7 +44,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
            "tmg_stats", "tmg_plan_info", "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
-           "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_destroy_batched"]
+           "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched"]
 
 
 def library_path() -> str:
@@ -88,10 +88,11 @@ def _lib():
         L.tmg_stats_batched.argtypes = [_vp, _ip, _dp, _ip]
         L.tmg_batch_info.argtypes = [_vp, _ip, _lp]
         L.tmg_batch_group_info.argtypes = [_vp, ctypes.c_int, _ip, _lp, _lp, _ip, _dp, _dp]
+        L.tmg_batch_tune_info.argtypes = [_vp, _dp, _dp]
         L.tmg_destroy_batched.argtypes = [_vp]
         L.tmg_destroy_batched.restype = None
         for name in ("tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched", "tmg_stats_batched",
-                     "tmg_batch_info", "tmg_batch_group_info"):
+                     "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info"):
             getattr(L, name).restype = ctypes.c_int
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
@@ -412,7 +413,10 @@ class Batch:
             groups.append({"p_t": p.value, "padded_length": Ng.value, "instances": n.value,
                            "schedule": {1: "grid", 2: "cta"}.get(sch.value, "?"), "ms_grid": mg.value,
                            "ms_cta": mc.value})
-        return {"groups": ng.value, "padded_values": pv.value, "group_info": groups}
+        mt, mgr = ctypes.c_double(0), ctypes.c_double(0)
+        _check(_lib().tmg_batch_tune_info(self._h, ctypes.byref(mt), ctypes.byref(mgr)), "tmg_batch_tune_info")
+        return {"groups": ng.value, "padded_values": pv.value, "group_info": groups,
+                "whole_batch_ms": {"tuned": mt.value, "all_grid": mgr.value}}
 
     def split(self, x):
         """Per-instance views (N_i, p_i + 1) of a packed host array."""
