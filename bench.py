@@ -47,6 +47,7 @@ WORKLOAD = "long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed
 # launch on the default workload, from one ncu capture (profiles/
 # k_updown0_long_horizon_p1_mixed.md); valid only for the kernel source it was
 # taken with (first 16 hex digits of the SHA-256 of tmg_kernels.cuh), else null.
+BATCH_STRIDE = 1          # every s-th heat mode (profiling of smaller cases only)
 UPDOWN0_TRAFFIC = {"bytes_per_launch": 1.0183e9, "kernels_sha256": "3288286ac656a1b0"}
 
 
@@ -375,12 +376,14 @@ def _time_batch(batch, f, u0, u, steps, stream, torch):
     return start.elapsed_time(end) / steps
 
 
-def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1):
+def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1,
+                        only=("heat", "uneven", "gradients"), precisions=("mixed", "fp64"), eager=False):
     """The batched workloads: decoupled 2-D heat modes, an uneven batch, and
     gradients through the adjoint.  One step = one batched solve (plus the
     adjoint for the gradient workload); inputs resident in HBM.  With several
     ranks each solves its shard of the instances (balanced by N (p_t+1)); the
-    value is all instances' DoFs over the slowest rank's time."""
+    value is all instances' DoFs over the slowest rank's time.  `only` and
+    `precisions` select workloads and forms (for profiling one of them)."""
     import numpy as np
     from paper_1409_5254_gb300 import inputs, replicas, tmg
 
@@ -388,8 +391,24 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
         return replicas.partition_instances(weights, world)[rank]
 
     out = {}
+    if "heat" in only:
+        out.update(_heat_modes(dev, stream, steps, torch, shard, precisions, eager))
+    if "uneven" in only:
+        out.update(_uneven(dev, stream, steps, torch, shard, precisions, eager))
+    if "gradients" in only:
+        out.update(_gradients(dev, stream, steps, torch, shard, eager))
+    if world > 1:
+        out["sharding"] = f"instances split over {world} ranks (no data exchange), weak in per-rank time"
+    return out
+
+
+def _heat_modes(dev, stream, steps, torch, shard, precisions, eager):
+    import numpy as np
+    from paper_1409_5254_gb300 import inputs, replicas, tmg
+    out = {}
     # 65,536 heat modes, N = 4096, p_t = 1, T = 1
     lam_all, amps_all, freqs_all = inputs.heat_modes_batch(2, 256, 4096, 1)
+    lam_all, amps_all, freqs_all = lam_all[::BATCH_STRIDE], amps_all[::BATCH_STRIDE], freqs_all[::BATCH_STRIDE]
     n_all, N, p = lam_all.shape[0], 4096, 1
     idx = shard(np.full(n_all, N * (p + 1)))
     lam, amps, freqs = lam_all[idx], amps_all[idx], freqs_all[idx]
@@ -398,9 +417,9 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
     u0 = torch.zeros(n, dtype=torch.float64, device=dev)
     u = torch.empty_like(f)
     res = {}
-    for prec in ("mixed", "fp64"):
+    for prec in precisions:
         with tmg.Batch([p] * n, 1.0 / N, lam, N, precision=prec, tol=TOL, max_cycles=200, stream=stream,
-                       nu1=NU[0], nu2=NU[1]) as B:
+                       nu1=NU[0], nu2=NU[1], use_graph=not eager) as B:
             B.solve(f, u0, u)
             ms = _time_batch(B, f, u0, u, max(1, steps // 10) if prec == "mixed" else 1, stream, torch)
             cyc, rel, mx = B.stats()
@@ -409,11 +428,16 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
         worst = replicas.max_over_ranks(float(rel.max()), dev)
         res[prec] = {"value": n_all * N * (p + 1) / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
                      "max_rel_res": worst}
-    out["heat_modes_65536x4096_p1"] = {"unit": "DoF/s", "instances": n_all, "N": N, "p_t": p,
+    out["heat_modes_65536x4096_p1" if BATCH_STRIDE == 1 else f"heat_modes_{n_all}x4096_p1"] = {"unit": "DoF/s", "instances": n_all, "N": N, "p_t": p,
                                        "lambda_range": [float(lam_all.min()), float(lam_all.max())], **res}
     del f, u, u0
     torch.cuda.empty_cache()
+    return out
 
+
+def _uneven(dev, stream, steps, torch, shard, precisions, eager):
+    from paper_1409_5254_gb300 import inputs, replicas, tmg
+    out = {}
     # uneven batch: 10,000 instances, N log-uniform in [2^6, 2^16], p_t in {0..3}, lambda tau in [1e-3, 1e3]
     Nv_all, pv_all, z_all = inputs.uneven_batch(3, 10000)
     A_all, K_all = inputs.sinusoid_batch_params(3, len(Nv_all))
@@ -429,11 +453,11 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
     u0 = torch.ones(len(Nv), dtype=torch.float64, device=dev)
     u = torch.empty_like(f)
     res = {}
-    for prec in ("mixed", "fp64"):
+    for prec in precisions:
         torch.cuda.synchronize()
         t_setup = time.perf_counter()
         with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream,
-                       nu1=NU[0], nu2=NU[1]) as B:
+                       nu1=NU[0], nu2=NU[1], use_graph=not eager) as B:
             setup_ms = (time.perf_counter() - t_setup) * 1e3
             B.solve(f, u0, u)
             ms = _time_batch(B, f, u0, u, max(1, steps // 10), stream, torch)
@@ -452,7 +476,13 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
                            "padded_dofs": info["padded_values"], **res}
     del f, u, u0
     torch.cuda.empty_cache()
+    return out
 
+
+def _gradients(dev, stream, steps, torch, shard, eager):
+    import numpy as np
+    from paper_1409_5254_gb300 import inputs, replicas, tmg
+    out = {}
     # gradients: 4096 instances, N = 16384, p_t = 2, lambda log-uniform in [1, 1e4], T = 1
     n_all, N, p = 4096, 16384, 2
     lam_all, u0_all, target_all = inputs.adjoint_problem(4, n_all, N, p)
@@ -464,7 +494,7 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
     y = torch.from_numpy(target_all[idx]).to(dev)
     u = torch.empty_like(f)
     with tmg.Batch([p] * n, 1.0 / N, lam_all[idx], N, precision="mixed", tol=TOL, max_cycles=300, stream=stream,
-                   nu1=NU[0], nu2=NU[1]) as B:
+                   nu1=NU[0], nu2=NU[1], use_graph=not eager) as B:
         def step():
             B.solve(f, u0, u)
             e = u.view(n, N, p + 1).sum(dim=2)
@@ -489,8 +519,6 @@ def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1
                                     "precision": "mixed", "cycle": f"V{NU}"}
     del f, u, u0, y
     torch.cuda.empty_cache()
-    if world > 1:
-        out["sharding"] = f"instances split over {world} ranks (no data exchange), weak in per-rank time"
     return out
 
 
@@ -566,15 +594,39 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64-form and other-degree side runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per launch of the dominant kernel")
-    ap.add_argument("--eager", action="store_true", help="host-driven cycle loop instead of the CUDA graph (profiling)")
+    ap.add_argument("--eager", action="store_true", help="host-driven cycle loop instead of the CUDA graph (profiling: "
+                    "ncu does not profile the kernels of a graph with conditional nodes one by one)")
     ap.add_argument("--n-log2", type=int, default=24, help="intervals = 2^n (smaller cases for ncu captures)")
+    ap.add_argument("--workload", default="all", choices=["all", "heat", "uneven", "gradients"],
+                    help="all: the benchmark line; otherwise only that batched workload (profiling)")
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
+                    help="forms of the batched workloads run with --workload")
+    ap.add_argument("--batch-stride", type=int, default=1,
+                    help="with --workload heat: every s-th mode only (smaller cases for ncu captures)")
     args = ap.parse_args()
+    global BATCH_STRIDE
+    BATCH_STRIDE = max(1, args.batch_stride) if args.workload == "heat" else 1
     global N_FULL
     N_FULL = 1 << args.n_log2
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "all":
+        run_one_batched(args)
     else:
         run_ours(args)
+
+
+def run_one_batched(args):
+    """One batched workload alone, one GPU (for profiling its kernels)."""
+    import torch
+    from paper_1409_5254_gb300 import build_ext
+    build_ext.build()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream()
+    prec = ("mixed", "fp64") if args.precision == "both" else (args.precision,)
+    out = run_batched_configs(dev, stream, args.steps, torch, only=(args.workload,), precisions=prec,
+                              eager=args.eager)
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
