@@ -438,6 +438,81 @@ __global__ void __launch_bounds__(kBNT) kb_up(const T* __restrict__ f, const T* 
     }
 }
 
+// Levels l and l+1 of the way down in one kernel, over the listed
+// instances (as k_down2): each lane holds four level-l intervals (a quad,
+// which never straddles an instance), pre-smooths, restricts onto two level
+// l+1 intervals, pre-smooths those and restricts onto one level-(l+2)
+// interval; f_{l+1} is never stored.  log2N: intervals per instance at level l.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_down2(const T* __restrict__ f, T* __restrict__ fcc, int log2N,
+                                                 const LevelK<T, D>* __restrict__ lk, int nlev, int level,
+                                                 Xfer<T, D> X, int nu1, int H, const BatchState* __restrict__ st,
+                                                 BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 2, per);
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 2);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
+        const LevelK<T, D> K0 = lk[inst * nlev + level];
+        const LevelK<T, D> K1 = lk[inst * nlev + level + 1];
+        T fv[4][D], h[4][D], u[4][D], w[4][D], r[4][D];
+        load_m<T, D, 4>(f, q, act, fv);
+        presmooth_zero_m<DIR, T, D, 4>(K0, fv, h, u, w, nu1, first);
+        residual_tracked_m<DIR, T, D, 4>(fv, u, w, r, first);
+        T f1[2][D], h1[2][D], u1[2][D], w1[2][D], r1[2][D], out[D];
+        restrict2<T, D>(X, r[0], r[1], f1[0]);
+        restrict2<T, D>(X, r[2], r[3], f1[1]);
+        presmooth_zero<DIR, T, D>(K1, f1, h1, u1, w1, nu1, first);
+        residual_tracked<DIR, T, D>(f1, u1, w1, r1, first);
+        restrict_pair<T, D>(X, r1, out);
+        if (act && lane >= H) VecIO<T, D>::store(fcc + q * D, out);
+    }
+}
+
+// Levels l+1 and l of the way up in one kernel (as k_up2): recompute level
+// l's way down and level l+1's right-hand side and pre-smoothing from f_l,
+// add the prolongated level-(l+2) correction ucc, post-smooth on level l+1,
+// prolongate onto level l, post-smooth there and write u_l.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_up2(const T* __restrict__ f, const T* __restrict__ ucc,
+                                               T* __restrict__ u, int log2N, const LevelK<T, D>* __restrict__ lk,
+                                               int nlev, int level, Xfer<T, D> X, int nu1, int nu2, int H,
+                                               const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 2, per);
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 2);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
+        const LevelK<T, D> K0 = lk[inst * nlev + level];
+        const LevelK<T, D> K1 = lk[inst * nlev + level + 1];
+        T fv[4][D], h[4][D], v[4][D], w[4][D], r[4][D], cc[D];
+        load_m<T, D, 4>(f, q, act, fv);
+        load_one<T, D>(ucc, q, act, cc);
+        presmooth_zero_m<DIR, T, D, 4>(K0, fv, h, v, w, nu1, first);
+        residual_tracked_m<DIR, T, D, 4>(fv, v, w, r, first);
+        T f1[2][D], h1[2][D], v1[2][D], w1[2][D];
+        restrict2<T, D>(X, r[0], r[1], f1[0]);
+        restrict2<T, D>(X, r[2], r[3], f1[1]);
+        presmooth_zero<DIR, T, D>(K1, f1, h1, v1, w1, nu1, first);
+        prolong_add<T, D>(X, cc, v1);
+        postsmooth<DIR, T, D>(K1, h1, v1, nu2, first);
+        prolong_add2<T, D>(X, v1[0], v[0], v[1]);
+        prolong_add2<T, D>(X, v1[1], v[2], v[3]);
+        postsmooth_m<DIR, T, D, 4>(K0, h, v, nu2, first);
+        if (act && lane >= H) store_m<T, D, 4>(u, q, v);
+    }
+}
+
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kBNT) kb_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
                                                int log2N, const LevelK<T, D>* __restrict__ lk, int nlev, Xfer<T, D> X,

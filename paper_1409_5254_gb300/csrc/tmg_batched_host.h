@@ -131,23 +131,53 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
                                                                (int)(G->Ng * D), G->st, G->bi);
         return cudaGetLastError();
     }
-    for (int l = 1; l < L - 1; ++l) {
-        const int H = halo(sw_down(nu1));
-        const int64_t nch = n * (G->Ng >> l) / 2;
-        kb_down<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
-            static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 1]), nch, G->log2Ng - l, lk, L, l, X, nu1, H,
-            G->st, G->bi);
+    // streaming levels 1 .. L-2, two per kernel where two remain (default for
+    // FP32 cycles, as in the single-problem solver)
+    const bool fuse = B->o.fuse_levels > 0 || (B->o.fuse_levels < 0 && std::is_same<T, float>::value);
+    int grp[kMaxLevels], ng = 0;
+    for (int l = 1; l < L - 1;) {
+        const bool two = fuse && l + 1 < L - 1;
+        grp[ng++] = two ? -l : l;      // negative: levels l and l+1 in one kernel
+        l += two ? 2 : 1;
+    }
+    for (int g = 0; g < ng; ++g) {
+        if (grp[g] < 0) {
+            const int l = -grp[g];
+            const int H = halo(halo(sw_down(nu1)) + sw_down(nu1));
+            const int64_t nq = n * (G->Ng >> l) / 4;
+            kb_down2<DIR, T, D><<<grid_tiles(B, nq, H), kBNT, 0, G->s>>>(
+                static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 2]), G->log2Ng - l, lk, L, l, X, nu1, H,
+                G->st, G->bi);
+        } else {
+            const int l = grp[g];
+            const int H = halo(sw_down(nu1));
+            const int64_t nch = n * (G->Ng >> l) / 2;
+            kb_down<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+                static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 1]), nch, G->log2Ng - l, lk, L, l, X,
+                nu1, H, G->st, G->bi);
+        }
     }
     kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(static_cast<const T*>(G->fl[L - 1]),
                                                                    static_cast<T*>(G->ul[L - 1]), n,
                                                                    (int)(G->Ng >> (L - 1)), lk, L, L - 1, G->st,
                                                                    G->bi);
-    for (int l = L - 2; l >= 1; --l) {
-        const int H = halo(sw_up(nu1, nu2));
-        const int64_t nch = n * (G->Ng >> l) / 2;
-        kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
-            static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 1]), static_cast<T*>(G->ul[l]), nch,
-            G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+    for (int g = ng - 1; g >= 0; --g) {
+        if (grp[g] < 0) {
+            const int l = -grp[g];
+            const int g1 = halo(sw_down(nu1)) + sw_up(nu1, nu2);
+            const int H = (2 * g1 + nu2 + 3) / 4;
+            const int64_t nq = n * (G->Ng >> l) / 4;
+            kb_up2<DIR, T, D><<<grid_tiles(B, nq, H), kBNT, 0, G->s>>>(
+                static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 2]), static_cast<T*>(G->ul[l]),
+                G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+        } else {
+            const int l = grp[g];
+            const int H = halo(sw_up(nu1, nu2));
+            const int64_t nch = n * (G->Ng >> l) / 2;
+            kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+                static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 1]), static_cast<T*>(G->ul[l]), nch,
+                G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+        }
     }
     if constexpr (std::is_same<T, float>::value) {
         if (rl != nullptr) {

@@ -362,7 +362,7 @@ __device__ __forceinline__ void postsmooth(const LevelK<T, D>& K, const T (&h)[2
 
 template <int DIR, typename T, int D, int M>
 __device__ __forceinline__ void presmooth_zero_m(const LevelK<T, D>& K, const T (&f)[M][D], T (&h)[M][D],
-                                                 T (&u)[M][D], T (&w)[M][D], int nu1) {
+                                                 T (&u)[M][D], T (&w)[M][D], int nu1, bool first = false) {
     const T om = K.omega, om1 = T(1) - K.omega;
     const T om_first = nu1 > 0 ? om : T(0);
 #pragma unroll
@@ -378,7 +378,8 @@ __device__ __forceinline__ void presmooth_zero_m(const LevelK<T, D>& K, const T 
         T e[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) e[i] = bval<DIR, T, D>(u[i]);
-        const T ep0 = shfl_prev(e[M - 1]);
+        const T ep_s = shfl_prev(e[M - 1]);
+        const T ep0 = first ? T(0) : ep_s;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const T ep = i == 0 ? ep0 : e[i - 1];
@@ -393,11 +394,12 @@ __device__ __forceinline__ void presmooth_zero_m(const LevelK<T, D>& K, const T 
 
 template <int DIR, typename T, int D, int M>
 __device__ __forceinline__ void residual_tracked_m(const T (&f)[M][D], const T (&u)[M][D], const T (&w)[M][D],
-                                                   T (&r)[M][D]) {
+                                                   T (&r)[M][D], bool first = false) {
     T e[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) e[i] = bval<DIR, T, D>(u[i]);
-    const T ep0 = shfl_prev(e[M - 1]);
+    const T ep_s = shfl_prev(e[M - 1]);
+    const T ep0 = first ? T(0) : ep_s;
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         const T ep = i == 0 ? ep0 : e[i - 1];
@@ -407,13 +409,15 @@ __device__ __forceinline__ void residual_tracked_m(const T (&f)[M][D], const T (
 }
 
 template <int DIR, typename T, int D, int M>
-__device__ __forceinline__ void postsmooth_m(const LevelK<T, D>& K, const T (&h)[M][D], T (&u)[M][D], int nu) {
+__device__ __forceinline__ void postsmooth_m(const LevelK<T, D>& K, const T (&h)[M][D], T (&u)[M][D], int nu,
+                                             bool first = false) {
     const T om = K.omega, om1 = T(1) - K.omega;
     for (int s = 0; s < nu; ++s) {
         T e[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) e[i] = bval<DIR, T, D>(u[i]);
-        const T ep0 = shfl_prev(e[M - 1]);
+        const T ep_s = shfl_prev(e[M - 1]);
+        const T ep0 = first ? T(0) : ep_s;
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const T ep = i == 0 ? ep0 : e[i - 1];

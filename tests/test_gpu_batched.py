@@ -69,6 +69,34 @@ def test_uniform_batch(dev, prec):
     print(f"uniform {prec}: max cycles {mx}, worst err {err:.2e}")
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 2), (3, 1), (0, 2)])
+def test_two_level_kernels_match_one_level(dev, prec, nu):
+    """The grid schedule's streaming levels two per kernel (kb_down2/kb_up2,
+    each lane four intervals, the halo restarting at every instance) against
+    one level per kernel: the same cycles, solutions within rounding of each
+    other, and both at the oracle's residual.  Lengths 256 .. 16384 give 1 to
+    7 streaming levels: pairs and a single level, instance boundaries inside
+    the lanes' windows."""
+    from paper_1409_5254_gb300 import tmg
+    rng = np.random.default_rng(11)
+    N = [int(x) for x in 2 ** rng.integers(8, 15, 24)]
+    p = [int(x) for x in rng.integers(0, 4, 24)]
+    z = 10.0 ** rng.uniform(-3, 1, 24)
+    Fs, u0, tau, lam = make_batch(11, p, N, z)
+    f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+    out = {}
+    for fuse in (True, False):
+        with tmg.Batch(p, tau, lam, N, precision=prec, tol=1e-10, max_cycles=300, nu1=nu[0], nu2=nu[1],
+                       fuse_levels=fuse, schedule=1) as B:
+            u = B.solve(f, torch.from_numpy(u0).to(dev)).cpu().numpy()
+            cyc, rel, mx = B.stats()
+            out[fuse] = (u, cyc, B)
+    assert np.abs(out[True][1] - out[False][1]).max() <= 1
+    err = check_solution(Fs, u0, tau, lam, p, N, out[True][0], out[True][2], 1e-10)
+    print(f"two-level {prec} nu={nu}: max cycles {out[True][1].max()}, worst err {err:.2e}")
+
+
 def test_uneven_batch_matches_oracle(dev):
     """Different degrees, lengths (not powers of two) and steps in one batch."""
     from paper_1409_5254_gb300 import tmg
