@@ -12,39 +12,54 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// One thread per interval (no integer division in the index arithmetic).
 __global__ void __launch_bounds__(kThreads) k_reverse(const double* __restrict__ src, double* __restrict__ dst,
                                                       int64_t N, int d) {
-    const int64_t total = N * d;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += stride) {
-        const int64_t n = i / d, k = i - n * d;
-        dst[(N - 1 - n) * d + k] = src[i];
+    for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += stride) {
+        const double* s = src + n * d;
+        double* o = dst + (N - 1 - n) * d;
+        for (int k = 0; k < d; ++k) o[k] = s[k];
     }
 }
 
 // Deterministic grid reduction of sum_n sum_k mu[n][k] u[n][k] / (2k+1); the
-// last block adds the partials in order and writes both gradients.
+// last block adds the partials in order and writes both gradients.  Each
+// thread takes whole intervals and keeps one sum per coefficient k; the
+// weights 1/(2k+1) are applied once per block.
 __global__ void __launch_bounds__(kThreads) k_adjoint_grads(const double* __restrict__ mu, const double* __restrict__ u,
                                                             int64_t N, int d, double tau,
                                                             double* __restrict__ partials, unsigned* ticket,
                                                             double* __restrict__ dJdu0,
                                                             double* __restrict__ dJdlambda) {
-    double s = 0.0;
-    const int64_t total = N * d;
+    double sk[tmg::kMaxD];
+#pragma unroll
+    for (int k = 0; k < tmg::kMaxD; ++k) sk[k] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < total; i += stride) {
-        const int k = (int)(i % d);
-        s = fma(mu[i], u[i] / (2.0 * k + 1.0), s);
+    for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += stride) {
+        const double* a = mu + n * d;
+        const double* b = u + n * d;
+#pragma unroll
+        for (int k = 0; k < tmg::kMaxD; ++k)
+            if (k < d) sk[k] = fma(a[k], b[k], sk[k]);
     }
-    __shared__ double red[kThreads / 32];
+    __shared__ double red[tmg::kMaxD][kThreads / 32];
     __shared__ int last;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int k = 0; k < tmg::kMaxD; ++k) {
+        double s = sk[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = s;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+        for (int k = 0; k < d; ++k) {
+            double tk = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) tk += red[k][w];
+            t += tk / (2.0 * k + 1.0);
+        }
         partials[blockIdx.x] = t;
         __threadfence();
         last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
@@ -64,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_grads(const double* __rest
 }  // namespace
 
 cudaError_t tmg_launch_reverse(const double* src, double* dst, int64_t N, int d, cudaStream_t s) {
-    int64_t blocks = (N * d + kThreads - 1) / kThreads;
+    int64_t blocks = (N + kThreads - 1) / kThreads;
     if (blocks > 4096) blocks = 4096;
     k_reverse<<<(int)blocks, kThreads, 0, s>>>(src, dst, N, d);
     return cudaGetLastError();
@@ -73,7 +88,7 @@ cudaError_t tmg_launch_reverse(const double* src, double* dst, int64_t N, int d,
 cudaError_t tmg_launch_adjoint_grads(const double* mu, const double* u, int64_t N, int d, double tau,
                                      double* partials, int max_blocks, unsigned* ticket, double* dJdu0,
                                      double* dJdlambda, cudaStream_t s) {
-    int64_t blocks = (N * d + kThreads - 1) / kThreads;
+    int64_t blocks = (N + kThreads - 1) / kThreads;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
     k_adjoint_grads<<<(int)blocks, kThreads, 0, s>>>(mu, u, N, d, tau, partials, ticket, dJdu0, dJdlambda);

@@ -59,55 +59,81 @@ __global__ void kb_init(BatchInst bi, int64_t n) {
 
 // dst[j][n][k] = src[off_j + m(n) d + k] for n < N_j (m = n, or N_j-1-n when
 // reversed), 0 on the padded intervals; also u0 of the group's instances.
+// One thread per interval of the group layout: Ng is a power of two, so the
+// instance and interval come from a shift and a mask (no integer division).
 __global__ void kb_gather(const double* __restrict__ src, double* __restrict__ dst, const int64_t* __restrict__ ids,
-                          const int64_t* __restrict__ Ni, const int64_t* __restrict__ off, int64_t n, int64_t Ng,
+                          const int64_t* __restrict__ Ni, const int64_t* __restrict__ off, int64_t n, int log2Ng,
                           int d, int reverse, const double* __restrict__ u0src, double* __restrict__ u0dst) {
-    const int64_t total = n * Ng * d;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / (Ng * d), rem = i - j * Ng * d;
-        const int64_t m = rem / d, k = rem - m * d;
+    const int64_t rows = n << log2Ng;
+    const int64_t mask = ((int64_t)1 << log2Ng) - 1;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = r >> log2Ng, m = r & mask;
         const int64_t nj = Ni[j];
-        double v = 0.0;
-        if (m < nj) v = src[off[j] + (reverse ? nj - 1 - m : m) * d + k];
-        dst[i] = v;
-        if (u0dst && rem == 0) u0dst[j] = u0src ? u0src[ids[j]] : 0.0;
+        double* o = dst + r * d;
+        if (m < nj) {
+            const double* s = src + off[j] + (reverse ? nj - 1 - m : m) * d;
+            for (int k = 0; k < d; ++k) o[k] = s[k];
+        } else {
+            for (int k = 0; k < d; ++k) o[k] = 0.0;
+        }
+        if (u0dst && m == 0) u0dst[j] = u0src ? u0src[ids[j]] : 0.0;
     }
 }
 
+// The inverse of kb_gather for the first N_j intervals of every instance.
 __global__ void kb_scatter(const double* __restrict__ src, double* __restrict__ dst, const int64_t* __restrict__ Ni,
-                           const int64_t* __restrict__ off, int64_t n, int64_t Ng, int d, int reverse) {
-    const int64_t total = n * Ng * d;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / (Ng * d), rem = i - j * Ng * d;
-        const int64_t m = rem / d, k = rem - m * d;
+                           const int64_t* __restrict__ off, int64_t n, int log2Ng, int d, int reverse) {
+    const int64_t rows = n << log2Ng;
+    const int64_t mask = ((int64_t)1 << log2Ng) - 1;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = r >> log2Ng, m = r & mask;
         const int64_t nj = Ni[j];
-        if (m < nj) dst[off[j] + (reverse ? nj - 1 - m : m) * d + k] = src[i];
+        if (m < nj) {
+            const double* s = src + r * d;
+            double* o = dst + off[j] + (reverse ? nj - 1 - m : m) * d;
+            for (int k = 0; k < d; ++k) o[k] = s[k];
+        }
     }
 }
 
 // Per-instance gradients (one block per instance, fixed summation order):
-// dJ/du0 = a^T mu_0, dJ/dlambda = -tau sum_n mu_n^T Mhat u_n.
+// dJ/du0 = a^T mu_0, dJ/dlambda = -tau sum_n mu_n^T Mhat u_n.  Each thread
+// takes whole intervals and keeps one sum per coefficient k; the weights
+// Mhat_kk = 1/(2k+1) are applied once, to the block totals.
 __global__ void kb_grads(const double* __restrict__ mu, const double* __restrict__ u, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ Nv, const int* __restrict__ pv, const double* __restrict__ tau,
                          int64_t n_inst, double* __restrict__ dJdu0, double* __restrict__ dJdlambda) {
-    __shared__ double red[kBNT / 32];
+    __shared__ double red[kMaxD][kBNT / 32];
     for (int64_t i = blockIdx.x; i < n_inst; i += gridDim.x) {
         const int d = pv[i] + 1;
-        const int64_t base = off[i], len = Nv[i] * d;
-        double s = 0.0;
-        for (int64_t t = threadIdx.x; t < len; t += kBNT) {
-            const int k = (int)(t % d);
-            s = fma(mu[base + t], u[base + t] / (2.0 * k + 1.0), s);
+        const int64_t base = off[i], N = Nv[i];
+        double sk[kMaxD];
+#pragma unroll
+        for (int k = 0; k < kMaxD; ++k) sk[k] = 0.0;
+        for (int64_t m = threadIdx.x; m < N; m += kBNT) {
+            const double* a = mu + base + m * d;
+            const double* b = u + base + m * d;
+#pragma unroll
+            for (int k = 0; k < kMaxD; ++k)
+                if (k < d) sk[k] = fma(a[k], b[k], sk[k]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        for (int k = 0; k < kMaxD; ++k) {
+            double s = sk[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
+            if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = s;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int w = 0; w < kBNT / 32; ++w) t += red[w];
+            for (int k = 0; k < d; ++k) {
+                double tk = 0.0;
+                for (int w = 0; w < kBNT / 32; ++w) tk += red[k][w];
+                t += tk / (2.0 * k + 1.0);
+            }
             dJdlambda[i] = -tau[i] * t;
             double g0 = 0.0;
             for (int k = 0; k < d; ++k) g0 += (k & 1) ? -mu[base + k] : mu[base + k];
@@ -720,12 +746,12 @@ tmg_status tmg_solve_batched(tmg_batch* B, const double* f, const double* u0, do
             s = ensure_gather(G);
             if (s != TMG_OK) return drain(B, s);
             const int64_t nv = G->n * G->Ng * G->d;
-            kb_gather<<<grid_flat(B, nv), kBNT, 0, G->s>>>(f, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d,
+            kb_gather<<<grid_flat(B, nv / G->d), kBNT, 0, G->s>>>(f, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->log2Ng, G->d,
                                                            0, u0, G->u0g);
             TB_CUDA(cudaGetLastError());
             s = start_group(B, G, G->Fg, G->ug, G->u0g, 0);
             if (s != TMG_OK) return drain(B, s);
-            kb_scatter<<<grid_flat(B, nv), kBNT, 0, G->s>>>(G->ug, u, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 0);
+            kb_scatter<<<grid_flat(B, nv / G->d), kBNT, 0, G->s>>>(G->ug, u, G->d_Ni, G->d_off, G->n, G->log2Ng, G->d, 0);
             TB_CUDA(cudaGetLastError());
         }
         if (s != TMG_OK) return drain(B, s);
@@ -755,12 +781,12 @@ tmg_status tmg_adjoint_batched(tmg_batch* B, const double* g, const double* u, d
         if (s != TMG_OK) return drain(B, s);
         const int64_t nv = G->n * G->Ng * G->d;
         // L^T mu = g in reversed time (causal there, so padding at the end stays exact)
-        kb_gather<<<grid_flat(B, nv), kBNT, 0, G->s>>>(g, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1,
+        kb_gather<<<grid_flat(B, nv / G->d), kBNT, 0, G->s>>>(g, G->Fg, G->d_ids, G->d_Ni, G->d_off, G->n, G->log2Ng, G->d, 1,
                                                        nullptr, G->u0g);
         TB_CUDA(cudaGetLastError());
         s = start_group(B, G, G->Fg, G->ug, G->u0g, 1);
         if (s != TMG_OK) return drain(B, s);
-        kb_scatter<<<grid_flat(B, nv), kBNT, 0, G->s>>>(G->ug, dJdf, G->d_Ni, G->d_off, G->n, G->Ng, G->d, 1);
+        kb_scatter<<<grid_flat(B, nv / G->d), kBNT, 0, G->s>>>(G->ug, dJdf, G->d_Ni, G->d_off, G->n, G->log2Ng, G->d, 1);
         TB_CUDA(cudaGetLastError());
         TB_CUDA(cudaEventRecord(G->done, G->s));
     }
