@@ -543,7 +543,7 @@ struct ff {
 // x = hi + lo: hi is x truncated to 24 significant bits, lo the remaining 29
 // bits truncated to 24.  Integer operations only.  |x| < 2^-126 gives 0;
 // |x| >= 2^128 (or Inf/NaN) gives +-Inf so that the norm flags it.
-__device__ __forceinline__ ff split_d(double x) {
+__device__ __forceinline__ ff split_d_general(double x) {
     const unsigned hw = (unsigned)__double2hiint(x);
     const unsigned lw = (unsigned)__double2loint(x);
     const unsigned sign = hw & 0x80000000u;
@@ -564,6 +564,26 @@ __device__ __forceinline__ ff split_d(double x) {
         const unsigned mant = ((r29 << (lz & 31)) >> 8) & 0x7FFFFFu;
         out.lo = (r29 != 0u && fe > 0) ? __uint_as_float(sign | ((unsigned)fe << 23) | mant) : 0.f;
     }
+    return out;
+}
+
+// The same split with lo rounded (instead of truncated) to 24 bits: for
+// 2^-74 <= |x| < 2^128 the remaining 29 mantissa bits are converted as an
+// integer and scaled by the exact power of two 2^(e - 1075), which the
+// conversion unit does in one instruction where the general form needs a
+// leading-zero count and a renormalisation.  Other x take split_d_general.
+// Either way hi + lo = x to within 2^-47 |x|.
+__device__ __forceinline__ ff split_d(double x) {
+    const unsigned hw = (unsigned)__double2hiint(x);
+    const unsigned lw = (unsigned)__double2loint(x);
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    if ((unsigned)(e - 949) > 201u) return split_d_general(x);
+    const unsigned sign = hw & 0x80000000u;
+    const unsigned m23 = __funnelshift_l(lw, hw, 3) & 0x7FFFFFu;      // mantissa bits 51..29
+    ff out;
+    out.hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | m23);
+    const float s = __uint_as_float((unsigned)(e - 948) << 23);         // 2^(e - 1075), a normal float
+    out.lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn(lw & 0x1FFFFFFFu) * s));
     return out;
 }
 
