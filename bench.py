@@ -38,9 +38,24 @@ LAM = 1.0
 U0 = 1.0
 P_MAIN = 1
 NU = (2, 2)               # pre-/post-smoothing sweeps of the timed cycles (the paper's plots use nu1 = nu2 in {1, 2, 5})
+N_MIN = 1 << 16           # coarsen while N_l > N_MIN: at N = 2^24 the coarsest level has 2^16 intervals,
+                          # solved exactly by the parallel affine scan (11 cycles, as with 64 intervals)
+
+
+def n_min_p(p: int) -> int:
+    """Coarsest level of the long-horizon lines: 2^16 intervals (scan) for
+    p_t <= 1; from p_t = 2 on the FP32 scan of so long a level costs more than
+    the levels it replaces, and the default 64 intervals (one warp) is faster."""
+    return N_MIN if p <= 1 else 64
+
+
+def n_min_for(n: int) -> int:
+    """The same hierarchy depth for a sample of n intervals (oracle runs)."""
+    return max(64, N_MIN * n // N_FULL)
 TOL = 1e-10
 METRIC = "time-DoFs/s solved to 1e-10 rel residual"
-WORKLOAD = "long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate refinement, V(2,2), omega*"
+WORKLOAD = ("long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate "
+            "refinement, V(2,2), omega*, coarsest level 2^16 intervals solved by the parallel affine scan")
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_updown0
@@ -48,7 +63,7 @@ WORKLOAD = "long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed
 # k_updown0_long_horizon_p1_mixed.md); valid only for the kernel source it was
 # taken with (first 16 hex digits of the SHA-256 of tmg_kernels.cuh), else null.
 BATCH_STRIDE = 1          # every s-th heat mode (profiling of smaller cases only)
-UPDOWN0_TRAFFIC = {"bytes_per_launch": 1.0183e9, "kernels_sha256": "3288286ac656a1b0"}
+UPDOWN0_TRAFFIC = {"bytes_per_launch": 1.0179e9, "kernels_sha256": "2bcd3e9776872448"}
 
 
 def measured_traffic():
@@ -194,7 +209,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
     plan = tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, use_graph=not args.eager,
-                    nu1=NU[0], nu2=NU[1])
+                    nu1=NU[0], nu2=NU[1], n_min=N_MIN)
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     for _ in range(args.warmup):
@@ -270,7 +285,7 @@ def run_ours(args):
                 "solve_ms_per_cycle": round(ms / max(st.cycles, 1), 5),
                 "kernel_ms": {"down0_confirm_once_per_solve": round(prof["down0"], 5),
                               "down_levels": round(prof["down_levels"], 5),
-                              "coarse_on_chip": round(prof["coarse_on_chip"], 5),
+                              "coarsest_solve": round(prof["coarse_on_chip"], 5),
                               "up_levels": round(prof["up_levels"], 5), "updown0": round(prof["up0"], 5),
                               "cycle_events": round(prof["cycle"], 5)}}
 
@@ -281,7 +296,7 @@ def run_ours(args):
     if rank == 0 and not args.quick:
         # plain FP64 form on the same problem
         with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="fp64", tol=TOL, stream=stream, nu1=NU[0], nu2=NU[1],
-                      use_graph=not args.eager) as p64:
+                      n_min=N_MIN, use_graph=not args.eager) as p64:
             p64.solve(F, U0, u)
             ms64 = time_solves(p64, F, u, max(2, args.steps // 4), stream, torch)
             s64 = p64.stats()
@@ -295,13 +310,14 @@ def run_ours(args):
             up = torch.empty_like(Fp)
             try:
                 with tmg.Plan(p, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, max_cycles=300,
-                              nu1=NU[0], nu2=NU[1],
+                              nu1=NU[0], nu2=NU[1], n_min=n_min_p(p),
                               use_graph=not args.eager) as pp:
                     pp.solve(Fp, U0, up)
                     msp = time_solves(pp, Fp, up, max(2, args.steps // 4), stream, torch)
                     sp = pp.stats()
                     per_p[str(p)] = {"value": N_FULL * (p + 1) / (msp * 1e-3), "ms_per_step": round(msp, 4),
-                                     "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": f"V{NU}"}
+                                     "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": f"V{NU}",
+                                     "coarsest_intervals": pp.info()["tail_intervals"]}
             except tmg.TmgError as e:
                 per_p[str(p)] = {"error": str(e)}
             del Fp, up
@@ -310,7 +326,7 @@ def run_ours(args):
         nus = {}
         for nu in ((1, 1), (1, 3), (2, 3), (3, 3)):
             with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, nu1=nu[0],
-                          nu2=nu[1], use_graph=not args.eager) as pn:
+                          nu2=nu[1], n_min=N_MIN, use_graph=not args.eager) as pn:
                 pn.solve(F, U0, u)
                 msn = time_solves(pn, F, u, max(2, args.steps // 4), stream, torch)
                 sn = pn.stats()
@@ -351,7 +367,8 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "N": N_FULL, "p_t": P_MAIN, "tau": TAU, "lambda": LAM, "u0": U0,
                            "tol": TOL, "cycles": st.cycles, "levels": info["levels"],
-                           "tail_level": info["tail_level"], "precision": "mixed",
+                           "tail_level": info["tail_level"], "coarsest_intervals": info["tail_intervals"],
+                           "precision": "mixed",
                            "l2": "inputs larger than L2 (268 MB load vector + 268 MB solution)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "rel_res_fp64": rel_fp64, "err_vs_fp64": err_vs_fp64, "time_steps_per_s": value / d,
@@ -535,7 +552,8 @@ def cpu_baseline(sample_N: int = 1 << 21):
     forcing = inputs.Forcing.draw(np.random.default_rng(1), T)
     F = _sample_load_vector(P_MAIN, sample_N, T, forcing)
     t0 = time.perf_counter()
-    _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1])
+    _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1],
+                              n_min=n_min_for(F.shape[0]))
     t_mg = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.fsub(P_MAIN, LAM * TAU, F, U0)
@@ -568,10 +586,12 @@ def run_reference(args):
     forcing = inputs.Forcing.draw(np.random.default_rng(1), T)
     F = _sample_load_vector(P_MAIN, n, T, forcing)
     for _ in range(args.warmup):
-        oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1])
+        oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1],
+                        n_min=n_min_for(F.shape[0]))
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1])
+        _, hist = oracle.mg_solve(P_MAIN, LAM * TAU, F, U0, tol=TOL, max_cycles=100, nu1=NU[0], nu2=NU[1],
+                              n_min=n_min_for(F.shape[0]))
     dt = (time.perf_counter() - t0) / args.steps
     value = n * d / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": args.gpus,

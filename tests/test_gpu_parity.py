@@ -257,14 +257,17 @@ def test_not_converged_status(dev):
         assert plan.stats().cycles == 2
 
 
-def test_full_size_long_horizon_sampled(dev):
+@pytest.mark.parametrize("n_min", [64, 1 << 16])
+def test_full_size_long_horizon_sampled(dev, n_min):
     """The benchmark workload (N = 2^24, tau = 1e-6, lambda = 1, p = 1, V(2,2)),
-    in the launch configuration the benchmark times: FP64 residual of the whole GPU
+    in the launch configuration the benchmark times (coarsest level 2^16
+    intervals, solved by the grid-wide affine scan) and with the library's
+    default hierarchy (coarsest 64 intervals): FP64 residual of the whole GPU
     result, and sampled intervals against exact forward substitution."""
     N, p = 1 << 24, 1
     prob = inputs.scalar_problem(1, N, p, lam=1.0, tau=1e-6, u0=1.0)
     Fd = torch.from_numpy(prob["F"]).to(dev)
-    with tmg().Plan(p, 1e-6, 1.0, N, precision="mixed", nu1=2, nu2=2) as plan:
+    with tmg().Plan(p, 1e-6, 1.0, N, precision="mixed", nu1=2, nu2=2, n_min=n_min) as plan:
         u = plan.solve(Fd, prob["u0"])
         r = plan.residual(Fd, prob["u0"], u)
         st = plan.stats()
