@@ -109,8 +109,11 @@ void tmg_opts_default(tmg_opts *opts);
  * and owns every workspace.  The levels below the first one that fits on one
  * SM's shared memory run in a single-CTA coarse solver; when even the
  * coarsest level is too large for that, it is solved exactly by a grid-wide
- * scan (see tmg_solve_direct).  Returns TMG_EINVAL for bad arguments,
- * TMG_EUNSUPPORTED for a W-cycle whose coarse levels are not all on chip,
+ * scan (see tmg_solve_direct).  W-cycles (gamma = 2) visit every level below
+ * level 0 twice per visit of its parent, the second visit starting from the
+ * first one's result (one launch per level and visit on the streaming levels,
+ * so their cost in launches doubles per level: keep the streaming part short
+ * with the default tail_cap).  Returns TMG_EINVAL for bad arguments,
  * TMG_ENOMEM / TMG_ECUDA on allocation failure.
  */
 tmg_status tmg_setup(tmg_plan **plan, int p_t, double tau, double lambda, int64_t N, int levels,

@@ -268,22 +268,21 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         P->scan_coarsest = true;
         P->tail_smem = 0;
     }
-    if (o.gamma == 2 && (P->lt > 1 || P->scan_coarsest)) {
-        tmg_destroy(P);
-        return TMG_EUNSUPPORTED;
-    }
 
     // workspace: level vectors in the cycle precision, level-0 residual,
     // tail constants, block partials, device state
     const size_t el = P->ops->elem;
     const size_t A = 256;
     size_t off = 0;
-    size_t off_f[tmg::kMaxLevels], off_u[tmg::kMaxLevels];
+    size_t off_f[tmg::kMaxLevels], off_u[tmg::kMaxLevels], off_u2[tmg::kMaxLevels];
+    const bool wcycle = o.gamma == 2 && P->lt >= 1;   // levels 1..lt are visited twice per visit of their parent
     for (int l = 0; l <= P->lt; ++l) {
         off_f[l] = off;
         off = align_up(off + el * P->lev[l].N * P->d, A);
         off_u[l] = off;
         off = align_up(off + el * P->lev[l].N * P->d, A);
+        off_u2[l] = off;
+        if (wcycle && l >= 1) off = align_up(off + el * P->lev[l].N * P->d, A);
     }
     // level-0 residual; the mixed form that keeps r as a float pair updated
     // between cycles (k_updown0) needs two buffers of high and of low parts
@@ -315,6 +314,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     for (int l = 0; l <= P->lt; ++l) {
         P->fl[l] = base + off_f[l];
         P->ul[l] = base + off_u[l];
+        P->ul2[l] = wcycle && l >= 1 ? base + off_u2[l] : nullptr;
     }
     P->rT = base + off_r;
     P->rl = updated_res ? base + off_rl : nullptr;
@@ -519,7 +519,8 @@ tmg_status tmg_inspect(const tmg_plan* P, int which, int level, void* host_dst, 
         }
     } else {
         if (level < 0 || level > P->lt || (level == 0 && which == 0)) return TMG_EINVAL;
-        src = which == 0 ? P->fl[level] : P->ul[level];
+        // the final correction of a level: in a W-cycle that of its second visit
+        src = which == 0 ? P->fl[level] : (P->ul2[level] != nullptr ? P->ul2[level] : P->ul[level]);
         n = P->lev[level].N;
     }
     const size_t need = (size_t)n * P->d * elem;

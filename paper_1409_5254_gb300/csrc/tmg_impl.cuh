@@ -180,6 +180,56 @@ struct Impl {
         launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, args...);
     }
 
+    // One visit of level l >= 1 in a W-cycle (gamma = 2): nz = the second
+    // visit of the level under the same parent visit, which starts from the
+    // first visit's result ul[l] and writes ul2[l]; a first visit starts from
+    // zero and writes ul[l].  Levels below visit level l+1 twice; the final
+    // correction of level l+1 is then in ul2[l+1].  The coarse part (level
+    // lt and below) is one launch per visit: the on-chip solver (with the
+    // start iterate on a second visit, and the W recursion inside) or the
+    // exact scan.
+    static void w_visit(tmg_plan* P, int l, bool nz, const Xfer<T, D>& X, const LevelK<T, D>* lk_tail, int nl) {
+        const int nu1 = P->o.nu1, nu2 = P->o.nu2;
+        T* ua = static_cast<T*>(P->ul[l]);
+        T* ub = static_cast<T*>(P->ul2[l]);
+        if (l == P->lt) {
+            if (P->scan_coarsest)
+                enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[l]), nz ? ub : ua, l, T(0), nullptr, P->st);
+            else
+                launch_tail(P, static_cast<const T*>(P->fl[l]), nz ? ub : ua, lk_tail, X, nl, P->lev[l].N, nu1, nu2,
+                            P->o.gamma, (const DevState*)P->st, nz ? (const T*)ua : (const T*)nullptr);
+            return;
+        }
+        const int64_t nch = P->lev[l].N / 2;
+        const LevelK<T, D> K = level_consts<T, D>(L(P)[l]);
+        const CoarseTail<T, D> ct_none{nullptr, nullptr, nullptr, 0, nullptr};
+        if (nz) {
+            const int H = halo_lanes(nu1 + 1);
+            static const int occ = resident_per_sm(k_down_nz<DIR, T, D>, 0);
+            launch(P, k_down_nz<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                   (const T*)ua, static_cast<T*>(P->fl[l + 1]), nch, K, X, nu1, H, (const DevState*)P->st);
+        } else {
+            const int H = halo_lanes(sweeps_down(nu1));
+            static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
+            launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                   static_cast<T*>(P->fl[l + 1]), nch, K, X, nu1, H, (const DevState*)P->st, ct_none);
+        }
+        w_visit(P, l + 1, false, X, lk_tail, nl);
+        w_visit(P, l + 1, true, X, lk_tail, nl);
+        const T* uc = static_cast<const T*>(P->ul2[l + 1]);
+        if (nz) {
+            const int H = halo_lanes(nu1 + nu2);
+            static const int occ = resident_per_sm(k_up_nz<DIR, T, D>, 0);
+            launch(P, k_up_nz<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                   (const T*)ua, uc, ub, nch, K, X, nu1, nu2, H, (const DevState*)P->st);
+        } else {
+            const int H = halo_lanes(sweeps_up(nu1, nu2));
+            static const int occ = resident_per_sm(k_up<DIR, T, D>, 0);
+            launch(P, k_up<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]), uc, ua,
+                   nch, K, X, nu1, nu2, H, (const DevState*)P->st);
+        }
+    }
+
     static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr, nullptr, nullptr); }
 
     // One correction cycle.  With ev != nullptr an event is recorded before
@@ -213,8 +263,8 @@ struct Impl {
             if (P->scan_coarsest)
                 enqueue_scan<T, T>(P, rT, static_cast<T*>(P->ul[0]), 0, T(0), nullptr, P->st);
             else
-                launch_tail(P,  rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N,
-                                                                      nu1, nu2, P->o.gamma, P->st);
+                launch_tail(P, rT, static_cast<T*>(P->ul[0]), lk, X, nl, P->N, nu1, nu2, P->o.gamma,
+                            (const DevState*)P->st, (const T*)nullptr);
             mark(kCatUp0);
             launch(P, k_update0<T>, grid_flat(P, P->N * D), kNT, 0, static_cast<const T*>(P->ul[0]),
                    (int64_t)(P->N * D), (const DevState*)P->st);
@@ -232,9 +282,18 @@ struct Impl {
             launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, k_down0_smem_bytes<D>(), rT, rl,
                    static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
         }
+        // W-cycle: level 1 is visited twice; the level-0 way up reads the
+        // correction of its second visit
+        const bool wcycle = P->o.gamma == 2;
+        const T* uc1 = static_cast<const T*>(wcycle ? P->ul2[1] : P->ul[1]);
+        if (wcycle) {
+            mark(kCatDown);
+            w_visit(P, 1, false, X, lk, nl);
+            w_visit(P, 1, true, X, lk, nl);
+        }
         // streaming levels 1 .. lt-1, two at a time where both exist
         int grp[kMaxLevels], ng = 0;
-        for (int l = 1; l < P->lt;) {
+        for (int l = 1; !wcycle && l < P->lt;) {
             // default (-1): fuse where the cycle runs in FP32; the FP64 form is
             // bound by FP64 arithmetic, which the fused way up repeats
             const bool fuse = P->o.fuse_levels > 0 || (P->o.fuse_levels < 0 && kMixed);
@@ -271,16 +330,15 @@ struct Impl {
                        (const DevState*)P->st, ct);
             }
         }
-        mark(kCatCoarse);
-        if (coarse_in_down) {
+        if (!wcycle) mark(kCatCoarse);
+        if (coarse_in_down || wcycle) {
             // solved above
         } else if (P->scan_coarsest)
             enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
                                nullptr, P->st);
         else
-            launch_tail(P,  static_cast<const T*>(P->fl[P->lt]),
-                                                             static_cast<T*>(P->ul[P->lt]), lk, X, nl,
-                                                             P->lev[P->lt].N, nu1, nu2, P->o.gamma, P->st);
+            launch_tail(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), lk, X, nl,
+                        P->lev[P->lt].N, nu1, nu2, P->o.gamma, (const DevState*)P->st, (const T*)nullptr);
         for (int g = ng - 1; g >= 0; --g) {
             mark(kCatUp);
             if (grp[g] < 0) {
@@ -311,7 +369,7 @@ struct Impl {
                 const int64_t nch = P->N / 2;
                 mark(kCatUp0);
                 static const int occ = resident_per_sm(k_updown0<DIR, D>, 0);
-                launch(P, k_updown0<DIR, D>, grid_for(P, nch, H, occ), kNT, 0, rT, rl, static_cast<const float*>(P->ul[1]),
+                launch(P, k_updown0<DIR, D>, grid_for(P, nch, H, occ), kNT, 0, rT, rl, (const float*)uc1,
                        static_cast<float*>(P->fl[1]), nch, R, level_consts<float, D>(L(P)[0]), X, nu1, nu2, H,
                        P->partials, P->st);
                 mark(kCatEnd);
@@ -324,7 +382,7 @@ struct Impl {
             const int64_t nch = P->N / 2;
             mark(kCatUp0);
             static const int occ = resident_per_sm(k_up0<DIR, T, D>, 0);
-            launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, (const T*)rT, static_cast<const T*>(P->ul[1]),
+            launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, (const T*)rT, uc1,
                    nch, level_consts<T, D>(L(P)[0]), X, nu1, nu2, H, (const DevState*)P->st);
         }
         mark(kCatEnd);

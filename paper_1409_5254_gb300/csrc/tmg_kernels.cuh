@@ -296,6 +296,31 @@ __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&
     }
 }
 
+// Pre-smoothing from a given iterate u (the second visit of a level in a
+// W-cycle): w = A u, then nu1 damped block-Jacobi sweeps of u and w; h =
+// A^{-1} f.  The same sweep as presmooth_zero's after its first.
+template <int DIR, typename T, int D>
+__device__ __forceinline__ void presmooth_from(const LevelK<T, D>& K, const T (&f)[2][D], T (&h)[2][D],
+                                               T (&u)[2][D], T (&w)[2][D], int nu1) {
+    const T om = K.omega, om1 = T(1) - K.omega;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        matvec<T, D>(K.Ainv, f[i], h[i]);
+        matvec<T, D>(K.A, u[i], w[i]);
+    }
+    for (int s = 0; s < nu1; ++s) {
+        const T e0 = bval<DIR, T, D>(u[0]);
+        const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
+            w[0][k] = om1 * w[0][k] + om * (f[0][k] + acoef<DIR>(k, ep));
+            u[1][k] = om1 * u[1][k] + om * fma(K.g[k], e0, h[1][k]);
+            w[1][k] = om1 * w[1][k] + om * (f[1][k] + acoef<DIR>(k, e0));
+        }
+    }
+}
+
 // Residual f + a e_{n-1} - A u of a pair, with A u = w carried along.
 template <int DIR, typename T, int D>
 __device__ __forceinline__ void residual_tracked(const T (&f)[2][D], const T (&u)[2][D], const T (&w)[2][D],
@@ -1001,6 +1026,59 @@ __global__ void __launch_bounds__(kNT) k_up(const T* __restrict__ f, const T* __
         prolong_add<T, D>(X, c, v);
         postsmooth<DIR, T, D>(K, h, v, nu2);
         if (inb && lane >= H) store_pair<T, D>(u, q, v);
+    }
+}
+
+// The second visit of level l >= 1 in a W-cycle (nonzero start u_in, the
+// result of the first visit): pre-smooth from u_in, residual, restrict.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kNT) k_down_nz(const T* __restrict__ f, const T* __restrict__ u_in,
+                                                 T* __restrict__ fc, int64_t nchunks, LevelK<T, D> K, Xfer<T, D> X,
+                                                 int nu1, int H, const DevState* __restrict__ st) {
+    pdl_enter();
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
+        load_pair<T, D>(f, q, inb, fv);
+        load_pair<T, D>(u_in, q, inb, u);
+        presmooth_from<DIR, T, D>(K, fv, h, u, w, nu1);
+        residual_tracked<DIR, T, D>(fv, u, w, r);
+        restrict_pair<T, D>(X, r, out);
+        if (inb && lane >= H) VecIO<T, D>::store(fc + q * D, out);
+    }
+}
+
+// The way up of that second visit: recompute the pre-smoothing from u_in, add
+// the prolongated coarse correction uc, post-smooth, write u_out (another
+// buffer than u_in: neighbouring tiles still read u_in).
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kNT) k_up_nz(const T* __restrict__ f, const T* __restrict__ u_in,
+                                               const T* __restrict__ uc, T* __restrict__ u_out, int64_t nchunks,
+                                               LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2, int H,
+                                               const DevState* __restrict__ st) {
+    pdl_enter();
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int64_t ntiles = (nchunks + per - 1) / per;
+    const int64_t nwarps = ((int64_t)gridDim.x * kNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const int64_t q = tw * per + lane - H;
+        const bool inb = q >= 0 && q < nchunks;
+        T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
+        load_pair<T, D>(f, q, inb, fv);
+        load_pair<T, D>(u_in, q, inb, v);
+        load_one<T, D>(uc, q, inb, c);
+        presmooth_from<DIR, T, D>(K, fv, h, v, w, nu1);
+        prolong_add<T, D>(X, c, v);
+        postsmooth<DIR, T, D>(K, h, v, nu2);
+        if (inb && lane >= H) store_pair<T, D>(u_out, q, v);
     }
 }
 
@@ -1712,19 +1790,20 @@ __device__ __forceinline__ TailView<T, D> tail_view(T* p, int64_t Nt, int nl) {
 }
 
 // One cycle on the levels held in V (tail index j = 0..nl-1), from a zero
-// start: V (gamma = 1) or W (gamma = 2) recursion written as a loop, the
-// coarsest level solved exactly.  V.f[0] holds the right-hand side, V.u[0]
-// receives the correction.  lk[j] are the constants of tail level j.  All
+// start (or, with init0, from the iterate V.u[0] holds): V (gamma = 1) or W
+// (gamma = 2) recursion written as a loop, the coarsest level solved exactly.
+// V.f[0] holds the right-hand side, V.u[0] receives the correction.  lk[j] are the constants of tail level j.  All
 // threads of the CTA take part; ends with the block synchronised.
 template <int DIR, typename T, int D>
 __device__ void tail_cycle(const TailView<T, D>& V, const LevelK<T, D>* __restrict__ lk, const Xfer<T, D>& X, int nl,
-                           int nu1, int nu2, int gamma) {
+                           int nu1, int nu2, int gamma, bool init0 = false) {
     int visits[kMaxLevels];
     bool has_init[kMaxLevels];
     for (int j = 0; j < nl; ++j) {
         visits[j] = 0;
         has_init[j] = false;
     }
+    has_init[0] = init0;   // V.u[0] holds the start iterate
     int j = 0;
     bool down = true;
     while (true) {
@@ -1812,19 +1891,23 @@ __device__ void tail_cycle(const TailView<T, D>& V, const LevelK<T, D>* __restri
 
 // The coarse part of the cycle, levels lt..lt+nl-1 (tail index j = l - lt),
 // entirely in shared memory (tail_cycle).  f_in is the right-hand side of
-// level lt, u_out receives its correction.
+// level lt, u_out receives its correction; u_init (or nullptr for zero) is
+// the start iterate of level lt (the second visit in a W-cycle).
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T* __restrict__ u_out,
                                                   const LevelK<T, D>* __restrict__ lk, Xfer<T, D> X, int nl,
                                                   int64_t Nt, int nu1, int nu2, int gamma,
-                                                  const DevState* __restrict__ st) {
+                                                  const DevState* __restrict__ st, const T* __restrict__ u_init) {
     pdl_enter();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char tail_smem[];
     const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(tail_smem), Nt, nl);
-    for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) V.f[0][i] = f_in[i];
+    for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) {
+        V.f[0][i] = f_in[i];
+        if (u_init != nullptr) V.u[0][i] = u_init[i];
+    }
     __syncthreads();
-    tail_cycle<DIR, T, D>(V, lk, X, nl, nu1, nu2, gamma);
+    tail_cycle<DIR, T, D>(V, lk, X, nl, nu1, nu2, gamma, u_init != nullptr);
     for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) u_out[i] = V.u[0][i];
 }
 

@@ -57,6 +57,7 @@ struct tmg_plan {
     int max_blocks;
     void* fl[tmg::kMaxLevels];   // level right-hand sides (cycle precision)
     void* ul[tmg::kMaxLevels];   // level corrections
+    void* ul2[tmg::kMaxLevels];  // W-cycles: the corrections of each level's second visit (levels 1..lt)
     void* rT;                    // level-0 residual (cycle precision)
     void* rl;                    // its low float parts (mixed form with an updated residual), else nullptr
     void* lk_dev;                // tail level constants of L

@@ -98,6 +98,58 @@ def test_fp64_cycles_match_textbook_cycle(dev, case):
         assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
 
 
+W_CASES = [
+    # (p, N, lam, n_min, tail_cap, nu1, nu2): W-cycles over streaming levels --
+    # every level below 1 visited twice per visit of its parent, the second
+    # visit starting from the first one's result
+    (0, 1 << 14, 1.0, 64, 64, 1, 1),        # 7 streaming levels, coarsest (64) by the on-chip solver
+    (1, 1 << 14, 3.0, 64, 512, 2, 1),       # 4 streaming levels, W inside the on-chip part (512 .. 64)
+    (2, 1 << 13, 1.0, 64, 1024, 1, 2),
+    (1, 1 << 14, 1.0, 64, 0, 2, 2),         # default cap 8192: level 1 is on chip, visited twice
+    (1, 1 << 16, 1.0, 16384, 0, 1, 1),      # coarsest level 16384 > 8192: the exact scan on each visit
+    (3, 1 << 13, 20.0, 64, 128, 0, 2),      # no pre-smoothing
+    (1, 1 << 13, 1.0, 64, 128, 1, 0),       # no post-smoothing
+]
+
+
+@pytest.mark.parametrize("case", W_CASES)
+def test_w_cycles_over_streaming_levels_match_textbook_cycle(dev, case):
+    """W-cycles whose streaming levels are visited twice (k_down_nz/k_up_nz
+    on second visits, the on-chip solver or the exact scan started from the
+    first visit's result): three FP64 cycles match the oracle's recursive
+    W-cycle to 1e-12."""
+    p, N, lam, n_min, cap, nu1, nu2 = case
+    prob = inputs.scalar_problem(N % 89, N, p, lam=lam, T=1.0, u0=0.5)
+    z = lam * prob["tau"]
+    Fhat = O.fold_u0(p, prob["F"], prob["u0"])
+    got, info = gpu_cycles(dev, p, prob["tau"], lam, prob["F"], prob["u0"], 3, nu1=nu1, nu2=nu2, gamma=2,
+                           n_min=n_min, tail_cap=cap)
+    assert info["tail_level"] >= 1
+    u = np.zeros_like(prob["F"])
+    for k in range(3):
+        u = O.mg_one_cycle(p, z, Fhat, u, n_min=n_min, nu1=nu1, nu2=nu2, gamma=2)
+        assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
+
+
+@pytest.mark.parametrize("p", [0, 1])
+def test_w_cycle_mixed_solve_reaches_tolerance(dev, p):
+    """A mixed-precision solve with W-cycles over streaming levels reaches the
+    FP64 tolerance; p_t = 0, whose V-cycles degrade on long horizons, needs
+    far fewer W-cycles than V-cycles."""
+    N = 1 << 16
+    prob = inputs.scalar_problem(31, N, p, lam=1.0, T=N * 1e-4, u0=1.0)
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    cycles = {}
+    for gamma in (1, 2):
+        with tmg().Plan(p, prob["tau"], 1.0, N, precision="mixed", gamma=gamma, tail_cap=256,
+                        max_cycles=300) as plan:
+            u = plan.solve(Fd, prob["u0"])
+            cycles[gamma] = plan.stats().cycles
+            assert rel_residual(p, prob["tau"], prob["F"], prob["u0"], u.cpu().numpy()) <= 1.05e-10
+    print(f"p={p}: V-cycles {cycles[1]}, W-cycles {cycles[2]}")
+    assert cycles[2] <= cycles[1]
+
+
 @pytest.mark.parametrize("tail_cap", [64, 128])
 @pytest.mark.parametrize("nu", [(1, 1), (2, 1), (0, 2), (1, 0), (3, 2)])
 def test_fused_level_pairs_match_textbook_cycle(dev, tail_cap, nu):
