@@ -55,14 +55,22 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("p,N,lam,prec", CASES)
-def test_adjoint_matches_oracle(dev, p, N, lam, prec):
+W_CASES = [
+    # W-cycles over streaming levels (on-chip part from 256 intervals down)
+    (0, 1 << 14, 1.0, "fp64", 2),
+    (2, 1 << 14, 10.0, "mixed", 2),
+]
+
+
+@pytest.mark.parametrize("p,N,lam,prec,gamma", [c + (1,) for c in CASES] + W_CASES)
+def test_adjoint_matches_oracle(dev, p, N, lam, prec, gamma):
     from paper_1409_5254_gb300 import tmg
     prob, target = problem(p + N % 7, N, p, lam)
     tau = prob["tau"]
     z = lam * tau
     tol = 1e-12 if prec == "fp64" else 1e-10
-    with tmg.Plan(p, tau, lam, N, precision=prec, tol=tol, max_cycles=400) as plan:
+    extra = {"gamma": 2, "tail_cap": 256} if gamma == 2 else {}
+    with tmg.Plan(p, tau, lam, N, precision=prec, tol=tol, max_cycles=400, **extra) as plan:
         F = torch.from_numpy(prob["F"]).to(dev)
         u = plan.solve(F, prob["u0"])
         uh = u.cpu().numpy()
@@ -77,7 +85,7 @@ def test_adjoint_matches_oracle(dev, p, N, lam, prec):
     _, du0_ref, dlam_ref = O.adjoint_grads(p, lam, tau, g, uh)
     assert float(du0) == pytest.approx(du0_ref, rel=allow, abs=1e-14)
     assert float(dlam) == pytest.approx(dlam_ref, rel=allow, abs=1e-14)
-    print(f"p={p} N={N} {prec}: adjoint cycles={st.cycles} mu err={rel(mu, mu_ref):.2e}")
+    print(f"p={p} N={N} {prec} gamma={gamma}: adjoint cycles={st.cycles} mu err={rel(mu, mu_ref):.2e}")
 
 
 @pytest.mark.parametrize("p", [0, 2])
