@@ -38,12 +38,12 @@ LAM = 1.0
 U0 = 1.0
 P_MAIN = 1
 NU = (2, 2)               # pre-/post-smoothing sweeps of the timed cycles (the paper's plots use nu1 = nu2 in {1, 2, 5})
-N_MIN = 1 << 16           # coarsen while N_l > N_MIN: at N = 2^24 the coarsest level has 2^16 intervals,
+N_MIN = 1 << 17           # coarsen while N_l > N_MIN: at N = 2^24 the coarsest level has 2^17 intervals,
                           # solved exactly by the parallel affine scan (11 cycles, as with 64 intervals)
 
 
 def n_min_p(p: int) -> int:
-    """Coarsest level of the long-horizon lines: 2^16 intervals (scan) for
+    """Coarsest level of the long-horizon lines: 2^17 intervals (scan) for
     p_t <= 1; from p_t = 2 on the FP32 scan of so long a level costs more than
     the levels it replaces, and the default 64 intervals (one warp) is faster."""
     return N_MIN if p <= 1 else 64
@@ -55,7 +55,7 @@ def n_min_for(n: int) -> int:
 TOL = 1e-10
 METRIC = "time-DoFs/s solved to 1e-10 rel residual"
 WORKLOAD = ("long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate "
-            "refinement, V(2,2), omega*, coarsest level 2^16 intervals solved by the parallel affine scan")
+            "refinement, V(2,2), omega*, coarsest level 2^17 intervals solved by the parallel affine scan")
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_updown0

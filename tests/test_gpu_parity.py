@@ -309,10 +309,10 @@ def test_not_converged_status(dev):
         assert plan.stats().cycles == 2
 
 
-@pytest.mark.parametrize("n_min", [64, 1 << 16])
+@pytest.mark.parametrize("n_min", [64, 1 << 17])
 def test_full_size_long_horizon_sampled(dev, n_min):
     """The benchmark workload (N = 2^24, tau = 1e-6, lambda = 1, p = 1, V(2,2)),
-    in the launch configuration the benchmark times (coarsest level 2^16
+    in the launch configuration the benchmark times (coarsest level 2^17
     intervals, solved by the grid-wide affine scan) and with the library's
     default hierarchy (coarsest 64 intervals): FP64 residual of the whole GPU
     result, and sampled intervals against exact forward substitution."""
