@@ -256,7 +256,8 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         const size_t b = P->ops->tail_bytes(P->lev[l].N, P->nlev - l);
         const int64_t cap = o.tail_cap > 0 ? (o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax)
                                            : (o.gamma == 2 ? kTailNmax : kTailDefaultV);
-        if ((P->lev[l].N <= cap || l == P->nlev - 1) && P->lev[l].N <= kTailNmax && b <= kTailSmemMax) {
+        if ((P->lev[l].N <= cap || l == P->nlev - 1) && P->lev[l].N <= kTailNmax && b <= kTailSmemMax &&
+            P->nlev - l <= tmg::kTailLevels) {
             P->lt = l;
             P->tail_smem = b;
             break;

@@ -236,7 +236,7 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     for (int64_t m = G->Ng; m > nmin && m % 2 == 0 && G->nlev < kMaxLevels; m /= 2) ++G->nlev;
     if ((G->Ng >> (G->nlev - 1)) > 64) return TMG_EUNSUPPORTED;
     G->cta_smem = cta_bytes(B, G);
-    G->cta_ok = G->cta_smem <= kCtaSmemMax;
+    G->cta_ok = G->cta_smem <= kCtaSmemMax && G->nlev <= kTailLevels;
     G->sched = B->o.schedule == TMG_SCHED_CTA && G->cta_ok ? TMG_SCHED_CTA : TMG_SCHED_GRID;
     G->ms_tune[0] = G->ms_tune[1] = NAN;
     // layout

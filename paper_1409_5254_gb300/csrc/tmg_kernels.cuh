@@ -1639,17 +1639,20 @@ __global__ void __launch_bounds__(kNT) k_normF(int64_t N, double* __restrict__ p
 // --------------------------------------------------- on-chip coarse solver --
 
 constexpr int kTailNT = 512;
+// Levels one CTA may hold: 8192 intervals (the largest on-chip level) halve
+// to 1 in 14 steps.
+constexpr int kTailLevels = 16;
 
 // Shared-memory image of the coarse hierarchy handled by one CTA.
 template <typename T, int D>
 struct TailView {
-    T* f[kMaxLevels];
-    T* u[kMaxLevels];
+    T* f[kTailLevels];
+    T* u[kTailLevels];
     T* w;        // A u during pre-smoothing
     T* e;        // endpoint values of one pass
     T* scanA;    // [kTailNT/32] warp-total slopes of the coarsest scan
     T* scanB;    // [2*kTailNT/32] warp-total offsets, then inclusive warp prefixes
-    int64_t N[kMaxLevels];
+    int64_t N[kTailLevels];
 };
 
 template <typename T, int D>
@@ -1797,8 +1800,8 @@ __device__ __forceinline__ TailView<T, D> tail_view(T* p, int64_t Nt, int nl) {
 template <int DIR, typename T, int D>
 __device__ void tail_cycle(const TailView<T, D>& V, const LevelK<T, D>* __restrict__ lk, const Xfer<T, D>& X, int nl,
                            int nu1, int nu2, int gamma, bool init0 = false) {
-    int visits[kMaxLevels];
-    bool has_init[kMaxLevels];
+    int visits[kTailLevels];
+    bool has_init[kTailLevels];
     for (int j = 0; j < nl; ++j) {
         visits[j] = 0;
         has_init[j] = false;
