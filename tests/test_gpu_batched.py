@@ -97,6 +97,24 @@ def test_two_level_kernels_match_one_level(dev, prec, nu):
     print(f"two-level {prec} nu={nu}: max cycles {out[True][1].max()}, worst err {err:.2e}")
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_tiny_instances_in_a_batch(dev, prec):
+    """Instances of 1, 2, 3 and 5 intervals (padded groups of 2 to 8
+    intervals, a single level: the exact warp solve and u += c) next to
+    larger ones, every degree; each against the oracle."""
+    from paper_1409_5254_gb300 import tmg
+    N = [1, 2, 3, 5, 1, 2, 64, 300, 1, 4096]
+    p = [0, 1, 2, 3, 5, 4, 1, 2, 3, 1]
+    z = [1.0, 0.1, 10.0, 1e-3, 2.0, 50.0, 0.5, 1e-2, 1e3, 1e-3]
+    Fs, u0, tau, lam = make_batch(17, p, N, z)
+    with tmg.Batch(p, tau, lam, N, precision=prec, tol=1e-10, max_cycles=300) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+    assert (rel <= 1e-10).all(), rel
+    check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, 1e-10)
+
+
 def test_uneven_batch_matches_oracle(dev):
     """Different degrees, lengths (not powers of two) and steps in one batch."""
     from paper_1409_5254_gb300 import tmg
