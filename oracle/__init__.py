@@ -61,6 +61,8 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             c_int, c_long, c_double = ctypes.c_int, ctypes.c_long, ctypes.c_double
+            L.orc_max_degree.argtypes = []
+            L.orc_max_degree.restype = c_int
             L.orc_blocks.argtypes = [c_int, _dp, _dp, _dp, _dp]
             L.orc_transfer.argtypes = [c_int, _dp, _dp]
             L.orc_alpha.argtypes = [c_int, c_double]
@@ -91,7 +93,20 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
+def max_degree() -> int:
+    """Largest DG degree p the oracle accepts (its fixed local arrays and the
+    Gauss rule exact for products of two basis functions)."""
+    return lib().orc_max_degree()
+
+
+def _deg(p: int) -> int:
+    if not 0 <= int(p) <= max_degree():
+        raise ValueError(f"degree p={p} outside 0..{max_degree()}")
+    return int(p)
+
+
 def _vec(F, p):
+    _deg(p)
     F = np.ascontiguousarray(F, dtype=np.float64)
     d = p + 1
     assert F.ndim == 2 and F.shape[1] == d, (F.shape, d)
@@ -100,7 +115,7 @@ def _vec(F, p):
 
 def blocks(p: int):
     """(K, Mhat, a, b) on the reference interval; N = outer(a, b) (Section 2)."""
-    d = p + 1
+    d = _deg(p) + 1
     K, M, a, b = (np.zeros((d, d)), np.zeros((d, d)), np.zeros(d), np.zeros(d))
     lib().orc_blocks(p, _ptr(K), _ptr(M), _ptr(a), _ptr(b))
     return K, M, a, b
@@ -108,7 +123,7 @@ def blocks(p: int):
 
 def transfer(p: int):
     """(P1, P2) = (R1^T, R2^T): coarse-to-fine maps onto the two halves (Section 4.2)."""
-    d = p + 1
+    d = _deg(p) + 1
     P1, P2 = np.zeros((d, d)), np.zeros((d, d))
     lib().orc_transfer(p, _ptr(P1), _ptr(P2))
     return P1, P2
@@ -116,12 +131,12 @@ def transfer(p: int):
 
 def alpha(p: int, z: float) -> float:
     """b^T (K + z Mhat)^{-1} a: the nonzero eigenvalue of A^{-1}N (Lemma chap4_theorem2)."""
-    return lib().orc_alpha(p, float(z))
+    return lib().orc_alpha(_deg(p), float(z))
 
 
 def omega_star(p: int, z: float) -> float:
     """omega* of Lemma chap4_lemma7 at z = lambda*tau_L."""
-    return lib().orc_omega_star(p, float(z))
+    return lib().orc_omega_star(_deg(p), float(z))
 
 
 def num_levels(N: int, n_min: int = 64, max_levels: int = 0) -> int:

@@ -35,16 +35,21 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORC_MAXD 8
+/* Degrees p = 0..20 (d <= 21).  The 22-point Gauss rule integrates every
+ * product of two basis functions (degree <= 2p = 40) exactly. */
+#define ORC_MAXD 21
 #define ORC_PI 3.14159265358979323846
-#define ORC_NQ 12
+#define ORC_NQ 22
 
 /* ---------------------------------------------------------------- basis -- */
 
 /* The quadratures below run in long double so that the FP64 blocks are the
- * correctly rounded values of their definitions (a 12-point rule summed in
- * double leaves errors of a few 1e-15 in the p = 3 entries). */
+ * correctly rounded values of their definitions (the same rule summed in
+ * double leaves errors of a few 1e-15 already in the p = 3 entries). */
 typedef long double ldbl;
+
+/* Largest degree p the oracle accepts. */
+int orc_max_degree(void) { return ORC_MAXD - 1; }
 
 /* Legendre P_k(x) and P_k'(x) for k = 0..n-1 by the three-term recurrence. */
 static void legendre(int n, ldbl x, ldbl *P, ldbl *dP) {

@@ -15,6 +15,8 @@ from paper_1409_5254_gb300 import inputs
 from conftest import load_golden
 
 PS = [0, 1, 2, 3, 4, 5]
+# the higher degrees of the p_t study (p_t = 10, 20) beside the paper's 0..5
+PS_WIDE = PS + [10, 20]
 
 
 def pade(p, z):
@@ -57,9 +59,76 @@ def test_homogeneous_nodal_values_higher_degrees(p, z):
     assert O.alpha(p, z) == pytest.approx(R, rel=1e-12, abs=1e-15)
 
 
+
+def pade_exact(m, n, z):
+    """The same closed form evaluated in exact rational arithmetic (z is a
+    float, so exactly representable): at p = 20 the alternating sums lose
+    every digit in double."""
+    from fractions import Fraction
+    from math import factorial as fa
+    z = Fraction(z)
+    num = sum(Fraction(fa(m + n - j) * fa(m), fa(m + n) * fa(j) * fa(m - j)) * z**j for j in range(m + 1))
+    den = sum(Fraction(fa(m + n - j) * fa(n), fa(m + n) * fa(j) * fa(n - j)) * (-z) ** j
+              for j in range(n + 1))
+    return float(num / den)
+
+
+@pytest.mark.parametrize("p", [10, 20])
+@pytest.mark.parametrize("z", [1e-3, 0.5, 2.0, 40.0, 1e3])
+def test_homogeneous_nodal_values_degrees_10_and_20(p, z):
+    """With f = 0 the nodal values are R(-z)^n u0 (Corollary chap4_corollary1)
+    with R the (p, p+1) sub-diagonal Pade approximant, here at p_t = 10 and 20.
+    alpha is a difference of O(1) terms, so its error is absolute (~1e-16):
+    at p = 20, z = 40 the value itself is 5.5e-10."""
+    N = 40
+    u = O.fsub(p, z, np.zeros((N, p + 1)), 1.0)
+    e = O.nodal_values(p, u)
+    R = pade_exact(p, p + 1, -z)
+    n = np.arange(1, N + 1)
+    assert np.all(np.abs(e - R ** n) <= 1e-12 * np.abs(R) ** n + 1e-14 * n)
+    assert O.alpha(p, z) == pytest.approx(R, rel=1e-12, abs=1e-15)
+
+
+def polynomial_case(p, lam=1.3, T=1.0, N=16, seed=0):
+    """A problem whose exact solution q is a polynomial of degree p on (0, T):
+    f = q' + lam q, u0 = q(0).  Returns (z, F, u0, U) with F[n,k] = tau
+    int_0^1 f(t_n + tau s) psi_k(s) ds and U[n] the shifted-Legendre
+    coefficients of q on interval n, both by a (p+12)-point Gauss rule with
+    numpy's Legendre routines."""
+    Lg = np.polynomial.legendre
+    rng = np.random.default_rng(seed)
+    c = rng.standard_normal(p + 1)                       # q(t) = sum_j c_j P_j(2t/T - 1)
+    dc = Lg.legder(c) * (2.0 / T)
+    q = lambda t: Lg.legval(2.0 * t / T - 1.0, c)              # noqa: E731
+    dq = lambda t: Lg.legval(2.0 * t / T - 1.0, dc) if p else 0.0 * t   # noqa: E731
+    xg, wg = Lg.leggauss(p + 12)
+    s, w = 0.5 * (xg + 1.0), 0.5 * wg
+    psi = np.stack([Lg.legval(2.0 * s - 1.0, np.eye(p + 1)[k]) for k in range(p + 1)])
+    tau = T / N
+    F, U = np.zeros((N, p + 1)), np.zeros((N, p + 1))
+    for n in range(N):
+        t = n * tau + tau * s
+        F[n] = tau * (psi * (w * (dq(t) + lam * q(t)))).sum(axis=1)
+        U[n] = (psi * (w * q(t))).sum(axis=1) * (2.0 * np.arange(p + 1) + 1.0)
+    return lam * tau, F, float(q(0.0)), U
+
+
+@pytest.mark.parametrize("p", PS_WIDE)
+def test_dg_reproduces_polynomial_solutions(p):
+    """Galerkin consistency of the variational form eq. chap4_discreteVarFormODE:
+    an exact solution inside the trial space (a polynomial of degree p, continuous,
+    so every upwind jump vanishes) satisfies the discrete equations, and the
+    block system returns its coefficients on every interval."""
+    z, F, u0, U = polynomial_case(p)
+    u = O.fsub(p, z, F, u0)
+    assert np.abs(u - U).max() <= 1e-13 * np.abs(U).max()
+    # the multigrid solve reaches the same coefficients
+    um, hist = O.mg_solve(p, z, F, u0, n_min=2, tol=1e-14, max_cycles=100)
+    assert np.abs(um - U).max() <= 1e-12 * np.abs(U).max()
+
 # --------------------------------------------------------------- blocks --
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 def test_blocks_match_legendre_identities(p):
     """K, Mhat, a, b against Legendre identities: P_k(1) = 1, P_k(-1) = (-1)^k,
     int_{-1}^{1} P_k P_l = 2/(2k+1) delta_kl, and P_k' = sum_{j<k, k-j odd} (2j+1) P_j,
@@ -73,7 +142,7 @@ def test_blocks_match_legendre_identities(p):
     np.testing.assert_allclose(b, np.ones(d), atol=1e-15)
 
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 def test_prolongation_is_exact_injection(p):
     """P1, P2 carry a coarse polynomial onto each half exactly (L2 projection of a
     polynomial of the same degree): check pointwise with numpy's Legendre evaluation."""
@@ -101,7 +170,7 @@ def dense_L(p, z, N):
     return L
 
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 @pytest.mark.parametrize("z", [1e-3, 0.7, 50.0])
 def test_galerkin_coarse_operator_equals_rediscretisation(p, z):
     """R L_tau P = L_{2tau}: with exact injection and the upwind DG form the
@@ -148,7 +217,7 @@ def test_homogeneous_nodal_values_follow_pade(p, z):
     assert O.alpha(p, z) == pytest.approx(R, rel=1e-13, abs=1e-15)
 
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 @pytest.mark.parametrize("z", [1e-3, 1.0, 1e3])
 def test_fsub_matches_dense_brute_force(p, z):
     for N in (1, 2, 5, 64):
@@ -209,7 +278,7 @@ def test_dg_with_radau_rhs_equals_radau_ia(p):
 
 # ------------------------------------------------------------- multigrid --
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 @pytest.mark.parametrize("gamma", [1, 2])
 def test_mg_converges_to_forward_substitution(p, gamma):
     prob = inputs.scalar_problem(0, 256, p, lam=2.0, T=1.0, u0=1.0)
@@ -297,7 +366,7 @@ def test_lfa_p0_closed_form(z):
     assert th == pytest.approx(np.pi / 2)
 
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 @pytest.mark.parametrize("z", [0.05, 0.6, 5.0])
 def test_lfa_equals_periodic_two_grid(p, z):
     """The Fourier analysis is exact for the time-periodic system
@@ -321,14 +390,20 @@ def test_lfa_claims_of_section_4():
     assert lfa.two_grid_factor(1, 3.0, N_L=256) < 1e-6
 
 
-@pytest.mark.parametrize("p", PS)
+@pytest.mark.parametrize("p", PS_WIDE)
 def test_alpha_range_and_smoothing_bounds(p):
     """Lemma chap4_lemma7: (5 - 3 sqrt 3)/2 <= alpha <= 1 and mu_S <= 1/sqrt 2 with
     omega*; Lemma chap4_lemma8: max_theta S_hat <= |alpha| (1 + |alpha|) / (1 + alpha^2);
     Lemma chap4_lemma4: rho(S(theta)) = max(|1 - omega|, S_hat) (S_hat alone for p = 0)."""
     lo = (5.0 - 3.0 * math.sqrt(3.0)) / 2.0
+    K, M, a, b = O.blocks(p)
     for z in np.logspace(-4, 4, 33):
         al = O.alpha(p, z)
+        # eigenvalue rounding of the rank-one A^{-1}N: eps |S| times the condition
+        # |A^{-1}a| |b| / |alpha| of its simple eigenvalue alpha (at p = 20 alpha
+        # falls to ~1e-8 at large z)
+        g = np.linalg.norm(np.linalg.solve(K + z * M, a)) * np.linalg.norm(b)
+        tol = 1e-10 + 16 * np.finfo(float).eps * g * g / max(abs(al), 1e-300)
         assert lo - 1e-12 <= al <= 1.0
         w = O.omega_star(p, z)
         assert w == pytest.approx(1.0 / (1.0 + al * al) if al >= 0 else 1.0)
@@ -339,7 +414,7 @@ def test_alpha_range_and_smoothing_bounds(p):
             # the eigenvalue 1 - omega comes from the zero eigenvalue of A^{-1}N,
             # which exists only when N_t = p + 1 >= 2
             expect = max(abs(1 - w), lfa.s_hat(w, al, th)) if p >= 1 else lfa.s_hat(w, al, th)
-            assert lfa.smoother_radius(p, z, th, w) == pytest.approx(expect, abs=1e-10)
+            assert lfa.smoother_radius(p, z, th, w) == pytest.approx(expect, abs=tol)
 
 
 @pytest.mark.parametrize("al", [-0.09, -0.03, 0.0, 0.2, 0.6, 0.95])
