@@ -63,7 +63,7 @@ WORKLOAD = ("long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixe
 # k_updown0_long_horizon_p1_mixed.md); valid only for the kernel source it was
 # taken with (first 16 hex digits of the SHA-256 of tmg_kernels.cuh), else null.
 BATCH_STRIDE = 1          # every s-th heat mode (profiling of smaller cases only)
-UPDOWN0_TRAFFIC = {"bytes_per_launch": 1.0180e9, "kernels_sha256": "53b5cbd99c133553"}
+UPDOWN0_TRAFFIC = {"bytes_per_launch": 1.0180e9, "kernels_sha256": "34384092ae2de274"}
 
 
 def measured_traffic():
@@ -322,6 +322,27 @@ def run_ours(args):
                 per_p[str(p)] = {"error": str(e)}
             del Fp, up
         extra["per_p_mixed"] = per_p
+        # p_t = 10 on the same long horizon, in both forms (the coarsest level is
+        # solved by the scan; the mixed form recomputes the level-0 residual from u)
+        pr = inputs.scalar_problem(1, N_FULL, 10, lam=LAM, tau=TAU, u0=U0)
+        Fp = torch.from_numpy(pr["F"]).to(dev)
+        up = torch.empty_like(Fp)
+        del pr
+        for prec in ("mixed", "fp64"):
+            key = f"p10_{prec}"
+            try:
+                with tmg.Plan(10, TAU, LAM, N_FULL, precision=prec, tol=TOL, stream=stream, max_cycles=300,
+                              nu1=NU[0], nu2=NU[1], n_min=64, use_graph=not args.eager) as pp:
+                    pp.solve(Fp, U0, up)
+                    msp = time_solves(pp, Fp, up, 2, stream, torch)
+                    sp = pp.stats()
+                    extra[key] = {"value": N_FULL * 11 / (msp * 1e-3), "ms_per_step": round(msp, 4),
+                                  "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": f"V{NU}",
+                                  "levels": pp.info()["levels"],
+                                  "coarsest_intervals": pp.info()["tail_intervals"]}
+            except tmg.TmgError as e:
+                extra[key] = {"error": str(e)}
+        del Fp, up
         # other sweep counts on the headline problem (same solver, same tolerance)
         nus = {}
         for nu in ((1, 1), (1, 3), (2, 3), (3, 3)):

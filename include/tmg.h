@@ -98,7 +98,10 @@ enum { TMG_SCHED_AUTO = 0, TMG_SCHED_GRID = 1, TMG_SCHED_CTA = 2 };
 void tmg_opts_default(tmg_opts *opts);
 
 /*
- * Build a plan for one problem: degree p_t in {0,1,2,3}, step tau > 0,
+ * Build a plan for one problem: degree p_t in 0..5, or p_t = 10 (forward
+ * solves only: tmg_adjoint returns TMG_EUNSUPPORTED; the coarsest level is
+ * always solved by the grid-wide scan; the mixed form recomputes the level-0
+ * residual from u in every cycle, as with update_residual = 0), step tau > 0,
  * lambda >= 0 (finite), N >= 1 intervals.  levels <= 0 picks the hierarchy
  * from opts->n_min; levels >= 1 caps the number of levels.  omega <= 0 uses
  * omega*(alpha(lambda tau_l)) per level (Lemma chap4_lemma7); 0 < omega < 2
@@ -113,7 +116,8 @@ void tmg_opts_default(tmg_opts *opts);
  * level 0 twice per visit of its parent, the second visit starting from the
  * first one's result (one launch per level and visit on the streaming levels,
  * so their cost in launches doubles per level: keep the streaming part short
- * with the default tail_cap).  Returns TMG_EINVAL for bad arguments,
+ * with the default tail_cap).  Returns TMG_EINVAL for bad arguments (p_t
+ * outside 0..20 among them), TMG_EUNSUPPORTED for the other degrees up to 20,
  * TMG_ENOMEM / TMG_ECUDA on allocation failure.
  */
 tmg_status tmg_setup(tmg_plan **plan, int p_t, double tau, double lambda, int64_t N, int levels,
@@ -160,6 +164,7 @@ tmg_status tmg_solve_direct(tmg_plan *plan, const double *f, double u0, double *
  * -tau sum_n mu_n^T Mhat u_n (L depends on lambda through lambda*tau*Mhat);
  * dJdu0 and dJdlambda are device doubles.  u must be the forward solution.
  * The first call allocates a 2 N (p_t+1) double buffer owned by the plan.
+ * Plans of p_t = 10 have no adjoint kernels: TMG_EUNSUPPORTED.
  */
 tmg_status tmg_adjoint(tmg_plan *plan, const double *g, const double *u, double *dJdf, double *dJdu0,
                        double *dJdlambda);
@@ -226,7 +231,7 @@ tmg_status tmg_inspect(const tmg_plan *plan, int which, int level, void *host_ds
  * it is the level-0 residual kernel with its block partial sums kept in a
  * fixed file-scope device array instead of a plan workspace.
  *
- * p_t, tau, lambda, N, f, u0, u as for tmg_setup/tmg_solve; f, u, r device
+ * p_t (0..5), tau, lambda, N, f, u0, u as for tmg_setup/tmg_solve; f, u, r device
  * [N][p_t+1] float64, 16-byte aligned; norm an 8-byte aligned device double.
  * N may not exceed 2^21 intervals (the scratch array holds 1024 block partial
  * sums of 2048 intervals each): larger N returns TMG_EUNSUPPORTED before any

@@ -40,6 +40,10 @@ int count_levels(int64_t N, int64_t n_min, int max_levels) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Degrees accepted as arguments (larger ones are rejected as invalid; those
+// between the built ones as unsupported).
+const int kMaxDegree = 20;
+
 const int64_t kTailNmax = 8192;
 // Default largest level of the on-chip coarse solver: small, because inside
 // a graph with programmatic dependent launch a streaming kernel on a small
@@ -200,11 +204,16 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     tmg_opts o;
     tmg_opts_default(&o);
     if (opts) o = *opts;
-    if (p_t < 0 || p_t > tmg::kMaxD - 1 || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
+    if (p_t < 0 || p_t > kMaxDegree || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
         !(omega < 2.0) || !isfinite(omega) || o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 ||
         o.gamma < 1 || o.gamma > 2 || (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 ||
         o.max_cycles < 0 || o.max_cycles >= tmg::kHist || !(o.tol >= 0.0))
         return TMG_EINVAL;
+    // p_t <= 5, and p_t = 10 (forward solves; in the mixed form the level-0
+    // residual is recomputed from u in every cycle: no updated float pair)
+    const bool wide = p_t + 1 > tmg::kMaxD;
+    if (wide && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
+    if (wide) o.update_residual = 0;
 
     tmg_plan* P = new (std::nothrow) tmg_plan();
     if (!P) return TMG_ENOMEM;
@@ -228,7 +237,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         P->own_stream = true;
     }
     P->ops = o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 0) : tmg_ops_f64(P->d, 0);
-    P->ops_adj = o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 1) : tmg_ops_f64(P->d, 1);
+    P->ops_adj = wide ? nullptr : o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 1) : tmg_ops_f64(P->d, 1);
 
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -250,9 +259,10 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     P->lev_adj.resize(P->nlev);
     for (int l = 0; l < P->nlev; ++l) level_setup_adjoint(P->d, P->lev[l], &P->lev_adj[l]);
 
-    // first level handled on chip: the largest that fits
+    // first level handled on chip: the largest that fits (no on-chip solver
+    // for the wide blocks)
     P->lt = -1;
-    for (int l = 0; l < P->nlev; ++l) {
+    for (int l = 0; !wide && l < P->nlev; ++l) {
         const size_t b = P->ops->tail_bytes(P->lev[l].N, P->nlev - l);
         const int64_t cap = o.tail_cap > 0 ? (o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax)
                                            : (o.gamma == 2 ? kTailNmax : kTailDefaultV);
@@ -293,9 +303,9 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     const size_t off_rl = off;
     if (updated_res) off = align_up(off + sizeof(short) * N * P->d * 2, A);
     const size_t off_lk = off;
-    off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxD>) * (P->nlev - P->lt), A);
+    off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxDWide>) * (P->nlev - P->lt), A);
     const size_t off_lk_adj = off;
-    off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxD>) * (P->nlev - P->lt), A);
+    off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxDWide>) * (P->nlev - P->lt), A);
     const size_t off_p = off;
     off = align_up(off + sizeof(double) * P->max_blocks, A);
     P->scan_tiles = (N + tmg::kScanTile - 1) / tmg::kScanTile;
@@ -335,7 +345,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     ce = cudaMemsetAsync(P->ws, 0, P->ws_bytes, P->s);
     // the attribute is per kernel, shared by every plan: set the common ceiling
     if (ce == cudaSuccess) ce = P->ops->upload(P);
-    if (ce == cudaSuccess) ce = P->ops_adj->upload(P);
+    if (ce == cudaSuccess && P->ops_adj) ce = P->ops_adj->upload(P);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(P->s);
     if (ce != cudaSuccess) {
         tmg_destroy(P);
@@ -375,6 +385,7 @@ tmg_status tmg_adjoint(tmg_plan* P, const double* g, const double* u, double* dJ
     if (!P || check_ptr(g) != TMG_OK || check_ptr(u) != TMG_OK || check_ptr(dJdf) != TMG_OK || !dJdu0 ||
         !dJdlambda || (reinterpret_cast<uintptr_t>(dJdu0) & 7u) || (reinterpret_cast<uintptr_t>(dJdlambda) & 7u))
         return TMG_EINVAL;
+    if (!P->ops_adj) return TMG_EUNSUPPORTED;   // no adjoint kernels at this degree
     const size_t nv = (size_t)P->N * P->d;
     if (!P->adj_buf) {
         cudaError_t e = cudaMalloc(&P->adj_buf, 2 * nv * sizeof(double));

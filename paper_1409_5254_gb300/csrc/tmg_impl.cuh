@@ -37,7 +37,7 @@ Xfer<T, D> xfer_consts(const tmg_plan* P, int dir) {
 
 inline Res0 res0_consts(const tmg_plan* P) {
     Res0 R;
-    for (int k = 0; k < kMaxD; ++k) {
+    for (int k = 0; k < kMaxDWide; ++k) {
         R.zm[k] = P->lev[0].z / (2.0 * k + 1.0);
         R.zm_hi[k] = (float)R.zm[k];
         R.zm_lo[k] = (float)(R.zm[k] - (double)R.zm_hi[k]);
@@ -173,11 +173,15 @@ struct Impl {
         }
     }
 
+    // The on-chip coarse solver exists for p_t <= 5; a plan of a wider block
+    // solves its coarsest level by the scan (checked in enqueue_cycle_timed).
     template <typename... Args>
     static void launch_tail(tmg_plan* P, Args... args) {
-        static const cudaError_t attr = allow_smem(k_tail<DIR, T, D>, kTailSmemMax);
-        (void)attr;   // a failed opt-in makes the launch fail, which the caller reports
-        launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, args...);
+        if constexpr (D <= kMaxD) {
+            static const cudaError_t attr = allow_smem(k_tail<DIR, T, D>, kTailSmemMax);
+            (void)attr;   // a failed opt-in makes the launch fail, which the caller reports
+            launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, args...);
+        }
     }
 
     // One visit of level l >= 1 in a W-cycle (gamma = 2): nz = the second
@@ -237,6 +241,9 @@ struct Impl {
     // between ev[i] and ev[i+1] (kCat*) and *nev the number of events
     // (at most 2 * nlev + 4).
     static cudaError_t enqueue_cycle_timed(tmg_plan* P, cudaEvent_t* ev, int* cat, int* nev) {
+        if constexpr (D > kMaxD) {
+            if (!P->scan_coarsest) return cudaErrorInvalidValue;
+        }
         P->launches_per_cycle = 0;
         int iev = 0;
         auto mark = [&](int c) {
@@ -296,7 +303,8 @@ struct Impl {
         for (int l = 1; !wcycle && l < P->lt;) {
             // default (-1): fuse where the cycle runs in FP32; the FP64 form is
             // bound by FP64 arithmetic, which the fused way up repeats
-            const bool fuse = P->o.fuse_levels > 0 || (P->o.fuse_levels < 0 && kMixed);
+            // (the two-level kernels exist for p_t <= 5)
+            const bool fuse = D <= kMaxD && (P->o.fuse_levels > 0 || (P->o.fuse_levels < 0 && kMixed));
             const int two = fuse && l + 1 < P->lt;
             grp[ng++] = two ? -l : l;      // negative: levels l and l+1 in one kernel
             l += two ? 2 : 1;
@@ -312,14 +320,16 @@ struct Impl {
             const CoarseTail<T, D> ct = coarse_in_down && g == ng - 1 ? ct_last : ct_none;
             mark(kCatDown);
             if (grp[g] < 0) {
-                const int l = -grp[g];
-                const int g0 = sweeps_down(nu1);
-                const int H = halo_lanes(halo_lanes(g0) + sweeps_down(nu1));
-                const int64_t nq = P->lev[l].N / 4;
-                static const int occ = resident_per_sm(k_down2<DIR, T, D>, 0);
-                launch(P, k_down2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
-                       static_cast<T*>(P->fl[l + 2]), nq, level_consts<T, D>(L(P)[l]),
-                       level_consts<T, D>(L(P)[l + 1]), X, nu1, H, (const DevState*)P->st, ct);
+                if constexpr (D <= kMaxD) {
+                    const int l = -grp[g];
+                    const int g0 = sweeps_down(nu1);
+                    const int H = halo_lanes(halo_lanes(g0) + sweeps_down(nu1));
+                    const int64_t nq = P->lev[l].N / 4;
+                    static const int occ = resident_per_sm(k_down2<DIR, T, D>, 0);
+                    launch(P, k_down2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                           static_cast<T*>(P->fl[l + 2]), nq, level_consts<T, D>(L(P)[l]),
+                           level_consts<T, D>(L(P)[l + 1]), X, nu1, H, (const DevState*)P->st, ct);
+                }
             } else {
                 const int l = grp[g];
                 const int H = halo_lanes(sweeps_down(nu1));
@@ -342,17 +352,19 @@ struct Impl {
         for (int g = ng - 1; g >= 0; --g) {
             mark(kCatUp);
             if (grp[g] < 0) {
-                const int l = -grp[g];
-                // level-l units: the recomputed way down, then level l+1 (recomputed
-                // pre-smoothing, post-smoothing), prolongated, then level-l post-smoothing
-                const int g1 = halo_lanes(sweeps_down(nu1)) + sweeps_up(nu1, nu2);
-                const int H = (2 * g1 + nu2 + 3) / 4;
-                const int64_t nq = P->lev[l].N / 4;
-                static const int occ = resident_per_sm(k_up2<DIR, T, D>, 0);
-                launch(P, k_up2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
-                       static_cast<const T*>(P->ul[l + 2]), static_cast<T*>(P->ul[l]), nq,
-                       level_consts<T, D>(L(P)[l]), level_consts<T, D>(L(P)[l + 1]), X, nu1, nu2, H,
-                       (const DevState*)P->st);
+                if constexpr (D <= kMaxD) {
+                    const int l = -grp[g];
+                    // level-l units: the recomputed way down, then level l+1 (recomputed
+                    // pre-smoothing, post-smoothing), prolongated, then level-l post-smoothing
+                    const int g1 = halo_lanes(sweeps_down(nu1)) + sweeps_up(nu1, nu2);
+                    const int H = (2 * g1 + nu2 + 3) / 4;
+                    const int64_t nq = P->lev[l].N / 4;
+                    static const int occ = resident_per_sm(k_up2<DIR, T, D>, 0);
+                    launch(P, k_up2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
+                           static_cast<const T*>(P->ul[l + 2]), static_cast<T*>(P->ul[l]), nq,
+                           level_consts<T, D>(L(P)[l]), level_consts<T, D>(L(P)[l + 1]), X, nu1, nu2, H,
+                           (const DevState*)P->st);
+                }
             } else {
                 const int l = grp[g];
                 const int H = halo_lanes(sweeps_up(nu1, nu2));
@@ -363,7 +375,7 @@ struct Impl {
                        level_consts<T, D>(L(P)[l]), X, nu1, nu2, H, (const DevState*)P->st);
             }
         }
-        if constexpr (kMixed) {
+        if constexpr (kMixed && D <= kMaxD) {   // (wider mixed plans recompute the residual from u)
             if (rl != nullptr) {
                 const int H = halo_lanes(sweeps_up(nu1, nu2) + 1 + sweeps_down(nu1));
                 const int64_t nch = P->N / 2;

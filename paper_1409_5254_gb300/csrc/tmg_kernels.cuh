@@ -29,7 +29,8 @@
 
 namespace tmg {
 
-constexpr int kMaxD = 6;          // p_t <= 5
+constexpr int kMaxD = 6;          // p_t <= 5: every form, the adjoint and the batched solve
+constexpr int kMaxDWide = 11;     // p_t = 10: the plain FP64 forward solve of one problem
 constexpr int kMaxLevels = 48;
 constexpr int kHist = 512;
 constexpr unsigned kFull = 0xffffffffu;
@@ -55,9 +56,9 @@ struct Xfer {
 // Level-0 residual constants: zm[k] = z_0 / (2k+1) in FP64 and as an
 // unevaluated float pair zm_hi + zm_lo.
 struct Res0 {
-    double zm[kMaxD];
-    float zm_hi[kMaxD];
-    float zm_lo[kMaxD];
+    double zm[kMaxDWide];
+    float zm_hi[kMaxDWide];
+    float zm_lo[kMaxDWide];
 };
 
 // Device-resident solve state.  Written by the last block of the residual

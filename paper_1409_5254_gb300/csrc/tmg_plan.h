@@ -17,10 +17,10 @@ constexpr size_t kTailSmemMax = 200 * 1024;
 struct tmg_level_host {
     int64_t N;          // intervals
     double z;           // lambda * tau_l
-    double A[tmg::kMaxD * tmg::kMaxD];       // K + z Mhat (row-major, D x D)
-    double Ainv[tmg::kMaxD * tmg::kMaxD];
-    double g[tmg::kMaxD];                    // A^{-1} a
-    double c[tmg::kMaxD];                    // b^T A^{-1}
+    double A[tmg::kMaxDWide * tmg::kMaxDWide];   // K + z Mhat (row-major, D x D)
+    double Ainv[tmg::kMaxDWide * tmg::kMaxDWide];
+    double g[tmg::kMaxDWide];                     // A^{-1} a
+    double c[tmg::kMaxDWide];                     // b^T A^{-1}
     double alpha;       // b^T A^{-1} a
     double omega;
 };
@@ -46,7 +46,8 @@ struct tmg_plan {
     size_t tail_smem;
     std::vector<tmg_level_host> lev;       // constants of L
     std::vector<tmg_level_host> lev_adj;   // constants of L^T in reversed time
-    double P1[tmg::kMaxD * tmg::kMaxD], P2[tmg::kMaxD * tmg::kMaxD];   // prolongation (coarse -> fine halves)
+    // prolongation (coarse -> fine halves)
+    double P1[tmg::kMaxDWide * tmg::kMaxDWide], P2[tmg::kMaxDWide * tmg::kMaxDWide];
 
     // device workspace (one allocation)
     void* ws;
@@ -101,6 +102,8 @@ const tmg_ops* tmg_ops_f32(int d, int dir);
 const tmg_ops* tmg_ops_f64(int d, int dir);
 const tmg_ops* tmg_ops_f32_hi(int d, int dir);   // d = 4..6
 const tmg_ops* tmg_ops_f64_hi(int d, int dir);
+const tmg_ops* tmg_ops_f32_wide(int d, int dir);   // d = 11, forward only (nullptr otherwise)
+const tmg_ops* tmg_ops_f64_wide(int d, int dir);   // d = 11, forward only (nullptr otherwise)
 
 // Adjoint helpers (tmg_adjoint.cu): reverse the interval order of an [N][d]
 // array, and the gradient reductions dJ/du0 = a^T mu_0,

@@ -28,7 +28,7 @@ inline void local_blocks(int d, double z, double* A) {
 
 // Gauss-Jordan inversion with partial pivoting; returns false if singular.
 inline bool invert(int d, const double* A, double* Ainv) {
-    double M[tmg::kMaxD][2 * tmg::kMaxD];
+    double M[tmg::kMaxDWide][2 * tmg::kMaxDWide];
     for (int i = 0; i < d; ++i)
         for (int j = 0; j < 2 * d; ++j) M[i][j] = j < d ? A[i * d + j] : (j - d == i ? 1.0 : 0.0);
     for (int c = 0; c < d; ++c) {
@@ -101,7 +101,7 @@ inline void level_setup(int d, double z, double omega_user, tmg_level_host* L) {
 // columns follow from composing P_k with that affine map and converting the
 // monomial coefficients back to the Legendre basis (exact polynomial algebra).
 inline void transfer_setup(int d, double* P1, double* P2) {
-    constexpr int M = tmg::kMaxD;
+    constexpr int M = tmg::kMaxDWide;
     double leg[M][M] = {{0}};   // monomial coefficients of P_0..P_{d-1}
     leg[0][0] = 1.0;
     if (d > 1) leg[1][1] = 1.0;

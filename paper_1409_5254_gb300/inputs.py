@@ -59,10 +59,14 @@ def _legendre_table(p: int, s: np.ndarray) -> np.ndarray:
     return np.stack([np.polynomial.legendre.legval(x, np.eye(p + 1)[l]) for l in range(p + 1)], axis=1)
 
 
-def load_vector(p: int, N: int, T: float, f, q: int = 8, chunk: int = 1 << 20,
+def load_vector(p: int, N: int, T: float, f, q: int | None = None, chunk: int = 1 << 20,
                 n_stop: int | None = None) -> np.ndarray:
     """Load vector (N, p+1) of forcing ``f`` on the uniform mesh t_n = n T / N
-    (only the first n_stop intervals when given)."""
+    (only the first n_stop intervals when given), by a q-point Gauss rule per
+    interval: 8 points, or p + 2 where that is more, so that every
+    coefficient of the load vector is an independent value."""
+    if q is None:
+        q = max(8, p + 2)
     tau = T / N
     xg, wg = np.polynomial.legendre.leggauss(q)
     s = 0.5 * (xg + 1.0)

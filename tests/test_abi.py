@@ -41,10 +41,14 @@ def test_strerror_and_defaults_without_gpu():
 def test_setup_rejects_bad_arguments_before_touching_the_gpu():
     lib = tmg._lib()
     h = ctypes.c_void_p()
-    bad = [(6, 0.1, 1.0, 16), (1, 0.0, 1.0, 16), (1, 0.1, -1.0, 16), (1, 0.1, 1.0, 0),
+    bad = [(21, 0.1, 1.0, 16), (1, 0.0, 1.0, 16), (1, 0.1, -1.0, 16), (1, 0.1, 1.0, 0),
            (1, float("nan"), 1.0, 16), (-1, 0.1, 1.0, 16)]
     for p, tau, lam, N in bad:
         st = lib.tmg_setup(ctypes.byref(h), p, tau, lam, N, 0, 0.0, None, None)
         assert st == tmg.TMG_EINVAL, (p, tau, lam, N, st)
+    # degrees up to 20 that are not built
+    for p in (6, 9, 11, 20):
+        st = lib.tmg_setup(ctypes.byref(h), p, 0.1, 1.0, 16, 0, 0.0, None, None)
+        assert st == tmg.TMG_EUNSUPPORTED, (p, st)
     st = lib.tmg_setup(ctypes.byref(h), 1, 0.1, 1.0, 16, 0, 2.5, None, None)
     assert st == tmg.TMG_EINVAL
