@@ -322,6 +322,24 @@ def run_ours(args):
                 per_p[str(p)] = {"error": str(e)}
             del Fp, up
         extra["per_p_mixed"] = per_p
+        # the same long horizon at the larger step tau = 1/1024 (z ~ 1e-3; T = 16384)
+        tau2 = 1.0 / 1024
+        pr = inputs.scalar_problem(1, N_FULL, P_MAIN, lam=LAM, tau=tau2, u0=U0)
+        Fp = torch.from_numpy(pr["F"]).to(dev)
+        up = torch.empty_like(Fp)
+        del pr
+        try:
+            with tmg.Plan(P_MAIN, tau2, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, max_cycles=300,
+                          nu1=NU[0], nu2=NU[1], n_min=N_MIN, use_graph=not args.eager) as pp:
+                pp.solve(Fp, U0, up)
+                msp = time_solves(pp, Fp, up, max(2, args.steps // 4), stream, torch)
+                sp = pp.stats()
+                extra["tau_1_1024"] = {"value": N_FULL * d / (msp * 1e-3), "ms_per_step": round(msp, 4),
+                                       "cycles": sp.cycles, "rel_res": sp.rel_res, "z": LAM * tau2,
+                                       "cycle": f"V{NU}"}
+        except tmg.TmgError as e:
+            extra["tau_1_1024"] = {"error": str(e)}
+        del Fp, up
         # p_t = 10 on the same long horizon, in both forms (the coarsest level is
         # solved by the scan; the mixed form recomputes the level-0 residual from u)
         pr = inputs.scalar_problem(1, N_FULL, 10, lam=LAM, tau=TAU, u0=U0)
