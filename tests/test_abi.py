@@ -52,3 +52,45 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
         assert st == tmg.TMG_EUNSUPPORTED, (p, st)
     st = lib.tmg_setup(ctypes.byref(h), 1, 0.1, 1.0, 16, 0, 2.5, None, None)
     assert st == tmg.TMG_EINVAL
+
+
+def test_batched_setup_rejects_bad_arguments_before_touching_the_gpu():
+    """tmg_setup_batched validates every instance and the options on the host:
+    degrees 0..5 only, tau > 0, lambda >= 0 (finite), N >= 1, V-cycles only,
+    a known schedule, omega < 2."""
+    import numpy as np
+    lib = tmg._lib()
+    h = ctypes.c_void_p()
+
+    def call(p, tau, lam, N, omega=0.0, **opt):
+        n = len(p)
+        pa = np.asarray(p, dtype=np.int32)
+        ta = np.asarray(tau, dtype=np.float64)
+        la = np.asarray(lam, dtype=np.float64)
+        Na = np.asarray(N, dtype=np.int64)
+        o = tmg._Opts()
+        lib.tmg_opts_default(ctypes.byref(o))
+        for k, v in opt.items():
+            setattr(o, k, v)
+        ip, dp, lp = (ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                      ctypes.POINTER(ctypes.c_int64))
+        return lib.tmg_setup_batched(ctypes.byref(h), n, pa.ctypes.data_as(ip), ta.ctypes.data_as(dp),
+                                     la.ctypes.data_as(dp), Na.ctypes.data_as(lp), omega, ctypes.byref(o), None)
+
+    ok = ([1, 2], [0.1, 0.1], [1.0, 2.0], [64, 128])
+    bad_instances = [
+        ([1, 6], [0.1, 0.1], [1.0, 2.0], [64, 128]),       # p_t = 6 (batches go to 5)
+        ([1, 10], [0.1, 0.1], [1.0, 2.0], [64, 128]),      # p_t = 10 (single problems only)
+        ([1, -1], [0.1, 0.1], [1.0, 2.0], [64, 128]),
+        ([1, 2], [0.1, 0.0], [1.0, 2.0], [64, 128]),       # tau = 0
+        ([1, 2], [0.1, 0.1], [1.0, -2.0], [64, 128]),      # lambda < 0
+        ([1, 2], [0.1, 0.1], [1.0, float("inf")], [64, 128]),
+        ([1, 2], [0.1, 0.1], [1.0, 2.0], [64, 0]),         # N = 0
+    ]
+    for args in bad_instances:
+        assert call(*args) == tmg.TMG_EINVAL, args
+    assert call(*ok, omega=2.5) == tmg.TMG_EINVAL
+    assert call(*ok, gamma=2) == tmg.TMG_EINVAL              # batches run V-cycles
+    assert call(*ok, schedule=3) == tmg.TMG_EINVAL
+    assert call(*ok, nu1=0, nu2=0) == tmg.TMG_EINVAL
+    assert call([], [], [], []) == tmg.TMG_EINVAL             # no instances
