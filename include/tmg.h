@@ -185,6 +185,21 @@ tmg_status tmg_residual(tmg_plan *plan, const double *f, double u0, const double
  */
 tmg_status tmg_stats(const tmg_plan *plan, int *cycles, double *rel_res, double *hist, int hist_len);
 
+/*
+ * The hierarchy tmg_setup builds for these arguments, computed on the host
+ * without touching the GPU (the same code tmg_setup runs): the number of
+ * levels (coarsening while a level has an even number of intervals, more
+ * than opts->n_min of them, and the level cap allows, Section 3's nested
+ * meshes); the first level handed to the single-CTA coarse solver; its
+ * number of intervals; and *scan_coarsest = 1 when no level fits that solver
+ * (or p_t = 10) and the coarsest level is solved by the grid-wide scan
+ * instead.  Output pointers are host pointers and may be NULL.  Same
+ * argument checks and status codes as tmg_setup.
+ */
+tmg_status tmg_plan_shape(int p_t, double tau, double lambda, int64_t N, int levels, double omega,
+                          const tmg_opts *opts, int *num_levels, int *tail_level, int64_t *tail_intervals,
+                          int *scan_coarsest);
+
 /* Level count and the first level handled by the on-chip coarse solver. */
 tmg_status tmg_plan_info(const tmg_plan *plan, int *num_levels, int *tail_level, int64_t *tail_intervals,
                          double *omega_per_level, int omega_len);

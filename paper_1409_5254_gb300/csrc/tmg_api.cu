@@ -51,6 +51,60 @@ const int64_t kTailNmax = 8192;
 // on-chip solver from level 1 and take the largest one.
 const int64_t kTailDefaultV = 64;
 
+// Argument checks shared by tmg_setup and tmg_plan_shape; fixes the options
+// a degree implies (p_t = 10 recomputes the mixed form's level-0 residual).
+tmg_status check_setup(int p_t, double tau, double lambda, int64_t N, double omega, tmg_opts* o) {
+    if (p_t < 0 || p_t > kMaxDegree || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) ||
+        N < 1 || !(omega < 2.0) || !isfinite(omega) || o->nu1 < 0 || o->nu1 > 8 || o->nu2 < 0 || o->nu2 > 8 ||
+        o->nu1 + o->nu2 < 1 || o->gamma < 1 || o->gamma > 2 || (o->precision != TMG_FP64 && o->precision != TMG_MIXED) ||
+        o->n_min < 1 || o->max_cycles < 0 || o->max_cycles >= tmg::kHist || !(o->tol >= 0.0))
+        return TMG_EINVAL;
+    // p_t <= 5, and p_t = 10 (forward solves; in the mixed form the level-0
+    // residual is recomputed from u in every cycle: no updated float pair)
+    const bool wide = p_t + 1 > tmg::kMaxD;
+    if (wide && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
+    if (wide) o->update_residual = 0;
+    return TMG_OK;
+}
+
+// Hierarchy of a plan (host arithmetic only): the number of levels, and the
+// first level handed to the on-chip coarse solver -- the largest that fits --
+// or, when none fits or the blocks are wider than that solver takes, the
+// coarsest level solved by the grid-wide scan.
+struct Shape {
+    int nlev;
+    int lt;
+    bool scan;
+    size_t tail_smem;
+};
+
+Shape plan_shape(const tmg_ops* ops, int d, int64_t N, int levels, const tmg_opts& o) {
+    Shape sh{count_levels(N, o.n_min, levels), -1, false, 0};
+    const bool wide = d > tmg::kMaxD;
+    for (int l = 0; !wide && l < sh.nlev; ++l) {
+        const int64_t Nl = N >> l;
+        const size_t b = ops->tail_bytes(Nl, sh.nlev - l);
+        const int64_t cap = o.tail_cap > 0 ? (o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax)
+                                           : (o.gamma == 2 ? kTailNmax : kTailDefaultV);
+        if ((Nl <= cap || l == sh.nlev - 1) && Nl <= kTailNmax && b <= kTailSmemMax &&
+            sh.nlev - l <= tmg::kTailLevels) {
+            sh.lt = l;
+            sh.tail_smem = b;
+            break;
+        }
+    }
+    if (sh.lt < 0) {
+        sh.lt = sh.nlev - 1;
+        sh.scan = true;
+        sh.tail_smem = 0;
+    }
+    return sh;
+}
+
+const tmg_ops* forward_ops(const tmg_opts& o, int d) {
+    return o.precision == TMG_MIXED ? tmg_ops_f32(d, 0) : tmg_ops_f64(d, 0);
+}
+
 tmg_status build_graph(tmg_plan* P, int dir) {
     cudaGraph_t g = nullptr;
     TMG_CUDA(cudaGraphCreate(&g, 0));
@@ -204,16 +258,9 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     tmg_opts o;
     tmg_opts_default(&o);
     if (opts) o = *opts;
-    if (p_t < 0 || p_t > kMaxDegree || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) || N < 1 ||
-        !(omega < 2.0) || !isfinite(omega) || o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 ||
-        o.gamma < 1 || o.gamma > 2 || (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 ||
-        o.max_cycles < 0 || o.max_cycles >= tmg::kHist || !(o.tol >= 0.0))
-        return TMG_EINVAL;
-    // p_t <= 5, and p_t = 10 (forward solves; in the mixed form the level-0
-    // residual is recomputed from u in every cycle: no updated float pair)
-    const bool wide = p_t + 1 > tmg::kMaxD;
-    if (wide && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
-    if (wide) o.update_residual = 0;
+    const tmg_status cs = check_setup(p_t, tau, lambda, N, omega, &o);
+    if (cs != TMG_OK) return cs;
+    const bool wide = p_t + 1 > tmg::kMaxD;   // no adjoint kernels
 
     tmg_plan* P = new (std::nothrow) tmg_plan();
     if (!P) return TMG_ENOMEM;
@@ -236,7 +283,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         }
         P->own_stream = true;
     }
-    P->ops = o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 0) : tmg_ops_f64(P->d, 0);
+    P->ops = forward_ops(o, P->d);
     P->ops_adj = wide ? nullptr : o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 1) : tmg_ops_f64(P->d, 1);
 
     int dev = 0;
@@ -249,7 +296,8 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     P->max_blocks = P->nsm * 8;
 
     // hierarchy and FP64 constants
-    P->nlev = count_levels(N, o.n_min, levels);
+    const Shape sh = plan_shape(P->ops, P->d, N, levels, o);
+    P->nlev = sh.nlev;
     P->lev.resize(P->nlev);
     for (int l = 0; l < P->nlev; ++l) {
         P->lev[l].N = N >> l;
@@ -259,26 +307,10 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     P->lev_adj.resize(P->nlev);
     for (int l = 0; l < P->nlev; ++l) level_setup_adjoint(P->d, P->lev[l], &P->lev_adj[l]);
 
-    // first level handled on chip: the largest that fits (no on-chip solver
-    // for the wide blocks)
-    P->lt = -1;
-    for (int l = 0; !wide && l < P->nlev; ++l) {
-        const size_t b = P->ops->tail_bytes(P->lev[l].N, P->nlev - l);
-        const int64_t cap = o.tail_cap > 0 ? (o.tail_cap < kTailNmax ? o.tail_cap : kTailNmax)
-                                           : (o.gamma == 2 ? kTailNmax : kTailDefaultV);
-        if ((P->lev[l].N <= cap || l == P->nlev - 1) && P->lev[l].N <= kTailNmax && b <= kTailSmemMax &&
-            P->nlev - l <= tmg::kTailLevels) {
-            P->lt = l;
-            P->tail_smem = b;
-            break;
-        }
-    }
-    if (P->lt < 0) {
-        // the coarsest level does not fit on one chip: solve it with the grid-wide scan
-        P->lt = P->nlev - 1;
-        P->scan_coarsest = true;
-        P->tail_smem = 0;
-    }
+    // first level handled on chip, or the coarsest level by the grid-wide scan
+    P->lt = sh.lt;
+    P->scan_coarsest = sh.scan;
+    P->tail_smem = sh.tail_smem;
 
     // workspace: level vectors in the cycle precision, level-0 residual,
     // tail constants, block partials, device state
@@ -439,6 +471,22 @@ tmg_status tmg_stats(const tmg_plan* P, int* cycles, double* rel_res, double* hi
     if (rel_res) *rel_res = P->last_rel;
     if (hist)
         for (int i = 0; i < hist_len; ++i) hist[i] = i < (int)P->last_hist.size() ? P->last_hist[i] : NAN;
+    return TMG_OK;
+}
+
+tmg_status tmg_plan_shape(int p_t, double tau, double lambda, int64_t N, int levels, double omega,
+                          const tmg_opts* opts, int* num_levels, int* tail_level, int64_t* tail_intervals,
+                          int* scan_coarsest) {
+    tmg_opts o;
+    tmg_opts_default(&o);
+    if (opts) o = *opts;
+    const tmg_status cs = check_setup(p_t, tau, lambda, N, omega, &o);
+    if (cs != TMG_OK) return cs;
+    const Shape sh = plan_shape(forward_ops(o, p_t + 1), p_t + 1, N, levels, o);
+    if (num_levels) *num_levels = sh.nlev;
+    if (tail_level) *tail_level = sh.lt;
+    if (tail_intervals) *tail_intervals = N >> sh.lt;
+    if (scan_coarsest) *scan_coarsest = sh.scan ? 1 : 0;
     return TMG_OK;
 }
 

@@ -42,7 +42,7 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
-           "tmg_stats", "tmg_plan_info", "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
+           "tmg_stats", "tmg_plan_shape", "tmg_plan_info", "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
            "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched"]
 
@@ -70,6 +70,10 @@ def _lib():
         L.tmg_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.tmg_residual.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
         L.tmg_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, ctypes.c_int]
+        L.tmg_plan_shape.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_double, ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int)]
         L.tmg_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int]
         L.tmg_inspect.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]
@@ -98,7 +102,7 @@ def _lib():
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
         for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual", "tmg_stats",
-                     "tmg_plan_info", "tmg_plan_launches", "tmg_inspect", "tmg_profile_cycle"):
+                     "tmg_plan_shape", "tmg_plan_info", "tmg_plan_launches", "tmg_inspect", "tmg_profile_cycle"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -317,6 +321,17 @@ def _opts(**kw) -> _Opts:
             v = _PREC[v]
         setattr(o, k, int(v) if isinstance(v, bool) else v)
     return o
+
+
+def plan_shape(p: int, tau: float, lam: float, N: int, levels: int = 0, omega: float = 0.0, **opts) -> dict:
+    """The hierarchy tmg_setup would build (tmg_plan_shape; host only, no GPU).
+    Keyword options as tmg_opts fields (precision="fp64"/"mixed", n_min, gamma,
+    tail_cap, ...)."""
+    nl, lt, sc = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    nt = ctypes.c_int64(0)
+    _check(_lib().tmg_plan_shape(p, tau, lam, N, levels, omega, ctypes.byref(_opts(**opts)), ctypes.byref(nl),
+                                 ctypes.byref(lt), ctypes.byref(nt), ctypes.byref(sc)), "tmg_plan_shape")
+    return {"levels": nl.value, "tail_level": lt.value, "tail_intervals": nt.value, "scan_coarsest": bool(sc.value)}
 
 
 class Batch:

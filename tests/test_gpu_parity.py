@@ -553,3 +553,17 @@ def test_launch_count_per_cycle(dev):
         info = plan.info()
         assert info["levels"] == 15 and info["tail_level"] == 14
         assert plan.launches_per_cycle() == 16
+
+
+@pytest.mark.parametrize("p,N,kw", [
+    (1, 1 << 24, {"n_min": 1 << 17}), (1, 1 << 14, {}), (0, 4096, {"gamma": 2}),
+    (1, 1 << 14, {"gamma": 2, "tail_cap": 128}), (2, 1 << 16, {"n_min": 16384}), (1, 3 * 1024, {"n_min": 2}),
+    (10, 1 << 12, {"precision": "fp64"}), (10, 37, {})])
+def test_plan_shape_matches_the_plan_setup_builds(dev, p, N, kw):
+    """tmg_plan_shape (host only) reports the hierarchy tmg_setup builds."""
+    T = tmg()
+    s = T.plan_shape(p, 1e-3, 1.0, N, **kw)
+    with T.Plan(p, 1e-3, 1.0, N, **kw) as plan:
+        info = plan.info()
+    assert (s["levels"], s["tail_level"], s["tail_intervals"]) == (info["levels"], info["tail_level"],
+                                                                    info["tail_intervals"])
