@@ -429,11 +429,15 @@ def test_omega_star_is_minimax(al):
     assert max(lfa.s_hat(w_star, al, t) for t in th) == pytest.approx(best_val, abs=1e-12)
 
 
-@pytest.mark.parametrize("p,z", [(0, 0.05), (1, 1e-2), (1, 1.0), (2, 0.3), (3, 1e-2)])
+@pytest.mark.parametrize("p", [0, 1, 2, 3])
+@pytest.mark.parametrize("z", [1e-4, 1e-2, 0.3, 1.0, 3.0, 30.0])
 def test_measured_two_grid_factor_matches_lfa(p, z):
     """Protocol of Section 4.2: N_L = 1024, f = 0, random start in [0,1], two-grid
     cycles until 1e-140 reduction; the measured asymptotic ratio (geometric mean
-    of the second half of ||r^{k+1}|| / ||r^k||) agrees with rho(M_tau)."""
+    of the second half of ||r^{k+1}|| / ||r^k||) agrees with rho(M_tau), over
+    the degrees and steps of the paper's plots.  At p = 1, z = 3 (the zero of
+    alpha) two smoothing steps solve exactly: the LFA value is rounding
+    (~sqrt(eps), a defective eigenvalue) and the measured one is below it."""
     N = 1024
     u_init = inputs.random_guess(7, N, p + 1)
     _, hist = O.mg_solve(p, z, np.zeros((N, p + 1)), 0.0, max_levels=2, tol=1e-140 * 0 + 0.0,
@@ -443,7 +447,10 @@ def test_measured_two_grid_factor_matches_lfa(p, z):
     half = ratios[len(ratios) // 2:]
     geo = float(np.exp(np.mean(np.log(half))))
     rho = lfa.two_grid_factor(p, z, N_L=N)
-    assert geo == pytest.approx(rho, rel=0.05)
+    if rho < 1e-6:
+        assert geo <= 1e-6
+    else:
+        assert geo == pytest.approx(rho, rel=0.05)
     assert ratios.max() <= max(1.35 * rho, rho + 0.15)
 
 
