@@ -200,6 +200,27 @@ tmg_status tmg_plan_shape(int p_t, double tau, double lambda, int64_t N, int lev
                           const tmg_opts *opts, int *num_levels, int *tail_level, int64_t *tail_intervals,
                           int *scan_coarsest);
 
+/*
+ * The FP64 set-up arithmetic of one level at step z = lambda*tau_l, on the
+ * host (what tmg_setup uploads per level): A = K + z Mhat (Section 2, the
+ * local matrices in the shifted Legendre basis), its inverse, g = A^{-1} a,
+ * c = A^{-T} b (so that c^T f = b^T A^{-1} f), alpha = b^T A^{-1} a (Lemma
+ * chap4_theorem2), and the damping: omega_user if 0 < omega_user < 2, else
+ * omega* of Lemma chap4_lemma7.  A and Ainv are row-major (p_t+1)^2 host
+ * arrays, g and c (p_t+1); any output may be NULL.  p_t and z >= 0 as for
+ * tmg_setup (TMG_EINVAL / TMG_EUNSUPPORTED likewise).
+ */
+tmg_status tmg_level_constants(int p_t, double z, double omega_user, double *A, double *Ainv, double *g,
+                               double *c, double *alpha, double *omega);
+
+/*
+ * The prolongation matrices P1 = R1^T and P2 = R2^T of Section 4.2 (eqs.
+ * chap4_restrictionTime / chap4_prolongationTime): column k holds the fine
+ * Legendre coefficients of coarse basis function k on the first (second)
+ * half of the coarse interval.  Row-major (p_t+1)^2 host arrays; host only.
+ */
+tmg_status tmg_transfer_matrices(int p_t, double *P1, double *P2);
+
 /* Level count and the first level handled by the on-chip coarse solver. */
 tmg_status tmg_plan_info(const tmg_plan *plan, int *num_levels, int *tail_level, int64_t *tail_intervals,
                          double *omega_per_level, int omega_len);

@@ -490,6 +490,34 @@ tmg_status tmg_plan_shape(int p_t, double tau, double lambda, int64_t N, int lev
     return TMG_OK;
 }
 
+tmg_status tmg_level_constants(int p_t, double z, double omega_user, double* A, double* Ainv, double* g, double* c,
+                               double* alpha, double* omega) {
+    if (p_t < 0 || p_t > kMaxDegree || !(z >= 0.0) || !isfinite(z) || !(omega_user < 2.0) || !isfinite(omega_user))
+        return TMG_EINVAL;
+    if (p_t + 1 > tmg::kMaxD && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
+    const int d = p_t + 1;
+    tmg_level_host L;
+    level_setup(d, z, omega_user, &L);
+    for (int i = 0; i < d * d; ++i) {
+        if (A) A[i] = L.A[i];
+        if (Ainv) Ainv[i] = L.Ainv[i];
+    }
+    for (int k = 0; k < d; ++k) {
+        if (g) g[k] = L.g[k];
+        if (c) c[k] = L.c[k];
+    }
+    if (alpha) *alpha = L.alpha;
+    if (omega) *omega = L.omega;
+    return TMG_OK;
+}
+
+tmg_status tmg_transfer_matrices(int p_t, double* P1, double* P2) {
+    if (p_t < 0 || p_t > kMaxDegree || !P1 || !P2) return TMG_EINVAL;
+    if (p_t + 1 > tmg::kMaxD && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
+    transfer_setup(p_t + 1, P1, P2);
+    return TMG_OK;
+}
+
 tmg_status tmg_plan_info(const tmg_plan* P, int* num_levels, int* tail_level, int64_t* tail_intervals,
                          double* omega_per_level, int omega_len) {
     if (!P) return TMG_EINVAL;

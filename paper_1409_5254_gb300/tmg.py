@@ -42,7 +42,8 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
-           "tmg_stats", "tmg_plan_shape", "tmg_plan_info", "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
+           "tmg_stats", "tmg_plan_shape", "tmg_level_constants", "tmg_transfer_matrices", "tmg_plan_info",
+           "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
            "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched"]
 
@@ -74,6 +75,9 @@ def _lib():
                                      ctypes.c_double, ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int)]
+        L.tmg_level_constants.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp,
+                                          _dp]
+        L.tmg_transfer_matrices.argtypes = [ctypes.c_int, _dp, _dp]
         L.tmg_plan_info.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64), _dp, ctypes.c_int]
         L.tmg_inspect.argtypes = [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]
@@ -102,7 +106,8 @@ def _lib():
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
         for name in ("tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual", "tmg_stats",
-                     "tmg_plan_shape", "tmg_plan_info", "tmg_plan_launches", "tmg_inspect", "tmg_profile_cycle"):
+                     "tmg_plan_shape", "tmg_level_constants", "tmg_transfer_matrices", "tmg_plan_info",
+                     "tmg_plan_launches", "tmg_inspect", "tmg_profile_cycle"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -332,6 +337,28 @@ def plan_shape(p: int, tau: float, lam: float, N: int, levels: int = 0, omega: f
     _check(_lib().tmg_plan_shape(p, tau, lam, N, levels, omega, ctypes.byref(_opts(**opts)), ctypes.byref(nl),
                                  ctypes.byref(lt), ctypes.byref(nt), ctypes.byref(sc)), "tmg_plan_shape")
     return {"levels": nl.value, "tail_level": lt.value, "tail_intervals": nt.value, "scan_coarsest": bool(sc.value)}
+
+
+def level_constants(p: int, z: float, omega: float = 0.0) -> dict:
+    """The library's host set-up of one level (tmg_level_constants): A, A^{-1},
+    g, c, alpha and the damping, as numpy arrays / floats."""
+    d = p + 1
+    A, Ai = np.zeros((d, d)), np.zeros((d, d))
+    g, c = np.zeros(d), np.zeros(d)
+    al, om = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(_lib().tmg_level_constants(p, z, omega, A.ctypes.data_as(_dp), Ai.ctypes.data_as(_dp),
+                                      g.ctypes.data_as(_dp), c.ctypes.data_as(_dp), ctypes.byref(al),
+                                      ctypes.byref(om)), "tmg_level_constants")
+    return {"A": A, "Ainv": Ai, "g": g, "c": c, "alpha": al.value, "omega": om.value}
+
+
+def transfer_matrices(p: int):
+    """The library's prolongation matrices (P1, P2) (tmg_transfer_matrices)."""
+    d = p + 1
+    P1, P2 = np.zeros((d, d)), np.zeros((d, d))
+    _check(_lib().tmg_transfer_matrices(p, P1.ctypes.data_as(_dp), P2.ctypes.data_as(_dp)),
+           "tmg_transfer_matrices")
+    return P1, P2
 
 
 class Batch:
