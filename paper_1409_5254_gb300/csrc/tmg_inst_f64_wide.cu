@@ -1,8 +1,8 @@
 // Explicit instantiation of the plain FP64 forward solver for p_t = 10
 // (11 x 11 blocks).  Only the per-level kernels and the grid-wide scan of the
-// coarsest level are instantiated: the two-level kernels and the on-chip
-// coarse solver keep 2 x 4 interval blocks per lane and would spill.  The
-// adjoint is not built at this degree.
+// coarsest level are instantiated: the two-level kernels (four interval
+// blocks per lane) and the on-chip coarse solver (a stack of levels per CTA)
+// would spill.  The adjoint is not built at this degree.
 #include "tmg_impl.cuh"
 
 const tmg_ops* tmg_ops_f64_wide(int d, int dir) {
