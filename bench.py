@@ -59,9 +59,9 @@ WORKLOAD = ("long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixe
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_updown0
-# launch on the default workload, from one ncu capture (profiles/
-# k_updown0_long_horizon_p1_mixed.md); valid only for the kernel source it was
-# taken with (first 16 hex digits of the SHA-256 of tmg_kernels.cuh), else null.
+# launch on the default workload, from one ncu capture; valid only for the
+# kernel source it was taken with (first 16 hex digits of the SHA-256 of
+# tmg_kernels.cuh), else null.
 BATCH_STRIDE = 1          # every s-th heat mode (profiling of smaller cases only)
 UPDOWN0_TRAFFIC = {"bytes_per_launch": 1.0180e9, "kernels_sha256": "34384092ae2de274"}
 

@@ -261,9 +261,9 @@ tmg_status tmg_inspect(const tmg_plan *plan, int which, int level, void *host_ds
  * Residual r = F - L u (FP64, written to r) and its norm ||r||_2 (written to
  * the single device double *norm), with no plan and no device allocation --
  * for callers that may not allocate device memory where they need this check
- * (code inside another library's stream capture, real-time loops that cannot
- * take the device synchronisation an allocation may cause, applications whose
- * device memory all belongs to their own pool).  The paper has no counterpart;
+ * (real-time loops that cannot take the device synchronisation an allocation
+ * may cause, applications whose device memory all belongs to their own
+ * pool).  The paper has no counterpart;
  * it is the level-0 residual kernel with its block partial sums kept in a
  * fixed file-scope device array instead of a plan workspace.
  *

@@ -208,8 +208,11 @@ cudaError_t launch_cta(tmg_batch* B, tmg_batch_group* G, const double* F, double
         X.P1[i] = (T)(DIR == 0 ? P1[i] : P2[i]);
         X.P2[i] = (T)(DIR == 0 ? P2[i] : P1[i]);
     }
-    static const cudaError_t attr = cudaFuncSetAttribute(kb_cta_solve<DIR, T, D>,
-                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCtaSmemMax);
+    static PerDevice<cudaError_t> attr_c;
+    const cudaError_t attr = attr_c.get([&] {
+        return cudaFuncSetAttribute(kb_cta_solve<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kCtaSmemMax);
+    });
     if (attr != cudaSuccess) return attr;
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb_cta_solve<DIR, T, D>, kTailNT, G->cta_smem);

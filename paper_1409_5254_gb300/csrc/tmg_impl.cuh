@@ -152,8 +152,10 @@ struct Impl {
         const ScanK<S, D> K = scan_consts<S>(L(P)[l]);
         const int grid = (int)(nt < P->max_blocks ? nt : P->max_blocks);
         // (a failed opt-in makes the launches below fail, which the caller reports)
-        static const cudaError_t attr_t = allow_smem(k_scan_tiles<S, D, TIO>, scan_smem_bytes<D, TIO>());
-        static const cudaError_t attr_a = allow_smem(k_scan_apply<S, D, TIO, TIO>, scan_smem_bytes<D, TIO>());
+        static PerDevice<cudaError_t> attr_t_c;
+        const cudaError_t attr_t = attr_t_c.get([&] { return allow_smem(k_scan_tiles<S, D, TIO>, scan_smem_bytes<D, TIO>()); });
+        static PerDevice<cudaError_t> attr_a_c;
+        const cudaError_t attr_a = attr_a_c.get([&] { return allow_smem(k_scan_apply<S, D, TIO, TIO>, scan_smem_bytes<D, TIO>()); });
         (void)attr_t;
         (void)attr_a;
         launch(P, k_scan_tiles<S, D, TIO>, grid, kScanNT, scan_smem_bytes<D, TIO>(), f, N, K, aggA, aggB, thrA, thrB,
@@ -178,7 +180,8 @@ struct Impl {
     template <typename... Args>
     static void launch_tail(tmg_plan* P, Args... args) {
         if constexpr (D <= kMaxD) {
-            static const cudaError_t attr = allow_smem(k_tail<DIR, T, D>, kTailSmemMax);
+            static PerDevice<cudaError_t> attr_c;
+        const cudaError_t attr = attr_c.get([&] { return allow_smem(k_tail<DIR, T, D>, kTailSmemMax); });
             (void)attr;   // a failed opt-in makes the launch fail, which the caller reports
             launch(P, k_tail<DIR, T, D>, 1, kTailNT, P->tail_smem, args...);
         }
@@ -209,12 +212,14 @@ struct Impl {
         const CoarseTail<T, D> ct_none{nullptr, nullptr, nullptr, 0, nullptr};
         if (nz) {
             const int H = halo_lanes(nu1 + 1);
-            static const int occ = resident_per_sm(k_down_nz<DIR, T, D>, 0);
+            static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_down_nz<DIR, T, D>, 0); });
             launch(P, k_down_nz<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                    (const T*)ua, static_cast<T*>(P->fl[l + 1]), nch, K, X, nu1, H, (const DevState*)P->st);
         } else {
             const int H = halo_lanes(sweeps_down(nu1));
-            static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
+            static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_down<DIR, T, D>, 0); });
             launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                    static_cast<T*>(P->fl[l + 1]), nch, K, X, nu1, H, (const DevState*)P->st, ct_none);
         }
@@ -223,12 +228,14 @@ struct Impl {
         const T* uc = static_cast<const T*>(P->ul2[l + 1]);
         if (nz) {
             const int H = halo_lanes(nu1 + nu2);
-            static const int occ = resident_per_sm(k_up_nz<DIR, T, D>, 0);
+            static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_up_nz<DIR, T, D>, 0); });
             launch(P, k_up_nz<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                    (const T*)ua, uc, ub, nch, K, X, nu1, nu2, H, (const DevState*)P->st);
         } else {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
-            static const int occ = resident_per_sm(k_up<DIR, T, D>, 0);
+            static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_up<DIR, T, D>, 0); });
             launch(P, k_up<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]), uc, ua,
                    nch, K, X, nu1, nu2, H, (const DevState*)P->st);
         }
@@ -283,9 +290,11 @@ struct Impl {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark(kCatDown0);
-            static const cudaError_t attr = allow_smem(k_down0<DIR, T, D>, k_down0_smem_bytes<D>());
+            static PerDevice<cudaError_t> attr_c;
+        const cudaError_t attr = attr_c.get([&] { return allow_smem(k_down0<DIR, T, D>, k_down0_smem_bytes<D>()); });
             if (attr != cudaSuccess) return attr;
-            static const int occ = resident_per_sm(k_down0<DIR, T, D>, k_down0_smem_bytes<D>());
+            static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_down0<DIR, T, D>, k_down0_smem_bytes<D>()); });
             launch(P, k_down0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, k_down0_smem_bytes<D>(), rT, rl,
                    static_cast<T*>(P->fl[1]), nch, R, level_consts<T, D>(L(P)[0]), X, nu1, H, P->partials, P->st);
         }
@@ -325,7 +334,8 @@ struct Impl {
                     const int g0 = sweeps_down(nu1);
                     const int H = halo_lanes(halo_lanes(g0) + sweeps_down(nu1));
                     const int64_t nq = P->lev[l].N / 4;
-                    static const int occ = resident_per_sm(k_down2<DIR, T, D>, 0);
+                    static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_down2<DIR, T, D>, 0); });
                     launch(P, k_down2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                            static_cast<T*>(P->fl[l + 2]), nq, level_consts<T, D>(L(P)[l]),
                            level_consts<T, D>(L(P)[l + 1]), X, nu1, H, (const DevState*)P->st, ct);
@@ -334,7 +344,8 @@ struct Impl {
                 const int l = grp[g];
                 const int H = halo_lanes(sweeps_down(nu1));
                 const int64_t nch = P->lev[l].N / 2;
-                static const int occ = resident_per_sm(k_down<DIR, T, D>, 0);
+                static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_down<DIR, T, D>, 0); });
                 launch(P, k_down<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                        static_cast<T*>(P->fl[l + 1]), nch, level_consts<T, D>(L(P)[l]), X, nu1, H,
                        (const DevState*)P->st, ct);
@@ -359,7 +370,8 @@ struct Impl {
                     const int g1 = halo_lanes(sweeps_down(nu1)) + sweeps_up(nu1, nu2);
                     const int H = (2 * g1 + nu2 + 3) / 4;
                     const int64_t nq = P->lev[l].N / 4;
-                    static const int occ = resident_per_sm(k_up2<DIR, T, D>, 0);
+                    static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_up2<DIR, T, D>, 0); });
                     launch(P, k_up2<DIR, T, D>, grid_for(P, nq, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                            static_cast<const T*>(P->ul[l + 2]), static_cast<T*>(P->ul[l]), nq,
                            level_consts<T, D>(L(P)[l]), level_consts<T, D>(L(P)[l + 1]), X, nu1, nu2, H,
@@ -369,7 +381,8 @@ struct Impl {
                 const int l = grp[g];
                 const int H = halo_lanes(sweeps_up(nu1, nu2));
                 const int64_t nch = P->lev[l].N / 2;
-                static const int occ = resident_per_sm(k_up<DIR, T, D>, 0);
+                static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_up<DIR, T, D>, 0); });
                 launch(P, k_up<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, static_cast<const T*>(P->fl[l]),
                        static_cast<const T*>(P->ul[l + 1]), static_cast<T*>(P->ul[l]), nch,
                        level_consts<T, D>(L(P)[l]), X, nu1, nu2, H, (const DevState*)P->st);
@@ -380,7 +393,8 @@ struct Impl {
                 const int H = halo_lanes(sweeps_up(nu1, nu2) + 1 + sweeps_down(nu1));
                 const int64_t nch = P->N / 2;
                 mark(kCatUp0);
-                static const int occ = resident_per_sm(k_updown0<DIR, D>, 0);
+                static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_updown0<DIR, D>, 0); });
                 launch(P, k_updown0<DIR, D>, grid_for(P, nch, H, occ), kNT, 0, rT, rl, (const float*)uc1,
                        static_cast<float*>(P->fl[1]), nch, R, level_consts<float, D>(L(P)[0]), X, nu1, nu2, H,
                        P->partials, P->st);
@@ -393,7 +407,8 @@ struct Impl {
             const int H = halo_lanes(sweeps_up(nu1, nu2));
             const int64_t nch = P->N / 2;
             mark(kCatUp0);
-            static const int occ = resident_per_sm(k_up0<DIR, T, D>, 0);
+            static PerDevice<int> occ_c;
+            const int occ = occ_c.get([&] { return resident_per_sm(k_up0<DIR, T, D>, 0); });
             launch(P, k_up0<DIR, T, D>, grid_for(P, nch, H, occ), kNT, 0, (const T*)rT, uc1,
                    nch, level_consts<T, D>(L(P)[0]), X, nu1, nu2, H, (const DevState*)P->st);
         }

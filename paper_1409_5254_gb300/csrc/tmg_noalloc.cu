@@ -2,13 +2,11 @@
 // allocation.
 //
 // Who needs this: code that may not call cudaMalloc at the point where it
-// wants to check a solution -- for example code running while another
-// library holds the stream in graph capture (a cudaMalloc there would break
-// the capture or synchronise the device), real-time loops that cannot afford
-// the implicit device synchronisation an allocation may cause, and
-// applications that hand all device memory to their own pool at start-up.
-// tmg_setup allocates a workspace, so those callers cannot build a plan at
-// that point; this entry point needs no plan and no allocation.
+// wants to check a solution -- real-time loops that cannot afford the
+// implicit device synchronisation an allocation may cause, and applications
+// that hand all device memory to their own pool at start-up.  tmg_setup
+// allocates a workspace, so those callers cannot build a plan at that point;
+// this entry point needs no plan and no allocation.
 //
 // The per-block partial sums of ||r||^2 and the completion ticket live in one
 // file-scope __device__ array of fixed size (kScratchBlocks partials, about

@@ -4,11 +4,41 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "../../include/tmg.h"
 #include "tmg_kernels.cuh"
 #include "tmg_scan.cuh"
+
+namespace tmg {
+
+// A launch property computed once per device -- the device current at the
+// call.  The shared-memory opt-in of a kernel is an attribute of the device it
+// was set on, and a process may build plans on several GPUs, so neither the
+// opt-in nor the occupancy it implies is cached process-wide.
+constexpr int kMaxDevices = 64;
+
+template <typename V>
+struct PerDevice {
+    std::mutex m;
+    bool have[kMaxDevices] = {};
+    V val[kMaxDevices] = {};
+
+    template <typename F>
+    V get(F compute) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute();
+        std::lock_guard<std::mutex> lock(m);
+        if (!have[dev]) {
+            val[dev] = compute();
+            have[dev] = true;
+        }
+        return val[dev];
+    }
+};
+
+}  // namespace tmg
 
 // Shared-memory ceiling of the single-CTA coarse solver.
 constexpr size_t kTailSmemMax = 200 * 1024;

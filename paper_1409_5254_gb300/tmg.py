@@ -306,13 +306,19 @@ def residual_norm_noalloc(p: int, tau: float, lam: float, f, u0: float, u, r, no
     """r = F - L u and ||r||_2 (into the one-element float64 CUDA tensor ``norm``)
     through tmg_residual_norm_noalloc: no plan and no device allocation, for
     callers that may not allocate device memory at that point.  Asynchronous on
-    ``stream`` (default: the legacy default stream)."""
+    ``stream``; by default torch's current stream on u's device.  A caller-given
+    stream first waits for torch's current stream, which may still be writing
+    f or u."""
     d = p + 1
     N = f.numel() // d
     import torch
     if not (isinstance(norm, torch.Tensor) and norm.is_cuda and norm.dtype == torch.float64 and norm.numel() == 1):
         raise TypeError("norm must be a one-element float64 CUDA tensor")
-    sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(u.device)
+    else:
+        _order_after_current(stream, u)
+    sp = ctypes.c_void_p(stream.cuda_stream)
     _check(_lib().tmg_residual_norm_noalloc(p, tau, lam, N, _dev_ptr(f, d, N, "f"), float(u0), _dev_ptr(u, d, N, "u"),
                                             _dev_ptr(r, d, N, "r"), ctypes.c_void_p(norm.data_ptr()), sp),
            "tmg_residual_norm_noalloc")
