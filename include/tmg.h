@@ -90,6 +90,12 @@ typedef struct {
                            of the group (graph loop); TMG_SCHED_CTA: one CTA per instance with
                            the whole hierarchy in shared memory and all cycles in one launch
                            (groups too large for one CTA fall back to the grid form) */
+    int check_fp64;     /* 1: after each solve, also solve the system exactly in FP64 (the
+                           parallel scan of tmg_solve_direct; for batches one warp per
+                           instance) and record max|u - u_exact| / max|u_exact|, reported by
+                           tmg_stats / tmg_stats_batched as err_vs_fp64 (default 0: not
+                           computed, reported as NAN).  Costs one exact solve per solve and,
+                           for a single problem, an N (p_t+1) double buffer owned by the plan */
 } tmg_opts;
 
 enum { TMG_SCHED_AUTO = 0, TMG_SCHED_GRID = 1, TMG_SCHED_CTA = 2 };
@@ -175,15 +181,30 @@ tmg_status tmg_adjoint(tmg_plan *plan, const double *g, const double *u, double 
  */
 tmg_status tmg_cycle(tmg_plan *plan, const double *f, double u0, double *u);
 
+/*
+ * Error of a result u against the exact FP64 solution of the same system:
+ * *err = max|u - u_exact| / max|u_exact| (host double), with u_exact the
+ * FP64 parallel-scan solve of tmg_solve_direct (block forward substitution of
+ * eq. chap4_generalLinearSystemODE written as a scan), held in an
+ * N (p_t+1) double buffer the plan allocates on first use.  tmg_stats reports
+ * the value afterwards as err_vs_fp64.  f, u device arrays as for tmg_solve;
+ * synchronises the stream.
+ */
+tmg_status tmg_error_vs_fp64(tmg_plan *plan, const double *f, double u0, const double *u, double *err);
+
 /* r = F - L u (FP64, device arrays [N][p_t+1]); F is f with a*u0 folded in. */
 tmg_status tmg_residual(tmg_plan *plan, const double *f, double u0, const double *u, double *r);
 
 /*
  * Statistics of the last tmg_solve: number of cycles applied, final relative
- * residual, and up to hist_len entries of the residual history
+ * residual, the error against the exact FP64 solution (*err_vs_fp64 =
+ * max|u - u_exact| / max|u_exact|, u_exact the FP64 parallel-scan solve of the
+ * same system, as tmg_solve_direct; NAN unless the plan was built with
+ * opts->check_fp64), and up to hist_len entries of the residual history
  * (hist[k] = ||F - L u_k|| / ||F||, k = 0..cycles).  Any pointer may be NULL.
  */
-tmg_status tmg_stats(const tmg_plan *plan, int *cycles, double *rel_res, double *hist, int hist_len);
+tmg_status tmg_stats(const tmg_plan *plan, int *cycles, double *rel_res, double *err_vs_fp64, double *hist,
+                     int hist_len);
 
 /*
  * The hierarchy tmg_setup builds for these arguments, computed on the host
@@ -320,9 +341,24 @@ tmg_status tmg_solve_batched(tmg_batch *batch, const double *f, const double *u0
 tmg_status tmg_adjoint_batched(tmg_batch *batch, const double *g, const double *u, double *dJdf, double *dJdu0,
                                double *dJdlambda);
 
-/* Per-instance cycles and final relative residuals of the last batched solve
- * (host arrays of length n_inst, may be NULL); *max_cycles_used = the most. */
-tmg_status tmg_stats_batched(const tmg_batch *batch, int *cycles, double *rel_res, int *max_cycles_used);
+/* Per-instance cycles, final relative residuals and errors against the exact
+ * FP64 solution (max|u_i - u_exact,i| / max|u_exact,i|, NAN unless the batch
+ * was built with opts->check_fp64) of the last batched solve (host arrays of
+ * length n_inst, may be NULL); *max_cycles_used = the most. */
+tmg_status tmg_stats_batched(const tmg_batch *batch, int *cycles, double *rel_res, double *err_vs_fp64,
+                             int *max_cycles_used);
+
+/*
+ * Errors of the batched results u against every instance's exact FP64
+ * solution, err_host[i] = max|u_i - u_exact,i| / max|u_exact,i| (host array of
+ * n_inst): one warp per instance composes the affine maps of contiguous chunks
+ * of the recurrence e_n = alpha e_{n-1} + c^T F_n, scans them across the warp
+ * and replays each chunk (exact block forward substitution, FP64).  f, u0, u
+ * device arrays as for tmg_solve_batched; tmg_stats_batched reports the values
+ * afterwards.  Synchronises the stream.
+ */
+tmg_status tmg_error_vs_fp64_batched(tmg_batch *batch, const double *f, const double *u0, const double *u,
+                                     double *err_host);
 
 /* Number of (p_t, padded length) groups and the padded number of values. */
 tmg_status tmg_batch_info(const tmg_batch *batch, int *n_groups, int64_t *padded_values);

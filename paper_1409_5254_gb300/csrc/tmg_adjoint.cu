@@ -1,4 +1,5 @@
-// Helpers of the adjoint solve: interval reversal and the gradient reductions.
+// Helpers of the adjoint solve (interval reversal, the gradient reductions)
+// and of the error check against the exact FP64 solve.
 //
 // For a loss J(u) of the solution of L u = F (F = f with a*u0 in the first
 // interval), mu = L^{-T} dJ/du gives dJ/df = mu, dJ/du0 = a^T mu_0 and
@@ -76,7 +77,43 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_grads(const double* __rest
     *ticket = 0u;
 }
 
+// max |u - v| and max |v| over n values into out[0], out[1] as the bit
+// patterns of non-negative doubles (their order as unsigned integers is the
+// order of the values, so atomicMax on the bits is a max of the values).  A
+// non-finite difference counts as infinite.
+__global__ void __launch_bounds__(kThreads) k_maxabs2(const double* __restrict__ u, const double* __restrict__ v,
+                                                      int64_t n, unsigned long long* __restrict__ out) {
+    double md = 0.0, mv = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        const double a = u[i], b = v[i];
+        const double dv = fabs(a - b);
+        md = (dv == dv && dv <= 1.0e308) ? fmax(md, dv) : INFINITY;
+        mv = fmax(mv, fabs(b));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, off));
+        mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(md));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(mv));
+    }
+}
+
 }  // namespace
+
+cudaError_t tmg_launch_maxabs2(const double* u, const double* v, int64_t n, unsigned long long* out2, int max_blocks,
+                               cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks < 1) blocks = 1;
+    k_maxabs2<<<(int)blocks, kThreads, 0, s>>>(u, v, n, out2);
+    return cudaGetLastError();
+}
 
 cudaError_t tmg_launch_reverse(const double* src, double* dst, int64_t N, int d, cudaStream_t s) {
     int64_t blocks = (N + kThreads - 1) / kThreads;

@@ -57,7 +57,8 @@ tmg_status check_setup(int p_t, double tau, double lambda, int64_t N, double ome
     if (p_t < 0 || p_t > kMaxDegree || !(tau > 0.0) || !isfinite(tau) || !(lambda >= 0.0) || !isfinite(lambda) ||
         N < 1 || !(omega < 2.0) || !isfinite(omega) || o->nu1 < 0 || o->nu1 > 8 || o->nu2 < 0 || o->nu2 > 8 ||
         o->nu1 + o->nu2 < 1 || o->gamma < 1 || o->gamma > 2 || (o->precision != TMG_FP64 && o->precision != TMG_MIXED) ||
-        o->n_min < 1 || o->max_cycles < 0 || o->max_cycles >= tmg::kHist || !(o->tol >= 0.0))
+        o->n_min < 1 || o->max_cycles < 0 || o->max_cycles >= tmg::kHist || !(o->tol >= 0.0) ||
+        o->check_fp64 < 0 || o->check_fp64 > 1)
         return TMG_EINVAL;
     // p_t <= 5, and p_t = 10 (forward solves; in the mixed form the level-0
     // residual is recomputed from u in every cycle: no updated float pair)
@@ -249,6 +250,7 @@ void tmg_opts_default(tmg_opts* o) {
     o->update_residual = 1;
     o->fuse_levels = -1;
     o->schedule = TMG_SCHED_AUTO;
+    o->check_fp64 = 0;
 }
 
 tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_t N, int levels, double omega,
@@ -271,6 +273,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     P->N = N;
     P->omega_user = omega;
     P->o = o;
+    P->last_err = NAN;
     P->s = static_cast<cudaStream_t>(stream);
     P->own_stream = false;
     if (P->s == nullptr) {
@@ -387,9 +390,41 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     return TMG_OK;
 }
 
+// Error of u against the exact FP64 solve of the same system (opts.check_fp64):
+// the FP64 parallel scan into the plan's buffer, then max|u - u_exact| and
+// max|u_exact| on the device.
+tmg_status error_vs_fp64(tmg_plan* P, const double* f, double u0, const double* u) {
+    const size_t nv = (size_t)P->N * P->d;
+    if (!P->ex_buf) {
+        cudaError_t e = cudaMalloc(&P->ex_buf, nv * sizeof(double));
+        if (e != cudaSuccess) {
+            P->ex_buf = nullptr;
+            g_last_cuda = (int)e;
+            return TMG_ENOMEM;
+        }
+    }
+    TMG_CUDA(tmg_ops_f64(P->d, 0)->enqueue_direct(P, f, u0, P->ex_buf));
+    unsigned long long* out2 = reinterpret_cast<unsigned long long*>(P->partials);
+    TMG_CUDA(tmg_launch_maxabs2(u, P->ex_buf, (int64_t)nv, out2, P->max_blocks, P->s));
+    unsigned long long h[2] = {0, 0};
+    TMG_CUDA(cudaMemcpyAsync(h, out2, sizeof(h), cudaMemcpyDeviceToHost, P->s));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    double md, mv;
+    memcpy(&md, &h[0], sizeof(double));
+    memcpy(&mv, &h[1], sizeof(double));
+    P->last_err = mv > 0.0 ? md / mv : md;
+    return TMG_OK;
+}
+
 tmg_status tmg_solve(tmg_plan* P, const double* f, double u0, double* u) {
     if (!P || !isfinite(u0)) return TMG_EINVAL;
-    return run_solve(P, f, u0, u);
+    P->last_err = NAN;
+    tmg_status s = run_solve(P, f, u0, u);
+    if ((s == TMG_OK || s == TMG_ENOTCONV) && P->o.check_fp64) {
+        const tmg_status se = error_vs_fp64(P, f, u0, u);
+        if (se != TMG_OK) return se;
+    }
+    return s;
 }
 
 tmg_status tmg_solve_host(tmg_plan* P, const double* f_host, double u0, double* u_host) {
@@ -405,8 +440,13 @@ tmg_status tmg_solve_host(tmg_plan* P, const double* f_host, double u0, double* 
     }
     TMG_CUDA(cudaMemcpyAsync(P->F_dev, f_host, bytes, cudaMemcpyHostToDevice, P->s));
     if (P->o.initial_guess) TMG_CUDA(cudaMemcpyAsync(P->u_dev, u_host, bytes, cudaMemcpyHostToDevice, P->s));
+    P->last_err = NAN;
     tmg_status s = run_solve(P, P->F_dev, u0, P->u_dev);
     if (s != TMG_OK && s != TMG_ENOTCONV) return s;
+    if (P->o.check_fp64) {
+        const tmg_status se = error_vs_fp64(P, P->F_dev, u0, P->u_dev);
+        if (se != TMG_OK) return se;
+    }
     TMG_CUDA(cudaMemcpyAsync(u_host, P->u_dev, bytes, cudaMemcpyDeviceToHost, P->s));
     TMG_CUDA(cudaStreamSynchronize(P->s));
     return s;
@@ -441,6 +481,14 @@ tmg_status tmg_adjoint(tmg_plan* P, const double* g, const double* u, double* dJ
     return s;
 }
 
+tmg_status tmg_error_vs_fp64(tmg_plan* P, const double* f, double u0, const double* u, double* err) {
+    if (!P || !err || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    const tmg_status s = error_vs_fp64(P, f, u0, u);
+    if (s != TMG_OK) return s;
+    *err = P->last_err;
+    return TMG_OK;
+}
+
 tmg_status tmg_solve_direct(tmg_plan* P, const double* f, double u0, double* u) {
     if (!P || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
     TMG_CUDA(tmg_ops_f64(P->d, 0)->enqueue_direct(P, f, u0, u));
@@ -465,10 +513,12 @@ tmg_status tmg_residual(tmg_plan* P, const double* f, double u0, const double* u
     return TMG_OK;
 }
 
-tmg_status tmg_stats(const tmg_plan* P, int* cycles, double* rel_res, double* hist, int hist_len) {
+tmg_status tmg_stats(const tmg_plan* P, int* cycles, double* rel_res, double* err_vs_fp64, double* hist,
+                     int hist_len) {
     if (!P) return TMG_EINVAL;
     if (cycles) *cycles = P->last_cycles;
     if (rel_res) *rel_res = P->last_rel;
+    if (err_vs_fp64) *err_vs_fp64 = P->last_err;
     if (hist)
         for (int i = 0; i < hist_len; ++i) hist[i] = i < (int)P->last_hist.size() ? P->last_hist[i] : NAN;
     return TMG_OK;
@@ -629,6 +679,7 @@ void tmg_destroy(tmg_plan* P) {
     if (P->ws) cudaFree(P->ws);
     if (P->st_host) cudaFreeHost(P->st_host);
     if (P->F_dev) cudaFree(P->F_dev);
+    if (P->ex_buf) cudaFree(P->ex_buf);
     if (P->u_dev) cudaFree(P->u_dev);
     if (P->own_stream) cudaStreamDestroy(P->s);
     delete P;

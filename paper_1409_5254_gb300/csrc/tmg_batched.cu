@@ -143,6 +143,88 @@ __global__ void kb_grads(const double* __restrict__ mu, const double* __restrict
     }
 }
 
+// Error of every instance's result against its exact FP64 solution, one warp
+// per instance.  Block forward substitution of the rank-one coupled system is
+// the scalar recurrence e_n = alpha e_{n-1} + c^T F_n (e_{-1} = u0, F the load
+// vector), with u_n = A^{-1} F_n + g e_{n-1}.  Each lane composes the affine
+// map of one contiguous chunk of intervals, the warp scans the chunk maps, and
+// each lane replays its chunk from its incoming e, comparing with u:
+// err = max|u - u_exact| / max|u_exact| (packed caller layout, instance j of
+// the group at value offset off[j]; K holds [A^{-1}, g, c, alpha] per instance).
+template <int D>
+__global__ void __launch_bounds__(kBNT) kb_exact_err(const double* __restrict__ F, const double* __restrict__ u,
+                                                     const double* __restrict__ u0, const int64_t* __restrict__ ids,
+                                                     const int64_t* __restrict__ off, const int64_t* __restrict__ Ni,
+                                                     const double* __restrict__ K, int64_t n,
+                                                     double* __restrict__ err) {
+    constexpr int KS = D * D + 2 * D + 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * kBNT) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; j < n; j += nw) {
+        const double* k = K + j * KS;
+        double Ai[D * D], g[D], c[D];
+#pragma unroll
+        for (int q = 0; q < D * D; ++q) Ai[q] = k[q];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+            g[q] = k[D * D + q];
+            c[q] = k[D * D + D + q];
+        }
+        const double al = k[D * D + 2 * D];
+        const int64_t N = Ni[j];
+        const double* Fi = F + off[j];
+        const double* ui = u + off[j];
+        const int64_t chunk = (N + 31) / 32;
+        const int64_t n0 = min(N, (int64_t)lane * chunk), n1 = min(N, n0 + chunk);
+        // chunk map: e_out = A e_in + Bv
+        double A = 1.0, Bv = 0.0;
+        for (int64_t m = n0; m < n1; ++m) {
+            double cf = 0.0;
+#pragma unroll
+            for (int q = 0; q < D; ++q) cf = fma(c[q], Fi[m * D + q], cf);
+            A *= al;
+            Bv = fma(al, Bv, cf);
+        }
+        // inclusive warp scan of the maps (composition in lane order)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double Ap = __shfl_up_sync(kFull, A, o), Bp = __shfl_up_sync(kFull, Bv, o);
+            if (lane >= o) {
+                Bv = fma(A, Bp, Bv);
+                A *= Ap;
+            }
+        }
+        const double e_start = u0[ids[j]];
+        const double e_incl = fma(A, e_start, Bv);
+        const double e_prev = __shfl_up_sync(kFull, e_incl, 1);
+        double e = lane == 0 ? e_start : e_prev;
+        double md = 0.0, mv = 0.0;
+        for (int64_t m = n0; m < n1; ++m) {
+            double f[D];
+#pragma unroll
+            for (int q = 0; q < D; ++q) f[q] = Fi[m * D + q];
+            double cf = 0.0;
+#pragma unroll
+            for (int q = 0; q < D; ++q) {
+                double x = g[q] * e;
+#pragma unroll
+                for (int l = 0; l < D; ++l) x = fma(Ai[q * D + l], f[l], x);
+                const double dv = fabs(ui[m * D + q] - x);
+                md = (dv == dv && dv <= 1.0e308) ? fmax(md, dv) : INFINITY;
+                mv = fmax(mv, fabs(x));
+                cf = fma(c[q], f[q], cf);
+            }
+            e = fma(al, e, cf);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            md = fmax(md, __shfl_xor_sync(kFull, md, o));
+            mv = fmax(mv, __shfl_xor_sync(kFull, mv, o));
+        }
+        if (lane == 0) err[ids[j]] = mv > 0.0 ? md / mv : md;
+    }
+}
+
 template <typename T, int DIR>
 cudaError_t enqueue_cycle_d(tmg_batch* B, tmg_batch_group* G) {
     switch (G->d) {
@@ -605,6 +687,60 @@ tmg_status drain(tmg_batch* B, tmg_status s) {
     return s;
 }
 
+// opts.check_fp64: the error of every instance of the last solve against its
+// exact FP64 solution (kb_exact_err per group on the caller's packed arrays),
+// on the batch stream after the groups have joined.
+tmg_status check_fp64(tmg_batch* B, const double* f, const double* u0, const double* u) {
+    if (!B->err_dev) {
+        cudaError_t e = cudaMalloc(&B->err_dev, sizeof(double) * B->n_inst);
+        if (e != cudaSuccess) {
+            B->err_dev = nullptr;
+            g_last_cuda_b = (int)e;
+            return TMG_ENOMEM;
+        }
+    }
+    for (tmg_batch_group* G : B->groups) {
+        const int D = G->d;
+        const int ks = D * D + 2 * D + 1;
+        if (!G->exk) {
+            std::vector<double> h((size_t)G->n * ks);
+            for (int64_t j = 0; j < G->n; ++j) {
+                const int64_t i = G->ids[j];
+                tmg_level_host L;
+                tmg_host::level_setup(D, B->lambda[i] * B->tau[i], B->omega, &L);
+                double* k = h.data() + (size_t)j * ks;
+                for (int q = 0; q < D * D; ++q) k[q] = L.Ainv[q];
+                for (int q = 0; q < D; ++q) {
+                    k[D * D + q] = L.g[q];
+                    k[D * D + D + q] = L.c[q];
+                }
+                k[D * D + 2 * D] = L.alpha;
+            }
+            cudaError_t e = cudaMalloc(&G->exk, sizeof(double) * h.size());
+            if (e != cudaSuccess) {
+                G->exk = nullptr;
+                g_last_cuda_b = (int)e;
+                return TMG_ENOMEM;
+            }
+            TB_CUDA(cudaMemcpyAsync(G->exk, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, B->s));
+            TB_CUDA(cudaStreamSynchronize(B->s));   // h goes out of scope
+        }
+        const int grid = grid_flat(B, G->n * 32);
+        switch (D) {
+            case 1: kb_exact_err<1><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            case 2: kb_exact_err<2><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            case 3: kb_exact_err<3><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            case 4: kb_exact_err<4><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            case 5: kb_exact_err<5><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            default: kb_exact_err<6><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+        }
+        TB_CUDA(cudaGetLastError());
+    }
+    TB_CUDA(cudaMemcpyAsync(B->err.data(), B->err_dev, sizeof(double) * B->n_inst, cudaMemcpyDeviceToHost, B->s));
+    TB_CUDA(cudaStreamSynchronize(B->s));
+    return TMG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -618,6 +754,7 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
     tmg_opts_default(&o);
     if (opts) o = *opts;
     if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 || o.gamma != 1 ||
+        o.check_fp64 < 0 || o.check_fp64 > 1 ||
         o.schedule < TMG_SCHED_AUTO || o.schedule > TMG_SCHED_CTA ||
         (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 || o.max_cycles < 0 ||
         !(o.tol >= 0.0))
@@ -644,6 +781,7 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
     B->omega = omega;
     B->cycles.assign(n_inst, 0);
     B->rel.assign(n_inst, NAN);
+    B->err.assign(n_inst, NAN);
     B->s = static_cast<cudaStream_t>(stream);
     if (!B->s) {
         cudaError_t e = cudaStreamCreate(&B->s);
@@ -734,6 +872,7 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
 
 tmg_status tmg_solve_batched(tmg_batch* B, const double* f, const double* u0, double* u) {
     if (!B || !aligned16(f) || !aligned16(u) || !u0 || (reinterpret_cast<uintptr_t>(u0) & 7u)) return TMG_EINVAL;
+    std::fill(B->err.begin(), B->err.end(), NAN);
     // fork: every group runs on its own stream after the caller's prior work
     TB_CUDA(cudaEventRecord(B->fork, B->s));
     tmg_status st = TMG_OK;
@@ -763,6 +902,10 @@ tmg_status tmg_solve_batched(tmg_batch* B, const double* f, const double* u0, do
         tmg_status s = finish_group(B, G);
         if (s != TMG_OK && s != TMG_ENOTCONV) return drain(B, s);
         st = worst(st, s);
+    }
+    if (B->o.check_fp64) {
+        tmg_status s = check_fp64(B, f, u0, u);
+        if (s != TMG_OK) return s;
     }
     TB_CUDA(cudaStreamSynchronize(B->s));
     return st;
@@ -809,12 +952,24 @@ tmg_status tmg_adjoint_batched(tmg_batch* B, const double* g, const double* u, d
     return st;
 }
 
-tmg_status tmg_stats_batched(const tmg_batch* B, int* cycles, double* rel_res, int* max_cycles_used) {
+tmg_status tmg_error_vs_fp64_batched(tmg_batch* B, const double* f, const double* u0, const double* u,
+                                     double* err_host) {
+    if (!B || !err_host || !aligned16(f) || !aligned16(u) || !u0 || (reinterpret_cast<uintptr_t>(u0) & 7u))
+        return TMG_EINVAL;
+    const tmg_status s = check_fp64(B, f, u0, u);
+    if (s != TMG_OK) return s;
+    for (int64_t i = 0; i < B->n_inst; ++i) err_host[i] = B->err[i];
+    return TMG_OK;
+}
+
+tmg_status tmg_stats_batched(const tmg_batch* B, int* cycles, double* rel_res, double* err_vs_fp64,
+                             int* max_cycles_used) {
     if (!B) return TMG_EINVAL;
     int mx = 0;
     for (int64_t i = 0; i < B->n_inst; ++i) {
         if (cycles) cycles[i] = B->cycles[i];
         if (rel_res) rel_res[i] = B->rel[i];
+        if (err_vs_fp64) err_vs_fp64[i] = B->err[i];
         mx = std::max(mx, B->cycles[i]);
     }
     if (max_cycles_used) *max_cycles_used = mx;
@@ -870,9 +1025,11 @@ void tmg_destroy_batched(tmg_batch* B) {
         if (G->Fg) cudaFree(G->Fg);
         if (G->ug) cudaFree(G->ug);
         if (G->u0g) cudaFree(G->u0g);
+        if (G->exk) cudaFree(G->exk);
         delete G;
     }
     if (B->table) cudaFree(B->table);
+    if (B->err_dev) cudaFree(B->err_dev);
     if (B->fork) cudaEventDestroy(B->fork);
     if (B->own_stream) cudaStreamDestroy(B->s);
     delete B;

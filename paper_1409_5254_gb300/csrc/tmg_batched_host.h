@@ -52,6 +52,8 @@ struct tmg_batch_group {
     size_t cta_smem;
     int sched;           // TMG_SCHED_GRID or TMG_SCHED_CTA
     double ms_tune[2];   // autotuner: one synthetic solve, grid form and CTA form (NAN: not timed)
+    double* exk;         // error check: FP64 level-0 constants per instance, [n][D*D + 2D + 1]
+                         // (A^{-1}, g, c, alpha), built on the first check
 };
 
 struct tmg_batch {
@@ -70,6 +72,8 @@ struct tmg_batch {
     void* table;          // device copies of off, N (int64), tau (double), p (int) for the gradient kernel
     std::vector<int> cycles;
     std::vector<double> rel;
+    std::vector<double> err;  // error against the exact FP64 solve per instance (NAN unless checked)
+    double* err_dev;          // its device copy (allocated on the first check)
     double ms_whole[2] = {NAN, NAN};   // autotuner: whole synthetic batch, per-group choices / all grid
 };
 

@@ -113,7 +113,9 @@ struct tmg_plan {
     // statistics of the last solve
     int last_cycles;
     double last_rel;
+    double last_err;               // error against the exact FP64 solve (NAN unless opts.check_fp64)
     std::vector<double> last_hist;
+    double* ex_buf;                // exact FP64 solution of the error check (allocated on first use)
 };
 
 // Per-(precision, D) entry points, instantiated in tmg_inst_*.cu.
@@ -139,6 +141,10 @@ const tmg_ops* tmg_ops_f64_wide(int d, int dir);   // d = 11, forward only (null
 // array, and the gradient reductions dJ/du0 = a^T mu_0,
 // dJ/dlambda = -tau sum_n mu_n^T Mhat u_n.
 cudaError_t tmg_launch_reverse(const double* src, double* dst, int64_t N, int d, cudaStream_t s);
+// max |u - v| and max |v| over n values (as the bits of non-negative doubles,
+// out2 zeroed first), for the error of a result against the exact FP64 solve.
+cudaError_t tmg_launch_maxabs2(const double* u, const double* v, int64_t n, unsigned long long* out2, int max_blocks,
+                               cudaStream_t s);
 cudaError_t tmg_launch_adjoint_grads(const double* mu, const double* u, int64_t N, int d, double tau,
                                      double* partials, int max_blocks, unsigned* ticket, double* dJdu0,
                                      double* dJdlambda, cudaStream_t s);

@@ -34,7 +34,7 @@ class _Opts(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("gamma", ctypes.c_int), ("precision", ctypes.c_int),
                 ("n_min", ctypes.c_int64), ("use_graph", ctypes.c_int), ("initial_guess", ctypes.c_int),
                 ("tail_cap", ctypes.c_int64), ("use_pdl", ctypes.c_int), ("update_residual", ctypes.c_int),
-                ("fuse_levels", ctypes.c_int), ("schedule", ctypes.c_int)]
+                ("fuse_levels", ctypes.c_int), ("schedule", ctypes.c_int), ("check_fp64", ctypes.c_int)]
 
 
 _LIB = None
@@ -42,10 +42,10 @@ _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
 EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
-           "tmg_stats", "tmg_plan_shape", "tmg_level_constants", "tmg_transfer_matrices", "tmg_plan_info",
+           "tmg_stats", "tmg_error_vs_fp64", "tmg_plan_shape", "tmg_level_constants", "tmg_transfer_matrices", "tmg_plan_info",
            "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
-           "tmg_stats_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched"]
+           "tmg_stats_batched", "tmg_error_vs_fp64_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched"]
 
 
 def library_path() -> str:
@@ -70,7 +70,7 @@ def _lib():
         L.tmg_solve_direct.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.tmg_residual.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
-        L.tmg_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, ctypes.c_int]
+        L.tmg_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), _dp, _dp, _dp, ctypes.c_int]
         L.tmg_plan_shape.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
                                      ctypes.c_double, ctypes.POINTER(_Opts), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
@@ -93,7 +93,11 @@ def _lib():
                                         ctypes.POINTER(_Opts), _vp]
         L.tmg_solve_batched.argtypes = [_vp, _vp, _vp, _vp]
         L.tmg_adjoint_batched.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
-        L.tmg_stats_batched.argtypes = [_vp, _ip, _dp, _ip]
+        L.tmg_stats_batched.argtypes = [_vp, _ip, _dp, _dp, _ip]
+        L.tmg_error_vs_fp64_batched.argtypes = [_vp, _vp, _vp, _vp, _dp]
+        L.tmg_error_vs_fp64_batched.restype = ctypes.c_int
+        L.tmg_error_vs_fp64.argtypes = [_vp, _vp, ctypes.c_double, _vp, _dp]
+        L.tmg_error_vs_fp64.restype = ctypes.c_int
         L.tmg_batch_info.argtypes = [_vp, _ip, _lp]
         L.tmg_batch_group_info.argtypes = [_vp, ctypes.c_int, _ip, _lp, _lp, _ip, _dp, _dp]
         L.tmg_batch_tune_info.argtypes = [_vp, _dp, _dp]
@@ -142,6 +146,7 @@ class SolveStats:
     cycles: int
     rel_res: float
     hist: np.ndarray
+    err_vs_fp64: float = float("nan")   # max|u - u_exact| / max|u_exact| (plans built with check_fp64)
 
 
 class Plan:
@@ -151,7 +156,7 @@ class Plan:
                  tol: float = 1e-10, max_cycles: int = 100, nu1: int = 1, nu2: int = 1, gamma: int = 1,
                  precision="mixed", n_min: int = 64, use_graph: bool = True, initial_guess: bool = False,
                  tail_cap: int = 0, use_pdl: bool = True, update_residual: bool = True,
-                 fuse_levels=None, stream=None):
+                 fuse_levels=None, check_fp64: bool = False, stream=None):
         L = _lib()
         o = _Opts()
         L.tmg_opts_default(ctypes.byref(o))
@@ -162,6 +167,7 @@ class Plan:
         o.use_pdl = int(use_pdl)
         o.update_residual = int(update_residual)
         o.fuse_levels = -1 if fuse_levels is None else int(bool(fuse_levels))
+        o.check_fp64 = int(bool(check_fp64))
         self.precision = _PREC[precision]
         self.p, self.d, self.N = p, p + 1, N
         self.tau, self.lam = tau, lam
@@ -208,6 +214,15 @@ class Plan:
                                        _dev_ptr(u, self.d, self.N, "u")), "tmg_solve_direct")
         return u
 
+    def error_vs_fp64(self, f, u0: float, u) -> float:
+        """max|u - u_exact| / max|u_exact| against the exact FP64 solve of the
+        same system (tmg_error_vs_fp64)."""
+        err = ctypes.c_double(0.0)
+        _order_after_current(self._stream, u)
+        _check(_lib().tmg_error_vs_fp64(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
+                                        _dev_ptr(u, self.d, self.N, "u"), ctypes.byref(err)), "tmg_error_vs_fp64")
+        return err.value
+
     def solve_host(self, f_host, u0: float, u_host) -> int:
         """f_host, u_host: contiguous float64 CPU tensors or numpy arrays (pinned tensors copy fastest)."""
         fp = ctypes.c_void_p(_host_ptr(f_host, self.d, self.N))
@@ -245,11 +260,12 @@ class Plan:
     def stats(self, hist_len: int = 512) -> SolveStats:
         cyc = ctypes.c_int(0)
         rel = ctypes.c_double(0.0)
+        err = ctypes.c_double(0.0)
         hist = np.full(hist_len, np.nan)
-        _check(_lib().tmg_stats(self._h, ctypes.byref(cyc), ctypes.byref(rel),
+        _check(_lib().tmg_stats(self._h, ctypes.byref(cyc), ctypes.byref(rel), ctypes.byref(err),
                                 hist.ctypes.data_as(_dp), hist_len), "tmg_stats")
         h = hist[: cyc.value + 1].copy()
-        return SolveStats(getattr(self, "last_status", TMG_OK), cyc.value, rel.value, h)
+        return SolveStats(getattr(self, "last_status", TMG_OK), cyc.value, rel.value, h, err.value)
 
     def profile_cycle(self, f, u0: float, u, reps: int = 10) -> dict:
         """Mean per-kernel milliseconds of one correction cycle (CUDA events on the plan's stream)."""
@@ -443,8 +459,26 @@ class Batch:
         rel = np.zeros(self.n)
         mx = ctypes.c_int(0)
         _check(_lib().tmg_stats_batched(self._h, cyc.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                                        rel.ctypes.data_as(_dp), ctypes.byref(mx)), "tmg_stats_batched")
+                                        rel.ctypes.data_as(_dp), None, ctypes.byref(mx)), "tmg_stats_batched")
         return cyc, rel, mx.value
+
+    def error_vs_fp64(self, f, u0, u) -> np.ndarray:
+        """Per-instance max|u_i - u_exact,i| / max|u_exact,i| of the given
+        results against the exact FP64 solves (tmg_error_vs_fp64_batched)."""
+        err = np.zeros(self.n)
+        _order_after_current(self._stream, u)
+        _check(_lib().tmg_error_vs_fp64_batched(self._h, self._ptr(f, self.total, "f"), self._ptr(u0, self.n, "u0"),
+                                                self._ptr(u, self.total, "u"), err.ctypes.data_as(_dp)),
+               "tmg_error_vs_fp64_batched")
+        return err
+
+    def err_vs_fp64(self) -> np.ndarray:
+        """Per-instance max|u_i - u_exact,i| / max|u_exact,i| of the last solve
+        against the exact FP64 solve (batches built with check_fp64=True; NAN
+        otherwise)."""
+        err = np.zeros(self.n)
+        _check(_lib().tmg_stats_batched(self._h, None, None, err.ctypes.data_as(_dp), None), "tmg_stats_batched")
+        return err
 
     def info(self):
         ng = ctypes.c_int(0)

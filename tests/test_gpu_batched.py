@@ -53,6 +53,92 @@ def check_solution(Fs, u0, tau, lam, p, N, u_packed, batch, tol):
     return worst
 
 
+def group_length(N):
+    """The length the batched solver gives an instance of N intervals inside
+    its group: padded at its end to a power of two (at least 2) with a zero
+    right-hand side."""
+    Ng = 2
+    while Ng < N:
+        Ng *= 2
+    return Ng
+
+
+def oracle_batched_iterates(p, z, F, u0, k, n_min=64, **kw):
+    """The oracle's textbook cycle (eq. chap4_errorTwoGridCycle) applied k
+    times to the instance as the batched solver holds it: padded to its
+    group's length, coarsened while a level is even and longer than
+    min(n_min, 64) intervals; the first N intervals of each iterate."""
+    N = F.shape[0]
+    Fh = np.zeros((group_length(N), p + 1))
+    Fh[:N] = O.fold_u0(p, F, u0)
+    u = np.zeros_like(Fh)
+    out = []
+    for _ in range(k):
+        u = O.mg_one_cycle(p, z, Fh, u, n_min=min(n_min, 64), **kw)
+        out.append(u[:N].copy())
+    return out
+
+
+BATCH_CYCLE_N = [1, 2, 3, 5, 64, 100, 1001, 4096, 16384, 12000, 777, 2048, 96, 33, 8192, 300, 5000, 130]
+
+
+@pytest.mark.parametrize("schedule", ["grid", "cta"])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 2), (0, 2), (3, 1)])
+def test_batched_fp64_cycles_match_textbook_cycle(dev, schedule, nu):
+    """Iterate-level parity of the batched FP64 path with the paper's cycle:
+    an uneven batch (p_t = 0..5, lengths 1 .. 16384 including non-powers of
+    two, z = 1e-3 .. 1e3) run for exactly k = 1, 2, 3 cycles (tol = 0,
+    max_cycles = k) in each schedule, every instance against k applications
+    of the oracle's textbook cycle on that instance's own hierarchy, 1e-12
+    relative.  The CTA form takes the groups that fit one CTA (the others fall
+    back to the grid form)."""
+    from paper_1409_5254_gb300 import tmg
+    rng = np.random.default_rng(31 + nu[0] + 4 * nu[1])
+    N = np.array(BATCH_CYCLE_N)
+    p = np.arange(len(N)) % 6
+    z = 10.0 ** rng.uniform(-3, 3, len(N))
+    Fs, u0, tau, lam = make_batch(31, p, N, z)
+    f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+    u0d = torch.from_numpy(u0).to(dev)
+    sched = tmg.SCHED_GRID if schedule == "grid" else tmg.SCHED_CTA
+    ref = [oracle_batched_iterates(int(p[i]), lam[i] * tau[i], Fs[i], u0[i], 3, nu1=nu[0], nu2=nu[1])
+           for i in range(len(N))]
+    for k in (1, 2, 3):
+        with tmg.Batch(p, tau, lam, N, precision="fp64", tol=0.0, max_cycles=k, schedule=sched, nu1=nu[0],
+                       nu2=nu[1]) as B:
+            u = B.solve(f, u0d, allow_notconv=True)
+            cyc, rel, mx = B.stats()
+            kinds = {g["schedule"] for g in B.info()["group_info"]}
+            us = B.split(u.cpu().numpy())
+        assert kinds == ({"grid"} if schedule == "grid" else {"grid", "cta"}), kinds
+        for i in range(len(N)):
+            # an instance whose residual is exactly zero stops early, as it should
+            c = int(cyc[i])
+            assert 1 <= c <= k and (c == k or rel[i] == 0.0), (i, c, rel[i])
+            e = np.abs(us[i] - ref[i][c - 1]).max() / max(np.abs(ref[i][c - 1]).max(), 1e-300)
+            assert e <= 1e-12, (k, i, int(p[i]), int(N[i]), z[i], e)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batched_error_against_fp64_is_reported(dev, prec):
+    """opts.check_fp64 on a batch: per-instance max|u_i - u_exact,i| /
+    max|u_exact,i| against the exact FP64 solve (one warp per instance, chunk
+    maps scanned across the warp), equal to the same error taken against the
+    oracle's forward substitution up to the exact solves' own difference."""
+    from paper_1409_5254_gb300 import tmg
+    N, p, z = inputs.uneven_batch(41, 30, nmin_exp=0.0, nmax_exp=14.0)
+    Fs, u0, tau, lam = make_batch(41, p, N, z)
+    f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+    with tmg.Batch(p, tau, lam, N, precision=prec, tol=1e-10, max_cycles=300, check_fp64=True) as B:
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        err = B.err_vs_fp64()
+        us = B.split(u.cpu().numpy())
+    for i in range(len(p)):
+        ex = O.fsub(int(p[i]), lam[i] * tau[i], Fs[i], u0[i])
+        err_or = np.abs(us[i] - ex).max() / np.abs(ex).max()
+        assert abs(err[i] - err_or) <= max(2e-13, 8 * N[i] * 2.2e-16) + 1e-6 * err_or, (i, err[i], err_or)
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_uniform_batch(dev, prec):
     from paper_1409_5254_gb300 import tmg

@@ -241,6 +241,25 @@ def test_edge_cases(dev, p, N, lam, prec):
     assert rel_err(u, u_ex) <= (1e-10 if prec == "fp64" else 1e-6)
 
 
+@pytest.mark.parametrize("p,N,lam,n_min", [e + (2,) for e in EDGE] + [(2, 1 << 14, 1e3 * (1 << 14), 1)])
+def test_edge_case_cycles_match_textbook_cycle(dev, p, N, lam, n_min):
+    """The edge cases above (one and two intervals, an odd length without
+    coarsening, 1001 = 7 * 11 * 13, lambda = 0, lambda tau = 1e3) and a
+    15-level hierarchy with z up to 1.6e7 on its coarsest level, held at the
+    iterate level: the FP64 iterates after 1, 2 and 3 cycles against the
+    oracle's textbook cycle (eq. chap4_errorTwoGridCycle with omega* of Lemma
+    chap4_lemma7 per level), 1e-12 relative."""
+    prob = inputs.scalar_problem(N, N, p, lam=lam, T=1.0, u0=-0.3)
+    z = lam * prob["tau"]
+    Fhat = O.fold_u0(p, prob["F"], prob["u0"])
+    got, info = gpu_cycles(dev, p, prob["tau"], lam, prob["F"], prob["u0"], 3, n_min=n_min)
+    assert info["levels"] == O.num_levels(N, n_min, 0)
+    u = np.zeros_like(prob["F"])
+    for k in range(3):
+        u = O.mg_one_cycle(p, z, Fhat, u, n_min=n_min)
+        assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
+
+
 def test_deep_hierarchy_large_z(dev):
     """lambda tau = 1e3 with many levels (z up to ~1e7 on the coarsest level)."""
     N = 1 << 14
@@ -567,3 +586,25 @@ def test_plan_shape_matches_the_plan_setup_builds(dev, p, N, kw):
         info = plan.info()
     assert (s["levels"], s["tail_level"], s["tail_intervals"]) == (info["levels"], info["tail_level"],
                                                                     info["tail_intervals"])
+
+
+@pytest.mark.parametrize("p,N,lam", [(1, 1 << 14, 1.0), (3, 4096, 200.0), (0, 1001, 5.0), (10, 2048, 3.0)])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_error_against_fp64_is_reported(dev, p, N, lam, prec):
+    """opts.check_fp64: tmg_stats reports max|u - u_exact| / max|u_exact| of
+    the solve against the exact FP64 solve; it agrees with the same error taken
+    against the oracle's forward substitution, up to the exact solves' own
+    difference (a few N eps, from the rounding of alpha in the recurrence)."""
+    prob = inputs.scalar_problem(N + 1, N, p, lam=lam, T=1.0, u0=0.4)
+    z = lam * prob["tau"]
+    Fd = torch.from_numpy(prob["F"]).to(dev)
+    with tmg().Plan(p, prob["tau"], lam, N, precision=prec, tol=1e-10, check_fp64=True) as plan:
+        u = plan.solve(Fd, prob["u0"]).cpu().numpy()
+        st = plan.stats()
+    with tmg().Plan(p, prob["tau"], lam, N, precision=prec, tol=1e-10) as plan:
+        plan.solve(Fd, prob["u0"])
+        assert np.isnan(plan.stats().err_vs_fp64)
+    ex = O.fsub(p, z, prob["F"], prob["u0"])
+    err_or = rel_err(u, ex)
+    assert np.isfinite(st.err_vs_fp64)
+    assert abs(st.err_vs_fp64 - err_or) <= max(2e-13, 8 * N * 2.2e-16) + 1e-6 * err_or, (st.err_vs_fp64, err_or)
