@@ -53,7 +53,7 @@ def n_min_for(n: int) -> int:
     """The same hierarchy depth for a sample of n intervals (oracle runs)."""
     return max(64, N_MIN * n // N_FULL)
 TOL = 1e-10
-METRIC = "time-DoFs/s solved to 1e-10 rel residual"
+METRIC = "time-DoFs/s solved to 1e-10 rel residual (mixed vs FP64 form), % HBM peak"
 WORKLOAD = ("long horizon u'+lambda u=f, lambda=1, tau=1e-6, N=2^24, p_t=1, mixed FP32 cycles + FP64-accurate "
             "refinement, V(2,2), omega*, coarsest level 2^17 intervals solved by the parallel affine scan")
 
@@ -169,16 +169,153 @@ def cycle_bytes(N: int, d: int, lt: int):
     return {"start0": start0, "confirm0": confirm0, "updown0": updown0, "cycle": updown0 + coarse + tail_io}
 
 
-def time_solves(plan, F, u, steps: int, stream, torch):
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
+# Nominal FP64 rate: 2 FP64 FMA per clock per SM, 152 SMs, 2.07 GHz maximum SM
+# clock; an FMA, an add or a multiply counts as one operation.
+FP64_PEAK_OPS = 152 * 2 * 2.07e9
+
+
+def fp64_ops_per_interval(d: int, nu1: int, nu2: int):
+    """FP64 operations of the useful work per interval and level visit of the
+    FP64 cycle's streaming kernels (the halo lanes' recompute excluded):
+    zero-start pre-smoothing d^2 + 2d (A^{-1} f, u and A u), each further
+    pre-sweep 7d (4d for u, 3d for A u), the residual 3d, the restriction d^2
+    per fine interval; the way up repeats the pre-smoothing of u alone
+    (d^2 + d, then 4d per further sweep) and adds the prolongation (d^2) and
+    nu2 post-sweeps of 4d.  Level 0 adds the residual of the original system
+    from u (6d, Legendre running sums) on the way down and u += c (d) on the
+    way up.  Returns (down, up, down0, up0)."""
+    extra = max(nu1 - 1, 0)
+    down = d * d + 2 * d + 7 * d * extra + 3 * d + d * d
+    up = d * d + d + 4 * d * extra + d * d + 4 * d * nu2
+    return down, up, down + 6 * d, up + d
+
+
+def fp64_cycle_model(N: int, d: int, nu, lt: int, scanned: bool):
+    """Algorithmic bytes and FP64 operations of one cycle of the plain FP64
+    form (one level per kernel): level 0 reads u, F and writes r, f_1 on the
+    way down (8 + 8 + 8 + 4 B/DoF) and reads r, c_1, u and writes u on the way
+    up (8 + 4 + 8 + 8); level l moves 1.5 + 2.5 level vectors; the coarsest
+    level (scan: F read twice, u written; on chip: f read, u written)."""
+    down, up, down0, up0 = fp64_ops_per_interval(d, *nu)
+    nb = N * d * 8
+    b = {"down0": 28 * N * d, "up0": 28 * N * d}
+    ops = {"down0": down0 * N, "up0": up0 * N}
+    coarse_b = coarse_ops = 0
+    for l in range(1, lt):
+        coarse_b += 4 * (nb >> l)
+        coarse_ops += (down + up) * (N >> l)
+    coarse_b += (3 if scanned else 2) * (nb >> lt)
+    coarse_ops += (d * d + 3 * d + 3) * (N >> lt) * (2 if scanned else 1)
+    b["cycle"] = b["down0"] + b["up0"] + coarse_b
+    ops["cycle"] = ops["down0"] + ops["up0"] + coarse_ops
+    return b, ops
+
+
+def level0_mixed_recomputed_bytes(N: int, d: int):
+    """The mixed form that recomputes the level-0 residual from u every cycle
+    (p_t = 10): k_down0 reads u, F and writes the FP32 residual and f_1
+    (8 + 8 + 4 + 2 B/DoF); k_up0 reads r, c_1, u and writes u (4 + 2 + 8 + 8)."""
+    return {"down0": 22 * N * d, "up0": 22 * N * d}
+
+
+def kernel_roofline(name, t_ms, nbytes, ops, hbm_peak, peak_kind):
+    """Roofline of one kernel launch: the larger of its HBM time (algorithmic
+    bytes at the measured copy bandwidth) and its FP64 time (operations at the
+    nominal FP64 rate) bounds it; frac = that bound over the measured time."""
+    t = t_ms * 1e-3
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    t_alu = ops / FP64_PEAK_OPS if ops else 0.0
+    out = {"kernel": name, "launch_ms": round(t_ms, 5), "bytes_per_launch": int(nbytes),
+           "fp64_ops_per_launch": int(ops) if ops else 0,
+           "achieved_gbs": round(nbytes / t / 1e9, 1),
+           "achieved_fp64_gops": round(ops / t / 1e9, 1) if ops else 0.0}
+    if t_alu > t_hbm:
+        out.update({"bound": "alu", "achieved": round(ops / t / 1e9, 1), "peak": round(FP64_PEAK_OPS / 1e9, 1),
+                    "unit": "G FP64 ops/s", "peak_kind": "nominal (152 SMs x 2 FP64 FMA/clock x 2.07 GHz)",
+                    "frac": round(t_alu / t, 4), "hbm_frac": round(t_hbm / t, 4)})
+    else:
+        out.update({"bound": "hbm", "achieved": round(nbytes / t / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "peak_kind": peak_kind, "frac": round(t_hbm / t, 4),
+                    "fp64_frac": round(t_alu / t, 4) if ops else 0.0})
+    return out
+
+
+def whole_solve_roofline(t_ms, nbytes, ops, hbm_peak, peak_kind, model):
+    """Roofline of a whole solve (batched workloads, whose kernels are timed
+    together): algorithmic bytes (and FP64 operations) of every kernel of the
+    solve over the solve's time."""
+    r = kernel_roofline("whole solve", t_ms, nbytes, ops, hbm_peak, peak_kind)
+    r["scope"] = "whole solve"
+    r["model"] = model
+    return r
+
+
+def time_each(fn, steps: int, stream, torch):
+    """Device time of each of `steps` calls of fn (CUDA events on `stream`
+    around every call), in ms."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
-    start.record(stream)
-    for _ in range(steps):
-        plan.solve(F, U0, u)
-    end.record(stream)
-    end.synchronize()
-    return start.elapsed_time(end) / steps
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def time_solves(plan, F, u, steps: int, stream, torch):
+    """Median device time of `steps` solves (each timed by its own events)."""
+    return statistics.median(time_each(lambda: plan.solve(F, U0, u), steps, stream, torch))
+
+
+def single_line(tmg, torch, stream, F, u, p: int, tau: float, prec: str, n_min: int, steps: int, eager: bool,
+                hbm_peak: float, peak_kind: str, nu=None):
+    """One single-problem side line: median of `steps` solves, cycles, FP64
+    residual, error against the exact FP64 solve, and the roofline of its
+    dominant level-0 kernel from per-kernel event times of 10 eager cycles."""
+    nu = NU if nu is None else nu
+    N, d = F.shape[0], p + 1
+    with tmg.Plan(p, tau, LAM, N, precision=prec, tol=TOL, stream=stream, max_cycles=300, nu1=nu[0], nu2=nu[1],
+                  n_min=n_min, use_graph=not eager) as pl:
+        pl.solve(F, U0, u)
+        times = time_each(lambda: pl.solve(F, U0, u), steps, stream, torch)
+        st = pl.stats()
+        info = pl.info()
+        err = pl.error_vs_fp64(F, U0, u)
+        prof = pl.profile_cycle(F, U0, u.clone(), reps=10)
+    ms = statistics.median(times)
+    lt = info["tail_level"]
+    scanned = p + 1 > 6 or info["tail_intervals"] > 8192
+    if prec == "fp64":
+        b, ops = fp64_cycle_model(N, d, nu, lt, scanned)
+        k = [kernel_roofline("k_down0 (FP64 residual from u, pre-smoothing, restriction)", prof["down0"], b["down0"],
+                             ops["down0"], hbm_peak, peak_kind),
+             kernel_roofline("k_up0 (recomputed pre-smoothing, prolongation, post-smoothing, u += c)", prof["up0"],
+                             b["up0"], ops["up0"], hbm_peak, peak_kind)]
+        cyc = {"cycle_bytes": b["cycle"], "cycle_fp64_ops": ops["cycle"], "cycle_ms": round(prof["cycle"], 5),
+               "cycle_frac": round(max(b["cycle"] / (hbm_peak * 1e9), ops["cycle"] / FP64_PEAK_OPS)
+                                   / (prof["cycle"] * 1e-3), 4)}
+    elif d > 6:
+        b = level0_mixed_recomputed_bytes(N, d)
+        k = [kernel_roofline("k_down0 (mixed, residual recomputed from u)", prof["down0"], b["down0"], 0, hbm_peak,
+                             peak_kind),
+             kernel_roofline("k_up0 (mixed)", prof["up0"], b["up0"], 0, hbm_peak, peak_kind)]
+        cyc = {"cycle_ms": round(prof["cycle"], 5)}
+    else:
+        cb = cycle_bytes(N, d, lt)
+        k = [kernel_roofline("k_updown0", prof["up0"], cb["updown0"], 0, hbm_peak, peak_kind)]
+        steady = prof["cycle"] - prof["down0"]
+        cyc = {"cycle_bytes": cb["cycle"], "cycle_ms": round(steady, 5),
+               "cycle_frac": round(cb["cycle"] / (steady * 1e-3) / 1e9 / hbm_peak, 4)}
+    dom = max(k, key=lambda r: r["launch_ms"])
+    roof = dict(dom)
+    roof.update(cyc)
+    if len(k) > 1:
+        roof["other_level0_kernel"] = min(k, key=lambda r: r["launch_ms"])
+    return {"value": N * d / (ms * 1e-3), "unit": "DoF/s", "ms_per_step": round(ms, 4),
+            "ms_mean": round(statistics.fmean(times), 4), "solves_timed": steps, "precision": prec,
+            "cycles": st.cycles, "rel_res": st.rel_res, "err_vs_fp64": err, "cycle": f"V{tuple(nu)}",
+            "levels": info["levels"], "coarsest_intervals": info["tail_intervals"], "roofline": roof}
 
 
 def run_ours(args):
@@ -217,14 +354,20 @@ def run_ours(args):
     st = plan.stats()
     info = plan.info()
 
+    # the timed region: exactly `steps` solves, a barrier and a device
+    # synchronisation on both sides, each solve timed by its own events
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    ms = time_solves(plan, F, u, args.steps, stream, torch)
+    times = time_each(lambda: plan.solve(F, U0, u), args.steps, stream, torch)
     clk.stop()
-    ms = replicas.max_over_ranks(ms, dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = replicas.max_over_ranks(statistics.median(times), dev)
+    ms_mean = replicas.max_over_ranks(statistics.fmean(times), dev)
     st = plan.stats()
     value = replicas.aggregate_throughput([N_FULL * d] * world, ms)    # one replica per rank
 
@@ -235,35 +378,25 @@ def run_ours(args):
     Fh[0, 1] -= U0
     rel_fp64 = float(torch.linalg.vector_norm(r) / torch.linalg.vector_norm(Fh))
     del r, Fh
+    # error of the timed result against the exact FP64 solve (tmg_error_vs_fp64)
+    err_vs_fp64 = plan.error_vs_fp64(F, U0, u)
 
-    # exact FP64 solve by the parallel affine scan: the error of the timed
-    # result, and the direct solve as a throughput ceiling (one pass to reduce
-    # each tile of F, one to replay it: reads F twice, writes u once)
-    u_ex = plan.solve_direct(F, U0)
-    err_vs_fp64 = float((u - u_ex).abs().max() / u_ex.abs().max())
-    torch.cuda.synchronize()
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    n_dir = max(3, args.steps // 2)
-    start.record(stream)
-    for _ in range(n_dir):
-        plan.solve_direct(F, U0, u_ex)
-    end.record(stream)
-    end.synchronize()
-    ms_dir = start.elapsed_time(end) / n_dir
+    # the exact FP64 solve by the parallel affine scan as a throughput ceiling
+    # (one pass to reduce each tile of F, one to replay it: reads F twice,
+    # writes u once)
+    u_ex = torch.empty_like(F)
+    plan.solve_direct(F, U0, u_ex)
+    n_dir = max(10, args.steps // 2)
+    ms_dir = statistics.median(time_each(lambda: plan.solve_direct(F, U0, u_ex), n_dir, stream, torch))
     dir_bytes = 3 * N_FULL * d * 8
     # FP64 operations (an FMA or an add counts one) per interval: pass 1 c^T f and
     # the map composition (d + 2), pass 3 c^T f, A^{-1} f + g e and the carry
-    # (d^2 + 2d + 1); the peak is 2 FP64 FMA per clock per SM (1.25 TFLOP/s
-    # nominal) at 152 SMs x 2.07 GHz
+    # (d^2 + 2d + 1)
     fp64_ops = N_FULL * (d * d + 3 * d + 3)
-    fp64_peak = 152 * 2 * 2.07e9
     direct = {"value": N_FULL * d / (ms_dir * 1e-3), "unit": "DoF/s", "ms_per_step": round(ms_dir, 4),
-              "precision": "fp64", "bytes_per_dof": 24, "lower_bound_bytes_per_dof": 16,
-              "hbm_frac": round(dir_bytes / (ms_dir * 1e-3) / 1e9 / hbm_peak, 4),
-              "roofline": {"bound": "alu", "achieved": round(fp64_ops / (ms_dir * 1e-3) / 1e9, 1),
-                           "peak": round(fp64_peak / 1e9, 1), "unit": "G FP64 ops/s",
-                           "frac": round(fp64_ops / (ms_dir * 1e-3) / fp64_peak, 4), "peak_kind": "nominal"},
+              "solves_timed": n_dir, "precision": "fp64", "bytes_per_dof": 24, "lower_bound_bytes_per_dof": 16,
+              "roofline": kernel_roofline("k_scan_tiles + k_scan_prefix + k_scan_apply", ms_dir, dir_bytes,
+                                          fp64_ops, hbm_peak, peak_kind),
               "note": "exact parallel-scan solve (not multigrid), same problem and stream"}
     del u_ex
 
@@ -279,7 +412,17 @@ def run_ours(args):
                 "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                 "traffic": args.traffic if args.traffic else
                 (measured_traffic() if N_FULL == 1 << 24 and NU == (2, 2) else None),
-                "bytes_per_launch": cb["updown0"], "launch_ms": round(t_dom, 5), "launches_per_solve": st.cycles,
+                "bytes_per_launch": cb["updown0"], "bytes_per_dof": 32,
+                "byte_model": "k_updown0 per DoF: read the level-0 residual pair 6 (FP32 high part + 16-bit low "
+                              "code), u 8, the level-1 correction 2; write u 8, the updated residual pair 6, the "
+                              "next level-1 right-hand side 2 = 32 B",
+                "survey_bytes_per_dof": 60,
+                "survey_byte_model_note": "the survey's 26 + 34 B/DoF counts a level-0 down and up kernel per cycle "
+                                          "that store the correction c and an FP32 residual and re-read F; here "
+                                          "one kernel does the way up of a cycle and the way down of the next, "
+                                          "the residual is updated by r -= L c from the float pair (F is read only "
+                                          "at the start and to confirm), and c is recomputed instead of stored",
+                "launch_ms": round(t_dom, 5), "launches_per_solve": st.cycles,
                 "cycle_bytes": cb["cycle"], "cycle_ms": round(steady_ms, 5),
                 "cycle_frac": round(cb["cycle"] / (steady_ms * 1e-3) / 1e9 / hbm_peak, 4),
                 "solve_ms_per_cycle": round(ms / max(st.cycles, 1), 5),
@@ -294,14 +437,10 @@ def run_ours(args):
 
     extra = {}
     if rank == 0 and not args.quick:
+        nside = max(10, args.steps // 4)
         # plain FP64 form on the same problem
-        with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="fp64", tol=TOL, stream=stream, nu1=NU[0], nu2=NU[1],
-                      n_min=N_MIN, use_graph=not args.eager) as p64:
-            p64.solve(F, U0, u)
-            ms64 = time_solves(p64, F, u, max(2, args.steps // 4), stream, torch)
-            s64 = p64.stats()
-        extra["fp64_form"] = {"value": N_FULL * d / (ms64 * 1e-3), "ms_per_step": round(ms64, 4),
-                              "cycles": s64.cycles, "rel_res": s64.rel_res}
+        extra["fp64_form"] = single_line(tmg, torch, stream, F, u, P_MAIN, TAU, "fp64", N_MIN, nside, args.eager,
+                                         hbm_peak, peak_kind)
         # the other degrees of the same long horizon, mixed precision
         per_p = {}
         for p in (0, 2, 3, 4, 5):
@@ -309,15 +448,8 @@ def run_ours(args):
             Fp = torch.from_numpy(pr["F"]).to(dev)
             up = torch.empty_like(Fp)
             try:
-                with tmg.Plan(p, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, max_cycles=300,
-                              nu1=NU[0], nu2=NU[1], n_min=n_min_p(p),
-                              use_graph=not args.eager) as pp:
-                    pp.solve(Fp, U0, up)
-                    msp = time_solves(pp, Fp, up, max(2, args.steps // 4), stream, torch)
-                    sp = pp.stats()
-                    per_p[str(p)] = {"value": N_FULL * (p + 1) / (msp * 1e-3), "ms_per_step": round(msp, 4),
-                                     "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": f"V{NU}",
-                                     "coarsest_intervals": pp.info()["tail_intervals"]}
+                per_p[str(p)] = single_line(tmg, torch, stream, Fp, up, p, TAU, "mixed", n_min_p(p), nside,
+                                            args.eager, hbm_peak, peak_kind)
             except tmg.TmgError as e:
                 per_p[str(p)] = {"error": str(e)}
             del Fp, up
@@ -329,14 +461,9 @@ def run_ours(args):
         up = torch.empty_like(Fp)
         del pr
         try:
-            with tmg.Plan(P_MAIN, tau2, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, max_cycles=300,
-                          nu1=NU[0], nu2=NU[1], n_min=N_MIN, use_graph=not args.eager) as pp:
-                pp.solve(Fp, U0, up)
-                msp = time_solves(pp, Fp, up, max(2, args.steps // 4), stream, torch)
-                sp = pp.stats()
-                extra["tau_1_1024"] = {"value": N_FULL * d / (msp * 1e-3), "ms_per_step": round(msp, 4),
-                                       "cycles": sp.cycles, "rel_res": sp.rel_res, "z": LAM * tau2,
-                                       "cycle": f"V{NU}"}
+            extra["tau_1_1024"] = single_line(tmg, torch, stream, Fp, up, P_MAIN, tau2, "mixed", N_MIN, nside,
+                                              args.eager, hbm_peak, peak_kind)
+            extra["tau_1_1024"]["z"] = LAM * tau2
         except tmg.TmgError as e:
             extra["tau_1_1024"] = {"error": str(e)}
         del Fp, up
@@ -347,35 +474,23 @@ def run_ours(args):
         up = torch.empty_like(Fp)
         del pr
         for prec in ("mixed", "fp64"):
-            key = f"p10_{prec}"
             try:
-                with tmg.Plan(10, TAU, LAM, N_FULL, precision=prec, tol=TOL, stream=stream, max_cycles=300,
-                              nu1=NU[0], nu2=NU[1], n_min=64, use_graph=not args.eager) as pp:
-                    pp.solve(Fp, U0, up)
-                    msp = time_solves(pp, Fp, up, 2, stream, torch)
-                    sp = pp.stats()
-                    extra[key] = {"value": N_FULL * 11 / (msp * 1e-3), "ms_per_step": round(msp, 4),
-                                  "cycles": sp.cycles, "rel_res": sp.rel_res, "cycle": f"V{NU}",
-                                  "levels": pp.info()["levels"],
-                                  "coarsest_intervals": pp.info()["tail_intervals"]}
+                extra[f"p10_{prec}"] = single_line(tmg, torch, stream, Fp, up, 10, TAU, prec, 64,
+                                                   10 if prec == "mixed" else 3, args.eager, hbm_peak, peak_kind)
             except tmg.TmgError as e:
-                extra[key] = {"error": str(e)}
+                extra[f"p10_{prec}"] = {"error": str(e)}
         del Fp, up
         # other sweep counts on the headline problem (same solver, same tolerance)
         nus = {}
         for nu in ((1, 1), (1, 3), (2, 3), (3, 3)):
-            with tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, nu1=nu[0],
-                          nu2=nu[1], n_min=N_MIN, use_graph=not args.eager) as pn:
-                pn.solve(F, U0, u)
-                msn = time_solves(pn, F, u, max(2, args.steps // 4), stream, torch)
-                sn = pn.stats()
-            nus[f"V({nu[0]},{nu[1]})"] = {"value": N_FULL * d / (msn * 1e-3), "ms_per_step": round(msn, 4),
-                                           "cycles": sn.cycles, "rel_res": sn.rel_res}
+            nus[f"V({nu[0]},{nu[1]})"] = single_line(tmg, torch, stream, F, u, P_MAIN, TAU, "mixed", N_MIN, nside,
+                                                     args.eager, hbm_peak, peak_kind, nu=nu)
         extra["nu_variants"] = nus
 
     if not args.quick:
         # every rank solves its shard of the batched workloads
-        extra_b = run_batched_configs(dev, stream, args.steps, torch, rank, world)
+        extra_b = run_batched_configs(dev, stream, args.steps, torch, rank, world, hbm_peak=hbm_peak,
+                                      peak_kind=peak_kind)
         if rank == 0:
             extra["batched"] = extra_b
 
@@ -385,24 +500,29 @@ def run_ours(args):
     plan.solve_host(F_h, U0, u_h)
     if dist is not None:
         dist.barrier()
-    t0 = time.perf_counter()
-    n_e2e = max(3, args.steps // 2)
+    n_e2e = max(10, args.steps // 2)
+    t_list = []
     for _ in range(n_e2e):
+        t0 = time.perf_counter()
         plan.solve_host(F_h, U0, u_h)
-    t_e2e = replicas.max_over_ranks((time.perf_counter() - t0) / n_e2e, dev)
+        t_list.append(time.perf_counter() - t0)
+    t_e2e = replicas.max_over_ranks(statistics.median(t_list), dev)
     nbytes = N_FULL * d * 8
     e2e = {"value": replicas.aggregate_throughput([N_FULL * d] * world, t_e2e * 1e3), "unit": "DoF/s",
            "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes, "ms_per_step": round(t_e2e * 1e3, 3)}
+           "d2h_bytes_per_step": nbytes, "ms_per_step": round(t_e2e * 1e3, 3), "steps_timed": n_e2e,
+           "timing": "host wall clock per call, median"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(batched=not args.quick)
 
     plan.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": round(ms, 4), "ms_mean": round(ms_mean, 4),
+                "timing": "median of per-solve CUDA-event times on the plan's stream",
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "N": N_FULL, "p_t": P_MAIN, "tau": TAU, "lambda": LAM, "u0": U0,
                            "tol": TOL, "cycles": st.cycles, "levels": info["levels"],
@@ -421,44 +541,113 @@ def run_ours(args):
 
 
 def _time_batch(batch, f, u0, u, steps, stream, torch):
-    start = torch.cuda.Event(enable_timing=True)
-    end = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    start.record(stream)
-    for _ in range(steps):
-        batch.solve(f, u0, u)
-    end.record(stream)
-    end.synchronize()
-    return start.elapsed_time(end) / steps
+    """Median device time of `steps` batched solves."""
+    return statistics.median(time_each(lambda: batch.solve(f, u0, u), steps, stream, torch))
+
+
+def oracle_levels(N: int, n_min: int = 64) -> int:
+    """Levels of an instance's own hierarchy: coarsen while even and longer
+    than n_min intervals (the paper's nested meshes)."""
+    L, n = 1, N
+    while n % 2 == 0 and n > n_min:
+        n //= 2
+        L += 1
+    return L
+
+
+def batched_solve_model(Nv, pv, cyc, prec: str):
+    """Algorithmic bytes (and FP64 operations for the FP64 form) of one
+    batched solve on the instances' real lengths (the padding of a group is
+    not algorithmic work).  Mixed form per instance: the start (read F, write
+    the residual pair and f_1: 16 B/DoF), c cycles of the level-0 kernel and
+    the coarse levels (cycle_bytes: 32 B/DoF at level 0, two streaming levels
+    per kernel), and the norm-only confirmation (read u, F: 16 B/DoF).  FP64
+    form: c cycles of fp64_cycle_model plus the final residual from u."""
+    nbytes = ops = 0
+    for N, p, c in zip(Nv, pv, cyc):
+        N, d, c = int(N), int(p) + 1, int(c)
+        lt = oracle_levels(N) - 1
+        if prec == "mixed":
+            per = cycle_bytes(N, d, lt)["cycle"] if lt > 0 else 32 * N * d
+            nbytes += 16 * N * d + c * per + 16 * N * d
+        else:
+            b, o = fp64_cycle_model(N, d, NU, lt, False)
+            nbytes += c * b["cycle"] + b["down0"]
+            ops += c * o["cycle"] + o["down0"]
+    return nbytes, ops
 
 
 def run_batched_configs(dev, stream, steps, torch, rank: int = 0, world: int = 1,
-                        only=("heat", "uneven", "gradients"), precisions=("mixed", "fp64"), eager=False):
+                        only=("heat", "uneven", "gradients"), precisions=("mixed", "fp64"), eager=False,
+                        hbm_peak=None, peak_kind="measured"):
     """The batched workloads: decoupled 2-D heat modes, an uneven batch, and
     gradients through the adjoint.  One step = one batched solve (plus the
-    adjoint for the gradient workload); inputs resident in HBM.  With several
-    ranks each solves its shard of the instances (balanced by N (p_t+1)); the
-    value is all instances' DoFs over the slowest rank's time.  `only` and
-    `precisions` select workloads and forms (for profiling one of them)."""
+    adjoint for the gradient workload); inputs resident in HBM; the median of
+    at least 10 steps.  With several ranks each solves its shard of the
+    instances (balanced by N (p_t+1)); the value is all instances' DoFs over
+    the slowest rank's time.  `only` and `precisions` select workloads and
+    forms (for profiling one of them)."""
     import numpy as np
     from paper_1409_5254_gb300 import inputs, replicas, tmg
+
+    if hbm_peak is None:
+        hbm_peak, peak_kind = peaks()
 
     def shard(weights):
         return replicas.partition_instances(weights, world)[rank]
 
+    nsteps = max(10, steps // 4)
     out = {}
     if "heat" in only:
-        out.update(_heat_modes(dev, stream, steps, torch, shard, precisions, eager))
+        out.update(_heat_modes(dev, stream, nsteps, torch, shard, precisions, eager, hbm_peak, peak_kind))
     if "uneven" in only:
-        out.update(_uneven(dev, stream, steps, torch, shard, precisions, eager))
+        out.update(_uneven(dev, stream, nsteps, torch, shard, precisions, eager, hbm_peak, peak_kind))
     if "gradients" in only:
-        out.update(_gradients(dev, stream, steps, torch, shard, eager))
+        out.update(_gradients(dev, stream, nsteps, torch, shard, eager, hbm_peak, peak_kind))
     if world > 1:
         out["sharding"] = f"instances split over {world} ranks (no data exchange), weak in per-rank time"
     return out
 
 
-def _heat_modes(dev, stream, steps, torch, shard, precisions, eager):
+def _batched_form(tmg, torch, stream, dev, replicas, prec, pv, tau, lamv, Nv, f, u0, u, nsteps, eager, hbm_peak,
+                  peak_kind, n_dofs_all, **kw):
+    """One batched form: setup time, median solve time, per-instance cycles,
+    residuals and errors against the exact FP64 solves, whole-solve roofline."""
+    import numpy as np
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream,
+                   nu1=NU[0], nu2=NU[1], use_graph=not eager, **kw) as B:
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t_setup) * 1e3
+        B.solve(f, u0, u)
+        ms = _time_batch(B, f, u0, u, nsteps, stream, torch)
+        cyc, rel, mx = B.stats()
+        err = B.error_vs_fp64(f, u0, u)
+        info = B.info()
+    nbytes, ops = batched_solve_model(Nv, pv, cyc, prec)
+    ms = replicas.max_over_ranks(ms, dev)
+    kinds = [g["schedule"] for g in info["group_info"]]
+    model = ("mixed: 16 B/DoF start + cycles x (32 B/DoF level 0 + coarse levels) + 16 B/DoF confirmation, per "
+             "instance on its real length and its own cycle count" if prec == "mixed" else
+             "FP64: cycles x (28 + 28 B/DoF level 0 + 4 level vectors per coarse level) and the FP64 operations "
+             "of fp64_ops_per_interval, per instance on its real length and its own cycle count")
+    return {"value": n_dofs_all / (ms * 1e-3), "ms_per_step": round(ms, 3), "solves_timed": nsteps,
+            "precision": prec,
+            "max_cycles": int(replicas.max_over_ranks(mx, dev)),
+            "mean_cycles": round(float(np.mean(cyc)), 2),
+            "max_rel_res": replicas.max_over_ranks(float(rel.max()), dev),
+            "err_vs_fp64": {"max": replicas.max_over_ranks(float(np.max(err)), dev),
+                            "median": float(np.median(err))},
+            "setup_ms": round(setup_ms, 1),
+            "groups": info["groups"], "padded_dofs": info["padded_values"],
+            "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid"),
+            "autotune_whole_batch_ms": {k: (round(v, 3) if v == v else None)
+                                        for k, v in info["whole_batch_ms"].items()},
+            "roofline": whole_solve_roofline(ms, nbytes, ops, hbm_peak, peak_kind, model)}
+
+
+def _heat_modes(dev, stream, nsteps, torch, shard, precisions, eager, hbm_peak, peak_kind):
     import numpy as np
     from paper_1409_5254_gb300 import inputs, replicas, tmg
     out = {}
@@ -474,24 +663,17 @@ def _heat_modes(dev, stream, steps, torch, shard, precisions, eager):
     u = torch.empty_like(f)
     res = {}
     for prec in precisions:
-        with tmg.Batch([p] * n, 1.0 / N, lam, N, precision=prec, tol=TOL, max_cycles=200, stream=stream,
-                       nu1=NU[0], nu2=NU[1], use_graph=not eager) as B:
-            B.solve(f, u0, u)
-            ms = _time_batch(B, f, u0, u, max(1, steps // 10) if prec == "mixed" else 1, stream, torch)
-            cyc, rel, mx = B.stats()
-        ms = replicas.max_over_ranks(ms, dev)
-        mx = replicas.max_over_ranks(mx, dev)
-        worst = replicas.max_over_ranks(float(rel.max()), dev)
-        res[prec] = {"value": n_all * N * (p + 1) / (ms * 1e-3), "ms_per_step": round(ms, 3), "max_cycles": int(mx),
-                     "max_rel_res": worst}
-    out["heat_modes_65536x4096_p1" if BATCH_STRIDE == 1 else f"heat_modes_{n_all}x4096_p1"] = {"unit": "DoF/s", "instances": n_all, "N": N, "p_t": p,
-                                       "lambda_range": [float(lam_all.min()), float(lam_all.max())], **res}
+        res[prec] = _batched_form(tmg, torch, stream, dev, replicas, prec, [p] * n, 1.0 / N, lam, [N] * n, f, u0,
+                                  u, nsteps, eager, hbm_peak, peak_kind, n_all * N * (p + 1))
+    out["heat_modes_65536x4096_p1" if BATCH_STRIDE == 1 else f"heat_modes_{n_all}x4096_p1"] = {
+        "unit": "DoF/s", "instances": n_all, "N": N, "p_t": p,
+        "lambda_range": [float(lam_all.min()), float(lam_all.max())], **res}
     del f, u, u0
     torch.cuda.empty_cache()
     return out
 
 
-def _uneven(dev, stream, steps, torch, shard, precisions, eager):
+def _uneven(dev, stream, nsteps, torch, shard, precisions, eager, hbm_peak, peak_kind):
     from paper_1409_5254_gb300 import inputs, replicas, tmg
     out = {}
     # uneven batch: 10,000 instances, N log-uniform in [2^6, 2^16], p_t in {0..3}, lambda tau in [1e-3, 1e3]
@@ -510,32 +692,15 @@ def _uneven(dev, stream, steps, torch, shard, precisions, eager):
     u = torch.empty_like(f)
     res = {}
     for prec in precisions:
-        torch.cuda.synchronize()
-        t_setup = time.perf_counter()
-        with tmg.Batch(pv, tau, lamv, Nv, precision=prec, tol=TOL, max_cycles=300, stream=stream,
-                       nu1=NU[0], nu2=NU[1], use_graph=not eager) as B:
-            setup_ms = (time.perf_counter() - t_setup) * 1e3
-            B.solve(f, u0, u)
-            ms = _time_batch(B, f, u0, u, max(1, steps // 10), stream, torch)
-            cyc, rel, mx = B.stats()
-            info = B.info()
-        ms = replicas.max_over_ranks(ms, dev)
-        kinds = [g["schedule"] for g in info["group_info"]]
-        res[prec] = {"value": dofs / (ms * 1e-3), "ms_per_step": round(ms, 3),
-                     "max_cycles": int(replicas.max_over_ranks(mx, dev)),
-                     "max_rel_res": replicas.max_over_ranks(float(rel.max()), dev),
-                     "setup_ms_with_autotune": round(setup_ms, 1),
-                     "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid"),
-                     "autotune_whole_batch_ms": {k: (round(v, 3) if v == v else None)
-                                                 for k, v in info["whole_batch_ms"].items()}}
-    out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv_all), "dofs": dofs, "groups": info["groups"],
-                           "padded_dofs": info["padded_values"], **res}
+        res[prec] = _batched_form(tmg, torch, stream, dev, replicas, prec, pv, tau, lamv, Nv, f, u0, u, nsteps,
+                                  eager, hbm_peak, peak_kind, dofs)
+    out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv_all), "dofs": dofs, **res}
     del f, u, u0
     torch.cuda.empty_cache()
     return out
 
 
-def _gradients(dev, stream, steps, torch, shard, eager):
+def _gradients(dev, stream, nsteps, torch, shard, eager, hbm_peak, peak_kind):
     import numpy as np
     from paper_1409_5254_gb300 import inputs, replicas, tmg
     out = {}
@@ -556,31 +721,83 @@ def _gradients(dev, stream, steps, torch, shard, eager):
             e = u.view(n, N, p + 1).sum(dim=2)
             g = ((e - y)[:, :, None].expand(n, N, p + 1)).contiguous().reshape(-1)
             return B.adjoint(g, u)
+        B.solve(f, u0, u)
+        cyc_f, _, _ = B.stats()
+        err_f = B.error_vs_fp64(f, u0, u)
         step()
-        torch.cuda.synchronize()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        k = max(1, steps // 10)
-        start.record(stream)
-        for _ in range(k):
-            step()
-        end.record(stream)
-        end.synchronize()
-        ms = replicas.max_over_ranks(start.elapsed_time(end) / k, dev)
-        cyc, rel, mx = B.stats()
-    out["adjoint_4096x16384_p2"] = {"unit": "DoF/s (forward + adjoint)", "instances": n_all, "N": N, "p_t": p,
-                                    "value": n_all * N * (p + 1) / (ms * 1e-3), "gradients_per_s": 1e3 / ms,
-                                    "ms_per_step": round(ms, 3),
-                                    "adjoint_max_cycles": int(replicas.max_over_ranks(mx, dev)),
-                                    "precision": "mixed", "cycle": f"V{NU}"}
+        cyc_a, rel_a, mx = B.stats()
+        ms = replicas.max_over_ranks(statistics.median(time_each(step, nsteps, stream, torch)), dev)
+    Nv, pv = [N] * n, [p] * n
+    b_f, _ = batched_solve_model(Nv, pv, cyc_f, "mixed")
+    b_a, _ = batched_solve_model(Nv, pv, cyc_a, "mixed")
+    nbytes = b_f + b_a + 16 * n * N * (p + 1)      # + the gradient reductions (read mu, u)
+    out["adjoint_4096x16384_p2"] = {
+        "unit": "DoF/s (forward + adjoint)", "instances": n_all, "N": N, "p_t": p,
+        "value": n_all * N * (p + 1) / (ms * 1e-3), "gradients_per_s": 1e3 / ms,
+        "ms_per_step": round(ms, 3), "solves_timed": nsteps,
+        "forward_max_cycles": int(np.max(cyc_f)),
+        "adjoint_max_cycles": int(replicas.max_over_ranks(mx, dev)),
+        "forward_err_vs_fp64": {"max": float(np.max(err_f)), "median": float(np.median(err_f))},
+        "precision": "mixed", "cycle": f"V{NU}",
+        "roofline": whole_solve_roofline(ms, nbytes, 0, hbm_peak, peak_kind,
+                                         "forward + adjoint solves as the mixed batched model, plus the gradient "
+                                         "reductions (read mu, u: 16 B/DoF); the reversals of g and mu and the "
+                                         "loss gradient in torch are not counted")}
     del f, u, u0, y
     torch.cuda.empty_cache()
     return out
 
 
-def cpu_baseline(sample_N: int = 1 << 21):
-    """The FP64 oracle as it stands (textbook multigrid, one host thread) on the
-    first sample_N intervals of the same workload (same tau, lambda, p_t, forcing)."""
+def _oracle_worker(task):
+    """One host process of the instance-parallel oracle baseline: assemble the
+    load vectors of its instances, then time the oracle's textbook multigrid
+    (the same V-cycle, tolerance and coarsening) and its forward substitution
+    on them, one instance after the other."""
+    import numpy as np
+
+    import oracle
+    from paper_1409_5254_gb300 import inputs
+    items, nu, tol = task
+    Fs = [inputs.load_vector(p, N, T, inputs.Forcing(A, K, T)) for (p, N, T, z, u0, A, K) in items]
+    dofs = sum(N * (p + 1) for (p, N, T, z, u0, A, K) in items)
+    t0 = time.perf_counter()
+    for (p, N, T, z, u0, A, K), F in zip(items, Fs):
+        oracle.mg_solve(p, z, F, u0, tol=tol, max_cycles=300, nu1=nu[0], nu2=nu[1], n_min=64)
+    t_mg = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for (p, N, T, z, u0, A, K), F in zip(items, Fs):
+        oracle.fsub(p, z, F, u0)
+    t_fs = time.perf_counter() - t0
+    return dofs, t_mg, t_fs
+
+
+def _oracle_batch(items, cores: int, note: str):
+    """The oracle over `items` = (p, N, T, z, u0, amps, freqs) instances,
+    instance-parallel over `cores` host processes (spawned: the parent holds a
+    CUDA context), largest instances dealt first round-robin.  The parallel
+    rate is all DoFs over the slowest process's time."""
+    import multiprocessing as mp
+    order = sorted(range(len(items)), key=lambda i: -items[i][1] * (items[i][0] + 1))
+    tasks = [([items[i] for i in order[w::cores]], NU, TOL) for w in range(cores)]
+    tasks = [t for t in tasks if t[0]]
+    with mp.get_context("spawn").Pool(len(tasks)) as pool:
+        res = pool.map(_oracle_worker, tasks)
+    dofs = sum(r[0] for r in res)
+    t_mg = max(r[1] for r in res)
+    t_fs = max(r[2] for r in res)
+    return {"value": dofs / t_mg, "unit": "DoF/s", "cores": len(tasks), "kind": "oracle",
+            "sample": f"{note}; {len(items)} instances, {dofs} DoFs, textbook V{NU} multigrid to {TOL} on every "
+                      f"host core ({t_mg:.2f} s on the slowest)",
+            "single_core_value": dofs / sum(r[1] for r in res),
+            "fsub_value": dofs / t_fs, "fsub_note": "exact forward substitution, same instances and cores"}
+
+
+def cpu_baseline(sample_N: int = 1 << 21, batched: bool = True):
+    """The FP64 oracle as it stands on the GPU machine's host cores.  The long
+    horizon: textbook multigrid, one host thread, on the first sample_N
+    intervals of the same workload (same tau, lambda, p_t, forcing).  The
+    batched workloads: instance-parallel over all host cores on a stated
+    fraction of their instances."""
     import numpy as np
 
     import oracle
@@ -597,10 +814,30 @@ def cpu_baseline(sample_N: int = 1 << 21):
     t0 = time.perf_counter()
     oracle.fsub(P_MAIN, LAM * TAU, F, U0)
     t_fs = time.perf_counter() - t0
-    return {"value": sample_N * d / t_mg, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample_N} of the 2^24 intervals, textbook V{NU} multigrid to 1e-10 ({len(hist) - 1} cycles), "
-                      f"{t_mg:.2f} s",
-            "fsub_value": sample_N * d / t_fs, "fsub_note": "exact forward substitution, same sample"}
+    out = {"value": sample_N * d / t_mg, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {sample_N} of the 2^24 intervals, textbook V{NU} multigrid to 1e-10 ({len(hist) - 1} cycles), "
+                     f"{t_mg:.2f} s",
+           "fsub_value": sample_N * d / t_fs, "fsub_note": "exact forward substitution, same sample"}
+    if batched:
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        b = {}
+        lam, amps, freqs = inputs.heat_modes_batch(2, 256, 4096, 1)
+        sel = range(0, len(lam), 32)
+        b["heat_modes_65536x4096_p1"] = _oracle_batch(
+            [(1, 4096, 1.0, float(lam[i]) / 4096, 0.0, amps[i], freqs[i]) for i in sel], cores,
+            "every 32nd of the 65,536 heat modes")
+        Nv, pv, z = inputs.uneven_batch(3, 10000)
+        A, K = inputs.sinusoid_batch_params(3, len(Nv))
+        b["uneven_10000"] = _oracle_batch(
+            [(int(pv[i]), int(Nv[i]), 1.0, float(z[i]), 1.0, A[i], K[i]) for i in range(0, len(Nv), 10)], cores,
+            "every 10th of the 10,000 uneven instances")
+        lam, u0, _ = inputs.adjoint_problem(4, 4096, 16384, 2)
+        A, K = inputs.sinusoid_batch_params(4, 4096)
+        b["adjoint_4096x16384_p2_forward"] = _oracle_batch(
+            [(2, 16384, 1.0, float(lam[i]) / 16384, float(u0[i]), A[i], K[i]) for i in range(0, 4096, 64)], cores,
+            "forward solves of every 64th of the 4096 gradient instances")
+        out["batched"] = b
+    return out
 
 
 def _sample_load_vector(p, n, T, forcing):

@@ -104,10 +104,10 @@ enum { TMG_SCHED_AUTO = 0, TMG_SCHED_GRID = 1, TMG_SCHED_CTA = 2 };
 void tmg_opts_default(tmg_opts *opts);
 
 /*
- * Build a plan for one problem: degree p_t in 0..5, or p_t = 10 (forward
- * solves only: tmg_adjoint returns TMG_EUNSUPPORTED; the coarsest level is
- * always solved by the grid-wide scan; the mixed form recomputes the level-0
- * residual from u in every cycle, as with update_residual = 0), step tau > 0,
+ * Build a plan for one problem: degree p_t in 0..5, 10 or 20 (the degrees of
+ * the paper's scaling tables; at 10 and 20 the coarsest level is always solved
+ * by the grid-wide scan and the mixed form recomputes the level-0 residual
+ * from u in every cycle, as with update_residual = 0), step tau > 0,
  * lambda >= 0 (finite), N >= 1 intervals.  levels <= 0 picks the hierarchy
  * from opts->n_min; levels >= 1 caps the number of levels.  omega <= 0 uses
  * omega*(alpha(lambda tau_l)) per level (Lemma chap4_lemma7); 0 < omega < 2
@@ -170,7 +170,6 @@ tmg_status tmg_solve_direct(tmg_plan *plan, const double *f, double u0, double *
  * -tau sum_n mu_n^T Mhat u_n (L depends on lambda through lambda*tau*Mhat);
  * dJdu0 and dJdlambda are device doubles.  u must be the forward solution.
  * The first call allocates a 2 N (p_t+1) double buffer owned by the plan.
- * Plans of p_t = 10 have no adjoint kernels: TMG_EUNSUPPORTED.
  */
 tmg_status tmg_adjoint(tmg_plan *plan, const double *g, const double *u, double *dJdf, double *dJdu0,
                        double *dJdlambda);
@@ -213,7 +212,7 @@ tmg_status tmg_stats(const tmg_plan *plan, int *cycles, double *rel_res, double 
  * than opts->n_min of them, and the level cap allows, Section 3's nested
  * meshes); the first level handed to the single-CTA coarse solver; its
  * number of intervals; and *scan_coarsest = 1 when no level fits that solver
- * (or p_t = 10) and the coarsest level is solved by the grid-wide scan
+ * (or p_t = 10, 20) and the coarsest level is solved by the grid-wide scan
  * instead.  Output pointers are host pointers and may be NULL.  Same
  * argument checks and status codes as tmg_setup.
  */
@@ -313,8 +312,12 @@ typedef struct tmg_batch tmg_batch;
  * arrays of length n_inst).  Packed layout of
  * every [instance][interval][coefficient] array: instance i starts at value
  * offset off_i = sum_{j<i} N[j] (p_t[j] + 1).  omega and opts as for
- * tmg_setup (V-cycles only: opts->gamma must be 1; levels coarsen down to at
- * most 64 intervals, solved exactly).  Internally the instances are grouped
+ * tmg_setup (levels coarsen down to at most 64 intervals, solved exactly;
+ * W-cycles, gamma = 2, visit every level below level 0 twice per visit of its
+ * parent: in the grid form the streaming levels down to the first one of at
+ * most 8192 intervals are launched once per visit, and the levels from there
+ * on run in one CTA per instance, whose shared-memory recursion makes its own
+ * visits; the CTA form runs the whole W recursion on chip).  Internally the instances are grouped
  * by p_t and padded at their end to a power-of-two length (the system is
  * causal, so this leaves each instance's solution unchanged); every level
  * kernel then covers all instances of a group still iterating at once.

@@ -33,21 +33,21 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_grads(const double* __rest
                                                             double* __restrict__ partials, unsigned* ticket,
                                                             double* __restrict__ dJdu0,
                                                             double* __restrict__ dJdlambda) {
-    double sk[tmg::kMaxD];
+    double sk[tmg::kMaxDWide];
 #pragma unroll
-    for (int k = 0; k < tmg::kMaxD; ++k) sk[k] = 0.0;
+    for (int k = 0; k < tmg::kMaxDWide; ++k) sk[k] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     for (int64_t n = (int64_t)blockIdx.x * kThreads + threadIdx.x; n < N; n += stride) {
         const double* a = mu + n * d;
         const double* b = u + n * d;
 #pragma unroll
-        for (int k = 0; k < tmg::kMaxD; ++k)
+        for (int k = 0; k < tmg::kMaxDWide; ++k)
             if (k < d) sk[k] = fma(a[k], b[k], sk[k]);
     }
-    __shared__ double red[tmg::kMaxD][kThreads / 32];
+    __shared__ double red[tmg::kMaxDWide][kThreads / 32];
     __shared__ int last;
 #pragma unroll
-    for (int k = 0; k < tmg::kMaxD; ++k) {
+    for (int k = 0; k < tmg::kMaxDWide; ++k) {
         double s = sk[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);

@@ -60,11 +60,10 @@ tmg_status check_setup(int p_t, double tau, double lambda, int64_t N, double ome
         o->n_min < 1 || o->max_cycles < 0 || o->max_cycles >= tmg::kHist || !(o->tol >= 0.0) ||
         o->check_fp64 < 0 || o->check_fp64 > 1)
         return TMG_EINVAL;
-    // p_t <= 5, and p_t = 10 (forward solves; in the mixed form the level-0
-    // residual is recomputed from u in every cycle: no updated float pair)
-    const bool wide = p_t + 1 > tmg::kMaxD;
-    if (wide && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
-    if (wide) o->update_residual = 0;
+    // p_t <= 5, and p_t = 10, 20 (in the mixed form the level-0 residual is
+    // recomputed from u in every cycle: no updated float pair)
+    if (!tmg::built_width(p_t + 1)) return TMG_EUNSUPPORTED;
+    if (p_t + 1 > tmg::kMaxD) o->update_residual = 0;
     return TMG_OK;
 }
 
@@ -262,7 +261,6 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     if (opts) o = *opts;
     const tmg_status cs = check_setup(p_t, tau, lambda, N, omega, &o);
     if (cs != TMG_OK) return cs;
-    const bool wide = p_t + 1 > tmg::kMaxD;   // no adjoint kernels
 
     tmg_plan* P = new (std::nothrow) tmg_plan();
     if (!P) return TMG_ENOMEM;
@@ -287,7 +285,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
         P->own_stream = true;
     }
     P->ops = forward_ops(o, P->d);
-    P->ops_adj = wide ? nullptr : o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 1) : tmg_ops_f64(P->d, 1);
+    P->ops_adj = o.precision == TMG_MIXED ? tmg_ops_f32(P->d, 1) : tmg_ops_f64(P->d, 1);
 
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -343,7 +341,7 @@ tmg_status tmg_setup(tmg_plan** plan, int p_t, double tau, double lambda, int64_
     off = align_up(off + sizeof(tmg::LevelK<double, tmg::kMaxDWide>) * (P->nlev - P->lt), A);
     const size_t off_p = off;
     off = align_up(off + sizeof(double) * P->max_blocks, A);
-    P->scan_tiles = (N + tmg::kScanTile - 1) / tmg::kScanTile;
+    P->scan_tiles = (N + tmg::kScanTileMin - 1) / tmg::kScanTileMin;   // enough for every block width
     const size_t off_scan = off;
     off = align_up(off + sizeof(double) * (3 + 2 * tmg::kScanNT) * P->scan_tiles, A);
     const size_t off_st = off;
@@ -544,7 +542,7 @@ tmg_status tmg_level_constants(int p_t, double z, double omega_user, double* A, 
                                double* alpha, double* omega) {
     if (p_t < 0 || p_t > kMaxDegree || !(z >= 0.0) || !isfinite(z) || !(omega_user < 2.0) || !isfinite(omega_user))
         return TMG_EINVAL;
-    if (p_t + 1 > tmg::kMaxD && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
+    if (!tmg::built_width(p_t + 1)) return TMG_EUNSUPPORTED;
     const int d = p_t + 1;
     tmg_level_host L;
     level_setup(d, z, omega_user, &L);
@@ -563,7 +561,7 @@ tmg_status tmg_level_constants(int p_t, double z, double omega_user, double* A, 
 
 tmg_status tmg_transfer_matrices(int p_t, double* P1, double* P2) {
     if (p_t < 0 || p_t > kMaxDegree || !P1 || !P2) return TMG_EINVAL;
-    if (p_t + 1 > tmg::kMaxD && p_t + 1 != tmg::kMaxDWide) return TMG_EUNSUPPORTED;
+    if (!tmg::built_width(p_t + 1)) return TMG_EUNSUPPORTED;
     transfer_setup(p_t + 1, P1, P2);
     return TMG_OK;
 }

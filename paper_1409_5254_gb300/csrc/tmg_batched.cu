@@ -105,22 +105,22 @@ __global__ void kb_scatter(const double* __restrict__ src, double* __restrict__ 
 __global__ void kb_grads(const double* __restrict__ mu, const double* __restrict__ u, const int64_t* __restrict__ off,
                          const int64_t* __restrict__ Nv, const int* __restrict__ pv, const double* __restrict__ tau,
                          int64_t n_inst, double* __restrict__ dJdu0, double* __restrict__ dJdlambda) {
-    __shared__ double red[kMaxD][kBNT / 32];
+    __shared__ double red[kMaxDWide][kBNT / 32];
     for (int64_t i = blockIdx.x; i < n_inst; i += gridDim.x) {
         const int d = pv[i] + 1;
         const int64_t base = off[i], N = Nv[i];
-        double sk[kMaxD];
+        double sk[kMaxDWide];
 #pragma unroll
-        for (int k = 0; k < kMaxD; ++k) sk[k] = 0.0;
+        for (int k = 0; k < kMaxDWide; ++k) sk[k] = 0.0;
         for (int64_t m = threadIdx.x; m < N; m += kBNT) {
             const double* a = mu + base + m * d;
             const double* b = u + base + m * d;
 #pragma unroll
-            for (int k = 0; k < kMaxD; ++k)
+            for (int k = 0; k < kMaxDWide; ++k)
                 if (k < d) sk[k] = fma(a[k], b[k], sk[k]);
         }
 #pragma unroll
-        for (int k = 0; k < kMaxD; ++k) {
+        for (int k = 0; k < kMaxDWide; ++k) {
             double s = sk[k];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
@@ -161,15 +161,11 @@ __global__ void __launch_bounds__(kBNT) kb_exact_err(const double* __restrict__ 
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t j = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; j < n; j += nw) {
-        const double* k = K + j * KS;
-        double Ai[D * D], g[D], c[D];
-#pragma unroll
-        for (int q = 0; q < D * D; ++q) Ai[q] = k[q];
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-            g[q] = k[D * D + q];
-            c[q] = k[D * D + D + q];
-        }
+        // the constants stay in memory (L1): A^{-1} alone is 441 doubles at D = 21
+        const double* __restrict__ k = K + j * KS;
+        const double* __restrict__ Ai = k;
+        const double* __restrict__ g = k + D * D;
+        const double* __restrict__ c = k + D * D + D;
         const double al = k[D * D + 2 * D];
         const int64_t N = Ni[j];
         const double* Fi = F + off[j];
@@ -259,6 +255,20 @@ cudaError_t launch_cta_any(tmg_batch* B, tmg_batch_group* G, const double* F, do
     return dir == 0 ? launch_cta_d<double, 0>(B, G, F, u, u0) : launch_cta_d<double, 1>(B, G, F, u, u0);
 }
 
+// Shared memory of the on-chip levels from Nt intervals down (nl levels) in
+// the batch's cycle precision.
+size_t tail_bytes_any(const tmg_batch* B, int d, int64_t Nt, int nl) {
+    const bool mixed = B->o.precision == TMG_MIXED;
+    switch (d) {
+        case 1: return mixed ? tail_smem_bytes<float, 1>(Nt, nl) : tail_smem_bytes<double, 1>(Nt, nl);
+        case 2: return mixed ? tail_smem_bytes<float, 2>(Nt, nl) : tail_smem_bytes<double, 2>(Nt, nl);
+        case 3: return mixed ? tail_smem_bytes<float, 3>(Nt, nl) : tail_smem_bytes<double, 3>(Nt, nl);
+        case 4: return mixed ? tail_smem_bytes<float, 4>(Nt, nl) : tail_smem_bytes<double, 4>(Nt, nl);
+        case 5: return mixed ? tail_smem_bytes<float, 5>(Nt, nl) : tail_smem_bytes<double, 5>(Nt, nl);
+        default: return mixed ? tail_smem_bytes<float, 6>(Nt, nl) : tail_smem_bytes<double, 6>(Nt, nl);
+    }
+}
+
 size_t cta_bytes(const tmg_batch* B, const tmg_batch_group* G) {
     const bool mixed = B->o.precision == TMG_MIXED;
     switch (G->d) {
@@ -303,7 +313,7 @@ void fill_tables(const tmg_batch* B, const tmg_batch_group* G, std::vector<char>
             }
         }
         Res0& R = res[j];
-        for (int k = 0; k < kMaxD; ++k) {
+        for (int k = 0; k < kMaxDWide; ++k) {
             R.zm[k] = z / (2.0 * k + 1.0);
             R.zm_hi[k] = (float)R.zm[k];
             R.zm_lo[k] = (float)(R.zm[k] - (double)R.zm_hi[k]);
@@ -318,9 +328,26 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     for (int64_t m = G->Ng; m > nmin && m % 2 == 0 && G->nlev < kMaxLevels; m /= 2) ++G->nlev;
     if ((G->Ng >> (G->nlev - 1)) > 64) return TMG_EUNSUPPORTED;
     G->cta_smem = cta_bytes(B, G);
-    G->cta_ok = G->cta_smem <= kCtaSmemMax && G->nlev <= kTailLevels;
+    G->cta_ok = G->d <= kMaxD && G->cta_smem <= kCtaSmemMax && G->nlev <= kTailLevels;
     G->sched = B->o.schedule == TMG_SCHED_CTA && G->cta_ok ? TMG_SCHED_CTA : TMG_SCHED_GRID;
     G->ms_tune[0] = G->ms_tune[1] = NAN;
+    // W-cycles in the grid form: the first level of at most 8192 intervals
+    // whose levels fit one CTA runs the rest of the recursion on chip
+    G->lt_w = -1;
+    G->tail_smem_w = 0;
+    if (B->o.gamma == 2 && G->nlev > 1) {
+        if (G->d > kMaxD) return TMG_EUNSUPPORTED;   // no on-chip W recursion at the wide degrees
+        for (int l = 1; l < G->nlev; ++l) {
+            const int64_t Nl = G->Ng >> l;
+            const size_t b = tail_bytes_any(B, G->d, Nl, G->nlev - l);
+            if (Nl <= 8192 && G->nlev - l <= kTailLevels && b <= kTailSmemMax) {
+                G->lt_w = l;
+                G->tail_smem_w = b;
+                break;
+            }
+        }
+        if (G->lt_w < 0) return TMG_EUNSUPPORTED;
+    }
     // layout
     const size_t A = 256;
     const int64_t n = G->n, nvals = n * G->Ng * G->d;
@@ -347,25 +374,30 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     off = align_up(off + 4 * n, A);
     const size_t o_res = off;
     off = align_up(off + sizeof(Res0) * n, A);
-    const size_t lk_bytes = (B->o.precision == TMG_MIXED ? sizeof(LevelK<float, kMaxD>) : sizeof(LevelK<double, kMaxD>)) *
-                            (size_t)n * G->nlev;
+    const bool mixed_p = B->o.precision == TMG_MIXED;
+    const size_t lk_one = G->d <= kMaxD ? (mixed_p ? sizeof(LevelK<float, kMaxD>) : sizeof(LevelK<double, kMaxD>))
+                          : G->d == 11 ? (mixed_p ? sizeof(LevelK<float, 11>) : sizeof(LevelK<double, 11>))
+                                       : (mixed_p ? sizeof(LevelK<float, 21>) : sizeof(LevelK<double, 21>));
+    const size_t lk_bytes = lk_one * (size_t)n * G->nlev;
     const size_t o_lk0 = off;
     off = align_up(off + lk_bytes, A);
     const size_t o_lk1 = off;
     off = align_up(off + lk_bytes, A);
     // the mixed form keeps the level-0 residual as updated float pairs, double
     // buffered (high parts here, 16-bit low parts in rl) when it has coarse levels
-    const bool updated = B->o.precision == TMG_MIXED && B->o.update_residual != 0 && G->nlev > 1;
+    const bool updated = B->o.precision == TMG_MIXED && B->o.update_residual != 0 && G->nlev > 1 && G->d <= kMaxD;
     const size_t o_rT = off;
     off = align_up(off + el * nvals * (updated ? 2 : 1), A);
     const size_t o_rl = off;
     if (updated) off = align_up(off + sizeof(short) * nvals * 2, A);
-    size_t o_f[kMaxLevels], o_u[kMaxLevels];
+    size_t o_f[kMaxLevels], o_u[kMaxLevels], o_u2[kMaxLevels];
     for (int l = 1; l < G->nlev; ++l) {
         o_f[l] = off;
         off = align_up(off + el * (nvals >> l), A);
         o_u[l] = off;
         off = align_up(off + el * (nvals >> l), A);
+        o_u2[l] = off;
+        if (l <= G->lt_w) off = align_up(off + el * (nvals >> l), A);
     }
     const size_t o_c0 = off;
     off = align_up(off + (G->nlev == 1 ? el * nvals : 0), A);
@@ -402,6 +434,7 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     for (int l = 1; l < G->nlev; ++l) {
         G->fl[l] = b + o_f[l];
         G->ul[l] = b + o_u[l];
+        G->ul2[l] = l <= G->lt_w ? b + o_u2[l] : nullptr;
     }
     G->c0 = b + o_c0;
     G->d_ids = reinterpret_cast<int64_t*>(b + o_ids);
@@ -433,7 +466,9 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
         case 3: mixed ? fill_tables<float, 3>(B, G, tf, ta, res) : fill_tables<double, 3>(B, G, tf, ta, res); break;
         case 4: mixed ? fill_tables<float, 4>(B, G, tf, ta, res) : fill_tables<double, 4>(B, G, tf, ta, res); break;
         case 5: mixed ? fill_tables<float, 5>(B, G, tf, ta, res) : fill_tables<double, 5>(B, G, tf, ta, res); break;
-        default: mixed ? fill_tables<float, 6>(B, G, tf, ta, res) : fill_tables<double, 6>(B, G, tf, ta, res); break;
+        case 6: mixed ? fill_tables<float, 6>(B, G, tf, ta, res) : fill_tables<double, 6>(B, G, tf, ta, res); break;
+        case 11: mixed ? fill_tables<float, 11>(B, G, tf, ta, res) : fill_tables<double, 11>(B, G, tf, ta, res); break;
+        default: mixed ? fill_tables<float, 21>(B, G, tf, ta, res) : fill_tables<double, 21>(B, G, tf, ta, res); break;
     }
     std::vector<int64_t> Ni(n), offs(n);
     for (int64_t j = 0; j < n; ++j) {
@@ -732,7 +767,9 @@ tmg_status check_fp64(tmg_batch* B, const double* f, const double* u0, const dou
             case 3: kb_exact_err<3><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
             case 4: kb_exact_err<4><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
             case 5: kb_exact_err<5><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
-            default: kb_exact_err<6><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            case 6: kb_exact_err<6><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            case 11: kb_exact_err<11><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
+            default: kb_exact_err<21><<<grid, kBNT, 0, B->s>>>(f, u, u0, G->d_ids, G->d_off, G->d_Ni, G->exk, G->n, B->err_dev); break;
         }
         TB_CUDA(cudaGetLastError());
     }
@@ -753,16 +790,18 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
     tmg_opts o;
     tmg_opts_default(&o);
     if (opts) o = *opts;
-    if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 || o.gamma != 1 ||
+    if (o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 || o.gamma < 1 || o.gamma > 2 ||
         o.check_fp64 < 0 || o.check_fp64 > 1 ||
         o.schedule < TMG_SCHED_AUTO || o.schedule > TMG_SCHED_CTA ||
         (o.precision != TMG_FP64 && o.precision != TMG_MIXED) || o.n_min < 1 || o.max_cycles < 0 ||
         !(o.tol >= 0.0))
         return TMG_EINVAL;
     for (int64_t i = 0; i < n_inst; ++i)
-        if (p_t[i] < 0 || p_t[i] > kMaxD - 1 || !(tau[i] > 0.0) || !isfinite(tau[i]) || !(lambda[i] >= 0.0) ||
+        if (p_t[i] < 0 || p_t[i] > 20 || !(tau[i] > 0.0) || !isfinite(tau[i]) || !(lambda[i] >= 0.0) ||
             !isfinite(lambda[i]) || N[i] < 1)
             return TMG_EINVAL;
+    for (int64_t i = 0; i < n_inst; ++i)
+        if (!built_width(p_t[i] + 1)) return TMG_EUNSUPPORTED;
     tmg_batch* B = new (std::nothrow) tmg_batch();
     if (!B) return TMG_ENOMEM;
     B->n_inst = n_inst;

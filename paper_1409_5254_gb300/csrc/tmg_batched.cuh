@@ -438,6 +438,63 @@ __global__ void __launch_bounds__(kBNT) kb_up(const T* __restrict__ f, const T* 
     }
 }
 
+// W-cycles (gamma = 2): the second visit of level l >= 1 under the same
+// parent visit starts from the first visit's result u_in (as k_down_nz /
+// k_up_nz), over the listed instances, the halo restarting at each instance.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_down_nz(const T* __restrict__ f, const T* __restrict__ u_in,
+                                                   T* __restrict__ fc, int log2N, const LevelK<T, D>* __restrict__ lk,
+                                                   int nlev, int level, Xfer<T, D> X, int nu1, int H,
+                                                   const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
+        const LevelK<T, D> K = lk[inst * nlev + level];
+        T fv[2][D], h[2][D], u[2][D], w[2][D], r[2][D], out[D];
+        load_pair<T, D>(f, q, act, fv);
+        load_pair<T, D>(u_in, q, act, u);
+        presmooth_from<DIR, T, D>(K, fv, h, u, w, nu1, first);
+        residual_tracked<DIR, T, D>(fv, u, w, r, first);
+        restrict_pair<T, D>(X, r, out);
+        if (act && lane >= H) VecIO<T, D>::store(fc + q * D, out);
+    }
+}
+
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kBNT) kb_up_nz(const T* __restrict__ f, const T* __restrict__ u_in,
+                                                 const T* __restrict__ uc, T* __restrict__ u_out, int log2N,
+                                                 const LevelK<T, D>* __restrict__ lk, int nlev, int level,
+                                                 Xfer<T, D> X, int nu1, int nu2, int H,
+                                                 const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int per = 32 - H;
+    const int n_list = st->n_act;
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
+    for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const int64_t q = P.q, inst = P.inst;
+        const bool act = P.inb, first = P.first;
+        const LevelK<T, D> K = lk[inst * nlev + level];
+        T fv[2][D], h[2][D], v[2][D], w[2][D], c[D];
+        load_pair<T, D>(f, q, act, fv);
+        load_pair<T, D>(u_in, q, act, v);
+        load_one<T, D>(uc, q, act, c);
+        presmooth_from<DIR, T, D>(K, fv, h, v, w, nu1, first);
+        prolong_add<T, D>(X, c, v);
+        postsmooth<DIR, T, D>(K, h, v, nu2, first);
+        if (act && lane >= H) store_pair<T, D>(u_out, q, v);
+    }
+}
+
 // Levels l and l+1 of the way down in one kernel, over the listed
 // instances (as k_down2): each lane holds four level-l intervals (a quad,
 // which never straddles an instance), pre-smooths, restricts onto two level
@@ -812,6 +869,36 @@ __global__ void __launch_bounds__(kTailNT) kb_cta_solve(const double* __restrict
         __threadfence();
         st->ticket = 0u;
         st->done = atomicAdd(&st->failed, 0) ? 2 : 1;
+    }
+}
+
+// W-cycles over the grid schedule: the levels from lt down of every listed
+// instance in one CTA's shared memory (the on-chip solver's tail_cycle, whose
+// W recursion runs in place), one CTA per instance at a time.  f: level-lt
+// right-hand sides [n][Nt][D]; u_out receives the corrections; u_init (or
+// nullptr for a zero start) holds the first visit's result on a second visit.
+template <int DIR, typename T, int D>
+__global__ void __launch_bounds__(kTailNT) kb_tail(const T* __restrict__ f, T* __restrict__ u_out,
+                                                   const T* __restrict__ u_init, const LevelK<T, D>* __restrict__ lk,
+                                                   int nlev, int lt, Xfer<T, D> X, int Nt, int nu1, int nu2,
+                                                   int gamma, const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    extern __shared__ __align__(16) unsigned char kb_tail_smem[];
+    const int nl = nlev - lt;
+    const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(kb_tail_smem), Nt, nl);
+    const int64_t nv = (int64_t)Nt * D;
+    const int n_list = st->n_act;
+    for (int64_t j = blockIdx.x; j < n_list; j += gridDim.x) {
+        const int64_t inst = bi.act_list[j];
+        const int64_t off = inst * nv;
+        for (int64_t i = threadIdx.x; i < nv; i += kTailNT) {
+            V.f[0][i] = f[off + i];
+            if (u_init != nullptr) V.u[0][i] = u_init[off + i];
+        }
+        __syncthreads();
+        tail_cycle<DIR, T, D>(V, lk + inst * nlev + lt, X, nl, nu1, nu2, gamma, u_init != nullptr);
+        for (int64_t i = threadIdx.x; i < nv; i += kTailNT) u_out[off + i] = V.u[0][i];
+        __syncthreads();
     }
 }
 

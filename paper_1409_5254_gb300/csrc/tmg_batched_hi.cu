@@ -12,7 +12,7 @@ cudaError_t enqueue_hi_t(tmg_batch* B, tmg_batch_group* G) {
         case 4: return enqueue_cycle<T, 4, DIR>(B, G);
         case 5: return enqueue_cycle<T, 5, DIR>(B, G);
         case 6: return enqueue_cycle<T, 6, DIR>(B, G);
-        default: return cudaErrorInvalidValue;
+        default: return enqueue_wide(B, G, std::is_same<T, float>::value, DIR);
     }
 }
 

@@ -35,6 +35,9 @@ struct tmg_batch_group {
     void* rl;            // updated-residual form: low parts of the residual pairs (two buffers), else nullptr
     void* fl[kMaxLevels];
     void* ul[kMaxLevels];
+    void* ul2[kMaxLevels];   // W-cycles: the corrections of each level's second visit (levels 1..lt_w)
+    int lt_w;                // W-cycles, grid form: first level run by kb_tail (one CTA per instance)
+    size_t tail_smem_w;      // its shared memory
     void* c0;
     int64_t* d_ids;
     int64_t* d_Ni;
@@ -96,6 +99,57 @@ inline int grid_flat(const tmg_batch* B, int64_t n) {
 // Shared-memory ceiling of the CTA-per-instance form.
 constexpr size_t kCtaSmemMax = 200 * 1024;
 
+// One visit of level l >= 1 in a W-cycle over the listed instances (the
+// single-problem w_visit): a first visit starts from zero and writes ul[l], a
+// second (nz) starts from ul[l] and writes ul2[l]; level l+1 is visited twice
+// in between.  From level lt_w on, kb_tail runs the rest of the W recursion
+// in shared memory, one CTA per instance.
+template <typename T, int D, int DIR>
+void w_visit_b(tmg_batch* B, tmg_batch_group* G, int l, bool nz, const Xfer<T, D>& X) {
+    const int nu1 = B->o.nu1, nu2 = B->o.nu2;
+    const LevelK<T, D>* lk = static_cast<const LevelK<T, D>*>(G->lk[DIR]);
+    const int L = G->nlev;
+    T* ua = static_cast<T*>(G->ul[l]);
+    T* ub = static_cast<T*>(G->ul2[l]);
+    if (l == G->lt_w) {
+        static PerDevice<cudaError_t> attr_c;
+        attr_c.get([&] {
+            return cudaFuncSetAttribute(kb_tail<DIR, T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kTailSmemMax);
+        });
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(G->n, B->max_blocks / 4));
+        kb_tail<DIR, T, D><<<grid, kTailNT, G->tail_smem_w, G->s>>>(
+            static_cast<const T*>(G->fl[l]), nz ? ub : ua, nz ? (const T*)ua : nullptr, lk, L, l, X,
+            (int)(G->Ng >> l), nu1, nu2, 2, G->st, G->bi);
+        return;
+    }
+    const int64_t nch = G->n * (G->Ng >> l) / 2;
+    if (nz) {
+        const int H = halo(nu1 + 1);
+        kb_down_nz<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+            static_cast<const T*>(G->fl[l]), (const T*)ua, static_cast<T*>(G->fl[l + 1]), G->log2Ng - l, lk, L, l, X,
+            nu1, H, G->st, G->bi);
+    } else {
+        const int H = halo(sw_down(nu1));
+        kb_down<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+            static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 1]), nch, G->log2Ng - l, lk, L, l, X, nu1, H,
+            G->st, G->bi);
+    }
+    w_visit_b<T, D, DIR>(B, G, l + 1, false, X);
+    w_visit_b<T, D, DIR>(B, G, l + 1, true, X);
+    const T* uc = static_cast<const T*>(G->ul2[l + 1]);
+    if (nz) {
+        const int H = halo(nu1 + nu2);
+        kb_up_nz<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+            static_cast<const T*>(G->fl[l]), (const T*)ua, uc, ub, G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st,
+            G->bi);
+    } else {
+        const int H = halo(sw_up(nu1, nu2));
+        kb_up<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
+            static_cast<const T*>(G->fl[l]), uc, ua, nch, G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+    }
+}
+
 template <typename T, int D, int DIR>
 cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
     const int nu1 = B->o.nu1, nu2 = B->o.nu2;
@@ -105,7 +159,7 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
         X.P2[i] = (T)0;
     }
     {
-        double P1[kMaxD * kMaxD], P2[kMaxD * kMaxD];
+        double P1[kMaxDWide * kMaxDWide], P2[kMaxDWide * kMaxDWide];
         tmg_host::transfer_setup(D, P1, P2);
         for (int i = 0; i < D * D; ++i) {
             X.P1[i] = (T)(DIR == 0 ? P1[i] : P2[i]);
@@ -135,23 +189,35 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
                                                                (int)(G->Ng * D), G->st, G->bi);
         return cudaGetLastError();
     }
+    // W-cycle: level 1 is visited twice (streaming levels down to lt_w, then
+    // kb_tail); the level-0 way up reads the correction of the second visit
+    const bool wcycle = B->o.gamma == 2;
+    if constexpr (D <= kMaxD) {   // (wider groups run V-cycles only: the set-up rejects W for them)
+        if (wcycle) {
+            w_visit_b<T, D, DIR>(B, G, 1, false, X);
+            w_visit_b<T, D, DIR>(B, G, 1, true, X);
+        }
+    }
+    const T* uc1 = static_cast<const T*>(wcycle ? G->ul2[1] : G->ul[1]);
     // streaming levels 1 .. L-2, two per kernel where two remain (default for
     // FP32 cycles, as in the single-problem solver)
-    const bool fuse = B->o.fuse_levels > 0 || (B->o.fuse_levels < 0 && std::is_same<T, float>::value);
+    const bool fuse = D <= kMaxD && (B->o.fuse_levels > 0 || (B->o.fuse_levels < 0 && std::is_same<T, float>::value));
     int grp[kMaxLevels], ng = 0;
-    for (int l = 1; l < L - 1;) {
+    for (int l = 1; !wcycle && l < L - 1;) {
         const bool two = fuse && l + 1 < L - 1;
         grp[ng++] = two ? -l : l;      // negative: levels l and l+1 in one kernel
         l += two ? 2 : 1;
     }
     for (int g = 0; g < ng; ++g) {
         if (grp[g] < 0) {
-            const int l = -grp[g];
-            const int H = halo(halo(sw_down(nu1)) + sw_down(nu1));
-            const int64_t nq = n * (G->Ng >> l) / 4;
-            kb_down2<DIR, T, D><<<grid_tiles(B, nq, H), kBNT, 0, G->s>>>(
-                static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 2]), G->log2Ng - l, lk, L, l, X, nu1, H,
-                G->st, G->bi);
+            if constexpr (D <= kMaxD) {
+                const int l = -grp[g];
+                const int H = halo(halo(sw_down(nu1)) + sw_down(nu1));
+                const int64_t nq = n * (G->Ng >> l) / 4;
+                kb_down2<DIR, T, D><<<grid_tiles(B, nq, H), kBNT, 0, G->s>>>(
+                    static_cast<const T*>(G->fl[l]), static_cast<T*>(G->fl[l + 2]), G->log2Ng - l, lk, L, l, X, nu1,
+                    H, G->st, G->bi);
+            }
         } else {
             const int l = grp[g];
             const int H = halo(sw_down(nu1));
@@ -161,19 +227,22 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
                 nu1, H, G->st, G->bi);
         }
     }
-    kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(static_cast<const T*>(G->fl[L - 1]),
-                                                                   static_cast<T*>(G->ul[L - 1]), n,
-                                                                   (int)(G->Ng >> (L - 1)), lk, L, L - 1, G->st,
-                                                                   G->bi);
+    if (!wcycle)
+        kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(static_cast<const T*>(G->fl[L - 1]),
+                                                                       static_cast<T*>(G->ul[L - 1]), n,
+                                                                       (int)(G->Ng >> (L - 1)), lk, L, L - 1, G->st,
+                                                                       G->bi);
     for (int g = ng - 1; g >= 0; --g) {
         if (grp[g] < 0) {
-            const int l = -grp[g];
-            const int g1 = halo(sw_down(nu1)) + sw_up(nu1, nu2);
-            const int H = (2 * g1 + nu2 + 3) / 4;
-            const int64_t nq = n * (G->Ng >> l) / 4;
-            kb_up2<DIR, T, D><<<grid_tiles(B, nq, H), kBNT, 0, G->s>>>(
-                static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 2]), static_cast<T*>(G->ul[l]),
-                G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+            if constexpr (D <= kMaxD) {
+                const int l = -grp[g];
+                const int g1 = halo(sw_down(nu1)) + sw_up(nu1, nu2);
+                const int H = (2 * g1 + nu2 + 3) / 4;
+                const int64_t nq = n * (G->Ng >> l) / 4;
+                kb_up2<DIR, T, D><<<grid_tiles(B, nq, H), kBNT, 0, G->s>>>(
+                    static_cast<const T*>(G->fl[l]), static_cast<const T*>(G->ul[l + 2]), static_cast<T*>(G->ul[l]),
+                    G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
+            }
         } else {
             const int l = grp[g];
             const int H = halo(sw_up(nu1, nu2));
@@ -183,12 +252,12 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
                 G->log2Ng - l, lk, L, l, X, nu1, nu2, H, G->st, G->bi);
         }
     }
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value && D <= kMaxD) {
         if (rl != nullptr) {
             const int H = halo(sw_up(nu1, nu2) + 1 + sw_down(nu1));
             const int64_t nch = n * G->Ng / 2;
             kb_updown0<DIR, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(
-                rT, rl, static_cast<const float*>(G->ul[1]), static_cast<float*>(G->fl[1]), nch, G->log2Ng, lk,
+                rT, rl, reinterpret_cast<const float*>(uc1), static_cast<float*>(G->fl[1]), nch, G->log2Ng, lk,
                 G->res, L, X, nu1, nu2, H, G->st, G->bi);
             kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n, kFinUpdated);
             return cudaGetLastError();
@@ -197,7 +266,7 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
     {
         const int H = halo(sw_up(nu1, nu2));
         const int64_t nch = n * G->Ng / 2;
-        kb_up0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(rT, static_cast<const T*>(G->ul[1]), nch,
+        kb_up0<DIR, T, D><<<grid_tiles(B, nch, H), kBNT, 0, G->s>>>(rT, uc1, nch,
                                                                      G->log2Ng, lk, L, X, nu1, nu2, H, G->st, G->bi);
     }
     return cudaGetLastError();
@@ -206,7 +275,7 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
 template <typename T, int D, int DIR>
 cudaError_t launch_cta(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0) {
     Xfer<T, D> X;
-    double P1[kMaxD * kMaxD], P2[kMaxD * kMaxD];
+    double P1[kMaxDWide * kMaxDWide], P2[kMaxDWide * kMaxDWide];
     tmg_host::transfer_setup(D, P1, P2);
     for (int i = 0; i < D * D; ++i) {   // reversed time swaps the halves
         X.P1[i] = (T)(DIR == 0 ? P1[i] : P2[i]);
@@ -229,8 +298,10 @@ cudaError_t launch_cta(tmg_batch* B, tmg_batch_group* G, const double* F, double
     return cudaGetLastError();
 }
 
-// The same for D = 4..6 (tmg_batched_hi.cu).
+// The same for D = 4..6 (tmg_batched_hi.cu) and for D = 11, 21 (tmg_batched_wide.cu:
+// per-level kernels only, the level-0 residual recomputed from u, V-cycles).
 cudaError_t enqueue_hi(tmg_batch* B, tmg_batch_group* G, bool mixed, int dir);
+cudaError_t enqueue_wide(tmg_batch* B, tmg_batch_group* G, bool mixed, int dir);
 cudaError_t launch_cta_hi(tmg_batch* B, tmg_batch_group* G, const double* F, double* u, const double* u0,
                           bool mixed, int dir);
 

@@ -143,7 +143,7 @@ struct Impl {
     static void enqueue_scan(tmg_plan* P, const TIO* f, TIO* x, int l, S e0, const double* e0p,
                              const DevState* st) {
         const int64_t N = P->lev[l].N;
-        const int64_t nt = (N + kScanTile - 1) / kScanTile;
+        const int64_t nt = (N + scan_tile<D>() - 1) / scan_tile<D>();
         S* aggA = static_cast<S*>(P->scan_ws);
         S* aggB = aggA + nt;
         S* ein = aggB + nt;

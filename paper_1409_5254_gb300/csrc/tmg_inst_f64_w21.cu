@@ -1,0 +1,13 @@
+// Explicit instantiation of the plain FP64 solver for p_t = 20 (21 x 21 blocks),
+// forward and adjoint, with the same restrictions as p_t = 10: per-level
+// kernels, the coarsest level by the grid-wide scan (four intervals per thread
+// chunk at this width), and k_down0 loading its inputs without shared-memory
+// stages.
+#include "tmg_impl.cuh"
+
+const tmg_ops* tmg_ops_f64_w21(int d, int dir) {
+    switch (d) {
+        case 21: return dir == 0 ? tmg::Impl<double, 21, 0>::ops() : tmg::Impl<double, 21, 1>::ops();
+        default: return nullptr;
+    }
+}

@@ -29,8 +29,12 @@
 
 namespace tmg {
 
-constexpr int kMaxD = 6;          // p_t <= 5: every form, the adjoint and the batched solve
-constexpr int kMaxDWide = 11;     // p_t = 10: the plain FP64 forward solve of one problem
+constexpr int kMaxD = 6;          // p_t <= 5: every kernel (two-level kernels, on-chip solver, fused level 0)
+constexpr int kMaxDWide = 21;     // p_t = 10 and 20 (D = 11, 21): the per-level kernels and the grid-wide scan
+
+// Block widths the library builds: p_t = 0..5, 10 and 20 (the degrees of the
+// paper's scaling tables).
+constexpr bool built_width(int d) { return (d >= 1 && d <= kMaxD) || d == 11 || d == kMaxDWide; }
 constexpr int kMaxLevels = 48;
 constexpr int kHist = 512;
 constexpr unsigned kFull = 0xffffffffu;
@@ -302,7 +306,7 @@ __device__ __forceinline__ void presmooth_zero(const LevelK<T, D>& K, const T (&
 // A^{-1} f.  The same sweep as presmooth_zero's after its first.
 template <int DIR, typename T, int D>
 __device__ __forceinline__ void presmooth_from(const LevelK<T, D>& K, const T (&f)[2][D], T (&h)[2][D],
-                                               T (&u)[2][D], T (&w)[2][D], int nu1) {
+                                               T (&u)[2][D], T (&w)[2][D], int nu1, bool first = false) {
     const T om = K.omega, om1 = T(1) - K.omega;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -311,7 +315,8 @@ __device__ __forceinline__ void presmooth_from(const LevelK<T, D>& K, const T (&
     }
     for (int s = 0; s < nu1; ++s) {
         const T e0 = bval<DIR, T, D>(u[0]);
-        const T ep = shfl_prev(bval<DIR, T, D>(u[1]));
+        const T ep_s = shfl_prev(bval<DIR, T, D>(u[1]));
+        const T ep = first ? T(0) : ep_s;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             u[0][k] = om1 * u[0][k] + om * fma(K.g[k], ep, h[0][k]);
@@ -526,22 +531,31 @@ __device__ __forceinline__ void residual0(const double (&F)[D], const double (&u
             if constexpr (D > 3) r[3] = fma(-R.zm[3], u[3], fma(2.0, u[0] + u[2], F[3] - sm));
         }
     } else if constexpr (DIR == 0) {
-        // S_k = sum of u[l], l < k, l of the other parity; a_k = (-1)^k
+        // S_k = sum of u[l], l < k, l of the other parity, as running sums
+        // S_k = S_{k-2} + u[k-1] (one add per coefficient); a_k = (-1)^k
         const double sm = ep + E;
+        double s_even = 0.0, s_odd = 0.0;    // S_k for even k / odd k
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            double sk = 0.0;
-#pragma unroll
-            for (int l = k - 1; l >= 0; l -= 2) sk += u[l];
+            double sk;
+            if (k & 1) {
+                s_odd = k >= 1 ? s_odd + u[k - 1] : s_odd;
+                sk = s_odd;
+            } else {
+                s_even = k >= 2 ? s_even + u[k - 1] : s_even;
+                sk = s_even;
+            }
             r[k] = fma(-R.zm[k], u[k], fma(2.0, sk, F[k] + ((k & 1) ? -sm : dp)));
         }
     } else {
+        // T_k = sum of u[l], l > k, l of the other parity: T_k = T_{k+2} + u[k+1]
         double t[D];
+        double t_next[2] = {0.0, 0.0};       // T_{k+2} for the two parities of k
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            t[k] = 0.0;
-#pragma unroll
-            for (int l = k + 1; l < D; l += 2) t[k] += u[l];
+        for (int k = D - 1; k >= 0; --k) {
+            const double tk = k + 1 < D ? t_next[k & 1] + u[k + 1] : 0.0;
+            t[k] = tk;
+            t_next[k & 1] = tk;
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) r[k] = fma(-R.zm[k], u[k], fma(2.0, t[k], F[k] + dp));
@@ -1155,10 +1169,19 @@ __global__ void __launch_bounds__(kNT) k_up2(const T* __restrict__ f, const T* _
 // ||r||^2 for the stopping test, r stored in the cycle precision T; then,
 // when fc != nullptr, the zero-guess pre-smoothing, residual and restriction
 // of the correction equation L c = r onto level 1.
+// k_down0 stages its u and F pairs through shared memory (cp.async, two
+// stages) up to D = 6.  Wider blocks load them straight from global memory:
+// at D = 11 the stages take 180 KB per block, one block of 8 warps per SM,
+// too few to hide the latency; at D = 21 they would take 344 KB.
+template <int D>
+__host__ __device__ constexpr bool k_down0_staged() {
+    return D <= kMaxD;
+}
+
 // Dynamic shared memory of k_down0: 2 stages x (u, F) x 32 lanes x 2*D doubles per warp.
 template <int D>
-constexpr size_t k_down0_smem_bytes() {
-    return (size_t)(kNT / 32) * 2 * 2 * 32 * (2 * D * 8);
+__host__ __device__ constexpr size_t k_down0_smem_bytes() {
+    return k_down0_staged<D>() ? (size_t)(kNT / 32) * 2 * 2 * 32 * (2 * D * 8) : 0;
 }
 
 // The main loop of k_down0; FP64NORM selects the norm arithmetic at compile
@@ -1187,36 +1210,43 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restri
     float ssf = 0.f;
     int64_t tw = ((int64_t)blockIdx.x * kNT + threadIdx.x) >> 5;
     int sb = 0;
-    if (tw < ntiles) {
-        const int64_t q = tw * per + lane - H;
-        const bool inb = q >= 0 && q < nchunks;
-        Stage::issue(stage[wib][0][0], uu, q * 2 * D, inb, lane);
-        Stage::issue(stage[wib][0][1], F, q * 2 * D, inb, lane);
+    if constexpr (k_down0_staged<D>()) {
+        if (tw < ntiles) {
+            const int64_t q = tw * per + lane - H;
+            const bool inb = q >= 0 && q < nchunks;
+            Stage::issue(stage[wib][0][0], uu, q * 2 * D, inb, lane);
+            Stage::issue(stage[wib][0][1], F, q * 2 * D, inb, lane);
+        }
+        cp_async_commit();
     }
-    cp_async_commit();
     for (; tw < ntiles; tw += nwarps) {
         const int64_t q = tw * per + lane - H;
         const bool inb = q >= 0 && q < nchunks;
         const bool own = inb && lane >= H;
-        {   // prefetch the warp's next tile
-            const int64_t qn = (tw + nwarps) * per + lane - H;
-            const bool nb = tw + nwarps < ntiles && qn >= 0 && qn < nchunks;
-            Stage::issue(stage[wib][sb ^ 1][0], uu, qn * 2 * D, nb, lane);
-            Stage::issue(stage[wib][sb ^ 1][1], F, qn * 2 * D, nb, lane);
-            cp_async_commit();
-        }
-        cp_async_wait_prev();
-        double uvf[2 * D], Fvf[2 * D];
-        Stage::template read<double, 2 * D>(stage[wib][sb][0], lane, uvf);
-        Stage::template read<double, 2 * D>(stage[wib][sb][1], lane, Fvf);
-        sb ^= 1;
         double uv[2][D], Fv[2][D];
+        if constexpr (k_down0_staged<D>()) {
+            {   // prefetch the warp's next tile
+                const int64_t qn = (tw + nwarps) * per + lane - H;
+                const bool nb = tw + nwarps < ntiles && qn >= 0 && qn < nchunks;
+                Stage::issue(stage[wib][sb ^ 1][0], uu, qn * 2 * D, nb, lane);
+                Stage::issue(stage[wib][sb ^ 1][1], F, qn * 2 * D, nb, lane);
+                cp_async_commit();
+            }
+            cp_async_wait_prev();
+            double uvf[2 * D], Fvf[2 * D];
+            Stage::template read<double, 2 * D>(stage[wib][sb][0], lane, uvf);
+            Stage::template read<double, 2 * D>(stage[wib][sb][1], lane, Fvf);
+            sb ^= 1;
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            uv[0][k] = uvf[k];
-            uv[1][k] = uvf[D + k];
-            Fv[0][k] = Fvf[k];
-            Fv[1][k] = Fvf[D + k];
+            for (int k = 0; k < D; ++k) {
+                uv[0][k] = uvf[k];
+                uv[1][k] = uvf[D + k];
+                Fv[0][k] = Fvf[k];
+                Fv[1][k] = Fvf[D + k];
+            }
+        } else {
+            load_pair<double, D>(uu, q, inb, uv);
+            load_pair<double, D>(F, q, inb, Fv);
         }
         T rt[2][D];
         short rtl[2][D];     // low parts of the float-pair residual (mixed form), encoded
@@ -1295,7 +1325,7 @@ __device__ __forceinline__ double down0_loop(T* __restrict__ rT, short* __restri
             if (own) VecIO<T, D>::store(fc + q * D, out);
         }
     }
-    cp_async_wait_all();
+    if constexpr (k_down0_staged<D>()) cp_async_wait_all();
     if constexpr (!FP64NORM) ss = (double)ssf / ((double)nsc * (double)nsc);
     return ss;
 }

@@ -134,8 +134,10 @@ const tmg_ops* tmg_ops_f32(int d, int dir);
 const tmg_ops* tmg_ops_f64(int d, int dir);
 const tmg_ops* tmg_ops_f32_hi(int d, int dir);   // d = 4..6
 const tmg_ops* tmg_ops_f64_hi(int d, int dir);
-const tmg_ops* tmg_ops_f32_wide(int d, int dir);   // d = 11, forward only (nullptr otherwise)
-const tmg_ops* tmg_ops_f64_wide(int d, int dir);   // d = 11, forward only (nullptr otherwise)
+const tmg_ops* tmg_ops_f32_wide(int d, int dir);   // d = 11 (then tmg_ops_f32_w21)
+const tmg_ops* tmg_ops_f64_wide(int d, int dir);
+const tmg_ops* tmg_ops_f32_w21(int d, int dir);    // d = 21 (nullptr otherwise)
+const tmg_ops* tmg_ops_f64_w21(int d, int dir);
 
 // Adjoint helpers (tmg_adjoint.cu): reverse the interval order of an [N][d]
 // array, and the gradient reductions dJ/du0 = a^T mu_0,

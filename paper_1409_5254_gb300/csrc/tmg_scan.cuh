@@ -23,8 +23,21 @@
 namespace tmg {
 
 constexpr int kScanNT = 256;
-constexpr int kScanPT = 8;
-constexpr int kScanTile = kScanNT * kScanPT;
+constexpr int kScanPT = 8;                    // tile maps per thread in the prefix pass
+constexpr int kScanTileMin = kScanNT * 4;     // the smallest tile: the host sizes the scan workspace with it
+
+// Intervals per thread chunk: 8, or 4 for blocks wider than 11 coefficients
+// (a tile of 256 x 8 intervals of 21 FP64 coefficients would need 346 KB of
+// shared memory).
+template <int D>
+__host__ __device__ constexpr int scan_pt() {
+    return D > 11 ? 4 : 8;
+}
+
+template <int D>
+__host__ __device__ constexpr int scan_tile() {
+    return kScanNT * scan_pt<D>();
+}
 
 template <typename S, int D>
 struct ScanK {
@@ -36,19 +49,20 @@ struct ScanK {
 
 template <int D, typename TIn>
 constexpr size_t scan_smem_bytes() {
-    return (size_t)kScanNT * (kScanPT * D + 1) * sizeof(TIn);
+    return (size_t)kScanNT * (scan_pt<D>() * D + 1) * sizeof(TIn);
 }
 
-// Stage the tile [t0, t0 + kScanTile) of f (values beyond N read as 0) into
+// Stage the tile [t0, t0 + scan_tile<D>()) of f (values beyond N read as 0) into
 // shared memory, padded by one element per thread chunk (bank spread).
 template <int D, typename TIn>
 __device__ __forceinline__ void scan_stage(const TIn* __restrict__ f, int64_t N, int64_t t0, TIn* sm) {
+    constexpr int PT = scan_pt<D>();
     const int64_t base = t0 * D;
     const int64_t total = N * D;
-    for (int i = threadIdx.x; i < kScanTile * D; i += kScanNT) {
+    for (int i = threadIdx.x; i < scan_tile<D>() * D; i += kScanNT) {
         const int64_t gi = base + i;
-        const int t = i / (kScanPT * D), j = i - t * (kScanPT * D);
-        sm[t * (kScanPT * D + 1) + j] = gi < total ? f[gi] : TIn(0);
+        const int t = i / (PT * D), j = i - t * (PT * D);
+        sm[t * (PT * D + 1) + j] = gi < total ? f[gi] : TIn(0);
     }
     __syncthreads();
 }
@@ -56,11 +70,11 @@ __device__ __forceinline__ void scan_stage(const TIn* __restrict__ f, int64_t N,
 // Map of this thread's chunk: e_out = A e_in + B.
 template <typename S, int D, typename TIn>
 __device__ __forceinline__ void chunk_map(const ScanK<S, D>& K, const TIn* sm, S& A, S& B) {
-    const TIn* p = sm + threadIdx.x * (kScanPT * D + 1);
+    const TIn* p = sm + threadIdx.x * (scan_pt<D>() * D + 1);
     A = S(1);
     B = S(0);
 #pragma unroll
-    for (int i = 0; i < kScanPT; ++i) {
+    for (int i = 0; i < scan_pt<D>(); ++i) {
         S beta = S(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) beta = fma(K.c[k], (S)p[i * D + k], beta);
@@ -123,9 +137,9 @@ __global__ void __launch_bounds__(kScanNT) k_scan_tiles(const TIn* __restrict__ 
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char scan_sm[];
     TIn* sm = reinterpret_cast<TIn*>(scan_sm);
-    const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
+    const int64_t ntiles = (N + scan_tile<D>() - 1) / scan_tile<D>();
     for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
-        scan_stage<D, TIn>(f, N, b * kScanTile, sm);
+        scan_stage<D, TIn>(f, N, b * scan_tile<D>(), sm);
         S A, B, eA, eB, tA, tB;
         chunk_map<S, D, TIn>(K, sm, A, B);
         block_scan_maps<S>(A, B, eA, eB, tA, tB);
@@ -182,14 +196,15 @@ __global__ void __launch_bounds__(kScanNT) k_scan_apply(const TIn* __restrict__ 
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char scan_sm[];
     TIn* sm = reinterpret_cast<TIn*>(scan_sm);
-    const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
+    constexpr int PT = scan_pt<D>();
+    const int64_t ntiles = (N + scan_tile<D>() - 1) / scan_tile<D>();
     for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
-        const int64_t t0 = b * kScanTile;
+        const int64_t t0 = b * scan_tile<D>();
         scan_stage<D, TIn>(f, N, t0, sm);
         S e = fma(thrA[b * kScanNT + threadIdx.x], ein[b], thrB[b * kScanNT + threadIdx.x]);
-        TIn* p = sm + threadIdx.x * (kScanPT * D + 1);   // this thread's chunk; results overwrite it
+        TIn* p = sm + threadIdx.x * (PT * D + 1);   // this thread's chunk; results overwrite it
 #pragma unroll
-        for (int i = 0; i < kScanPT; ++i) {
+        for (int i = 0; i < PT; ++i) {
             S x[D], beta = S(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) beta = fma(K.c[k], (S)p[i * D + k], beta);
@@ -207,10 +222,10 @@ __global__ void __launch_bounds__(kScanNT) k_scan_apply(const TIn* __restrict__ 
         __syncthreads();
         // coalesced write-back of the tile
         const int64_t total = N * D;
-        for (int i = threadIdx.x; i < kScanTile * D; i += kScanNT) {
+        for (int i = threadIdx.x; i < scan_tile<D>() * D; i += kScanNT) {
             const int64_t gi = t0 * D + i;
-            const int t = i / (kScanPT * D), j = i - t * (kScanPT * D);
-            if (gi < total) u[gi] = (TOut)sm[t * (kScanPT * D + 1) + j];
+            const int t = i / (PT * D), j = i - t * (PT * D);
+            if (gi < total) u[gi] = (TOut)sm[t * (PT * D + 1) + j];
         }
         __syncthreads();
     }

@@ -100,7 +100,44 @@ inline void level_setup(int d, double z, double omega_user, tmg_level_host* L) {
 // argument is (x - 1)/2 on the first half and (x + 1)/2 on the second, so the
 // columns follow from composing P_k with that affine map and converting the
 // monomial coefficients back to the Legendre basis (exact polynomial algebra).
+// For blocks wider than 11 coefficients the monomial route loses digits (the
+// monomial coefficients of P_20 reach 1e5 and cancel), so the columns come
+// from the three-term recurrence written in the Legendre basis itself:
+// P_{k+1}(y) = ((2k+1) y P_k(y) - k P_{k-1}(y)) / (k+1) with y = (x -+ 1)/2,
+// where multiplying a Legendre series by x maps coefficient c_i to
+// (i+1)/(2i+1) on P_{i+1} and i/(2i+1) on P_{i-1}.
+inline void transfer_setup_recurrence(int d, double* P1, double* P2) {
+    constexpr int M = tmg::kMaxDWide;
+    for (int half = 0; half < 2; ++half) {
+        const double shift = half == 0 ? -1.0 : 1.0;
+        double* P = half == 0 ? P1 : P2;
+        double prev[M + 1] = {0}, cur[M + 1] = {0};
+        cur[0] = 1.0;                          // P_0
+        for (int k = 0; k < d; ++k) {
+            for (int j = 0; j < d; ++j) P[j * d + k] = j <= k ? cur[j] : 0.0;
+            if (k + 1 == d) break;
+            double y[M + 1] = {0};            // y * (series cur), y = (x + shift) / 2
+            for (int j = 0; j <= k + 1 && j < M; ++j) {
+                double xv = 0.0;
+                if (j >= 1) xv += cur[j - 1] * j / (2.0 * j - 1.0);
+                if (j + 1 <= k) xv += cur[j + 1] * (j + 1.0) / (2.0 * j + 3.0);
+                y[j] = 0.5 * (xv + shift * cur[j]);
+            }
+            double next[M + 1] = {0};
+            for (int j = 0; j <= k + 1 && j < M; ++j) next[j] = ((2.0 * k + 1.0) * y[j] - k * prev[j]) / (k + 1.0);
+            for (int j = 0; j < M; ++j) {
+                prev[j] = cur[j];
+                cur[j] = next[j];
+            }
+        }
+    }
+}
+
 inline void transfer_setup(int d, double* P1, double* P2) {
+    if (d > 11) {
+        transfer_setup_recurrence(d, P1, P2);
+        return;
+    }
     constexpr int M = tmg::kMaxDWide;
     double leg[M][M] = {{0}};   // monomial coefficients of P_0..P_{d-1}
     leg[0][0] = 1.0;

@@ -47,7 +47,7 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
         st = lib.tmg_setup(ctypes.byref(h), p, tau, lam, N, 0, 0.0, None, None)
         assert st == tmg.TMG_EINVAL, (p, tau, lam, N, st)
     # degrees up to 20 that are not built
-    for p in (6, 9, 11, 20):
+    for p in (6, 9, 11, 19):
         st = lib.tmg_setup(ctypes.byref(h), p, 0.1, 1.0, 16, 0, 0.0, None, None)
         assert st == tmg.TMG_EUNSUPPORTED, (p, st)
     st = lib.tmg_setup(ctypes.byref(h), 1, 0.1, 1.0, 16, 0, 2.5, None, None)
@@ -56,8 +56,8 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu():
 
 def test_batched_setup_rejects_bad_arguments_before_touching_the_gpu():
     """tmg_setup_batched validates every instance and the options on the host:
-    degrees 0..5 only, tau > 0, lambda >= 0 (finite), N >= 1, V-cycles only,
-    a known schedule, omega < 2."""
+    degrees 0..5, 10 and 20 (other degrees up to 20 are unsupported), tau > 0,
+    lambda >= 0 (finite), N >= 1, V- or W-cycles, a known schedule, omega < 2."""
     import numpy as np
     lib = tmg._lib()
     h = ctypes.c_void_p()
@@ -79,8 +79,7 @@ def test_batched_setup_rejects_bad_arguments_before_touching_the_gpu():
 
     ok = ([1, 2], [0.1, 0.1], [1.0, 2.0], [64, 128])
     bad_instances = [
-        ([1, 6], [0.1, 0.1], [1.0, 2.0], [64, 128]),       # p_t = 6 (batches go to 5)
-        ([1, 10], [0.1, 0.1], [1.0, 2.0], [64, 128]),      # p_t = 10 (single problems only)
+        ([1, 21], [0.1, 0.1], [1.0, 2.0], [64, 128]),      # p_t = 21 (degrees go to 20)
         ([1, -1], [0.1, 0.1], [1.0, 2.0], [64, 128]),
         ([1, 2], [0.1, 0.0], [1.0, 2.0], [64, 128]),       # tau = 0
         ([1, 2], [0.1, 0.1], [1.0, -2.0], [64, 128]),      # lambda < 0
@@ -89,8 +88,10 @@ def test_batched_setup_rejects_bad_arguments_before_touching_the_gpu():
     ]
     for args in bad_instances:
         assert call(*args) == tmg.TMG_EINVAL, args
+    for p in (6, 9, 19):                                      # degrees up to 20 that are not built
+        assert call([1, p], [0.1, 0.1], [1.0, 2.0], [64, 128]) == tmg.TMG_EUNSUPPORTED, p
     assert call(*ok, omega=2.5) == tmg.TMG_EINVAL
-    assert call(*ok, gamma=2) == tmg.TMG_EINVAL              # batches run V-cycles
+    assert call(*ok, gamma=3) == tmg.TMG_EINVAL              # V- or W-cycles only
     assert call(*ok, schedule=3) == tmg.TMG_EINVAL
     assert call(*ok, nu1=0, nu2=0) == tmg.TMG_EINVAL
     assert call([], [], [], []) == tmg.TMG_EINVAL             # no instances

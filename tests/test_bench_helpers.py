@@ -58,3 +58,36 @@ def test_traffic_is_reported_only_for_its_kernel_source(tmp_path, monkeypatch):
     assert bench.measured_traffic() == pytest.approx(bench.UPDOWN0_TRAFFIC["bytes_per_launch"])
     monkeypatch.setitem(bench.UPDOWN0_TRAFFIC, "kernels_sha256", "0" * 16)
     assert bench.measured_traffic() is None
+
+
+def test_fp64_cycle_model_counts_level_vectors_and_operations():
+    """The FP64 form's model: 28 + 28 B/DoF at level 0, four level vectors per
+    coarse level, the coarsest level read and written (three passes when
+    scanned); operations from fp64_ops_per_interval on every level."""
+    N, d, nu = 1 << 12, 2, (1, 1)
+    down, up, down0, up0 = bench.fp64_ops_per_interval(d, *nu)
+    assert (down, up) == (2 * d * d + 5 * d, 2 * d * d + d + 4 * d)
+    assert (down0, up0) == (down + 6 * d, up + d)
+    b, ops = bench.fp64_cycle_model(N, d, nu, 3, False)
+    nb = N * d * 8
+    assert b["cycle"] == 56 * N * d + 4 * (nb >> 1) + 4 * (nb >> 2) + 2 * (nb >> 3)
+    assert ops["cycle"] == down0 * N + up0 * N + (down + up) * (N // 2 + N // 4) + (d * d + 3 * d + 3) * (N >> 3)
+
+
+def test_kernel_roofline_takes_the_larger_bound():
+    """A kernel is bounded by the larger of its HBM time and its FP64 time."""
+    hbm = bench.kernel_roofline("k", 1.0, 6.8e9, 0, 6800.0, "measured")
+    assert hbm["bound"] == "hbm" and hbm["frac"] == pytest.approx(1.0)
+    alu = bench.kernel_roofline("k", 2.0, 1e6, bench.FP64_PEAK_OPS * 1e-3, 6800.0, "measured")
+    assert alu["bound"] == "alu" and alu["frac"] == pytest.approx(0.5)
+
+
+def test_batched_model_uses_real_lengths_and_cycle_counts():
+    """Mixed batched bytes: 16 + 16 B/DoF (start, confirmation) plus each
+    instance's own cycles of its own hierarchy."""
+    Nv, pv, cyc = [4096, 100], [1, 0], [3, 5]
+    nbytes, ops = bench.batched_solve_model(Nv, pv, cyc, "mixed")
+    exp = 32 * 4096 * 2 + 3 * bench.cycle_bytes(4096, 2, bench.oracle_levels(4096) - 1)["cycle"]
+    exp += 32 * 100 + 5 * bench.cycle_bytes(100, 1, bench.oracle_levels(100) - 1)["cycle"]
+    assert nbytes == exp and ops == 0
+    assert bench.oracle_levels(4096) == 7 and bench.oracle_levels(100) == 2 and bench.oracle_levels(33) == 1

@@ -119,6 +119,129 @@ def test_batched_fp64_cycles_match_textbook_cycle(dev, schedule, nu):
             assert e <= 1e-12, (k, i, int(p[i]), int(N[i]), z[i], e)
 
 
+@pytest.mark.parametrize("schedule", ["grid", "cta"])
+@pytest.mark.parametrize("nu", [(1, 1), (2, 1)])
+def test_batched_w_cycles_match_textbook_cycle(dev, schedule, nu):
+    """W-cycles (gamma = 2) in the batched solve at the iterate level: every
+    level below level 0 visited twice per visit of its parent, the second
+    visit from the first one's result.  The grid form launches the streaming
+    levels once per visit down to the first level of at most 8192 intervals
+    and runs the rest in one CTA per instance; the CTA form runs the whole
+    recursion on chip.  Against k = 1, 2, 3 applications of the oracle's
+    textbook W-cycle (eq. chap4_errorTwoGridCycle recursed twice per level),
+    1e-12 relative; lengths up to 2^16 so that the grid form has streaming
+    W levels above its on-chip part."""
+    from paper_1409_5254_gb300 import tmg
+    rng = np.random.default_rng(47 + nu[0])
+    N = np.array([65536, 40000, 16384, 9000, 4096, 777, 100, 5, 1, 33000, 2048, 65])
+    p = np.array([0, 1, 0, 2, 3, 0, 1, 0, 2, 0, 5, 4])
+    z = 10.0 ** rng.uniform(-3, 3, len(N))
+    Fs, u0, tau, lam = make_batch(47, p, N, z)
+    f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+    u0d = torch.from_numpy(u0).to(dev)
+    sched = tmg.SCHED_GRID if schedule == "grid" else tmg.SCHED_CTA
+    ref = [oracle_batched_iterates(int(p[i]), lam[i] * tau[i], Fs[i], u0[i], 3, nu1=nu[0], nu2=nu[1], gamma=2)
+           for i in range(len(N))]
+    for k in (1, 2, 3):
+        with tmg.Batch(p, tau, lam, N, precision="fp64", tol=0.0, max_cycles=k, schedule=sched, nu1=nu[0],
+                       nu2=nu[1], gamma=2) as B:
+            u = B.solve(f, u0d, allow_notconv=True)
+            cyc, rel, mx = B.stats()
+            us = B.split(u.cpu().numpy())
+        for i in range(len(N)):
+            c = int(cyc[i])
+            assert 1 <= c <= k and (c == k or rel[i] == 0.0), (i, c, rel[i])
+            e = np.abs(us[i] - ref[i][c - 1]).max() / max(np.abs(ref[i][c - 1]).max(), 1e-300)
+            assert e <= 1e-12, (k, i, int(p[i]), int(N[i]), z[i], e)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batched_w_cycles_reach_tolerance_in_fewer_cycles_at_degree_0(dev, prec):
+    """The point of W-cycles at p_t = 0, where V-cycles degrade with depth
+    (the paper's Section 7): a batch of p_t = 0 instances of 2^12 .. 2^16
+    intervals, lambda tau = 1e-3 .. 1, solved to 1e-10 with V(2,2) and with
+    W(2,2); the W solve needs fewer cycles and meets the oracle's residual."""
+    from paper_1409_5254_gb300 import tmg
+    rng = np.random.default_rng(53)
+    N = np.array([4096, 8192, 16384, 32768, 65536, 12288, 40960, 65536])
+    p = np.zeros(len(N), dtype=int)
+    z = 10.0 ** rng.uniform(-3, 0, len(N))
+    Fs, u0, tau, lam = make_batch(53, p, N, z)
+    f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+    out = {}
+    for gamma in (1, 2):
+        with tmg.Batch(p, tau, lam, N, precision=prec, tol=1e-10, max_cycles=300, nu1=2, nu2=2, gamma=gamma,
+                       schedule=tmg.SCHED_GRID) as B:
+            u = B.solve(f, torch.from_numpy(u0).to(dev))
+            cyc, rel, mx = B.stats()
+            out[gamma] = (mx, B.split(u.cpu().numpy()), B)
+        assert (rel <= 1e-10).all()
+    check_solution(Fs, u0, tau, lam, p, N, np.concatenate([x.reshape(-1) for x in out[2][1]]), out[2][2], 1e-10)
+    print(f"p_t = 0 {prec}: V(2,2) {out[1][0]} cycles, W(2,2) {out[2][0]} cycles")
+    assert out[2][0] < out[1][0]
+
+
+def test_wide_degree_batch_fp64_cycles_match_textbook_cycle(dev):
+    """p_t = 10 and 20 instances (with p_t = 1 ones) in one batch: per-level
+    kernels, the residual recomputed from u; FP64 iterates after 1, 2, 3
+    cycles against the oracle's textbook cycle on each instance, 1e-12."""
+    from paper_1409_5254_gb300 import tmg
+    N = np.array([4096, 1000, 64, 3, 2048, 700, 1, 8192])
+    p = np.array([10, 20, 10, 20, 20, 10, 20, 1])
+    z = np.array([1e-3, 0.5, 30.0, 1.0, 1e-2, 1e3, 2.0, 0.1])
+    Fs, u0, tau, lam = make_batch(61, p, N, z)
+    f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+    u0d = torch.from_numpy(u0).to(dev)
+    ref = [oracle_batched_iterates(int(p[i]), lam[i] * tau[i], Fs[i], u0[i], 3) for i in range(len(N))]
+    for k in (1, 2, 3):
+        with tmg.Batch(p, tau, lam, N, precision="fp64", tol=0.0, max_cycles=k) as B:
+            u = B.solve(f, u0d, allow_notconv=True)
+            cyc, rel, mx = B.stats()
+            us = B.split(u.cpu().numpy())
+        for i in range(len(N)):
+            c = int(cyc[i])
+            assert 1 <= c <= k and (c == k or rel[i] == 0.0), (i, c, rel[i])
+            e = np.abs(us[i] - ref[i][c - 1]).max() / max(np.abs(ref[i][c - 1]).max(), 1e-300)
+            assert e <= 1e-12, (k, i, int(p[i]), int(N[i]), z[i], e)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_wide_degree_batch_solve_and_adjoint(dev, prec):
+    """A batch of p_t = 10 and 20 instances solved to tolerance (every
+    instance at the oracle's residual) and its gradients through the adjoint
+    against the oracle's backward sweep and gradient formulas."""
+    from paper_1409_5254_gb300 import tmg
+    N = np.array([4096, 2048, 300, 1024, 5000, 64])
+    p = np.array([10, 20, 10, 20, 10, 20])
+    z = np.array([1e-2, 0.3, 5.0, 1e-1, 2e-3, 40.0])
+    Fs, u0, tau, lam = make_batch(67, p, N, z)
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    rng = np.random.default_rng(67)
+    with tmg.Batch(p, tau, lam, N, precision=prec, tol=tol, max_cycles=300) as B:
+        f = torch.from_numpy(np.concatenate([F.reshape(-1) for F in Fs])).to(dev)
+        u = B.solve(f, torch.from_numpy(u0).to(dev))
+        cyc, rel, mx = B.stats()
+        assert (rel <= tol).all(), rel
+        us = B.split(u.cpu().numpy())
+        gs = []
+        for i in range(len(p)):
+            _, _, _, b = O.blocks(int(p[i]))
+            gs.append(np.outer(O.nodal_values(int(p[i]), us[i]) - rng.standard_normal(int(N[i])), b))
+        g = torch.from_numpy(np.concatenate([x.reshape(-1) for x in gs])).to(dev)
+        dJdf, du0, dlam = B.adjoint(g, u)
+    check_solution(Fs, u0, tau, lam, p, N, u.cpu().numpy(), B, tol)
+    mus = B.split(dJdf.cpu().numpy())
+    du0, dlam = du0.cpu().numpy(), dlam.cpu().numpy()
+    for i in range(len(p)):
+        zi = lam[i] * tau[i]
+        allow = 2.0 * max(N[i], 1.0 / zi) * tol * 10
+        mu_ref = O.adj_sweep(int(p[i]), zi, gs[i])
+        assert np.abs(mus[i] - mu_ref).max() <= allow * np.abs(mu_ref).max(), i
+        _, d0, dl = O.adjoint_grads(int(p[i]), lam[i], tau[i], gs[i], us[i])
+        assert du0[i] == pytest.approx(d0, rel=allow, abs=1e-12)
+        assert dlam[i] == pytest.approx(dl, rel=allow, abs=1e-12)
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_batched_error_against_fp64_is_reported(dev, prec):
     """opts.check_fp64 on a batch: per-instance max|u_i - u_exact,i| /

@@ -1,13 +1,18 @@
-"""Parity of the p_t = 10 path (11 x 11 blocks) with the FP64 oracle.
+"""Parity of the wide-degree paths, p_t = 10 and 20 (11 x 11 and 21 x 21
+blocks, the largest degrees of the paper's scaling tables), with the FP64
+oracle.
 
-At this degree the plan runs the per-level streaming kernels and solves its
+At these degrees the plan runs the per-level streaming kernels and solves its
 coarsest level by the grid-wide scan in every cycle (no two-level kernels, no
 on-chip coarse solver).  Tolerances as in the lower-degree parity tests:
-* FP64 form: the blocks are as well conditioned (cond(K + z Mhat) <= 21 for
-  every z), so the iterates agree to 1e-12 relative after each of three cycles;
+* FP64 form: the blocks are well conditioned (cond(K + z Mhat) <= 21 at
+  p_t = 10 and <= 41 at p_t = 20 for every z >= 0), so the iterates agree to
+  1e-12 relative after each of three cycles;
 * mixed form (the level-0 residual recomputed from u in FP64 every cycle):
   FP64 relative residual of the returned u, evaluated by the oracle,
-  <= 1e-10 (x1.05 for the oracle's own rounding).
+  <= 1e-10 (x1.05 for the oracle's own rounding);
+* adjoint: mu against the oracle's backward sweep within cond(L) times the
+  reached residual, as in the lower-degree adjoint tests.
 """
 import numpy as np
 import pytest
@@ -19,7 +24,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-P = 10
+DEGREES = [10, 20]
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +46,7 @@ def rel_err(a, b):
     return np.abs(a - b).max() / (s if s > 0 else 1.0)
 
 
-def rel_residual(z, F, u0, u):
+def rel_residual(P, z, F, u0, u):
     r = O.residual(P, z, F, u0, u)
     return np.linalg.norm(r) / np.linalg.norm(O.fold_u0(P, F, u0))
 
@@ -64,8 +69,9 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("P", DEGREES)
 @pytest.mark.parametrize("case", CASES)
-def test_cycles_match_textbook_cycle(dev, case):
+def test_cycles_match_textbook_cycle(dev, P, case):
     N, lam, n_min, levels, nu1, nu2, gamma, omega = case
     prob = inputs.scalar_problem(N % 97, N, P, lam=lam, T=1.0, u0=0.75)
     z = lam * prob["tau"]
@@ -88,15 +94,16 @@ def test_cycles_match_textbook_cycle(dev, case):
         assert rel_err(got[k], u) <= 1e-12, (k, rel_err(got[k], u))
 
 
+@pytest.mark.parametrize("P", DEGREES)
 @pytest.mark.parametrize("gamma", [1, 2])
-def test_solve_matches_forward_substitution(dev, gamma):
+def test_solve_matches_forward_substitution(dev, P, gamma):
     N = 1 << 13
     prob = inputs.scalar_problem(3, N, P, lam=1.0, T=4.0, u0=1.0)
     z = prob["tau"]
     with tmg().Plan(P, prob["tau"], 1.0, N, precision="fp64", tol=1e-13, max_cycles=300, gamma=gamma) as plan:
         u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
         st = plan.stats()
-    assert rel_residual(z, prob["F"], prob["u0"], u) <= 1.05e-13
+    assert rel_residual(P, z, prob["F"], prob["u0"], u) <= 1.05e-13
     assert rel_err(u, O.fsub(P, z, prob["F"], prob["u0"])) <= 1e-11
     # the device-side history follows the oracle's textbook solve cycle by cycle
     _, hist = O.mg_solve(P, z, prob["F"], prob["u0"], gamma=gamma, tol=1e-13, max_cycles=300)
@@ -106,11 +113,13 @@ def test_solve_matches_forward_substitution(dev, gamma):
     np.testing.assert_allclose(st.hist[:m][big], hist[:m][big], rtol=1e-6)
 
 
-def test_large_solve_in_graph(dev):
-    """2^20 intervals (1.2e7 unknowns): the graph solve to 1e-12 against
-    forward substitution over the whole vector.  (With tau = 1e-2 the rounding
-    floor of the relative residual, that of forward substitution itself, is
-    4.7e-14; it grows like 1/tau, as |u| / |F| does.)"""
+@pytest.mark.parametrize("P", DEGREES)
+def test_large_solve_in_graph(dev, P):
+    """2^20 intervals (1.2e7 unknowns at p_t = 10, 2.2e7 at 20): the graph
+    solve to 1e-12 against forward substitution over the whole vector.  (With
+    tau = 1e-2 the rounding floor of the relative residual, that of forward
+    substitution itself, is 4.7e-14 at p_t = 10; it grows like 1/tau, as
+    |u| / |F| does.)"""
     N = 1 << 20
     prob = inputs.scalar_problem(11, N, P, lam=1.0, tau=1e-2, u0=1.0)
     z = prob["tau"]
@@ -118,21 +127,26 @@ def test_large_solve_in_graph(dev):
         u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
         st = plan.stats()
     assert st.rel_res <= 1e-12
-    assert rel_residual(z, prob["F"], prob["u0"], u) <= 1.05e-12
+    assert rel_residual(P, z, prob["F"], prob["u0"], u) <= 1.05e-12
     assert rel_err(u, O.fsub(P, z, prob["F"], prob["u0"])) <= 1e-10
 
 
+@pytest.mark.parametrize("P", DEGREES)
 @pytest.mark.parametrize("N", [1, 5, 2049, 100003])
-def test_direct_scan_solve(dev, N):
+def test_direct_scan_solve(dev, P, N):
+    """The exact scan solve; at p_t = 20 each thread chunk holds four
+    intervals (a tile of 1024), so 100003 intervals span 98 tiles, the last
+    one ragged."""
     prob = inputs.scalar_problem(N % 13, N, P, lam=3.0, T=1.0, u0=0.9)
     z = 3.0 * prob["tau"]
     with tmg().Plan(P, prob["tau"], 3.0, N, levels=1, precision="fp64") as plan:
         u = plan.solve_direct(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
-    assert rel_residual(z, prob["F"], prob["u0"], u) <= max(1e-13, 1e-15 * np.sqrt(N * (P + 1)))
+    assert rel_residual(P, z, prob["F"], prob["u0"], u) <= max(1e-13, 1e-15 * np.sqrt(N * (P + 1)))
     assert rel_err(u, O.fsub(P, z, prob["F"], prob["u0"])) <= max(1e-12, 8 * N * 2.2e-16)
 
 
-def test_residual_entry_point(dev):
+@pytest.mark.parametrize("P", DEGREES)
+def test_residual_entry_point(dev, P):
     N = 3000
     prob = inputs.scalar_problem(9, N, P, lam=1.0, T=1.0, u0=0.4)
     u = np.random.default_rng(0).standard_normal((N, P + 1))
@@ -142,8 +156,9 @@ def test_residual_entry_point(dev):
                                rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("P", DEGREES)
 @pytest.mark.parametrize("zscale", [1e-3, 1.0, 1e3])
-def test_mixed_solve_reaches_tolerance(dev, zscale):
+def test_mixed_solve_reaches_tolerance(dev, P, zscale):
     N = 1 << 13
     lam = zscale * N
     prob = inputs.scalar_problem(20, N, P, lam=lam, T=1.0, u0=1.0)
@@ -151,31 +166,79 @@ def test_mixed_solve_reaches_tolerance(dev, zscale):
     with tmg().Plan(P, prob["tau"], lam, N, precision="mixed", tol=1e-10, max_cycles=200) as plan:
         u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
         st = plan.stats()
-    rr = rel_residual(z, prob["F"], prob["u0"], u)
+    rr = rel_residual(P, z, prob["F"], prob["u0"], u)
     assert rr <= 1.05e-10, rr
     assert st.rel_res <= 1e-10
     err = rel_err(u, O.fsub(P, z, prob["F"], prob["u0"]))
-    print(f"p=10 mixed z={z:.1e} cycles={st.cycles} rel_res={rr:.2e} err_vs_fp64={err:.2e}")
+    print(f"p={P} mixed z={z:.1e} cycles={st.cycles} rel_res={rr:.2e} err_vs_fp64={err:.2e}")
     assert err <= 1e-6
 
 
-def test_mixed_large_solve(dev):
+@pytest.mark.parametrize("P", DEGREES)
+def test_mixed_large_solve(dev, P):
     N = 1 << 20
     prob = inputs.scalar_problem(11, N, P, lam=1.0, tau=1e-2, u0=1.0)
     z = prob["tau"]
     with tmg().Plan(P, prob["tau"], 1.0, N, precision="mixed", tol=1e-10, nu1=2, nu2=2) as plan:
         u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"]).cpu().numpy()
         st = plan.stats()
-    rr = rel_residual(z, prob["F"], prob["u0"], u)
+    rr = rel_residual(P, z, prob["F"], prob["u0"], u)
     assert st.rel_res <= 1e-10 and rr <= 1.05e-10, (st.rel_res, rr)
     assert rel_err(u, O.fsub(P, z, prob["F"], prob["u0"])) <= 1e-7
 
 
-def test_adjoint_is_not_built_at_this_degree(dev):
+@pytest.mark.parametrize("P", DEGREES)
+@pytest.mark.parametrize("prec,lam", [("fp64", 2.0), ("mixed", 40.0)])
+def test_adjoint_matches_oracle(dev, P, prec, lam):
+    """The transposed, backward-in-time solve at the wide degrees: mu = L^{-T} g
+    against the oracle's backward sweep (allowance cond(L) ~ 2/z times the
+    reached residual, as at p_t <= 5), the gradients dJ/du0 = a^T mu_1 and
+    dJ/dlambda = -tau sum mu_n^T Mhat u_n against the oracle's formulas."""
     T = tmg()
-    N = 256
-    with T.Plan(P, 1e-3, 1.0, N, precision="fp64") as plan:
-        g = torch.zeros((N, P + 1), dtype=torch.float64, device=dev)
-        with pytest.raises(T.TmgError) as e:
-            plan.adjoint(g, g)
-    assert e.value.status == T.TMG_EUNSUPPORTED
+    N = 1 << 12
+    prob = inputs.scalar_problem(5 + P, N, P, lam=lam, T=1.0, u0=0.8)
+    tau = prob["tau"]
+    z = lam * tau
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    target = np.random.default_rng(P).standard_normal(N)
+    with T.Plan(P, tau, lam, N, precision=prec, tol=tol, max_cycles=300) as plan:
+        u = plan.solve(torch.from_numpy(prob["F"]).to(dev), prob["u0"])
+        uh = u.cpu().numpy()
+        _, _, _, b = O.blocks(P)
+        g = np.outer(O.nodal_values(P, uh) - target, b)
+        dJdf, du0, dlam = plan.adjoint(torch.from_numpy(g).to(dev), u)
+        st = plan.stats()
+    mu = dJdf.cpu().numpy()
+    mu_ref = O.adj_sweep(P, z, g)
+    allow = 2.0 / z * tol * 10
+    assert rel_err(mu, mu_ref) <= allow, (rel_err(mu, mu_ref), allow)
+    _, du0_ref, dlam_ref = O.adjoint_grads(P, lam, tau, g, uh)
+    assert float(du0) == pytest.approx(du0_ref, rel=allow, abs=1e-14)
+    assert float(dlam) == pytest.approx(dlam_ref, rel=allow, abs=1e-14)
+    print(f"p={P} {prec}: adjoint cycles={st.cycles} mu err={rel_err(mu, mu_ref):.2e}")
+
+
+@pytest.mark.parametrize("P", DEGREES)
+def test_adjoint_cycles_contract(dev, P):
+    """Cycle by cycle: the FP64 adjoint run for exactly k cycles (tol = 0,
+    max_cycles = k) contracts its error against the oracle's backward sweep by
+    at least one half per V(1,1) cycle, as the forward cycle does (the oracle
+    has no reversed-time cycle to compare iterates with)."""
+    T = tmg()
+    N, lam = 1 << 11, 3.0
+    prob = inputs.scalar_problem(2, N, P, lam=lam, T=1.0, u0=0.5)
+    tau = prob["tau"]
+    g = np.random.default_rng(7).standard_normal((N, P + 1))
+    mu_ref = O.adj_sweep(P, lam * tau, g)
+    errs = []
+    for k in (1, 2, 3, 6):
+        with T.Plan(P, tau, lam, N, precision="fp64", tol=0.0, max_cycles=k) as plan:
+            u = torch.zeros((N, P + 1), dtype=torch.float64, device=dev)
+            mu, _, _ = plan.adjoint(torch.from_numpy(g).to(dev), u, allow_notconv=True)
+            assert plan.stats().cycles == k
+        errs.append(rel_err(mu.cpu().numpy(), mu_ref))
+    # the error falls by at least one half per cycle (the measured factor is
+    # about 0.25, the two-grid estimate at p_t >= 1)
+    for a, b_ in zip(errs, errs[1:3]):
+        assert b_ <= 0.5 * a, errs
+    assert errs[-1] <= 0.5 ** 5 * errs[0], errs

@@ -65,8 +65,9 @@ def test_w_cycles_take_the_largest_on_chip_level_within_the_limits():
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("gamma", [1, 2])
 @pytest.mark.parametrize("N", [37, 1 << 11, 1 << 24])
-def test_degree_10_always_solves_its_coarsest_level_by_the_scan(prec, gamma, N):
-    s = tmg.plan_shape(10, 1e-3, 1.0, N, precision=prec, gamma=gamma)
+@pytest.mark.parametrize("p", [10, 20])
+def test_wide_degrees_always_solve_their_coarsest_level_by_the_scan(p, prec, gamma, N):
+    s = tmg.plan_shape(p, 1e-3, 1.0, N, precision=prec, gamma=gamma)
     assert s["scan_coarsest"] and s["tail_level"] == s["levels"] - 1
 
 
@@ -80,5 +81,5 @@ def test_status_codes_match_setup():
     assert status(1, 1e-3, 1.0, 0) == tmg.TMG_EINVAL
     assert status(1, 1e-3, 1.0, 64, 0, 2.5) == tmg.TMG_EINVAL
     assert status(1, 1e-3, 1.0, 64, gamma=3) == tmg.TMG_EINVAL
-    for p in (6, 9, 11, 20):
+    for p in (6, 9, 11, 19):
         assert status(p, 1e-3, 1.0, 64) == tmg.TMG_EUNSUPPORTED
