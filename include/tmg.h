@@ -191,6 +191,28 @@ tmg_status tmg_cycle(tmg_plan *plan, const double *f, double u0, double *u);
  */
 tmg_status tmg_error_vs_fp64(tmg_plan *plan, const double *f, double u0, const double *u, double *err);
 
+/*
+ * One correction cycle split at the plan's coarsest level, for callers that
+ * solve that level themselves -- the time-slab partition of one long horizon
+ * over several GPUs, where every slab's coarsest-level right-hand sides are
+ * gathered and the coarse part of the cycle (eq. chap4_errorTwoGridCycle
+ * below that level) runs on the gathered problem.  tmg_cycle_down evaluates
+ * r = F - L u (FP64) and runs the way down of one V-cycle on L c = r:
+ * pre-smoothing, residual and restriction on every level above the coarsest,
+ * whose right-hand side it writes to fc (device, N_c (p_t+1) doubles, N_c the
+ * coarsest level's intervals, tmg_plan_info).  tmg_cycle_up takes that
+ * level's correction uc (device, same size), runs the way up (prolongation,
+ * post-smoothing on every level) and updates u += c; u must be the array
+ * passed to the tmg_cycle_down call it completes.  Together with uc = the
+ * exact or multigrid correction of the coarsest level they apply the same
+ * cycle as tmg_cycle.  The plan must run V-cycles, have at least two levels,
+ * no on-chip solver above its coarsest level (opts->tail_cap = 1), and no
+ * updated level-0 residual (TMG_FP64, or update_residual = 0): else
+ * TMG_EUNSUPPORTED.  Both synchronise the stream.
+ */
+tmg_status tmg_cycle_down(tmg_plan *plan, const double *f, double u0, double *u, double *fc);
+tmg_status tmg_cycle_up(tmg_plan *plan, const double *uc, double *u);
+
 /* r = F - L u (FP64, device arrays [N][p_t+1]); F is f with a*u0 folded in. */
 tmg_status tmg_residual(tmg_plan *plan, const double *f, double u0, const double *u, double *r);
 

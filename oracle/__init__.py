@@ -15,7 +15,8 @@ Parts (each cites the paper passage it follows):
 * ``fsub`` -- exact block forward substitution for eq.
   chap4_generalLinearSystemODE (the plain definition of the result).
 * ``dense_solve`` -- brute-force Gaussian elimination of the assembled system.
-* ``mg_solve`` / ``mg_one_cycle`` -- a textbook recursive multigrid cycle:
+* ``mg_solve`` / ``mg_one_cycle`` / ``mg_cycle_down`` / ``mg_cycle_up`` -- a
+  textbook recursive multigrid cycle (the last two cut it at a level):
   damped block Jacobi (eq. chap4_ODESmoother), residual, restriction R = P^T
   (eqs. chap4_restrictionTime/chap4_prolongationTime), recursion (V or W) with
   an exact coarsest solve, prolongation, post-smoothing
@@ -82,6 +83,8 @@ def lib():
             L.orc_mg_one_cycle.argtypes = [c_int, c_double, c_long, _dp, _dp, c_long, c_int,
                                            c_int, c_int, c_int, c_double]
             L.orc_residual.argtypes = [c_int, c_double, c_long, _dp, c_double, _dp, _dp]
+            L.orc_mg_cycle_split.argtypes = [c_int, c_double, c_long, _dp, _dp, c_long, c_int, c_int, c_int,
+                                             c_double, c_int, c_int, _dp, _dp]
             L.orc_adj_sweep.argtypes = [c_int, c_double, c_long, _dp, _dp]
             L.orc_adjoint_grads.argtypes = [c_int, c_double, c_double, c_long, _dp, _dp, _dp, _dp, _dp]
             _lib = L
@@ -190,6 +193,31 @@ def mg_one_cycle(p: int, z: float, Fhat, u, *, n_min: int = 64, max_levels: int 
     u = _vec(u, p).copy()
     lib().orc_mg_one_cycle(p, float(z), Fhat.shape[0], _ptr(Fhat), _ptr(u), int(n_min),
                            int(max_levels), int(nu1), int(nu2), int(gamma), float(omega))
+    return u
+
+
+def mg_cycle_down(p: int, z: float, Fhat, u, stop: int, *, n_min: int = 64, max_levels: int = 0, nu1: int = 1,
+                  nu2: int = 1, omega: float = 0.0) -> np.ndarray:
+    """The way down of one V-cycle on L u = Fhat to level `stop` of its
+    hierarchy: that level's right-hand side (N/2^stop intervals); u unchanged."""
+    Fhat = _vec(Fhat, p)
+    u = _vec(u, p).copy()
+    fc = np.zeros((Fhat.shape[0] >> stop, p + 1))
+    lib().orc_mg_cycle_split(p, float(z), Fhat.shape[0], _ptr(Fhat), _ptr(u), int(n_min), int(max_levels), int(nu1),
+                             int(nu2), float(omega), int(stop), 0, _ptr(fc), _ptr(fc))
+    return fc
+
+
+def mg_cycle_up(p: int, z: float, Fhat, u, uc, stop: int, *, n_min: int = 64, max_levels: int = 0, nu1: int = 1,
+                nu2: int = 1, omega: float = 0.0) -> np.ndarray:
+    """The same way down again, then uc as level `stop`'s correction and the
+    way up: the cycle's new iterate."""
+    Fhat = _vec(Fhat, p)
+    u = _vec(u, p).copy()
+    uc = np.ascontiguousarray(uc, dtype=np.float64)
+    assert uc.shape == (Fhat.shape[0] >> stop, p + 1)
+    lib().orc_mg_cycle_split(p, float(z), Fhat.shape[0], _ptr(Fhat), _ptr(u), int(n_min), int(max_levels), int(nu1),
+                             int(nu2), float(omega), int(stop), 1, _ptr(uc), _ptr(uc))
     return u
 
 

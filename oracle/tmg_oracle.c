@@ -366,9 +366,28 @@ static void smooth(const orc_hier *h, int lev, long N, double *u, const double *
     free(Lu);
 }
 
-static void mg_cycle(const orc_hier *h, int lev, double *u, const double *f) {
+/* A cycle cut at level `stop`: mode 0 stops the way down there and hands out
+ * that level's right-hand side; mode 1 takes that level's correction from the
+ * caller instead of recursing (the coarse part of the cycle solved elsewhere,
+ * e.g. on the gathered coarse problem of several time slabs). */
+typedef struct {
+    int stop, mode;
+    double *fc_out;
+    const double *uc_in;
+} orc_split;
+
+static void mg_cycle_s(const orc_hier *h, int lev, double *u, const double *f, const orc_split *sp);
+
+static void mg_cycle(const orc_hier *h, int lev, double *u, const double *f) { mg_cycle_s(h, lev, u, f, NULL); }
+
+static void mg_cycle_s(const orc_hier *h, int lev, double *u, const double *f, const orc_split *sp) {
     int d = h->d;
     long N = h->Nl[lev];
+    if (sp && lev == sp->stop) {
+        if (sp->mode == 0) memcpy(sp->fc_out, f, sizeof(double) * N * d);
+        else memcpy(u, sp->uc_in, sizeof(double) * N * d);
+        return;
+    }
     if (lev == h->nlev - 1) {          /* coarsest level: exact solve */
         orc_fsub(h->p, h->z[lev], N, f, 0.0, u);
         return;
@@ -391,7 +410,13 @@ static void mg_cycle(const orc_hier *h, int lev, double *u, const double *f) {
                 s += h->P1[l * d + k] * r[(2 * m) * d + l] + h->P2[l * d + k] * r[(2 * m + 1) * d + l];
             fc[m * d + k] = s;
         }
-    for (int g = 0; g < h->gamma; ++g) mg_cycle(h, lev + 1, uc, fc);
+    for (int g = 0; g < h->gamma; ++g) mg_cycle_s(h, lev + 1, uc, fc, sp);
+    if (sp && sp->mode == 0) {         /* the way down ended at sp->stop */
+        free(r);
+        free(fc);
+        free(uc);
+        return;
+    }
     /* prolongation u_{2m} += P1 uc_m, u_{2m+1} += P2 uc_m */
     for (long m = 0; m < Nc; ++m)
         for (int k = 0; k < d; ++k) {
@@ -478,6 +503,42 @@ void orc_mg_one_cycle(int p, double z, long N, const double *F, double *u,
     double K[ORC_MAXD * ORC_MAXD], Mh[ORC_MAXD * ORC_MAXD];
     orc_blocks(p, K, Mh, h.a, h.b);
     mg_cycle(&h, 0, u, F);
+    free(h.Nl); free(h.z); free(h.om);
+}
+
+/* One V-cycle on L u = F (u0 folded into F) cut at level `stop` of its
+ * hierarchy (0 < stop < number of levels).  mode 0: the way down only, on a
+ * copy of u (u is left unchanged); the right-hand side of level `stop`,
+ * N/2^stop intervals, is written to fc_out.  mode 1: the same way down again
+ * (the same arithmetic), then uc_in as the correction of level `stop`, and
+ * the way up, updating u.  With uc_in = one cycle of the level-stop problem
+ * from zero the two calls apply exactly orc_mg_one_cycle. */
+void orc_mg_cycle_split(int p, double z, long N, const double *F, double *u, long n_min, int max_levels, int nu1,
+                        int nu2, double omega, int stop, int mode, double *fc_out, const double *uc_in) {
+    orc_hier h;
+    int d = p + 1;
+    h.p = p; h.d = d; h.nu1 = nu1; h.nu2 = nu2; h.gamma = 1;
+    h.nlev = orc_num_levels(N, n_min, max_levels);
+    h.Nl = (long *)malloc(sizeof(long) * h.nlev);
+    h.z = (double *)malloc(sizeof(double) * h.nlev);
+    h.om = (double *)malloc(sizeof(double) * h.nlev);
+    for (int l = 0; l < h.nlev; ++l) {
+        h.Nl[l] = N >> l;
+        h.z[l] = ldexp(z, l);
+        h.om[l] = omega > 0.0 ? omega : orc_omega_star(p, h.z[l]);
+    }
+    orc_transfer(p, h.P1, h.P2);
+    double K[ORC_MAXD * ORC_MAXD], Mh[ORC_MAXD * ORC_MAXD];
+    orc_blocks(p, K, Mh, h.a, h.b);
+    orc_split sp = {stop, mode, fc_out, uc_in};
+    if (mode == 0) {
+        double *w = (double *)malloc(sizeof(double) * N * d);
+        memcpy(w, u, sizeof(double) * N * d);
+        mg_cycle_s(&h, 0, w, F, &sp);
+        free(w);
+    } else {
+        mg_cycle_s(&h, 0, u, F, &sp);
+    }
     free(h.Nl); free(h.z); free(h.om);
 }
 

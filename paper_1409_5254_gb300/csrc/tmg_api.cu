@@ -503,6 +503,43 @@ tmg_status tmg_cycle(tmg_plan* P, const double* f, double u0, double* u) {
     return TMG_OK;
 }
 
+// A plan whose cycle can be split at its coarsest level: V-cycles, the
+// coarsest level below at least one streaming level and not part of an
+// on-chip multi-level solver, and no updated level-0 residual (whose fused
+// kernel joins the way up of one cycle to the way down of the next).
+static bool splittable(const tmg_plan* P) {
+    return P->o.gamma == 1 && P->lt >= 1 && P->lt == P->nlev - 1 && P->rl == nullptr;
+}
+
+tmg_status tmg_cycle_down(tmg_plan* P, const double* f, double u0, double* u, double* fc) {
+    if (!P || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK || !fc ||
+        (reinterpret_cast<uintptr_t>(fc) & 7u))
+        return TMG_EINVAL;
+    if (!splittable(P)) return TMG_EUNSUPPORTED;
+    tmg_status s = stage_state(P, f, u0, u, -1.0, 1 << 30, 0, 1);
+    if (s != TMG_OK) return s;
+    P->split = 1;
+    const cudaError_t e = P->ops->enqueue_cycle(P);
+    P->split = 0;
+    TMG_CUDA(e);
+    TMG_CUDA(P->ops->enqueue_coarse_io(P, fc, nullptr));
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return TMG_OK;
+}
+
+tmg_status tmg_cycle_up(tmg_plan* P, const double* uc, double* u) {
+    if (!P || !uc || (reinterpret_cast<uintptr_t>(uc) & 7u) || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    if (!splittable(P)) return TMG_EUNSUPPORTED;
+    if (P->st_host->u != u) return TMG_EINVAL;   // the u of the tmg_cycle_down call this completes
+    TMG_CUDA(P->ops->enqueue_coarse_io(P, nullptr, uc));
+    P->split = 2;
+    const cudaError_t e = P->ops->enqueue_cycle(P);
+    P->split = 0;
+    TMG_CUDA(e);
+    TMG_CUDA(cudaStreamSynchronize(P->s));
+    return TMG_OK;
+}
+
 tmg_status tmg_residual(tmg_plan* P, const double* f, double u0, const double* u, double* r) {
     if (!P || !isfinite(u0) || check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK || check_ptr(r) != TMG_OK)
         return TMG_EINVAL;

@@ -111,6 +111,14 @@ inline void launch(const tmg_plan* P, void (*kernel)(KArgs...), int grid, int bl
     ++P->launches_per_cycle;
 }
 
+// Element-wise copy with conversion (the coarsest level's right-hand side out
+// to FP64, its correction in from FP64).
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kNT) k_convert(const Tin* __restrict__ in, Tout* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * kNT + threadIdx.x; i < n; i += (int64_t)gridDim.x * kNT)
+        out[i] = (Tout)in[i];
+}
+
 template <typename T, int D, int DIR>
 struct Impl {
     static const std::vector<tmg_level_host>& L(const tmg_plan* P) { return DIR == 0 ? P->lev : P->lev_adj; }
@@ -243,6 +251,17 @@ struct Impl {
 
     static cudaError_t enqueue_cycle(tmg_plan* P) { return enqueue_cycle_timed(P, nullptr, nullptr, nullptr); }
 
+    // tmg_cycle_down / tmg_cycle_up: the coarsest level's right-hand side out
+    // (fc_out != nullptr) or its correction in (uc_in != nullptr).
+    static cudaError_t enqueue_coarse_io(tmg_plan* P, double* fc_out, const double* uc_in) {
+        const int64_t n = P->lev[P->lt].N * D;
+        if (fc_out != nullptr)
+            k_convert<T, double><<<grid_flat(P, n), kNT, 0, P->s>>>(static_cast<const T*>(P->fl[P->lt]), fc_out, n);
+        if (uc_in != nullptr)
+            k_convert<double, T><<<grid_flat(P, n), kNT, 0, P->s>>>(uc_in, static_cast<T*>(P->ul[P->lt]), n);
+        return cudaGetLastError();
+    }
+
     // One correction cycle.  With ev != nullptr an event is recorded before
     // every kernel group and after the last one; cat[i] receives the group
     // between ev[i] and ev[i+1] (kCat*) and *nev the number of events
@@ -286,7 +305,8 @@ struct Impl {
             if (nev) *nev = iev;
             return cudaGetLastError();
         }
-        {
+        const int split = P->split;   // 1: the way down only, 2: the way up only (tmg_cycle_down/up)
+        if (split != 2) {
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark(kCatDown0);
@@ -320,12 +340,12 @@ struct Impl {
         }
         // the coarsest level (at most 64 intervals, directly below the streaming
         // levels) is solved by the last block of the last down kernel
-        const bool coarse_in_down = P->o.gamma == 1 && !P->scan_coarsest && P->lt == P->nlev - 1 && ng > 0 &&
-                                    P->lev[P->lt].N <= 64;
+        const bool coarse_in_down = split == 0 && P->o.gamma == 1 && !P->scan_coarsest && P->lt == P->nlev - 1 &&
+                                    ng > 0 && P->lev[P->lt].N <= 64;
         CoarseTail<T, D> ct_none{nullptr, nullptr, nullptr, 0, nullptr};
         CoarseTail<T, D> ct_last{lk, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]),
                                  (int)P->lev[P->lt].N, &P->st->ticket2};
-        for (int g = 0; g < ng; ++g) {
+        for (int g = 0; split != 2 && g < ng; ++g) {
             const CoarseTail<T, D> ct = coarse_in_down && g == ng - 1 ? ct_last : ct_none;
             mark(kCatDown);
             if (grp[g] < 0) {
@@ -351,15 +371,20 @@ struct Impl {
                        (const DevState*)P->st, ct);
             }
         }
-        if (!wcycle) mark(kCatCoarse);
-        if (coarse_in_down || wcycle) {
-            // solved above
+        if (!wcycle && split == 0) mark(kCatCoarse);
+        if (coarse_in_down || wcycle || split != 0) {
+            // solved above, or exported / imported by tmg_cycle_down / tmg_cycle_up
         } else if (P->scan_coarsest)
             enqueue_scan<T, T>(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), P->lt, T(0),
                                nullptr, P->st);
         else
             launch_tail(P, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]), lk, X, nl,
                         P->lev[P->lt].N, nu1, nu2, P->o.gamma, (const DevState*)P->st, (const T*)nullptr);
+        if (split == 1) {
+            mark(kCatEnd);
+            if (nev) *nev = iev;
+            return cudaGetLastError();
+        }
         for (int g = ng - 1; g >= 0; --g) {
             mark(kCatUp);
             if (grp[g] < 0) {
@@ -429,7 +454,8 @@ struct Impl {
 
     static const tmg_ops* ops() {
         static const tmg_ops o = {sizeof(T),        &tail_bytes,       &upload,        &enqueue_cycle,
-                                  &enqueue_cycle_timed, &enqueue_normF, &enqueue_residual, &enqueue_direct};
+                                  &enqueue_cycle_timed, &enqueue_normF, &enqueue_residual, &enqueue_direct,
+                                  &enqueue_coarse_io};
         return &o;
     }
 };

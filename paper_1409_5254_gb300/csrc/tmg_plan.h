@@ -110,6 +110,11 @@ struct tmg_plan {
     // kernels launched by the last enqueued cycle (counted by launch())
     mutable int launches_per_cycle;
 
+    // tmg_cycle_down / tmg_cycle_up: 1 = enqueue only the way down to the
+    // coarsest level (its right-hand side is exported, not solved), 2 = only
+    // the way up from an imported coarsest-level correction; 0 = whole cycles
+    int split;
+
     // statistics of the last solve
     int last_cycles;
     double last_rel;
@@ -128,6 +133,8 @@ struct tmg_ops {
     cudaError_t (*enqueue_normF)(tmg_plan*);       // ||F|| for a caller-given start
     cudaError_t (*enqueue_residual)(tmg_plan*, const double* f, double u0, const double* u, double* r);
     cudaError_t (*enqueue_direct)(tmg_plan*, const double* f, double u0, double* u);   // FP64 exact scan solve
+    // the coarsest level's right-hand side out to, and its correction in from, FP64 arrays
+    cudaError_t (*enqueue_coarse_io)(tmg_plan*, double* fc_out, const double* uc_in);
 };
 
 const tmg_ops* tmg_ops_f32(int d, int dir);

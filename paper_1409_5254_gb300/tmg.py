@@ -41,7 +41,8 @@ _LIB = None
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 
-EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle", "tmg_residual",
+EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_solve_direct", "tmg_adjoint", "tmg_cycle",
+           "tmg_cycle_down", "tmg_cycle_up", "tmg_residual",
            "tmg_stats", "tmg_error_vs_fp64", "tmg_plan_shape", "tmg_level_constants", "tmg_transfer_matrices", "tmg_plan_info",
            "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
@@ -67,6 +68,10 @@ def _lib():
         L.tmg_solve.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_solve_host.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_cycle.argtypes = [_vp, _vp, ctypes.c_double, _vp]
+        L.tmg_cycle_down.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
+        L.tmg_cycle_up.argtypes = [_vp, _vp, _vp]
+        L.tmg_cycle_down.restype = ctypes.c_int
+        L.tmg_cycle_up.restype = ctypes.c_int
         L.tmg_solve_direct.argtypes = [_vp, _vp, ctypes.c_double, _vp]
         L.tmg_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
         L.tmg_residual.argtypes = [_vp, _vp, ctypes.c_double, _vp, _vp]
@@ -245,6 +250,30 @@ class Plan:
         _order_after_current(self._stream, f)
         _check(_lib().tmg_cycle(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
                                 _dev_ptr(u, self.d, self.N, "u")), "tmg_cycle")
+        return u
+
+    def coarse_intervals(self) -> int:
+        return self.info()["tail_intervals"]
+
+    def cycle_down(self, f, u0: float, u, fc=None):
+        """The way down of one V-cycle (tmg_cycle_down): returns the coarsest
+        level's right-hand side fc (N_c, p+1) as a float64 CUDA tensor."""
+        import torch
+        nc = self.coarse_intervals()
+        if fc is None:
+            fc = torch.empty((nc, self.d), dtype=torch.float64, device=f.device)
+        _order_after_current(self._stream, f)
+        _check(_lib().tmg_cycle_down(self._h, _dev_ptr(f, self.d, self.N, "f"), float(u0),
+                                     _dev_ptr(u, self.d, self.N, "u"), _dev_ptr(fc, self.d, nc, "fc")),
+               "tmg_cycle_down")
+        return fc
+
+    def cycle_up(self, uc, u):
+        """The way up of the cycle begun by cycle_down, from the coarsest
+        level's correction uc (tmg_cycle_up); u += c."""
+        _order_after_current(self._stream, uc)
+        _check(_lib().tmg_cycle_up(self._h, _dev_ptr(uc, self.d, self.coarse_intervals(), "uc"),
+                                   _dev_ptr(u, self.d, self.N, "u")), "tmg_cycle_up")
         return u
 
     def residual(self, f, u0: float, u, r=None):
