@@ -284,6 +284,18 @@ def single_line(tmg, torch, stream, F, u, p: int, tau: float, prec: str, n_min: 
         err = pl.error_vs_fp64(F, U0, u)
         prof = pl.profile_cycle(F, U0, u.clone(), reps=10)
     ms = statistics.median(times)
+    roof = level0_roofline(prec, p, N, nu, prof, info, hbm_peak, peak_kind)
+    return {"value": N * d / (ms * 1e-3), "unit": "DoF/s", "ms_per_step": round(ms, 4),
+            "ms_mean": round(statistics.fmean(times), 4), "solves_timed": steps, "precision": prec,
+            "cycles": st.cycles, "rel_res": st.rel_res, "err_vs_fp64": err, "cycle": f"V{tuple(nu)}",
+            "levels": info["levels"], "coarsest_intervals": info["tail_intervals"], "roofline": roof}
+
+
+def level0_roofline(prec: str, p: int, N: int, nu, prof: dict, info: dict, hbm_peak: float, peak_kind: str):
+    """Roofline of the dominant level-0 kernel of a single-problem solve from
+    the per-kernel event times of tmg_profile_cycle (`prof`) and the byte and
+    FP64-operation models above."""
+    d = p + 1
     lt = info["tail_level"]
     scanned = p + 1 > 6 or info["tail_intervals"] > 8192
     if prec == "fp64":
@@ -312,10 +324,7 @@ def single_line(tmg, torch, stream, F, u, p: int, tau: float, prec: str, n_min: 
     roof.update(cyc)
     if len(k) > 1:
         roof["other_level0_kernel"] = min(k, key=lambda r: r["launch_ms"])
-    return {"value": N * d / (ms * 1e-3), "unit": "DoF/s", "ms_per_step": round(ms, 4),
-            "ms_mean": round(statistics.fmean(times), 4), "solves_timed": steps, "precision": prec,
-            "cycles": st.cycles, "rel_res": st.rel_res, "err_vs_fp64": err, "cycle": f"V{tuple(nu)}",
-            "levels": info["levels"], "coarsest_intervals": info["tail_intervals"], "roofline": roof}
+    return roof
 
 
 def run_ours(args):
@@ -346,7 +355,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
     plan = tmg.Plan(P_MAIN, TAU, LAM, N_FULL, precision="mixed", tol=TOL, stream=stream, use_graph=not args.eager,
-                    nu1=NU[0], nu2=NU[1], n_min=N_MIN)
+                    nu1=NU[0], nu2=NU[1], n_min=n_min_p(P_MAIN))
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t_setup) * 1e3
     for _ in range(args.warmup):
@@ -432,6 +441,8 @@ def run_ours(args):
                               "up_levels": round(prof["up_levels"], 5), "updown0": round(prof["up0"], 5),
                               "cycle_events": round(prof["cycle"], 5)}}
 
+    if d > 6:   # --p-t 10 / 20 (profiling runs): no fused level-0 kernel at these widths
+        roofline = level0_roofline("mixed", P_MAIN, N_FULL, NU, prof, info, hbm_peak, peak_kind)
     # every kernel of the graph body launches in each of the cycles + 1 loop iterations
     launches = args.steps * (st.cycles + 1) * plan.launches_per_cycle()
 
@@ -479,6 +490,21 @@ def run_ours(args):
                                                    10 if prec == "mixed" else 3, args.eager, hbm_peak, peak_kind)
             except tmg.TmgError as e:
                 extra[f"p10_{prec}"] = {"error": str(e)}
+        del Fp, up
+        # p_t = 20 (21 x 21 blocks, the paper's largest degree) on the first
+        # 2^22 intervals of the same step (3.7e8 values per vector at 2^24)
+        n20 = N_FULL >> 2
+        pr = inputs.scalar_problem(1, n20, 20, lam=LAM, tau=TAU, u0=U0)
+        Fp = torch.from_numpy(pr["F"]).to(dev)
+        up = torch.empty_like(Fp)
+        del pr
+        for prec in ("mixed", "fp64"):
+            try:
+                extra[f"p20_{prec}"] = single_line(tmg, torch, stream, Fp, up, 20, TAU, prec, 64,
+                                                   10 if prec == "mixed" else 3, args.eager, hbm_peak, peak_kind)
+                extra[f"p20_{prec}"]["N"] = n20
+            except tmg.TmgError as e:
+                extra[f"p20_{prec}"] = {"error": str(e)}
         del Fp, up
         # other sweep counts on the headline problem (same solver, same tolerance)
         nus = {}
@@ -636,11 +662,13 @@ def _batched_form(tmg, torch, stream, dev, replicas, prec, pv, tau, lamv, Nv, f,
             "precision": prec,
             "max_cycles": int(replicas.max_over_ranks(mx, dev)),
             "mean_cycles": round(float(np.mean(cyc)), 2),
+            "max_cycles_by_degree": {str(int(q)): int(np.max(cyc[np.asarray(pv) == q]))
+                                     for q in sorted(set(int(x) for x in np.asarray(pv)))},
             "max_rel_res": replicas.max_over_ranks(float(rel.max()), dev),
             "err_vs_fp64": {"max": replicas.max_over_ranks(float(np.max(err)), dev),
                             "median": float(np.median(err))},
             "setup_ms": round(setup_ms, 1),
-            "groups": info["groups"], "padded_dofs": info["padded_values"],
+            "groups": info["groups"], "computed_dofs": info["padded_values"],
             "groups_cta": kinds.count("cta"), "groups_grid": kinds.count("grid"),
             "autotune_whole_batch_ms": {k: (round(v, 3) if v == v else None)
                                         for k, v in info["whole_batch_ms"].items()},
@@ -694,6 +722,11 @@ def _uneven(dev, stream, nsteps, torch, shard, precisions, eager, hbm_peak, peak
     for prec in precisions:
         res[prec] = _batched_form(tmg, torch, stream, dev, replicas, prec, pv, tau, lamv, Nv, f, u0, u, nsteps,
                                   eager, hbm_peak, peak_kind, dofs)
+    if "mixed" in precisions:
+        # W(2,2) cycles for the whole batch (the p_t = 0 instances need fewer cycles)
+        res["mixed_W"] = _batched_form(tmg, torch, stream, dev, replicas, "mixed", pv, tau, lamv, Nv, f, u0, u,
+                                       nsteps, eager, hbm_peak, peak_kind, dofs, gamma=2)
+        res["mixed_W"]["cycle"] = f"W{NU}"
     out["uneven_10000"] = {"unit": "DoF/s", "instances": len(Nv_all), "dofs": dofs, **res}
     del f, u, u0
     torch.cuda.empty_cache()
@@ -893,6 +926,8 @@ def main():
     ap.add_argument("--eager", action="store_true", help="host-driven cycle loop instead of the CUDA graph (profiling: "
                     "ncu does not profile the kernels of a graph with conditional nodes one by one)")
     ap.add_argument("--n-log2", type=int, default=24, help="intervals = 2^n (smaller cases for ncu captures)")
+    ap.add_argument("--p-t", type=int, default=1, help="degree of the long-horizon line (profiling other degrees "
+                    "with --quick; the benchmark line is p_t = 1)")
     ap.add_argument("--workload", default="all", choices=["all", "heat", "uneven", "gradients"],
                     help="all: the benchmark line; otherwise only that batched workload (profiling)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
@@ -902,8 +937,9 @@ def main():
     args = ap.parse_args()
     global BATCH_STRIDE
     BATCH_STRIDE = max(1, args.batch_stride) if args.workload == "heat" else 1
-    global N_FULL
+    global N_FULL, P_MAIN
     N_FULL = 1 << args.n_log2
+    P_MAIN = args.p_t
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "all":

@@ -330,21 +330,27 @@ typedef struct tmg_batch tmg_batch;
 /*
  * Plan for n_inst (1 <= n_inst <= 2^31 - 1) independent problems
  * u' + lambda_i u = f_i, u(0) = u0_i, instance i with degree p_t[i] in
- * {0..5}, step tau[i] > 0, lambda[i] >= 0 and N[i] >= 1 intervals (host
- * arrays of length n_inst).  Packed layout of
- * every [instance][interval][coefficient] array: instance i starts at value
- * offset off_i = sum_{j<i} N[j] (p_t[j] + 1).  omega and opts as for
- * tmg_setup (levels coarsen down to at most 64 intervals, solved exactly;
- * W-cycles, gamma = 2, visit every level below level 0 twice per visit of its
- * parent: in the grid form the streaming levels down to the first one of at
- * most 8192 intervals are launched once per visit, and the levels from there
- * on run in one CTA per instance, whose shared-memory recursion makes its own
- * visits; the CTA form runs the whole W recursion on chip).  Internally the instances are grouped
- * by p_t and padded at their end to a power-of-two length (the system is
- * causal, so this leaves each instance's solution unchanged); every level
- * kernel then covers all instances of a group still iterating at once.
- * Per-instance FP64
- * constants are computed on the host.  Returns as tmg_setup.
+ * {0..5, 10, 20}, step tau[i] > 0, lambda[i] >= 0 and N[i] >= 1 intervals
+ * (host arrays of length n_inst).  Packed layout of every
+ * [instance][interval][coefficient] array: instance i starts at value offset
+ * off_i = sum_{j<i} N[j] (p_t[j] + 1).  omega and opts as for tmg_setup;
+ * levels coarsen while even and longer than nmin = min(opts->n_min, 64)
+ * intervals, the coarsest level solved exactly.  Internally the instances are
+ * grouped: an instance whose own hierarchy coarsens at least once down to at
+ * most nmin intervals joins the group of its degree and depth and is solved on
+ * its own intervals with its own hierarchy (the level kernels tile only real
+ * intervals); any other instance (at most 64 intervals, or an odd coarsest
+ * level longer than nmin) is padded at its end to a power-of-two length (the
+ * system is causal, so this leaves its solution unchanged).  Every level
+ * kernel covers all instances of a group still iterating at once.
+ * W-cycles (gamma = 2) visit every level below level 0 twice per visit of
+ * its parent: in the grid form the streaming levels down to the first one of
+ * at most 8192 intervals are launched once per visit, and the levels from
+ * there on run in one CTA per instance, whose shared-memory recursion makes
+ * its own visits; the CTA form runs the whole W recursion on chip.  Degrees
+ * 10 and 20 run V-cycles in the grid form, the level-0 residual recomputed
+ * from u in every cycle.  Per-instance FP64 constants are computed on the
+ * host.  Returns as tmg_setup.
  */
 tmg_status tmg_setup_batched(tmg_batch **batch, int64_t n_inst, const int *p_t, const double *tau,
                              const double *lambda, const int64_t *N, double omega, const tmg_opts *opts,
@@ -385,7 +391,8 @@ tmg_status tmg_stats_batched(const tmg_batch *batch, int *cycles, double *rel_re
 tmg_status tmg_error_vs_fp64_batched(tmg_batch *batch, const double *f, const double *u0, const double *u,
                                      double *err_host);
 
-/* Number of (p_t, padded length) groups and the padded number of values. */
+/* Number of groups and the number of values the level kernels cover (the real
+ * values of variable-length groups, the padded slots of power-of-two ones). */
 tmg_status tmg_batch_info(const tmg_batch *batch, int *n_groups, int64_t *padded_values);
 
 /*

@@ -6,6 +6,7 @@
 
 #include <new>
 
+#include "tmg_nvtx.h"
 #include "tmg_plan.h"
 #include "tmg_setup_math.h"
 
@@ -186,6 +187,7 @@ tmg_status check_ptr(const void* p) {
 
 tmg_status run_solve(tmg_plan* P, const double* f, double u0, double* u, int dir = 0, int initial_guess = -1) {
     if (check_ptr(f) != TMG_OK || check_ptr(u) != TMG_OK) return TMG_EINVAL;
+    const tmg::NvtxRange r_solve(dir == 0 ? "tmg_solve" : "tmg_adjoint solve");
     const tmg_ops* ops = dir == 0 ? P->ops : P->ops_adj;
     if (initial_guess < 0) initial_guess = P->o.initial_guess;
     const int use_graph = P->o.use_graph != 0;

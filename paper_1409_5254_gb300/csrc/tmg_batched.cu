@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <new>
 #include <vector>
 
@@ -324,8 +325,12 @@ void fill_tables(const tmg_batch* B, const tmg_batch_group* G, std::vector<char>
 tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     const size_t el = B->o.precision == TMG_MIXED ? sizeof(float) : sizeof(double);
     const int64_t nmin = std::min<int64_t>(B->o.n_min, 64);
-    G->nlev = 1;
-    for (int64_t m = G->Ng; m > nmin && m % 2 == 0 && G->nlev < kMaxLevels; m /= 2) ++G->nlev;
+    if (G->var) {
+        G->nlev = G->log2Ng - G->log2M + 1;   // the instances' own depth s, down to m_i <= 2^log2M intervals
+    } else {
+        G->nlev = 1;
+        for (int64_t m = G->Ng; m > nmin && m % 2 == 0 && G->nlev < kMaxLevels; m /= 2) ++G->nlev;
+    }
     if ((G->Ng >> (G->nlev - 1)) > 64) return TMG_EUNSUPPORTED;
     G->cta_smem = cta_bytes(B, G);
     G->cta_ok = G->d <= kMaxD && G->cta_smem <= kCtaSmemMax && G->nlev <= kTailLevels;
@@ -401,6 +406,19 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     }
     const size_t o_c0 = off;
     off = align_up(off + (G->nlev == 1 ? el * nvals : 0), A);
+    // variable lengths: m per instance, and per list the unit prefix and the
+    // list position of every unit
+    const int64_t units = G->var ? (n << G->log2M) : 0;
+    const size_t o_m = off;
+    off = align_up(off + (G->var ? 4 * n : 0), A);
+    const size_t o_upa = off;
+    off = align_up(off + (G->var ? 4 * (n + 1) : 0), A);
+    const size_t o_upf = off;
+    off = align_up(off + (G->var ? 4 * (n + 1) : 0), A);
+    const size_t o_u2a = off;
+    off = align_up(off + 4 * units, A);
+    const size_t o_u2f = off;
+    off = align_up(off + 4 * units, A);
     const size_t o_ids = off;
     off = align_up(off + 8 * n, A);
     const size_t o_Ni = off;
@@ -426,6 +444,12 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     G->bi.act_list = reinterpret_cast<int*>(b + o_al);
     G->bi.full_list = reinterpret_cast<int*>(b + o_fl);
     G->bi.nvals_per_inst = (long long)G->Ng * G->d;
+    G->bi.m = G->var ? reinterpret_cast<const int*>(b + o_m) : nullptr;
+    G->bi.upre_a = reinterpret_cast<int*>(b + o_upa);
+    G->bi.upre_f = reinterpret_cast<int*>(b + o_upf);
+    G->bi.u2p_a = reinterpret_cast<int*>(b + o_u2a);
+    G->bi.u2p_f = reinterpret_cast<int*>(b + o_u2f);
+    G->bi.log2M = G->log2M;
     G->res = reinterpret_cast<Res0*>(b + o_res);
     G->lk[0] = b + o_lk0;
     G->lk[1] = b + o_lk1;
@@ -481,6 +505,12 @@ tmg_status setup_group(tmg_batch* B, tmg_batch_group* G) {
     TB_CUDA(cudaMemcpyAsync(G->d_ids, G->ids.data(), 8 * n, cudaMemcpyHostToDevice, B->s));
     TB_CUDA(cudaMemcpyAsync(G->d_Ni, Ni.data(), 8 * n, cudaMemcpyHostToDevice, B->s));
     TB_CUDA(cudaMemcpyAsync(G->d_off, offs.data(), 8 * n, cudaMemcpyHostToDevice, B->s));
+    std::vector<int> mv;
+    if (G->var) {
+        mv.resize(n);
+        for (int64_t j = 0; j < n; ++j) mv[j] = (int)(Ni[j] >> (G->nlev - 1));
+        TB_CUDA(cudaMemcpyAsync(const_cast<int*>(G->bi.m), mv.data(), 4 * n, cudaMemcpyHostToDevice, B->s));
+    }
     TB_CUDA(cudaStreamSynchronize(B->s));   // host vectors go out of scope
     return TMG_OK;
 }
@@ -558,6 +588,10 @@ tmg_status start_group(tmg_batch* B, tmg_batch_group* G, const double* F, double
     TB_CUDA(cudaMemcpyAsync(G->st, h, sizeof(BatchState), cudaMemcpyHostToDevice, G->s));
     kb_init<<<grid_flat(B, G->n), kBNT, 0, G->s>>>(G->bi, G->n);
     TB_CUDA(cudaGetLastError());
+    if (G->var) {
+        kb_units<<<2, kUnitsNT, 0, G->s>>>(G->st, G->bi);   // unit tables of the initial lists
+        TB_CUDA(cudaGetLastError());
+    }
     TB_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * G->n * G->Ng * G->d, G->s));
     if (use_graph) {
         TB_CUDA(cudaGraphLaunch(G->gexec[dir], G->s));
@@ -844,12 +878,31 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
         tmg_destroy_batched(B);
         return fail(e);
     }
-    // group by (p, padded length)
-    std::map<std::pair<int, int64_t>, std::vector<int64_t>> key;
+    // Group the instances.  An instance whose own hierarchy -- coarsen while
+    // even and longer than nmin = min(n_min, 64) -- has s >= 1 coarsenings and
+    // ends at m <= nmin intervals joins the variable-length group (p_t, s):
+    // slots of 2^log2M 2^s intervals (2^log2M >= nmin), tiles over its own
+    // intervals, its own hierarchy.  The others (at most 64 intervals, or an
+    // odd coarsest level longer than nmin) are padded at their end to a power
+    // of two and grouped by (p_t, padded length).
+    const int64_t nmin = std::min<int64_t>(o.n_min, 64);
+    int log2M = 0;
+    while ((int64_t(1) << log2M) < nmin) ++log2M;
+    std::map<std::tuple<int, int, int64_t>, std::vector<int64_t>> key;
     for (int64_t i = 0; i < n_inst; ++i) {
-        int64_t Ng = 2;
-        while (Ng < N[i]) Ng *= 2;
-        key[{p_t[i], Ng}].push_back(i);
+        int s = 0;
+        int64_t m = N[i];
+        while (m % 2 == 0 && m > nmin) {
+            m /= 2;
+            ++s;
+        }
+        if (s >= 1 && m <= nmin) {
+            key[{p_t[i], 1, int64_t(1) << (log2M + s)}].push_back(i);
+        } else {
+            int64_t Ng = 2;
+            while (Ng < N[i]) Ng *= 2;
+            key[{p_t[i], 0, Ng}].push_back(i);
+        }
     }
     for (auto& kv : key) {
         tmg_batch_group* G = new (std::nothrow) tmg_batch_group();
@@ -858,10 +911,15 @@ tmg_status tmg_setup_batched(tmg_batch** out, int64_t n_inst, const int* p_t, co
             return TMG_ENOMEM;
         }
         B->groups.push_back(G);
-        G->p = kv.first.first;
+        G->p = std::get<0>(kv.first);
         G->d = G->p + 1;
-        G->Ng = kv.first.second;
+        G->Ng = std::get<2>(kv.first);
         G->log2Ng = ilog2(G->Ng);
+        G->log2M = log2M;
+        // a group whose instances all fill their slots needs no unit tables
+        G->var = false;
+        if (std::get<1>(kv.first) != 0)
+            for (int64_t i : kv.second) G->var = G->var || N[i] != G->Ng;
         G->ids = kv.second;
         G->n = (int64_t)G->ids.size();
         tmg_status s = setup_group(B, G);
@@ -1019,8 +1077,15 @@ tmg_status tmg_batch_info(const tmg_batch* B, int* n_groups, int64_t* padded_val
     if (!B) return TMG_EINVAL;
     if (n_groups) *n_groups = (int)B->groups.size();
     if (padded_values) {
+        // values the level kernels cover: the real ones in variable-length
+        // groups, the padded slots otherwise
         int64_t t = 0;
-        for (auto* G : B->groups) t += G->n * G->Ng * G->d;
+        for (auto* G : B->groups) {
+            if (G->var)
+                for (int64_t i : G->ids) t += B->N[i] * G->d;
+            else
+                t += G->n * G->Ng * G->d;
+        }
         *padded_values = t;
     }
     return TMG_OK;

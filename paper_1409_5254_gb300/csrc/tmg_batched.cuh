@@ -52,6 +52,19 @@ struct BatchInst {
     float* nscale;    // power of two bringing instance i's residual near 1 (FP32 norms)
     int* act_list;    // the instances still iterating (st->n_act of them, any order)
     int* full_list;   // updated-residual form: the instances with full[i] != 0 (st->n_full of them)
+    // Variable-length groups: the instances share the hierarchy depth s and
+    // instance i has m_i 2^s intervals (m_i <= 2^log2M) in a slot of
+    // 2^(log2M + s); the tiles cover only the real intervals.  m[i] per
+    // instance; per list, the prefix of m over the listed instances (upre,
+    // n_list + 1 entries) and the list position of every unit (u2p, one entry
+    // per unit of m).  m == nullptr in power-of-two groups, whose instances
+    // all fill their slot.
+    const int* m;
+    int* upre_a;
+    int* u2p_a;
+    int* upre_f;
+    int* u2p_f;
+    int log2M;
 };
 
 // Lane `lane` of virtual tile tw over the pairs of the listed instances,
@@ -66,20 +79,36 @@ struct ListPos {
 };
 
 __device__ __forceinline__ ListPos list_pos(int64_t tw, int per, int H, int lane, const int* __restrict__ list,
-                                            int n_list, int log2P) {
+                                            int n_list, int log2P, const int* __restrict__ upre = nullptr,
+                                            const int* __restrict__ u2p = nullptr, int log2M = 0) {
     const int64_t qv = tw * per + lane - H;
-    const int64_t loc = qv & ((int64_t(1) << log2P) - 1);
     ListPos p;
-    p.inb = qv >= 0 && qv < ((int64_t)n_list << log2P);
-    p.inst = p.inb ? (int64_t)list[qv >> log2P] : 0;
+    if (upre == nullptr) {
+        const int64_t loc = qv & ((int64_t(1) << log2P) - 1);
+        p.inb = qv >= 0 && qv < ((int64_t)n_list << log2P);
+        p.inst = p.inb ? (int64_t)list[qv >> log2P] : 0;
+        p.q = (p.inst << log2P) + loc;
+        p.first = loc == 0;
+        return p;
+    }
+    // variable lengths: instance i has m_i units of 2^sh items (pairs or
+    // quads), sh = log2P - log2M; the unit's list position comes from u2p
+    const int sh = log2P - log2M;
+    p.inb = qv >= 0 && qv < ((int64_t)upre[n_list] << sh);
+    const int pos = p.inb ? u2p[qv >> sh] : 0;
+    p.inst = p.inb ? (int64_t)list[pos] : 0;
+    const int64_t loc = p.inb ? qv - ((int64_t)upre[pos] << sh) : 0;
     p.q = (p.inst << log2P) + loc;
     p.first = loc == 0;
     return p;
 }
 
-// Tiles covering n_list instances of 2^log2P pairs.
-__device__ __forceinline__ int64_t list_tiles(int n_list, int log2P, int per) {
-    return (((int64_t)n_list << log2P) + per - 1) / per;
+// Tiles covering n_list instances of 2^log2P items (or their real items in a
+// variable-length group).
+__device__ __forceinline__ int64_t list_tiles(int n_list, int log2P, int per, const int* __restrict__ upre = nullptr,
+                                              int log2M = 0) {
+    const int64_t items = upre == nullptr ? ((int64_t)n_list << log2P) : ((int64_t)upre[n_list] << (log2P - log2M));
+    return (items + per - 1) / per;
 }
 
 // Segmented warp sum of v over lanes with the same instance id (ids are
@@ -182,12 +211,14 @@ __global__ void __launch_bounds__(kBNT) kb_down0(T* __restrict__ rT, short* __re
     constexpr bool kMixed = std::is_same<T, float>::value;
     const int* __restrict__ list = rlo != nullptr ? bi.full_list : bi.act_list;
     const int n_list = rlo != nullptr ? st->n_full : st->n_act;
+    const int* __restrict__ upre = bi.m == nullptr ? nullptr : rlo != nullptr ? bi.upre_f : bi.upre_a;
+    const int* __restrict__ u2p = rlo != nullptr ? bi.u2p_f : bi.u2p_a;
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, upre, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, list, n_list, log2N - 1, upre, u2p, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
@@ -387,6 +418,55 @@ static __global__ void __launch_bounds__(kBNT) kb_finalize(BatchState* st, Batch
     }
 }
 
+// Variable-length groups, after kb_finalize: the unit prefix of an instance
+// list and the list position of every unit, for list_pos.  Block 0 serves
+// act_list, block 1 (when launched) full_list.  Each thread takes a
+// contiguous chunk of the list: sums its units, the block scans the chunk
+// sums, and the thread writes its chunk's prefixes and unit positions.
+constexpr int kUnitsNT = 1024;
+
+static __global__ void __launch_bounds__(kUnitsNT) kb_units(const BatchState* __restrict__ st, BatchInst bi) {
+    if (st->done) return;
+    const bool act = blockIdx.x == 0;
+    const int* __restrict__ list = act ? bi.act_list : bi.full_list;
+    const int n = act ? st->n_act : st->n_full;
+    int* __restrict__ upre = act ? bi.upre_a : bi.upre_f;
+    int* __restrict__ u2p = act ? bi.u2p_a : bi.u2p_f;
+    const int chunk = (n + kUnitsNT - 1) / kUnitsNT;
+    const int j0 = min(n, (int)threadIdx.x * chunk), j1 = min(n, j0 + chunk);
+    int own = 0;
+    for (int j = j0; j < j1; ++j) own += bi.m[list[j]];
+    // block-wide exclusive scan of the chunk sums
+    __shared__ int wsum[kUnitsNT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    int u = (warp > 0 ? wsum[warp - 1] : 0) + x - own;
+    for (int j = j0; j < j1; ++j) {
+        upre[j] = u;
+        const int mj = bi.m[list[j]];
+        for (int k = 0; k < mj; ++k) u2p[u + k] = j;
+        u += mj;
+    }
+    if (threadIdx.x == kUnitsNT - 1) upre[n] = wsum[kUnitsNT / 32 - 1];
+}
+
 template <int DIR, typename T, int D>
 __global__ void __launch_bounds__(kBNT) kb_down(const T* __restrict__ f, T* __restrict__ fc, int64_t nchunks,
                                                 int log2N, const LevelK<T, D>* __restrict__ lk, int nlev, int level,
@@ -396,10 +476,10 @@ __global__ void __launch_bounds__(kBNT) kb_down(const T* __restrict__ f, T* __re
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const LevelK<T, D> K = lk[inst * nlev + level];
@@ -421,10 +501,10 @@ __global__ void __launch_bounds__(kBNT) kb_up(const T* __restrict__ f, const T* 
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const LevelK<T, D> K = lk[inst * nlev + level];
@@ -450,10 +530,10 @@ __global__ void __launch_bounds__(kBNT) kb_down_nz(const T* __restrict__ f, cons
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const LevelK<T, D> K = lk[inst * nlev + level];
@@ -477,10 +557,10 @@ __global__ void __launch_bounds__(kBNT) kb_up_nz(const T* __restrict__ f, const 
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const LevelK<T, D> K = lk[inst * nlev + level];
@@ -509,10 +589,10 @@ __global__ void __launch_bounds__(kBNT) kb_down2(const T* __restrict__ f, T* __r
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 2, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 2, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 2);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 2, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const LevelK<T, D> K0 = lk[inst * nlev + level];
@@ -544,10 +624,10 @@ __global__ void __launch_bounds__(kBNT) kb_up2(const T* __restrict__ f, const T*
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 2, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 2, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 2);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 2, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const LevelK<T, D> K0 = lk[inst * nlev + level];
@@ -580,10 +660,10 @@ __global__ void __launch_bounds__(kBNT) kb_up0(const T* __restrict__ rT, const T
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
@@ -622,13 +702,15 @@ __global__ void __launch_bounds__(kBNT) kb_coarse(const T* __restrict__ f, T* __
     const int64_t wid = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * kBNT) >> 5;
     const int n_list = st->n_act;
+    const int slot = Nc;
     for (int64_t j = wid; j < n_list; j += nw) {
         const int64_t inst = bi.act_list[j];
         const LevelK<T, D> K = lk[inst * nlev + level];
+        if (bi.m != nullptr) Nc = bi.m[inst];    // variable lengths: the instance's own coarsest level
         const int n0 = 2 * lane, n1 = 2 * lane + 1;
         T f0[D], f1[D];
-        load_one<T, D>(f + inst * (int64_t)Nc * D, n0, n0 < Nc, f0);
-        load_one<T, D>(f + inst * (int64_t)Nc * D, n1, n1 < Nc, f1);
+        load_one<T, D>(f + inst * (int64_t)slot * D, n0, n0 < Nc, f0);
+        load_one<T, D>(f + inst * (int64_t)slot * D, n1, n1 < Nc, f1);
         const T b0 = dotc<T, D>(K.c, f0), b1 = dotc<T, D>(K.c, f1);
         T A = n1 < Nc ? K.alpha * K.alpha : (n0 < Nc ? K.alpha : T(1));
         T B = n1 < Nc ? fma(K.alpha, b0, b1) : (n0 < Nc ? b0 : T(0));
@@ -652,7 +734,7 @@ __global__ void __launch_bounds__(kBNT) kb_coarse(const T* __restrict__ f, T* __
             x0[k] = fma(K.g[k], ein, x0[k]);
             x1[k] = fma(K.g[k], emid, x1[k]);
         }
-        T* ub = u + inst * (int64_t)Nc * D;
+        T* ub = u + inst * (int64_t)slot * D;
         if (n0 < Nc) VecIO<T, D>::store(ub + n0 * D, x0);
         if (n1 < Nc) VecIO<T, D>::store(ub + n1 * D, x1);
     }
@@ -683,10 +765,10 @@ __global__ void __launch_bounds__(kBNT, D <= 2 ? 4 : 2) kb_updown0(float* __rest
     const int lane = threadIdx.x & 31;
     const int per = 32 - H;
     const int n_list = st->n_act;
-    const int64_t ntiles = list_tiles(n_list, log2N - 1, per);
+    const int64_t ntiles = list_tiles(n_list, log2N - 1, per, bi.m ? bi.upre_a : nullptr, bi.log2M);
     const int64_t nwarps = ((int64_t)gridDim.x * kBNT) >> 5;
     for (int64_t tw = ((int64_t)blockIdx.x * kBNT + threadIdx.x) >> 5; tw < ntiles; tw += nwarps) {
-        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1);
+        const ListPos P = list_pos(tw, per, H, lane, bi.act_list, n_list, log2N - 1, bi.m ? bi.upre_a : nullptr, bi.u2p_a, bi.log2M);
         const int64_t q = P.q, inst = P.inst;
         const bool act = P.inb, first = P.first;
         const bool own = act && lane >= H;
@@ -800,17 +882,21 @@ __global__ void __launch_bounds__(kTailNT) kb_cta_solve(const double* __restrict
     double* Fs = reinterpret_cast<double*>(cta_smem);
     double* us = Fs + (int64_t)Ng * D;
     double* red = us + (int64_t)Ng * D;
-    const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(red + 32), Ng, nlev);
-    const int64_t nv = (int64_t)Ng * D;
+    const int64_t slot = (int64_t)Ng * D;
     const double tol = st->tol;
     const int max_cycles = st->max_cycles;
     int failed = 0;
     for (int64_t inst = blockIdx.x; inst < n_inst; inst += gridDim.x) {
+        // variable lengths: the instance's own intervals (its hierarchy has
+        // the group's nlev levels down to m_i intervals)
+        const int Ni = bi.m != nullptr ? bi.m[inst] << (nlev - 1) : Ng;
+        const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(red + 32), Ni, nlev);
+        const int64_t nv = (int64_t)Ni * D;
         const LevelK<T, D>* lki = lk + inst * nlev;
         const Res0 R = res[inst];
         const double u0i = u0[inst];
         for (int64_t i = threadIdx.x; i < nv; i += kTailNT) {
-            Fs[i] = F[inst * nv + i];
+            Fs[i] = F[inst * slot + i];
             us[i] = 0.0;
         }
         __syncthreads();
@@ -818,7 +904,7 @@ __global__ void __launch_bounds__(kTailNT) kb_cta_solve(const double* __restrict
         int k = 0;
         while (true) {
             double ss = 0.0;
-            for (int64_t n = threadIdx.x; n < Ng; n += kTailNT) {
+            for (int64_t n = threadIdx.x; n < Ni; n += kTailNT) {
                 double uv[D], Fv[D], r[D];
 #pragma unroll
                 for (int q = 0; q < D; ++q) {
@@ -848,7 +934,7 @@ __global__ void __launch_bounds__(kTailNT) kb_cta_solve(const double* __restrict
             __syncthreads();
             ++k;
         }
-        for (int64_t i = threadIdx.x; i < nv; i += kTailNT) u[inst * nv + i] = us[i];
+        for (int64_t i = threadIdx.x; i < nv; i += kTailNT) u[inst * slot + i] = us[i];
         if (threadIdx.x == 0) {
             bi.cycles[inst] = k;
             bi.rel[inst] = rel;
@@ -885,12 +971,15 @@ __global__ void __launch_bounds__(kTailNT) kb_tail(const T* __restrict__ f, T* _
     if (st->done) return;
     extern __shared__ __align__(16) unsigned char kb_tail_smem[];
     const int nl = nlev - lt;
-    const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(kb_tail_smem), Nt, nl);
-    const int64_t nv = (int64_t)Nt * D;
+    const int64_t slot = (int64_t)Nt * D;
     const int n_list = st->n_act;
     for (int64_t j = blockIdx.x; j < n_list; j += gridDim.x) {
         const int64_t inst = bi.act_list[j];
-        const int64_t off = inst * nv;
+        // variable lengths: the instance's own intervals on level lt
+        const int Ni = bi.m != nullptr ? bi.m[inst] << (nl - 1) : Nt;
+        const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(kb_tail_smem), Ni, nl);
+        const int64_t nv = (int64_t)Ni * D;
+        const int64_t off = inst * slot;
         for (int64_t i = threadIdx.x; i < nv; i += kTailNT) {
             V.f[0][i] = f[off + i];
             if (u_init != nullptr) V.u[0][i] = u_init[off + i];

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "tmg_batched.cuh"
+#include "tmg_nvtx.h"
 #include "tmg_setup_math.h"
 
 using namespace tmg;
@@ -18,9 +19,13 @@ using namespace tmg;
 struct tmg_batch_group {
     int p, d;
     int64_t n;           // instances in the group
-    int64_t Ng;          // padded length (power of two, >= 2)
+    int64_t Ng;          // slot length (power of two, >= 2)
     int log2Ng;
     int nlev;
+    bool var;            // variable lengths: instances of the same depth s = nlev - 1, each of its own
+                         // m_i 2^s intervals (m_i <= 2^log2M), tiles over real intervals only; else
+                         // every instance padded at its end to Ng
+    int log2M;
     bool direct;         // group arrays are the caller's arrays
     std::vector<int64_t> ids;
 
@@ -152,6 +157,7 @@ void w_visit_b(tmg_batch* B, tmg_batch_group* G, int l, bool nz, const Xfer<T, D
 
 template <typename T, int D, int DIR>
 cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
+    const NvtxRange r_cycle("tmg batch cycle, group of degree %d", G->p);
     const int nu1 = B->o.nu1, nu2 = B->o.nu2;
     Xfer<T, D> X;
     for (int i = 0; i < D * D; ++i) {   // reversed time swaps the halves
@@ -180,6 +186,7 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
             G->bi);
     }
     kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n, rl != nullptr ? kFinFull : kFinPlain);
+    if (G->var) kb_units<<<1, kUnitsNT, 0, G->s>>>(G->st, G->bi);   // act_list changed
     if (L == 1) {
         kb_coarse<DIR, T, D><<<grid_flat(B, n * 32), kBNT, 0, G->s>>>(rT, static_cast<T*>(G->c0), n, (int)G->Ng, lk,
                                                                        L, 0, G->st, G->bi);
@@ -260,6 +267,7 @@ cudaError_t enqueue_cycle(tmg_batch* B, tmg_batch_group* G) {
                 rT, rl, reinterpret_cast<const float*>(uc1), static_cast<float*>(G->fl[1]), nch, G->log2Ng, lk,
                 G->res, L, X, nu1, nu2, H, G->st, G->bi);
             kb_finalize<<<grid_flat(B, n), kBNT, 0, G->s>>>(G->st, G->bi, n, kFinUpdated);
+            if (G->var) kb_units<<<2, kUnitsNT, 0, G->s>>>(G->st, G->bi);   // both lists changed
             return cudaGetLastError();
         }
     }

@@ -3,6 +3,7 @@
 
 #include <string.h>
 
+#include "tmg_nvtx.h"
 #include "tmg_plan.h"
 
 namespace tmg {
@@ -204,6 +205,7 @@ struct Impl {
     // start iterate on a second visit, and the W recursion inside) or the
     // exact scan.
     static void w_visit(tmg_plan* P, int l, bool nz, const Xfer<T, D>& X, const LevelK<T, D>* lk_tail, int nl) {
+        const NvtxRange r_visit(nz ? "tmg level %d second visit" : "tmg level %d visit", l);
         const int nu1 = P->o.nu1, nu2 = P->o.nu2;
         T* ua = static_cast<T*>(P->ul[l]);
         T* ub = static_cast<T*>(P->ul2[l]);
@@ -270,6 +272,7 @@ struct Impl {
         if constexpr (D > kMaxD) {
             if (!P->scan_coarsest) return cudaErrorInvalidValue;
         }
+        const NvtxRange r_cycle(DIR == 0 ? "tmg cycle" : "tmg adjoint cycle");
         P->launches_per_cycle = 0;
         int iev = 0;
         auto mark = [&](int c) {
@@ -307,6 +310,7 @@ struct Impl {
         }
         const int split = P->split;   // 1: the way down only, 2: the way up only (tmg_cycle_down/up)
         if (split != 2) {
+            const NvtxRange r_lev("tmg level %d down", 0);
             const int H = halo_lanes(1 + sweeps_down(nu1));
             const int64_t nch = P->N / 2;
             mark(kCatDown0);
@@ -346,6 +350,7 @@ struct Impl {
         CoarseTail<T, D> ct_last{lk, static_cast<const T*>(P->fl[P->lt]), static_cast<T*>(P->ul[P->lt]),
                                  (int)P->lev[P->lt].N, &P->st->ticket2};
         for (int g = 0; split != 2 && g < ng; ++g) {
+            const NvtxRange r_lev(grp[g] < 0 ? "tmg levels %d,+1 down" : "tmg level %d down", grp[g] < 0 ? -grp[g] : grp[g]);
             const CoarseTail<T, D> ct = coarse_in_down && g == ng - 1 ? ct_last : ct_none;
             mark(kCatDown);
             if (grp[g] < 0) {
@@ -372,6 +377,7 @@ struct Impl {
             }
         }
         if (!wcycle && split == 0) mark(kCatCoarse);
+        const NvtxRange r_coarse("tmg coarsest level %d", P->lt);
         if (coarse_in_down || wcycle || split != 0) {
             // solved above, or exported / imported by tmg_cycle_down / tmg_cycle_up
         } else if (P->scan_coarsest)
@@ -386,6 +392,7 @@ struct Impl {
             return cudaGetLastError();
         }
         for (int g = ng - 1; g >= 0; --g) {
+            const NvtxRange r_lev(grp[g] < 0 ? "tmg levels %d,+1 up" : "tmg level %d up", grp[g] < 0 ? -grp[g] : grp[g]);
             mark(kCatUp);
             if (grp[g] < 0) {
                 if constexpr (D <= kMaxD) {

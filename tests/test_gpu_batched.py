@@ -53,10 +53,20 @@ def check_solution(Fs, u0, tau, lam, p, N, u_packed, batch, tol):
     return worst
 
 
-def group_length(N):
-    """The length the batched solver gives an instance of N intervals inside
-    its group: padded at its end to a power of two (at least 2) with a zero
-    right-hand side."""
+def group_length(N, n_min=64):
+    """The length of the system the batched solver solves for an instance of
+    N intervals.  An instance whose own hierarchy (coarsen while even and
+    longer than nmin = min(n_min, 64) intervals) coarsens at least once down
+    to at most nmin intervals is solved on its own N intervals; any other is
+    padded at its end to a power of two (at least 2) with a zero right-hand
+    side."""
+    nmin = min(n_min, 64)
+    s, m = 0, N
+    while m % 2 == 0 and m > nmin:
+        m //= 2
+        s += 1
+    if s >= 1 and m <= nmin:
+        return N
     Ng = 2
     while Ng < N:
         Ng *= 2
@@ -65,11 +75,11 @@ def group_length(N):
 
 def oracle_batched_iterates(p, z, F, u0, k, n_min=64, **kw):
     """The oracle's textbook cycle (eq. chap4_errorTwoGridCycle) applied k
-    times to the instance as the batched solver holds it: padded to its
-    group's length, coarsened while a level is even and longer than
-    min(n_min, 64) intervals; the first N intervals of each iterate."""
+    times to the instance as the batched solver holds it (group_length),
+    coarsened while a level is even and longer than min(n_min, 64)
+    intervals; the first N intervals of each iterate."""
     N = F.shape[0]
-    Fh = np.zeros((group_length(N), p + 1))
+    Fh = np.zeros((group_length(N, n_min), p + 1))
     Fh[:N] = O.fold_u0(p, F, u0)
     u = np.zeros_like(Fh)
     out = []
@@ -80,6 +90,16 @@ def oracle_batched_iterates(p, z, F, u0, k, n_min=64, **kw):
 
 
 BATCH_CYCLE_N = [1, 2, 3, 5, 64, 100, 1001, 4096, 16384, 12000, 777, 2048, 96, 33, 8192, 300, 5000, 130]
+
+
+def test_uneven_lengths_are_not_padded():
+    """The uneven-batch recipe rounds every N to m 2^s with m in (32, 64]: each
+    such instance is solved on its own intervals (no padding beyond 5%: only
+    the instances of at most 64 intervals are padded)."""
+    N, p, z = inputs.uneven_batch(3, 10000)
+    real = int((N * (p + 1)).sum())
+    solved = sum(group_length(int(n)) * (int(q) + 1) for n, q in zip(N, p))
+    assert solved <= 1.05 * real
 
 
 @pytest.mark.parametrize("schedule", ["grid", "cta"])
