@@ -750,6 +750,29 @@ __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double 
                                              double up0, ff spB, ff snE, const Res0& R, float (&r)[D],
                                              float (&rlo)[D]) {
     const ff d = split_d(up0 - u[0]);
+    // 2 S_k (DIR = 0: u[l], l < k of the other parity, without the u[0] term
+    // of odd k, which a_k d already holds) or 2 T_k (DIR = 1: l > k of the
+    // other parity).  Up to D = 6 each term enters the residual's compensated
+    // sum directly; wider blocks keep compensated running sums per parity,
+    // S_k = S_{k-2} + 2 u[k-1] (T_k = T_{k+2} + 2 u[k+1]): one pair add per
+    // coefficient instead of O(D^2 / 4).
+    ff run[D];
+    if constexpr (D > 6) {
+        ff par[2] = {ff{0.f, 0.f}, ff{0.f, 0.f}};
+        if constexpr (DIR == 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                if (k >= 2) acc_add(par[k & 1].hi, par[k & 1].lo, 2.f * us[k - 1].hi, 2.f * us[k - 1].lo);
+                run[k] = par[k & 1];
+            }
+        } else {
+#pragma unroll
+            for (int k = D - 1; k >= 0; --k) {
+                if (k + 1 < D) acc_add(par[k & 1].hi, par[k & 1].lo, 2.f * us[k + 1].hi, 2.f * us[k + 1].lo);
+                run[k] = par[k & 1];
+            }
+        }
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const ff Fk = split_d(F[k]);
@@ -758,8 +781,9 @@ __device__ __forceinline__ void residual0_ff(const double (&F)[D], const double 
         acc_add(s, c, sg * d.hi, sg * d.lo);
         acc_add(s, c, sg * spB.hi, sg * spB.lo);
         acc_add(s, c, -snE.hi, -snE.lo);
-        if constexpr (DIR == 0) {
-            // 2 S_k with S_k's u[0] term (odd k) already inside a_k d
+        if constexpr (D > 6) {
+            acc_add(s, c, run[k].hi, run[k].lo);
+        } else if constexpr (DIR == 0) {
 #pragma unroll
             for (int l = k - 1; l >= 1; l -= 2) acc_add(s, c, 2.f * us[l].hi, 2.f * us[l].lo);
         } else {
