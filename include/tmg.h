@@ -416,6 +416,50 @@ tmg_status tmg_batch_group_info(const tmg_batch *batch, int g, int *p_t, int64_t
 
 void tmg_destroy_batched(tmg_batch *batch);
 
+/* ----------------------------------------------- space-time heat -- */
+
+typedef struct tmg_heat tmg_heat;
+
+/*
+ * The paper's outlook (Section 7): the heat equation u_t - Delta u = f on the
+ * unit square, zero Dirichlet boundary values, the 5-point finite-difference
+ * Laplacian A_h on an n x n interior grid (h = 1/(n+1), n = 2^k - 1), and the
+ * DG-in-time discretisation of Section 2 of degree p_t (0..5) with N = 2^j
+ * steps of size tau.  The system is block lower-bidiagonal (eq.
+ * chap4_generalLinearSystemODE with lambda replaced by A_h): diagonal blocks
+ * G = K (x) I + tau Mhat (x) A_h, sub-diagonal blocks -(a b^T) (x) I.  Arrays
+ * are device FP64, [N][p_t+1][n][n] (interval, Legendre coefficient, row,
+ * column); f is the load vector, u0 the initial field [n][n].
+ *
+ * The solver is the time multigrid of Section 3 with the damped block Jacobi
+ * smoother of eq. chap4_ODESmoother (omega = 1/2, the uniform damping that
+ * bounds the smoothing factor of every spatial mode), in which each block
+ * inverse is replaced by one multigrid V(1,1)-cycle in space (damped
+ * point-block Jacobi omega = 4/5, full weighting, bilinear prolongation,
+ * down to one grid point); time coarsens by two to one interval, solved by
+ * nu_c (1..16) spatial V-cycles.  opts: tol, max_cycles, nu1, nu2 (V-cycles
+ * only, gamma = 1); the arithmetic is FP64 whatever opts->precision says.
+ * Returns TMG_EINVAL for other sizes or options.
+ */
+tmg_status tmg_heat_setup(tmg_heat **plan, int p_t, double tau, int n, int64_t N, const tmg_opts *opts, int nu_c,
+                          void *stream);
+
+/* Cycles from u = 0 until ||F - L u|| <= tol ||F|| (F: f with a (x) u0 in the
+ * first interval); TMG_ENOTCONV after max_cycles.  Synchronises the stream. */
+tmg_status tmg_heat_solve(tmg_heat *plan, const double *f, const double *u0, double *u);
+
+/* Exactly one cycle applied to u in place. */
+tmg_status tmg_heat_cycle(tmg_heat *plan, const double *f, const double *u0, double *u);
+
+/* r = F - L u (device arrays as above). */
+tmg_status tmg_heat_residual(tmg_heat *plan, const double *f, const double *u0, const double *u, double *r);
+
+/* Cycles and relative residual of the last tmg_heat_solve, and up to hist_len
+ * entries of its residual history; any pointer may be NULL. */
+tmg_status tmg_heat_stats(const tmg_heat *plan, int *cycles, double *rel_res, double *hist, int hist_len);
+
+void tmg_heat_destroy(tmg_heat *plan);
+
 /* Release the plan and every resource it owns.  NULL is ignored. */
 void tmg_destroy(tmg_plan *plan);
 

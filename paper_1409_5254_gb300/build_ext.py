@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtmg.so")
 SOURCES = ["tmg_inst_f64_w21.cu", "tmg_inst_f32_w21.cu", "tmg_inst_f64_wide.cu", "tmg_inst_f32_wide.cu",
            "tmg_api.cu", "tmg_inst_f32.cu", "tmg_inst_f32_hi.cu", "tmg_inst_f64.cu", "tmg_inst_f64_hi.cu",
-           "tmg_adjoint.cu", "tmg_batched.cu", "tmg_batched_hi.cu", "tmg_batched_wide.cu", "tmg_noalloc.cu"]
+           "tmg_adjoint.cu", "tmg_batched.cu", "tmg_batched_hi.cu", "tmg_batched_wide.cu", "tmg_noalloc.cu", "tmg_heat.cu"]
 HEADERS = ["tmg_kernels.cuh", "tmg_impl.cuh", "tmg_plan.h", "tmg_batched.cuh", "tmg_batched_host.h",
            "tmg_scan.cuh", "tmg_setup_math.h", "tmg_nvtx.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -20,6 +20,9 @@ Recipes (seed = workload index unless stated):
   log-uniform in [1e-3, 1e3].
 * ``random_guess``        -- U(0, 1) initial vectors (the measurement protocol of
   Section 4.2: zero right-hand side, random start).
+* ``heat_problem``        -- the space-time heat equation on an n x n grid:
+  f(t, x) = sum_{j<3} s_j(x) sin(2 pi m_j t / T), s_j(x) ~ U(-1, 1) per grid
+  point, m_j ~ U{1..8}; u0(x) ~ U(-1, 1); tau = T / N.
 """
 from __future__ import annotations
 
@@ -28,7 +31,7 @@ import math
 import numpy as np
 
 __all__ = ["Forcing", "scalar_problem", "load_vector", "random_guess", "heat_modes",
-           "uneven_batch", "adjoint_problem"]
+           "uneven_batch", "adjoint_problem", "heat_problem"]
 
 
 class Forcing:
@@ -204,3 +207,21 @@ def sinusoid_batch_params(seed: int, n: int, n_terms: int = 4):
     """Per-instance sinusoid forcings as in the single-problem recipe."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-1.0, 1.0, (n, n_terms)), rng.integers(1, 9, (n, n_terms)).astype(np.float64)
+
+
+def heat_problem(seed: int, N: int, p: int, n: int, T: float = 1.0, q: int = 8):
+    """(tau, F, u0): load vectors F of shape (N, p+1, n, n) and u0 of shape (n, n)."""
+    rng = np.random.default_rng(seed)
+    sx = rng.uniform(-1.0, 1.0, (3, n, n))
+    m = rng.integers(1, 9, 3).astype(np.float64)
+    u0 = rng.uniform(-1.0, 1.0, (n, n))
+    tau = T / N
+    xg, wg = np.polynomial.legendre.leggauss(q)
+    sq = 0.5 * (xg + 1.0)
+    tab = _legendre_table(p, sq) * (0.5 * wg)[:, None]      # (q, d)
+    t = (np.arange(N, dtype=np.float64)[:, None] + sq[None, :]) * tau   # (N, q)
+    F = np.zeros((N, p + 1, n, n))
+    for j in range(3):
+        lt = tau * (np.sin(2.0 * math.pi * m[j] / T * t) @ tab)       # (N, d)
+        F += lt[:, :, None, None] * sx[j][None, None]
+    return tau, F, u0

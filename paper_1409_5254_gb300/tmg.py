@@ -46,7 +46,9 @@ EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_
            "tmg_stats", "tmg_error_vs_fp64", "tmg_plan_shape", "tmg_level_constants", "tmg_transfer_matrices", "tmg_plan_info",
            "tmg_plan_launches", "tmg_profile_cycle", "tmg_inspect", "tmg_residual_norm_noalloc", "tmg_destroy", "tmg_strerror",
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
-           "tmg_stats_batched", "tmg_error_vs_fp64_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched"]
+           "tmg_stats_batched", "tmg_error_vs_fp64_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched",
+           "tmg_heat_setup", "tmg_heat_solve", "tmg_heat_cycle", "tmg_heat_residual", "tmg_heat_stats",
+           "tmg_heat_destroy"]
 
 
 def library_path() -> str:
@@ -111,6 +113,16 @@ def _lib():
         for name in ("tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched", "tmg_stats_batched",
                      "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info"):
             getattr(L, name).restype = ctypes.c_int
+        L.tmg_heat_setup.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int64, ctypes.POINTER(_Opts), ctypes.c_int, _vp]
+        L.tmg_heat_solve.argtypes = [_vp, _vp, _vp, _vp]
+        L.tmg_heat_cycle.argtypes = [_vp, _vp, _vp, _vp]
+        L.tmg_heat_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.tmg_heat_stats.argtypes = [_vp, _ip, _dp, _dp, ctypes.c_int]
+        for name in ("tmg_heat_setup", "tmg_heat_solve", "tmg_heat_cycle", "tmg_heat_residual", "tmg_heat_stats"):
+            getattr(L, name).restype = ctypes.c_int
+        L.tmg_heat_destroy.argtypes = [_vp]
+        L.tmg_heat_destroy.restype = None
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
@@ -534,3 +546,81 @@ class Batch:
         x = np.asarray(x)
         return [x[self.offsets[i]:self.offsets[i + 1]].reshape(int(self.N[i]), int(self.p[i]) + 1)
                 for i in range(self.n)]
+
+
+class HeatPlan:
+    """tmg_heat_setup / tmg_heat_solve / tmg_heat_destroy: the space-time heat
+    equation on an n x n grid with N DG-in-time intervals of degree p (see
+    include/tmg.h).  Arrays are float64 CUDA tensors of shape (N, p+1, n, n);
+    u0 has shape (n, n)."""
+
+    def __init__(self, p: int, tau: float, n: int, N: int, *, tol: float = 1e-10, max_cycles: int = 100,
+                 nu1: int = 1, nu2: int = 1, nu_c: int = 2, stream=None):
+        L = _lib()
+        o = _opts(tol=tol, max_cycles=max_cycles, nu1=nu1, nu2=nu2, gamma=1, precision="fp64")
+        self.p, self.d, self.n, self.N, self.tau = p, p + 1, n, N, tau
+        self._stream = stream
+        handle = _vp()
+        sp = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        _check(L.tmg_heat_setup(ctypes.byref(handle), p, tau, n, N, ctypes.byref(o), nu_c, sp), "tmg_heat_setup")
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().tmg_heat_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _ptr(self, t, shape, name):
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+        if tuple(t.shape) != tuple(shape) and t.numel() != int(np.prod(shape)):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        _order_after_current(self._stream, t)
+        return ctypes.c_void_p(t.data_ptr())
+
+    def _shape(self):
+        return (self.N, self.d, self.n, self.n)
+
+    def solve(self, f, u0, u=None, *, allow_notconv: bool = False):
+        import torch
+        if u is None:
+            u = torch.empty(self._shape(), dtype=torch.float64, device=f.device)
+        ok = (TMG_OK, TMG_ENOTCONV) if allow_notconv else (TMG_OK,)
+        _check(_lib().tmg_heat_solve(self._h, self._ptr(f, self._shape(), "f"), self._ptr(u0, (self.n, self.n), "u0"),
+                                     self._ptr(u, self._shape(), "u")), "tmg_heat_solve", ok)
+        return u
+
+    def cycle(self, f, u0, u):
+        _check(_lib().tmg_heat_cycle(self._h, self._ptr(f, self._shape(), "f"), self._ptr(u0, (self.n, self.n), "u0"),
+                                     self._ptr(u, self._shape(), "u")), "tmg_heat_cycle")
+        return u
+
+    def residual(self, f, u0, u, r=None):
+        import torch
+        if r is None:
+            r = torch.empty(self._shape(), dtype=torch.float64, device=f.device)
+        _check(_lib().tmg_heat_residual(self._h, self._ptr(f, self._shape(), "f"),
+                                        self._ptr(u0, (self.n, self.n), "u0"), self._ptr(u, self._shape(), "u"),
+                                        self._ptr(r, self._shape(), "r")), "tmg_heat_residual")
+        return r
+
+    def stats(self, hist_len: int = 256) -> SolveStats:
+        c = ctypes.c_int(0)
+        rel = ctypes.c_double(0)
+        hist = np.full(hist_len, np.nan)
+        _check(_lib().tmg_heat_stats(self._h, ctypes.byref(c), ctypes.byref(rel),
+                                     hist.ctypes.data_as(_dp), hist_len), "tmg_heat_stats")
+        return SolveStats(TMG_OK, c.value, rel.value, hist[~np.isnan(hist)])
