@@ -512,6 +512,8 @@ def run_ours(args):
             nus[f"V({nu[0]},{nu[1]})"] = single_line(tmg, torch, stream, F, u, P_MAIN, TAU, "mixed", N_MIN, nside,
                                                      args.eager, hbm_peak, peak_kind, nu=nu)
         extra["nu_variants"] = nus
+        # the space-time heat equation with a spatial operator (Section 7 outlook)
+        extra["space_time_heat"] = _space_time_heat(dev, stream, nside, torch, hbm_peak, peak_kind, args.eager)
 
     if not args.quick:
         # every rank solves its shard of the batched workloads
@@ -542,6 +544,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(batched=not args.quick)
+        if not args.quick:
+            cpu["space_time_heat"] = heat_cpu_baseline()
 
     plan.close()
     if rank == 0:
@@ -564,6 +568,98 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+HEAT_N, HEAT_NX, HEAT_P = 4096, 127, 1   # space-time heat: intervals, interior grid points a side, degree
+
+
+def _space_time_heat(dev, stream, nsteps, torch, hbm_peak, peak_kind, eager):
+    """The space-time heat equation of the paper's outlook (Section 7): the
+    5-point Laplacian on a 127 x 127 interior grid (h = 1/128), N = 4096 DG
+    intervals of degree 1 on (0, 1), 1.32e8 space-time unknowns (the size of
+    the paper's own heat run), to TOL.  One step = one solve from zero,
+    median of `nsteps` (mixed form) or 3 (FP64 form) CUDA-event timed solves
+    on the plan's stream.  The roofline is the level-0 post kernel's
+    (prolongation + post-smoothing accumulating into the correction: reads
+    r and the coarse correction, reads and writes the output, 4-byte
+    values)."""
+    from paper_1409_5254_gb300 import inputs, tmg
+    tau, F, u0 = inputs.heat_problem(1, HEAT_N, HEAT_P, HEAT_NX)
+    Fd = torch.from_numpy(F).to(dev)
+    u0d = torch.from_numpy(u0).to(dev)
+    del F
+    u = torch.empty_like(Fd)
+    d, n, N = HEAT_P + 1, HEAT_NX, HEAT_N
+    nc = (n - 1) // 2
+    dofs = Fd.numel()
+    out = {"unit": "DoF/s", "grid": f"{n}x{n}", "N": N, "p_t": HEAT_P, "tau": tau, "dofs": dofs, "tol": TOL,
+           "data": "synthetic: f(t,x) = sum of 3 space fields U(-1,1) x sin(2 pi m t), u0 ~ U(-1,1)"}
+    u_mixed = None
+    for prec, steps in (("mixed", nsteps), ("fp64", 3)):
+        with tmg.HeatPlan(HEAT_P, tau, n, N, tol=TOL, max_cycles=100, precision=prec, use_graph=not eager,
+                          stream=stream) as hp:
+            hp.solve(Fd, u0d, u)
+            times = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hp.solve(Fd, u0d, u)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ms = statistics.median(times)
+            st = hp.stats()
+            info = hp.info()
+            res = {"value": dofs / (ms * 1e-3), "ms_per_step": round(ms, 3), "solves_timed": steps,
+                   "cycles": st.cycles, "rel_res_fp64": st.rel_res,
+                   "launches_per_cycle": info["launches_per_cycle"], "time_levels": info["time_levels"],
+                   "space_levels": info["space_levels"], "workspace_bytes": info["workspace_bytes"]}
+            if prec == "mixed":
+                u_mixed = u.clone()
+            else:
+                res["mixed_vs_fp64_max_rel"] = float((u_mixed - u).abs().max() / u.abs().max())
+            prof = hp.profile(Fd, u0d, u, reps=10)
+            es = 4 if prec == "mixed" else 8
+            post_bytes = es * d * N * (3 * n * n + nc * nc)
+            res["kernels_ms"] = {k: round(v, 4) for k, v in prof.items()}
+            if prec == "mixed":
+                res["roofline"] = {"kernel": "kh_post_w (spatial level 0, accumulating)", "bound": "hbm",
+                                   "achieved": post_bytes / (prof["post"] * 1e-3) / 1e9, "peak": hbm_peak,
+                                   "unit": "GB/s",
+                                   "frac": post_bytes / (prof["post"] * 1e-3) / 1e9 / hbm_peak,
+                                   "traffic": None, "peak_kind": peak_kind,
+                                   "bytes_model": "4 B x (p_t+1) x N x (3 n^2 + nc^2): r, out read+write, "
+                                                  "coarse correction"}
+                pre_bytes = 4 * d * N * (n * n + nc * nc)
+                res_bytes = 4 * d * N * n * n * 3
+                upd_bytes = d * N * n * n * (4 + 16 + 16)
+                res["kernel_fracs"] = {
+                    "pre": round(pre_bytes / (prof["pre"] * 1e-3) / 1e9 / hbm_peak, 3),
+                    "post": round(post_bytes / (prof["post"] * 1e-3) / 1e9 / hbm_peak, 3),
+                    "time_residual": round(res_bytes / (prof["resid"] * 1e-3) / 1e9 / hbm_peak, 3),
+                    "pair_update": round(upd_bytes / (prof["update"] * 1e-3) / 1e9 / hbm_peak, 3),
+                    "note": "algorithmic bytes / event time / measured HBM copy bandwidth"}
+            out[prec] = res
+    out["value"] = out["mixed"]["value"]
+    del Fd, u0d, u, u_mixed
+    torch.cuda.empty_cache()
+    return out
+
+
+def heat_cpu_baseline(sample_N: int = 16):
+    """The heat oracle (oracle/heat.py) on one host core, on the first
+    sample_N of the 4096 intervals of the same problem (same grid, step and
+    forcing)."""
+    import oracle.heat as oheat
+    from paper_1409_5254_gb300 import inputs
+    tau, F, u0 = inputs.heat_problem(1, HEAT_N, HEAT_P, HEAT_NX)
+    F = F[:sample_N].copy()
+    t0 = time.perf_counter()
+    _, hist = oheat.solve(HEAT_P, tau, HEAT_NX, F, u0, tol=TOL, max_cycles=100)
+    t = time.perf_counter() - t0
+    return {"value": F.size / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_N} of the 4096 intervals, {HEAT_NX}x{HEAT_NX} grid, textbook space-time "
+                      f"cycle to {TOL} ({len(hist) - 1} cycles), {t:.2f} s"}
 
 
 def _time_batch(batch, f, u0, u, steps, stream, torch):
@@ -928,8 +1024,9 @@ def main():
     ap.add_argument("--n-log2", type=int, default=24, help="intervals = 2^n (smaller cases for ncu captures)")
     ap.add_argument("--p-t", type=int, default=1, help="degree of the long-horizon line (profiling other degrees "
                     "with --quick; the benchmark line is p_t = 1)")
-    ap.add_argument("--workload", default="all", choices=["all", "heat", "uneven", "gradients"],
-                    help="all: the benchmark line; otherwise only that batched workload (profiling)")
+    ap.add_argument("--workload", default="all", choices=["all", "heat", "uneven", "gradients", "space_time_heat"],
+                    help="all: the benchmark line; otherwise only that batched workload, or the space-time heat "
+                         "equation (profiling)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="forms of the batched workloads run with --workload")
     ap.add_argument("--batch-stride", type=int, default=1,
@@ -942,6 +1039,8 @@ def main():
     P_MAIN = args.p_t
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "space_time_heat":
+        run_space_time_heat(args)
     elif args.workload != "all":
         run_one_batched(args)
     else:
@@ -959,6 +1058,17 @@ def run_one_batched(args):
     out = run_batched_configs(dev, stream, args.steps, torch, only=(args.workload,), precisions=prec,
                               eager=args.eager)
     print(json.dumps(out))
+
+
+def run_space_time_heat(args):
+    """The space-time heat line alone, one GPU (for profiling its kernels)."""
+    import torch
+    from paper_1409_5254_gb300 import build_ext
+    build_ext.build()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream()
+    hbm_peak, peak_kind = peaks()
+    print(json.dumps(_space_time_heat(dev, stream, max(3, args.steps), torch, hbm_peak, peak_kind, args.eager)))
 
 
 if __name__ == "__main__":

@@ -438,8 +438,14 @@ typedef struct tmg_heat tmg_heat;
  * point-block Jacobi omega = 4/5, full weighting, bilinear prolongation,
  * down to one grid point); time coarsens by two to one interval, solved by
  * nu_c (1..16) spatial V-cycles.  opts: tol, max_cycles, nu1, nu2 (V-cycles
- * only, gamma = 1); the arithmetic is FP64 whatever opts->precision says.
- * Returns TMG_EINVAL for other sizes or options.
+ * only, gamma = 1), use_graph (each cycle replayed from a CUDA graph captured
+ * at its first use for the given arrays), precision: TMG_FP64 (every step in
+ * FP64, the textbook iterates) or TMG_MIXED (the residual of the FP64 iterate
+ * formed in FP64, one cycle in FP32 from a zero correction c, u += c in FP64;
+ * iterative refinement to the same FP64 tolerance).  The convergence test
+ * always uses the FP64 residual.  n <= 2^14 - 1, N <= 2^40.  Returns
+ * TMG_EINVAL for other sizes or options, TMG_ENOMEM when the workspace
+ * (about 7 N (p_t+1) n^2 values of the cycle precision) does not fit.
  */
 tmg_status tmg_heat_setup(tmg_heat **plan, int p_t, double tau, int n, int64_t N, const tmg_opts *opts, int nu_c,
                           void *stream);
@@ -457,6 +463,23 @@ tmg_status tmg_heat_residual(tmg_heat *plan, const double *f, const double *u0, 
 /* Cycles and relative residual of the last tmg_heat_solve, and up to hist_len
  * entries of its residual history; any pointer may be NULL. */
 tmg_status tmg_heat_stats(const tmg_heat *plan, int *cycles, double *rel_res, double *hist, int hist_len);
+
+/* Diagnostics: CUDA-event times on the plan's stream (ms per launch, mean of
+ * reps) of the level-0 kernels after one cycle from u: ms[0] the time
+ * residual in the cycle precision, ms[1] the fused pre-smoothing, residual
+ * and restriction of spatial level 0, ms[2] the fused prolongation and
+ * post-smoothing of spatial level 0 accumulating into a work array, ms[3]
+ * the mixed form's float-pair residual update (u += c, r -= L c) or the FP64
+ * form's FP64 residual, ms[4] one whole cycle.  n_ms >= 5.  u is left
+ * arbitrary (solve again afterwards). */
+tmg_status tmg_heat_profile(tmg_heat *plan, const double *f, const double *u0, double *u, int reps, double *ms,
+                            int n_ms);
+
+/* Time and spatial levels of the hierarchy, kernels (and memsets) one cycle
+ * issues after its first use (0 before), workspace bytes; any pointer may be
+ * NULL. */
+tmg_status tmg_heat_info(const tmg_heat *plan, int *time_levels, int *space_levels, int *launches_per_cycle,
+                         size_t *workspace_bytes);
 
 void tmg_heat_destroy(tmg_heat *plan);
 

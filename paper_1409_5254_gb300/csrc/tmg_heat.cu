@@ -17,16 +17,33 @@
 // exactly.  Time coarsens by two down to one interval, whose block is solved
 // by nu_c spatial V-cycles; restriction and prolongation in time act on the
 // Legendre coefficients of every grid point (eqs. chap4_restrictionTime,
-// chap4_prolongationTime).  FP64 throughout.
+// chap4_prolongationTime).
 //
-// Layout: [interval][coefficient][row][column], row-major, FP64.  Every
-// spatial V-cycle runs on all intervals of a time level at once; the kernels
-// are grid-stride loops over (interval, row, column) points or values.
+// Two precisions.  TMG_FP64: every step in FP64 (the textbook iterates).
+// TMG_MIXED: the residual of the FP64 iterate is formed in FP64 and rounded
+// to FP32, one cycle in FP32 computes the correction c from zero, u += c in
+// FP64 -- iterative refinement, which reaches the FP64 solution because the
+// FP32 cycle contracts the error of every correction.
+//
+// Kernels.  The spatial V-cycle keeps no smoothed iterate in memory: the
+// first Jacobi sweep from zero is pointwise (x = omega Dinv r), so the
+// "pre" kernel recomputes x from r, forms the residual r - G x and restricts
+// it by full weighting in one pass; the "post" kernel recomputes x, adds the
+// bilinear prolongation of the coarse correction, applies the second sweep
+// and writes (or accumulates into the time iterate) the result.  Per spatial
+// level: read r twice, the coarse values once, write the result once.  Both
+// stream a warp down a 64-column strip with the stencil's rows in registers.
+// In the mixed form the residual of the FP64 iterate is kept as a float pair
+// and updated by r -= L c after every cycle (float-pair arithmetic on the
+// exact FP32 correction), with one FP64 residual to confirm convergence.
+//
+// Layout: [interval][coefficient][row][column], row-major.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/tmg.h"
@@ -40,262 +57,685 @@ constexpr double kOmegaT = 0.5;
 constexpr double kOmegaS = 0.8;
 
 // Constants of one (time level, spatial level): the block G_tau on grid
-// spacing h, its point block's inverse, the damping.
-template <int D>
+// spacing h and its point block's inverse.
+template <int D, typename T>
 struct HeatK {
-    double K[D * D];      // upwind DG stiffness block (Section 2)
-    double Mh[D];         // reference mass matrix diagonal 1/(2k+1)
-    double Dinv[D * D];   // (K + tau (4/h^2) Mhat)^{-1}
-    double tau;
-    double h2inv;         // 1/h^2
+    T K[D * D];      // upwind DG stiffness block (Section 2)
+    T Mh[D];         // reference mass matrix diagonal 1/(2k+1), times tau / h^2
+    T Dinv[D * D];   // (K + tau (4/h^2) Mhat)^{-1}
 };
 
-template <int D>
-HeatK<D> heat_consts(double tau, int n) {
-    HeatK<D> C;
+template <int D, typename T>
+HeatK<D, T> heat_consts(double tau, int n) {
+    HeatK<D, T> C;
     double A[tmg::kMaxDWide * tmg::kMaxDWide], Ai[tmg::kMaxDWide * tmg::kMaxDWide];
     tmg_host::local_blocks(D, 0.0, A);   // K
-    for (int i = 0; i < D * D; ++i) C.K[i] = A[i];
-    for (int k = 0; k < D; ++k) C.Mh[k] = 1.0 / (2.0 * k + 1.0);
-    const double h = 1.0 / (n + 1);
-    C.h2inv = 1.0 / (h * h);
-    C.tau = tau;
-    tmg_host::local_blocks(D, tau * 4.0 * C.h2inv, A);   // K + tau (4/h^2) Mhat
+    for (int i = 0; i < D * D; ++i) C.K[i] = (T)A[i];
+    const double h = 1.0 / (n + 1), h2inv = 1.0 / (h * h);
+    for (int k = 0; k < D; ++k) C.Mh[k] = (T)(tau * h2inv / (2.0 * k + 1.0));
+    tmg_host::local_blocks(D, tau * 4.0 * h2inv, A);   // K + tau (4/h^2) Mhat
     tmg_host::invert(D, A, Ai);
-    for (int i = 0; i < D * D; ++i) C.Dinv[i] = Ai[i];
+    for (int i = 0; i < D * D; ++i) C.Dinv[i] = (T)Ai[i];
     return C;
 }
 
-// (G x)_k at one grid point: K x + tau Mhat (A_h x); x at (m, i, j) for every
-// coefficient and the four neighbours' values (zero outside the grid).
-template <int D>
-__device__ __forceinline__ void block_at(const HeatK<D>& C, const double* __restrict__ x, int64_t base, int n, int i,
-                                         int j, double (&xc)[D], double (&gx)[D]) {
-    const int64_t nn = (int64_t)n * n;
-    double lap[D];
+// (G x)_k at one grid point from x there (c) and the sum of its four
+// neighbours (nb, zero outside the grid): K c + (tau/h^2) Mhat (4 c - nb).
+template <int D, typename T>
+__device__ __forceinline__ void apply_G(const HeatK<D, T>& C, const T (&c)[D], const T (&nb)[D], T (&gx)[D]) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        const double* xk = x + base + k * nn;
-        const int64_t o = (int64_t)i * n + j;
-        const double c = xk[o];
-        double s = 4.0 * c;
-        if (i > 0) s -= xk[o - n];
-        if (i + 1 < n) s -= xk[o + n];
-        if (j > 0) s -= xk[o - 1];
-        if (j + 1 < n) s -= xk[o + 1];
-        xc[k] = c;
-        lap[k] = s * C.h2inv;
-    }
+        T s = C.Mh[k] * (T(4) * c[k] - nb[k]);
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        double s = C.tau * C.Mh[k] * lap[k];
-#pragma unroll
-        for (int l = 0; l < D; ++l) s = fma(C.K[k * D + l], xc[l], s);
+        for (int l = 0; l < D; ++l) s = fma(C.K[k * D + l], c[l], s);
         gx[k] = s;
     }
 }
 
-// Point (m, i, j) of a grid-stride loop over npts = N n^2 points.
-struct Pt {
-    int64_t m;
-    int i, j;
-    int64_t base;   // offset of (m, 0, 0, 0)
-    int64_t o;      // i n + j
-};
-
-template <int D>
-__device__ __forceinline__ Pt point(int64_t t, int n) {
-    const int64_t nn = (int64_t)n * n;
-    Pt p;
-    p.m = t / nn;
-    p.o = t - p.m * nn;
-    p.i = (int)(p.o / n);
-    p.j = (int)(p.o - (int64_t)p.i * n);
-    p.base = p.m * D * nn;
-    return p;
+// y = Dinv v
+template <int D, typename T>
+__device__ __forceinline__ void apply_Dinv(const HeatK<D, T>& C, const T (&v)[D], T (&y)[D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        T s = T(0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(C.Dinv[k * D + l], v[l], s);
+        y[k] = s;
+    }
 }
 
-// Time residual g = F + a e_{m-1} - G_tau u (a_k = (-1)^k, e = sum_k u_k of
-// the previous interval; u0 before the first one, or 0 when u0 is nullptr);
-// with norm2 != nullptr also sum g^2 (atomic per block).
-template <int D>
-__global__ void __launch_bounds__(kHT) kh_time_resid(const double* __restrict__ F, const double* __restrict__ u,
-                                                     const double* __restrict__ u0, double* __restrict__ g, int64_t N,
-                                                     int n, HeatK<D> C, double* __restrict__ norm2) {
-    const int64_t nn = (int64_t)n * n, npts = N * nn;
-    double ss = 0.0;
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < npts; t += (int64_t)gridDim.x * kHT) {
-        const Pt p = point<D>(t, n);
-        double xc[D], gx[D];
-        block_at<D>(C, u, p.base, n, p.i, p.j, xc, gx);
-        double e = 0.0;
-        if (p.m > 0) {
+// ---------------------------------------------------------------- row tasks
+// Kernels on the full spatial grid of a time level (residuals, updates,
+// transfers in time) run one CTA-wide task per (interval, block of kRB grid
+// rows), kRT threads across the row, each thread down the kRB rows of its
+// column; offsets within an interval are 32-bit (D n^2 < 2^31).
+constexpr int kRT = 128;
+constexpr int kRB = 4;   // rows per task: four independent points per thread keep loads in flight
+
+struct RowTask {
+    int64_t m;
+    int i0;
+};
+
+__device__ __forceinline__ int row_blocks(int n) { return (n + kRB - 1) / kRB; }
+
+__device__ __forceinline__ RowTask row_task(int64_t t, int nrb) {
+    RowTask r;
+    r.m = t / nrb;
+    r.i0 = (int)(t - r.m * nrb) * kRB;
+    return r;
+}
+
+// x at (i, j) of one interval (pointer at its coefficient 0) and the sum of
+// its four neighbours, zero outside the grid.
+template <int D, typename T>
+__device__ __forceinline__ void stencil_at(const T* __restrict__ x, int nn, int n, int i, int j, T (&c)[D],
+                                           T (&nb)[D]) {
+    const int o = i * n + j;
 #pragma unroll
-            for (int k = 0; k < D; ++k) e += u[p.base - D * nn + k * nn + p.o];
-        } else if (u0 != nullptr) {
-            e = u0[p.o];
-        }
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            const int64_t idx = p.base + k * nn + p.o;
-            const double v = F[idx] + ((k & 1) ? -e : e) - gx[k];
-            g[idx] = v;
-            ss = fma(v, v, ss);
-        }
+    for (int k = 0; k < D; ++k) {
+        const T* xk = x + (int64_t)k * nn;
+        c[k] = xk[o];
+        T s = T(0);
+        if (i > 0) s += xk[o - n];
+        if (i + 1 < n) s += xk[o + n];
+        if (j > 0) s += xk[o - 1];
+        if (j + 1 < n) s += xk[o + 1];
+        nb[k] = s;
     }
-    if (norm2 != nullptr) {
+}
+
+template <bool NORM>
+__device__ __forceinline__ void norm_flush(double ss, double* __restrict__ norm2) {
+    if (NORM) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, off);
         if ((threadIdx.x & 31) == 0) atomicAdd(norm2, ss);
     }
 }
 
-// x = omega_s Dinv r (the first Jacobi sweep from zero); with n = 1 and
-// omega = 1 the exact solve of a one-point grid.
-template <int D>
-__global__ void __launch_bounds__(kHT) kh_smooth0(const double* __restrict__ r, double* __restrict__ x, int64_t npts,
-                                                  int64_t nn, HeatK<D> C, double omega) {
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < npts; t += (int64_t)gridDim.x * kHT) {
-        const int64_t m = t / nn, o = t - m * nn, base = m * D * nn + o;
-        double rv[D];
+// Residual g = F + a e_{m-1} - G_tau u (TIME: a_k = (-1)^k, e = sum_k u_k of
+// the previous interval, u0 before the first one or 0 when u0 is nullptr;
+// without TIME the residual r - G x of independent block solves), computed
+// in T and stored as TO.  PAIR: stored as the float pair (g, gl) with
+// g + gl = the FP64 value to 2^-48.  NORM: sum of squares into *norm2.
+template <int D, typename T, typename TO, bool TIME, bool NORM, bool PAIR>
+__global__ void __launch_bounds__(kRT) kh_resid(const T* __restrict__ F, const T* __restrict__ u,
+                                                const double* __restrict__ u0, TO* __restrict__ g,
+                                                float* __restrict__ gl, int64_t N, int n, HeatK<D, T> C,
+                                                double* __restrict__ norm2) {
+    const int nn = n * n;
+    const int nrb = row_blocks(n);
+    const int64_t tasks = N * nrb;
+    double ss = 0.0;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const RowTask rt = row_task(t, nrb);
+        const int64_t base = rt.m * D * (int64_t)nn;
+        const T* um = u + base;
+        for (int j = threadIdx.x; j < n; j += kRT)
 #pragma unroll
-        for (int k = 0; k < D; ++k) rv[k] = r[base + k * nn];
+        for (int rr = 0; rr < kRB; ++rr) {
+            const int i = rt.i0 + rr;
+            if (i >= n) break;
+            const int o = i * n + j;
+            T c[D], nb[D], gx[D];
+            stencil_at<D, T>(um, nn, n, i, j, c, nb);
+            apply_G<D, T>(C, c, nb, gx);
+            T e = T(0);
+            if (TIME) {
+                if (rt.m > 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            double s = 0.0;
-#pragma unroll
-            for (int l = 0; l < D; ++l) s = fma(C.Dinv[k * D + l], rv[l], s);
-            x[base + k * nn] = omega * s;
-        }
-    }
-}
-
-// y = r - G x (mode 0), or y = x + omega_s Dinv (r - G x) (mode 1: a Jacobi
-// sweep, out of place).
-template <int D>
-__global__ void __launch_bounds__(kHT) kh_sweep(const double* __restrict__ r, const double* __restrict__ x,
-                                                double* __restrict__ y, int64_t N, int n, HeatK<D> C, int mode,
-                                                double omega) {
-    const int64_t nn = (int64_t)n * n, npts = N * nn;
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < npts; t += (int64_t)gridDim.x * kHT) {
-        const Pt p = point<D>(t, n);
-        double xc[D], gx[D], res[D];
-        block_at<D>(C, x, p.base, n, p.i, p.j, xc, gx);
-#pragma unroll
-        for (int k = 0; k < D; ++k) res[k] = r[p.base + k * nn + p.o] - gx[k];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            double v = res[k];
-            if (mode == 1) {
-                double s = 0.0;
-#pragma unroll
-                for (int l = 0; l < D; ++l) s = fma(C.Dinv[k * D + l], res[l], s);
-                v = fma(omega, s, xc[k]);
+                    for (int k = 0; k < D; ++k) e += um[(int64_t)(k - D) * nn + o];
+                } else if (u0 != nullptr) {
+                    e = (T)u0[o];
+                }
             }
-            y[p.base + k * nn + p.o] = v;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int64_t idx = base + (int64_t)k * nn + o;
+                const T v = F[idx] + ((k & 1) ? -e : e) - gx[k];
+                if (PAIR) {
+                    const float h = (float)v;
+                    g[idx] = (TO)h;
+                    gl[idx] = (float)(v - (T)h);
+                } else {
+                    g[idx] = (TO)v;
+                }
+                if (NORM) ss = fma((double)v, (double)v, ss);
+            }
+        }
+    }
+    norm_flush<NORM>(ss, norm2);
+}
+
+// Residual of u = 0 as a float pair: r = F, plus a (x) u0 in the first
+// interval; sum of squares into *norm2.
+template <int D>
+__global__ void __launch_bounds__(kRT) kh_init_pair(const double* __restrict__ F, const double* __restrict__ u0,
+                                                    float* __restrict__ rh, float* __restrict__ rl, int64_t N, int n,
+                                                    double* __restrict__ norm2) {
+    const int nn = n * n;
+    const int nrb = row_blocks(n);
+    const int64_t tasks = N * nrb;
+    double ss = 0.0;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const RowTask rt = row_task(t, nrb);
+        const int64_t base = rt.m * D * (int64_t)nn;
+        for (int j = threadIdx.x; j < n; j += kRT)
+#pragma unroll
+        for (int rr = 0; rr < kRB; ++rr) {
+            const int i = rt.i0 + rr;
+            if (i >= n) break;
+            const int o = i * n + j;
+            const double e = rt.m == 0 ? u0[o] : 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int64_t idx = base + (int64_t)k * nn + o;
+                const double v = F[idx] + ((k & 1) ? -e : e);
+                const float h = (float)v;
+                rh[idx] = h;
+                rl[idx] = (float)(v - (double)h);
+                ss = fma(v, v, ss);
+            }
+        }
+    }
+    norm_flush<true>(ss, norm2);
+}
+
+// Float-pair arithmetic (a value h + l, |l| <= ulp(h)/2): the error-free sum
+// of Knuth and the FMA-based error-free product; the products use __fmul_rn
+// so that no multiply is contracted into an FMA that would change them.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ FF quick_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    FF s = two_sum(a.h, b.h);
+    const FF t = two_sum(a.l, b.l);
+    s = quick_two_sum(s.h, s.l + t.h);
+    return quick_two_sum(s.h, s.l + t.l);
+}
+
+__device__ __forceinline__ FF ff_add_f(FF a, float b) {
+    const FF s = two_sum(a.h, b);
+    return quick_two_sum(s.h, s.l + a.l);
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.h, b.h);
+    const float e = fmaf(a.h, b.h, -p);
+    return quick_two_sum(p, fmaf(a.h, b.l, fmaf(a.l, b.h, e)));
+}
+
+// tau Mhat_kk / h^2 of one time level as float pairs (the K entries are +-1,
+// exact in any precision).
+template <int D>
+struct PairK {
+    float mh[D], ml[D];
+    float K[D * D];
+};
+
+template <int D>
+PairK<D> pair_consts(double tau, int n) {
+    PairK<D> P;
+    double A[tmg::kMaxDWide * tmg::kMaxDWide];
+    tmg_host::local_blocks(D, 0.0, A);
+    for (int i = 0; i < D * D; ++i) P.K[i] = (float)A[i];
+    const double h = 1.0 / (n + 1), h2inv = 1.0 / (h * h);
+    for (int k = 0; k < D; ++k) {
+        const double mu = tau * h2inv / (2.0 * k + 1.0);
+        P.mh[k] = (float)mu;
+        P.ml[k] = (float)(mu - (double)P.mh[k]);
+    }
+    return P;
+}
+
+// The mixed form's update after one FP32 correction cycle: u += c (FP64),
+// r -= L c in float-pair arithmetic (c is exact in FP32, so L c is formed to
+// about 2^-44 of its size and the updated residual follows the true residual
+// of u across the cycles), sum of r_h^2 into *norm2.  (L c)_m =
+// G_tau c_m - a (b^T c_{m-1}); the first interval has no predecessor term
+// (u0 is part of the initial residual).
+template <int D>
+__global__ void __launch_bounds__(kRT) kh_update_pair(double* __restrict__ u, const float* __restrict__ c,
+                                                      float* __restrict__ rh, float* __restrict__ rl, int64_t N,
+                                                      int n, PairK<D> P, double* __restrict__ norm2) {
+    const int nn = n * n;
+    const int nrb = row_blocks(n);
+    const int64_t tasks = N * nrb;
+    float ss = 0.0f;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const RowTask rt = row_task(t, nrb);
+        const int64_t base = rt.m * D * (int64_t)nn;
+        const float* cm = c + base;
+        for (int j = threadIdx.x; j < n; j += kRT)
+#pragma unroll
+        for (int rr = 0; rr < kRB; ++rr) {
+            const int i = rt.i0 + rr;
+            if (i >= n) break;
+            const int o = i * n + j;
+            float cv[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) cv[k] = cm[(int64_t)k * nn + o];
+            FF e = {0.0f, 0.0f};   // b^T c_{m-1}
+            if (rt.m > 0) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) e = ff_add_f(e, cm[(int64_t)(k - D) * nn + o]);
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float* ck = cm + (int64_t)k * nn;
+                const float up = i > 0 ? ck[o - n] : 0.0f, dn = i + 1 < n ? ck[o + n] : 0.0f;
+                const float lt = j > 0 ? ck[o - 1] : 0.0f, rt_ = j + 1 < n ? ck[o + 1] : 0.0f;
+                // 4 c - (up + dn + lt + rt), then times tau Mhat_kk / h^2
+                FF d = ff_add(two_sum(up, dn), two_sum(lt, rt_));
+                d = ff_add_f(ff_neg(d), 4.0f * cv[k]);
+                FF tk = ff_mul(FF{P.mh[k], P.ml[k]}, d);
+#pragma unroll
+                for (int l = 0; l < D; ++l) tk = ff_add_f(tk, P.K[k * D + l] * cv[l]);
+                tk = ff_add(tk, (k & 1) ? e : ff_neg(e));   // - a_k e, a_k = (-1)^k
+                const int64_t idx = base + (int64_t)k * nn + o;
+                const FF r = ff_add(FF{rh[idx], rl[idx]}, ff_neg(tk));
+                rh[idx] = r.h;
+                rl[idx] = r.l;
+                ss = fmaf(r.h, r.h, ss);
+                u[idx] += (double)cv[k];
+            }
+        }
+    }
+    norm_flush<true>((double)ss, norm2);
+}
+
+// ------------------------------------------------------------- warp strips
+// The spatial V-cycle kernels run one warp per (interval, strip of columns,
+// chunk of rows).  Lane L holds the adjacent local columns q = 2L and
+// 2L + 1 of a 64-column window and streams down the rows with a three-row
+// window of the smoothed iterate in registers; the columns next to a lane's
+// pair come from the neighbouring lanes by shuffles.  Windows overlap: the
+// outermost local columns only feed their neighbours, so strips advance by
+// 62 (post) or 60 (pre: 30 coarse columns) fine columns and no lane runs
+// extra halo code.  The loads of row i + 2 are issued before row i is
+// computed.
+constexpr int kPreRows = 16;    // coarse rows per pre task
+constexpr int kPostRows = 32;   // fine rows per post task
+constexpr int kPreStride = 30;  // coarse columns per pre strip
+constexpr int kPostStride = 62; // fine columns per post strip
+
+template <typename T>
+__device__ __forceinline__ T shup(T v) {
+    return __shfl_up_sync(0xffffffffu, v, 1);
+}
+template <typename T>
+__device__ __forceinline__ T shdn(T v) {
+    return __shfl_down_sync(0xffffffffu, v, 1);
+}
+
+// r at fine (i, j) of one interval, zero outside the grid.
+template <int D, typename T>
+__device__ __forceinline__ void r_at(const T* __restrict__ r, int nn, int n, int i, int j, T (&rv)[D]) {
+    const bool in = (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
+    const int o = in ? i * n + j : 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) rv[k] = in ? r[k * nn + o] : T(0);
+}
+
+// d = omega Dinv r (the first Jacobi sweep from zero).
+template <int D, typename T>
+__device__ __forceinline__ void smooth0(const HeatK<D, T>& C, T omega, const T (&rv)[D], T (&dv)[D]) {
+    T t[D];
+    apply_Dinv<D, T>(C, rv, t);
+#pragma unroll
+    for (int k = 0; k < D; ++k) dv[k] = omega * t[k];
+}
+
+// Pre-smoothing, residual and full weighting in one pass: x = omega Dinv r,
+// y = r - G x, rc = FW(y) on the coarse grid nc = (n-1)/2 (coarse (I, J) on
+// fine (2I+1, 2J+1), weights [1 2 1]^T [1 2 1] / 16: across the columns at
+// the odd ones, then down the rows).  Window origin c0 = 60s - 2: lane L's
+// odd column c0 + 2L + 1 is coarse column 30s - 1 + L, written by lanes
+// 1..30.
+template <int D, typename T>
+__global__ void __launch_bounds__(kHT) kh_pre_w(const T* __restrict__ r, T* __restrict__ rc, int64_t N, int n,
+                                                int nc, HeatK<D, T> C, T omega) {
+    const int lane = threadIdx.x & 31;
+    const int nn = n * n, ncc = nc * nc;
+    const int strips = (nc + kPreStride - 1) / kPreStride, chunks = (nc + kPreRows - 1) / kPreRows;
+    const int per = strips * chunks;
+    const int64_t tasks = N * per;
+    const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * kHT + threadIdx.x) >> 5; w < tasks; w += nw) {
+        const int64_t m = w / per;
+        const int rem = (int)(w - m * per);
+        const int s = rem / chunks, ch = rem - s * chunks;
+        const int I0 = ch * kPreRows, I1 = min(I0 + kPreRows, nc);
+        const T* rm = r + m * D * (int64_t)nn;
+        T* rcm = rc + m * D * (int64_t)ncc;
+        const int c0 = 2 * kPreStride * s - 2;
+        const int ce = c0 + 2 * lane, co = ce + 1;   // this lane's even and odd fine column
+        const int J = kPreStride * s - 1 + lane;     // coarse column of co
+        const bool writer = lane >= 1 && lane <= 30 && J < nc;
+        const int f0 = 2 * I0, f1 = 2 * I1;           // fine rows f0 .. f1
+        T xe[3][D], xo[3][D], re[D], ro[D], ren[D], ron[D], pe[D], po[D], acc[D];
+        {
+            T t0[D], t1[D];
+            r_at<D, T>(rm, nn, n, f0 - 1, ce, t0);
+            r_at<D, T>(rm, nn, n, f0 - 1, co, t1);
+            smooth0<D, T>(C, omega, t0, xe[0]);
+            smooth0<D, T>(C, omega, t1, xo[0]);
+        }
+        r_at<D, T>(rm, nn, n, f0, ce, re);
+        r_at<D, T>(rm, nn, n, f0, co, ro);
+        smooth0<D, T>(C, omega, re, xe[1]);
+        smooth0<D, T>(C, omega, ro, xo[1]);
+        r_at<D, T>(rm, nn, n, f0 + 1, ce, ren);
+        r_at<D, T>(rm, nn, n, f0 + 1, co, ron);
+        smooth0<D, T>(C, omega, ren, xe[2]);
+        smooth0<D, T>(C, omega, ron, xo[2]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] = T(0);
+        for (int i = f0;; ++i) {
+            // loads of row i + 2, consumed after row i is done
+            r_at<D, T>(rm, nn, n, i + 2, ce, pe);
+            r_at<D, T>(rm, nn, n, i + 2, co, po);
+            // y = r - G x at row i; H = y(even) + 2 y(odd) + y(next lane's even)
+            T nbe[D], nbo[D], ge[D], go[D], H[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T left = shup(xo[1][k]), right = shdn(xe[1][k]);
+                nbe[k] = (xe[0][k] + xe[2][k]) + (left + xo[1][k]);
+                nbo[k] = (xo[0][k] + xo[2][k]) + (xe[1][k] + right);
+            }
+            apply_G<D, T>(C, xe[1], nbe, ge);
+            apply_G<D, T>(C, xo[1], nbo, go);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T ye = re[k] - ge[k], yo = ro[k] - go[k];
+                H[k] = (ye + shdn(ye)) + T(2) * yo;
+            }
+            // down the rows: coarse row I takes fine rows 2I, 2I+1, 2I+2 with weights 1, 2, 1
+            if ((i & 1) == 0) {
+                if (i > f0) {
+                    const int I = i / 2 - 1;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        acc[k] += H[k];
+                        if (writer) rcm[k * ncc + I * nc + J] = acc[k] * T(0.0625);
+                    }
+                }
+                if (i == f1) break;
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc[k] = H[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < D; ++k) acc[k] += T(2) * H[k];
+            }
+            // advance the window to row i + 1
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                xe[0][k] = xe[1][k];
+                xe[1][k] = xe[2][k];
+                xo[0][k] = xo[1][k];
+                xo[1][k] = xo[2][k];
+                re[k] = ren[k];
+                ro[k] = ron[k];
+                ren[k] = pe[k];
+                ron[k] = po[k];
+            }
+            smooth0<D, T>(C, omega, pe, xe[2]);
+            smooth0<D, T>(C, omega, po, xo[2]);
         }
     }
 }
 
-// Full weighting onto the coarse grid (nc = (n-1)/2): coarse (I, J) sits on
-// fine (2I+1, 2J+1); weights 4 centre, 2 edge neighbours, 1 corners, / 16.
-// One thread per coarse value (interval, coefficient, I, J).
-__global__ void __launch_bounds__(kHT) kh_restrict_space(const double* __restrict__ y, double* __restrict__ rc,
-                                                         int64_t nvals_c, int n, int nc) {
-    const int64_t ncc = (int64_t)nc * nc, nnf = (int64_t)n * n;
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < nvals_c; t += (int64_t)gridDim.x * kHT) {
-        const int64_t f = t / ncc, o = t - f * ncc;   // f = interval * D + coefficient
-        const int I = (int)(o / nc), J = (int)(o - (int64_t)I * nc);
-        const double* yf = y + f * nnf;
-        const int i = 2 * I + 1, j = 2 * J + 1;
-        auto at = [&](int a, int b) { return yf[(int64_t)a * n + b]; };
-        double s = 4.0 * at(i, j);
-        s += 2.0 * (at(i - 1, j) + at(i + 1, j) + at(i, j - 1) + at(i, j + 1));
-        s += at(i - 1, j - 1) + at(i + 1, j - 1) + at(i - 1, j + 1) + at(i + 1, j + 1);
-        rc[t] = s * 0.0625;
+// Coarse-grid correction and post-smoothing in one pass: x = omega Dinv r +
+// P xc (the pre-smoothed iterate recomputed, plus the bilinear prolongation
+// of the coarse correction, rows interpolated first), z = x + omega Dinv
+// (r - G x); out = alpha z (acc = 0) or out += alpha z (acc = 1).  Window
+// origin c0 = 62s - 1: lane L's first column c0 + 2L is odd and lies on
+// coarse column Jl = 31s - 1 + L, its second column lies between Jl and
+// Jl + 1 (the next lane's); z is written at local columns 1..62.
+template <int D, typename T>
+__global__ void __launch_bounds__(kHT) kh_post_w(const T* __restrict__ r, const T* __restrict__ xc,
+                                                 T* __restrict__ out, int64_t N, int n, int nc, HeatK<D, T> C,
+                                                 T omega, T alpha, int acc) {
+    const int lane = threadIdx.x & 31;
+    const int nn = n * n, ncc = nc * nc;
+    const int strips = (n + kPostStride - 1) / kPostStride, chunks = (n + kPostRows - 1) / kPostRows;
+    const int per = strips * chunks;
+    const int64_t tasks = N * per;
+    const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * kHT + threadIdx.x) >> 5; w < tasks; w += nw) {
+        const int64_t m = w / per;
+        const int rem = (int)(w - m * per);
+        const int s = rem / chunks, ch = rem - s * chunks;
+        const int i0 = ch * kPostRows, i1 = min(i0 + kPostRows, n);
+        const T* rm = r + m * D * (int64_t)nn;
+        const T* cm = xc + m * D * (int64_t)ncc;
+        T* om = out + m * D * (int64_t)nn;
+        const int c0 = kPostStride * s - 1;
+        const int ca = c0 + 2 * lane, cb = ca + 1;    // odd and even fine column of this lane
+        const int Jl = (ca - 1) >> 1;                 // coarse column of ca (31s - 1 + L)
+        const bool wa = lane >= 1 && ca < n, wb = lane <= 30 && cb < n;
+        const bool jin = (unsigned)Jl < (unsigned)nc, jin1 = (unsigned)(Jl + 1) < (unsigned)nc;
+        // coarse values of fine row a at Jl (q) and Jl + 1 (q1, lane 31 only: the
+        // others take it from the next lane): rows (a-1)/2 for odd a, else the
+        // two rows a/2 - 1 and a/2 (zero outside the coarse grid)
+        auto cload = [&](int a, T (&q)[D], T (&q2)[D], T (&q1)[D], T (&q12)[D]) {
+            const int Ia = (a & 1) ? (a - 1) >> 1 : (a >> 1) - 1, Ib = (a & 1) ? -1 : a >> 1;
+            const bool ia = (unsigned)Ia < (unsigned)nc, ib = (unsigned)Ib < (unsigned)nc;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T* ck = cm + k * ncc;
+                q[k] = (ia && jin) ? ck[Ia * nc + Jl] : T(0);
+                q2[k] = (ib && jin) ? ck[Ib * nc + Jl] : T(0);
+                q1[k] = (lane == 31 && ia && jin1) ? ck[Ia * nc + Jl + 1] : T(0);
+                q12[k] = (lane == 31 && ib && jin1) ? ck[Ib * nc + Jl + 1] : T(0);
+            }
+        };
+        // x at fine row a from its loads: d = omega Dinv r plus the prolongation
+        auto xrow = [&](int a, const T (&ra)[D], const T (&rb)[D], const T (&q)[D], const T (&q2)[D],
+                        const T (&q1)[D], const T (&q12)[D], T (&xa)[D], T (&xb)[D]) {
+            T da[D], db[D];
+            smooth0<D, T>(C, omega, ra, da);
+            smooth0<D, T>(C, omega, rb, db);
+            const bool odd = a & 1, rowin = (unsigned)a < (unsigned)n;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T cr = odd ? q[k] : T(0.5) * (q[k] + q2[k]);       // row-interpolated at Jl
+                const T cr1l = odd ? q1[k] : T(0.5) * (q1[k] + q12[k]);  // lane 31's own Jl + 1
+                const T nxt = shdn(cr);
+                const T cr1 = lane == 31 ? cr1l : nxt;
+                xa[k] = (rowin && (unsigned)ca < (unsigned)n) ? da[k] + cr : T(0);
+                xb[k] = (rowin && (unsigned)cb < (unsigned)n) ? db[k] + T(0.5) * (cr + cr1) : T(0);
+            }
+        };
+        T xa[3][D], xb[3][D], ra[D], rb[D], ran[D], rbn[D], pa[D], pb[D];
+        T q[D], q2[D], q1[D], q12[D];
+        {
+            T t0[D], t1[D];
+            r_at<D, T>(rm, nn, n, i0 - 1, ca, t0);
+            r_at<D, T>(rm, nn, n, i0 - 1, cb, t1);
+            cload(i0 - 1, q, q2, q1, q12);
+            xrow(i0 - 1, t0, t1, q, q2, q1, q12, xa[0], xb[0]);
+        }
+        r_at<D, T>(rm, nn, n, i0, ca, ra);
+        r_at<D, T>(rm, nn, n, i0, cb, rb);
+        cload(i0, q, q2, q1, q12);
+        xrow(i0, ra, rb, q, q2, q1, q12, xa[1], xb[1]);
+        r_at<D, T>(rm, nn, n, i0 + 1, ca, ran);
+        r_at<D, T>(rm, nn, n, i0 + 1, cb, rbn);
+        cload(i0 + 1, q, q2, q1, q12);
+        xrow(i0 + 1, ran, rbn, q, q2, q1, q12, xa[2], xb[2]);
+        for (int i = i0; i < i1; ++i) {
+            // loads of row i + 2, consumed after row i is written
+            r_at<D, T>(rm, nn, n, i + 2, ca, pa);
+            r_at<D, T>(rm, nn, n, i + 2, cb, pb);
+            cload(i + 2, q, q2, q1, q12);
+            T nba[D], nbb[D], ga[D], gb[D], ea[D], eb[D], ya[D], yb[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T left = shup(xb[1][k]), right = shdn(xa[1][k]);
+                nba[k] = (xa[0][k] + xa[2][k]) + (left + xb[1][k]);
+                nbb[k] = (xb[0][k] + xb[2][k]) + (xa[1][k] + right);
+            }
+            apply_G<D, T>(C, xa[1], nba, ga);
+            apply_G<D, T>(C, xb[1], nbb, gb);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                ea[k] = ra[k] - ga[k];
+                eb[k] = rb[k] - gb[k];
+            }
+            apply_Dinv<D, T>(C, ea, ya);
+            apply_Dinv<D, T>(C, eb, yb);
+            T* oi = om + i * n;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T za = fma(omega, ya[k], xa[1][k]), zb = fma(omega, yb[k], xb[1][k]);
+                if (wa) {
+                    T* p = oi + k * nn + ca;
+                    *p = acc ? fma(alpha, za, *p) : alpha * za;
+                }
+                if (wb) {
+                    T* p = oi + k * nn + cb;
+                    *p = acc ? fma(alpha, zb, *p) : alpha * zb;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                xa[0][k] = xa[1][k];
+                xa[1][k] = xa[2][k];
+                xb[0][k] = xb[1][k];
+                xb[1][k] = xb[2][k];
+                ra[k] = ran[k];
+                rb[k] = rbn[k];
+                ran[k] = pa[k];
+                rbn[k] = pb[k];
+            }
+            xrow(i + 2, pa, pb, q, q2, q1, q12, xa[2], xb[2]);
+        }
     }
 }
 
-// x += bilinear interpolation of the coarse correction; one thread per fine
-// value.  Fine (i, j) lies between coarse rows (i-1)/2 .. (i+1)/2 (zero
-// beyond the boundary).
-__global__ void __launch_bounds__(kHT) kh_prolong_add(const double* __restrict__ xc, double* __restrict__ x,
-                                                      int64_t nvals, int n, int nc) {
-    const int64_t nnf = (int64_t)n * n, ncc = (int64_t)nc * nc;
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < nvals; t += (int64_t)gridDim.x * kHT) {
-        const int64_t f = t / nnf, o = t - f * nnf;
-        const int i = (int)(o / n), j = (int)(o - (int64_t)i * n);
-        const double* c = xc + f * ncc;
-        auto cv = [&](int a, int b) { return (a < 0 || b < 0 || a >= nc || b >= nc) ? 0.0 : c[(int64_t)a * nc + b]; };
-        // coarse index of fine point i: odd i = 2I+1 -> on a coarse row; even i -> between rows i/2-1 and i/2
-        double v;
-        const bool ri = i & 1, rj = j & 1;
-        const int I = ri ? (i - 1) / 2 : i / 2 - 1, J = rj ? (j - 1) / 2 : j / 2 - 1;
-        if (ri && rj) v = cv(I, J);
-        else if (ri) v = 0.5 * (cv(I, J) + cv(I, J + 1));
-        else if (rj) v = 0.5 * (cv(I, J) + cv(I + 1, J));
-        else v = 0.5 * (0.5 * (cv(I, J) + cv(I + 1, J)) + 0.5 * (cv(I, J + 1) + cv(I + 1, J + 1)));
-        x[t] += v;
+// One grid point: G_tau is its point block, solved exactly.
+// out = alpha Dinv r (acc = 0) or out += alpha Dinv r (acc = 1).
+template <int D, typename T>
+__global__ void __launch_bounds__(kHT) kh_point_solve(const T* __restrict__ r, T* __restrict__ out, int64_t N,
+                                                      HeatK<D, T> C, T alpha, int acc) {
+    for (int64_t m = (int64_t)blockIdx.x * kHT + threadIdx.x; m < N; m += (int64_t)gridDim.x * kHT) {
+        T v[D], y[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[k] = r[m * D + k];
+        apply_Dinv<D, T>(C, v, y);
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[m * D + k] = acc ? fma(alpha, y[k], out[m * D + k]) : alpha * y[k];
     }
 }
 
 // Time restriction of the residual: fc[m] = P1^T g[2m] + P2^T g[2m+1] on the
-// Legendre axis of every grid point (eq. chap4_restrictionTime).
-template <int D>
-__global__ void __launch_bounds__(kHT) kh_restrict_time(const double* __restrict__ g, double* __restrict__ fc,
-                                                        int64_t Nc, int64_t nn, tmg::Xfer<double, D> X) {
-    const int64_t npts = Nc * nn;
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < npts; t += (int64_t)gridDim.x * kHT) {
-        const int64_t m = t / nn, o = t - m * nn;
-        double a[D], b[D];
+// Legendre axis of every grid point (eq. chap4_restrictionTime).  Row tasks
+// over the coarse intervals.
+template <int D, typename T>
+__global__ void __launch_bounds__(kRT) kh_restrict_time(const T* __restrict__ g, T* __restrict__ fc, int64_t Nc,
+                                                        int n, tmg::Xfer<T, D> X) {
+    const int nn = n * n;
+    const int nrb = row_blocks(n);
+    const int64_t tasks = Nc * nrb;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const RowTask rt = row_task(t, nrb);
+        const T* g0 = g + 2 * rt.m * D * (int64_t)nn;
+        const T* g1 = g0 + D * (int64_t)nn;
+        T* f = fc + rt.m * D * (int64_t)nn;
+        for (int j = threadIdx.x; j < n; j += kRT)
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            a[l] = g[(2 * m) * D * nn + l * nn + o];
-            b[l] = g[(2 * m + 1) * D * nn + l * nn + o];
-        }
+        for (int rr = 0; rr < kRB; ++rr) {
+            const int i = rt.i0 + rr;
+            if (i >= n) break;
+            const int o = i * n + j;
+            T a[D], b[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            double s = 0.0;
+            for (int l = 0; l < D; ++l) {
+                a[l] = g0[(int64_t)l * nn + o];
+                b[l] = g1[(int64_t)l * nn + o];
+            }
 #pragma unroll
-            for (int l = 0; l < D; ++l) s = fma(X.P1[l * D + k], a[l], fma(X.P2[l * D + k], b[l], s));
-            fc[m * D * nn + k * nn + o] = s;
+            for (int k = 0; k < D; ++k) {
+                T s = T(0);
+#pragma unroll
+                for (int l = 0; l < D; ++l) s = fma(X.P1[l * D + k], a[l], fma(X.P2[l * D + k], b[l], s));
+                f[(int64_t)k * nn + o] = s;
+            }
         }
     }
 }
 
 // Time prolongation: u[2m] += P1 uc[m], u[2m+1] += P2 uc[m] (eq.
 // chap4_prolongationTime).
-template <int D>
-__global__ void __launch_bounds__(kHT) kh_prolong_time(const double* __restrict__ uc, double* __restrict__ u,
-                                                       int64_t Nc, int64_t nn, tmg::Xfer<double, D> X) {
-    const int64_t npts = Nc * nn;
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < npts; t += (int64_t)gridDim.x * kHT) {
-        const int64_t m = t / nn, o = t - m * nn;
-        double c[D];
+template <int D, typename T>
+__global__ void __launch_bounds__(kRT) kh_prolong_time(const T* __restrict__ uc, T* __restrict__ u, int64_t Nc, int n,
+                                                       tmg::Xfer<T, D> X) {
+    const int nn = n * n;
+    const int nrb = row_blocks(n);
+    const int64_t tasks = Nc * nrb;
+    for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+        const RowTask rt = row_task(t, nrb);
+        const T* c = uc + rt.m * D * (int64_t)nn;
+        T* u0p = u + 2 * rt.m * D * (int64_t)nn;
+        T* u1p = u0p + D * (int64_t)nn;
+        for (int j = threadIdx.x; j < n; j += kRT)
 #pragma unroll
-        for (int l = 0; l < D; ++l) c[l] = uc[m * D * nn + l * nn + o];
+        for (int rr = 0; rr < kRB; ++rr) {
+            const int i = rt.i0 + rr;
+            if (i >= n) break;
+            const int o = i * n + j;
+            T cv[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-            double s1 = 0.0, s2 = 0.0;
+            for (int l = 0; l < D; ++l) cv[l] = c[(int64_t)l * nn + o];
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                s1 = fma(X.P1[k * D + l], c[l], s1);
-                s2 = fma(X.P2[k * D + l], c[l], s2);
+            for (int k = 0; k < D; ++k) {
+                T s1 = T(0), s2 = T(0);
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
+                    s1 = fma(X.P1[k * D + l], cv[l], s1);
+                    s2 = fma(X.P2[k * D + l], cv[l], s2);
+                }
+                u0p[(int64_t)k * nn + o] += s1;
+                u1p[(int64_t)k * nn + o] += s2;
             }
-            u[(2 * m) * D * nn + k * nn + o] += s1;
-            u[(2 * m + 1) * D * nn + k * nn + o] += s2;
         }
     }
 }
 
-// u += omega x
-__global__ void __launch_bounds__(kHT) kh_axpy(double* __restrict__ u, const double* __restrict__ x, int64_t nv,
-                                               double omega) {
-    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < nv; t += (int64_t)gridDim.x * kHT)
-        u[t] = fma(omega, x[t], u[t]);
+// u += x
+template <typename T>
+__global__ void __launch_bounds__(kHT) kh_add(T* __restrict__ u, const T* __restrict__ x, int64_t nv) {
+    for (int64_t t = (int64_t)blockIdx.x * kHT + threadIdx.x; t < nv; t += (int64_t)gridDim.x * kHT) u[t] += x[t];
 }
 
 }  // namespace
+
+// Buffers of one cycle precision: time levels (right-hand side and
+// correction; level 0 only for the correction cycle of the mixed form), the
+// time residual, the spatial hierarchy (levels >= 1: restricted right-hand
+// side and V-cycle result), the coarsest time level's block solve.
+template <typename T>
+struct HeatBufs {
+    std::vector<T*> ft, ut, rs, ys;
+    T* g = nullptr;
+    T* g2 = nullptr;
+    T* cx = nullptr;
+};
 
 struct tmg_heat {
     int p, d, n;
@@ -307,21 +747,25 @@ struct tmg_heat {
     int nu1, nu2, nu_c;
     double tol;
     int max_cycles;
+    int precision;                // TMG_FP64 or TMG_MIXED
+    int use_graph;
     cudaStream_t s;
     bool own_stream;
     int max_blocks;
-    void* ws;                     // one allocation for every buffer below
-    std::vector<double*> ft, ut;  // time levels l >= 1: right-hand side and correction
-    std::vector<double*> rs, xs, ys;   // spatial levels: right-hand side, iterate, Jacobi output
-    double* g;                    // time residual of the current time level
-    double* g2;                   // coarsest time level: residual of the block solve
-    double* cx;                   // coarsest time level: accumulated block solution
-    double* norm2;                // device ||g||^2 of the level-0 residual
+    void* ws;                     // one allocation for every buffer
+    HeatBufs<double> b64;
+    HeatBufs<float> b32;
+    float* rl;                    // mixed: low part of the residual pair (high part: b32.ft[0])
+    bool fresh;                   // mixed: the pair was formed from u directly, not updated
+    double* norm2;                // device ||F - L u||^2 of the FP64 iterate
     double* host2;                // pinned copy
     double P1[tmg::kMaxD * tmg::kMaxD], P2[tmg::kMaxD * tmg::kMaxD];
+    cudaGraphExec_t graph;        // one cycle, captured for (gF, gu, gu0)
+    const void *gF, *gu, *gu0;
     int last_cycles;
     double last_rel;
     std::vector<double> hist;
+    int launches_per_cycle;       // kernels and memsets one cycle issues
 };
 
 namespace {
@@ -343,126 +787,328 @@ int grid_of(const tmg_heat* H, int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 
-template <int D>
+// CTAs for a grid-stride loop over warp tasks (8 per CTA) or row tasks
+// (one per CTA of kRT threads): at most what is resident at once.
+int grid_warps(const tmg_heat* H, int64_t tasks) {
+    const int64_t b = (tasks + kHT / 32 - 1) / (kHT / 32);
+    return (int)(b < 1 ? 1 : (b > H->max_blocks ? H->max_blocks : b));
+}
+
+int host_row_blocks(int n) { return (n + kRB - 1) / kRB; }
+
+int grid_rows(const tmg_heat* H, int64_t tasks) {
+    const int64_t cap = 2 * (int64_t)H->max_blocks;
+    return (int)(tasks < 1 ? 1 : (tasks > cap ? cap : tasks));
+}
+
+HeatBufs<double>& bufs_of(tmg_heat* H, double*) { return H->b64; }
+HeatBufs<float>& bufs_of(tmg_heat* H, float*) { return H->b32; }
+
+thread_local int g_launches = 0;   // kernels and memsets issued (counted while a cycle is issued)
+
+template <int D, typename T>
 struct HeatImpl {
-    static tmg::Xfer<double, D> xfer(const tmg_heat* H) {
-        tmg::Xfer<double, D> X;
+    static HeatBufs<T>& B(tmg_heat* H) { return bufs_of(H, static_cast<T*>(nullptr)); }
+
+    static tmg::Xfer<T, D> xfer(const tmg_heat* H) {
+        tmg::Xfer<T, D> X;
         for (int i = 0; i < D * D; ++i) {
-            X.P1[i] = H->P1[i];
-            X.P2[i] = H->P2[i];
+            X.P1[i] = (T)H->P1[i];
+            X.P2[i] = (T)H->P2[i];
         }
         return X;
     }
 
     // One spatial V(1,1)-cycle from zero on G_tau x = rhs for N intervals at
-    // spatial level sl; returns the buffer holding x.
-    static const double* vcycle(tmg_heat* H, int sl, const double* rhs, int64_t N, double tau) {
+    // spatial level sl: out = alpha x (acc = 0) or out += alpha x (acc = 1).
+    static void vcycle(tmg_heat* H, int sl, const T* rhs, int64_t N, double tau, T* out, T alpha, int acc) {
         const tmg::NvtxRange r_lev("tmg heat spatial level %d", sl);
+        HeatBufs<T>& b = B(H);
         const int n = H->nsz[sl];
-        const int64_t nn = (int64_t)n * n, npts = N * nn;
-        const HeatK<D> C = heat_consts<D>(tau, n);
-        if (n == 1) {   // one grid point: G_tau is its point block, solved exactly
-            kh_smooth0<D><<<grid_of(H, npts), kHT, 0, H->s>>>(rhs, H->xs[sl], npts, nn, C, 1.0);
-            return H->xs[sl];
+        const HeatK<D, T> C = heat_consts<D, T>(tau, n);
+        ++g_launches;
+        if (n == 1) {
+            kh_point_solve<D, T><<<grid_of(H, N), kHT, 0, H->s>>>(rhs, out, N, C, alpha, acc);
+            return;
         }
         const int nc = H->nsz[sl + 1];
-        kh_smooth0<D><<<grid_of(H, npts), kHT, 0, H->s>>>(rhs, H->xs[sl], npts, nn, C, kOmegaS);
-        kh_sweep<D><<<grid_of(H, npts), kHT, 0, H->s>>>(rhs, H->xs[sl], H->ys[sl], N, n, C, 0, 0.0);
-        const int64_t nvc = N * D * (int64_t)nc * nc;
-        kh_restrict_space<<<grid_of(H, nvc), kHT, 0, H->s>>>(H->ys[sl], H->rs[sl + 1], nvc, n, nc);
-        const double* xc = vcycle(H, sl + 1, H->rs[sl + 1], N, tau);
-        const int64_t nv = N * D * nn;
-        kh_prolong_add<<<grid_of(H, nv), kHT, 0, H->s>>>(xc, H->xs[sl], nv, n, nc);
-        kh_sweep<D><<<grid_of(H, npts), kHT, 0, H->s>>>(rhs, H->xs[sl], H->ys[sl], N, n, C, 1, kOmegaS);
-        return H->ys[sl];
+        const int64_t pre_tasks = N * ((nc + kPreStride - 1) / kPreStride) * ((nc + kPreRows - 1) / kPreRows);
+        kh_pre_w<D, T><<<grid_warps(H, pre_tasks), kHT, 0, H->s>>>(rhs, b.rs[sl + 1], N, n, nc, C, (T)kOmegaS);
+        vcycle(H, sl + 1, b.rs[sl + 1], N, tau, b.ys[sl + 1], T(1), 0);
+        const int64_t post_tasks = N * ((n + kPostStride - 1) / kPostStride) * ((n + kPostRows - 1) / kPostRows);
+        ++g_launches;
+        kh_post_w<D, T><<<grid_warps(H, post_tasks), kHT, 0, H->s>>>(rhs, b.ys[sl + 1], out, N, n, nc, C,
+                                                                    (T)kOmegaS, alpha, acc);
     }
 
-    // Time residual of level l into H->g (and ||g||^2 into H->norm2 when asked).
-    static void time_resid(tmg_heat* H, const double* F, const double* u, const double* u0, int64_t N, double tau,
-                           bool norm) {
-        const int64_t npts = N * (int64_t)H->n * H->n;
-        kh_time_resid<D><<<grid_of(H, npts), kHT, 0, H->s>>>(F, u, u0, H->g, N, H->n, heat_consts<D>(tau, H->n),
-                                                            norm ? H->norm2 : nullptr);
+    // Time residual of level l (u0 only at level 0) into b.g.
+    static const T* resid(tmg_heat* H, const T* F, const T* u, const double* u0, int64_t N, double tau) {
+        HeatBufs<T>& b = B(H);
+        ++g_launches;
+        kh_resid<D, T, T, true, false, false><<<grid_rows(H, N * host_row_blocks(H->n)), kRT, 0, H->s>>>(
+            F, u, u0, b.g, nullptr, N, H->n, heat_consts<D, T>(tau, H->n), nullptr);
+        return b.g;
     }
 
-    // One smoothing step of every interval: u += omega_t (one spatial V-cycle on g).
-    static void smooth(tmg_heat* H, double* u, int64_t N, double tau) {
-        const double* x = vcycle(H, 0, H->g, N, tau);
-        const int64_t nv = N * D * (int64_t)H->n * H->n;
-        kh_axpy<<<grid_of(H, nv), kHT, 0, H->s>>>(u, x, nv, kOmegaT);
-    }
-
-    // One V-cycle in time at level l on L_l u = F (u0 only at level 0);
-    // g_ready: H->g already holds this level's residual of u.
-    static void tcycle(tmg_heat* H, int l, const double* F, double* u, const double* u0, bool g_ready) {
+    // One V-cycle in time at level l on L_l u = F (u0 only at level 0).
+    // g0: the residual of u, when the caller already has it; zero: u is zero
+    // on entry (its residual is F, and the first smoothing step writes u).
+    static void tcycle(tmg_heat* H, int l, const T* F, T* u, const double* u0, const T* g0, bool zero) {
         const tmg::NvtxRange r_lev("tmg heat time level %d", l);
+        HeatBufs<T>& b = B(H);
         const int64_t N = H->N >> l;
         const double tau = ldexp(H->tau, l);
         const int64_t nn = (int64_t)H->n * H->n, nv = N * D * nn;
+        const T wt = (T)kOmegaT;
         if (N == 1) {
-            // nu_c spatial V-cycles on the block: x = 0; x += V(r - G x)
-            if (!g_ready) time_resid(H, F, u, u0, 1, tau, false);
-            const HeatK<D> C = heat_consts<D>(tau, H->n);
+            // nu_c spatial V-cycles on the block: x = V(g); x += V(g - G x)
+            const T* g = g0 ? g0 : resid(H, F, u, u0, 1, tau);
+            T* x = zero ? u : b.cx;
             for (int c = 0; c < H->nu_c; ++c) {
                 if (c == 0) {
-                    const double* x = vcycle(H, 0, H->g, 1, tau);
-                    cudaMemcpyAsync(H->cx, x, sizeof(double) * nv, cudaMemcpyDeviceToDevice, H->s);
+                    vcycle(H, 0, g, 1, tau, x, T(1), 0);
                 } else {
-                    kh_sweep<D><<<grid_of(H, nn), kHT, 0, H->s>>>(H->g, H->cx, H->g2, 1, H->n, C, 0, 0.0);
-                    const double* x = vcycle(H, 0, H->g2, 1, tau);
-                    kh_axpy<<<grid_of(H, nv), kHT, 0, H->s>>>(H->cx, x, nv, 1.0);
+                    ++g_launches;
+                    kh_resid<D, T, T, false, false, false><<<grid_rows(H, host_row_blocks(H->n)), kRT, 0, H->s>>>(
+                        g, x, nullptr, b.g2, nullptr, 1, H->n, heat_consts<D, T>(tau, H->n), nullptr);
+                    vcycle(H, 0, b.g2, 1, tau, x, T(1), 1);
                 }
             }
-            kh_axpy<<<grid_of(H, nv), kHT, 0, H->s>>>(u, H->cx, nv, 1.0);
+            if (!zero) {
+                ++g_launches;
+                kh_add<T><<<grid_of(H, nv), kHT, 0, H->s>>>(u, b.cx, nv);
+            }
             return;
         }
+        if (zero && H->nu1 == 0) {
+            ++g_launches;
+            cudaMemsetAsync(u, 0, sizeof(T) * nv, H->s);
+        }
         for (int k = 0; k < H->nu1; ++k) {
-            if (!(g_ready && k == 0)) time_resid(H, F, u, u0, N, tau, false);
-            smooth(H, u, N, tau);
+            const T* rhs = (k == 0 && g0) ? g0 : resid(H, F, u, u0, N, tau);
+            vcycle(H, 0, rhs, N, tau, u, wt, (zero && k == 0) ? 0 : 1);
         }
-        if (!(g_ready && H->nu1 == 0)) time_resid(H, F, u, u0, N, tau, false);
-        const tmg::Xfer<double, D> X = xfer(H);
-        kh_restrict_time<D><<<grid_of(H, (N / 2) * nn), kHT, 0, H->s>>>(H->g, H->ft[l + 1], N / 2, nn, X);
-        cudaMemsetAsync(H->ut[l + 1], 0, sizeof(double) * (nv / 2), H->s);
-        tcycle(H, l + 1, H->ft[l + 1], H->ut[l + 1], nullptr, false);
-        kh_prolong_time<D><<<grid_of(H, (N / 2) * nn), kHT, 0, H->s>>>(H->ut[l + 1], u, N / 2, nn, X);
-        for (int k = 0; k < H->nu2; ++k) {
-            time_resid(H, F, u, u0, N, tau, false);
-            smooth(H, u, N, tau);
-        }
+        const T* rhs = (H->nu1 == 0 && g0) ? g0 : resid(H, F, u, u0, N, tau);
+        const tmg::Xfer<T, D> X = xfer(H);
+        ++g_launches;
+        kh_restrict_time<D, T><<<grid_rows(H, (N / 2) * host_row_blocks(H->n)), kRT, 0, H->s>>>(rhs, b.ft[l + 1], N / 2, H->n, X);
+        tcycle(H, l + 1, b.ft[l + 1], b.ut[l + 1], nullptr, b.ft[l + 1], true);
+        ++g_launches;
+        kh_prolong_time<D, T><<<grid_rows(H, (N / 2) * host_row_blocks(H->n)), kRT, 0, H->s>>>(b.ut[l + 1], u, N / 2, H->n, X);
+        for (int k = 0; k < H->nu2; ++k) vcycle(H, 0, resid(H, F, u, u0, N, tau), N, tau, u, wt, 1);
     }
 };
 
+// The work of one cycle after the residual of u has been formed: FP64 --
+// the cycle on L u = F with the residual in b64.g; mixed -- the FP32 cycle on
+// L c = r_h from c = 0, then u += c and r -= L c (float pair) with ||r||^2.
+template <int D>
+void cycle_body(tmg_heat* H, const double* F, double* u, const double* u0) {
+    if (H->precision == TMG_FP64) {
+        HeatImpl<D, double>::tcycle(H, 0, F, u, u0, H->b64.g, false);
+    } else {
+        HeatBufs<float>& b = H->b32;
+        HeatImpl<D, float>::tcycle(H, 0, b.ft[0], b.ut[0], nullptr, b.ft[0], true);
+        g_launches += 2;
+        cudaMemsetAsync(H->norm2, 0, sizeof(double), H->s);
+        kh_update_pair<D><<<grid_rows(H, H->N * host_row_blocks(H->n)), kRT, 0, H->s>>>(u, b.ut[0], b.ft[0], H->rl, H->N, H->n,
+                                                                      pair_consts<D>(H->tau, H->n), H->norm2);
+    }
+}
+
+// One cycle: replayed from a graph captured for these arrays (the FP64 form
+// reads F, u and u0 inside the cycle; the mixed form only u), else issued.
+template <int D>
+tmg_status run_cycle(tmg_heat* H, const double* F, double* u, const double* u0) {
+    const bool fp64 = H->precision == TMG_FP64;
+    const void* kF = fp64 ? F : nullptr;
+    const void* ku0 = fp64 ? u0 : nullptr;
+    if (!H->use_graph) {
+        g_launches = 0;
+        cycle_body<D>(H, F, u, u0);
+        H->launches_per_cycle = g_launches;
+        TH_CUDA(cudaGetLastError());
+        return TMG_OK;
+    }
+    if (!H->graph || H->gF != kF || H->gu != u || H->gu0 != ku0) {
+        if (H->graph) {
+            cudaGraphExecDestroy(H->graph);
+            H->graph = nullptr;
+        }
+        TH_CUDA(cudaStreamBeginCapture(H->s, cudaStreamCaptureModeThreadLocal));
+        g_launches = 0;
+        cycle_body<D>(H, F, u, u0);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e1 = cudaStreamEndCapture(H->s, &g);
+        if (e1 != cudaSuccess || g == nullptr) {
+            cudaGetLastError();
+            g_heat_cuda = (int)e1;
+            return TMG_ECUDA;
+        }
+        const cudaError_t e2 = cudaGraphInstantiate(&H->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) {
+            H->graph = nullptr;
+            g_heat_cuda = (int)e2;
+            return TMG_ECUDA;
+        }
+        H->launches_per_cycle = g_launches;
+        H->gF = kF;
+        H->gu = u;
+        H->gu0 = ku0;
+    }
+    TH_CUDA(cudaGraphLaunch(H->graph, H->s));
+    return TMG_OK;
+}
+
+// ||F - L u||^2 of the FP64 iterate into *norm2, the residual itself into
+// b64.g (FP64 form) or the float pair (b32.ft[0], rl) (mixed form).
+template <int D>
+tmg_status residual_fp64(tmg_heat* H, const double* F, const double* u, const double* u0) {
+    const HeatK<D, double> C = heat_consts<D, double>(H->tau, H->n);
+    TH_CUDA(cudaMemsetAsync(H->norm2, 0, sizeof(double), H->s));
+    const int grid = grid_rows(H, H->N * host_row_blocks(H->n));
+    if (H->precision == TMG_FP64)
+        kh_resid<D, double, double, true, true, false><<<grid, kRT, 0, H->s>>>(F, u, u0, H->b64.g, nullptr, H->N,
+                                                                              H->n, C, H->norm2);
+    else
+        kh_resid<D, double, float, true, true, true><<<grid, kRT, 0, H->s>>>(F, u, u0, H->b32.ft[0], H->rl, H->N,
+                                                                            H->n, C, H->norm2);
+    TH_CUDA(cudaGetLastError());
+    return TMG_OK;
+}
+
+tmg_status read_norm(tmg_heat* H, double* nr) {
+    TH_CUDA(cudaMemcpyAsync(H->host2, H->norm2, sizeof(double), cudaMemcpyDeviceToHost, H->s));
+    TH_CUDA(cudaStreamSynchronize(H->s));
+    *nr = sqrt(*H->host2);
+    return TMG_OK;
+}
+
+// solve: cycles from u = 0 until the relative residual is below tol; the
+// mixed form confirms a converged float-pair residual by the FP64 residual
+// of u before it stops.  !solve: one cycle applied to u.
 template <int D>
 tmg_status run_heat(tmg_heat* H, const double* F, const double* u0, double* u, bool solve) {
     const int64_t nv = H->N * D * (int64_t)H->n * H->n;
-    if (solve) TH_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * nv, H->s));
+    const bool fp64 = H->precision == TMG_FP64;
+    tmg_status st;
+    if (!solve) {
+        if ((st = residual_fp64<D>(H, F, u, u0)) != TMG_OK) return st;
+        if ((st = run_cycle<D>(H, F, u, u0)) != TMG_OK) return st;
+        TH_CUDA(cudaGetLastError());
+        TH_CUDA(cudaStreamSynchronize(H->s));
+        return TMG_OK;
+    }
+    TH_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * nv, H->s));
     H->hist.clear();
+    if (fp64) {
+        if ((st = residual_fp64<D>(H, F, u, u0)) != TMG_OK) return st;
+    } else {
+        TH_CUDA(cudaMemsetAsync(H->norm2, 0, sizeof(double), H->s));
+        kh_init_pair<D><<<grid_rows(H, H->N * host_row_blocks(H->n)), kRT, 0, H->s>>>(F, u0, H->b32.ft[0], H->rl, H->N, H->n,
+                                                                    H->norm2);
+        TH_CUDA(cudaGetLastError());
+    }
+    H->fresh = true;
     double nF = 0.0;
     for (int k = 0;; ++k) {
-        // residual of the current iterate and its norm; it also serves the
-        // cycle's first smoothing step
-        TH_CUDA(cudaMemsetAsync(H->norm2, 0, sizeof(double), H->s));
-        HeatImpl<D>::time_resid(H, F, u, u0, H->N, H->tau, true);
-        if (solve) {
-            TH_CUDA(cudaMemcpyAsync(H->host2, H->norm2, sizeof(double), cudaMemcpyDeviceToHost, H->s));
-            TH_CUDA(cudaStreamSynchronize(H->s));
-            const double nr = sqrt(*H->host2);
-            if (k == 0) nF = nr;
-            const double rel = nF > 0.0 ? nr / nF : nr;
-            H->hist.push_back(rel);
-            H->last_cycles = k;
-            H->last_rel = rel;
-            if (!(rel == rel) || rel > 1e300) return TMG_ENUMERIC;
-            if (rel <= H->tol) return TMG_OK;
-            if (k >= H->max_cycles) return TMG_ENOTCONV;
+        double nr = 0.0;
+        if ((st = read_norm(H, &nr)) != TMG_OK) return st;
+        if (k == 0) nF = nr;
+        double rel = nF > 0.0 ? nr / nF : nr;
+        if (!fp64 && rel <= H->tol && !H->fresh) {
+            // confirm from u itself (this also restarts the pair from the true residual)
+            if ((st = residual_fp64<D>(H, F, u, u0)) != TMG_OK) return st;
+            if ((st = read_norm(H, &nr)) != TMG_OK) return st;
+            rel = nF > 0.0 ? nr / nF : nr;
+            H->fresh = true;
         }
-        HeatImpl<D>::tcycle(H, 0, F, u, u0, true);
+        H->hist.push_back(rel);
+        H->last_cycles = k;
+        H->last_rel = rel;
+        if (!(rel == rel) || rel > 1e300) return TMG_ENUMERIC;
+        if (rel <= H->tol) return TMG_OK;
+        if (k >= H->max_cycles) return TMG_ENOTCONV;
+        if ((st = run_cycle<D>(H, F, u, u0)) != TMG_OK) return st;
         TH_CUDA(cudaGetLastError());
-        if (!solve) {
-            TH_CUDA(cudaStreamSynchronize(H->s));
-            return TMG_OK;
+        H->fresh = false;
+        if (fp64 && (st = residual_fp64<D>(H, F, u, u0)) != TMG_OK) return st;
+    }
+}
+
+// Event timings (ms per launch, mean of reps) of the level-0 kernels on the
+// plan's stream after one cycle has filled the buffers: [0] time residual in
+// the cycle precision, [1] pre (spatial level 0), [2] post with
+// accumulation (spatial level 0), [3] the mixed form's pair update or the
+// FP64 form's FP64 residual, [4] one whole cycle.
+template <int D>
+tmg_status profile_heat(tmg_heat* H, const double* F, const double* u0, double* u, int reps, double* ms) {
+    tmg_status st;
+    if ((st = residual_fp64<D>(H, F, u, u0)) != TMG_OK) return st;
+    if ((st = run_cycle<D>(H, F, u, u0)) != TMG_OK) return st;
+    const int64_t N = H->N;
+    const int n = H->n, nc = H->ns > 1 ? H->nsz[1] : 0;
+    cudaEvent_t e0, e1;
+    TH_CUDA(cudaEventCreate(&e0));
+    TH_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto&& launch) -> double {
+        cudaEventRecord(e0, H->s);
+        for (int r = 0; r < reps; ++r) launch();
+        cudaEventRecord(e1, H->s);
+        cudaEventSynchronize(e1);
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        return (double)t / reps;
+    };
+    auto level0 = [&](auto* tag, auto& b, const auto* rhs, const auto* uu, auto* out) {
+        using T = typename std::remove_pointer<decltype(tag)>::type;
+        const HeatK<D, T> C = heat_consts<D, T>(H->tau, n);
+        ms[0] = timed([&] {
+            kh_resid<D, T, T, true, false, false><<<grid_rows(H, N * host_row_blocks(n)), kRT, 0, H->s>>>(
+                rhs, uu, nullptr, b.g, nullptr, N, n, C, nullptr);
+        });
+        if (nc > 0) {
+            const int64_t pre_tasks = N * ((nc + kPreStride - 1) / kPreStride) * ((nc + kPreRows - 1) / kPreRows);
+            ms[1] = timed([&] {
+                kh_pre_w<D, T><<<grid_warps(H, pre_tasks), kHT, 0, H->s>>>(rhs, b.rs[1], N, n, nc, C, (T)kOmegaS);
+            });
+            const int64_t post_tasks = N * ((n + kPostStride - 1) / kPostStride) * ((n + kPostRows - 1) / kPostRows);
+            ms[2] = timed([&] {
+                kh_post_w<D, T><<<grid_warps(H, post_tasks), kHT, 0, H->s>>>(rhs, b.ys[1], out, N, n, nc, C,
+                                                                            (T)kOmegaS, (T)kOmegaT, 1);
+            });
         }
+    };
+    ms[1] = ms[2] = 0.0;
+    if (H->precision == TMG_FP64) {
+        level0(static_cast<double*>(nullptr), H->b64, F, u, H->b64.g);
+        ms[3] = timed([&] { residual_fp64<D>(H, F, u, u0); });
+    } else {
+        HeatBufs<float>& b = H->b32;
+        level0(static_cast<float*>(nullptr), b, b.ft[0], b.ut[0], b.g);
+        const PairK<D> P = pair_consts<D>(H->tau, n);
+        ms[3] = timed([&] {
+            kh_update_pair<D><<<grid_rows(H, N * host_row_blocks(n)), kRT, 0, H->s>>>(u, b.ut[0], b.ft[0], H->rl, N,
+                                                                                     n, P, H->norm2);
+        });
+    }
+    ms[4] = timed([&] { run_cycle<D>(H, F, u, u0); });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TH_CUDA(cudaGetLastError());
+    TH_CUDA(cudaStreamSynchronize(H->s));
+    return TMG_OK;
+}
+
+tmg_status profile_heat_d(tmg_heat* H, const double* F, const double* u0, double* u, int reps, double* ms) {
+    switch (H->d) {
+        case 1: return profile_heat<1>(H, F, u0, u, reps, ms);
+        case 2: return profile_heat<2>(H, F, u0, u, reps, ms);
+        case 3: return profile_heat<3>(H, F, u0, u, reps, ms);
+        case 4: return profile_heat<4>(H, F, u0, u, reps, ms);
+        case 5: return profile_heat<5>(H, F, u0, u, reps, ms);
+        default: return profile_heat<6>(H, F, u0, u, reps, ms);
     }
 }
 
@@ -490,12 +1136,12 @@ tmg_status tmg_heat_setup(tmg_heat** out, int p_t, double tau, int n, int64_t N,
     tmg_opts o;
     tmg_opts_default(&o);
     if (opts) o = *opts;
-    bool pow2n = n >= 1, pow2N = N >= 1;
-    for (int64_t m = n + 1; pow2n && m > 1; m >>= 1) pow2n = (m & 1) == 0;
+    bool pow2n = n >= 1 && n < (1 << 14), pow2N = N >= 1 && N <= (int64_t(1) << 40);
+    for (int64_t m = (int64_t)n + 1; pow2n && m > 1; m >>= 1) pow2n = (m & 1) == 0;
     for (int64_t m = N; pow2N && m > 1; m >>= 1) pow2N = (m & 1) == 0;
     if (p_t < 0 || p_t > tmg::kMaxD - 1 || !(tau > 0.0) || !isfinite(tau) || !pow2n || !pow2N || nu_c < 1 ||
         nu_c > 16 || o.nu1 < 0 || o.nu1 > 8 || o.nu2 < 0 || o.nu2 > 8 || o.nu1 + o.nu2 < 1 || o.gamma != 1 ||
-        o.max_cycles < 0 || !(o.tol >= 0.0))
+        o.max_cycles < 0 || !(o.tol >= 0.0) || (o.precision != TMG_FP64 && o.precision != TMG_MIXED))
         return TMG_EINVAL;
     tmg_heat* H = new (std::nothrow) tmg_heat();
     if (!H) return TMG_ENOMEM;
@@ -509,6 +1155,8 @@ tmg_status tmg_heat_setup(tmg_heat** out, int p_t, double tau, int n, int64_t N,
     H->nu_c = nu_c;
     H->tol = o.tol;
     H->max_cycles = o.max_cycles;
+    H->precision = o.precision;
+    H->use_graph = o.use_graph ? 1 : 0;
     H->last_rel = NAN;
     H->nt = 1;
     for (int64_t m = N; m > 1; m >>= 1) ++H->nt;
@@ -538,54 +1186,70 @@ tmg_status tmg_heat_setup(tmg_heat** out, int p_t, double tau, int n, int64_t N,
         H->P1[i] = P1[i];
         H->P2[i] = P2[i];
     }
-    // workspace: time levels 1.., the residual, the spatial hierarchy for the
-    // level-0 batch, the coarse-level block solve
+    // workspace, in the cycle precision: time levels (level 0 only for the
+    // mixed form's correction), the time residual, the spatial hierarchy
+    // below level 0, the coarsest time level's block solve
+    const bool fp64 = H->precision == TMG_FP64;
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
     const int64_t nv0 = N * H->d * (int64_t)n * n, blk = (int64_t)H->d * n * n;
     std::vector<int64_t> sizes;
-    for (int l = 1; l < H->nt; ++l) {
+    for (int l = fp64 ? 1 : 0; l < H->nt; ++l) {
         sizes.push_back(nv0 >> l);   // ft
         sizes.push_back(nv0 >> l);   // ut
     }
     sizes.push_back(nv0);            // g
-    for (int sl = 0; sl < H->ns; ++sl) {
+    for (int sl = 1; sl < H->ns; ++sl) {
         const int64_t v = N * H->d * (int64_t)H->nsz[sl] * H->nsz[sl];
-        if (sl > 0) sizes.push_back(v);   // rs (level 0 reads the time residual)
-        sizes.push_back(v);          // xs
+        sizes.push_back(v);          // rs
         sizes.push_back(v);          // ys
     }
     sizes.push_back(blk);            // g2
     sizes.push_back(blk);            // cx
-    sizes.push_back(1);              // norm2
-    size_t bytes = 0;
-    for (int64_t v : sizes) bytes += ((size_t)v * sizeof(double) + 255) / 256 * 256;
+    if (!fp64) sizes.push_back(nv0); // rl (float)
+    auto padded = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t bytes = padded(sizeof(double));   // norm2
+    for (int64_t v : sizes) bytes += padded((size_t)v * es);
     if (cudaMalloc(&H->ws, bytes) != cudaSuccess) {
+        cudaGetLastError();
         H->ws = nullptr;
         tmg_heat_destroy(H);
         return TMG_ENOMEM;
     }
-    char* b = static_cast<char*>(H->ws);
+    char* base = static_cast<char*>(H->ws);
     size_t off = 0, k = 0;
-    auto take = [&](void) {
-        double* p = reinterpret_cast<double*>(b + off);
-        off += ((size_t)sizes[k++] * sizeof(double) + 255) / 256 * 256;
-        return p;
+    H->norm2 = reinterpret_cast<double*>(base);
+    off = padded(sizeof(double));
+    auto take = [&]() -> void* {
+        void* q = base + off;
+        off += padded((size_t)sizes[k++] * es);
+        return q;
     };
-    H->ft.assign(H->nt, nullptr);
-    H->ut.assign(H->nt, nullptr);
-    for (int l = 1; l < H->nt; ++l) {
-        H->ft[l] = take();
-        H->ut[l] = take();
+    auto carve = [&](auto& b) {
+        using P = typename std::remove_reference<decltype(b.ft[0])>::type;
+        b.ft.assign(H->nt, nullptr);
+        b.ut.assign(H->nt, nullptr);
+        for (int l = fp64 ? 1 : 0; l < H->nt; ++l) {
+            b.ft[l] = static_cast<P>(take());
+            b.ut[l] = static_cast<P>(take());
+        }
+        b.g = static_cast<P>(take());
+        b.rs.assign(H->ns, nullptr);
+        b.ys.assign(H->ns, nullptr);
+        for (int sl = 1; sl < H->ns; ++sl) {
+            b.rs[sl] = static_cast<P>(take());
+            b.ys[sl] = static_cast<P>(take());
+        }
+        b.g2 = static_cast<P>(take());
+        b.cx = static_cast<P>(take());
+    };
+    if (fp64) {
+        carve(H->b64);
+    } else {
+        carve(H->b32);
+        H->rl = static_cast<float*>(take());
     }
-    H->g = take();
-    for (int sl = 0; sl < H->ns; ++sl) {
-        H->rs.push_back(sl > 0 ? take() : nullptr);
-        H->xs.push_back(take());
-        H->ys.push_back(take());
-    }
-    H->g2 = take();
-    H->cx = take();
-    H->norm2 = take();
     if (cudaMallocHost(&H->host2, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
         H->host2 = nullptr;
         tmg_heat_destroy(H);
         return TMG_ENOMEM;
@@ -608,12 +1272,11 @@ tmg_status tmg_heat_cycle(tmg_heat* H, const double* f, const double* u0, double
 tmg_status tmg_heat_residual(tmg_heat* H, const double* f, const double* u0, const double* u, double* r) {
     if (!H || !aligned16(f) || !aligned16(u) || !aligned16(r) || !u0 || (reinterpret_cast<uintptr_t>(u0) & 7u))
         return TMG_EINVAL;
-    const int64_t npts = H->N * (int64_t)H->n * H->n;
     switch (H->d) {
-#define TMG_HEAT_RES(DD)                                                                                    \
-    case DD:                                                                                                \
-        kh_time_resid<DD><<<grid_of(H, npts), kHT, 0, H->s>>>(f, u, u0, r, H->N, H->n,                      \
-                                                              heat_consts<DD>(H->tau, H->n), nullptr);     \
+#define TMG_HEAT_RES(DD)                                                                                  \
+    case DD:                                                                                              \
+        kh_resid<DD, double, double, true, false, false><<<grid_rows(H, H->N * host_row_blocks(H->n)), kRT, 0, H->s>>>(   \
+            f, u, u0, r, nullptr, H->N, H->n, heat_consts<DD, double>(H->tau, H->n), nullptr);            \
         break;
         TMG_HEAT_RES(1)
         TMG_HEAT_RES(2)
@@ -629,6 +1292,14 @@ tmg_status tmg_heat_residual(tmg_heat* H, const double* f, const double* u0, con
     return TMG_OK;
 }
 
+tmg_status tmg_heat_profile(tmg_heat* H, const double* f, const double* u0, double* u, int reps, double* ms,
+                            int n_ms) {
+    if (!H || !aligned16(f) || !aligned16(u) || !u0 || (reinterpret_cast<uintptr_t>(u0) & 7u) || reps < 1 ||
+        !ms || n_ms < 5)
+        return TMG_EINVAL;
+    return profile_heat_d(H, f, u0, u, reps, ms);
+}
+
 tmg_status tmg_heat_stats(const tmg_heat* H, int* cycles, double* rel_res, double* hist, int hist_len) {
     if (!H) return TMG_EINVAL;
     if (cycles) *cycles = H->last_cycles;
@@ -638,9 +1309,29 @@ tmg_status tmg_heat_stats(const tmg_heat* H, int* cycles, double* rel_res, doubl
     return TMG_OK;
 }
 
+tmg_status tmg_heat_info(const tmg_heat* H, int* time_levels, int* space_levels, int* launches_per_cycle,
+                         size_t* workspace_bytes) {
+    if (!H) return TMG_EINVAL;
+    if (time_levels) *time_levels = H->nt;
+    if (space_levels) *space_levels = H->ns;
+    if (launches_per_cycle) *launches_per_cycle = H->launches_per_cycle;
+    if (workspace_bytes) {
+        size_t b = 0;
+        const size_t es = H->precision == TMG_FP64 ? sizeof(double) : sizeof(float);
+        const int64_t nv0 = H->N * H->d * (int64_t)H->n * H->n;
+        for (int l = H->precision == TMG_FP64 ? 1 : 0; l < H->nt; ++l) b += 2 * (size_t)(nv0 >> l) * es;
+        b += (size_t)nv0 * es;
+        for (int sl = 1; sl < H->ns; ++sl) b += 2 * (size_t)(H->N * H->d * (int64_t)H->nsz[sl] * H->nsz[sl]) * es;
+        if (H->precision != TMG_FP64) b += (size_t)nv0 * sizeof(float);
+        *workspace_bytes = b;
+    }
+    return TMG_OK;
+}
+
 void tmg_heat_destroy(tmg_heat* H) {
     if (!H) return;
     if (H->s) cudaStreamSynchronize(H->s);
+    if (H->graph) cudaGraphExecDestroy(H->graph);
     if (H->ws) cudaFree(H->ws);
     if (H->host2) cudaFreeHost(H->host2);
     if (H->own_stream) cudaStreamDestroy(H->s);

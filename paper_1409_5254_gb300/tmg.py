@@ -48,7 +48,7 @@ EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
            "tmg_stats_batched", "tmg_error_vs_fp64_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched",
            "tmg_heat_setup", "tmg_heat_solve", "tmg_heat_cycle", "tmg_heat_residual", "tmg_heat_stats",
-           "tmg_heat_destroy"]
+           "tmg_heat_info", "tmg_heat_profile", "tmg_heat_destroy"]
 
 
 def library_path() -> str:
@@ -119,7 +119,10 @@ def _lib():
         L.tmg_heat_cycle.argtypes = [_vp, _vp, _vp, _vp]
         L.tmg_heat_residual.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.tmg_heat_stats.argtypes = [_vp, _ip, _dp, _dp, ctypes.c_int]
-        for name in ("tmg_heat_setup", "tmg_heat_solve", "tmg_heat_cycle", "tmg_heat_residual", "tmg_heat_stats"):
+        L.tmg_heat_info.argtypes = [_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_size_t)]
+        L.tmg_heat_profile.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, _dp, ctypes.c_int]
+        for name in ("tmg_heat_setup", "tmg_heat_solve", "tmg_heat_cycle", "tmg_heat_residual", "tmg_heat_stats",
+                     "tmg_heat_info", "tmg_heat_profile"):
             getattr(L, name).restype = ctypes.c_int
         L.tmg_heat_destroy.argtypes = [_vp]
         L.tmg_heat_destroy.restype = None
@@ -555,9 +558,11 @@ class HeatPlan:
     u0 has shape (n, n)."""
 
     def __init__(self, p: int, tau: float, n: int, N: int, *, tol: float = 1e-10, max_cycles: int = 100,
-                 nu1: int = 1, nu2: int = 1, nu_c: int = 2, stream=None):
+                 nu1: int = 1, nu2: int = 1, nu_c: int = 2, precision="mixed", use_graph: bool = True,
+                 stream=None):
         L = _lib()
-        o = _opts(tol=tol, max_cycles=max_cycles, nu1=nu1, nu2=nu2, gamma=1, precision="fp64")
+        o = _opts(tol=tol, max_cycles=max_cycles, nu1=nu1, nu2=nu2, gamma=1, precision=precision,
+                  use_graph=use_graph)
         self.p, self.d, self.n, self.N, self.tau = p, p + 1, n, N, tau
         self._stream = stream
         handle = _vp()
@@ -624,3 +629,20 @@ class HeatPlan:
         _check(_lib().tmg_heat_stats(self._h, ctypes.byref(c), ctypes.byref(rel),
                                      hist.ctypes.data_as(_dp), hist_len), "tmg_heat_stats")
         return SolveStats(TMG_OK, c.value, rel.value, hist[~np.isnan(hist)])
+
+    def info(self) -> dict:
+        tl, sl, lc = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        ws = ctypes.c_size_t(0)
+        _check(_lib().tmg_heat_info(self._h, ctypes.byref(tl), ctypes.byref(sl), ctypes.byref(lc), ctypes.byref(ws)),
+               "tmg_heat_info")
+        return {"time_levels": tl.value, "space_levels": sl.value, "launches_per_cycle": lc.value,
+                "workspace_bytes": ws.value}
+
+    def profile(self, f, u0, u, reps: int = 10) -> dict:
+        """Per-launch CUDA-event times (ms) of the level-0 kernels and of one
+        cycle (tmg_heat_profile); u is left arbitrary."""
+        ms = np.zeros(5)
+        _check(_lib().tmg_heat_profile(self._h, self._ptr(f, self._shape(), "f"), self._ptr(u0, (self.n, self.n), "u0"),
+                                       self._ptr(u, self._shape(), "u"), reps, ms.ctypes.data_as(_dp), 5),
+               "tmg_heat_profile")
+        return {"resid": ms[0], "pre": ms[1], "post": ms[2], "update": ms[3], "cycle": ms[4]}
