@@ -1029,13 +1029,16 @@ def main():
                          "equation (profiling)")
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"],
                     help="forms of the batched workloads run with --workload")
+    ap.add_argument("--heat-n-log2", type=int, default=12,
+                    help="intervals of the space-time heat line = 2^k (smaller cases for ncu captures)")
     ap.add_argument("--batch-stride", type=int, default=1,
                     help="with --workload heat: every s-th mode only (smaller cases for ncu captures)")
     args = ap.parse_args()
     global BATCH_STRIDE
     BATCH_STRIDE = max(1, args.batch_stride) if args.workload == "heat" else 1
-    global N_FULL, P_MAIN
+    global N_FULL, P_MAIN, HEAT_N
     N_FULL = 1 << args.n_log2
+    HEAT_N = 1 << args.heat_n_log2
     P_MAIN = args.p_t
     if args.impl == "reference":
         run_reference(args)
