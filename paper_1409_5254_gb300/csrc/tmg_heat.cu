@@ -628,6 +628,280 @@ __global__ void __launch_bounds__(kHT) kh_post_w(const T* __restrict__ r, const 
     }
 }
 
+// ----------------------------------------------------------- full-row warps
+// For n + 1 <= 128 a warp spans whole grid rows, both boundary columns
+// included: lane L' of a segment of SW = (n+1)/CPL lanes holds the local
+// columns CPL L' + q (q < CPL), which are fine columns CPL L' + q - 1.  Local
+// column 0 is the left boundary (x = 0); the right neighbour of the last
+// local column is the right boundary.  No lane carries halo work and every
+// lane holds grid columns; with n + 1 < 32 one warp holds 32/SW intervals.
+template <int CPL>
+struct RowGeom {
+    int SW, IPW, ls, seg;
+    __device__ RowGeom(int n, int lane) {
+        SW = (n + 1) / CPL;
+        IPW = 32 / SW;
+        ls = lane % SW;
+        seg = lane / SW;
+    }
+};
+
+// Neighbour values of local column q at the current row from the row vector
+// v[CPL][D] of every lane: left (q-1) and right (q+1), zero beyond the right
+// boundary.  All lanes call it (shuffles).
+template <int D, typename T, int CPL>
+__device__ __forceinline__ void row_neighbours(const T (&v)[CPL][D], bool last, T (&lt)[CPL][D], T (&rt)[CPL][D]) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const T fromL = shup(v[CPL - 1][k]);
+        const T fromR = shdn(v[0][k]);
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            lt[q][k] = q > 0 ? v[q - 1][k] : fromL;
+            rt[q][k] = q + 1 < CPL ? v[q + 1][k] : (last ? T(0) : fromR);
+        }
+    }
+}
+
+template <int D, typename T, int CPL>
+__device__ __forceinline__ void row_load(const T* __restrict__ rm, int nn, int n, int i, int lc0, bool live,
+                                         T (&v)[CPL][D]) {
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+        const int j = lc0 + q - 1;
+        const bool in = live && (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
+        const int o = in ? i * n + j : 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[q][k] = in ? rm[k * nn + o] : T(0);
+    }
+}
+
+// Pre-smoothing, residual and full weighting (as kh_pre_w) on full rows:
+// coarse column J sits on the even local column 2J + 2; its weights take y
+// at local columns 2J + 1, 2J + 2, 2J + 3.
+template <int D, typename T, int CPL>
+__global__ void __launch_bounds__(kHT) kh_pre_f(const T* __restrict__ r, T* __restrict__ rc, int64_t N, int n,
+                                                int nc, HeatK<D, T> C, T omega) {
+    constexpr int NO = CPL >= 2 ? CPL / 2 : 1;   // coarse outputs per lane
+    const int lane = threadIdx.x & 31;
+    const RowGeom<CPL> G(n, lane);
+    const bool last = G.ls == G.SW - 1;
+    const int nn = n * n, ncc = nc * nc;
+    const int chunks = (nc + kPreRows - 1) / kPreRows;
+    const int64_t groups = (N + G.IPW - 1) / G.IPW;
+    const int64_t tasks = groups * chunks;
+    const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
+    const int lc0 = CPL * G.ls;
+    for (int64_t w = ((int64_t)blockIdx.x * kHT + threadIdx.x) >> 5; w < tasks; w += nw) {
+        const int64_t g = w / chunks;
+        const int ch = (int)(w - g * chunks);
+        const int64_t m = g * G.IPW + G.seg;
+        const bool live = m < N;
+        const int I0 = ch * kPreRows, I1 = min(I0 + kPreRows, nc);
+        const T* rm = r + (live ? m : 0) * D * (int64_t)nn;
+        T* rcm = rc + (live ? m : 0) * D * (int64_t)ncc;
+        const int f0 = 2 * I0, f1 = 2 * I1;
+        T x[3][CPL][D], rv[CPL][D], rn[CPL][D], pf[CPL][D], acc[NO][D];
+        {
+            T t0[CPL][D];
+            row_load<D, T, CPL>(rm, nn, n, f0 - 1, lc0, live, t0);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) smooth0<D, T>(C, omega, t0[q], x[0][q]);
+        }
+        row_load<D, T, CPL>(rm, nn, n, f0, lc0, live, rv);
+        row_load<D, T, CPL>(rm, nn, n, f0 + 1, lc0, live, rn);
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            smooth0<D, T>(C, omega, rv[q], x[1][q]);
+            smooth0<D, T>(C, omega, rn[q], x[2][q]);
+        }
+#pragma unroll
+        for (int o = 0; o < NO; ++o)
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc[o][k] = T(0);
+        for (int i = f0;; ++i) {
+            row_load<D, T, CPL>(rm, nn, n, i + 2, lc0, live, pf);
+            // y = r - G x at row i
+            T lt[CPL][D], rt[CPL][D], y[CPL][D];
+            row_neighbours<D, T, CPL>(x[1], last, lt, rt);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                T nb[D], gx[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) nb[k] = (x[0][q][k] + x[2][q][k]) + (lt[q][k] + rt[q][k]);
+                apply_G<D, T>(C, x[1][q], nb, gx);
+#pragma unroll
+                for (int k = 0; k < D; ++k) y[q][k] = rv[q][k] - gx[k];
+            }
+            // across the columns at the even local columns: H = y(q-1) + 2 y(q) + y(q+1)
+            T yl[CPL][D], yr[CPL][D], H[NO][D];
+            row_neighbours<D, T, CPL>(y, last, yl, yr);
+#pragma unroll
+            for (int o = 0; o < NO; ++o) {
+                const int q = CPL >= 2 ? 2 * o : 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) H[o][k] = (yl[q][k] + yr[q][k]) + T(2) * y[q][k];
+            }
+            if ((i & 1) == 0) {
+                if (i > f0) {
+                    const int I = i / 2 - 1;
+#pragma unroll
+                    for (int o = 0; o < NO; ++o) {
+                        const int lc = lc0 + (CPL >= 2 ? 2 * o : 0);
+                        const int J = (lc - 2) >> 1;
+                        const bool wr = live && (lc & 1) == 0 && lc >= 2 && J < nc;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) {
+                            acc[o][k] += H[o][k];
+                            if (wr) rcm[k * ncc + I * nc + J] = acc[o][k] * T(0.0625);
+                        }
+                    }
+                }
+                if (i == f1) break;
+#pragma unroll
+                for (int o = 0; o < NO; ++o)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc[o][k] = H[o][k];
+            } else {
+#pragma unroll
+                for (int o = 0; o < NO; ++o)
+#pragma unroll
+                    for (int k = 0; k < D; ++k) acc[o][k] += T(2) * H[o][k];
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    x[0][q][k] = x[1][q][k];
+                    x[1][q][k] = x[2][q][k];
+                    rv[q][k] = rn[q][k];
+                    rn[q][k] = pf[q][k];
+                }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) smooth0<D, T>(C, omega, pf[q], x[2][q]);
+        }
+    }
+}
+
+// Coarse-grid correction and post-smoothing (as kh_post_w) on full rows.
+// A lane's fine columns lc0 - 1 .. lc0 + CPL - 2 read the row-interpolated
+// coarse correction at coarse columns jlo .. jlo + NJ - 1; an odd fine column
+// 2J+1 takes J, an even one 2J the mean of J-1 and J.
+template <int D, typename T, int CPL>
+__global__ void __launch_bounds__(kHT) kh_post_f(const T* __restrict__ r, const T* __restrict__ xc,
+                                                 T* __restrict__ out, int64_t N, int n, int nc, HeatK<D, T> C,
+                                                 T omega, T alpha, int acc) {
+    constexpr int NJ = CPL >= 2 ? CPL / 2 + 1 : 2;
+    const int lane = threadIdx.x & 31;
+    const RowGeom<CPL> G(n, lane);
+    const bool last = G.ls == G.SW - 1;
+    const int nn = n * n, ncc = nc * nc;
+    const int chunks = (n + kPostRows - 1) / kPostRows;
+    const int64_t groups = (N + G.IPW - 1) / G.IPW;
+    const int64_t tasks = groups * chunks;
+    const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
+    const int lc0 = CPL * G.ls;
+    const int j0 = lc0 - 1;                                   // fine column of q = 0
+    const int jlo = (j0 & 1) ? (j0 - 1) >> 1 : (j0 >> 1) - 1;  // first coarse column read
+    const bool j0odd = j0 & 1;
+    for (int64_t w = ((int64_t)blockIdx.x * kHT + threadIdx.x) >> 5; w < tasks; w += nw) {
+        const int64_t g = w / chunks;
+        const int ch = (int)(w - g * chunks);
+        const int64_t m = g * G.IPW + G.seg;
+        const bool live = m < N;
+        const int i0 = ch * kPostRows, i1 = min(i0 + kPostRows, n);
+        const T* rm = r + (live ? m : 0) * D * (int64_t)nn;
+        const T* cm = xc + (live ? m : 0) * D * (int64_t)ncc;
+        T* om = out + (live ? m : 0) * D * (int64_t)nn;
+        // x at fine row a from its r values
+        auto xrow = [&](int a, const T (&ra)[CPL][D], T (&xa)[CPL][D]) {
+            T cr[NJ][D];
+            const int Ia = (a & 1) ? (a - 1) >> 1 : (a >> 1) - 1, Ib = (a & 1) ? -1 : a >> 1;
+            const bool ia = live && (unsigned)Ia < (unsigned)nc, ib = live && (unsigned)Ib < (unsigned)nc;
+#pragma unroll
+            for (int t = 0; t < NJ; ++t) {
+                const int J = jlo + t;
+                const bool jin = (unsigned)J < (unsigned)nc;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const T* ck = cm + k * ncc;
+                    const T va = (ia && jin) ? ck[Ia * nc + J] : T(0);
+                    if (a & 1) {
+                        cr[t][k] = va;
+                    } else {
+                        const T vb = (ib && jin) ? ck[Ib * nc + J] : T(0);
+                        cr[t][k] = T(0.5) * (va + vb);
+                    }
+                }
+            }
+            const bool rowin = (unsigned)a < (unsigned)n;
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                T d[D];
+                smooth0<D, T>(C, omega, ra[q], d);
+                const int j = j0 + q;
+                const bool in = rowin && (unsigned)j < (unsigned)n;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    T p;
+                    if (CPL >= 2) {   // j0 odd: even q on a coarse column, odd q between two
+                        p = (q & 1) ? T(0.5) * (cr[(q - 1) / 2][k] + cr[(q + 1) / 2][k]) : cr[q / 2][k];
+                    } else {
+                        p = j0odd ? cr[0][k] : T(0.5) * (cr[0][k] + cr[1][k]);
+                    }
+                    xa[q][k] = in ? d[k] + p : T(0);
+                }
+            }
+        };
+        T x[3][CPL][D], rv[CPL][D], rn[CPL][D], pf[CPL][D];
+        {
+            T t0[CPL][D];
+            row_load<D, T, CPL>(rm, nn, n, i0 - 1, lc0, live, t0);
+            xrow(i0 - 1, t0, x[0]);
+        }
+        row_load<D, T, CPL>(rm, nn, n, i0, lc0, live, rv);
+        xrow(i0, rv, x[1]);
+        row_load<D, T, CPL>(rm, nn, n, i0 + 1, lc0, live, rn);
+        xrow(i0 + 1, rn, x[2]);
+        for (int i = i0; i < i1; ++i) {
+            row_load<D, T, CPL>(rm, nn, n, i + 2, lc0, live, pf);
+            T ov[CPL][D];   // the accumulated output of row i, loaded early
+            if (acc) row_load<D, T, CPL>(om, nn, n, i, lc0, live, ov);
+            T lt[CPL][D], rt[CPL][D];
+            row_neighbours<D, T, CPL>(x[1], last, lt, rt);
+            T* oi = om + i * n;
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                T nb[D], gx[D], e[D], y[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) nb[k] = (x[0][q][k] + x[2][q][k]) + (lt[q][k] + rt[q][k]);
+                apply_G<D, T>(C, x[1][q], nb, gx);
+#pragma unroll
+                for (int k = 0; k < D; ++k) e[k] = rv[q][k] - gx[k];
+                apply_Dinv<D, T>(C, e, y);
+                const int j = j0 + q;
+                if (live && (unsigned)j < (unsigned)n) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        const T z = fma(omega, y[k], x[1][q][k]);
+                        oi[k * nn + j] = acc ? fma(alpha, z, ov[q][k]) : alpha * z;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    x[0][q][k] = x[1][q][k];
+                    x[1][q][k] = x[2][q][k];
+                    rv[q][k] = rn[q][k];
+                    rn[q][k] = pf[q][k];
+                }
+            xrow(i + 2, pf, x[2]);
+        }
+    }
+}
+
 // One grid point: G_tau is its point block, solved exactly.
 // out = alpha Dinv r (acc = 0) or out += alpha Dinv r (acc = 1).
 template <int D, typename T>
@@ -832,13 +1106,57 @@ struct HeatImpl {
             return;
         }
         const int nc = H->nsz[sl + 1];
-        const int64_t pre_tasks = N * ((nc + kPreStride - 1) / kPreStride) * ((nc + kPreRows - 1) / kPreRows);
-        kh_pre_w<D, T><<<grid_warps(H, pre_tasks), kHT, 0, H->s>>>(rhs, b.rs[sl + 1], N, n, nc, C, (T)kOmegaS);
+        pre(H, rhs, b.rs[sl + 1], N, n, nc, C);
         vcycle(H, sl + 1, b.rs[sl + 1], N, tau, b.ys[sl + 1], T(1), 0);
-        const int64_t post_tasks = N * ((n + kPostStride - 1) / kPostStride) * ((n + kPostRows - 1) / kPostRows);
         ++g_launches;
-        kh_post_w<D, T><<<grid_warps(H, post_tasks), kHT, 0, H->s>>>(rhs, b.ys[sl + 1], out, N, n, nc, C,
-                                                                    (T)kOmegaS, alpha, acc);
+        post(H, rhs, b.ys[sl + 1], out, N, n, nc, C, alpha, acc);
+    }
+
+    // Fused pre kernel of one spatial level: full-row warps up to n = 127,
+    // 64-column strips above.
+    // Full rows for n + 1 = 32 CPL with CPL = 1, or with a row window of at
+    // most 32 bytes per lane and coefficient set (registers); strips otherwise.
+    static bool full_rows(int n) {
+        return n + 1 <= 32 || ((n + 1 == 64 || n + 1 == 128) && D * ((n + 1) / 32) * (int)sizeof(T) <= 32);
+    }
+
+    static void pre(tmg_heat* H, const T* rhs, T* rc, int64_t N, int n, int nc, const HeatK<D, T>& C) {
+        const T w = (T)kOmegaS;
+        const int64_t rows = (nc + kPreRows - 1) / kPreRows;
+        if (!full_rows(n)) {
+            const int64_t tasks = N * ((nc + kPreStride - 1) / kPreStride) * rows;
+            kh_pre_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
+        } else if (n + 1 <= 32) {
+            const int64_t tasks = ((N + 32 / (n + 1) - 1) / (32 / (n + 1))) * rows;
+            kh_pre_f<D, T, 1><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
+        } else if (n + 1 == 64) {
+            kh_pre_f<D, T, 2><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
+        } else if (n + 1 == 128) {
+            kh_pre_f<D, T, 4><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
+        } else {
+            const int64_t tasks = N * ((nc + kPreStride - 1) / kPreStride) * rows;
+            kh_pre_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
+        }
+    }
+
+    static void post(tmg_heat* H, const T* rhs, const T* xc, T* out, int64_t N, int n, int nc,
+                     const HeatK<D, T>& C, T alpha, int acc) {
+        const T w = (T)kOmegaS;
+        const int64_t rows = (n + kPostRows - 1) / kPostRows;
+        if (!full_rows(n)) {
+            const int64_t tasks = N * ((n + kPostStride - 1) / kPostStride) * rows;
+            kh_post_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
+        } else if (n + 1 <= 32) {
+            const int64_t tasks = ((N + 32 / (n + 1) - 1) / (32 / (n + 1))) * rows;
+            kh_post_f<D, T, 1><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
+        } else if (n + 1 == 64) {
+            kh_post_f<D, T, 2><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
+        } else if (n + 1 == 128) {
+            kh_post_f<D, T, 4><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
+        } else {
+            const int64_t tasks = N * ((n + kPostStride - 1) / kPostStride) * rows;
+            kh_post_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
+        }
     }
 
     // Time residual of level l (u0 only at level 0) into b.g.
@@ -1069,15 +1387,8 @@ tmg_status profile_heat(tmg_heat* H, const double* F, const double* u0, double* 
                 rhs, uu, nullptr, b.g, nullptr, N, n, C, nullptr);
         });
         if (nc > 0) {
-            const int64_t pre_tasks = N * ((nc + kPreStride - 1) / kPreStride) * ((nc + kPreRows - 1) / kPreRows);
-            ms[1] = timed([&] {
-                kh_pre_w<D, T><<<grid_warps(H, pre_tasks), kHT, 0, H->s>>>(rhs, b.rs[1], N, n, nc, C, (T)kOmegaS);
-            });
-            const int64_t post_tasks = N * ((n + kPostStride - 1) / kPostStride) * ((n + kPostRows - 1) / kPostRows);
-            ms[2] = timed([&] {
-                kh_post_w<D, T><<<grid_warps(H, post_tasks), kHT, 0, H->s>>>(rhs, b.ys[1], out, N, n, nc, C,
-                                                                            (T)kOmegaS, (T)kOmegaT, 1);
-            });
+            ms[1] = timed([&] { HeatImpl<D, T>::pre(H, rhs, b.rs[1], N, n, nc, C); });
+            ms[2] = timed([&] { HeatImpl<D, T>::post(H, rhs, b.ys[1], out, N, n, nc, C, (T)kOmegaT, 1); });
         }
     };
     ms[1] = ms[2] = 0.0;

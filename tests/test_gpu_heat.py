@@ -3,8 +3,10 @@ against the FP64 oracle (oracle/heat.py), through the C ABI.
 
 * one and two cycles from zero and from a random start: every value of the
   iterate within 1e-12 of the oracle's (relative to the largest value), over
-  degrees 0..5, grids of 1, 3, 7, 15 and 31 points a side (one to five
-  spatial levels) and 1..64 intervals (one to seven time levels);
+  degrees 0..5, grids of 1 to 255 points a side (one to eight spatial
+  levels; whole-row warps with 1, 2 or 4 columns per lane and several
+  intervals per warp on the small grids, 64-column strips on the others) and
+  1..64 intervals (one to seven time levels);
 * the residual r = F - L u value by value;
 * full solves: the residual history matches the oracle's cycle by cycle, and
   the converged solution matches the exact block forward substitution;
@@ -42,7 +44,8 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("p,n,N", [(0, 7, 16), (1, 7, 16), (2, 15, 8), (1, 15, 64), (3, 3, 4), (5, 7, 2),
-                                   (1, 31, 8), (4, 1, 8), (1, 7, 1), (2, 1, 1)])
+                                   (1, 31, 8), (4, 1, 8), (1, 7, 1), (2, 1, 1), (1, 63, 4), (3, 63, 2),
+                                   (1, 127, 2), (0, 255, 2)])
 def test_cycle_iterates(p, n, N):
     H = _H()
     tau, F, u0 = inputs.heat_problem(10 + p + n + N, N, p, n)
@@ -130,7 +133,8 @@ def test_rejects_bad_sizes():
         tmg.HeatPlan(1, 1e-3, 7, 16, nu1=0, nu2=0)
 
 
-@pytest.mark.parametrize("p,n,N", [(1, 15, 16), (2, 31, 8), (0, 7, 64), (5, 7, 4), (1, 1, 8)])
+@pytest.mark.parametrize("p,n,N", [(1, 15, 16), (2, 31, 8), (0, 7, 64), (5, 7, 4), (1, 1, 8), (1, 63, 4),
+                                   (1, 127, 2), (3, 127, 2), (0, 255, 2)])
 def test_mixed_cycle_within_fp32(p, n, N):
     """u + C(F - L u) with the cycle C in FP32: within FP32 rounding of the
     oracle's FP64 cycle, measured against the size of the correction."""
