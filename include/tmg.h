@@ -72,8 +72,8 @@ typedef struct {
     int use_graph;      /* 1: whole solve as one CUDA graph launch (default 1) */
     int initial_guess;  /* 1: tmg_solve starts from the u passed in (default 0: u = 0) */
     int64_t tail_cap;   /* most intervals the on-chip coarse solver takes (0: default, 64 for
-                           V-cycles, 8192 for W-cycles; at most 8192); smaller values move
-                           more levels to the streaming kernels */
+                           V-cycles, 8192 for W-cycles, 2048 for W-cycles of batches; at most
+                           8192); smaller values move more levels to the streaming kernels */
     int use_pdl;        /* 1: programmatic dependent launch between the kernels of a cycle,
                            hiding each launch behind its predecessor's tail (default 1) */
     int update_residual; /* TMG_MIXED: 1 = keep the level-0 residual as a float pair (about
@@ -345,7 +345,7 @@ typedef struct tmg_batch tmg_batch;
  * kernel covers all instances of a group still iterating at once.
  * W-cycles (gamma = 2) visit every level below level 0 twice per visit of
  * its parent: in the grid form the streaming levels down to the first one of
- * at most 8192 intervals are launched once per visit, and the levels from
+ * at most tail_cap (default 2048) intervals are launched once per visit, and the levels from
  * there on run in one CTA per instance, whose shared-memory recursion makes
  * its own visits; the CTA form runs the whole W recursion on chip.  Degrees
  * 10 and 20 run V-cycles in the grid form, the level-0 residual recomputed

@@ -1418,8 +1418,12 @@ __device__ __forceinline__ double start0_loop(float* __restrict__ rT, short* __r
     return ss;
 }
 
+// At D = 11 two blocks per SM (128 registers, a few hundred bytes of spill
+// per thread) beat one block at 160 registers: p_t = 10 mixed solve 46.9 ms
+// against 52.6 ms; three blocks (80 registers) spill 2.7 KB and take 54.8 ms,
+// and two blocks at D = 21 take 62.9 ms against 56.0 ms.
 template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
+__global__ void __launch_bounds__(kNT, (D > 6 && D <= 11) ? 2 : 1) k_down0(T* __restrict__ rT, short* __restrict__ rlo, T* __restrict__ fc,
                                                int64_t nchunks, Res0 R, LevelK<T, D> K, Xfer<T, D> X, int nu1,
                                                int H, double* __restrict__ partials, DevState* st) {
     pdl_enter();
@@ -1451,7 +1455,7 @@ __global__ void __launch_bounds__(kNT) k_down0(T* __restrict__ rT, short* __rest
 // Level 0 on the way up: recompute the pre-smoothed correction from r, add
 // the prolongated level-1 correction, post-smooth, and update u += c in FP64.
 template <int DIR, typename T, int D>
-__global__ void __launch_bounds__(kNT) k_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
+__global__ void __launch_bounds__(kNT, (D > 6 && D <= 11) ? 2 : 1) k_up0(const T* __restrict__ rT, const T* __restrict__ uc, int64_t nchunks,
                                              LevelK<T, D> K, Xfer<T, D> X, int nu1, int nu2, int H,
                                              const DevState* __restrict__ st) {
     pdl_enter();

@@ -139,14 +139,15 @@ def test_batched_fp64_cycles_match_textbook_cycle(dev, schedule, nu):
             assert e <= 1e-12, (k, i, int(p[i]), int(N[i]), z[i], e)
 
 
-@pytest.mark.parametrize("schedule", ["grid", "cta"])
+@pytest.mark.parametrize("schedule,cap", [("grid", 0), ("grid", 8192), ("cta", 0)])
 @pytest.mark.parametrize("nu", [(1, 1), (2, 1)])
-def test_batched_w_cycles_match_textbook_cycle(dev, schedule, nu):
+def test_batched_w_cycles_match_textbook_cycle(dev, schedule, cap, nu):
     """W-cycles (gamma = 2) in the batched solve at the iterate level: every
     level below level 0 visited twice per visit of its parent, the second
     visit from the first one's result.  The grid form launches the streaming
-    levels once per visit down to the first level of at most 8192 intervals
-    and runs the rest in one CTA per instance; the CTA form runs the whole
+    levels once per visit down to the first level of at most tail_cap
+    intervals (the default 2048, and 8192) and runs the rest in one CTA per
+    instance; the CTA form runs the whole
     recursion on chip.  Against k = 1, 2, 3 applications of the oracle's
     textbook W-cycle (eq. chap4_errorTwoGridCycle recursed twice per level),
     1e-12 relative; lengths up to 2^16 so that the grid form has streaming
@@ -164,7 +165,7 @@ def test_batched_w_cycles_match_textbook_cycle(dev, schedule, nu):
            for i in range(len(N))]
     for k in (1, 2, 3):
         with tmg.Batch(p, tau, lam, N, precision="fp64", tol=0.0, max_cycles=k, schedule=sched, nu1=nu[0],
-                       nu2=nu[1], gamma=2) as B:
+                       nu2=nu[1], gamma=2, tail_cap=cap) as B:
             u = B.solve(f, u0d, allow_notconv=True)
             cyc, rel, mx = B.stats()
             us = B.split(u.cpu().numpy())
