@@ -368,8 +368,8 @@ __global__ void __launch_bounds__(kRT) kh_update_pair(double* __restrict__ u, co
 // 62 (post) or 60 (pre: 30 coarse columns) fine columns and no lane runs
 // extra halo code.  The loads of row i + 2 are issued before row i is
 // computed.
-constexpr int kPreRows = 16;    // coarse rows per pre task
-constexpr int kPostRows = 32;   // fine rows per post task
+constexpr int kPreRows = 16;    // coarse rows per pre task (at most; fewer when that leaves SMs idle)
+constexpr int kPostRows = 32;   // fine rows per post task (at most)
 constexpr int kPreStride = 30;  // coarse columns per pre strip
 constexpr int kPostStride = 62; // fine columns per post strip
 
@@ -408,10 +408,10 @@ __device__ __forceinline__ void smooth0(const HeatK<D, T>& C, T omega, const T (
 // 1..30.
 template <int D, typename T>
 __global__ void __launch_bounds__(kHT) kh_pre_w(const T* __restrict__ r, T* __restrict__ rc, int64_t N, int n,
-                                                int nc, HeatK<D, T> C, T omega) {
+                                                int nc, int rows, HeatK<D, T> C, T omega) {
     const int lane = threadIdx.x & 31;
     const int nn = n * n, ncc = nc * nc;
-    const int strips = (nc + kPreStride - 1) / kPreStride, chunks = (nc + kPreRows - 1) / kPreRows;
+    const int strips = (nc + kPreStride - 1) / kPreStride, chunks = (nc + rows - 1) / rows;
     const int per = strips * chunks;
     const int64_t tasks = N * per;
     const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kHT) kh_pre_w(const T* __restrict__ r, T* __re
         const int64_t m = w / per;
         const int rem = (int)(w - m * per);
         const int s = rem / chunks, ch = rem - s * chunks;
-        const int I0 = ch * kPreRows, I1 = min(I0 + kPreRows, nc);
+        const int I0 = ch * rows, I1 = min(I0 + rows, nc);
         const T* rm = r + m * D * (int64_t)nn;
         T* rcm = rc + m * D * (int64_t)ncc;
         const int c0 = 2 * kPreStride * s - 2;
@@ -508,11 +508,11 @@ __global__ void __launch_bounds__(kHT) kh_pre_w(const T* __restrict__ r, T* __re
 // Jl + 1 (the next lane's); z is written at local columns 1..62.
 template <int D, typename T>
 __global__ void __launch_bounds__(kHT) kh_post_w(const T* __restrict__ r, const T* __restrict__ xc,
-                                                 T* __restrict__ out, int64_t N, int n, int nc, HeatK<D, T> C,
-                                                 T omega, T alpha, int acc) {
+                                                 T* __restrict__ out, int64_t N, int n, int nc, int rows,
+                                                 HeatK<D, T> C, T omega, T alpha, int acc) {
     const int lane = threadIdx.x & 31;
     const int nn = n * n, ncc = nc * nc;
-    const int strips = (n + kPostStride - 1) / kPostStride, chunks = (n + kPostRows - 1) / kPostRows;
+    const int strips = (n + kPostStride - 1) / kPostStride, chunks = (n + rows - 1) / rows;
     const int per = strips * chunks;
     const int64_t tasks = N * per;
     const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(kHT) kh_post_w(const T* __restrict__ r, const 
         const int64_t m = w / per;
         const int rem = (int)(w - m * per);
         const int s = rem / chunks, ch = rem - s * chunks;
-        const int i0 = ch * kPostRows, i1 = min(i0 + kPostRows, n);
+        const int i0 = ch * rows, i1 = min(i0 + rows, n);
         const T* rm = r + m * D * (int64_t)nn;
         const T* cm = xc + m * D * (int64_t)ncc;
         T* om = out + m * D * (int64_t)nn;
@@ -681,13 +681,13 @@ __device__ __forceinline__ void row_load(const T* __restrict__ rm, int nn, int n
 // at local columns 2J + 1, 2J + 2, 2J + 3.
 template <int D, typename T, int CPL>
 __global__ void __launch_bounds__(kHT) kh_pre_f(const T* __restrict__ r, T* __restrict__ rc, int64_t N, int n,
-                                                int nc, HeatK<D, T> C, T omega) {
+                                                int nc, int rows, HeatK<D, T> C, T omega) {
     constexpr int NO = CPL >= 2 ? CPL / 2 : 1;   // coarse outputs per lane
     const int lane = threadIdx.x & 31;
     const RowGeom<CPL> G(n, lane);
     const bool last = G.ls == G.SW - 1;
     const int nn = n * n, ncc = nc * nc;
-    const int chunks = (nc + kPreRows - 1) / kPreRows;
+    const int chunks = (nc + rows - 1) / rows;
     const int64_t groups = (N + G.IPW - 1) / G.IPW;
     const int64_t tasks = groups * chunks;
     const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(kHT) kh_pre_f(const T* __restrict__ r, T* __re
         const int ch = (int)(w - g * chunks);
         const int64_t m = g * G.IPW + G.seg;
         const bool live = m < N;
-        const int I0 = ch * kPreRows, I1 = min(I0 + kPreRows, nc);
+        const int I0 = ch * rows, I1 = min(I0 + rows, nc);
         const T* rm = r + (live ? m : 0) * D * (int64_t)nn;
         T* rcm = rc + (live ? m : 0) * D * (int64_t)ncc;
         const int f0 = 2 * I0, f1 = 2 * I1;
@@ -789,14 +789,14 @@ __global__ void __launch_bounds__(kHT) kh_pre_f(const T* __restrict__ r, T* __re
 // 2J+1 takes J, an even one 2J the mean of J-1 and J.
 template <int D, typename T, int CPL>
 __global__ void __launch_bounds__(kHT) kh_post_f(const T* __restrict__ r, const T* __restrict__ xc,
-                                                 T* __restrict__ out, int64_t N, int n, int nc, HeatK<D, T> C,
-                                                 T omega, T alpha, int acc) {
+                                                 T* __restrict__ out, int64_t N, int n, int nc, int rows,
+                                                 HeatK<D, T> C, T omega, T alpha, int acc) {
     constexpr int NJ = CPL >= 2 ? CPL / 2 + 1 : 2;
     const int lane = threadIdx.x & 31;
     const RowGeom<CPL> G(n, lane);
     const bool last = G.ls == G.SW - 1;
     const int nn = n * n, ncc = nc * nc;
-    const int chunks = (n + kPostRows - 1) / kPostRows;
+    const int chunks = (n + rows - 1) / rows;
     const int64_t groups = (N + G.IPW - 1) / G.IPW;
     const int64_t tasks = groups * chunks;
     const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
@@ -809,7 +809,7 @@ __global__ void __launch_bounds__(kHT) kh_post_f(const T* __restrict__ r, const 
         const int ch = (int)(w - g * chunks);
         const int64_t m = g * G.IPW + G.seg;
         const bool live = m < N;
-        const int i0 = ch * kPostRows, i1 = min(i0 + kPostRows, n);
+        const int i0 = ch * rows, i1 = min(i0 + rows, n);
         const T* rm = r + (live ? m : 0) * D * (int64_t)nn;
         const T* cm = xc + (live ? m : 0) * D * (int64_t)ncc;
         T* om = out + (live ? m : 0) * D * (int64_t)nn;
@@ -1120,43 +1120,55 @@ struct HeatImpl {
         return n + 1 <= 32 || ((n + 1 == 64 || n + 1 == 128) && D * ((n + 1) / 32) * (int)sizeof(T) <= 32);
     }
 
+    // Rows per warp task: the longest of max_rows, halving down to 4, that
+    // still gives every SM 16 warps; short grids and coarse time levels
+    // would otherwise leave few warps, each walking a long chain of rows.
+    static int chunk_rows(const tmg_heat* H, int64_t row_sets, int total_rows, int max_rows) {
+        const int64_t want = (int64_t)(H->max_blocks / 8) * 16;
+        int rows = max_rows;
+        while (rows > 4 && row_sets * ((total_rows + rows - 1) / rows) < want) rows /= 2;
+        return rows;
+    }
+
+    // Warp tasks per row chunk: intervals x strips (strip kernels), intervals
+    // (whole-row kernels, CPL >= 2), interval groups of 32 / (n + 1) (CPL = 1).
+    static int64_t row_sets(int64_t N, int n, int cols, int stride) {
+        if (!full_rows(n)) return N * ((cols + stride - 1) / stride);
+        if (n + 1 <= 32) return (N + 32 / (n + 1) - 1) / (32 / (n + 1));
+        return N;
+    }
+
     static void pre(tmg_heat* H, const T* rhs, T* rc, int64_t N, int n, int nc, const HeatK<D, T>& C) {
         const T w = (T)kOmegaS;
-        const int64_t rows = (nc + kPreRows - 1) / kPreRows;
-        if (!full_rows(n)) {
-            const int64_t tasks = N * ((nc + kPreStride - 1) / kPreStride) * rows;
-            kh_pre_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
-        } else if (n + 1 <= 32) {
-            const int64_t tasks = ((N + 32 / (n + 1) - 1) / (32 / (n + 1))) * rows;
-            kh_pre_f<D, T, 1><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
-        } else if (n + 1 == 64) {
-            kh_pre_f<D, T, 2><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
-        } else if (n + 1 == 128) {
-            kh_pre_f<D, T, 4><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
-        } else {
-            const int64_t tasks = N * ((nc + kPreStride - 1) / kPreStride) * rows;
-            kh_pre_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, rc, N, n, nc, C, w);
-        }
+        const int64_t sets = row_sets(N, n, nc, kPreStride);
+        const int rows = chunk_rows(H, sets, nc, kPreRows);
+        const int64_t tasks = sets * ((nc + rows - 1) / rows);
+        const int g = grid_warps(H, tasks);
+        if (!full_rows(n))
+            kh_pre_w<D, T><<<g, kHT, 0, H->s>>>(rhs, rc, N, n, nc, rows, C, w);
+        else if (n + 1 <= 32)
+            kh_pre_f<D, T, 1><<<g, kHT, 0, H->s>>>(rhs, rc, N, n, nc, rows, C, w);
+        else if (n + 1 == 64)
+            kh_pre_f<D, T, 2><<<g, kHT, 0, H->s>>>(rhs, rc, N, n, nc, rows, C, w);
+        else
+            kh_pre_f<D, T, 4><<<g, kHT, 0, H->s>>>(rhs, rc, N, n, nc, rows, C, w);
     }
 
     static void post(tmg_heat* H, const T* rhs, const T* xc, T* out, int64_t N, int n, int nc,
                      const HeatK<D, T>& C, T alpha, int acc) {
         const T w = (T)kOmegaS;
-        const int64_t rows = (n + kPostRows - 1) / kPostRows;
-        if (!full_rows(n)) {
-            const int64_t tasks = N * ((n + kPostStride - 1) / kPostStride) * rows;
-            kh_post_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
-        } else if (n + 1 <= 32) {
-            const int64_t tasks = ((N + 32 / (n + 1) - 1) / (32 / (n + 1))) * rows;
-            kh_post_f<D, T, 1><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
-        } else if (n + 1 == 64) {
-            kh_post_f<D, T, 2><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
-        } else if (n + 1 == 128) {
-            kh_post_f<D, T, 4><<<grid_warps(H, N * rows), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
-        } else {
-            const int64_t tasks = N * ((n + kPostStride - 1) / kPostStride) * rows;
-            kh_post_w<D, T><<<grid_warps(H, tasks), kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, C, w, alpha, acc);
-        }
+        const int64_t sets = row_sets(N, n, n, kPostStride);
+        const int rows = chunk_rows(H, sets, n, kPostRows);
+        const int64_t tasks = sets * ((n + rows - 1) / rows);
+        const int g = grid_warps(H, tasks);
+        if (!full_rows(n))
+            kh_post_w<D, T><<<g, kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, rows, C, w, alpha, acc);
+        else if (n + 1 <= 32)
+            kh_post_f<D, T, 1><<<g, kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, rows, C, w, alpha, acc);
+        else if (n + 1 == 64)
+            kh_post_f<D, T, 2><<<g, kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, rows, C, w, alpha, acc);
+        else
+            kh_post_f<D, T, 4><<<g, kHT, 0, H->s>>>(rhs, xc, out, N, n, nc, rows, C, w, alpha, acc);
     }
 
     // Time residual of level l (u0 only at level 0) into b.g.
