@@ -681,8 +681,11 @@ __device__ __forceinline__ void row_load(const T* __restrict__ rm, int nn, int n
 // Pre-smoothing, residual and full weighting (as kh_pre_w) on full rows:
 // coarse column J sits on the even local column 2J + 2; its weights take y
 // at local columns 2J + 1, 2J + 2, 2J + 3.
+// (at CPL = 4 in FP32, three blocks per SM: 80 registers, 12 bytes of spill;
+// 0.155 ms against 0.182 ms on the 127^2 x 4096 level; the same bound on
+// kh_post_f spills 112 bytes and makes it slower, 0.62 against 0.50 ms)
 template <int D, typename T, int CPL>
-__global__ void __launch_bounds__(kHT) kh_pre_f(const T* __restrict__ r, T* __restrict__ rc, int64_t N, int n,
+__global__ void __launch_bounds__(kHT, (CPL == 4 && sizeof(T) == 4) ? 3 : 1) kh_pre_f(const T* __restrict__ r, T* __restrict__ rc, int64_t N, int n,
                                                 int nc, int rows, HeatK<D, T> C, T omega) {
     constexpr int NO = CPL >= 2 ? CPL / 2 : 1;   // coarse outputs per lane
     const int lane = threadIdx.x & 31;
