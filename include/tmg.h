@@ -492,6 +492,13 @@ const char *tmg_strerror(tmg_status status);
 /* Last CUDA error code seen by the library in this process (0 if none). */
 int tmg_last_cuda_error(void);
 
+/* Debug build only (the library compiled with -DTMG_BOUNDS): the number of
+ * out-of-range indices its kernels met since the last call, and the first
+ * (site << 40 | low 40 bits of the index; sites are listed in
+ * csrc/tmg_bounds.h), both cleared.  Each such access was skipped (a load
+ * gave 0).  Returns TMG_EUNSUPPORTED from the normal build. */
+tmg_status tmg_debug_bounds(unsigned *violations, unsigned long long *first);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 
 #include <new>
 
+#include "tmg_bounds.h"
 #include "tmg_nvtx.h"
 #include "tmg_plan.h"
 #include "tmg_setup_math.h"
@@ -737,5 +738,20 @@ const char* tmg_strerror(tmg_status s) {
 }
 
 int tmg_last_cuda_error(void) { return g_last_cuda; }
+
+tmg_status tmg_debug_bounds(unsigned* violations, unsigned long long* first) {
+    if (!violations || !first) return TMG_EINVAL;
+    *violations = 0;
+    *first = 0;
+    if (tmg::bounds_readers().empty()) return TMG_EUNSUPPORTED;
+    for (tmg::BoundsReader rd : tmg::bounds_readers()) {
+        unsigned c = 0;
+        unsigned long long f = 0;
+        if (rd(&c, &f) != 0) return TMG_ECUDA;
+        *violations += c;
+        if (*first == 0) *first = f;
+    }
+    return TMG_OK;
+}
 
 }  // extern "C"

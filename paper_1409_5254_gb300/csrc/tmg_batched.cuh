@@ -891,6 +891,7 @@ __global__ void __launch_bounds__(kTailNT) kb_cta_solve(const double* __restrict
         // the group's nlev levels down to m_i intervals)
         const int Ni = bi.m != nullptr ? bi.m[inst] << (nlev - 1) : Ng;
         const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(red + 32), Ni, nlev);
+        if (!tail_view_fits<T, D>(V, cta_smem)) continue;   // debug build: layout outside shared memory
         const int64_t nv = (int64_t)Ni * D;
         const LevelK<T, D>* lki = lk + inst * nlev;
         const Res0 R = res[inst];
@@ -978,6 +979,7 @@ __global__ void __launch_bounds__(kTailNT) kb_tail(const T* __restrict__ f, T* _
         // variable lengths: the instance's own intervals on level lt
         const int Ni = bi.m != nullptr ? bi.m[inst] << (nl - 1) : Nt;
         const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(kb_tail_smem), Ni, nl);
+        if (!tail_view_fits<T, D>(V, kb_tail_smem)) continue;   // debug build: layout outside shared memory
         const int64_t nv = (int64_t)Ni * D;
         const int64_t off = inst * slot;
         for (int64_t i = threadIdx.x; i < nv; i += kTailNT) {

@@ -47,6 +47,7 @@
 #include <vector>
 
 #include "../../include/tmg.h"
+#include "tmg_bounds.h"
 #include "tmg_nvtx.h"
 #include "tmg_setup_math.h"
 
@@ -132,10 +133,11 @@ template <int D, typename T>
 __device__ __forceinline__ void stencil_at(const T* __restrict__ x, int nn, int n, int i, int j, T (&c)[D],
                                            T (&nb)[D]) {
     const int o = i * n + j;
+    const bool ok = TMG_IN(o, nn, 43);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         const T* xk = x + (int64_t)k * nn;
-        c[k] = xk[o];
+        c[k] = ok ? xk[o] : T(0);
         T s = T(0);
         if (i > 0) s += xk[o - n];
         if (i + 1 < n) s += xk[o + n];
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(kRT) kh_resid(const T* __restrict__ F, const T
             const int i = rt.i0 + rr;
             if (i >= n) break;
             const int o = i * n + j;
+            if (!TMG_IN(o, nn, 37)) continue;
             T c[D], nb[D], gx[D];
             stencil_at<D, T>(um, nn, n, i, j, c, nb);
             apply_G<D, T>(C, c, nb, gx);
@@ -227,6 +230,7 @@ __global__ void __launch_bounds__(kRT) kh_init_pair(const double* __restrict__ F
             const int i = rt.i0 + rr;
             if (i >= n) break;
             const int o = i * n + j;
+            if (!TMG_IN(o, nn, 37)) continue;
             const double e = rt.m == 0 ? u0[o] : 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -328,6 +332,7 @@ __global__ void __launch_bounds__(kRT, 12) kh_update_pair(double* __restrict__ u
             const int i = rt.i0 + rr;
             if (i >= n) break;
             const int o = i * n + j;
+            if (!TMG_IN(o, nn, 37)) continue;
             float cv[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) cv[k] = cm[(int64_t)k * nn + o];
@@ -389,8 +394,9 @@ template <int D, typename T>
 __device__ __forceinline__ void r_at(const T* __restrict__ r, int nn, int n, int i, int j, T (&rv)[D]) {
     const bool in = (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
     const int o = in ? i * n + j : 0;
+    const bool ok = in && TMG_IN(o, nn, 30);
 #pragma unroll
-    for (int k = 0; k < D; ++k) rv[k] = in ? r[k * nn + o] : T(0);
+    for (int k = 0; k < D; ++k) rv[k] = ok ? r[k * nn + o] : T(0);
 }
 
 // d = omega Dinv r (the first Jacobi sweep from zero).
@@ -473,7 +479,7 @@ __global__ void __launch_bounds__(kHT) kh_pre_w(const T* __restrict__ r, T* __re
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
                         acc[k] += H[k];
-                        if (writer) rcm[k * ncc + I * nc + J] = acc[k] * T(0.0625);
+                        if (writer && TMG_IN(I * nc + J, ncc, 33)) rcm[k * ncc + I * nc + J] = acc[k] * T(0.0625);
                     }
                 }
                 if (i == f1) break;
@@ -540,8 +546,8 @@ __global__ void __launch_bounds__(kHT) kh_post_w(const T* __restrict__ r, const 
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const T* ck = cm + k * ncc;
-                q[k] = (ia && jin) ? ck[Ia * nc + Jl] : T(0);
-                q2[k] = (ib && jin) ? ck[Ib * nc + Jl] : T(0);
+                q[k] = (ia && jin && TMG_IN(Ia * nc + Jl, ncc, 32)) ? ck[Ia * nc + Jl] : T(0);
+                q2[k] = (ib && jin && TMG_IN(Ib * nc + Jl, ncc, 32)) ? ck[Ib * nc + Jl] : T(0);
                 q1[k] = (lane == 31 && ia && jin1) ? ck[Ia * nc + Jl + 1] : T(0);
                 q12[k] = (lane == 31 && ib && jin1) ? ck[Ib * nc + Jl + 1] : T(0);
             }
@@ -605,11 +611,11 @@ __global__ void __launch_bounds__(kHT) kh_post_w(const T* __restrict__ r, const 
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const T za = fma(omega, ya[k], xa[1][k]), zb = fma(omega, yb[k], xb[1][k]);
-                if (wa) {
+                if (wa && TMG_IN(i * n + ca, nn, 36)) {
                     T* p = oi + k * nn + ca;
                     *p = acc ? fma(alpha, za, *p) : alpha * za;
                 }
-                if (wb) {
+                if (wb && TMG_IN(i * n + cb, nn, 36)) {
                     T* p = oi + k * nn + cb;
                     *p = acc ? fma(alpha, zb, *p) : alpha * zb;
                 }
@@ -673,8 +679,9 @@ __device__ __forceinline__ void row_load(const T* __restrict__ rm, int nn, int n
         const int j = lc0 + q - 1;
         const bool in = live && (unsigned)i < (unsigned)n && (unsigned)j < (unsigned)n;
         const int o = in ? i * n + j : 0;
+        const bool ok = in && TMG_IN(o, nn, 31);
 #pragma unroll
-        for (int k = 0; k < D; ++k) v[q][k] = in ? rm[k * nn + o] : T(0);
+        for (int k = 0; k < D; ++k) v[q][k] = ok ? rm[k * nn + o] : T(0);
     }
 }
 
@@ -758,7 +765,7 @@ __global__ void __launch_bounds__(kHT, (CPL == 4 && sizeof(T) == 4) ? 3 : 1) kh_
 #pragma unroll
                         for (int k = 0; k < D; ++k) {
                             acc[o][k] += H[o][k];
-                            if (wr) rcm[k * ncc + I * nc + J] = acc[o][k] * T(0.0625);
+                            if (wr && TMG_IN(I * nc + J, ncc, 34)) rcm[k * ncc + I * nc + J] = acc[o][k] * T(0.0625);
                         }
                     }
                 }
@@ -830,11 +837,11 @@ __global__ void __launch_bounds__(kHT) kh_post_f(const T* __restrict__ r, const 
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
                     const T* ck = cm + k * ncc;
-                    const T va = (ia && jin) ? ck[Ia * nc + J] : T(0);
+                    const T va = (ia && jin && TMG_IN(Ia * nc + J, ncc, 35)) ? ck[Ia * nc + J] : T(0);
                     if (a & 1) {
                         cr[t][k] = va;
                     } else {
-                        const T vb = (ib && jin) ? ck[Ib * nc + J] : T(0);
+                        const T vb = (ib && jin && TMG_IN(Ib * nc + J, ncc, 35)) ? ck[Ib * nc + J] : T(0);
                         cr[t][k] = T(0.5) * (va + vb);
                     }
                 }
@@ -885,7 +892,7 @@ __global__ void __launch_bounds__(kHT) kh_post_f(const T* __restrict__ r, const 
                 for (int k = 0; k < D; ++k) e[k] = rv[q][k] - gx[k];
                 apply_Dinv<D, T>(C, e, y);
                 const int j = j0 + q;
-                if (live && (unsigned)j < (unsigned)n) {
+                if (live && (unsigned)j < (unsigned)n && TMG_IN(i * n + j, nn, 36)) {
 #pragma unroll
                     for (int k = 0; k < D; ++k) {
                         const T z = fma(omega, y[k], x[1][q][k]);
@@ -942,6 +949,7 @@ __global__ void __launch_bounds__(kRT) kh_restrict_time(const T* __restrict__ g,
             const int i = rt.i0 + rr;
             if (i >= n) break;
             const int o = i * n + j;
+            if (!TMG_IN(o, nn, 37)) continue;
             T a[D], b[D];
 #pragma unroll
             for (int l = 0; l < D; ++l) {
@@ -978,6 +986,7 @@ __global__ void __launch_bounds__(kRT) kh_prolong_time(const T* __restrict__ uc,
             const int i = rt.i0 + rr;
             if (i >= n) break;
             const int o = i * n + j;
+            if (!TMG_IN(o, nn, 37)) continue;
             T cv[D];
 #pragma unroll
             for (int l = 0; l < D; ++l) cv[l] = c[(int64_t)l * nn + o];

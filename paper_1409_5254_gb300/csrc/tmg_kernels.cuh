@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "tmg_bounds.h"
+
 #include <type_traits>
 
 namespace tmg {
@@ -187,10 +189,14 @@ struct VecIO {
     }
 };
 
+// The level-vector helpers take the number of valid elements nq of their
+// array (pairs, intervals, groups of M); the debug build checks q against it
+// (q >= 0 only when nq < 0) and skips an access outside.
 template <typename T, int D>
-__device__ __forceinline__ void load_pair(const T* __restrict__ base, int64_t q, bool ok, T (&x)[2][D]) {
+__device__ __forceinline__ void load_pair(const T* __restrict__ base, int64_t q, bool ok, T (&x)[2][D],
+                                          int64_t nq = -1) {
     T v[2 * D];
-    if (ok) {
+    if (ok && TMG_IN(q, nq < 0 ? INT64_MAX : nq, 1)) {
         VecIO<T, 2 * D>::load(base + q * 2 * D, v);
     } else {
 #pragma unroll
@@ -204,7 +210,8 @@ __device__ __forceinline__ void load_pair(const T* __restrict__ base, int64_t q,
 }
 
 template <typename T, int D>
-__device__ __forceinline__ void store_pair(T* __restrict__ base, int64_t q, const T (&x)[2][D]) {
+__device__ __forceinline__ void store_pair(T* __restrict__ base, int64_t q, const T (&x)[2][D], int64_t nq = -1) {
+    if (!TMG_IN(q, nq < 0 ? INT64_MAX : nq, 2)) return;
     T v[2 * D];
 #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -215,8 +222,9 @@ __device__ __forceinline__ void store_pair(T* __restrict__ base, int64_t q, cons
 }
 
 template <typename T, int D>
-__device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t q, bool ok, T (&x)[D]) {
-    if (ok) {
+__device__ __forceinline__ void load_one(const T* __restrict__ base, int64_t q, bool ok, T (&x)[D],
+                                         int64_t nq = -1) {
+    if (ok && TMG_IN(q, nq < 0 ? INT64_MAX : nq, 3)) {
         VecIO<T, D>::load(base + q * D, x);
     } else {
 #pragma unroll
@@ -487,9 +495,10 @@ __device__ __forceinline__ void prolong_add2(const Xfer<T, D>& X, const T (&uc)[
 }
 
 template <typename T, int D, int M>
-__device__ __forceinline__ void load_m(const T* __restrict__ base, int64_t q, bool ok, T (&x)[M][D]) {
+__device__ __forceinline__ void load_m(const T* __restrict__ base, int64_t q, bool ok, T (&x)[M][D],
+                                       int64_t nq = -1) {
     T v[M * D];
-    if (ok) {
+    if (ok && TMG_IN(q, nq < 0 ? INT64_MAX : nq, 4)) {
         VecIO<T, M * D>::load(base + q * M * D, v);
     } else {
 #pragma unroll
@@ -502,7 +511,8 @@ __device__ __forceinline__ void load_m(const T* __restrict__ base, int64_t q, bo
 }
 
 template <typename T, int D, int M>
-__device__ __forceinline__ void store_m(T* __restrict__ base, int64_t q, const T (&x)[M][D]) {
+__device__ __forceinline__ void store_m(T* __restrict__ base, int64_t q, const T (&x)[M][D], int64_t nq = -1) {
+    if (!TMG_IN(q, nq < 0 ? INT64_MAX : nq, 5)) return;
     T v[M * D];
 #pragma unroll
     for (int i = 0; i < M; ++i)
@@ -1851,6 +1861,24 @@ __device__ __forceinline__ TailView<T, D> tail_view(T* p, int64_t Nt, int nl) {
     return V;
 }
 
+// Debug build: the view ends inside the dynamic shared memory that starts
+// at dyn (the launch's size); false (and recorded) otherwise, and the
+// kernel skips the work.
+template <typename T, int D>
+__device__ __forceinline__ bool tail_view_fits(const TailView<T, D>& V, const void* dyn) {
+#ifdef TMG_BOUNDS
+    unsigned dyn_bytes;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    const long long end = (long long)(reinterpret_cast<const char*>(V.scanB + 2 * (kTailNT / 32)) -
+                                      reinterpret_cast<const char*>(dyn));
+    return TMG_IN(end - 1, (long long)dyn_bytes, 10);
+#else
+    (void)V;
+    (void)dyn;
+    return true;
+#endif
+}
+
 // One cycle on the levels held in V (tail index j = 0..nl-1), from a zero
 // start (or, with init0, from the iterate V.u[0] holds): V (gamma = 1) or W
 // (gamma = 2) recursion written as a loop, the coarsest level solved exactly.
@@ -1964,6 +1992,7 @@ __global__ void __launch_bounds__(kTailNT) k_tail(const T* __restrict__ f_in, T*
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(16) unsigned char tail_smem[];
     const TailView<T, D> V = tail_view<T, D>(reinterpret_cast<T*>(tail_smem), Nt, nl);
+    if (!tail_view_fits<T, D>(V, tail_smem)) return;
     for (int64_t i = threadIdx.x; i < Nt * D; i += kTailNT) {
         V.f[0][i] = f_in[i];
         if (u_init != nullptr) V.u[0][i] = u_init[i];

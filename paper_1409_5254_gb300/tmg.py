@@ -48,17 +48,19 @@ EXPORTS = ["tmg_opts_default", "tmg_setup", "tmg_solve", "tmg_solve_host", "tmg_
            "tmg_last_cuda_error", "tmg_setup_batched", "tmg_solve_batched", "tmg_adjoint_batched",
            "tmg_stats_batched", "tmg_error_vs_fp64_batched", "tmg_batch_info", "tmg_batch_group_info", "tmg_batch_tune_info", "tmg_destroy_batched",
            "tmg_heat_setup", "tmg_heat_solve", "tmg_heat_cycle", "tmg_heat_residual", "tmg_heat_stats",
-           "tmg_heat_info", "tmg_heat_profile", "tmg_heat_destroy"]
+           "tmg_heat_info", "tmg_heat_profile", "tmg_heat_destroy", "tmg_debug_bounds"]
 
 
 def library_path() -> str:
-    return build_ext.LIB
+    """The library in use: the debug build with bounds checks when the
+    environment sets TMG_BOUNDS=1, else the normal build."""
+    return build_ext.LIB_BOUNDS if os.environ.get("TMG_BOUNDS") == "1" else build_ext.LIB
 
 
 def _lib():
     global _LIB
     if _LIB is None:
-        path = build_ext.LIB
+        path = library_path()
         if not os.path.exists(path):
             raise ImportError(f"libtmg.so not built ({path}); run __graft_entry__.build() "
                               "or python -m paper_1409_5254_gb300.build_ext")
@@ -126,6 +128,8 @@ def _lib():
             getattr(L, name).restype = ctypes.c_int
         L.tmg_heat_destroy.argtypes = [_vp]
         L.tmg_heat_destroy.restype = None
+        L.tmg_debug_bounds.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_ulonglong)]
+        L.tmg_debug_bounds.restype = ctypes.c_int
         L.tmg_strerror.argtypes = [ctypes.c_int]
         L.tmg_strerror.restype = ctypes.c_char_p
         L.tmg_last_cuda_error.argtypes = []
@@ -135,6 +139,17 @@ def _lib():
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
+
+
+def debug_bounds():
+    """(violations, first record) of the debug build's bounds checks since
+    the last call (tmg_debug_bounds), or None from the normal build."""
+    c, f = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+    st = _lib().tmg_debug_bounds(ctypes.byref(c), ctypes.byref(f))
+    if st == TMG_EUNSUPPORTED:
+        return None
+    _check(st, "tmg_debug_bounds")
+    return c.value, f.value
 
 
 def _check(status: int, where: str, ok=(TMG_OK,)):

@@ -23,3 +23,17 @@ def load_golden(name):
                 continue
             rows.append([[float(x) for x in field.split()] for field in line.split(";")])
     return rows
+
+
+@pytest.fixture(autouse=True)
+def _bounds_clean(request):
+    """Under the debug build with bounds checks (TMG_BOUNDS=1), every GPU test
+    must leave no out-of-range index behind in any kernel it ran."""
+    yield
+    if os.environ.get("TMG_BOUNDS") != "1" or request.node.get_closest_marker("gpu") is None:
+        return
+    from paper_1409_5254_gb300 import tmg
+    res = tmg.debug_bounds()
+    assert res is not None, "TMG_BOUNDS=1 but the loaded library has no bounds checks"
+    count, first = res
+    assert count == 0, f"{count} out-of-range indices; first: site {first >> 40}, index {first & ((1 << 40) - 1)}"
