@@ -914,6 +914,75 @@ __global__ void __launch_bounds__(kHT) kh_post_f(const T* __restrict__ r, const 
     }
 }
 
+// Time residual on full rows (as kh_resid with TIME, no norm, stored in T):
+// g = F + a e_{m-1} - G u, with the three-row window of u in registers and
+// the loads of row i + 2 issued before row i is computed.
+template <int D, typename T, int CPL>
+__global__ void __launch_bounds__(kHT) kh_resid_f(const T* __restrict__ F, const T* __restrict__ u,
+                                                  const double* __restrict__ u0, T* __restrict__ g, int64_t N, int n,
+                                                  int rows, HeatK<D, T> C) {
+    const int lane = threadIdx.x & 31;
+    const RowGeom<CPL> G(n, lane);
+    const bool last = G.ls == G.SW - 1;
+    const int nn = n * n;
+    const int chunks = (n + rows - 1) / rows;
+    const int64_t groups = (N + G.IPW - 1) / G.IPW;
+    const int64_t tasks = groups * chunks;
+    const int64_t nw = ((int64_t)gridDim.x * kHT) >> 5;
+    const int lc0 = CPL * G.ls;
+    for (int64_t w = ((int64_t)blockIdx.x * kHT + threadIdx.x) >> 5; w < tasks; w += nw) {
+        const int64_t gi = w / chunks;
+        const int ch = (int)(w - gi * chunks);
+        const int64_t m = gi * G.IPW + G.seg;
+        const bool live = m < N;
+        const int i0 = ch * rows, i1 = min(i0 + rows, n);
+        const int64_t base = (live ? m : 0) * D * (int64_t)nn;
+        const T* um = u + base;
+        const T* Fm = F + base;
+        const T* up = (live && m > 0) ? um - D * (int64_t)nn : nullptr;   // previous interval
+        T* gm = g + base;
+        T x[3][CPL][D], pf[CPL][D];
+        row_load<D, T, CPL>(um, nn, n, i0 - 1, lc0, live, x[0]);
+        row_load<D, T, CPL>(um, nn, n, i0, lc0, live, x[1]);
+        row_load<D, T, CPL>(um, nn, n, i0 + 1, lc0, live, x[2]);
+        for (int i = i0; i < i1; ++i) {
+            row_load<D, T, CPL>(um, nn, n, i + 2, lc0, live, pf);
+            T fv[CPL][D], pv[CPL][D];
+            row_load<D, T, CPL>(Fm, nn, n, i, lc0, live, fv);
+            if (up != nullptr) row_load<D, T, CPL>(up, nn, n, i, lc0, live, pv);
+            T lt[CPL][D], rt[CPL][D];
+            row_neighbours<D, T, CPL>(x[1], last, lt, rt);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const int j = lc0 + q - 1;
+                T nb[D], gx[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) nb[k] = (x[0][q][k] + x[2][q][k]) + (lt[q][k] + rt[q][k]);
+                apply_G<D, T>(C, x[1][q], nb, gx);
+                T e = T(0);
+                if (up != nullptr) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) e += pv[q][k];
+                } else if (m == 0 && u0 != nullptr && (unsigned)j < (unsigned)n && TMG_IN(i * n + j, nn, 38)) {
+                    e = (T)u0[i * n + j];
+                }
+                if (live && (unsigned)j < (unsigned)n && TMG_IN(i * n + j, nn, 38)) {
+#pragma unroll
+                    for (int k = 0; k < D; ++k) gm[k * nn + i * n + j] = fv[q][k] + ((k & 1) ? -e : e) - gx[k];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    x[0][q][k] = x[1][q][k];
+                    x[1][q][k] = x[2][q][k];
+                    x[2][q][k] = pf[q][k];
+                }
+        }
+    }
+}
+
 // One grid point: G_tau is its point block, solved exactly.
 // out = alpha Dinv r (acc = 0) or out += alpha Dinv r (acc = 1).
 template <int D, typename T>
@@ -1189,8 +1258,22 @@ struct HeatImpl {
     static const T* resid(tmg_heat* H, const T* F, const T* u, const double* u0, int64_t N, double tau) {
         HeatBufs<T>& b = B(H);
         ++g_launches;
-        kh_resid<D, T, T, true, false, false><<<grid_rows(H, N * host_row_blocks(H->n)), kRT, 0, H->s>>>(
-            F, u, u0, b.g, nullptr, N, H->n, heat_consts<D, T>(tau, H->n), nullptr);
+        const int n = H->n;
+        const HeatK<D, T> C = heat_consts<D, T>(tau, n);
+        if (full_rows(n) && n > 1) {
+            const int64_t sets = row_sets(N, n, n, kPostStride);
+            const int rows = chunk_rows(H, sets, n, kPostRows);
+            const int gsz = grid_warps(H, sets * ((n + rows - 1) / rows));
+            if (n + 1 <= 32)
+                kh_resid_f<D, T, 1><<<gsz, kHT, 0, H->s>>>(F, u, u0, b.g, N, n, rows, C);
+            else if (n + 1 == 64)
+                kh_resid_f<D, T, 2><<<gsz, kHT, 0, H->s>>>(F, u, u0, b.g, N, n, rows, C);
+            else
+                kh_resid_f<D, T, 4><<<gsz, kHT, 0, H->s>>>(F, u, u0, b.g, N, n, rows, C);
+        } else {
+            kh_resid<D, T, T, true, false, false><<<grid_rows(H, N * host_row_blocks(n)), kRT, 0, H->s>>>(
+                F, u, u0, b.g, nullptr, N, n, C, nullptr);
+        }
         return b.g;
     }
 
@@ -1408,10 +1491,7 @@ tmg_status profile_heat(tmg_heat* H, const double* F, const double* u0, double* 
     auto level0 = [&](auto* tag, auto& b, const auto* rhs, const auto* uu, auto* out) {
         using T = typename std::remove_pointer<decltype(tag)>::type;
         const HeatK<D, T> C = heat_consts<D, T>(H->tau, n);
-        ms[0] = timed([&] {
-            kh_resid<D, T, T, true, false, false><<<grid_rows(H, N * host_row_blocks(n)), kRT, 0, H->s>>>(
-                rhs, uu, nullptr, b.g, nullptr, N, n, C, nullptr);
-        });
+        ms[0] = timed([&] { HeatImpl<D, T>::resid(H, rhs, uu, nullptr, N, H->tau); });
         if (nc > 0) {
             ms[1] = timed([&] { HeatImpl<D, T>::pre(H, rhs, b.rs[1], N, n, nc, C); });
             ms[2] = timed([&] { HeatImpl<D, T>::post(H, rhs, b.ys[1], out, N, n, nc, C, (T)kOmegaT, 1); });
