@@ -32,7 +32,9 @@
 // bilinear prolongation of the coarse correction, applies the second sweep
 // and writes (or accumulates into the time iterate) the result.  Per spatial
 // level: read r twice, the coarse values once, write the result once.  Both
-// stream a warp down a 64-column strip with the stencil's rows in registers.
+// stream a warp down the rows of one interval with the stencil's rows in
+// registers: whole rows (4, 2 or 1 columns per lane) for grids up to 127
+// points a side, overlapping 64-column strips above.
 // In the mixed form the residual of the FP64 iterate is kept as a float pair
 // and updated by r -= L c after every cycle (float-pair arithmetic on the
 // exact FP32 correction), with one FP64 residual to confirm convergence.
