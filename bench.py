@@ -571,6 +571,7 @@ def run_ours(args):
 
 
 HEAT_N, HEAT_NX, HEAT_P = 4096, 127, 1   # space-time heat: intervals, interior grid points a side, degree
+HEAT_NU, HEAT_NUC = (2, 2), 1             # V(2,2) in time (as the long horizon), one V-cycle on the last interval
 
 
 def _space_time_heat(dev, stream, nsteps, torch, hbm_peak, peak_kind, eager):
@@ -593,11 +594,12 @@ def _space_time_heat(dev, stream, nsteps, torch, hbm_peak, peak_kind, eager):
     nc = (n - 1) // 2
     dofs = Fd.numel()
     out = {"unit": "DoF/s", "grid": f"{n}x{n}", "N": N, "p_t": HEAT_P, "tau": tau, "dofs": dofs, "tol": TOL,
+           "cycle": f"V{HEAT_NU} in time, one spatial V(1,1)-cycle per block solve, nu_c = {HEAT_NUC}",
            "data": "synthetic: f(t,x) = sum of 3 space fields U(-1,1) x sin(2 pi m t), u0 ~ U(-1,1)"}
     u_mixed = None
     for prec, steps in (("mixed", nsteps), ("fp64", 3)):
         with tmg.HeatPlan(HEAT_P, tau, n, N, tol=TOL, max_cycles=100, precision=prec, use_graph=not eager,
-                          stream=stream) as hp:
+                          nu1=HEAT_NU[0], nu2=HEAT_NU[1], nu_c=HEAT_NUC, stream=stream) as hp:
             hp.solve(Fd, u0d, u)
             times = []
             for _ in range(steps):
@@ -640,6 +642,24 @@ def _space_time_heat(dev, stream, nsteps, torch, hbm_peak, peak_kind, eager):
                     "pair_update": round(upd_bytes / (prof["update"] * 1e-3) / 1e9 / hbm_peak, 3),
                     "note": "algorithmic bytes / event time / measured HBM copy bandwidth"}
             out[prec] = res
+    # other sweep counts in time, mixed form
+    variants = {}
+    for nu in ((1, 1), (3, 3)):
+        with tmg.HeatPlan(HEAT_P, tau, n, N, tol=TOL, max_cycles=100, precision="mixed", use_graph=not eager,
+                          nu1=nu[0], nu2=nu[1], nu_c=HEAT_NUC, stream=stream) as hp:
+            hp.solve(Fd, u0d, u)
+            times = []
+            for _ in range(max(3, nsteps // 2)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                hp.solve(Fd, u0d, u)
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            st = hp.stats()
+            variants[f"V({nu[0]},{nu[1]})"] = {"ms_per_step": round(statistics.median(times), 3), "cycles": st.cycles,
+                                               "rel_res_fp64": st.rel_res}
+    out["mixed_variants"] = variants
     out["value"] = out["mixed"]["value"]
     del Fd, u0d, u, u_mixed
     torch.cuda.empty_cache()
@@ -655,11 +675,12 @@ def heat_cpu_baseline(sample_N: int = 16):
     tau, F, u0 = inputs.heat_problem(1, HEAT_N, HEAT_P, HEAT_NX)
     F = F[:sample_N].copy()
     t0 = time.perf_counter()
-    _, hist = oheat.solve(HEAT_P, tau, HEAT_NX, F, u0, tol=TOL, max_cycles=100)
+    _, hist = oheat.solve(HEAT_P, tau, HEAT_NX, F, u0, tol=TOL, max_cycles=100, nu1=HEAT_NU[0], nu2=HEAT_NU[1],
+                          nu_c=HEAT_NUC)
     t = time.perf_counter() - t0
     return {"value": F.size / t, "unit": "DoF/s", "cores": 1, "kind": "oracle",
             "sample": f"first {sample_N} of the 4096 intervals, {HEAT_NX}x{HEAT_NX} grid, textbook space-time "
-                      f"cycle to {TOL} ({len(hist) - 1} cycles), {t:.2f} s"}
+                      f"V{HEAT_NU} cycle to {TOL} ({len(hist) - 1} cycles), {t:.2f} s"}
 
 
 def _time_batch(batch, f, u0, u, steps, stream, torch):

@@ -64,7 +64,7 @@ def test_cycle_iterates(p, n, N):
                 assert _rel(got, want) <= TOL_ITER, (p, n, N, _rel(got, want))
 
 
-@pytest.mark.parametrize("nu1,nu2,nu_c", [(2, 1, 1), (0, 2, 3), (1, 0, 2)])
+@pytest.mark.parametrize("nu1,nu2,nu_c", [(2, 1, 1), (0, 2, 3), (1, 0, 2), (2, 2, 1), (3, 3, 1)])
 def test_cycle_smoothing_counts(nu1, nu2, nu_c):
     H = _H()
     p, n, N = 1, 15, 16
