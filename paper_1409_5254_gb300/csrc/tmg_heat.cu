@@ -985,6 +985,178 @@ __global__ void __launch_bounds__(kHT) kh_resid_f(const T* __restrict__ F, const
     }
 }
 
+// ----------------------------------------------------- small-grid V-cycle
+// The whole spatial V(1,1)-cycle of a grid of at most kSmallN points a side
+// (and every coarser level down to one point) in shared memory, one CTA per
+// interval: the same steps as kh_pre_f / kh_post_f / kh_point_solve level by
+// level, with every level's right-hand side, iterate and a scratch array
+// on chip.  out = alpha x (acc = 0) or out += alpha x (acc = 1).
+constexpr int kSmallN = 31;
+constexpr int kSmallLevels = 5;   // 31, 15, 7, 3, 1
+constexpr int kSmallNT = 256;
+
+template <int D, typename T>
+struct SmallK {
+    HeatK<D, T> k[kSmallLevels];
+    int n[kSmallLevels];
+    int nl;   // levels, the last of one point
+};
+
+template <int D>
+__host__ __device__ constexpr int small_values() {   // values per array over the levels 31, 15, 7, 3, 1
+    return D * (31 * 31 + 15 * 15 + 7 * 7 + 3 * 3 + 1);
+}
+
+template <typename T>
+size_t small_smem(int D) {
+    return (size_t)3 * D * (31 * 31 + 15 * 15 + 7 * 7 + 3 * 3 + 1) * sizeof(T);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kSmallNT) kh_vsmall(const T* __restrict__ rhs, T* __restrict__ out, int64_t N,
+                                                      SmallK<D, T> S, T omega, T alpha, int acc) {
+    extern __shared__ __align__(16) unsigned char small_smem_raw[];
+    T* R = reinterpret_cast<T*>(small_smem_raw);   // right-hand sides of every level
+    T* X = R + small_values<D>();                   // iterates
+    T* Y = X + small_values<D>();                   // scratch
+    int off[kSmallLevels];
+    {
+        int o = 0;
+        for (int l = 0; l < S.nl; ++l) {
+            off[l] = o;
+            o += D * S.n[l] * S.n[l];
+        }
+    }
+    const int n0 = S.n[0], nn0 = n0 * n0;
+    for (int64_t m = blockIdx.x; m < N; m += gridDim.x) {
+        const T* rm = rhs + m * D * (int64_t)nn0;
+        for (int p = threadIdx.x; p < D * nn0; p += kSmallNT)
+            if (TMG_IN(p, D * nn0, 44)) R[p] = rm[p];
+        __syncthreads();
+        // down: x = omega Dinv r, y = r - G x, r_{l+1} = FW(y)
+        for (int l = 0; l + 1 < S.nl; ++l) {
+            const int n = S.n[l], nn = n * n, nc = S.n[l + 1], ncc = nc * nc;
+            const HeatK<D, T>& C = S.k[l];
+            T* r = R + off[l];
+            T* x = X + off[l];
+            T* y = Y + off[l];
+            for (int p = threadIdx.x; p < nn; p += kSmallNT) {
+                T v[D], d[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) v[k] = r[k * nn + p];
+                apply_Dinv<D, T>(C, v, d);
+#pragma unroll
+                for (int k = 0; k < D; ++k) x[k * nn + p] = omega * d[k];
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < nn; p += kSmallNT) {
+                const int i = p / n, j = p - i * n;
+                T c[D], nb[D], gx[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const T* xk = x + k * nn;
+                    c[k] = xk[p];
+                    T s = T(0);
+                    if (i > 0) s += xk[p - n];
+                    if (i + 1 < n) s += xk[p + n];
+                    if (j > 0) s += xk[p - 1];
+                    if (j + 1 < n) s += xk[p + 1];
+                    nb[k] = s;
+                }
+                apply_G<D, T>(C, c, nb, gx);
+#pragma unroll
+                for (int k = 0; k < D; ++k) y[k * nn + p] = r[k * nn + p] - gx[k];
+            }
+            __syncthreads();
+            T* rc = R + off[l + 1];
+            for (int p = threadIdx.x; p < ncc; p += kSmallNT) {
+                const int I = p / nc, J = p - I * nc;
+                const int q = (2 * I + 1) * n + (2 * J + 1);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const T* Yk = y + k * nn;
+                    T s = T(4) * Yk[q];
+                    s += T(2) * ((Yk[q - n] + Yk[q + n]) + (Yk[q - 1] + Yk[q + 1]));
+                    s += (Yk[q - n - 1] + Yk[q - n + 1]) + (Yk[q + n - 1] + Yk[q + n + 1]);
+                    rc[k * ncc + p] = s * T(0.0625);
+                }
+            }
+            __syncthreads();
+        }
+        // one grid point: G is its point block, solved exactly
+        {
+            const int l = S.nl - 1;
+            if (threadIdx.x == 0) {
+                T v[D], d[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) v[k] = R[off[l] + k];
+                apply_Dinv<D, T>(S.k[l], v, d);
+#pragma unroll
+                for (int k = 0; k < D; ++k) X[off[l] + k] = d[k];
+            }
+            __syncthreads();
+        }
+        // up: x += P x_c, z = x + omega Dinv (r - G x)
+        for (int l = S.nl - 2; l >= 0; --l) {
+            const int n = S.n[l], nn = n * n, nc = S.n[l + 1], ncc = nc * nc;
+            const HeatK<D, T>& C = S.k[l];
+            const T* r = R + off[l];
+            T* x = X + off[l];
+            T* z = Y + off[l];
+            const T* xc = X + off[l + 1];
+            for (int p = threadIdx.x; p < nn; p += kSmallNT) {
+                const int i = p / n, j = p - i * n;
+                const bool ri = i & 1, rj = j & 1;
+                const int I = ri ? (i - 1) / 2 : i / 2 - 1, J = rj ? (j - 1) / 2 : j / 2 - 1;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const T* ck = xc + k * ncc;
+                    auto cv = [&](int a, int b) -> T {
+                        return (a < 0 || b < 0 || a >= nc || b >= nc) ? T(0) : ck[a * nc + b];
+                    };
+                    T v;
+                    if (ri && rj) v = cv(I, J);
+                    else if (ri) v = T(0.5) * (cv(I, J) + cv(I, J + 1));
+                    else if (rj) v = T(0.5) * (cv(I, J) + cv(I + 1, J));
+                    else v = T(0.5) * (T(0.5) * (cv(I, J) + cv(I + 1, J)) + T(0.5) * (cv(I, J + 1) + cv(I + 1, J + 1)));
+                    x[k * nn + p] += v;
+                }
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < nn; p += kSmallNT) {
+                const int i = p / n, j = p - i * n;
+                T c[D], nb[D], gx[D], e[D], d[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const T* xk = x + k * nn;
+                    c[k] = xk[p];
+                    T s = T(0);
+                    if (i > 0) s += xk[p - n];
+                    if (i + 1 < n) s += xk[p + n];
+                    if (j > 0) s += xk[p - 1];
+                    if (j + 1 < n) s += xk[p + 1];
+                    nb[k] = s;
+                }
+                apply_G<D, T>(C, c, nb, gx);
+#pragma unroll
+                for (int k = 0; k < D; ++k) e[k] = r[k * nn + p] - gx[k];
+                apply_Dinv<D, T>(C, e, d);
+#pragma unroll
+                for (int k = 0; k < D; ++k) z[k * nn + p] = fma(omega, d[k], c[k]);
+            }
+            __syncthreads();
+            if (l > 0) {   // the coarse level's result becomes its iterate for the next prolongation
+                for (int p = threadIdx.x; p < D * nn; p += kSmallNT) x[p] = z[p];
+                __syncthreads();
+            }
+        }
+        T* om = out + m * D * (int64_t)nn0;
+        for (int p = threadIdx.x; p < D * nn0; p += kSmallNT)
+            if (TMG_IN(p, D * nn0, 45)) om[p] = acc ? fma(alpha, Y[p], om[p]) : alpha * Y[p];
+        __syncthreads();
+    }
+}
+
 // One grid point: G_tau is its point block, solved exactly.
 // out = alpha Dinv r (acc = 0) or out += alpha Dinv r (acc = 1).
 template <int D, typename T>
@@ -1190,6 +1362,17 @@ struct HeatImpl {
             kh_point_solve<D, T><<<grid_of(H, N), kHT, 0, H->s>>>(rhs, out, N, C, alpha, acc);
             return;
         }
+        if (n <= kSmallN) {   // this level and all coarser ones in one kernel, in shared memory
+            SmallK<D, T> S;
+            S.nl = H->ns - sl;
+            for (int l = 0; l < S.nl; ++l) {
+                S.n[l] = H->nsz[sl + l];
+                S.k[l] = heat_consts<D, T>(tau, S.n[l]);
+            }
+            const int64_t g = N < H->max_blocks ? N : H->max_blocks;
+            kh_vsmall<D, T><<<(int)g, kSmallNT, small_smem<T>(D), H->s>>>(rhs, out, N, S, (T)kOmegaS, alpha, acc);
+            return;
+        }
         const int nc = H->nsz[sl + 1];
         pre(H, rhs, b.rs[sl + 1], N, n, nc, C);
         vcycle(H, sl + 1, b.rs[sl + 1], N, tau, b.ys[sl + 1], T(1), 0);
@@ -1257,6 +1440,11 @@ struct HeatImpl {
     }
 
     // Time residual of level l (u0 only at level 0) into b.g.
+    static cudaError_t set_smem() {
+        return cudaFuncSetAttribute(kh_vsmall<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)small_smem<T>(D));
+    }
+
     static const T* resid(tmg_heat* H, const T* F, const T* u, const double* u0, int64_t N, double tau) {
         HeatBufs<T>& b = B(H);
         ++g_launches;
@@ -1531,6 +1719,21 @@ tmg_status profile_heat_d(tmg_heat* H, const double* F, const double* u0, double
     }
 }
 
+cudaError_t set_smem_d(int d, bool fp64) {
+    switch (d) {
+#define TMG_HEAT_SMEM(DD) \
+    case DD: return fp64 ? HeatImpl<DD, double>::set_smem() : HeatImpl<DD, float>::set_smem();
+        TMG_HEAT_SMEM(1)
+        TMG_HEAT_SMEM(2)
+        TMG_HEAT_SMEM(3)
+        TMG_HEAT_SMEM(4)
+        TMG_HEAT_SMEM(5)
+        TMG_HEAT_SMEM(6)
+#undef TMG_HEAT_SMEM
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 tmg_status run_heat_d(tmg_heat* H, const double* F, const double* u0, double* u, bool solve) {
     switch (H->d) {
         case 1: return run_heat<1>(H, F, u0, u, solve);
@@ -1594,7 +1797,8 @@ tmg_status tmg_heat_setup(tmg_heat** out, int p_t, double tau, int n, int64_t N,
     }
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        set_smem_d(H->d, H->precision == TMG_FP64) != cudaSuccess) {
         tmg_heat_destroy(H);
         return TMG_ECUDA;
     }
