@@ -95,3 +95,34 @@ def test_batched_setup_rejects_bad_arguments_before_touching_the_gpu():
     assert call(*ok, schedule=3) == tmg.TMG_EINVAL
     assert call(*ok, nu1=0, nu2=0) == tmg.TMG_EINVAL
     assert call([], [], [], []) == tmg.TMG_EINVAL             # no instances
+
+
+def test_heat_setup_rejects_bad_arguments_before_any_device_call():
+    """tmg_heat_setup validates sizes and options on the host and returns
+    TMG_EINVAL before it touches the device (runs without a GPU)."""
+    import ctypes
+    from paper_1409_5254_gb300 import tmg
+    L = tmg._lib()
+    o = tmg._opts(precision="mixed")
+    h = ctypes.c_void_p()
+    bad = [(1, 1e-3, 6, 16, 2),      # n + 1 not a power of two
+           (1, 1e-3, 7, 12, 2),      # N not a power of two
+           (6, 1e-3, 7, 16, 2),      # degree above 5
+           (1, 0.0, 7, 16, 2),       # tau <= 0
+           (1, 1e-3, 1 << 14, 16, 2),  # n too large for 32-bit offsets
+           (1, 1e-3, 7, 16, 0)]      # nu_c < 1
+    for p, tau, n, N, nuc in bad:
+        st = L.tmg_heat_setup(ctypes.byref(h), p, tau, n, N, ctypes.byref(o), nuc, None)
+        assert st == tmg.TMG_EINVAL, (p, tau, n, N, nuc, st)
+    o.gamma = 2
+    assert L.tmg_heat_setup(ctypes.byref(h), 1, 1e-3, 7, 16, ctypes.byref(o), 2, None) == tmg.TMG_EINVAL
+
+
+def test_debug_bounds_query_without_the_debug_build():
+    """The normal library has no bounds records: tmg_debug_bounds answers
+    TMG_EUNSUPPORTED (no device access)."""
+    import ctypes
+    from paper_1409_5254_gb300 import tmg
+    c, f = ctypes.c_uint(1), ctypes.c_ulonglong(1)
+    assert tmg._lib().tmg_debug_bounds(ctypes.byref(c), ctypes.byref(f)) == tmg.TMG_EUNSUPPORTED
+    assert c.value == 0 and f.value == 0
